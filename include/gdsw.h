@@ -1,0 +1,178 @@
+/*
+ * gdsw.h - C ABI of libgdsw, a GDSW two-level overlapping Schwarz preconditioner
+ * and the Krylov solves it accelerates, written for one NVIDIA B300 (sm_103a).
+ *
+ * Paper: Yamazaki, Heinlein, Rajamanickam, "An Experimental Study of Two-Level
+ * Schwarz Domain Decomposition Preconditioners on GPUs" (arXiv 2304.04876).
+ *
+ * The operator (Sec. III, Eq. 1):
+ *     M^-1 r = Phi A0^-1 Phi^T r + sum_s R_s^T A_s^-1 R_s r,   A0 = Phi^T A Phi,
+ * with the GDSW coarse basis of Eq. 2, Phi = [-A_II^-1 A_IGamma; I] Phi_Gamma.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices and partitions passed to gdsw_setup are HOST memory; the library
+ *    copies what it needs and never keeps the caller's pointers.
+ *  - Vector arguments of gdsw_apply / gdsw_spmv / gdsw_solve are DEVICE
+ *    pointers to n doubles, borrowed for the duration of the call; work is
+ *    enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *    default stream).  gdsw_apply and gdsw_spmv return once the work is
+ *    enqueued; gdsw_solve returns with the solution in place.
+ *  - gdsw_solve_host takes HOST vectors and includes the copies.
+ *  - A handle owns all device memory of one problem (factors, Phi, A0^-1,
+ *    Krylov workspace) until gdsw_destroy.  Handles are independent; one
+ *    handle must not be used from two host threads at once.
+ *  - Every call returns a gdsw_status; nothing aborts the process and no call
+ *    resets the device.  gdsw_last_error() gives a one-line description of
+ *    the most recent failure on the calling thread.
+ */
+#ifndef GDSW_H
+#define GDSW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GDSW_OK = 0,
+  GDSW_ERR_INVALID_ARG = 1,   /* malformed CSR / partition / options */
+  GDSW_ERR_OUT_OF_MEMORY = 2, /* a device allocation failed */
+  GDSW_ERR_BREAKDOWN = 3,     /* non-positive (IC, Cholesky) or zero (ILU) pivot */
+  GDSW_ERR_NOT_CONVERGED = 4, /* maxit reached, or NaN/Inf in the residual */
+  GDSW_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+  GDSW_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  GDSW_ERR_UNSUPPORTED = 7    /* valid input outside what this build handles */
+} gdsw_status;
+
+/* local solver A_s^-1 (Sec. V-B) */
+enum { GDSW_LOCAL_EXACT = 0, /* Cholesky of A_s, applied as its dense inverse   */
+       GDSW_LOCAL_IC0 = 1,   /* IC(0) by synchronous fixed-point sweeps          */
+       GDSW_LOCAL_ILU0 = 2   /* ILU(0) by synchronous fixed-point sweeps         */ };
+/* triangular solves of IC(0)/ILU(0) factors (Sec. V-B2, V-B3) */
+enum { GDSW_TRSV_LEVELSCHED = 0, GDSW_TRSV_JACOBI = 1 };
+/* storage/compute precision of the preconditioner (Sec. V-A2); the Krylov
+ * vectors, dot products, residual and the coarse solve stay FP64 */
+enum { GDSW_PREC_FP64 = 0, GDSW_PREC_FP32 = 1 };
+enum { GDSW_KRYLOV_PCG = 0, GDSW_KRYLOV_GMRES = 1 };
+enum { GDSW_COARSE_GDSW = 0, GDSW_COARSE_NONE = 1 };
+
+/* Square sparse matrix, CSR, host memory.  rowptr[n+1], colind[nnz] (0-based,
+ * strictly increasing within each row, diagonal stored), val[nnz].  The
+ * pattern must be structurally symmetric (it is the pattern of the
+ * incomplete factors). */
+typedef struct {
+  int32_t n;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+} gdsw_csr;
+
+/* Structured nonoverlapping decomposition.  Unknown d of node (i,j,k) is
+ * d + dofs_per_node*(i + nx*(j + ny*k)).  cut[a][0..ncut[a]) lists ascending
+ * separator node planes along axis a; a plane belongs to the block below it.
+ * Gamma = nodes on at least one plane (Sec. III). */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t dofs_per_node;
+  int32_t ncut[3];
+  const int32_t* cut[3];
+} gdsw_partition;
+
+typedef struct {
+  int32_t local_solver;   /* GDSW_LOCAL_*                 (default IC0)   */
+  int32_t trsv;           /* GDSW_TRSV_*                  (LEVELSCHED)    */
+  int32_t sweeps_factor;  /* fixed-point factor sweeps    (3)             */
+  int32_t sweeps_trsv;    /* Jacobi sweeps per triangle   (5)             */
+  int32_t overlap;        /* layers of algebraic overlap  (1)             */
+  int32_t precision;      /* GDSW_PREC_*                  (FP64)          */
+  int32_t krylov;         /* GDSW_KRYLOV_*                (PCG)           */
+  int32_t restart;        /* GMRES restart length         (30)            */
+  int32_t maxit;          /* iteration cap                (2000)          */
+  int32_t coarse;         /* GDSW_COARSE_*                (GDSW)          */
+  int32_t flexible;       /* PCG beta (r, z - z_old)/(r_old, z_old): 1 = on,
+                             0 = off, -1 = on exactly when precision != FP64 */
+  double tol;             /* relative residual target     (1e-8)          */
+} gdsw_options;
+
+typedef struct {
+  int32_t iters;          /* products with A after the initial residual   */
+  int32_t converged;      /* 1 when the true residual met tol             */
+  double true_relres;     /* ||b - A x||_2 / ||b||_2 recomputed in FP64   */
+  double seconds;         /* wall time of the call                        */
+} gdsw_solve_info;
+
+/* Sizes of a set-up problem, for bandwidth accounting and admission. */
+typedef struct {
+  int64_t n, nnz, n_sub, n0, n_comp;
+  int64_t sum_omega;      /* sum of |Omega_s'| (unknowns)                   */
+  int64_t max_omega;
+  int64_t nnz_L, nnz_U;   /* stored entries of the local factors, diagonal
+                             included (0 for the exact solver)             */
+  int64_t ell_L, ell_U;   /* stored ELL slots incl. padding                 */
+  int64_t nnz_phi;        /* stored entries of Phi (interior blocks + Gamma) */
+  int64_t n_levels_L, n_levels_U; /* summed over subdomains                 */
+  int64_t max_levels;     /* per subdomain                                  */
+  int64_t dense_local;    /* entries of the exact solver's dense inverses   */
+  int64_t n_blocks;       /* Phi blocks: interiors + interface components   */
+  int64_t device_bytes;   /* device memory held by the handle               */
+  double setup_seconds;
+  double setup_phase_seconds[8]; /* [0] symbolic [1] local factors [2] Phi_Gamma
+                                    [3] Phi_I [4] A0 [5] A0^-1 [6] exact local
+                                    [7] Krylov workspace and graph            */
+} gdsw_stats;
+
+typedef struct gdsw_ctx* gdsw_handle;
+
+/* Fill *opt with the defaults listed above. */
+void gdsw_default_options(gdsw_options* opt);
+
+/* Symbolic + numeric setup (Sec. V-A1 three phases; here symbolic on the host,
+ * numeric on the device): decomposition and Gamma components (Sec. III),
+ * overlap, local matrices A_s = R_s A R_s^T, local factors by fixed-point
+ * sweeps (Sec. V-B3) or exact Cholesky, Phi_Gamma from the null space Z
+ * (n x nn, column-major, host; NULL with nn = 0 means the constant vector),
+ * Phi_I = -A_II^-1 A_IGamma Phi_Gamma (Eq. 2), A0 = Phi^T A Phi and its inverse.
+ * Errors: INVALID_ARG (sizes, unsorted or non-symmetric pattern, partition not
+ * matching n or not splitting the matrix graph), BREAKDOWN, OUT_OF_MEMORY,
+ * UNSUPPORTED (a subdomain with more than 65535 unknowns, or an exact local
+ * solver beyond its memory cap). */
+gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const double* Z,
+                       int32_t nn, const gdsw_options* opt, void* stream, gdsw_handle* out);
+
+/* z = M^-1 r (Eq. 1), device vectors. */
+gdsw_status gdsw_apply(gdsw_handle h, const double* r, double* z, void* stream);
+
+/* As gdsw_apply, then waits and reports per-phase device times in ms measured
+ * with CUDA events on `stream`: [0] gather + local solve, [1] Phi^T r,
+ * [2] coarse solve, [3] scatter-add + prolongation. */
+gdsw_status gdsw_apply_timed(gdsw_handle h, const double* r, double* z, void* stream,
+                             double* phase_ms);
+
+/* y = A x with the CSR matrix given at setup, device vectors. */
+gdsw_status gdsw_spmv(gdsw_handle h, const double* x, double* y, void* stream);
+
+/* Solve A x = b with the Krylov method of the options, preconditioned by M.
+ * x holds the initial guess on entry and the solution on return (device).
+ * Returns NOT_CONVERGED (info still filled) when tol was not met. */
+gdsw_status gdsw_solve(gdsw_handle h, const double* b, double* x, gdsw_solve_info* info,
+                       void* stream);
+
+/* As gdsw_solve with HOST b and x: copies b (and the initial x) to the device,
+ * solves, copies x back; the copies are part of the call. */
+gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
+                            gdsw_solve_info* info, void* stream);
+
+gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st);
+
+/* Frees every device allocation of the handle.  NULL is accepted. */
+gdsw_status gdsw_destroy(gdsw_handle h);
+
+const char* gdsw_status_string(gdsw_status s);
+const char* gdsw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDSW_H */

@@ -1,0 +1,236 @@
+// Internal declarations of libgdsw: the host-side plan built by the symbolic
+// phase, the device context of a handle, and the launchers shared between
+// translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gdsw.h"
+
+namespace gdsw {
+
+void set_error(const char* fmt, ...);
+
+#define GDSW_CK(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      ::gdsw::set_error("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                 \
+      return GDSW_ERR_CUDA;                                                        \
+    }                                                                              \
+  } while (0)
+
+#define GDSW_TRY(expr)            \
+  do {                            \
+    gdsw_status s_ = (expr);      \
+    if (s_ != GDSW_OK) return s_; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Host plan (symbolic phase, Sec. V-A1 (a)): index structures only, no values.
+// ---------------------------------------------------------------------------
+
+// Triangular factor of every subdomain in "level-sliced ELL" form: the rows of
+// one level are contiguous, and the off-diagonal entries of a level are stored
+// column-major (slot k of row t at off + k*nr + t), padded to the level's
+// widest row with a zero entry pointing at the row itself.
+struct EllPlan {
+  std::vector<int> sub_lev;        // nsub+1: level range of each subdomain
+  std::vector<int> lev_start;      // per level: first level-ordered row (absolute)
+  std::vector<int> lev_nr;         // rows in the level
+  std::vector<int> lev_K;          // padded width
+  std::vector<int> lev_off;        // first slot
+  std::vector<uint16_t> lrows;     // level-ordered local row index (sum_m)
+  std::vector<uint16_t> col;       // local column of each slot
+  std::vector<int> src;            // local-CSR entry giving the slot value, -1 = padding
+  std::vector<int> dsrc;           // local-CSR diagonal entry of each row, -1 = unit
+  int64_t nnz = 0;                 // true entries incl. diagonal
+  int64_t slots = 0;
+  int max_levels = 0;
+};
+
+struct Plan {
+  int n = 0, dpn = 1, nnodes = 0, nsub = 0, ncomp = 0;
+  int64_t nnz = 0;
+  int nb[3] = {1, 1, 1};
+  // decomposition (Sec. III)
+  std::vector<int> node_sub, node_comp, comp_type;
+  std::vector<int> comp_ptr, comp_dofs;   // dofs of each interface component
+  std::vector<int> int_ptr, int_dofs;     // interior dofs of each subdomain
+  std::vector<int> om_ptr, om_dofs;       // dofs of each overlapping subdomain
+  int max_m = 0;
+  int64_t sum_m = 0;
+  // per dof
+  std::vector<int> dof_comp;              // -1 for interior dofs
+  std::vector<int> dof_comprow;           // row inside its component
+  std::vector<int> dof_introw;            // row inside its subdomain interior
+  // local matrices A_s in Omega_s' order, concatenated (rows = sum_m)
+  std::vector<int> lm_rowptr;             // sum_m+1, absolute entry offsets
+  std::vector<int> lm_col;                // local column
+  std::vector<uint16_t> lm_row;           // local row of every entry
+  std::vector<int> lm_gent;               // entry of the global CSR
+  std::vector<int> lm_tpos;               // entry holding the transposed position
+  std::vector<int> lm_diag;               // diagonal entry of each local row
+  std::vector<int> lm_sub_ent;            // nsub+1: entry range of each subdomain
+  EllPlan L, U;
+  // components adjacent (through A) to the interior of each subdomain
+  std::vector<std::vector<int>> int_adj;
+  std::vector<int> int_bw;                // bandwidth of A_IsIs (local order)
+  std::vector<int> om_bw;                 // bandwidth of A_s (local order)
+  // scatter lists: per dof, the positions in the concatenated local vectors,
+  // ascending subdomain order
+  std::vector<int> pull_dof_ptr, pull_dof_pos;
+};
+
+// Coarse-space layout once the rank of every component is known.
+struct CoarsePlan {
+  int n0 = 0;
+  std::vector<int> comp_c0;               // first coarse column of each component
+  std::vector<int> comp_k;
+  // Phi blocks: b < nsub is the interior of subdomain b, b >= nsub component b-nsub.
+  int nblk = 0;
+  std::vector<int> brow_ptr, brow_dof;    // every dof exactly once
+  std::vector<int> bcol_ptr, bcol;        // coarse columns of each block
+  std::vector<int64_t> phi_off;           // column-major block values
+  int64_t phi_len = 0;
+  std::vector<int> cs_ptr, cs_idx;        // per coarse column: partial slots
+  std::vector<int> pull_ptr, pull_pos;    // scatter lists in block-row order
+  std::vector<int> dof_blk, dof_blkrow;
+};
+
+gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
+                       bool need_levels, Plan* P);
+gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, bool coarse,
+                              CoarsePlan* C);
+
+// ---------------------------------------------------------------------------
+// Device context
+// ---------------------------------------------------------------------------
+
+// Scalars of the Krylov loop, in device memory.  Reductions write partial sums
+// per CTA and the last CTA to finish (ticket counter) adds them in a fixed
+// order, so every scalar is bitwise reproducible.
+struct KrylovScalars {
+  double rz, rz_new, rz_oldz;    // (r,z), new (r,z), (r, z_old) for flexible beta
+  double pq, rr, bb;
+  double alpha, beta;
+  double tol2;                   // tol^2 * ||b||^2
+  int iter, done, maxit, flexible;
+  int bad;                       // NaN / Inf seen
+  int pad;
+  unsigned int ticket[8];        // last-block reduction counters
+};
+
+struct Ctx {
+  int device = 0;
+  gdsw_options opt;
+  int n = 0, nsub = 0, ncomp = 0, n0 = 0, nblk = 0, dpn = 1;
+  int64_t nnz = 0;
+  int max_m = 0;
+  int64_t sum_m = 0;
+  bool fp32 = false;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  gdsw_stats stats{};
+
+  // global matrix
+  int* rowptr = nullptr;
+  int* colind = nullptr;
+  double* val = nullptr;
+  // overlap
+  int* om_ptr = nullptr;
+  int* om_dofs = nullptr;
+  // level ELL factors (apply precision)
+  int* L_sub_lev = nullptr; int4* L_lev = nullptr; uint16_t* L_lrows = nullptr;
+  uint16_t* L_col = nullptr; void* L_val = nullptr; void* L_dinv = nullptr;
+  int* U_sub_lev = nullptr; int4* U_lev = nullptr; uint16_t* U_lrows = nullptr;
+  uint16_t* U_col = nullptr; void* U_val = nullptr; void* U_dinv = nullptr;
+  int max_levels = 0;
+  // exact local solver: dense inverses
+  void* ainv = nullptr;
+  int64_t* ainv_off = nullptr;
+  int ainv_chunks = 0;
+  // Phi blocks
+  int* brow_ptr = nullptr; int* brow_dof = nullptr;
+  int* bcol_ptr = nullptr; int* bcol = nullptr;
+  int64_t* phi_off = nullptr;
+  void* phi = nullptr;
+  int* cs_ptr = nullptr; int* cs_idx = nullptr;
+  int* pull_ptr = nullptr; int* pull_pos = nullptr;
+  int max_bcols = 0;
+  int n_slots = 0;
+  double* partial = nullptr;     // per (block, column) slot
+  double* cvec = nullptr;
+  double* yvec = nullptr;
+  double* A0inv = nullptr;
+  void* zloc = nullptr;          // local solutions, sum_m
+  // Krylov workspace
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
+  double* red = nullptr;         // partial sums for reductions
+  int red_len = 0;
+  KrylovScalars* ks = nullptr;
+  KrylovScalars* ks_host = nullptr;   // pinned mirror
+  // GMRES workspace
+  double* V = nullptr;           // (restart+1) x n
+  double* Zk = nullptr;          // restart x n (right-preconditioned directions)
+  double* hcol = nullptr;        // restart+2 doubles
+  // graphs
+  cudaGraph_t pcg_graph = nullptr;
+  cudaGraphExec_t pcg_exec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  // host staging for gdsw_solve_host
+  double* hpin = nullptr;
+  // events for timed apply
+  cudaEvent_t ev[8] = {};
+  int red_grid = 0;
+};
+
+template <class T>
+gdsw_status dalloc(Ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return GDSW_ERR_OUT_OF_MEMORY;
+  }
+  c->allocs.push_back(q);
+  c->bytes += count * sizeof(T);
+  *p = static_cast<T*>(q);
+  return GDSW_OK;
+}
+
+template <class T>
+gdsw_status upload(Ctx* c, T** p, const std::vector<T>& v, cudaStream_t s) {
+  GDSW_TRY(dalloc(c, p, v.size()));
+  if (!v.empty())
+    GDSW_CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return GDSW_OK;
+}
+
+// setup.cu
+gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double* Z, int nn,
+                          cudaStream_t s);
+// apply.cu
+// z = M^-1 r.  When rz_dots is set, the scatter kernel also accumulates
+// (r, z_new) and (r, z_old) into the Krylov scalars (z_old read before it is
+// overwritten).  Kernels return at once when ks->done is set.
+gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bool rz_dots);
+gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms);
+// krylov.cu
+gdsw_status krylov_init(Ctx* c, cudaStream_t s);
+gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s);
+gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
+gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
+                        cudaStream_t s);
+
+constexpr int kNumSMs = 148;
+
+}  // namespace gdsw

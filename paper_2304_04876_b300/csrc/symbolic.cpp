@@ -1,0 +1,473 @@
+// Symbolic phase (Sec. V-A1 (a)): everything that depends only on the sparsity
+// pattern and the partition, computed once on the host.
+//
+//  * nonoverlapping blocks, the interface Gamma and its vertex / edge / face
+//    components (Sec. III, Fig. 1), read from the separator node planes;
+//  * overlapping subdomains Omega_s' by algebraic overlap (Sec. VII: one
+//    layer) at node level;
+//  * the pattern of every local matrix A_s = R_s A R_s^T with the map back to
+//    the entries of A (so values can be refreshed on the device);
+//  * level sets of the lower and upper triangles (Sec. V-B2, V-B3) and the
+//    level-sliced ELL layout the device triangular solves stream;
+//  * the scatter lists that sum the overlapping local solutions in ascending
+//    subdomain order;
+//  * once the component ranks are known, the layout of the GDSW basis (Eq. 2)
+//    as dense per-block column panels.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace gdsw {
+
+namespace {
+
+bool fits_i32(int64_t v) { return v >= 0 && v < (int64_t(1) << 31); }
+
+// Levels of a triangle of one subdomain's local CSR.  lower: entries j < i, in
+// increasing row order; upper: entries j > i, in decreasing row order.
+void build_ell(const Plan& P, int s, bool lower, int local_solver, EllPlan* E) {
+  const int base = P.om_ptr[s];
+  const int m = P.om_ptr[s + 1] - base;
+  std::vector<int> lev(m, 0);
+  int nlev = 0;
+  auto off_entries = [&](int i, int& first, int& last) {
+    const int r0 = P.lm_rowptr[base + i], r1 = P.lm_rowptr[base + i + 1];
+    const int d = P.lm_diag[base + i];
+    if (lower) { first = r0; last = d; } else { first = d + 1; last = r1; }
+  };
+  if (lower) {
+    for (int i = 0; i < m; ++i) {
+      int a, b;
+      off_entries(i, a, b);
+      int l = 0;
+      for (int e = a; e < b; ++e) l = std::max(l, lev[P.lm_col[e]] + 1);
+      lev[i] = l;
+      nlev = std::max(nlev, l + 1);
+    }
+  } else {
+    for (int i = m - 1; i >= 0; --i) {
+      int a, b;
+      off_entries(i, a, b);
+      int l = 0;
+      for (int e = a; e < b; ++e) l = std::max(l, lev[P.lm_col[e]] + 1);
+      lev[i] = l;
+      nlev = std::max(nlev, l + 1);
+    }
+  }
+  if (m == 0) nlev = 0;
+  // bucket rows by level, ascending row inside a level
+  std::vector<int> cnt(nlev + 1, 0);
+  for (int i = 0; i < m; ++i) cnt[lev[i] + 1]++;
+  for (int l = 0; l < nlev; ++l) cnt[l + 1] += cnt[l];
+  std::vector<int> order(m);
+  {
+    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+    for (int i = 0; i < m; ++i) order[pos[lev[i]]++] = i;
+  }
+  E->max_levels = std::max(E->max_levels, nlev);
+  for (int l = 0; l < nlev; ++l) {
+    const int nr = cnt[l + 1] - cnt[l];
+    int K = 0;
+    for (int t = 0; t < nr; ++t) {
+      int a, b;
+      off_entries(order[cnt[l] + t], a, b);
+      K = std::max(K, b - a);
+    }
+    const int start = base + cnt[l];
+    const int64_t off = E->slots;
+    E->lev_start.push_back(start);
+    E->lev_nr.push_back(nr);
+    E->lev_K.push_back(K);
+    E->lev_off.push_back(static_cast<int>(off));
+    E->col.resize(off + int64_t(K) * nr);
+    E->src.resize(off + int64_t(K) * nr);
+    for (int t = 0; t < nr; ++t) {
+      const int i = order[cnt[l] + t];
+      E->lrows[start + t] = static_cast<uint16_t>(i);
+      const int d = P.lm_diag[base + i];
+      E->dsrc[start + t] = (lower && local_solver == GDSW_LOCAL_ILU0) ? -1 : d;
+      int a, b;
+      off_entries(i, a, b);
+      E->nnz += (b - a) + 1;
+      for (int k = 0; k < K; ++k) {
+        const int64_t slot = off + int64_t(k) * nr + t;
+        if (a + k < b) {
+          const int e = a + k;
+          E->col[slot] = static_cast<uint16_t>(P.lm_col[e]);
+          // IC: the upper factor is L^T, read from the transposed lower entry
+          E->src[slot] = (!lower && local_solver == GDSW_LOCAL_IC0) ? P.lm_tpos[e] : e;
+        } else {
+          E->col[slot] = static_cast<uint16_t>(i);
+          E->src[slot] = -1;
+        }
+      }
+    }
+    E->slots = off + int64_t(K) * nr;
+  }
+}
+
+}  // namespace
+
+gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
+                       bool need_levels, Plan* P) {
+  if (!A || !part || !opt || !P) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  if (!A->rowptr || !A->colind || !A->val) { set_error("null CSR array"); return GDSW_ERR_INVALID_ARG; }
+  const int n = A->n;
+  const int dpn = part->dofs_per_node;
+  const int dims[3] = {part->nx, part->ny, part->nz};
+  if (n <= 0 || dpn <= 0 || dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0) {
+    set_error("non-positive size"); return GDSW_ERR_INVALID_ARG;
+  }
+  const int64_t nnodes64 = int64_t(dims[0]) * dims[1] * dims[2];
+  if (nnodes64 * dpn != n) {
+    set_error("partition has %lld unknowns, matrix %d", (long long)(nnodes64 * dpn), n);
+    return GDSW_ERR_INVALID_ARG;
+  }
+  const int* rp = A->rowptr;
+  const int* ci = A->colind;
+  if (rp[0] != 0) { set_error("rowptr[0] != 0"); return GDSW_ERR_INVALID_ARG; }
+  for (int i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) { set_error("rowptr not monotone at %d", i); return GDSW_ERR_INVALID_ARG; }
+    bool diag = false;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      if (ci[e] < 0 || ci[e] >= n) { set_error("column out of range in row %d", i); return GDSW_ERR_INVALID_ARG; }
+      if (e > rp[i] && ci[e] <= ci[e - 1]) { set_error("columns not strictly increasing in row %d", i); return GDSW_ERR_INVALID_ARG; }
+      diag |= ci[e] == i;
+    }
+    if (!diag) { set_error("row %d has no stored diagonal", i); return GDSW_ERR_INVALID_ARG; }
+  }
+  P->n = n;
+  P->dpn = dpn;
+  P->nnz = rp[n];
+  P->nnodes = static_cast<int>(nnodes64);
+  const int nn = P->nnodes;
+
+  // ---- blocks and interface (Sec. III) ----
+  std::vector<int> blk[3];
+  std::vector<char> onp[3];
+  for (int a = 0; a < 3; ++a) {
+    const int nc = part->ncut[a];
+    if (nc < 0 || (nc > 0 && !part->cut[a])) { set_error("bad cut list on axis %d", a); return GDSW_ERR_INVALID_ARG; }
+    for (int t = 0; t < nc; ++t) {
+      const int c = part->cut[a][t];
+      if (c < 0 || c >= dims[a] - 1 || (t > 0 && c <= part->cut[a][t - 1])) {
+        set_error("cut %d on axis %d must be ascending in [0, %d)", c, a, dims[a] - 1);
+        return GDSW_ERR_INVALID_ARG;
+      }
+    }
+    blk[a].assign(dims[a], 0);
+    onp[a].assign(dims[a], 0);
+    int t = 0;
+    for (int i = 0; i < dims[a]; ++i) {
+      while (t < nc && part->cut[a][t] < i) ++t;
+      blk[a][i] = t;
+      onp[a][i] = (t < nc && part->cut[a][t] == i) ? 1 : 0;
+    }
+    P->nb[a] = nc + 1;
+  }
+  const int64_t nsub64 = int64_t(P->nb[0]) * P->nb[1] * P->nb[2];
+  if (!fits_i32(nsub64)) { set_error("too many subdomains"); return GDSW_ERR_INVALID_ARG; }
+  P->nsub = static_cast<int>(nsub64);
+  const int nsub = P->nsub;
+  P->node_sub.resize(nn);
+  P->node_comp.assign(nn, -1);
+  const int64_t nkeys = int64_t(8) * P->nb[0] * P->nb[1] * P->nb[2];
+  std::vector<int> key2comp(nkeys, -1);
+  for (int k = 0; k < dims[2]; ++k)
+    for (int j = 0; j < dims[1]; ++j)
+      for (int i = 0; i < dims[0]; ++i) {
+        const int u = i + dims[0] * (j + dims[1] * k);
+        P->node_sub[u] = blk[0][i] + P->nb[0] * (blk[1][j] + P->nb[1] * blk[2][k]);
+        const int np = onp[0][i] + onp[1][j] + onp[2][k];
+        if (np == 0) continue;
+        const int64_t key = (2 * blk[0][i] + onp[0][i]) +
+                            int64_t(2 * P->nb[0]) * ((2 * blk[1][j] + onp[1][j]) +
+                                                     int64_t(2 * P->nb[1]) * (2 * blk[2][k] + onp[2][k]));
+        int c = key2comp[key];
+        if (c < 0) {
+          c = key2comp[key] = P->ncomp++;
+          P->comp_type.push_back(np);
+        }
+        P->node_comp[u] = c;
+      }
+  const int ncomp = P->ncomp;
+  // component and interior dof lists (natural order, node-major)
+  P->comp_ptr.assign(ncomp + 1, 0);
+  P->int_ptr.assign(nsub + 1, 0);
+  for (int u = 0; u < nn; ++u) {
+    if (P->node_comp[u] >= 0) P->comp_ptr[P->node_comp[u] + 1] += dpn;
+    else P->int_ptr[P->node_sub[u] + 1] += dpn;
+  }
+  for (int c = 0; c < ncomp; ++c) P->comp_ptr[c + 1] += P->comp_ptr[c];
+  for (int s = 0; s < nsub; ++s) P->int_ptr[s + 1] += P->int_ptr[s];
+  P->comp_dofs.resize(P->comp_ptr[ncomp]);
+  P->int_dofs.resize(P->int_ptr[nsub]);
+  P->dof_comp.assign(n, -1);
+  P->dof_comprow.assign(n, -1);
+  P->dof_introw.assign(n, -1);
+  {
+    std::vector<int> cpos(P->comp_ptr.begin(), P->comp_ptr.end() - 1);
+    std::vector<int> ipos(P->int_ptr.begin(), P->int_ptr.end() - 1);
+    for (int u = 0; u < nn; ++u) {
+      const int c = P->node_comp[u];
+      for (int d = 0; d < dpn; ++d) {
+        const int g = dpn * u + d;
+        if (c >= 0) {
+          P->dof_comp[g] = c;
+          P->dof_comprow[g] = cpos[c] - P->comp_ptr[c];
+          P->comp_dofs[cpos[c]++] = g;
+        } else {
+          const int s = P->node_sub[u];
+          P->dof_introw[g] = ipos[s] - P->int_ptr[s];
+          P->int_dofs[ipos[s]++] = g;
+        }
+      }
+    }
+  }
+
+  // ---- node graph and overlapping subdomains ----
+  std::vector<int> nptr(nn + 1, 0), nadj;
+  {
+    std::vector<int> mark(nn, -1);
+    nadj.reserve(static_cast<size_t>(P->nnz / (int64_t(dpn) * dpn) + nn));
+    for (int u = 0; u < nn; ++u) {
+      for (int d = 0; d < dpn; ++d) {
+        const int g = dpn * u + d;
+        for (int e = rp[g]; e < rp[g + 1]; ++e) {
+          const int v = ci[e] / dpn;
+          if (mark[v] != u) { mark[v] = u; nadj.push_back(v); }
+        }
+      }
+      nptr[u + 1] = static_cast<int>(nadj.size());
+    }
+  }
+  std::vector<int> sub_nptr(nsub + 1, 0), sub_nodes(nn);
+  for (int u = 0; u < nn; ++u) sub_nptr[P->node_sub[u] + 1]++;
+  for (int s = 0; s < nsub; ++s) sub_nptr[s + 1] += sub_nptr[s];
+  {
+    std::vector<int> pos(sub_nptr.begin(), sub_nptr.end() - 1);
+    for (int u = 0; u < nn; ++u) sub_nodes[pos[P->node_sub[u]]++] = u;
+  }
+  const int delta = std::max(0, opt->overlap);
+  P->om_ptr.assign(nsub + 1, 0);
+  std::vector<std::vector<int>> om_nodes(nsub);
+  {
+    std::vector<int> mark(nn, -1);
+    for (int s = 0; s < nsub; ++s) {
+      std::vector<int>& list = om_nodes[s];
+      for (int q = sub_nptr[s]; q < sub_nptr[s + 1]; ++q) { list.push_back(sub_nodes[q]); mark[sub_nodes[q]] = s; }
+      size_t front0 = 0;
+      for (int layer = 0; layer < delta; ++layer) {
+        const size_t front1 = list.size();
+        for (size_t q = front0; q < front1; ++q) {
+          const int u = list[q];
+          for (int e = nptr[u]; e < nptr[u + 1]; ++e) {
+            const int v = nadj[e];
+            if (mark[v] != s) { mark[v] = s; list.push_back(v); }
+          }
+        }
+        front0 = front1;
+      }
+      std::sort(list.begin(), list.end());
+      if (!fits_i32(int64_t(P->om_ptr[s]) + int64_t(list.size()) * dpn)) {
+        set_error("overlap too large"); return GDSW_ERR_UNSUPPORTED;
+      }
+      P->om_ptr[s + 1] = P->om_ptr[s] + static_cast<int>(list.size()) * dpn;
+    }
+  }
+  P->sum_m = P->om_ptr[nsub];
+  P->om_dofs.resize(P->sum_m);
+  P->max_m = 0;
+  for (int s = 0; s < nsub; ++s) {
+    int q = P->om_ptr[s];
+    for (int u : om_nodes[s])
+      for (int d = 0; d < dpn; ++d) P->om_dofs[q++] = dpn * u + d;
+    P->max_m = std::max(P->max_m, P->om_ptr[s + 1] - P->om_ptr[s]);
+  }
+  om_nodes.clear();
+  if (P->max_m > 65535) {
+    set_error("subdomain with %d unknowns exceeds the 16-bit local index limit", P->max_m);
+    return GDSW_ERR_UNSUPPORTED;
+  }
+
+  // ---- local matrices, bandwidths, interior adjacency ----
+  P->lm_rowptr.assign(P->sum_m + 1, 0);
+  P->lm_diag.assign(P->sum_m, -1);
+  P->lm_sub_ent.assign(nsub + 1, 0);
+  P->om_bw.assign(nsub, 0);
+  P->int_bw.assign(nsub, 0);
+  P->int_adj.assign(nsub, {});
+  {
+    std::vector<int> g2l(n, -1);
+    int64_t ent = 0;
+    for (int s = 0; s < nsub; ++s) {
+      const int base = P->om_ptr[s], m = P->om_ptr[s + 1] - base;
+      for (int i = 0; i < m; ++i) g2l[P->om_dofs[base + i]] = i;
+      int bw = 0;
+      for (int i = 0; i < m; ++i) {
+        const int g = P->om_dofs[base + i];
+        for (int e = rp[g]; e < rp[g + 1]; ++e) {
+          const int j = g2l[ci[e]];
+          if (j < 0) continue;
+          if (j == i) P->lm_diag[base + i] = static_cast<int>(ent);
+          P->lm_col.push_back(j);
+          P->lm_row.push_back(static_cast<uint16_t>(i));
+          P->lm_gent.push_back(e);
+          bw = std::max(bw, std::abs(i - j));
+          ++ent;
+        }
+        if (!fits_i32(ent)) { set_error("local matrices too large"); return GDSW_ERR_UNSUPPORTED; }
+        P->lm_rowptr[base + i + 1] = static_cast<int>(ent);
+      }
+      P->lm_sub_ent[s + 1] = static_cast<int>(ent);
+      P->om_bw[s] = bw;
+      for (int i = 0; i < m; ++i) g2l[P->om_dofs[base + i]] = -1;
+    }
+    // interior bandwidth and adjacent components
+    for (int s = 0; s < nsub; ++s) {
+      int bw = 0;
+      std::vector<int>& adj = P->int_adj[s];
+      for (int q = P->int_ptr[s]; q < P->int_ptr[s + 1]; ++q) {
+        const int g = P->int_dofs[q];
+        const int i = P->dof_introw[g];
+        for (int e = rp[g]; e < rp[g + 1]; ++e) {
+          const int c = ci[e];
+          if (P->dof_comp[c] >= 0) { adj.push_back(P->dof_comp[c]); continue; }
+          if (P->node_sub[c / dpn] != s) {
+            set_error("interiors of subdomains %d and %d are coupled: the separator planes do "
+                      "not split the matrix graph", s, P->node_sub[c / dpn]);
+            return GDSW_ERR_INVALID_ARG;
+          }
+          bw = std::max(bw, std::abs(i - P->dof_introw[c]));
+        }
+      }
+      std::sort(adj.begin(), adj.end());
+      adj.erase(std::unique(adj.begin(), adj.end()), adj.end());
+      P->int_bw[s] = bw;
+    }
+  }
+  // transposed positions (structural symmetry is required)
+  P->lm_tpos.assign(P->lm_col.size(), -1);
+  for (int s = 0; s < nsub; ++s) {
+    const int base = P->om_ptr[s], m = P->om_ptr[s + 1] - base;
+    for (int i = 0; i < m; ++i) {
+      for (int e = P->lm_rowptr[base + i]; e < P->lm_rowptr[base + i + 1]; ++e) {
+        const int j = P->lm_col[e];
+        const int* b0 = P->lm_col.data() + P->lm_rowptr[base + j];
+        const int* b1 = P->lm_col.data() + P->lm_rowptr[base + j + 1];
+        const int* f = std::lower_bound(b0, b1, i);
+        if (f == b1 || *f != i) {
+          set_error("matrix pattern is not structurally symmetric");
+          return GDSW_ERR_INVALID_ARG;
+        }
+        P->lm_tpos[e] = static_cast<int>(f - P->lm_col.data());
+      }
+    }
+  }
+
+  // ---- level-sliced ELL of the triangles ----
+  if (need_levels) {
+    for (EllPlan* E : {&P->L, &P->U}) {
+      E->sub_lev.assign(nsub + 1, 0);
+      E->lrows.assign(P->sum_m, 0);
+      E->dsrc.assign(P->sum_m, -1);
+    }
+    for (int s = 0; s < nsub; ++s) {
+      build_ell(*P, s, true, opt->local_solver, &P->L);
+      P->L.sub_lev[s + 1] = static_cast<int>(P->L.lev_nr.size());
+      build_ell(*P, s, false, opt->local_solver, &P->U);
+      P->U.sub_lev[s + 1] = static_cast<int>(P->U.lev_nr.size());
+      if (!fits_i32(P->L.slots) || !fits_i32(P->U.slots)) {
+        set_error("factor too large"); return GDSW_ERR_UNSUPPORTED;
+      }
+    }
+  }
+
+  // ---- scatter lists per dof (ascending subdomain) ----
+  P->pull_dof_ptr.assign(n + 1, 0);
+  for (int64_t q = 0; q < P->sum_m; ++q) P->pull_dof_ptr[P->om_dofs[q] + 1]++;
+  for (int g = 0; g < n; ++g) P->pull_dof_ptr[g + 1] += P->pull_dof_ptr[g];
+  P->pull_dof_pos.resize(P->sum_m);
+  {
+    std::vector<int> pos(P->pull_dof_ptr.begin(), P->pull_dof_ptr.end() - 1);
+    for (int64_t q = 0; q < P->sum_m; ++q) P->pull_dof_pos[pos[P->om_dofs[q]]++] = static_cast<int>(q);
+  }
+  return GDSW_OK;
+}
+
+gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, bool coarse,
+                              CoarsePlan* C) {
+  const int nsub = P.nsub, ncomp = P.ncomp, n = P.n;
+  C->comp_c0.assign(ncomp, 0);
+  C->comp_k.assign(ncomp, 0);
+  int n0 = 0;
+  for (int c = 0; c < ncomp; ++c) {
+    C->comp_c0[c] = n0;
+    C->comp_k[c] = coarse ? comp_rank[c] : 0;
+    n0 += C->comp_k[c];
+  }
+  C->n0 = n0;
+  C->nblk = nsub + ncomp;
+  const int nblk = C->nblk;
+  C->brow_ptr.assign(nblk + 1, 0);
+  C->bcol_ptr.assign(nblk + 1, 0);
+  C->phi_off.assign(nblk + 1, 0);
+  C->brow_dof.clear();
+  C->brow_dof.reserve(n);
+  C->bcol.clear();
+  for (int b = 0; b < nblk; ++b) {
+    if (b < nsub) {
+      C->brow_dof.insert(C->brow_dof.end(), P.int_dofs.begin() + P.int_ptr[b],
+                         P.int_dofs.begin() + P.int_ptr[b + 1]);
+      for (int c : P.int_adj[b])
+        for (int t = 0; t < C->comp_k[c]; ++t) C->bcol.push_back(C->comp_c0[c] + t);
+    } else {
+      const int c = b - nsub;
+      C->brow_dof.insert(C->brow_dof.end(), P.comp_dofs.begin() + P.comp_ptr[c],
+                         P.comp_dofs.begin() + P.comp_ptr[c + 1]);
+      for (int t = 0; t < C->comp_k[c]; ++t) C->bcol.push_back(C->comp_c0[c] + t);
+    }
+    C->brow_ptr[b + 1] = static_cast<int>(C->brow_dof.size());
+    C->bcol_ptr[b + 1] = static_cast<int>(C->bcol.size());
+    const int64_t rows = C->brow_ptr[b + 1] - C->brow_ptr[b];
+    const int64_t cols = C->bcol_ptr[b + 1] - C->bcol_ptr[b];
+    C->phi_off[b + 1] = C->phi_off[b] + rows * cols;
+  }
+  C->phi_len = C->phi_off[nblk];
+  if (static_cast<int>(C->brow_dof.size()) != n) {
+    set_error("internal: blocks do not cover the unknowns"); return GDSW_ERR_INVALID_ARG;
+  }
+  C->dof_blk.assign(n, -1);
+  C->dof_blkrow.assign(n, -1);
+  for (int b = 0; b < nblk; ++b)
+    for (int q = C->brow_ptr[b]; q < C->brow_ptr[b + 1]; ++q) {
+      C->dof_blk[C->brow_dof[q]] = b;
+      C->dof_blkrow[C->brow_dof[q]] = q - C->brow_ptr[b];
+    }
+  // partial slots per coarse column, ascending block order
+  C->cs_ptr.assign(n0 + 1, 0);
+  for (int q = 0; q < C->bcol_ptr[nblk]; ++q) C->cs_ptr[C->bcol[q] + 1]++;
+  for (int l = 0; l < n0; ++l) C->cs_ptr[l + 1] += C->cs_ptr[l];
+  C->cs_idx.resize(C->bcol_ptr[nblk]);
+  {
+    std::vector<int> pos(C->cs_ptr.begin(), C->cs_ptr.end() - 1);
+    for (int q = 0; q < C->bcol_ptr[nblk]; ++q) C->cs_idx[pos[C->bcol[q]]++] = q;
+  }
+  // scatter lists in block-row order
+  C->pull_ptr.assign(n + 1, 0);
+  C->pull_pos.clear();
+  C->pull_pos.reserve(P.sum_m);
+  for (int q = 0; q < n; ++q) {
+    const int g = C->brow_dof[q];
+    for (int t = P.pull_dof_ptr[g]; t < P.pull_dof_ptr[g + 1]; ++t) C->pull_pos.push_back(P.pull_dof_pos[t]);
+    C->pull_ptr[q + 1] = static_cast<int>(C->pull_pos.size());
+  }
+  return GDSW_OK;
+}
+
+}  // namespace gdsw
