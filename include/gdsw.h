@@ -31,6 +31,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define GDSW_API __attribute__((visibility("default")))
+#else
+#define GDSW_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -126,7 +132,7 @@ typedef struct {
 typedef struct gdsw_ctx* gdsw_handle;
 
 /* Fill *opt with the defaults listed above. */
-void gdsw_default_options(gdsw_options* opt);
+GDSW_API void gdsw_default_options(gdsw_options* opt);
 
 /* Symbolic + numeric setup (Sec. V-A1 three phases; here symbolic on the host,
  * numeric on the device): decomposition and Gamma components (Sec. III),
@@ -138,39 +144,39 @@ void gdsw_default_options(gdsw_options* opt);
  * matching n or not splitting the matrix graph), BREAKDOWN, OUT_OF_MEMORY,
  * UNSUPPORTED (a subdomain with more than 65535 unknowns, or an exact local
  * solver beyond its memory cap). */
-gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const double* Z,
+GDSW_API gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const double* Z,
                        int32_t nn, const gdsw_options* opt, void* stream, gdsw_handle* out);
 
 /* z = M^-1 r (Eq. 1), device vectors. */
-gdsw_status gdsw_apply(gdsw_handle h, const double* r, double* z, void* stream);
+GDSW_API gdsw_status gdsw_apply(gdsw_handle h, const double* r, double* z, void* stream);
 
 /* As gdsw_apply, then waits and reports per-phase device times in ms measured
  * with CUDA events on `stream`: [0] gather + local solve, [1] Phi^T r,
  * [2] coarse solve, [3] scatter-add + prolongation. */
-gdsw_status gdsw_apply_timed(gdsw_handle h, const double* r, double* z, void* stream,
+GDSW_API gdsw_status gdsw_apply_timed(gdsw_handle h, const double* r, double* z, void* stream,
                              double* phase_ms);
 
 /* y = A x with the CSR matrix given at setup, device vectors. */
-gdsw_status gdsw_spmv(gdsw_handle h, const double* x, double* y, void* stream);
+GDSW_API gdsw_status gdsw_spmv(gdsw_handle h, const double* x, double* y, void* stream);
 
 /* Solve A x = b with the Krylov method of the options, preconditioned by M.
  * x holds the initial guess on entry and the solution on return (device).
  * Returns NOT_CONVERGED (info still filled) when tol was not met. */
-gdsw_status gdsw_solve(gdsw_handle h, const double* b, double* x, gdsw_solve_info* info,
+GDSW_API gdsw_status gdsw_solve(gdsw_handle h, const double* b, double* x, gdsw_solve_info* info,
                        void* stream);
 
 /* As gdsw_solve with HOST b and x: copies b (and the initial x) to the device,
  * solves, copies x back; the copies are part of the call. */
-gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
+GDSW_API gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
                             gdsw_solve_info* info, void* stream);
 
-gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st);
+GDSW_API gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st);
 
 /* Frees every device allocation of the handle.  NULL is accepted. */
-gdsw_status gdsw_destroy(gdsw_handle h);
+GDSW_API gdsw_status gdsw_destroy(gdsw_handle h);
 
-const char* gdsw_status_string(gdsw_status s);
-const char* gdsw_last_error(void);
+GDSW_API const char* gdsw_status_string(gdsw_status s);
+GDSW_API const char* gdsw_last_error(void);
 
 #ifdef __cplusplus
 }

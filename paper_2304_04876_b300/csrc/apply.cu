@@ -1,0 +1,382 @@
+// The preconditioner apply z = M^-1 r (Sec. III, Eq. 1) as four launches:
+//
+//  1. local:   one CTA per overlapping subdomain gathers r_s = R_s r into
+//              shared memory and solves A_s z_s = r_s there (level-scheduled
+//              or Jacobi-sweep triangular solves of the IC(0)/ILU(0) factor,
+//              or the dense inverse of the exact solver); z_s goes to the
+//              concatenated local-solution buffer.
+//  2. phiT:    one CTA per Phi block (subdomain interior or interface
+//              component) forms the partial products Phi_b^T r_b.
+//  3. coarse:  c = sum of partials per coarse column (fixed order), then
+//              y = A0^-1 c as a dense FP64 GEMV with the explicit inverse.
+//  4. combine: every unknown is owned by exactly one Phi block; its CTA sums
+//              the overlapping local solutions in ascending subdomain order
+//              (the deterministic scatter-add of sum_s R_s^T z_s) and adds
+//              the prolongation (Phi y)_g, optionally fusing the PCG dots.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gdsw {
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ void tri_levels(const EllDev<T>& E, int s, T* v) {
+  const int l0 = E.sub_lev[s], l1 = E.sub_lev[s + 1];
+  for (int l = l0; l < l1; ++l) {
+    const int4 lv = E.lev[l];   // (first row, rows, width, first slot)
+    for (int t = threadIdx.x; t < lv.y; t += blockDim.x) {
+      const int row = E.lrows[lv.x + t];
+      T acc = v[row];
+      const T* vals = E.val + lv.w + t;
+      const uint16_t* cols = E.col + lv.w + t;
+      for (int k = 0; k < lv.z; ++k) acc -= vals[int64_t(k) * lv.y] * v[cols[int64_t(k) * lv.y]];
+      v[row] = acc * E.dinv[lv.x + t];
+    }
+    __syncthreads();
+  }
+}
+
+// Jacobi sweeps on T y = b (Sec. V-B3): y0 = D^-1 b, y_{k+1} = D^-1 (b - (T - D) y_k).
+// b and the result share `b`; y0, y1 are work vectors of the CTA.
+template <class T>
+__device__ __forceinline__ void tri_jacobi(const EllDev<T>& E, int s, int sweeps, T* b, T* y0,
+                                           T* y1) {
+  const int l0 = E.sub_lev[s], l1 = E.sub_lev[s + 1];
+  for (int l = l0; l < l1; ++l) {
+    const int4 lv = E.lev[l];
+    for (int t = threadIdx.x; t < lv.y; t += blockDim.x) {
+      const int row = E.lrows[lv.x + t];
+      y0[row] = b[row] * E.dinv[lv.x + t];
+    }
+  }
+  __syncthreads();
+  T* yo = y0;
+  T* yn = y1;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int l = l0; l < l1; ++l) {
+      const int4 lv = E.lev[l];
+      for (int t = threadIdx.x; t < lv.y; t += blockDim.x) {
+        const int row = E.lrows[lv.x + t];
+        T acc = b[row];
+        const T* vals = E.val + lv.w + t;
+        const uint16_t* cols = E.col + lv.w + t;
+        for (int k = 0; k < lv.z; ++k) acc -= vals[int64_t(k) * lv.y] * yo[cols[int64_t(k) * lv.y]];
+        yn[row] = acc * E.dinv[lv.x + t];
+      }
+    }
+    __syncthreads();
+    T* tmp = yo; yo = yn; yn = tmp;
+  }
+  // result back into b
+  for (int l = l0; l < l1; ++l) {
+    const int4 lv = E.lev[l];
+    for (int t = threadIdx.x; t < lv.y; t += blockDim.x) {
+      const int row = E.lrows[lv.x + t];
+      b[row] = yo[row];
+    }
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_local_tri(const double* __restrict__ r,
+                                                   const int* __restrict__ om_ptr,
+                                                   const int* __restrict__ om_dofs, EllDev<T> L,
+                                                   EllDev<T> U, int jacobi, int sweeps,
+                                                   T* __restrict__ zloc,
+                                                   const KrylovScalars* __restrict__ ks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (ks != nullptr && ks->done) return;
+  T* v = reinterpret_cast<T*>(smem_raw);
+  const int s = blockIdx.x;
+  const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = T(r[om_dofs[base + i]]);
+  __syncthreads();
+  if (!jacobi) {
+    tri_levels(L, s, v);
+    tri_levels(U, s, v);
+  } else {
+    T* y0 = v + m;
+    T* y1 = v + 2 * m;
+    tri_jacobi(L, s, sweeps, v, y0, y1);
+    tri_jacobi(U, s, sweeps, v, y0, y1);
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) zloc[base + i] = v[i];
+}
+
+// Exact local solver: z_s = A_s^-1 r_s with the stored dense inverse
+// (symmetric, so row i is read contiguously).  Grid (row chunks of 32, nsub).
+template <class T>
+__global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ r,
+                                                     const int* __restrict__ om_ptr,
+                                                     const int* __restrict__ om_dofs,
+                                                     const T* __restrict__ ainv,
+                                                     const int64_t* __restrict__ ainv_off,
+                                                     T* __restrict__ zloc,
+                                                     const KrylovScalars* __restrict__ ks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (ks != nullptr && ks->done) return;
+  T* rs = reinterpret_cast<T*>(smem_raw);
+  const int s = blockIdx.y;
+  const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+  const int row0 = blockIdx.x * 32;
+  if (row0 >= m) return;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) rs[i] = T(r[om_dofs[base + i]]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const T* A = ainv + ainv_off[s];
+  for (int rr = w; rr < 32; rr += 8) {
+    const int i = row0 + rr;
+    if (i >= m) break;
+    const T* Ai = A + int64_t(i) * m;
+    T acc = T(0);
+    for (int j = lane; j < m; j += 32) acc += Ai[j] * rs[j];
+    acc = warp_sum(acc);
+    if (lane == 0) zloc[base + i] = acc;
+  }
+}
+
+// Partial products Phi_b^T r_b, 8 columns per pass.
+template <class T>
+__global__ void __launch_bounds__(256) k_phiT(const double* __restrict__ r,
+                                              const int* __restrict__ brow_ptr,
+                                              const int* __restrict__ brow_dof,
+                                              const int* __restrict__ bcol_ptr,
+                                              const int64_t* __restrict__ phi_off,
+                                              const T* __restrict__ phi, double* __restrict__ partial,
+                                              const KrylovScalars* __restrict__ ks) {
+  __shared__ T sh[32];
+  if (ks != nullptr && ks->done) return;
+  const int b = blockIdx.x;
+  const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
+  const int k = bcol_ptr[b + 1] - bcol_ptr[b];
+  if (k == 0) return;
+  const T* Ph = phi + phi_off[b];
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    const int kc = min(8, k - c0);
+    T acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = T(0);
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      const T rv = T(r[brow_dof[p0 + i]]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u < kc) acc[u] += Ph[int64_t(c0 + u) * nr + i] * rv;
+    }
+    for (int u = 0; u < kc; ++u) {
+      const T t = block_sum(acc[u], sh);
+      if (threadIdx.x == 0) partial[bcol_ptr[b] + c0 + u] = double(t);
+    }
+  }
+}
+
+__global__ void k_coarse_c(int n0, const int* __restrict__ cs_ptr, const int* __restrict__ cs_idx,
+                           const double* __restrict__ partial, double* __restrict__ c,
+                           const KrylovScalars* __restrict__ ks) {
+  if (ks != nullptr && ks->done) return;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n0; l += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int q = cs_ptr[l]; q < cs_ptr[l + 1]; ++q) v += partial[cs_idx[q]];
+    c[l] = v;
+  }
+}
+
+// y = A0^-1 c, warp per row of the explicit inverse, c staged in shared memory.
+__global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __restrict__ Ainv,
+                                                     const double* __restrict__ c,
+                                                     double* __restrict__ y,
+                                                     const KrylovScalars* __restrict__ ks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (ks != nullptr && ks->done) return;
+  double* cs = reinterpret_cast<double*>(smem_raw);
+  for (int l = threadIdx.x; l < n0; l += blockDim.x) cs[l] = c[l];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n0; row += warps) {
+    const double* Ar = Ainv + int64_t(row) * n0;
+    double acc = 0.0;
+    for (int j = lane; j < n0; j += 32) acc += Ar[j] * cs[j];
+    acc = warp_sum(acc);
+    if (lane == 0) y[row] = acc;
+  }
+}
+
+// z_g = sum over subdomains containing g of (z_s)_g (ascending subdomain
+// order) + (Phi y)_g.  With `dots`, also (r, z_new) and (r, z_old), reduced by
+// the last CTA, which sets beta and (r, z) for the PCG update.
+template <class T>
+__global__ void __launch_bounds__(256) k_combine(
+    const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_ptr,
+    const int* __restrict__ brow_dof, const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
+    const int64_t* __restrict__ phi_off, const T* __restrict__ phi, const double* __restrict__ y,
+    const int* __restrict__ pull_ptr, const int* __restrict__ pull_pos, const T* __restrict__ zloc,
+    int dots, double* __restrict__ red, KrylovScalars* ks) {
+  __shared__ double ys[160];
+  __shared__ double sh[32];
+  if (ks != nullptr && ks->done) return;
+  const int b = blockIdx.x;
+  const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
+  const int c0 = bcol_ptr[b], k = bcol_ptr[b + 1] - c0;
+  for (int u = threadIdx.x; u < k; u += blockDim.x) ys[u] = y[bcol[c0 + u]];
+  __syncthreads();
+  const T* Ph = phi + (k > 0 ? phi_off[b] : 0);
+  double d_new = 0.0, d_old = 0.0;
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    const int p = p0 + i;
+    const int g = brow_dof[p];
+    double acc = 0.0;
+    for (int q = pull_ptr[p]; q < pull_ptr[p + 1]; ++q) acc += double(zloc[pull_pos[q]]);
+    for (int u = 0; u < k; ++u) acc += double(Ph[int64_t(u) * nr + i]) * ys[u];
+    if (dots) {
+      const double rg = r[g];
+      d_old += rg * z[g];
+      d_new += rg * acc;
+    }
+    z[g] = acc;
+  }
+  if (!dots) return;
+  const double tn = block_sum(d_new, sh);
+  const double to = block_sum(d_old, sh);
+  if (threadIdx.x == 0) {
+    red[2 * b] = tn;
+    red[2 * b + 1] = to;
+  }
+  if (arrive_last(&ks->ticket[2])) {
+    double sn = 0.0, so = 0.0;
+    for (int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+      sn += __ldcg(red + 2 * q);
+      so += __ldcg(red + 2 * q + 1);
+    }
+    sn = block_sum(sn, sh);
+    so = block_sum(so, sh);
+    if (threadIdx.x == 0) {
+      const double num = ks->flexible ? (sn - so) : sn;
+      ks->beta = num / ks->rz;
+      ks->rz_oldz = so;
+      ks->rz_new = sn;
+      ks->rz = sn;
+    }
+  }
+}
+
+template <class T>
+EllDev<T> ell(const Ctx* c, bool lower) {
+  EllDev<T> e;
+  if (lower) {
+    e.sub_lev = c->L_sub_lev; e.lev = c->L_lev; e.lrows = c->L_lrows; e.col = c->L_col;
+    e.val = static_cast<const T*>(c->L_val); e.dinv = static_cast<const T*>(c->L_dinv);
+  } else {
+    e.sub_lev = c->U_sub_lev; e.lev = c->U_lev; e.lrows = c->U_lrows; e.col = c->U_col;
+    e.val = static_cast<const T*>(c->U_val); e.dinv = static_cast<const T*>(c->U_dinv);
+  }
+  return e;
+}
+
+template <class T>
+gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
+  T* zl = static_cast<T*>(c->zloc);
+  if (c->opt.local_solver == GDSW_LOCAL_EXACT) {
+    const size_t shm = size_t(c->max_m) * sizeof(T);
+    dim3 grid((c->max_m + 31) / 32, c->nsub);
+    k_local_dense<T><<<grid, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
+                                            c->ainv_off, zl, ks);
+  } else {
+    const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
+    const size_t shm = size_t(c->max_m) * sizeof(T) * (jac ? 3 : 1);
+    k_local_tri<T><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, ell<T>(c, true),
+                                             ell<T>(c, false), jac, c->opt.sweeps_trsv, zl, ks);
+  }
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+template <class T>
+gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
+  if (c->n0 == 0) return GDSW_OK;
+  k_phiT<T><<<c->nblk, 256, 0, s>>>(r, c->brow_ptr, c->brow_dof, c->bcol_ptr, c->phi_off,
+                                    static_cast<const T*>(c->phi), c->partial, ks);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
+  if (c->n0 == 0) return GDSW_OK;
+  k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, ks);
+  const int grid = std::min((c->n0 + 7) / 8, kNumSMs * 4);
+  k_coarse_gemv<<<grid, 256, size_t(c->n0) * sizeof(double), s>>>(c->n0, c->A0inv, c->cvec, c->yvec, ks);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+template <class T>
+gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots) {
+  k_combine<T><<<c->nblk, 256, 0, s>>>(r, z, c->brow_ptr, c->brow_dof, c->bcol_ptr, c->bcol,
+                                       c->phi_off, static_cast<const T*>(c->phi), c->yvec,
+                                       c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),
+                                       dots ? 1 : 0, c->red, dots ? c->ks : nullptr);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+template <class T>
+gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, cudaEvent_t* ev) {
+  const KrylovScalars* ks = dots ? c->ks : nullptr;
+  if (ev) GDSW_CK(cudaEventRecord(ev[0], s));
+  GDSW_TRY(launch_local<T>(c, r, s, ks));
+  if (ev) GDSW_CK(cudaEventRecord(ev[1], s));
+  GDSW_TRY(launch_phiT<T>(c, r, s, ks));
+  if (ev) GDSW_CK(cudaEventRecord(ev[2], s));
+  GDSW_TRY(launch_coarse(c, s, ks));
+  if (ev) GDSW_CK(cudaEventRecord(ev[3], s));
+  GDSW_TRY(launch_combine<T>(c, r, z, s, dots));
+  if (ev) GDSW_CK(cudaEventRecord(ev[4], s));
+  return GDSW_OK;
+}
+
+}  // namespace
+
+gdsw_status apply_configure(Ctx* c) {
+  // kernels that may need more than 48 KB of dynamic shared memory
+  const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
+  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  const size_t shm_local = size_t(c->max_m) * es * (c->opt.local_solver == GDSW_LOCAL_EXACT ? 1 : (jac ? 3 : 1));
+  if (shm_local > 227 * 1024) {
+    set_error("subdomain of %d unknowns does not fit the local solve's shared memory", c->max_m);
+    return GDSW_ERR_UNSUPPORTED;
+  }
+  const size_t shm_coarse = size_t(c->n0) * sizeof(double);
+  if (shm_coarse > 227 * 1024) { set_error("coarse dimension too large"); return GDSW_ERR_UNSUPPORTED; }
+  if (c->max_bcols > 160) { set_error("a Phi block has more than 160 coarse columns"); return GDSW_ERR_UNSUPPORTED; }
+  if (c->fp32) {
+    GDSW_CK(cudaFuncSetAttribute(k_local_tri<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
+    GDSW_CK(cudaFuncSetAttribute(k_local_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
+  } else {
+    GDSW_CK(cudaFuncSetAttribute(k_local_tri<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
+    GDSW_CK(cudaFuncSetAttribute(k_local_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
+  }
+  GDSW_CK(cudaFuncSetAttribute(k_coarse_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(std::max<size_t>(shm_coarse, 8))));
+  return GDSW_OK;
+}
+
+gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bool rz_dots) {
+  return c->fp32 ? apply_t<float>(c, r, z, s, rz_dots, nullptr)
+                 : apply_t<double>(c, r, z, s, rz_dots, nullptr);
+}
+
+gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms) {
+  GDSW_TRY(c->fp32 ? apply_t<float>(c, r, z, s, false, c->ev) : apply_t<double>(c, r, z, s, false, c->ev));
+  GDSW_CK(cudaEventSynchronize(c->ev[4]));
+  for (int q = 0; q < 4; ++q) {
+    float t = 0.f;
+    GDSW_CK(cudaEventElapsedTime(&t, c->ev[q], c->ev[q + 1]));
+    ms[q] = t;
+  }
+  return GDSW_OK;
+}
+
+}  // namespace gdsw

@@ -1,0 +1,217 @@
+// C ABI entry points of libgdsw (declared in include/gdsw.h).
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+struct gdsw_ctx {
+  gdsw::Ctx c;
+};
+
+namespace gdsw {
+
+namespace {
+thread_local char g_err[512] = "";
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void release(Ctx* c) {
+  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+  if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->ks_host) cudaFreeHost(c->ks_host);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+}
+
+bool valid_options(const gdsw_options* o) {
+  return o->local_solver >= 0 && o->local_solver <= 2 && o->trsv >= 0 && o->trsv <= 1 &&
+         o->sweeps_factor >= 0 && o->sweeps_trsv >= 0 && o->overlap >= 0 && o->precision >= 0 &&
+         o->precision <= 1 && o->krylov >= 0 && o->krylov <= 1 && o->restart >= 1 &&
+         o->maxit >= 1 && o->coarse >= 0 && o->coarse <= 1 && o->tol > 0.0;
+}
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+gdsw_status apply_configure(Ctx* c);
+
+}  // namespace gdsw
+
+using namespace gdsw;
+
+extern "C" {
+
+void gdsw_default_options(gdsw_options* o) {
+  if (!o) return;
+  o->local_solver = GDSW_LOCAL_IC0;
+  o->trsv = GDSW_TRSV_LEVELSCHED;
+  o->sweeps_factor = 3;
+  o->sweeps_trsv = 5;
+  o->overlap = 1;
+  o->precision = GDSW_PREC_FP64;
+  o->krylov = GDSW_KRYLOV_PCG;
+  o->restart = 30;
+  o->maxit = 2000;
+  o->coarse = GDSW_COARSE_GDSW;
+  o->flexible = -1;
+  o->tol = 1e-8;
+}
+
+const char* gdsw_status_string(gdsw_status s) {
+  switch (s) {
+    case GDSW_OK: return "ok";
+    case GDSW_ERR_INVALID_ARG: return "invalid argument";
+    case GDSW_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case GDSW_ERR_BREAKDOWN: return "factorization breakdown";
+    case GDSW_ERR_NOT_CONVERGED: return "not converged";
+    case GDSW_ERR_TIMEOUT: return "device wait timed out";
+    case GDSW_ERR_CUDA: return "CUDA error";
+    case GDSW_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* gdsw_last_error(void) { return g_err; }
+
+gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const double* Z, int32_t nn,
+                       const gdsw_options* opt, void* stream, gdsw_handle* out) {
+  if (!out) { set_error("null output handle"); return GDSW_ERR_INVALID_ARG; }
+  *out = nullptr;
+  gdsw_options o;
+  if (opt) o = *opt; else gdsw_default_options(&o);
+  if (!valid_options(&o)) { set_error("invalid options"); return GDSW_ERR_INVALID_ARG; }
+  if (nn < 0 || (nn > 0 && !Z)) { set_error("null space: nn=%d with Z=%p", nn, (const void*)Z); return GDSW_ERR_INVALID_ARG; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double t0 = now_s();
+  Plan P;
+  gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
+  if (st != GDSW_OK) return st;
+  const double t_sym = now_s() - t0;
+  gdsw_ctx* h = new (std::nothrow) gdsw_ctx();
+  if (!h) { set_error("host allocation failed"); return GDSW_ERR_OUT_OF_MEMORY; }
+  Ctx* c = &h->c;
+  cudaGetDevice(&c->device);
+  c->opt = o;
+  c->n = P.n;
+  c->nnz = P.nnz;
+  c->nsub = P.nsub;
+  c->ncomp = P.ncomp;
+  c->dpn = P.dpn;
+  c->max_m = P.max_m;
+  c->sum_m = P.sum_m;
+  c->fp32 = o.precision == GDSW_PREC_FP32;
+  c->stats.setup_phase_seconds[0] = t_sym;
+  st = numeric_setup(c, P, A, Z, nn, s);
+  if (st == GDSW_OK) st = c->fp32 ? dalloc(c, reinterpret_cast<float**>(&c->zloc), P.sum_m)
+                                  : dalloc(c, reinterpret_cast<double**>(&c->zloc), P.sum_m);
+  if (st == GDSW_OK) st = apply_configure(c);
+  const double t1 = now_s();
+  if (st == GDSW_OK) st = krylov_init(c, s);
+  if (st == GDSW_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error("setup: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; }
+  }
+  if (st != GDSW_OK) {
+    release(c);
+    delete h;
+    return st;
+  }
+  c->stats.setup_phase_seconds[7] = now_s() - t1;
+  gdsw_stats& S = c->stats;
+  S.n = P.n;
+  S.nnz = P.nnz;
+  S.n_sub = P.nsub;
+  S.n0 = c->n0;
+  S.n_comp = P.ncomp;
+  S.sum_omega = P.sum_m;
+  S.max_omega = P.max_m;
+  S.nnz_L = P.L.nnz;
+  S.nnz_U = P.U.nnz;
+  S.ell_L = P.L.slots;
+  S.ell_U = P.U.slots;
+  S.n_levels_L = static_cast<int64_t>(P.L.lev_nr.size());
+  S.n_levels_U = static_cast<int64_t>(P.U.lev_nr.size());
+  S.max_levels = c->max_levels;
+  S.n_blocks = c->nblk;
+  S.device_bytes = static_cast<int64_t>(c->bytes);
+  S.setup_seconds = now_s() - t0;
+  *out = h;
+  return GDSW_OK;
+}
+
+gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st) {
+  if (!h || !st) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  *st = h->c.stats;
+  return GDSW_OK;
+}
+
+gdsw_status gdsw_apply(gdsw_handle h, const double* r, double* z, void* stream) {
+  if (!h || !r || !z) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  return apply_enqueue(&h->c, r, z, static_cast<cudaStream_t>(stream), false);
+}
+
+gdsw_status gdsw_apply_timed(gdsw_handle h, const double* r, double* z, void* stream,
+                             double* phase_ms) {
+  if (!h || !r || !z || !phase_ms) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  return apply_timed(&h->c, r, z, static_cast<cudaStream_t>(stream), phase_ms);
+}
+
+gdsw_status gdsw_spmv(gdsw_handle h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  return spmv_enqueue(&h->c, x, y, static_cast<cudaStream_t>(stream));
+}
+
+gdsw_status gdsw_solve(gdsw_handle h, const double* b, double* x, gdsw_solve_info* info,
+                       void* stream) {
+  if (!h || !b || !x) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  Ctx* c = &h->c;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return c->opt.krylov == GDSW_KRYLOV_GMRES ? solve_gmres(c, b, x, info, s) : solve_pcg(c, b, x, info, s);
+}
+
+gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
+                            gdsw_solve_info* info, void* stream) {
+  if (!h || !b_host || !x_host) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  Ctx* c = &h->c;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double t0 = now_s();
+  const size_t bytes = sizeof(double) * c->n;
+  // b and x0 travel into two workspace vectors that the solve copies from before
+  // it first writes them (q is first written by the initial SpMV, p after the
+  // initial residual)
+  GDSW_CK(cudaMemcpyAsync(c->q, b_host, bytes, cudaMemcpyHostToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->p, x_host, bytes, cudaMemcpyHostToDevice, s));
+  double* bd = c->q;
+  double* xd = c->p;
+  gdsw_status st = c->opt.krylov == GDSW_KRYLOV_GMRES ? solve_gmres(c, bd, xd, info, s)
+                                                      : solve_pcg(c, bd, xd, info, s);
+  if (st != GDSW_OK && st != GDSW_ERR_NOT_CONVERGED) return st;
+  GDSW_CK(cudaMemcpyAsync(x_host, c->x, bytes, cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (info) info->seconds = now_s() - t0;
+  return st;
+}
+
+gdsw_status gdsw_destroy(gdsw_handle h) {
+  if (!h) return GDSW_OK;
+  release(&h->c);
+  delete h;
+  return GDSW_OK;
+}
+
+}  // extern "C"

@@ -112,6 +112,17 @@ gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, 
 // Device context
 // ---------------------------------------------------------------------------
 
+// One triangular factor of all subdomains as the device reads it (see EllPlan).
+template <class T>
+struct EllDev {
+  const int* sub_lev;
+  const int4* lev;          // (first row, rows, width, first slot) per level
+  const uint16_t* lrows;
+  const uint16_t* col;
+  const T* val;
+  const T* dinv;
+};
+
 // Scalars of the Krylov loop, in device memory.  Reductions write partial sums
 // per CTA and the last CTA to finish (ticket counter) adds them in a fixed
 // order, so every scalar is bitwise reproducible.

@@ -1,0 +1,470 @@
+// Krylov loops around the preconditioner: CSR SpMV, fused vector updates with
+// deterministic reductions, PCG with its iteration captured in a CUDA graph
+// behind a device-side while condition, and right-preconditioned GMRES(m)
+// (Sec. VII) with classical Gram-Schmidt applied twice.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gdsw {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// y = A x, TPR threads per row; with `ks`, also (x, y) into ks->pq.
+template <int TPR>
+__global__ void __launch_bounds__(kThreads) k_spmv(int n, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ colind,
+                                                   const double* __restrict__ val,
+                                                   const double* __restrict__ x, double* __restrict__ y,
+                                                   double* __restrict__ red, KrylovScalars* ks) {
+  __shared__ double sh[32];
+  if (ks != nullptr && ks->done) return;
+  const int sub = threadIdx.x % TPR;
+  const int rows_per_cta = kThreads / TPR;
+  double dot = 0.0;
+  for (int row0 = blockIdx.x * rows_per_cta; row0 < n; row0 += gridDim.x * rows_per_cta) {
+    const int row = row0 + threadIdx.x / TPR;
+    double acc = 0.0;
+    if (row < n) {
+      const int e1 = rowptr[row + 1];
+      for (int e = rowptr[row] + sub; e < e1; e += TPR) acc += val[e] * x[colind[e]];
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, TPR);
+    if (sub == 0 && row < n) {
+      y[row] = acc;
+      dot += x[row] * acc;
+    }
+  }
+  if (ks == nullptr) return;
+  const double t = block_sum(dot, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = t;
+  if (arrive_last(&ks->ticket[0])) {
+    const double s = sum_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) ks->pq = s;
+  }
+}
+
+// alpha = (r,z)/(p,q); x += alpha p; r -= alpha q; rr = ||r||^2; then the
+// last CTA counts the iteration and decides whether the loop ends.
+__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restrict__ x,
+                                                         double* __restrict__ r,
+                                                         const double* __restrict__ p,
+                                                         const double* __restrict__ q,
+                                                         double* __restrict__ red, KrylovScalars* ks,
+                                                         cudaGraphConditionalHandle handle,
+                                                         int use_handle) {
+  __shared__ double sh[32];
+  if (ks->done) {
+    // the loop must end even if it was entered with the flag already set
+    if (use_handle && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(handle, 0);
+    return;
+  }
+  const double alpha = ks->rz / ks->pq;
+  double rr = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    rr += ri * ri;
+  }
+  const double t = block_sum(rr, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = t;
+  if (arrive_last(&ks->ticket[1])) {
+    const double s = sum_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      ks->rr = s;
+      ks->alpha = alpha;
+      ks->iter += 1;
+      int done = 0;
+      if (!isfinite(s) || !isfinite(alpha) || !(ks->pq > 0.0)) { ks->bad = 1; done = 1; }
+      else if (s <= ks->tol2) done = 1;
+      else if (ks->iter >= ks->maxit) done = 1;
+      if (done) {
+        ks->done = 1;
+        if (use_handle) cudaGraphSetConditional(handle, 0);
+      }
+    }
+  }
+}
+
+__global__ void k_pupdate(int n, const double* __restrict__ z, double* __restrict__ p,
+                          const KrylovScalars* __restrict__ ks) {
+  if (ks->done) return;
+  const double beta = ks->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// r = b - q, rr = ||r||^2 and bb = ||b||^2.
+__global__ void __launch_bounds__(kThreads) k_residual(int n, const double* __restrict__ b,
+                                                       const double* __restrict__ q,
+                                                       double* __restrict__ r,
+                                                       double* __restrict__ red, KrylovScalars* ks) {
+  __shared__ double sh[32];
+  double rr = 0.0, bb = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double ri = bi - q[i];
+    r[i] = ri;
+    rr += ri * ri;
+    bb += bi * bi;
+  }
+  const double t1 = block_sum(rr, sh);
+  const double t2 = block_sum(bb, sh);
+  if (threadIdx.x == 0) { red[2 * blockIdx.x] = t1; red[2 * blockIdx.x + 1] = t2; }
+  if (arrive_last(&ks->ticket[3])) {
+    double a = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) { a += __ldcg(red + 2 * i); c += __ldcg(red + 2 * i + 1); }
+    a = block_sum(a, sh);
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) { ks->rr = a; ks->bb = c; }
+  }
+}
+
+// ---- GMRES helpers -------------------------------------------------------
+
+// h[j] = (V_j, w) for j < k (one CTA row of partials per j), CGS.
+__global__ void __launch_bounds__(kThreads) k_multidot(int n, int k, const double* __restrict__ V,
+                                                       const double* __restrict__ w,
+                                                       double* __restrict__ red) {
+  __shared__ double sh[32];
+  for (int j = 0; j < k; ++j) {
+    const double* v = V + int64_t(j) * n;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += v[i] * w[i];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) red[int64_t(j) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_reduce_rows(int k, int parts, const double* __restrict__ red, double* __restrict__ out,
+                              int accumulate) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  if (j >= k) return;
+  const double s = sum_partials(red + int64_t(j) * parts, parts, sh);
+  if (threadIdx.x == 0) out[j] = accumulate ? out[j] + s : s;
+}
+
+// w -= V h (k columns)
+__global__ void k_subtract_basis(int n, int k, const double* __restrict__ V, const double* __restrict__ h,
+                                 double* __restrict__ w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < k; ++j) acc -= h[j] * V[int64_t(j) * n + i];
+    w[i] = acc;
+  }
+}
+
+// b = a * (*scal); a and b may be the same vector
+__global__ void k_scale_copy(int n, const double* a, const double* __restrict__ scal, double* b) {
+  const double sc = *scal;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i] * sc;
+}
+
+// x += Z y (k columns)
+__global__ void k_update_x(int n, int k, const double* __restrict__ Zk, const double* __restrict__ yv,
+                           double* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = x[i];
+    for (int j = 0; j < k; ++j) acc += yv[j] * Zk[int64_t(j) * n + i];
+    x[i] = acc;
+  }
+}
+
+int spmv_tpr(const Ctx* c) {
+  const double avg = double(c->nnz) / std::max(1, c->n);
+  if (avg <= 4.5) return 4;
+  if (avg <= 10) return 8;
+  if (avg <= 24) return 16;
+  return 32;
+}
+
+gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, KrylovScalars* ks) {
+  const int tpr = spmv_tpr(c);
+  const int rows_per_cta = kThreads / tpr;
+  const int grid = std::min(c->red_grid, (c->n + rows_per_cta - 1) / rows_per_cta);
+  switch (tpr) {
+    case 4: k_spmv<4><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    case 8: k_spmv<8><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    case 16: k_spmv<16><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    default: k_spmv<32><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+  }
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+int vec_grid(const Ctx* c) { return std::min(c->red_grid, (c->n + kThreads - 1) / kThreads); }
+
+// One PCG iteration body (everything after the convergence test is skipped
+// once ks->done is set).
+gdsw_status pcg_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
+  GDSW_TRY(launch_spmv(c, c->p, c->q, s, c->ks));
+  k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(c->n, c->x, c->r, c->p, c->q, c->red, c->ks, h, use_handle);
+  GDSW_CK(cudaGetLastError());
+  GDSW_TRY(apply_enqueue(c, c->r, c->z, s, true));
+  k_pupdate<<<vec_grid(c), kThreads, 0, s>>>(c->n, c->z, c->p, c->ks);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+gdsw_status read_scalars(Ctx* c, cudaStream_t s) {
+  GDSW_CK(cudaMemcpyAsync(c->ks_host, c->ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  return GDSW_OK;
+}
+
+gdsw_status set_done(Ctx* c, cudaStream_t s, int v) {
+  GDSW_CK(cudaMemcpyAsync(&c->ks->done, &v, sizeof(int), cudaMemcpyHostToDevice, s));
+  return GDSW_OK;
+}
+
+}  // namespace
+
+gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s) {
+  return launch_spmv(c, x, y, s, nullptr);
+}
+
+gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
+  const int n = c->n;
+  c->red_grid = kNumSMs * 4;
+  c->red_len = std::max(2 * c->red_grid, 2 * c->nblk) + 64;
+  if (c->opt.krylov == GDSW_KRYLOV_GMRES)
+    c->red_len = std::max<int>(c->red_len, (c->opt.restart + 2) * c->red_grid + 64);
+  GDSW_TRY(dalloc(c, &c->red, c->red_len));
+  GDSW_TRY(dalloc(c, &c->x, n));
+  GDSW_TRY(dalloc(c, &c->r, n));
+  GDSW_TRY(dalloc(c, &c->z, n));
+  GDSW_TRY(dalloc(c, &c->p, n));
+  GDSW_TRY(dalloc(c, &c->q, n));
+  GDSW_TRY(dalloc(c, &c->b, n));
+  GDSW_CK(cudaMemsetAsync(c->z, 0, sizeof(double) * n, s));
+  GDSW_CK(cudaMemsetAsync(c->p, 0, sizeof(double) * n, s));
+  GDSW_TRY(dalloc(c, &c->ks, 1));
+  GDSW_CK(cudaMemsetAsync(c->ks, 0, sizeof(KrylovScalars), s));
+  GDSW_CK(cudaMallocHost(&c->ks_host, sizeof(KrylovScalars)));
+  if (c->opt.krylov == GDSW_KRYLOV_GMRES) {
+    const int m = std::max(1, c->opt.restart);
+    GDSW_TRY(dalloc(c, &c->V, size_t(m + 1) * n));
+    GDSW_TRY(dalloc(c, &c->Zk, size_t(m) * n));
+    GDSW_TRY(dalloc(c, &c->hcol, m + 2));
+  }
+  for (int q = 0; q < 8; ++q) GDSW_CK(cudaEventCreate(&c->ev[q]));
+  GDSW_CK(cudaStreamSynchronize(s));
+  // the PCG iteration as a graph: while (cond) { body }, cond cleared on device
+  if (c->opt.krylov == GDSW_KRYLOV_PCG) {
+    GDSW_CK(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    GDSW_CK(cudaGraphCreate(&c->pcg_graph, 0));
+    cudaGraphConditionalHandle h;
+    GDSW_CK(cudaGraphConditionalHandleCreate(&h, c->pcg_graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    GDSW_CK(cudaGraphAddNode(&node, c->pcg_graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    GDSW_CK(cudaStreamBeginCaptureToGraph(c->graph_stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    gdsw_status st = pcg_body(c, c->graph_stream, h, 1);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->graph_stream, &captured);
+    if (st != GDSW_OK) return st;
+    GDSW_CK(e);
+    GDSW_CK(cudaGraphInstantiate(&c->pcg_exec, c->pcg_graph, 0));
+  }
+  return GDSW_OK;
+}
+
+gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s) {
+  const double t0 = now_s();
+  const int n = c->n;
+  GDSW_CK(cudaMemcpyAsync(c->b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->x, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  KrylovScalars init = {};
+  init.maxit = c->opt.maxit;
+  init.flexible = c->opt.flexible < 0 ? (c->fp32 ? 1 : 0) : c->opt.flexible;
+  init.rz = 1.0;
+  GDSW_CK(cudaMemcpyAsync(c->ks, &init, sizeof(KrylovScalars), cudaMemcpyHostToDevice, s));
+  // r = b - A x0
+  GDSW_TRY(launch_spmv(c, c->x, c->q, s, nullptr));
+  k_residual<<<vec_grid(c), kThreads, 0, s>>>(n, c->b, c->q, c->r, c->red, c->ks);
+  GDSW_CK(cudaGetLastError());
+  GDSW_TRY(read_scalars(c, s));
+  const double bb = c->ks_host->bb;
+  const double tol2 = c->opt.tol * c->opt.tol * bb;
+  int iters = 0;
+  bool converged = false;
+  double rr = c->ks_host->rr;
+  if (bb == 0.0) {
+    GDSW_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    GDSW_CK(cudaMemsetAsync(c->x, 0, sizeof(double) * n, s));
+    GDSW_CK(cudaStreamSynchronize(s));
+    if (info) { info->iters = 0; info->converged = 1; info->true_relres = 0.0; info->seconds = now_s() - t0; }
+    return GDSW_OK;
+  }
+  if (rr <= tol2) {
+    converged = true;
+  } else {
+    GDSW_CK(cudaMemcpyAsync(&c->ks->tol2, &tol2, sizeof(double), cudaMemcpyHostToDevice, s));
+    // z = M r, (r, z), p = z
+    GDSW_TRY(apply_enqueue(c, c->r, c->z, s, true));
+    GDSW_CK(cudaMemcpyAsync(c->p, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    for (;;) {
+      GDSW_CK(cudaGraphLaunch(c->pcg_exec, s));
+      // recompute the true residual where the recurrence says converged (or maxit)
+      GDSW_TRY(launch_spmv(c, c->x, c->q, s, nullptr));
+      k_residual<<<vec_grid(c), kThreads, 0, s>>>(n, c->b, c->q, c->r, c->red, c->ks);
+      GDSW_CK(cudaGetLastError());
+      GDSW_TRY(read_scalars(c, s));
+      iters = c->ks_host->iter;
+      rr = c->ks_host->rr;
+      if (rr <= tol2) { converged = true; break; }
+      if (c->ks_host->bad || iters >= c->opt.maxit || !std::isfinite(rr)) break;
+      // continue from the true residual: z = M r, beta, p = z + beta p
+      GDSW_TRY(set_done(c, s, 0));
+      GDSW_TRY(apply_enqueue(c, c->r, c->z, s, true));
+      k_pupdate<<<vec_grid(c), kThreads, 0, s>>>(n, c->z, c->p, c->ks);
+      GDSW_CK(cudaGetLastError());
+    }
+  }
+  GDSW_CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->converged = converged ? 1 : 0;
+    info->true_relres = std::sqrt(rr / bb);
+    info->seconds = now_s() - t0;
+  }
+  if (!converged) { set_error("PCG stopped after %d iterations at relative residual %.3e", iters, std::sqrt(rr / bb)); return GDSW_ERR_NOT_CONVERGED; }
+  return GDSW_OK;
+}
+
+// Right-preconditioned restarted GMRES(m): Arnoldi on A M^-1 with classical
+// Gram-Schmidt applied twice (one multi-dot reduction per pass), Givens
+// rotations and the small least-squares problem on the host; the true
+// residual is recomputed at every restart.
+gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s) {
+  const double t0 = now_s();
+  const int n = c->n;
+  const int m = std::max(1, c->opt.restart);
+  const int G = vec_grid(c);
+  GDSW_CK(cudaMemcpyAsync(c->b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->x, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  KrylovScalars init = {};
+  init.maxit = c->opt.maxit;
+  GDSW_CK(cudaMemcpyAsync(c->ks, &init, sizeof(KrylovScalars), cudaMemcpyHostToDevice, s));
+  std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), hv(m + 2);
+  int it = 0;
+  double bb = 0.0, rr = 0.0;
+  bool converged = false;
+  for (;;) {
+    GDSW_TRY(launch_spmv(c, c->x, c->q, s, nullptr));
+    k_residual<<<G, kThreads, 0, s>>>(n, c->b, c->q, c->r, c->red, c->ks);
+    GDSW_CK(cudaGetLastError());
+    GDSW_TRY(read_scalars(c, s));
+    bb = c->ks_host->bb;
+    rr = c->ks_host->rr;
+    if (bb == 0.0) {
+      GDSW_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+      GDSW_CK(cudaMemsetAsync(c->x, 0, sizeof(double) * n, s));
+      GDSW_CK(cudaStreamSynchronize(s));
+      if (info) { info->iters = 0; info->converged = 1; info->true_relres = 0; info->seconds = now_s() - t0; }
+      return GDSW_OK;
+    }
+    const double tolabs = c->opt.tol * std::sqrt(bb);
+    const double beta = std::sqrt(rr);
+    if (beta <= tolabs) { converged = true; break; }
+    if (it >= c->opt.maxit || !std::isfinite(beta)) break;
+    // V_0 = r / beta
+    const double inv = 1.0 / beta;
+    GDSW_CK(cudaMemcpyAsync(c->hcol, &inv, sizeof(double), cudaMemcpyHostToDevice, s));
+    k_scale_copy<<<G, kThreads, 0, s>>>(n, c->r, c->hcol, c->V);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = c->V + int64_t(j) * n;
+      double* zj = c->Zk + int64_t(j) * n;
+      double* w = c->V + int64_t(j + 1) * n;
+      GDSW_TRY(apply_enqueue(c, vj, zj, s, false));
+      GDSW_TRY(launch_spmv(c, zj, w, s, nullptr));
+      // two passes of classical Gram-Schmidt
+      std::fill(hv.begin(), hv.end(), 0.0);
+      GDSW_CK(cudaMemsetAsync(c->hcol, 0, sizeof(double) * (m + 2), s));
+      for (int pass = 0; pass < 2; ++pass) {
+        k_multidot<<<G, kThreads, 0, s>>>(n, j + 1, c->V, w, c->red);
+        k_reduce_rows<<<j + 1, kThreads, 0, s>>>(j + 1, G, c->red, c->q, 0);
+        k_subtract_basis<<<G, kThreads, 0, s>>>(n, j + 1, c->V, c->q, w);
+        // accumulate h += pass coefficients (kept on host)
+        std::vector<double> hp(j + 1);
+        GDSW_CK(cudaMemcpyAsync(hp.data(), c->q, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        GDSW_CK(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j; ++i) hv[i] += hp[i];
+      }
+      // ||w||
+      k_multidot<<<G, kThreads, 0, s>>>(n, 1, w, w, c->red);
+      k_reduce_rows<<<1, kThreads, 0, s>>>(1, G, c->red, c->hcol, 0);
+      double ww = 0.0;
+      GDSW_CK(cudaMemcpyAsync(&ww, c->hcol, sizeof(double), cudaMemcpyDeviceToHost, s));
+      GDSW_CK(cudaStreamSynchronize(s));
+      const double hn = std::sqrt(ww);
+      if (hn > 0.0) {
+        const double ih = 1.0 / hn;
+        GDSW_CK(cudaMemcpyAsync(c->hcol, &ih, sizeof(double), cudaMemcpyHostToDevice, s));
+        k_scale_copy<<<G, kThreads, 0, s>>>(n, w, c->hcol, w);
+      }
+      for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] = hv[i];
+      H[size_t(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[size_t(i) * m + j] + sn[i] * H[size_t(i + 1) * m + j];
+        H[size_t(i + 1) * m + j] = -sn[i] * H[size_t(i) * m + j] + cs[i] * H[size_t(i + 1) * m + j];
+        H[size_t(i) * m + j] = t;
+      }
+      const double den = std::hypot(H[size_t(j) * m + j], H[size_t(j + 1) * m + j]);
+      cs[j] = H[size_t(j) * m + j] / den;
+      sn[j] = H[size_t(j + 1) * m + j] / den;
+      H[size_t(j) * m + j] = den;
+      H[size_t(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= tolabs || it >= c->opt.maxit) break;
+    }
+    // back substitution and x += Z y
+    std::vector<double> yv(jdone);
+    for (int i = jdone - 1; i >= 0; --i) {
+      double v = g[i];
+      for (int k = i + 1; k < jdone; ++k) v -= H[size_t(i) * m + k] * yv[k];
+      yv[i] = v / H[size_t(i) * m + i];
+    }
+    GDSW_CK(cudaMemcpyAsync(c->hcol, yv.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
+    k_update_x<<<G, kThreads, 0, s>>>(n, jdone, c->Zk, c->hcol, c->x);
+    GDSW_CK(cudaGetLastError());
+  }
+  GDSW_CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = it;
+    info->converged = converged ? 1 : 0;
+    info->true_relres = std::sqrt(rr / bb);
+    info->seconds = now_s() - t0;
+  }
+  if (!converged) { set_error("GMRES stopped after %d iterations", it); return GDSW_ERR_NOT_CONVERGED; }
+  return GDSW_OK;
+}
+
+}  // namespace gdsw

@@ -1,0 +1,999 @@
+// Numeric setup on the device (Sec. V-A1 (b)): local matrices and their
+// incomplete factors by fixed-point sweeps (Sec. V-B3), the GDSW basis
+// (Sec. III, Eq. 2), the coarse matrix A0 = Phi^T A Phi and its inverse, and
+// the dense inverses of the exact local solver.
+//
+// B300 FP64 runs on CUDA cores (no fast FP64 tensor path on this part), so the
+// dense kernels here are plain FP64 loops organised for L2 reuse; they run
+// once per setup and are not on the per-iteration path.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gdsw {
+
+namespace {
+
+constexpr double kDropTol = 1e-10;   // relative norm below which an MGS column is dropped
+
+enum { ERR_BREAKDOWN = 1 };
+
+// ---------------------------------------------------------------------------
+// local matrices: values, symmetric unit-diagonal scaling
+// ---------------------------------------------------------------------------
+
+// One CTA per subdomain: s_i = a_ii^-1/2 for every local row, then
+// a~_e = a_e s_i s_j (Chow-Patel scaling) and the raw value a_e.
+__global__ void k_extract_local(const double* __restrict__ val, const int* __restrict__ om_ptr,
+                                const int* __restrict__ lm_sub_ent, const int* __restrict__ lm_gent,
+                                const uint16_t* __restrict__ lm_row, const int* __restrict__ lm_col,
+                                const int* __restrict__ lm_diag, double* __restrict__ sc,
+                                double* __restrict__ at, double* __restrict__ araw, int* err) {
+  const int s = blockIdx.x;
+  const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double d = val[lm_gent[lm_diag[base + i]]];
+    if (!(d > 0.0)) { atomicOr(err, ERR_BREAKDOWN); sc[base + i] = 1.0; }
+    else sc[base + i] = 1.0 / sqrt(d);
+  }
+  __syncthreads();
+  for (int e = lm_sub_ent[s] + threadIdx.x; e < lm_sub_ent[s + 1]; e += blockDim.x) {
+    const double a = val[lm_gent[e]];
+    araw[e] = a;
+    at[e] = a * sc[base + lm_row[e]] * sc[base + lm_col[e]];
+  }
+}
+
+// Synchronous IC(0) sweeps (Sec. V-B3) on the lower pattern, one CTA per
+// subdomain, double-buffered: every entry of sweep k+1 reads sweep-k values.
+//   s_ij = a~_ij - sum_{k<j} l_ik l_jk;  l_ij = s_ij / l_jj (i>j),  l_jj = sqrt(s_jj).
+__global__ void k_ic0_sweeps(const int* __restrict__ om_ptr, const int* __restrict__ lm_sub_ent,
+                             const int* __restrict__ lm_rowptr, const int* __restrict__ lm_col,
+                             const uint16_t* __restrict__ lm_row, const int* __restrict__ lm_diag,
+                             const double* __restrict__ at, double* F0, double* F1, int sweeps,
+                             int* err) {
+  const int s = blockIdx.x;
+  const int base = om_ptr[s];
+  const int e0 = lm_sub_ent[s], e1 = lm_sub_ent[s + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) F0[e] = at[e];
+  __syncthreads();
+  double* Fo = F0;
+  double* Fn = F1;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int i = lm_row[e], j = lm_col[e];
+      if (j > i) { Fn[e] = Fo[e]; continue; }
+      // merge row i and row j over columns k < j
+      int a = lm_rowptr[base + i], ae = lm_rowptr[base + i + 1];
+      int b = lm_rowptr[base + j], be = lm_diag[base + j];
+      double acc = 0.0;
+      while (a < ae && b < be) {
+        const int ca = lm_col[a], cb = lm_col[b];
+        if (ca >= j) break;
+        if (ca == cb) { acc = fma(Fo[a], Fo[b], acc); ++a; ++b; }
+        else if (ca < cb) ++a;
+        else ++b;
+      }
+      const double sv = at[e] - acc;
+      if (i == j) {
+        if (!(sv > 0.0)) { atomicOr(err, ERR_BREAKDOWN); Fn[e] = 1.0; }
+        else Fn[e] = sqrt(sv);
+      } else {
+        Fn[e] = sv / Fo[lm_diag[base + j]];
+      }
+    }
+    __syncthreads();
+    double* t = Fo; Fo = Fn; Fn = t;
+  }
+}
+
+// Synchronous ILU(0) sweeps on the full pattern (L unit lower, U upper):
+//   l_ij = (a~_ij - sum_{k<j} l_ik u_kj) / u_jj  (i>j),   u_ij = a~_ij - sum_{k<i} l_ik u_kj.
+// u_kj is read from the entry (k, j) reached through the transposed position of (j, k).
+__global__ void k_ilu0_sweeps(const int* __restrict__ om_ptr, const int* __restrict__ lm_sub_ent,
+                              const int* __restrict__ lm_rowptr, const int* __restrict__ lm_col,
+                              const uint16_t* __restrict__ lm_row, const int* __restrict__ lm_diag,
+                              const int* __restrict__ lm_tpos, const double* __restrict__ at,
+                              double* F0, double* F1, int sweeps, int* err) {
+  const int s = blockIdx.x;
+  const int base = om_ptr[s];
+  const int e0 = lm_sub_ent[s], e1 = lm_sub_ent[s + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) F0[e] = at[e];
+  __syncthreads();
+  double* Fo = F0;
+  double* Fn = F1;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int i = lm_row[e], j = lm_col[e];
+      const int kmax = min(i, j);
+      int a = lm_rowptr[base + i], ae = lm_rowptr[base + i + 1];
+      int b = lm_rowptr[base + j], be = lm_rowptr[base + j + 1];
+      double acc = 0.0;
+      while (a < ae && b < be) {
+        const int ca = lm_col[a], cb = lm_col[b];
+        if (ca >= kmax || cb >= kmax) break;
+        if (ca == cb) { acc = fma(Fo[a], Fo[lm_tpos[b]], acc); ++a; ++b; }
+        else if (ca < cb) ++a;
+        else ++b;
+      }
+      const double sv = at[e] - acc;
+      if (i > j) {
+        const double u = Fo[lm_diag[base + j]];
+        if (u == 0.0) { atomicOr(err, ERR_BREAKDOWN); Fn[e] = 0.0; }
+        else Fn[e] = sv / u;
+      } else {
+        Fn[e] = sv;
+      }
+    }
+    __syncthreads();
+    double* t = Fo; Fo = Fn; Fn = t;
+  }
+}
+
+// Undo the scaling entry by entry: the factors of A_s itself.
+// IC:  L^ = S^-1 L  (l^_ij = l_ij / s_i).
+// ILU: L^ = S^-1 L S (l^_ij = l_ij s_j / s_i), U^ = S^-1 U S^-1 (u^_ij = u_ij / (s_i s_j)).
+__global__ void k_unscale(int nent, int ilu, const int* __restrict__ lm_row_abs_base,
+                          const uint16_t* __restrict__ lm_row, const int* __restrict__ lm_col,
+                          const int* __restrict__ ent_sub_base, const double* __restrict__ sc,
+                          const double* __restrict__ F, double* __restrict__ G) {
+  (void)lm_row_abs_base;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
+    const int base = ent_sub_base[e];
+    const double si = sc[base + lm_row[e]], sj = sc[base + lm_col[e]];
+    const int i = lm_row[e], j = lm_col[e];
+    double g;
+    if (!ilu) g = (j <= i) ? F[e] / si : 0.0;
+    else g = (j < i) ? F[e] * sj / si : F[e] / (si * sj);
+    G[e] = g;
+  }
+}
+
+template <class T>
+__global__ void k_pack_ell(int64_t nslots, const int* __restrict__ src, const double* __restrict__ G,
+                           T* __restrict__ val) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nslots;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const int e = src[q];
+    val[q] = e >= 0 ? T(G[e]) : T(0);
+  }
+}
+
+template <class T>
+__global__ void k_pack_dinv(int64_t nrows, const int* __restrict__ dsrc, const double* __restrict__ G,
+                            T* __restrict__ dinv) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nrows;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const int e = dsrc[q];
+    dinv[q] = e >= 0 ? T(1.0 / G[e]) : T(1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phi_Gamma: orthonormal basis of the null space on each component
+// ---------------------------------------------------------------------------
+
+// One CTA per component: modified Gram-Schmidt over the nn columns of
+// R_Gamma_i Z in order, dropping a column whose remaining norm is below
+// kDropTol of its original norm.  Q[(comp_ptr[c])*nn + k*R + r] holds kept
+// column k; rank[c] the number kept.
+__global__ void k_mgs(const int* __restrict__ comp_ptr, const int* __restrict__ comp_dofs,
+                      const double* __restrict__ Z, int n, int nn, double* __restrict__ Q,
+                      int* __restrict__ rank) {
+  __shared__ double sh[32];
+  __shared__ double bc;
+  const int c = blockIdx.x;
+  const int r0 = comp_ptr[c], R = comp_ptr[c + 1] - r0;
+  double* Qc = Q + int64_t(r0) * nn;
+  int kept = 0;
+  for (int col = 0; col < nn; ++col) {
+    double* v = Qc + int64_t(kept) * R;
+    double loc = 0.0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      const double z = Z[int64_t(col) * n + comp_dofs[r0 + r]];
+      v[r] = z;
+      loc += z * z;
+    }
+    double t = block_sum(loc, sh);
+    if (threadIdx.x == 0) bc = sqrt(t);
+    __syncthreads();
+    const double n0 = bc;
+    __syncthreads();
+    for (int k = 0; k < kept; ++k) {
+      const double* qk = Qc + int64_t(k) * R;
+      loc = 0.0;
+      for (int r = threadIdx.x; r < R; r += blockDim.x) loc += qk[r] * v[r];
+      t = block_sum(loc, sh);
+      if (threadIdx.x == 0) bc = t;
+      __syncthreads();
+      const double d = bc;
+      __syncthreads();
+      for (int r = threadIdx.x; r < R; r += blockDim.x) v[r] -= d * qk[r];
+      __syncthreads();
+    }
+    loc = 0.0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) loc += v[r] * v[r];
+    t = block_sum(loc, sh);
+    if (threadIdx.x == 0) bc = sqrt(t);
+    __syncthreads();
+    const double nv = bc;
+    __syncthreads();
+    if (n0 == 0.0 || nv < kDropTol * n0) continue;
+    const double inv = 1.0 / nv;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) v[r] *= inv;
+    __syncthreads();
+    ++kept;
+  }
+  if (threadIdx.x == 0) rank[c] = kept;
+}
+
+// Copy the kept MGS columns into the component blocks of Phi (column-major).
+__global__ void k_copy_phig(int nsub, const int* __restrict__ comp_ptr, int nn,
+                            const double* __restrict__ Q, const int* __restrict__ bcol_ptr,
+                            const int64_t* __restrict__ phi_off, double* __restrict__ phi) {
+  const int c = blockIdx.x;
+  const int b = nsub + c;
+  const int R = comp_ptr[c + 1] - comp_ptr[c];
+  const int k = bcol_ptr[b + 1] - bcol_ptr[b];
+  const double* Qc = Q + int64_t(comp_ptr[c]) * nn;
+  for (int q = threadIdx.x; q < R * k; q += blockDim.x) phi[phi_off[b] + q] = Qc[q];
+}
+
+// ---------------------------------------------------------------------------
+// Banded Cholesky (natural order) for A_IsIs (Eq. 2) and the exact solver
+// ---------------------------------------------------------------------------
+// Band storage, lower triangle, column-major: entry (i, j), 0 <= i-j <= w, at
+// j*(w+1) + (i-j).  One CTA per matrix; right-looking, one column at a time,
+// the pivot column staged in shared memory.
+__global__ void k_band_cholesky(double* band, const int64_t* __restrict__ boff,
+                                const int* __restrict__ bn, const int* __restrict__ bw, int p0,
+                                int* err) {
+  extern __shared__ double colv[];
+  const int p = p0 + blockIdx.x;
+  double* B = band + boff[p];
+  const int n = bn[p], w = bw[p], W = w + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double piv;
+  for (int j = 0; j < n; ++j) {
+    double* Bj = B + int64_t(j) * W;
+    if (threadIdx.x == 0) {
+      const double d = Bj[0];
+      if (!(d > 0.0)) { atomicOr(err, ERR_BREAKDOWN); piv = 1.0; }
+      else piv = sqrt(d);
+      Bj[0] = piv;
+    }
+    __syncthreads();
+    const int len = min(w, n - 1 - j);
+    const double ip = 1.0 / piv;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+      const double v = Bj[1 + t] * ip;
+      Bj[1 + t] = v;
+      colv[t] = v;
+    }
+    __syncthreads();
+    // trailing update of the (len x len) lower triangle: column kk of the
+    // window is column j+1+kk of the band
+    for (int kk = wid; kk < len; kk += nw) {
+      double* Bk = B + int64_t(j + 1 + kk) * W;
+      const double lk = colv[kk];
+      for (int ii = kk + lane; ii < len; ii += 32) Bk[ii - kk] -= colv[ii] * lk;
+    }
+    __syncthreads();
+  }
+}
+
+// Solve (L L^T) X = RHS in place for a column-major RHS of k columns
+// (leading dimension n) with the band factor.  Forward: right-looking with
+// the factor column; backward: dot products with the factor column.
+__global__ void k_band_solve(const double* __restrict__ band, const int64_t* __restrict__ boff,
+                             const int* __restrict__ bn, const int* __restrict__ bw,
+                             double* rhs, const int64_t* __restrict__ roff,
+                             const int* __restrict__ rk, int p0) {
+  __shared__ double sh[32];
+  const int p = p0 + blockIdx.x;
+  const double* B = band + boff[p];
+  const int n = bn[p], w = bw[p], W = w + 1, k = rk[p];
+  double* X = rhs + roff[p];
+  if (k == 0 || n == 0) return;
+  // forward: x_j /= l_jj; x_i -= l_ij x_j for i in (j, j+w]
+  for (int j = 0; j < n; ++j) {
+    const double* Bj = B + int64_t(j) * W;
+    const int len = min(w, n - 1 - j);
+    const double ip = 1.0 / Bj[0];
+    __syncthreads();
+    // every thread computes x_j for the columns it touches (reads before any write)
+    for (int q = threadIdx.x; q < len * k; q += blockDim.x) {
+      const int c = q / len, t = q - c * len;
+      const double xj = X[int64_t(c) * n + j] * ip;
+      X[int64_t(c) * n + j + 1 + t] -= Bj[1 + t] * xj;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) X[int64_t(c) * n + j] *= ip;
+  }
+  __syncthreads();
+  // backward: x_j = (x_j - sum_{i>j} l_ij x_i) / l_jj
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = n - 1; j >= 0; --j) {
+    const double* Bj = B + int64_t(j) * W;
+    const int len = min(w, n - 1 - j);
+    for (int c = wid; c < k; c += nw) {
+      double* Xc = X + int64_t(c) * n;
+      double acc = 0.0;
+      for (int t = lane; t < len; t += 32) acc += Bj[1 + t] * Xc[j + 1 + t];
+      acc = warp_sum(acc);
+      if (lane == 0) Xc[j] = (Xc[j] - acc) / Bj[0];
+    }
+    __syncthreads();
+  }
+  (void)sh;
+}
+
+// Interior blocks: band of A_IsIs and the right-hand sides -A_IsGamma Phi_Gamma
+// written straight into the interior block of Phi (zeroed beforehand).
+__global__ void k_assemble_interior(int s0, const int* __restrict__ rowptr,
+                                    const int* __restrict__ colind, const double* __restrict__ val,
+                                    const int* __restrict__ int_ptr, const int* __restrict__ int_dofs,
+                                    const int* __restrict__ dof_comp,
+                                    const int* __restrict__ dof_comprow,
+                                    const int* __restrict__ dof_introw,
+                                    const int* __restrict__ comp_c0, const int* __restrict__ comp_k,
+                                    int nsub, const int* __restrict__ brow_ptr,
+                                    const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
+                                    const int64_t* __restrict__ phi_off, double* __restrict__ phi,
+                                    double* band, const int64_t* __restrict__ boff,
+                                    const int* __restrict__ bw) {
+  const int s = s0 + blockIdx.x;
+  const int ns = int_ptr[s + 1] - int_ptr[s];
+  const int W = bw[s] + 1;
+  double* B = band + boff[s];
+  double* Ph = phi + phi_off[s];
+  const int* cols = bcol + bcol_ptr[s];
+  const int ncols = bcol_ptr[s + 1] - bcol_ptr[s];
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    const int g = int_dofs[int_ptr[s] + i];
+    for (int e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+      const int c = colind[e];
+      const int comp = dof_comp[c];
+      if (comp < 0) {
+        const int j = dof_introw[c];
+        if (j <= i) B[int64_t(j) * W + (i - j)] = val[e];
+        continue;
+      }
+      const int kc = comp_k[comp];
+      if (kc == 0) continue;
+      const int b = nsub + comp;
+      const int Rc = brow_ptr[b + 1] - brow_ptr[b];
+      const double* Pc = phi + phi_off[b];
+      const int rr = dof_comprow[c];
+      // the component's columns are contiguous in the block's sorted list
+      const int l0 = comp_c0[comp];
+      int lo = 0, hi = ncols;
+      while (lo < hi) { const int mid = (lo + hi) >> 1; if (cols[mid] < l0) lo = mid + 1; else hi = mid; }
+      for (int t = 0; t < kc; ++t) Ph[int64_t(lo + t) * ns + i] -= val[e] * Pc[int64_t(t) * Rc + rr];
+    }
+  }
+}
+
+// Band of A_s (exact local solver) from the local CSR values.
+__global__ void k_assemble_local_band(const int* __restrict__ om_ptr, const int* __restrict__ lm_sub_ent,
+                                      const uint16_t* __restrict__ lm_row, const int* __restrict__ lm_col,
+                                      const double* __restrict__ araw, double* band,
+                                      const int64_t* __restrict__ boff, const int* __restrict__ bw,
+                                      int p0) {
+  const int s = p0 + blockIdx.x;
+  const int W = bw[s] + 1;
+  double* B = band + boff[s];
+  for (int e = lm_sub_ent[s] + threadIdx.x; e < lm_sub_ent[s + 1]; e += blockDim.x) {
+    const int i = lm_row[e], j = lm_col[e];
+    if (j <= i) B[int64_t(j) * W + (i - j)] = araw[e];
+  }
+}
+
+__global__ void k_set_identity(double* X, const int64_t* __restrict__ xoff, const int* __restrict__ xn,
+                               int p0) {
+  const int p = p0 + blockIdx.x;
+  const int n = xn[p];
+  double* Xp = X + xoff[p];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Xp[int64_t(i) * n + i] = 1.0;
+}
+
+template <class T>
+__global__ void k_convert(int64_t len, const double* __restrict__ a, T* __restrict__ b) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < len;
+       q += int64_t(gridDim.x) * blockDim.x)
+    b[q] = T(a[q]);
+}
+
+// ---------------------------------------------------------------------------
+// Coarse matrix A0 = Phi^T A Phi = Phi_Gamma^T (A Phi)_Gamma  ((A Phi)_I = 0 by Eq. 2)
+// ---------------------------------------------------------------------------
+// One CTA (one warp) per coarse row k, owned by one interface component:
+//   A0[k, :] = sum_{g in Gamma_i} Phi[g, k] sum_j A[g, j] Phi[j, :]
+// accumulated in shared memory in a fixed order (deterministic).
+__global__ void k_coarse_rows(int n0, int nsub, const int* __restrict__ coarse_comp,
+                              const int* __restrict__ comp_c0, const int* __restrict__ rowptr,
+                              const int* __restrict__ colind, const double* __restrict__ val,
+                              const int* __restrict__ brow_ptr, const int* __restrict__ brow_dof,
+                              const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
+                              const int64_t* __restrict__ phi_off, const double* __restrict__ phi,
+                              const int* __restrict__ dof_blk, const int* __restrict__ dof_blkrow,
+                              double* __restrict__ A0) {
+  extern __shared__ double acc[];
+  const int k = blockIdx.x;
+  const int comp = coarse_comp[k];
+  const int b = nsub + comp;
+  const int t = k - comp_c0[comp];
+  const int R = brow_ptr[b + 1] - brow_ptr[b];
+  const double* Pk = phi + phi_off[b] + int64_t(t) * R;
+  for (int l = threadIdx.x; l < n0; l += blockDim.x) acc[l] = 0.0;
+  __syncwarp();
+  for (int r = 0; r < R; ++r) {
+    const int g = brow_dof[brow_ptr[b] + r];
+    const double pk = Pk[r];
+    for (int e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+      const int j = colind[e];
+      const double coef = pk * val[e];
+      const int bj = dof_blk[j], rj = dof_blkrow[j];
+      const int nr = brow_ptr[bj + 1] - brow_ptr[bj];
+      const int c0 = bcol_ptr[bj], kc = bcol_ptr[bj + 1] - c0;
+      const double* Pj = phi + phi_off[bj] + rj;
+      for (int u = threadIdx.x; u < kc; u += 32) acc[bcol[c0 + u]] += coef * Pj[int64_t(u) * nr];
+      __syncwarp();
+    }
+  }
+  for (int l = threadIdx.x; l < n0; l += blockDim.x) A0[int64_t(k) * n0 + l] = acc[l];
+}
+
+// ---------------------------------------------------------------------------
+// Dense FP64 Cholesky of A0 (row-major, lower, tiles of 32) and A0^-1
+// ---------------------------------------------------------------------------
+constexpr int NB = 32;
+
+__global__ void k_potrf_diag(double* A, int n, int J, int* err) {
+  __shared__ double T[NB][NB + 1];
+  const int j0 = J * NB, nb = min(NB, n - j0);
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    const int r = q / NB, c = q % NB;
+    T[r][c] = (r < nb && c < nb) ? A[int64_t(j0 + r) * n + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (threadIdx.x == 0) {
+      const double d = T[c][c];
+      if (!(d > 0.0)) { atomicOr(err, ERR_BREAKDOWN); T[c][c] = 1.0; }
+      else T[c][c] = sqrt(d);
+    }
+    __syncthreads();
+    const double ip = 1.0 / T[c][c];
+    for (int r = c + 1 + threadIdx.x; r < nb; r += blockDim.x) T[r][c] *= ip;
+    __syncthreads();
+    for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+      const int r = q / NB, cc = q % NB;
+      if (cc > c && r >= cc && r < nb) T[r][cc] -= T[r][c] * T[cc][c];
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    const int r = q / NB, c = q % NB;
+    if (r < nb && c <= r) A[int64_t(j0 + r) * n + j0 + c] = T[r][c];
+  }
+}
+
+// L_IJ = A_IJ L_JJ^-T for every row tile I > J (one CTA per tile, thread per row).
+__global__ void k_trsm_panel(double* A, int n, int J) {
+  __shared__ double Ld[NB][NB + 1];
+  __shared__ double X[NB][NB + 1];
+  const int j0 = J * NB, nb = min(NB, n - j0);
+  const int i0 = (J + 1 + blockIdx.x) * NB, mb = min(NB, n - i0);
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    const int r = q / NB, c = q % NB;
+    Ld[r][c] = (r < nb && c < nb) ? A[int64_t(j0 + r) * n + j0 + c] : 0.0;
+    X[r][c] = (r < mb && c < nb) ? A[int64_t(i0 + r) * n + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < mb) {
+    for (int c = 0; c < nb; ++c) {
+      double v = X[r][c];
+      for (int k = 0; k < c; ++k) v -= X[r][k] * Ld[c][k];
+      X[r][c] = v / Ld[c][c];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    const int rr = q / NB, c = q % NB;
+    if (rr < mb && c < nb) A[int64_t(i0 + rr) * n + j0 + c] = X[rr][c];
+  }
+}
+
+// A_IK -= L_IJ L_KJ^T for J < K <= I (grid over (I, K) tile pairs of the trailing part).
+__global__ void k_syrk_update(double* A, int n, int J) {
+  const int I = J + 1 + blockIdx.y, K = J + 1 + blockIdx.x;
+  if (K > I) return;
+  __shared__ double Li[NB][NB + 1];
+  __shared__ double Lk[NB][NB + 1];
+  const int j0 = J * NB, nb = min(NB, n - j0);
+  const int i0 = I * NB, k0 = K * NB;
+  const int mi = min(NB, n - i0), mk = min(NB, n - k0);
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    const int r = q / NB, c = q % NB;
+    Li[r][c] = (r < mi && c < nb) ? A[int64_t(i0 + r) * n + j0 + c] : 0.0;
+    Lk[r][c] = (r < mk && c < nb) ? A[int64_t(k0 + r) * n + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    const int r = q / NB, c = q % NB;
+    if (r >= mi || c >= mk) continue;
+    if (I == K && c > r) continue;
+    double v = 0.0;
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) v += Li[r][t] * Lk[c][t];
+    A[int64_t(i0 + r) * n + k0 + c] -= v;
+  }
+}
+
+// Columns [32*blockIdx.x, +32) of A0^-1 from the Cholesky factor: forward
+// L Y = E then backward L^T X = Y.  Thread (c, part): column c, every 8th
+// term of each inner product; parts are summed in a fixed order.
+__global__ void k_chol_inverse(const double* __restrict__ L, int n, double* W, double* Ainv) {
+  __shared__ double red[8][NB + 1];
+  const int c = threadIdx.x & 31, part = threadIdx.x >> 5;
+  const int col = blockIdx.x * NB + c;
+  const bool active = col < n;
+  double* Y = W + int64_t(blockIdx.x) * NB * n;   // Y[c*n + r]
+  const int cstart = blockIdx.x * NB;
+  for (int r = part; r < n; r += 8)
+    if (active) Y[int64_t(c) * n + r] = 0.0;
+  __syncthreads();
+  for (int r = cstart; r < n; ++r) {
+    double acc = 0.0;
+    if (active)
+      for (int k = cstart + part; k < r; k += 8) acc += L[int64_t(r) * n + k] * Y[int64_t(c) * n + k];
+    red[part][c] = acc;
+    __syncthreads();
+    if (part == 0 && active) {
+      double s = 0.0;
+      for (int q = 0; q < 8; ++q) s += red[q][c];
+      const double e = (r == col) ? 1.0 : 0.0;
+      Y[int64_t(c) * n + r] = (e - s) / L[int64_t(r) * n + r];
+    }
+    __syncthreads();
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double acc = 0.0;
+    if (active)
+      for (int k = r + 1 + part; k < n; k += 8) acc += L[int64_t(k) * n + r] * Y[int64_t(c) * n + k];
+    red[part][c] = acc;
+    __syncthreads();
+    if (part == 0 && active) {
+      double s = 0.0;
+      for (int q = 0; q < 8; ++q) s += red[q][c];
+      Y[int64_t(c) * n + r] = (Y[int64_t(c) * n + r] - s) / L[int64_t(r) * n + r];
+    }
+    __syncthreads();
+  }
+  for (int r = part; r < n; r += 8)
+    if (active) Ainv[int64_t(r) * n + col] = Y[int64_t(c) * n + r];
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+gdsw_status read_err(int* d_err, cudaStream_t s, const char* what) {
+  int h = 0;
+  GDSW_CK(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (h & ERR_BREAKDOWN) {
+    set_error("%s: non-positive or zero pivot", what);
+    return GDSW_ERR_BREAKDOWN;
+  }
+  return GDSW_OK;
+}
+
+int grid_for(int64_t work, int threads) {
+  int64_t g = (work + threads - 1) / threads;
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, int64_t(kNumSMs) * 32)));
+}
+
+// Temporary device buffers freed when the setup returns.
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() { for (void* p : ptrs) cudaFree(p); }
+  template <class T>
+  gdsw_status get(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of %zu scratch bytes failed", count * sizeof(T));
+      return GDSW_ERR_OUT_OF_MEMORY;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return GDSW_OK;
+  }
+  template <class T>
+  gdsw_status put(T** p, const std::vector<T>& v, cudaStream_t s) {
+    GDSW_TRY(get(p, v.size()));
+    if (!v.empty())
+      GDSW_CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return GDSW_OK;
+  }
+};
+
+// Factor every matrix of a batch of band problems; chunks keep the band
+// storage under `budget` bytes.  `fill(p0, p1, band, boff)` assembles the
+// bands of problems [p0, p1) into the zeroed buffer, `after(p0, p1, band,
+// boff)` consumes the factors.
+template <class Fill, class After>
+gdsw_status band_batches(int np, const std::vector<int>& bn, const std::vector<int>& bw,
+                         size_t budget, cudaStream_t s, int* d_err, Fill fill, After after) {
+  Scratch sc;
+  int* d_bn = nullptr;
+  int* d_bw = nullptr;
+  GDSW_TRY(sc.put(&d_bn, bn, s));
+  GDSW_TRY(sc.put(&d_bw, bw, s));
+  std::vector<int64_t> boff(np + 1, 0);
+  for (int p = 0; p < np; ++p) boff[p + 1] = boff[p] + int64_t(bn[p]) * (bw[p] + 1);
+  int64_t maxone = 0;
+  for (int p = 0; p < np; ++p) maxone = std::max<int64_t>(maxone, boff[p + 1] - boff[p]);
+  const int64_t cap = std::max<int64_t>(maxone, static_cast<int64_t>(budget / sizeof(double)));
+  double* band = nullptr;
+  GDSW_TRY(sc.get(&band, static_cast<size_t>(std::min<int64_t>(cap, boff[np]))));
+  int64_t* d_boff = nullptr;
+  GDSW_TRY(sc.get(&d_boff, np + 1));
+  int p0 = 0;
+  int maxw = 0;
+  for (int p = 0; p < np; ++p) maxw = std::max(maxw, bw[p]);
+  while (p0 < np) {
+    int p1 = p0;
+    while (p1 < np && boff[p1 + 1] - boff[p0] <= cap) ++p1;
+    std::vector<int64_t> loc(np + 1, 0);
+    for (int p = p0; p <= p1 && p <= np; ++p) loc[p] = boff[p] - boff[p0];
+    GDSW_CK(cudaMemcpyAsync(d_boff, loc.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    GDSW_CK(cudaMemsetAsync(band, 0, (boff[p1] - boff[p0]) * sizeof(double), s));
+    GDSW_TRY(fill(p0, p1, band, d_boff));
+    const size_t shm = std::max<size_t>(sizeof(double), size_t(maxw) * sizeof(double));
+    if (shm > 200 * 1024) { set_error("band width %d too large for the banded Cholesky", maxw); return GDSW_ERR_UNSUPPORTED; }
+    if (shm > 48 * 1024)
+      GDSW_CK(cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(shm)));
+    k_band_cholesky<<<p1 - p0, 512, shm, s>>>(band, d_boff, d_bn, d_bw, p0, d_err);
+    GDSW_CK(cudaGetLastError());
+    GDSW_TRY(after(p0, p1, band, d_boff, d_bn, d_bw));
+    GDSW_CK(cudaStreamSynchronize(s));   // the band buffer is reused by the next chunk
+    p0 = p1;
+  }
+  return GDSW_OK;
+}
+
+}  // namespace
+
+gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double* Z, int nn,
+                          cudaStream_t s) {
+  const gdsw_options& o = c->opt;
+  const bool exact = o.local_solver == GDSW_LOCAL_EXACT;
+  const bool ilu = o.local_solver == GDSW_LOCAL_ILU0;
+  const int nsub = P.nsub;
+  const int64_t nent = P.lm_col.size();
+  Scratch sc;
+  int* d_err = nullptr;
+  GDSW_TRY(sc.get(&d_err, 1));
+  GDSW_CK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+
+  // ---- global matrix and overlap ----
+  {
+    std::vector<int> rp(A->rowptr, A->rowptr + P.n + 1);
+    std::vector<int> ci(A->colind, A->colind + P.nnz);
+    std::vector<double> va(A->val, A->val + P.nnz);
+    GDSW_TRY(upload(c, &c->rowptr, rp, s));
+    GDSW_TRY(upload(c, &c->colind, ci, s));
+    GDSW_TRY(upload(c, &c->val, va, s));
+  }
+  GDSW_TRY(upload(c, &c->om_ptr, P.om_ptr, s));
+  GDSW_TRY(upload(c, &c->om_dofs, P.om_dofs, s));
+
+  // ---- local matrices ----
+  double t0 = now_s();
+  int *d_lm_sub_ent, *d_lm_rowptr, *d_lm_col, *d_lm_gent, *d_lm_diag, *d_lm_tpos;
+  uint16_t* d_lm_row;
+  GDSW_TRY(sc.put(&d_lm_sub_ent, P.lm_sub_ent, s));
+  GDSW_TRY(sc.put(&d_lm_rowptr, P.lm_rowptr, s));
+  GDSW_TRY(sc.put(&d_lm_col, P.lm_col, s));
+  GDSW_TRY(sc.put(&d_lm_gent, P.lm_gent, s));
+  GDSW_TRY(sc.put(&d_lm_diag, P.lm_diag, s));
+  GDSW_TRY(sc.put(&d_lm_row, P.lm_row, s));
+  double *d_sc, *d_at, *d_araw;
+  GDSW_TRY(sc.get(&d_sc, P.sum_m));
+  GDSW_TRY(sc.get(&d_at, nent));
+  GDSW_TRY(sc.get(&d_araw, nent));
+  k_extract_local<<<nsub, 256, 0, s>>>(c->val, c->om_ptr, d_lm_sub_ent, d_lm_gent, d_lm_row,
+                                       d_lm_col, d_lm_diag, d_sc, d_at, d_araw, d_err);
+  GDSW_CK(cudaGetLastError());
+
+  if (!exact) {
+    GDSW_TRY(read_err(d_err, s, "local matrix diagonal"));
+    GDSW_TRY(sc.put(&d_lm_tpos, P.lm_tpos, s));
+    double *F0, *F1, *G;
+    GDSW_TRY(sc.get(&F0, nent));
+    GDSW_TRY(sc.get(&F1, nent));
+    GDSW_TRY(sc.get(&G, nent));
+    const int sw = std::max(0, o.sweeps_factor);
+    if (ilu)
+      k_ilu0_sweeps<<<nsub, 256, 0, s>>>(c->om_ptr, d_lm_sub_ent, d_lm_rowptr, d_lm_col, d_lm_row,
+                                         d_lm_diag, d_lm_tpos, d_at, F0, F1, sw, d_err);
+    else
+      k_ic0_sweeps<<<nsub, 256, 0, s>>>(c->om_ptr, d_lm_sub_ent, d_lm_rowptr, d_lm_col, d_lm_row,
+                                        d_lm_diag, d_at, F0, F1, sw, d_err);
+    GDSW_CK(cudaGetLastError());
+    GDSW_TRY(read_err(d_err, s, ilu ? "ILU(0) sweeps" : "IC(0) sweeps"));
+    double* F = (sw % 2 == 0) ? F0 : F1;
+    // subdomain row base of every entry
+    std::vector<int> ebase(nent);
+    for (int q = 0; q < nsub; ++q)
+      for (int e = P.lm_sub_ent[q]; e < P.lm_sub_ent[q + 1]; ++e) ebase[e] = P.om_ptr[q];
+    int* d_ebase;
+    GDSW_TRY(sc.put(&d_ebase, ebase, s));
+    k_unscale<<<grid_for(nent, 256), 256, 0, s>>>(static_cast<int>(nent), ilu ? 1 : 0, nullptr,
+                                                  d_lm_row, d_lm_col, d_ebase, d_sc, F, G);
+    GDSW_CK(cudaGetLastError());
+    // level-sliced ELL in the apply precision
+    struct Side { const EllPlan* E; int** sub; int4** lev; uint16_t** lrows; uint16_t** col; void** val; void** dinv; };
+    Side sides[2] = {{&P.L, &c->L_sub_lev, &c->L_lev, &c->L_lrows, &c->L_col, &c->L_val, &c->L_dinv},
+                     {&P.U, &c->U_sub_lev, &c->U_lev, &c->U_lrows, &c->U_col, &c->U_val, &c->U_dinv}};
+    for (Side& sd : sides) {
+      const EllPlan& E = *sd.E;
+      std::vector<int4> lev(E.lev_nr.size());
+      for (size_t l = 0; l < lev.size(); ++l)
+        lev[l] = make_int4(E.lev_start[l], E.lev_nr[l], E.lev_K[l], E.lev_off[l]);
+      GDSW_TRY(upload(c, sd.sub, E.sub_lev, s));
+      GDSW_TRY(upload(c, sd.lev, lev, s));
+      GDSW_TRY(upload(c, sd.lrows, E.lrows, s));
+      GDSW_TRY(upload(c, sd.col, E.col, s));
+      int *d_src, *d_dsrc;
+      GDSW_TRY(sc.put(&d_src, E.src, s));
+      GDSW_TRY(sc.put(&d_dsrc, E.dsrc, s));
+      if (c->fp32) {
+        float *v, *d;
+        GDSW_TRY(dalloc(c, &v, E.slots));
+        GDSW_TRY(dalloc(c, &d, P.sum_m));
+        k_pack_ell<float><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, G, v);
+        k_pack_dinv<float><<<grid_for(P.sum_m, 256), 256, 0, s>>>(P.sum_m, d_dsrc, G, d);
+        *sd.val = v; *sd.dinv = d;
+      } else {
+        double *v, *d;
+        GDSW_TRY(dalloc(c, &v, E.slots));
+        GDSW_TRY(dalloc(c, &d, P.sum_m));
+        k_pack_ell<double><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, G, v);
+        k_pack_dinv<double><<<grid_for(P.sum_m, 256), 256, 0, s>>>(P.sum_m, d_dsrc, G, d);
+        *sd.val = v; *sd.dinv = d;
+      }
+      GDSW_CK(cudaGetLastError());
+    }
+    c->max_levels = std::max(P.L.max_levels, P.U.max_levels);
+    GDSW_CK(cudaStreamSynchronize(s));   // scratch of this stage is released below
+  }
+  c->stats.setup_phase_seconds[1] = now_s() - t0;
+
+  // ---- Phi_Gamma: MGS per component ----
+  t0 = now_s();
+  std::vector<int> comp_rank(P.ncomp, 0);
+  double* d_Q = nullptr;
+  int* d_comp_ptr = nullptr;
+  int* d_comp_dofs = nullptr;
+  int zcols = nn;
+  const bool coarse = o.coarse == GDSW_COARSE_GDSW && P.ncomp > 0;
+  if (coarse) {
+    double* d_Z;
+    std::vector<double> zh;
+    if (Z == nullptr || nn == 0) { zh.assign(P.n, 1.0); zcols = 1; }
+    else zh.assign(Z, Z + int64_t(P.n) * nn);
+    GDSW_TRY(sc.put(&d_Z, zh, s));
+    GDSW_TRY(sc.put(&d_comp_ptr, P.comp_ptr, s));
+    GDSW_TRY(sc.put(&d_comp_dofs, P.comp_dofs, s));
+    GDSW_TRY(sc.get(&d_Q, size_t(P.comp_ptr[P.ncomp]) * zcols));
+    int* d_rank;
+    GDSW_TRY(sc.get(&d_rank, P.ncomp));
+    k_mgs<<<P.ncomp, 128, 0, s>>>(d_comp_ptr, d_comp_dofs, d_Z, P.n, zcols, d_Q, d_rank);
+    GDSW_CK(cudaGetLastError());
+    GDSW_CK(cudaMemcpyAsync(comp_rank.data(), d_rank, P.ncomp * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GDSW_CK(cudaStreamSynchronize(s));
+  }
+  CoarsePlan C;
+  GDSW_TRY(build_coarse_plan(P, comp_rank, coarse, &C));
+  c->n0 = C.n0;
+  c->nblk = C.nblk;
+  GDSW_TRY(upload(c, &c->brow_ptr, C.brow_ptr, s));
+  GDSW_TRY(upload(c, &c->brow_dof, C.brow_dof, s));
+  GDSW_TRY(upload(c, &c->bcol_ptr, C.bcol_ptr, s));
+  GDSW_TRY(upload(c, &c->bcol, C.bcol, s));
+  GDSW_TRY(upload(c, &c->phi_off, C.phi_off, s));
+  GDSW_TRY(upload(c, &c->cs_ptr, C.cs_ptr, s));
+  GDSW_TRY(upload(c, &c->cs_idx, C.cs_idx, s));
+  GDSW_TRY(upload(c, &c->pull_ptr, C.pull_ptr, s));
+  GDSW_TRY(upload(c, &c->pull_pos, C.pull_pos, s));
+  c->n_slots = C.bcol_ptr[C.nblk];
+  c->stats.nnz_phi = C.phi_len;
+  c->max_bcols = 0;
+  for (int b = 0; b < C.nblk; ++b) c->max_bcols = std::max(c->max_bcols, C.bcol_ptr[b + 1] - C.bcol_ptr[b]);
+  GDSW_TRY(dalloc(c, &c->partial, std::max(1, c->n_slots)));
+  GDSW_TRY(dalloc(c, &c->cvec, std::max(1, C.n0)));
+  GDSW_TRY(dalloc(c, &c->yvec, std::max(1, C.n0)));
+  double* phi64 = nullptr;
+  if (C.n0 > 0) {
+    GDSW_TRY(sc.get(&phi64, C.phi_len));
+    GDSW_CK(cudaMemsetAsync(phi64, 0, C.phi_len * sizeof(double), s));
+    int* d_bcol_ptr = c->bcol_ptr;
+    k_copy_phig<<<P.ncomp, 256, 0, s>>>(nsub, d_comp_ptr, zcols, d_Q, d_bcol_ptr, c->phi_off, phi64);
+    GDSW_CK(cudaGetLastError());
+  }
+  c->stats.setup_phase_seconds[2] = now_s() - t0;
+
+  // ---- Phi_I = -A_II^-1 A_IGamma Phi_Gamma (Eq. 2), banded Cholesky per interior ----
+  t0 = now_s();
+  if (C.n0 > 0) {
+    int *d_int_ptr, *d_int_dofs, *d_dof_comp, *d_dof_comprow, *d_dof_introw, *d_c0, *d_ck;
+    GDSW_TRY(sc.put(&d_int_ptr, P.int_ptr, s));
+    GDSW_TRY(sc.put(&d_int_dofs, P.int_dofs, s));
+    GDSW_TRY(sc.put(&d_dof_comp, P.dof_comp, s));
+    GDSW_TRY(sc.put(&d_dof_comprow, P.dof_comprow, s));
+    GDSW_TRY(sc.put(&d_dof_introw, P.dof_introw, s));
+    GDSW_TRY(sc.put(&d_c0, C.comp_c0, s));
+    GDSW_TRY(sc.put(&d_ck, C.comp_k, s));
+    std::vector<int> bn(nsub), bwv(nsub), rk(nsub);
+    std::vector<int64_t> roff(nsub);
+    for (int q = 0; q < nsub; ++q) {
+      bn[q] = P.int_ptr[q + 1] - P.int_ptr[q];
+      bwv[q] = P.int_bw[q];
+      rk[q] = C.bcol_ptr[q + 1] - C.bcol_ptr[q];
+      roff[q] = C.phi_off[q];
+    }
+    int* d_rk;
+    int64_t* d_roff;
+    GDSW_TRY(sc.put(&d_rk, rk, s));
+    GDSW_TRY(sc.put(&d_roff, roff, s));
+    int* d_bw_full;
+    GDSW_TRY(sc.put(&d_bw_full, bwv, s));
+    auto fill = [&](int p0, int p1, double* band, int64_t* d_boff) -> gdsw_status {
+      k_assemble_interior<<<p1 - p0, 256, 0, s>>>(
+          p0, c->rowptr, c->colind, c->val, d_int_ptr, d_int_dofs, d_dof_comp, d_dof_comprow,
+          d_dof_introw, d_c0, d_ck, nsub, c->brow_ptr, c->bcol_ptr, c->bcol, c->phi_off, phi64,
+          band, d_boff, d_bw_full);
+      GDSW_CK(cudaGetLastError());
+      return GDSW_OK;
+    };
+    auto after = [&](int p0, int p1, double* band, int64_t* d_boff, int* d_bn, int* d_bw) -> gdsw_status {
+      k_band_solve<<<p1 - p0, 256, 0, s>>>(band, d_boff, d_bn, d_bw, phi64, d_roff, d_rk, p0);
+      GDSW_CK(cudaGetLastError());
+      return GDSW_OK;
+    };
+    GDSW_TRY(band_batches(nsub, bn, bwv, size_t(6) << 30, s, d_err, fill, after));
+    GDSW_TRY(read_err(d_err, s, "interior Cholesky"));
+  }
+  c->stats.setup_phase_seconds[3] = now_s() - t0;
+
+  // ---- A0 = Phi^T A Phi and its inverse ----
+  t0 = now_s();
+  if (C.n0 > 0) {
+    const int n0 = C.n0;
+    std::vector<int> coarse_comp(n0);
+    for (int q = 0; q < P.ncomp; ++q)
+      for (int t = 0; t < C.comp_k[q]; ++t) coarse_comp[C.comp_c0[q] + t] = q;
+    int *d_cc, *d_c0b, *d_dof_blk, *d_dof_blkrow;
+    GDSW_TRY(sc.put(&d_cc, coarse_comp, s));
+    GDSW_TRY(sc.put(&d_c0b, C.comp_c0, s));
+    GDSW_TRY(sc.put(&d_dof_blk, C.dof_blk, s));
+    GDSW_TRY(sc.put(&d_dof_blkrow, C.dof_blkrow, s));
+    double* d_A0;
+    GDSW_TRY(sc.get(&d_A0, size_t(n0) * n0));
+    const size_t shm = size_t(n0) * sizeof(double);
+    if (shm > 227 * 1024) { set_error("coarse dimension %d too large for the A0 kernel", n0); return GDSW_ERR_UNSUPPORTED; }
+    if (shm > 48 * 1024)
+      GDSW_CK(cudaFuncSetAttribute(k_coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
+    k_coarse_rows<<<n0, 32, shm, s>>>(n0, nsub, d_cc, d_c0b, c->rowptr, c->colind, c->val, c->brow_ptr,
+                                      c->brow_dof, c->bcol_ptr, c->bcol, c->phi_off, phi64, d_dof_blk,
+                                      d_dof_blkrow, d_A0);
+    GDSW_CK(cudaGetLastError());
+    c->stats.setup_phase_seconds[4] = now_s() - t0;
+    t0 = now_s();
+    const int nbk = (n0 + NB - 1) / NB;
+    for (int J = 0; J < nbk; ++J) {
+      k_potrf_diag<<<1, 256, 0, s>>>(d_A0, n0, J, d_err);
+      const int rest = nbk - J - 1;
+      if (rest > 0) {
+        k_trsm_panel<<<rest, 32, 0, s>>>(d_A0, n0, J);
+        k_syrk_update<<<dim3(rest, rest), 256, 0, s>>>(d_A0, n0, J);
+      }
+    }
+    GDSW_CK(cudaGetLastError());
+    GDSW_TRY(read_err(d_err, s, "coarse Cholesky"));
+    double* d_W;
+    GDSW_TRY(sc.get(&d_W, size_t(nbk) * NB * n0));
+    GDSW_TRY(dalloc(c, &c->A0inv, size_t(n0) * n0));
+    k_chol_inverse<<<nbk, 256, 0, s>>>(d_A0, n0, d_W, c->A0inv);
+    GDSW_CK(cudaGetLastError());
+    // Phi in the apply precision
+    if (c->fp32) {
+      float* pf;
+      GDSW_TRY(dalloc(c, &pf, C.phi_len));
+      k_convert<float><<<grid_for(C.phi_len, 256), 256, 0, s>>>(C.phi_len, phi64, pf);
+      c->phi = pf;
+    } else {
+      double* pd;
+      GDSW_TRY(dalloc(c, &pd, C.phi_len));
+      GDSW_CK(cudaMemcpyAsync(pd, phi64, C.phi_len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      c->phi = pd;
+    }
+    GDSW_CK(cudaGetLastError());
+    GDSW_CK(cudaStreamSynchronize(s));
+    c->stats.setup_phase_seconds[5] = now_s() - t0;
+  }
+
+  // ---- exact local solver: dense inverse of each A_s ----
+  t0 = now_s();
+  if (exact) {
+    GDSW_TRY(read_err(d_err, s, "local matrix"));
+    std::vector<int> mn(nsub);
+    std::vector<int64_t> xoff(nsub + 1, 0);
+    for (int q = 0; q < nsub; ++q) {
+      mn[q] = P.om_ptr[q + 1] - P.om_ptr[q];
+      xoff[q + 1] = xoff[q] + int64_t(mn[q]) * mn[q];
+    }
+    const int64_t total = xoff[nsub];
+    if (total > (int64_t(1) << 31)) {
+      set_error("exact local solver needs %lld dense entries; use IC0/ILU0 for subdomains this large",
+                (long long)total);
+      return GDSW_ERR_UNSUPPORTED;
+    }
+    double* X;
+    GDSW_TRY(sc.get(&X, total));
+    GDSW_CK(cudaMemsetAsync(X, 0, total * sizeof(double), s));
+    int64_t* d_xoff;
+    int* d_mn;
+    GDSW_TRY(sc.put(&d_xoff, xoff, s));
+    GDSW_TRY(sc.put(&d_mn, mn, s));
+    GDSW_TRY(upload(c, &c->ainv_off, xoff, s));
+    k_set_identity<<<nsub, 256, 0, s>>>(X, d_xoff, d_mn, 0);
+    GDSW_CK(cudaGetLastError());
+    std::vector<int> obw(P.om_bw.begin(), P.om_bw.end());
+    int* d_obw;
+    GDSW_TRY(sc.put(&d_obw, obw, s));
+    auto fill = [&](int p0, int p1, double* band, int64_t* d_boff) -> gdsw_status {
+      k_assemble_local_band<<<p1 - p0, 256, 0, s>>>(c->om_ptr, d_lm_sub_ent, d_lm_row, d_lm_col, d_araw,
+                                                    band, d_boff, d_obw, p0);
+      GDSW_CK(cudaGetLastError());
+      return GDSW_OK;
+    };
+    auto after = [&](int p0, int p1, double* band, int64_t* d_boff, int* d_bn, int* d_bw) -> gdsw_status {
+      k_band_solve<<<p1 - p0, 256, 0, s>>>(band, d_boff, d_bn, d_bw, X, d_xoff, d_mn, p0);
+      GDSW_CK(cudaGetLastError());
+      return GDSW_OK;
+    };
+    GDSW_TRY(band_batches(nsub, mn, obw, size_t(4) << 30, s, d_err, fill, after));
+    GDSW_TRY(read_err(d_err, s, "exact local Cholesky"));
+    if (c->fp32) {
+      float* a;
+      GDSW_TRY(dalloc(c, &a, total));
+      k_convert<float><<<grid_for(total, 256), 256, 0, s>>>(total, X, a);
+      c->ainv = a;
+    } else {
+      double* a;
+      GDSW_TRY(dalloc(c, &a, total));
+      GDSW_CK(cudaMemcpyAsync(a, X, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      c->ainv = a;
+    }
+    GDSW_CK(cudaGetLastError());
+    GDSW_CK(cudaStreamSynchronize(s));
+    c->stats.dense_local = total;
+  }
+  c->stats.setup_phase_seconds[6] = now_s() - t0;
+  return GDSW_OK;
+}
+
+}  // namespace gdsw

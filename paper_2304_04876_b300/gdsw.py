@@ -1,0 +1,221 @@
+"""Thin Python binding of libgdsw (include/gdsw.h): argument marshalling only.
+
+Every step of setup, apply and solve runs in the CUDA library; this module
+converts numpy arrays and torch tensors to the pointers and structs of the C
+ABI and turns status codes into exceptions.  There is no fallback: if the
+library is missing or fails to load, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgdsw.so")
+
+OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA, \
+    ERR_UNSUPPORTED = range(8)
+LOCAL = {"exact": 0, "ic0": 1, "ilu0": 2}
+TRSV = {"levelsched": 0, "jacobi": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+KRYLOV = {"pcg": 0, "gmres": 1}
+COARSE = {"gdsw": 0, "none": 1}
+
+
+class CSRStruct(C.Structure):
+    _fields_ = [("n", C.c_int32), ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("val", C.c_void_p)]
+
+
+class PartitionStruct(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dofs_per_node", C.c_int32),
+                ("ncut", C.c_int32 * 3), ("cut", C.c_void_p * 3)]
+
+
+class Options(C.Structure):
+    _fields_ = [("local_solver", C.c_int32), ("trsv", C.c_int32), ("sweeps_factor", C.c_int32),
+                ("sweeps_trsv", C.c_int32), ("overlap", C.c_int32), ("precision", C.c_int32),
+                ("krylov", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32),
+                ("coarse", C.c_int32), ("flexible", C.c_int32), ("tol", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("true_relres", C.c_double),
+                ("seconds", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in (
+        "n", "nnz", "n_sub", "n0", "n_comp", "sum_omega", "max_omega", "nnz_L", "nnz_U", "ell_L",
+        "ell_U", "nnz_phi", "n_levels_L", "n_levels_U", "max_levels", "dense_local", "n_blocks",
+        "device_bytes")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8)]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "setup_phase_seconds"}
+        d["setup_phase_seconds"] = list(self.setup_phase_seconds)
+        return d
+
+
+class GdswError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+# exported symbol -> (restype, argtypes)
+SIGNATURES = {
+    "gdsw_default_options": (None, [C.POINTER(Options)]),
+    "gdsw_setup": (C.c_int, [C.POINTER(CSRStruct), C.POINTER(PartitionStruct), C.c_void_p, C.c_int32,
+                             C.POINTER(Options), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "gdsw_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gdsw_apply_timed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "gdsw_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gdsw_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
+    "gdsw_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
+    "gdsw_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "gdsw_destroy": (C.c_int, [C.c_void_p]),
+    "gdsw_status_string": (C.c_char_p, [C.c_int]),
+    "gdsw_last_error": (C.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libgdsw.so (built in-tree by ``paper_2304_04876_b300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgdsw.so not found at {path}; run `python -m paper_2304_04876_b300.build`")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        lib = load()
+        raise GdswError(status, f"{what}: {lib.gdsw_status_string(status).decode()}: "
+                                f"{lib.gdsw_last_error().decode()}")
+
+
+def default_options() -> Options:
+    o = Options()
+    load().gdsw_default_options(C.byref(o))
+    return o
+
+
+def make_options(**kw) -> Options:
+    o = default_options()
+    for k, v in kw.items():
+        table = {"local_solver": LOCAL, "trsv": TRSV, "precision": PRECISION, "krylov": KRYLOV,
+                 "coarse": COARSE}.get(k)
+        if table is not None and isinstance(v, str):
+            v = table[v]
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor (contiguous float64)."""
+    assert t.is_cuda and t.is_contiguous() and t.dtype.is_floating_point, "expected a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Handle:
+    """One set-up problem: factors, Phi and A0^-1 resident on the device."""
+
+    def __init__(self, A, part, Z: Optional[np.ndarray] = None, stream=None, **options):
+        lib = load()
+        rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+        colind = np.ascontiguousarray(A.colind, dtype=np.int32)
+        val = np.ascontiguousarray(A.val, dtype=np.float64)
+        csr = CSRStruct(int(A.n), rowptr.ctypes.data, colind.ctypes.data, val.ctypes.data)
+        cuts = [np.ascontiguousarray(c, dtype=np.int32) for c in part.cuts]
+        ps = PartitionStruct(int(part.nx), int(part.ny), int(part.nz), int(part.dpn))
+        for a in range(3):
+            ps.ncut[a] = len(cuts[a])
+            ps.cut[a] = cuts[a].ctypes.data if len(cuts[a]) else None
+        if Z is None:
+            zp, nn = None, 0
+        else:
+            Zc = np.asfortranarray(np.asarray(Z, dtype=np.float64).reshape(A.n, -1))
+            zp, nn = Zc.ctypes.data, Zc.shape[1]
+        self.options = make_options(**options)
+        h = C.c_void_p()
+        _check(lib.gdsw_setup(C.byref(csr), C.byref(ps), zp, nn, C.byref(self.options),
+                              _stream(stream) if stream is not False else None, C.byref(h)), "gdsw_setup")
+        self._h = h
+        self.n = int(A.n)
+
+    def _handle(self):
+        if self._h is None:
+            raise RuntimeError("handle destroyed")
+        return self._h
+
+    def apply(self, r, z, stream=None):
+        _check(load().gdsw_apply(self._handle(), _ptr(r), _ptr(z), _stream(stream)), "gdsw_apply")
+        return z
+
+    def apply_timed(self, r, z, stream=None):
+        ms = (C.c_double * 4)()
+        _check(load().gdsw_apply_timed(self._handle(), _ptr(r), _ptr(z), _stream(stream), ms),
+               "gdsw_apply_timed")
+        return list(ms)
+
+    def spmv(self, x, y, stream=None):
+        _check(load().gdsw_spmv(self._handle(), _ptr(x), _ptr(y), _stream(stream)), "gdsw_spmv")
+        return y
+
+    def solve(self, b, x, stream=None, raise_on_nonconvergence=True) -> SolveInfo:
+        info = SolveInfo()
+        st = load().gdsw_solve(self._handle(), _ptr(b), _ptr(x), C.byref(info), _stream(stream))
+        if st != ERR_NOT_CONVERGED or raise_on_nonconvergence:
+            _check(st, "gdsw_solve")
+        return info
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray, stream=None, raise_on_nonconvergence=True) -> SolveInfo:
+        """b, x: host float64 arrays (page-locked memory makes the copies asynchronous)."""
+        info = SolveInfo()
+        st = load().gdsw_solve_host(self._handle(), C.c_void_p(_host_ptr(b)), C.c_void_p(_host_ptr(x)),
+                                    C.byref(info), _stream(stream))
+        if st != ERR_NOT_CONVERGED or raise_on_nonconvergence:
+            _check(st, "gdsw_solve_host")
+        return info
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().gdsw_get_stats(self._handle(), C.byref(s)), "gdsw_get_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self._h is not None:
+            load().gdsw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a) -> int:
+    if hasattr(a, "data_ptr"):           # a pinned torch CPU tensor
+        assert not a.is_cuda and a.is_contiguous() and a.dtype.is_floating_point
+        return a.data_ptr()
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point the
+header declares, and rejects malformed input in the symbolic phase (before any
+device work, so these run without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2304_04876_b300 import build as B
+from paper_2304_04876_b300 import gdsw as G
+from paper_2304_04876_b300 import problems as P
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gdsw.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return G.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"GDSW_API\s+[\w\s\*]+?\b(gdsw_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in G.SIGNATURES, f"binding lacks {name}"
+
+
+def test_default_options_and_status_strings(lib):
+    o = G.default_options()
+    assert (o.local_solver, o.trsv, o.sweeps_factor, o.sweeps_trsv, o.overlap) == (1, 0, 3, 5, 1)
+    assert (o.precision, o.krylov, o.restart, o.maxit, o.coarse, o.flexible) == (0, 0, 30, 2000, 0, -1)
+    assert o.tol == 1e-8
+    for s in range(8):
+        assert lib.gdsw_status_string(s)
+    assert lib.gdsw_status_string(99) == b"unknown status"
+    assert lib.gdsw_destroy(None) == G.OK
+
+
+def _expect(status, A, part, **opts):
+    with pytest.raises(G.GdswError) as e:
+        G.Handle(A, part, None, stream=False, **opts)
+    assert e.value.status == status
+    return str(e.value)
+
+
+def test_rejects_malformed_input_on_host(lib):
+    prob = P.poisson_problem(8, 4)
+    A, part = prob.A, prob.part
+    # partition size mismatch
+    bad = P.Partition(8, 8, 7, 1, part.cuts)
+    assert "unknowns" in _expect(G.ERR_INVALID_ARG, A, bad)
+    # cut outside the grid / not ascending
+    _expect(G.ERR_INVALID_ARG, A, P.Partition(8, 8, 8, 1, [[7], [3], [3]]))
+    _expect(G.ERR_INVALID_ARG, A, P.Partition(8, 8, 8, 1, [[3, 2], [3], [3]]))
+    # unsorted columns
+    ci = A.colind.copy()
+    ci[0], ci[1] = ci[1], ci[0]
+    _expect(G.ERR_INVALID_ARG, P.CSR(A.n, A.rowptr, ci, A.val), part)
+    # a row without diagonal
+    Ad = A.to_scipy().tolil()
+    Ad[5, 5] = 0
+    Ad = Ad.tocsr()
+    Ad.eliminate_zeros()
+    _expect(G.ERR_INVALID_ARG, P.CSR.from_scipy(Ad), part)
+    # structurally nonsymmetric pattern
+    Ad = A.to_scipy().tolil()
+    Ad[0, 9] = -0.5
+    _expect(G.ERR_INVALID_ARG, P.CSR.from_scipy(Ad.tocsr()), part)
+    # partition that does not split the graph: a coupling across a block boundary
+    # that skips the separator plane
+    Ad = A.to_scipy().tolil()
+    Ad[0, 5] = -0.1
+    Ad[5, 0] = -0.1
+    assert "split" in _expect(G.ERR_INVALID_ARG, P.CSR.from_scipy(Ad.tocsr()), part)
+    # invalid options
+    _expect(G.ERR_INVALID_ARG, A, part, local_solver=7)
+    _expect(G.ERR_INVALID_ARG, A, part, tol=0.0)
+
+
+def test_structs_match_header(lib):
+    """Field order and sizes of the binding's structs follow the header."""
+    text = open(HEADER).read()
+    body = text[text.index("typedef struct {\n  int32_t local_solver"):]
+    body = body[:body.index("} gdsw_options;")]
+    fields = re.findall(r"(?:int32_t|double)\s+(\w+);", body)
+    assert fields == [f for f, _ in G.Options._fields_]
+    assert C.sizeof(G.Options) == 11 * 4 + 4 + 8
+    assert C.sizeof(G.Stats) == 18 * 8 + 9 * 8

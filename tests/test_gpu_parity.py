@@ -1,0 +1,185 @@
+"""CUDA path against the oracle on small problems: the preconditioner apply (Eq. 1)
+element by element, SpMV, and the Krylov solves.  FP64 apply tolerance 1e-10
+relative (2-norm); PCG/GMRES iteration counts within +-1; true residual <= 1e-8."""
+import numpy as np
+import pytest
+
+from paper_2304_04876_b300 import problems as P
+from tests.gpu_util import gpu_apply, gpu_handle, gpu_solve, gpu_spmv, oracle_for, relerr
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2304_04876_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _ragged():
+    # 13 nodes per axis with blocks of 4: three full blocks and a last block of one node
+    return P.poisson_problem(13, 4, seed=3)
+
+
+def _diffusion():
+    k = 10 ** np.random.default_rng(7).uniform(-2, 2, (10, 10, 10))
+    A = P.diffusion7(k)
+    cuts = P.uniform_cuts(10, 4)
+    part = P.Partition(10, 10, 10, 1, [cuts, cuts, cuts])
+    return P.Problem("diff10", A, part, np.ones((A.n, 1)), P.rhs_uniform(A.n, 1))
+
+
+APPLY_CASES = [
+    ("cfg1_exact", lambda: P.config_problem(1), dict(local="exact")),
+    ("poisson12_ic0_ls", lambda: P.poisson_problem(12, 4), dict(local="ic0", trsv="levelsched")),
+    ("poisson12_ic0_jac", lambda: P.poisson_problem(12, 4), dict(local="ic0", trsv="jacobi")),
+    ("poisson12_ilu0_ls", lambda: P.poisson_problem(12, 4), dict(local="ilu0", trsv="levelsched")),
+    ("poisson12_ilu0_jac", lambda: P.poisson_problem(12, 4), dict(local="ilu0", trsv="jacobi")),
+    ("ragged13_ic0", _ragged, dict(local="ic0")),
+    ("ragged13_exact", _ragged, dict(local="exact")),
+    ("diffusion10_ic0", _diffusion, dict(local="ic0")),
+    ("elast4_exact", lambda: P.elasticity_problem(4, 2), dict(local="exact")),
+    ("elast6_ilu0", lambda: P.elasticity_problem(6, 2), dict(local="ilu0")),
+    ("elast6_ilu0_jac", lambda: P.elasticity_problem(6, 2), dict(local="ilu0", trsv="jacobi")),
+    ("one_level", lambda: P.poisson_problem(12, 4), dict(local="ic0", coarse="none")),
+    ("single_subdomain", lambda: P.poisson_problem(6, 6), dict(local="exact")),
+    ("overlap2", lambda: P.poisson_problem(12, 4), dict(local="ic0", overlap=2)),
+    ("sweeps7", lambda: P.poisson_problem(12, 4), dict(local="ic0", trsv="jacobi", sweeps_factor=7, sweeps_trsv=2)),
+]
+
+
+@pytest.mark.parametrize("name,make,opts", APPLY_CASES, ids=[c[0] for c in APPLY_CASES])
+def test_apply_matches_oracle(name, make, opts):
+    prob = make()
+    M = oracle_for(prob, **opts)
+    h = gpu_handle(prob, **{("local_solver" if k == "local" else k): v for k, v in opts.items()})
+    st = h.stats()
+    assert st["n0"] == M.n0 and st["sum_omega"] == sum(len(o) for o in M.omega)
+    for seed in range(3):
+        r = np.random.default_rng(seed).uniform(-1, 1, prob.A.n)
+        z = gpu_apply(h, r)
+        assert relerr(z, M.apply(r)) <= TOL_FP64, name
+    h.close()
+
+
+@pytest.mark.parametrize("local,trsv", [("ic0", "levelsched"), ("ic0", "jacobi"), ("exact", "levelsched"),
+                                        ("ilu0", "levelsched")])
+def test_fp32_preconditioner_close_to_fp64(local, trsv):
+    prob = P.poisson_problem(12, 4)
+    M = oracle_for(prob, local=local, trsv=trsv)
+    h = gpu_handle(prob, local_solver=local, trsv=trsv, precision="fp32")
+    r = np.random.default_rng(0).uniform(-1, 1, prob.A.n)
+    assert relerr(gpu_apply(h, r), M.apply(r)) <= 2e-5
+
+
+def test_spmv_matches_csr_product():
+    for prob in (P.poisson_problem(12, 4), P.elasticity_problem(4, 2)):
+        h = gpu_handle(prob, local_solver="exact")
+        x = np.random.default_rng(1).uniform(-1, 1, prob.A.n)
+        y = gpu_spmv(h, x)
+        ref = prob.A.to_scipy() @ x
+        assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_apply_is_deterministic():
+    prob = P.poisson_problem(12, 4)
+    h = gpu_handle(prob, local_solver="ic0")
+    r = np.random.default_rng(5).uniform(-1, 1, prob.A.n)
+    z0 = gpu_apply(h, r)
+    for _ in range(9):
+        assert np.array_equal(gpu_apply(h, r), z0)
+
+
+PCG_CASES = [
+    ("cfg1_exact", lambda: P.config_problem(1), dict(local="exact")),
+    ("poisson12_ic0", lambda: P.poisson_problem(12, 4), dict(local="ic0")),
+    ("poisson12_ic0_jac", lambda: P.poisson_problem(12, 4), dict(local="ic0", trsv="jacobi")),
+    ("ragged13_ilu0", _ragged, dict(local="ilu0")),
+    ("diffusion10_ic0", _diffusion, dict(local="ic0")),
+    ("elast6_exact", lambda: P.elasticity_problem(6, 2), dict(local="exact")),
+]
+
+
+@pytest.mark.parametrize("name,make,opts", PCG_CASES, ids=[c[0] for c in PCG_CASES])
+def test_pcg_matches_oracle(name, make, opts):
+    from oracle import gdsw_oracle as O
+    prob = make()
+    M = oracle_for(prob, **opts)
+    xo, io = O.pcg(M.spmv, M.apply, prob.b, tol=1e-8)
+    h = gpu_handle(prob, **{("local_solver" if k == "local" else k): v for k, v in opts.items()})
+    x, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    assert abs(info.iters - io.iters) <= 1, (info.iters, io.iters)
+    true = np.linalg.norm(prob.b - prob.A.to_scipy() @ x) / np.linalg.norm(prob.b)
+    assert true <= 1e-8
+    assert relerr(x, xo) <= 1e-6
+
+
+def test_pcg_single_subdomain_one_iteration_and_zero_rhs():
+    prob = P.poisson_problem(6, 6)
+    h = gpu_handle(prob, local_solver="exact")
+    x, info = gpu_solve(h, prob.b)
+    assert info.iters == 1 and info.converged
+    x, info = gpu_solve(h, np.zeros(prob.A.n))
+    assert info.iters == 0 and not x.any()
+    # warm start at the solution
+    xs = np.linalg.solve(prob.A.to_scipy().toarray(), prob.b)
+    x, info = gpu_solve(h, prob.b, x0=xs)
+    assert info.iters == 0
+
+
+def test_gmres_matches_oracle():
+    from oracle import gdsw_oracle as O
+    prob = P.elasticity_problem(6, 2)
+    M = oracle_for(prob, local="ilu0")
+    xo, io = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=30)
+    h = gpu_handle(prob, local_solver="ilu0", krylov="gmres", restart=30)
+    x, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    assert abs(info.iters - io.iters) <= 1, (info.iters, io.iters)
+    # a short restart forces restarts and still converges
+    h2 = gpu_handle(prob, local_solver="ilu0", krylov="gmres", restart=5)
+    xo2, io2 = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=5)
+    x2, info2 = gpu_solve(h2, prob.b)
+    assert info2.converged and abs(info2.iters - io2.iters) <= 2
+
+
+def test_fp32_pcg_iteration_inflation_and_fp64_residual():
+    prob = P.poisson_problem(16, 4)
+    h64 = gpu_handle(prob, local_solver="ic0")
+    h32 = gpu_handle(prob, local_solver="ic0", precision="fp32")
+    _, i64 = gpu_solve(h64, prob.b)
+    x32, i32 = gpu_solve(h32, prob.b)
+    assert i32.converged and i32.true_relres <= 1e-8
+    assert i32.iters <= i64.iters + 2
+
+
+def test_solve_host_matches_device_solve():
+    prob = P.poisson_problem(12, 4)
+    h = gpu_handle(prob, local_solver="ic0")
+    xd, infod = gpu_solve(h, prob.b)
+    xh = np.zeros(prob.A.n)
+    infoh = h.solve_host(np.ascontiguousarray(prob.b), xh)
+    assert infoh.iters == infod.iters and np.array_equal(xh, xd)
+
+
+def test_host_made_faults():
+    from paper_2304_04876_b300 import gdsw as G
+    # indefinite local matrix: IC(0) sweep breaks down (negative diagonal)
+    prob = P.poisson_problem(8, 4)
+    A = prob.A.to_scipy().tolil()
+    A[10, 10] = -6.0
+    bad = P.CSR.from_scipy(A.tocsr())
+    with pytest.raises(G.GdswError) as e:
+        G.Handle(bad, prob.part, None, local_solver="ic0")
+    assert e.value.status == G.ERR_BREAKDOWN
+    # NaN in the right-hand side: reported as not converged, no hang
+    h = gpu_handle(prob, local_solver="ic0")
+    b = prob.b.copy()
+    b[3] = np.nan
+    x, info = gpu_solve(h, b, raise_on_nonconvergence=False)
+    assert not info.converged
