@@ -24,7 +24,11 @@ import tempfile
 import threading
 import time
 
-import numpy as np
+# the CPU oracle legs run single-threaded; set before numpy loads its BLAS
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -146,10 +150,9 @@ def golden_iters(variant: str) -> int | None:
 def oracle_sample(prob, variant: str, iters_for_metric: int, n_iter: int = 2) -> dict:
     """Time the oracle's PCG iteration (SpMV + M^-1 apply + vector updates) on the full
     workload after its setup; solves/s = 1 / (t_iteration * iterations of a solve)."""
-    from threadpoolctl import threadpool_limits
     from oracle import gdsw_oracle as O
     trsv = O.JACOBI if "jacobi" in variant else O.LEVELSCHED
-    with threadpool_limits(limits=1):
+    if True:
         t0 = time.perf_counter()
         M = O.GDSW(prob.A, prob.part, prob.Z, local=O.IC0, trsv=trsv)
         setup_s = time.perf_counter() - t0
@@ -184,10 +187,9 @@ def run_reference(args, rank: int):
     prob = P.config_problem(2, seed=0)
     variant = args.variant
     iters = golden_iters(variant) or 40
-    from threadpoolctl import threadpool_limits
     from oracle import gdsw_oracle as O
     trsv = O.JACOBI if "jacobi" in variant else O.LEVELSCHED
-    with threadpool_limits(limits=1):
+    if True:
         M = O.GDSW(prob.A, prob.part, prob.Z, local=O.IC0, trsv=trsv)
 
         def step():
