@@ -175,6 +175,26 @@ GDSW_API gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st);
 /* Frees every device allocation of the handle.  NULL is accepted. */
 GDSW_API gdsw_status gdsw_destroy(gdsw_handle h);
 
+/* y = A x and *dot = (x, y) without allocating device memory (the paper has no
+ * counterpart; this is a service for callers that cannot allocate).
+ * Callers that give all device memory to their own pool allocator, or that
+ * cannot afford the synchronisation an allocation implies in the middle of
+ * their stream work, can call this instead of creating a handle.
+ * All pointers are DEVICE memory owned by the caller: rowptr[n+1],
+ * colind[nnz], val[nnz] (CSR, as for gdsw_setup), x[n], y[n], dot[1]; nnz is
+ * the caller's count of stored entries and only selects the row width.
+ * The partial sums live in a fixed array of 65536 doubles (512 KB) inside the
+ * library, so n is limited to 65536 blocks of rows (about 2.1 million rows of
+ * 5-10 entries, 0.5 million rows of more than 24): larger n returns
+ * GDSW_ERR_UNSUPPORTED with the limit in gdsw_last_error().  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Every call on a device
+ * shares the array: calls whose kernels may overlap on the GPU race and must
+ * be ordered by the caller.  Work is enqueued on `stream`. */
+GDSW_API gdsw_status gdsw_spmv_dot_noalloc(int32_t n, int64_t nnz, const int32_t* rowptr,
+                                           const int32_t* colind, const double* val,
+                                           const double* x, double* y, double* dot, void* stream);
+
 GDSW_API const char* gdsw_status_string(gdsw_status s);
 GDSW_API const char* gdsw_last_error(void);
 

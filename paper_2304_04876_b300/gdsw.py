@@ -77,6 +77,8 @@ SIGNATURES = {
     "gdsw_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
     "gdsw_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "gdsw_destroy": (C.c_int, [C.c_void_p]),
+    "gdsw_spmv_dot_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_status_string": (C.c_char_p, [C.c_int]),
     "gdsw_last_error": (C.c_char_p, []),
 }
@@ -219,3 +221,15 @@ def _host_ptr(a) -> int:
         return a.data_ptr()
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data
+
+
+def spmv_dot_noalloc(rowptr, colind, val, x, y, dot, nnz: int, stream=None):
+    """y = A x and dot[0] = (x, y) through gdsw_spmv_dot_noalloc (no device allocation).
+
+    rowptr/colind (int32) and val, x, y, dot (float64) are CUDA tensors owned by the caller.
+    """
+    n = x.numel()
+    _check(load().gdsw_spmv_dot_noalloc(n, int(nnz), rowptr.data_ptr(), colind.data_ptr(), _ptr(val),
+                                        _ptr(x), _ptr(y), _ptr(dot), _stream(stream)),
+           "gdsw_spmv_dot_noalloc")
+    return y, dot
