@@ -14,6 +14,7 @@
 //              (the deterministic scatter-add of sum_s R_s^T z_s) and adds
 //              the prolongation (Phi y)_g, optionally fusing the PCG dots.
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.h"
@@ -107,6 +108,87 @@ __global__ void __launch_bounds__(256) k_local_tri(const double* __restrict__ r,
   for (int i = threadIdx.x; i < m; i += blockDim.x) zloc[base + i] = v[i];
 }
 
+// Level-scheduled triangular solves streamed through shared memory.  The L
+// levels and then the U levels of subdomain s are a sequence of records (one
+// per level, 16-byte aligned, see the setup); thread 0 keeps S records in
+// flight with TMA bulk copies into a ring of stages, each stage tracked by an
+// mbarrier, while all threads compute the current level from shared memory:
+//     v[row] = (v[row] - sum_k val_k v[col_k]) * dinv
+// Every wait is bounded; a wait that runs out sets err[0], waits (bounded)
+// for the copies still in flight, and ends the CTA without writing z_s.
+constexpr long long kWaitLimit = 2000000000LL;   // cycles, about 1 s
+
+template <class T, int S>
+__global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r,
+                                                    const int* __restrict__ om_ptr,
+                                                    const int* __restrict__ om_dofs,
+                                                    const int* __restrict__ rec_ptr,
+                                                    const uint32_t* __restrict__ rec_off16,
+                                                    const uint32_t* __restrict__ rec_bytes,
+                                                    const uint8_t* __restrict__ stream, int stage_bytes,
+                                                    T* __restrict__ zloc,
+                                                    const KrylovScalars* __restrict__ ks, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[S];
+  if (ks != nullptr && ks->done) return;
+  const int s = blockIdx.x;
+  const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+  const int r0 = rec_ptr[s], nrec = rec_ptr[s + 1] - r0;
+  unsigned char* stages = smem_raw;
+  T* v = reinterpret_cast<T*>(smem_raw + size_t(S) * stage_bytes);
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < S; ++j) mbar_init(&bar[j], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < S && j < nrec; ++j) {
+      const unsigned nb = rec_bytes[r0 + j];
+      mbar_expect_tx(&bar[j], nb);
+      bulk_g2s(stages + size_t(j) * stage_bytes, stream + size_t(rec_off16[r0 + j]) * 16, nb, &bar[j]);
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = T(r[om_dofs[base + i]]);
+  __syncthreads();
+  for (int i = 0; i < nrec; ++i) {
+    const int st = i % S;
+    const unsigned parity = (i / S) & 1;
+    const bool ok = mbar_wait_bounded(&bar[st], parity, kWaitLimit);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(err, 1);
+        // let the copies already issued land before the CTA's shared memory goes away
+        for (int j = i; j < nrec && j < i + S; ++j) mbar_wait_bounded(&bar[j % S], (j / S) & 1, kWaitLimit);
+      }
+      return;
+    }
+    const unsigned char* rec = stages + size_t(st) * stage_bytes;
+    const int4 hdr = *reinterpret_cast<const int4*>(rec);
+    const int nr = hdr.x, K = hdr.y;
+    const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 16);
+    const size_t o_d = 16 + ((size_t(2) * nr + 15) & ~size_t(15));
+    const T* dinv = reinterpret_cast<const T*>(rec + o_d);
+    const size_t o_v = o_d + ((size_t(nr) * sizeof(T) + 15) & ~size_t(15));
+    const T* vals = reinterpret_cast<const T*>(rec + o_v);
+    const size_t o_c = o_v + ((size_t(K) * nr * sizeof(T) + 15) & ~size_t(15));
+    const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + o_c);
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const int row = lrows[t];
+      T acc = v[row];
+      for (int k = 0; k < K; ++k) acc -= vals[k * nr + t] * v[cols[k * nr + t]];
+      v[row] = acc * dinv[t];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && i + S < nrec) {
+      fence_proxy_async_smem();
+      const unsigned nb = rec_bytes[r0 + i + S];
+      mbar_expect_tx(&bar[st], nb);
+      bulk_g2s(stages + size_t(st) * stage_bytes, stream + size_t(rec_off16[r0 + i + S]) * 16, nb, &bar[st]);
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) zloc[base + i] = v[i];
+}
+
 // Exact local solver: z_s = A_s^-1 r_s with the stored dense inverse
 // (symmetric, so row i is read contiguously).  Grid (row chunks of 32, nsub).
 template <class T>
@@ -139,36 +221,54 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
   }
 }
 
-// Partial products Phi_b^T r_b, 8 columns per pass.
+// Partial products Phi_b^T r_b over one chunk of at most 1024 rows of a
+// block (one CTA per chunk, up to four rows per thread, 8 columns per pass).
 template <class T>
 __global__ void __launch_bounds__(256) k_phiT(const double* __restrict__ r,
                                               const int* __restrict__ brow_ptr,
                                               const int* __restrict__ brow_dof,
                                               const int* __restrict__ bcol_ptr,
                                               const int64_t* __restrict__ phi_off,
-                                              const T* __restrict__ phi, double* __restrict__ partial,
+                                              const T* __restrict__ phi,
+                                              const int* __restrict__ chunk_blk,
+                                              const int* __restrict__ chunk_r0,
+                                              const int* __restrict__ chunk_r1,
+                                              const int* __restrict__ chunk_slot,
+                                              double* __restrict__ partial,
                                               const KrylovScalars* __restrict__ ks) {
   __shared__ T sh[32];
   if (ks != nullptr && ks->done) return;
-  const int b = blockIdx.x;
+  const int q = blockIdx.x;
+  const int b = chunk_blk[q];
   const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
+  const int i0 = chunk_r0[q], i1 = chunk_r1[q];
   const int k = bcol_ptr[b + 1] - bcol_ptr[b];
-  if (k == 0) return;
   const T* Ph = phi + phi_off[b];
+  // r of this thread's (up to) four rows, loaded once
+  T rv[4];
+  int ri[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = i0 + threadIdx.x + j * 256;
+    ri[j] = i;
+    rv[j] = i < i1 ? T(r[brow_dof[p0 + i]]) : T(0);
+  }
   for (int c0 = 0; c0 < k; c0 += 8) {
     const int kc = min(8, k - c0);
     T acc[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] = T(0);
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-      const T rv = T(r[brow_dof[p0 + i]]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (ri[j] >= i1) continue;
+      const T* col = Ph + int64_t(c0) * nr + ri[j];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (u < kc) acc[u] += Ph[int64_t(c0 + u) * nr + i] * rv;
+        if (u < kc) acc[u] += col[int64_t(u) * nr] * rv[j];
     }
     for (int u = 0; u < kc; ++u) {
       const T t = block_sum(acc[u], sh);
-      if (threadIdx.x == 0) partial[bcol_ptr[b] + c0 + u] = double(t);
+      if (threadIdx.x == 0) partial[chunk_slot[q] + c0 + u] = double(t);
     }
   }
 }
@@ -206,44 +306,74 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
 }
 
 // z_g = sum over subdomains containing g of (z_s)_g (ascending subdomain
-// order) + (Phi y)_g.  With `dots`, also (r, z_new) and (r, z_old), reduced by
-// the last CTA, which sets beta and (r, z) for the PCG update.
+// order) + (Phi y)_g, one unknown per thread over the block-row positions
+// (pos_blk gives the Phi block of each position).  With `dots`, also
+// (r, z_new) and (r, z_old), reduced by the last CTA, which sets beta and
+// (r, z) for the PCG update.
+template <class T>
+__device__ __forceinline__ double combine_one(int p, const int* __restrict__ pos_blk,
+                                              const int* __restrict__ brow_ptr,
+                                              const int* __restrict__ bcol_ptr,
+                                              const int* __restrict__ bcol,
+                                              const int64_t* __restrict__ phi_off,
+                                              const T* __restrict__ phi, const double* __restrict__ y,
+                                              const int* __restrict__ pull_ptr,
+                                              const int* __restrict__ pull_pos,
+                                              const T* __restrict__ zloc) {
+  double acc = 0.0;
+  const int q0 = pull_ptr[p], q1 = pull_ptr[p + 1];
+  for (int q = q0; q < q1; ++q) acc += double(zloc[pull_pos[q]]);
+  const int b = pos_blk[p];
+  const int c0 = bcol_ptr[b], k = bcol_ptr[b + 1] - c0;
+  if (k > 0) {
+    const int p0 = brow_ptr[b];
+    const int nr = brow_ptr[b + 1] - p0;
+    const T* Ph = phi + phi_off[b] + (p - p0);
+    T py = T(0);
+    for (int u = 0; u < k; ++u) py += Ph[int64_t(u) * nr] * T(y[bcol[c0 + u]]);
+    acc += double(py);
+  }
+  return acc;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_combine(
-    const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_ptr,
-    const int* __restrict__ brow_dof, const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
+    int n, const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_dof,
+    const int* __restrict__ pos_blk, const int* __restrict__ brow_ptr,
+    const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
     const int64_t* __restrict__ phi_off, const T* __restrict__ phi, const double* __restrict__ y,
     const int* __restrict__ pull_ptr, const int* __restrict__ pull_pos, const T* __restrict__ zloc,
     int dots, double* __restrict__ red, KrylovScalars* ks) {
-  __shared__ double ys[160];
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
-  const int b = blockIdx.x;
-  const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
-  const int c0 = bcol_ptr[b], k = bcol_ptr[b + 1] - c0;
-  for (int u = threadIdx.x; u < k; u += blockDim.x) ys[u] = y[bcol[c0 + u]];
-  __syncthreads();
-  const T* Ph = phi + (k > 0 ? phi_off[b] : 0);
   double d_new = 0.0, d_old = 0.0;
-  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-    const int p = p0 + i;
+  const int stride = gridDim.x * blockDim.x;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += 2 * stride) {
+    // two independent positions per trip keep more loads in flight
+    const int p2 = p + stride;
     const int g = brow_dof[p];
-    double acc = 0.0;
-    for (int q = pull_ptr[p]; q < pull_ptr[p + 1]; ++q) acc += double(zloc[pull_pos[q]]);
-    for (int u = 0; u < k; ++u) acc += double(Ph[int64_t(u) * nr + i]) * ys[u];
+    const int g2 = p2 < n ? brow_dof[p2] : 0;
+    const double a = combine_one(p, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc);
+    const double a2 = p2 < n ? combine_one(p2, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc) : 0.0;
     if (dots) {
       const double rg = r[g];
-      d_old += rg * z[g];
-      d_new += rg * acc;
+      d_old = fma(rg, z[g], d_old);
+      d_new = fma(rg, a, d_new);
+      if (p2 < n) {
+        const double rg2 = r[g2];
+        d_old = fma(rg2, z[g2], d_old);
+        d_new = fma(rg2, a2, d_new);
+      }
     }
-    z[g] = acc;
+    z[g] = a;
+    if (p2 < n) z[g2] = a2;
   }
   if (!dots) return;
   const double tn = block_sum(d_new, sh);
   const double to = block_sum(d_old, sh);
   if (threadIdx.x == 0) {
-    red[2 * b] = tn;
-    red[2 * b + 1] = to;
+    red[2 * blockIdx.x] = tn;
+    red[2 * blockIdx.x + 1] = to;
   }
   if (arrive_last(&ks->ticket[2])) {
     double sn = 0.0, so = 0.0;
@@ -284,6 +414,14 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
     dim3 grid((c->max_m + 31) / 32, c->nsub);
     k_local_dense<T><<<grid, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
                                             c->ainv_off, zl, ks);
+  } else if (c->rec_stages > 0) {
+    const size_t shm = size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * sizeof(T);
+    switch (c->rec_stages) {
+      case 2: k_local_pipe<T, 2><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
+      case 3: k_local_pipe<T, 3><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
+      case 4: k_local_pipe<T, 4><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
+      default: k_local_pipe<T, 6><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
+    }
   } else {
     const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
     const size_t shm = size_t(c->max_m) * sizeof(T) * (jac ? 3 : 1);
@@ -297,8 +435,10 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
 template <class T>
 gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
   if (c->n0 == 0) return GDSW_OK;
-  k_phiT<T><<<c->nblk, 256, 0, s>>>(r, c->brow_ptr, c->brow_dof, c->bcol_ptr, c->phi_off,
-                                    static_cast<const T*>(c->phi), c->partial, ks);
+  if (c->n_chunks == 0) return GDSW_OK;
+  k_phiT<T><<<c->n_chunks, 256, 0, s>>>(r, c->brow_ptr, c->brow_dof, c->bcol_ptr, c->phi_off,
+                                        static_cast<const T*>(c->phi), c->chunk_blk, c->chunk_r0,
+                                        c->chunk_r1, c->chunk_slot, c->partial, ks);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -314,10 +454,11 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
 
 template <class T>
 gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots) {
-  k_combine<T><<<c->nblk, 256, 0, s>>>(r, z, c->brow_ptr, c->brow_dof, c->bcol_ptr, c->bcol,
-                                       c->phi_off, static_cast<const T*>(c->phi), c->yvec,
-                                       c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),
-                                       dots ? 1 : 0, c->red, dots ? c->ks : nullptr);
+  const int grid = std::min(kNumSMs * 8, (c->n + 511) / 512);
+  k_combine<T><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
+                                    c->bcol, c->phi_off, static_cast<const T*>(c->phi), c->yvec,
+                                    c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),
+                                    dots ? 1 : 0, c->red, dots ? c->ks : nullptr);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -340,6 +481,10 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
 }  // namespace
 
 gdsw_status apply_configure(Ctx* c) {
+  if (c->derr == nullptr) {
+    GDSW_TRY(dalloc(c, &c->derr, 4));
+    GDSW_CK(cudaMemset(c->derr, 0, 4 * sizeof(int)));
+  }
   // kernels that may need more than 48 KB of dynamic shared memory
   const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
   const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
@@ -350,7 +495,32 @@ gdsw_status apply_configure(Ctx* c) {
   }
   const size_t shm_coarse = size_t(c->n0) * sizeof(double);
   if (shm_coarse > 227 * 1024) { set_error("coarse dimension too large"); return GDSW_ERR_UNSUPPORTED; }
-  if (c->max_bcols > 160) { set_error("a Phi block has more than 160 coarse columns"); return GDSW_ERR_UNSUPPORTED; }
+  // pipelined level-scheduled solve: deepest ring (6, 4, 3, 2 stages) that fits
+  // next to the subdomain vector; otherwise the plain kernel
+  c->rec_stages = 0;
+  const char* env = getenv("GDSW_LOCAL_PIPE");
+  const bool pipe_ok = (env == nullptr || env[0] != '0') && c->rec_stream != nullptr &&
+                       c->opt.local_solver != GDSW_LOCAL_EXACT && !jac;
+  if (pipe_ok) {
+    const int depth_env = getenv("GDSW_PIPE_STAGES") ? atoi(getenv("GDSW_PIPE_STAGES")) : 0;
+    const int cand[4] = {6, 4, 3, 2};
+    for (int q = 0; q < 4; ++q) {
+      if (depth_env > 0 && cand[q] != depth_env) continue;
+      const size_t shm = size_t(cand[q]) * c->rec_stage_bytes + size_t(c->max_m) * es;
+      if (shm <= 200 * 1024 && (depth_env > 0 || shm <= 112 * 1024 || cand[q] == 2)) {
+        c->rec_stages = cand[q];
+        break;
+      }
+    }
+  }
+  if (c->rec_stages > 0) {
+    const int shm = int(size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * es);
+#define GDSW_PIPE_ATTR(TT, SS)                                                                     \
+  GDSW_CK(cudaFuncSetAttribute(k_local_pipe<TT, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+    if (c->fp32) { GDSW_PIPE_ATTR(float, 2) GDSW_PIPE_ATTR(float, 3) GDSW_PIPE_ATTR(float, 4) GDSW_PIPE_ATTR(float, 6) }
+    else { GDSW_PIPE_ATTR(double, 2) GDSW_PIPE_ATTR(double, 3) GDSW_PIPE_ATTR(double, 4) GDSW_PIPE_ATTR(double, 6) }
+#undef GDSW_PIPE_ATTR
+  }
   if (c->fp32) {
     GDSW_CK(cudaFuncSetAttribute(k_local_tri<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
     GDSW_CK(cudaFuncSetAttribute(k_local_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
@@ -363,6 +533,20 @@ gdsw_status apply_configure(Ctx* c) {
   return GDSW_OK;
 }
 
+// Reads (and clears) the device error flags; a bounded wait that ran out is
+// reported as GDSW_ERR_TIMEOUT.
+gdsw_status check_device_errors(Ctx* c, cudaStream_t s) {
+  int h = 0;
+  GDSW_CK(cudaMemcpyAsync(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (h != 0) {
+    GDSW_CK(cudaMemsetAsync(c->derr, 0, sizeof(int), s));
+    set_error("a bounded device wait in the local solve ran out");
+    return GDSW_ERR_TIMEOUT;
+  }
+  return GDSW_OK;
+}
+
 gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bool rz_dots) {
   return c->fp32 ? apply_t<float>(c, r, z, s, rz_dots, nullptr)
                  : apply_t<double>(c, r, z, s, rz_dots, nullptr);
@@ -371,6 +555,7 @@ gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bo
 gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms) {
   GDSW_TRY(c->fp32 ? apply_t<float>(c, r, z, s, false, c->ev) : apply_t<double>(c, r, z, s, false, c->ev));
   GDSW_CK(cudaEventSynchronize(c->ev[4]));
+  GDSW_TRY(check_device_errors(c, s));
   for (int q = 0; q < 4; ++q) {
     float t = 0.f;
     GDSW_CK(cudaEventElapsedTime(&t, c->ev[q], c->ev[q + 1]));

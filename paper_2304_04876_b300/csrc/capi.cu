@@ -120,6 +120,7 @@ gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const doub
   if (st == GDSW_OK) st = c->fp32 ? dalloc(c, reinterpret_cast<float**>(&c->zloc), P.sum_m)
                                   : dalloc(c, reinterpret_cast<double**>(&c->zloc), P.sum_m);
   if (st == GDSW_OK) st = apply_configure(c);
+  if (st == GDSW_OK) st = spmv_configure(c, A->rowptr);
   const double t1 = now_s();
   if (st == GDSW_OK) st = krylov_init(c, s);
   if (st == GDSW_OK) {

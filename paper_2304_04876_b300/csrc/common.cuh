@@ -32,13 +32,14 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // Returns true in every thread of the CTA that is the last of the grid to
-// arrive at `ticket`; that CTA sees the partial results the others published
-// before arriving (they fence first).  The ticket is reset for the next use.
+// arrive at `ticket`.  Thread 0 must have published the CTA's partial result
+// before the call; it fences that write, so the last CTA sees every partial.
+// The ticket is reset for the next use.
 __device__ __forceinline__ bool arrive_last(unsigned int* ticket) {
   __shared__ bool last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
     last = (t == gridDim.x * gridDim.y - 1);
     if (last) *ticket = 0u;
@@ -53,6 +54,64 @@ __device__ __forceinline__ double sum_partials(const double* part, int count, do
   double v = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) v += __ldcg(part + i);
   return block_sum(v, sh);
+}
+
+}  // namespace gdsw
+
+namespace gdsw {
+
+// ---- TMA bulk copies and mbarriers (sm_90+ PTX) ---------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false when `cycles` SM clock cycles (about 1 s for 2e9)
+// passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long cycles) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > cycles) return false;
+  return true;
 }
 
 }  // namespace gdsw

@@ -101,6 +101,11 @@ struct CoarsePlan {
   std::vector<int> cs_ptr, cs_idx;        // per coarse column: partial slots
   std::vector<int> pull_ptr, pull_pos;    // scatter lists in block-row order
   std::vector<int> dof_blk, dof_blkrow;
+  std::vector<int> pos_blk;               // block of every block-row position
+  // Phi^T r work split: chunk q covers rows [chunk_r0, chunk_r1) of block
+  // chunk_blk; its partial products go to slots chunk_slot[q] .. + block columns
+  std::vector<int> chunk_blk, chunk_r0, chunk_r1, chunk_slot;
+  int n_slots = 0;
 };
 
 gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
@@ -137,6 +142,8 @@ struct KrylovScalars {
   unsigned int ticket[8];        // last-block reduction counters
 };
 
+constexpr int kNumSMsForCtx = 148;
+
 struct Ctx {
   int device = 0;
   gdsw_options opt;
@@ -162,6 +169,15 @@ struct Ctx {
   int* U_sub_lev = nullptr; int4* U_lev = nullptr; uint16_t* U_lrows = nullptr;
   uint16_t* U_col = nullptr; void* U_val = nullptr; void* U_dinv = nullptr;
   int max_levels = 0;
+  // the same factors as a stream of per-level records (pipelined solve)
+  uint8_t* rec_stream = nullptr;
+  int* rec_ptr = nullptr;            // nsub+1: record range of each subdomain
+  uint32_t* rec_off16 = nullptr;     // record offset in 16-byte units
+  uint32_t* rec_bytes = nullptr;
+  int rec_stage_bytes = 0;
+  int64_t rec_total_bytes = 0;
+  int rec_stages = 0;                // ring depth chosen at setup (0 = not used)
+  int* derr = nullptr;               // device error flags (bounded waits that ran out)
   // exact local solver: dense inverses
   void* ainv = nullptr;
   int64_t* ainv_off = nullptr;
@@ -173,6 +189,9 @@ struct Ctx {
   void* phi = nullptr;
   int* cs_ptr = nullptr; int* cs_idx = nullptr;
   int* pull_ptr = nullptr; int* pull_pos = nullptr;
+  int* pos_blk = nullptr;
+  int* chunk_blk = nullptr; int* chunk_r0 = nullptr; int* chunk_r1 = nullptr; int* chunk_slot = nullptr;
+  int n_chunks = 0;
   int max_bcols = 0;
   int n_slots = 0;
   double* partial = nullptr;     // per (block, column) slot
@@ -199,6 +218,7 @@ struct Ctx {
   // events for timed apply
   cudaEvent_t ev[8] = {};
   int red_grid = 0;
+  int spmv_R = 256, spmv_maxne = 1, spmv_tiles = 1, spmv_grid = kNumSMsForCtx;
 };
 
 template <class T>
@@ -235,9 +255,11 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
 // overwritten).  Kernels return at once when ks->done is set.
 gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bool rz_dots);
 gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms);
+gdsw_status check_device_errors(Ctx* c, cudaStream_t s);
 // krylov.cu
 gdsw_status krylov_init(Ctx* c, cudaStream_t s);
 gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s);
+gdsw_status spmv_configure(Ctx* c, const int* rowptr_host);
 gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
 gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
                         cudaStream_t s);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.h"
@@ -15,38 +16,59 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// y = A x, TPR threads per row; with `ks`, also (x, y) into ks->pq.
-template <int TPR>
-__global__ void __launch_bounds__(kThreads) k_spmv(int n, const int* __restrict__ rowptr,
+// y = A x by row tiles of R rows: the tile's values and the gathered x
+// entries are streamed once, coalesced, into shared memory (several
+// independent loads in flight per thread), then one thread per row forms its
+// sum with one FMA per entry in column order (the FP64 pipe of B300 is narrow,
+// so no separate multiply and add).  With `ks`, also (x, y) into ks->pq.
+template <int R>
+__global__ void __launch_bounds__(R) k_spmv_stream(int n, int ntiles, const int* __restrict__ rowptr,
                                                    const int* __restrict__ colind,
                                                    const double* __restrict__ val,
                                                    const double* __restrict__ x, double* __restrict__ y,
                                                    double* __restrict__ red, KrylovScalars* ks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int rp[R + 1];
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
-  const int sub = threadIdx.x % TPR;
-  const int rows_per_cta = kThreads / TPR;
+  double* va = reinterpret_cast<double*>(smem_raw);
   double dot = 0.0;
-  for (int row0 = blockIdx.x * rows_per_cta; row0 < n; row0 += gridDim.x * rows_per_cta) {
-    const int row = row0 + threadIdx.x / TPR;
-    double acc = 0.0;
-    if (row < n) {
-      const int e1 = rowptr[row + 1];
-      for (int e = rowptr[row] + sub; e < e1; e += TPR) acc += val[e] * x[colind[e]];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int r0 = tile * R;
+    const int nr = min(R, n - r0);
+    for (int i = threadIdx.x; i <= nr; i += R) rp[i] = rowptr[r0 + i];
+    __syncthreads();
+    const int e0 = rp[0];
+    const int ne = rp[nr] - e0;
+    double* xa = va + ne;   // gathered x right after the values
+    const double* v = val + e0;
+    const int* ci = colind + e0;
+    int j = threadIdx.x;
+    for (; j + 3 * R < ne; j += 4 * R) {
+      const int c0 = ci[j], c1 = ci[j + R], c2 = ci[j + 2 * R], c3 = ci[j + 3 * R];
+      const double a0 = v[j], a1 = v[j + R], a2 = v[j + 2 * R], a3 = v[j + 3 * R];
+      const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+      va[j] = a0; va[j + R] = a1; va[j + 2 * R] = a2; va[j + 3 * R] = a3;
+      xa[j] = x0; xa[j + R] = x1; xa[j + 2 * R] = x2; xa[j + 3 * R] = x3;
     }
-#pragma unroll
-    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, TPR);
-    if (sub == 0 && row < n) {
+    for (; j < ne; j += R) { va[j] = v[j]; xa[j] = x[ci[j]]; }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      const int a = rp[threadIdx.x] - e0, b = rp[threadIdx.x + 1] - e0;
+      double acc = 0.0;
+      for (int q = a; q < b; ++q) acc = fma(va[q], xa[q], acc);
+      const int row = r0 + threadIdx.x;
       y[row] = acc;
-      dot += x[row] * acc;
+      dot = fma(x[row], acc, dot);
     }
+    __syncthreads();
   }
   if (ks == nullptr) return;
   const double t = block_sum(dot, sh);
   if (threadIdx.x == 0) red[blockIdx.x] = t;
   if (arrive_last(&ks->ticket[0])) {
-    const double s = sum_partials(red, gridDim.x, sh);
-    if (threadIdx.x == 0) ks->pq = s;
+    const double s2 = sum_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) ks->pq = s2;
   }
 }
 
@@ -67,7 +89,23 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
   }
   const double alpha = ks->rz / ks->pq;
   double rr = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int n2 = n >> 1;
+  const int stride = gridDim.x * blockDim.x;
+  double2* x2 = reinterpret_cast<double2*>(x);
+  double2* r2 = reinterpret_cast<double2*>(r);
+  const double2* p2 = reinterpret_cast<const double2*>(p);
+  const double2* q2 = reinterpret_cast<const double2*>(q);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double2 pi = p2[i], qi = q2[i];
+    double2 xi = x2[i], ri = r2[i];
+    xi.x += alpha * pi.x; xi.y += alpha * pi.y;
+    ri.x -= alpha * qi.x; ri.y -= alpha * qi.y;
+    x2[i] = xi;
+    r2[i] = ri;
+    rr += ri.x * ri.x + ri.y * ri.y;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int i = n - 1;
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
@@ -97,8 +135,17 @@ __global__ void k_pupdate(int n, const double* __restrict__ z, double* __restric
                           const KrylovScalars* __restrict__ ks) {
   if (ks->done) return;
   const double beta = ks->beta;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  const int n2 = n >> 1;
+  const double2* z2 = reinterpret_cast<const double2*>(z);
+  double2* p2 = reinterpret_cast<double2*>(p);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+    const double2 zi = z2[i];
+    double2 pi = p2[i];
+    pi.x = zi.x + beta * pi.x;
+    pi.y = zi.y + beta * pi.y;
+    p2[i] = pi;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = z[n - 1] + beta * p[n - 1];
 }
 
 // r = b - q, rr = ||r||^2 and bb = ||b||^2.
@@ -178,23 +225,14 @@ __global__ void k_update_x(int n, int k, const double* __restrict__ Zk, const do
   }
 }
 
-int spmv_tpr(const Ctx* c) {
-  const double avg = double(c->nnz) / std::max(1, c->n);
-  if (avg <= 4.5) return 4;
-  if (avg <= 10) return 8;
-  if (avg <= 24) return 16;
-  return 32;
-}
-
 gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, KrylovScalars* ks) {
-  const int tpr = spmv_tpr(c);
-  const int rows_per_cta = kThreads / tpr;
-  const int grid = std::min(c->red_grid, (c->n + rows_per_cta - 1) / rows_per_cta);
-  switch (tpr) {
-    case 4: k_spmv<4><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-    case 8: k_spmv<8><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-    case 16: k_spmv<16><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-    default: k_spmv<32><<<grid, kThreads, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+  const int grid = std::min(c->spmv_grid, c->spmv_tiles);
+  const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
+  switch (c->spmv_R) {
+    case 256: k_spmv_stream<256><<<grid, 256, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    case 128: k_spmv_stream<128><<<grid, 128, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    case 64: k_spmv_stream<64><<<grid, 64, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    default: k_spmv_stream<32><<<grid, 32, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
   }
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
@@ -231,14 +269,51 @@ gdsw_status set_done(Ctx* c, cudaStream_t s, int v) {
 
 }  // namespace
 
+// Tile height for the stream SpMV: the largest R in {256, 128, 64, 32} whose
+// worst tile keeps its products within 64 KB of shared memory; the grid is the
+// number of CTAs that fit on the SMs at once.
+gdsw_status spmv_configure(Ctx* c, const int* rowptr) {
+  const int n = c->n;
+  int R = 256, maxne = 0;
+  for (; R >= 32; R >>= 1) {
+    maxne = 0;
+    for (int r0 = 0; r0 < n; r0 += R) maxne = std::max(maxne, rowptr[std::min(n, r0 + R)] - rowptr[r0]);
+    if (size_t(maxne) * 2 * sizeof(double) <= 64 * 1024 || R == 32) break;
+  }
+  if (size_t(maxne) * 2 * sizeof(double) > 200 * 1024) {
+    set_error("rows too long for the SpMV tile (%d entries in 32 rows)", maxne);
+    return GDSW_ERR_UNSUPPORTED;
+  }
+  c->spmv_R = R;
+  c->spmv_maxne = std::max(1, maxne);
+  c->spmv_tiles = (n + R - 1) / R;
+  const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
+  int per_sm = 1;
+  switch (R) {
+#define GDSW_SPMV_CFG(RR)                                                                         \
+  case RR:                                                                                         \
+    GDSW_CK(cudaFuncSetAttribute(k_spmv_stream<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 int(std::max<size_t>(shm, 16))));                                 \
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_stream<RR>, RR, shm));  \
+    break;
+    GDSW_SPMV_CFG(256)
+    GDSW_SPMV_CFG(128)
+    GDSW_SPMV_CFG(64)
+    GDSW_SPMV_CFG(32)
+#undef GDSW_SPMV_CFG
+  }
+  c->spmv_grid = std::max(1, per_sm) * kNumSMs;
+  return GDSW_OK;
+}
+
 gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s) {
   return launch_spmv(c, x, y, s, nullptr);
 }
 
 gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   const int n = c->n;
-  c->red_grid = kNumSMs * 4;
-  c->red_len = std::max(2 * c->red_grid, 2 * c->nblk) + 64;
+  c->red_grid = kNumSMs * 8;
+  c->red_len = std::max(std::max(2 * c->red_grid, 2 * c->nblk), c->spmv_grid) + 64;
   if (c->opt.krylov == GDSW_KRYLOV_GMRES)
     c->red_len = std::max<int>(c->red_len, (c->opt.restart + 2) * c->red_grid + 64);
   GDSW_TRY(dalloc(c, &c->red, c->red_len));
@@ -262,7 +337,9 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   for (int q = 0; q < 8; ++q) GDSW_CK(cudaEventCreate(&c->ev[q]));
   GDSW_CK(cudaStreamSynchronize(s));
   // the PCG iteration as a graph: while (cond) { body }, cond cleared on device
-  if (c->opt.krylov == GDSW_KRYLOV_PCG) {
+  const char* env = getenv("GDSW_PCG_GRAPH");
+  const bool use_graph = env == nullptr || env[0] != '0';
+  if (c->opt.krylov == GDSW_KRYLOV_PCG && use_graph) {
     GDSW_CK(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     GDSW_CK(cudaGraphCreate(&c->pcg_graph, 0));
     cudaGraphConditionalHandle h;
@@ -322,7 +399,17 @@ gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
     GDSW_TRY(apply_enqueue(c, c->r, c->z, s, true));
     GDSW_CK(cudaMemcpyAsync(c->p, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     for (;;) {
-      GDSW_CK(cudaGraphLaunch(c->pcg_exec, s));
+      if (c->pcg_exec != nullptr) {
+        GDSW_CK(cudaGraphLaunch(c->pcg_exec, s));
+      } else {
+        // the same iteration body launched from the host (no CUDA graph), with
+        // the stop flag read back after every iteration
+        for (;;) {
+          GDSW_TRY(pcg_body(c, s, cudaGraphConditionalHandle{}, 0));
+          GDSW_TRY(read_scalars(c, s));
+          if (c->ks_host->done) break;
+        }
+      }
       // recompute the true residual where the recurrence says converged (or maxit)
       GDSW_TRY(launch_spmv(c, c->x, c->q, s, nullptr));
       k_residual<<<vec_grid(c), kThreads, 0, s>>>(n, c->b, c->q, c->r, c->red, c->ks);
@@ -341,6 +428,7 @@ gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
   }
   GDSW_CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GDSW_CK(cudaStreamSynchronize(s));
+  GDSW_TRY(check_device_errors(c, s));
   if (info) {
     info->iters = iters;
     info->converged = converged ? 1 : 0;
@@ -457,6 +545,7 @@ gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* inf
   }
   GDSW_CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GDSW_CK(cudaStreamSynchronize(s));
+  GDSW_TRY(check_device_errors(c, s));
   if (info) {
     info->iters = it;
     info->converged = converged ? 1 : 0;

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
@@ -170,6 +171,25 @@ __global__ void k_pack_dinv(int64_t nrows, const int* __restrict__ dsrc, const d
        q += int64_t(gridDim.x) * blockDim.x) {
     const int e = dsrc[q];
     dinv[q] = e >= 0 ? T(1.0 / G[e]) : T(1);
+  }
+}
+
+// Values of the per-level record stream (see build_records): slot q of the
+// level-sliced ELL goes to element valpos[q] of the stream, the inverse
+// diagonal of level-ordered row i to element dinvpos[i].
+template <class T>
+__global__ void k_fill_records(int64_t nslots, const int* __restrict__ src,
+                               const uint32_t* __restrict__ valpos, int64_t nrows,
+                               const int* __restrict__ dsrc, const uint32_t* __restrict__ dinvpos,
+                               const double* __restrict__ G, T* __restrict__ stream) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nslots; q += stride) {
+    const int e = src[q];
+    stream[valpos[q]] = e >= 0 ? T(G[e]) : T(0);
+  }
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nrows; q += stride) {
+    const int e = dsrc[q];
+    stream[dinvpos[q]] = e >= 0 ? T(1.0 / G[e]) : T(1);
   }
 }
 
@@ -777,6 +797,88 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       GDSW_CK(cudaGetLastError());
     }
     c->max_levels = std::max(P.L.max_levels, P.U.max_levels);
+    // Per-level records for the pipelined level-scheduled solve: for every
+    // subdomain its L levels then its U levels, each record 16-byte aligned:
+    //   int4 {rows, width, 0, 0} | rows x uint16 local row | rows x T inverse
+    //   diagonal | width*rows x T values | width*rows x uint16 columns,
+    // every section padded to 16 bytes so a record is one bulk copy.
+    {
+      const size_t vb = c->fp32 ? sizeof(float) : sizeof(double);
+      auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+      std::vector<int> rec_ptr(nsub + 1, 0);
+      std::vector<uint32_t> rec_off16, rec_bytes;
+      std::vector<uint32_t> valposL(P.L.slots), valposU(P.U.slots), dinvposL(P.sum_m), dinvposU(P.sum_m);
+      size_t total = 0;
+      for (int pass = 0; pass < 2; ++pass) {      // pass 0 sizes, pass 1 fills
+        std::vector<uint8_t> dummy;
+        total = 0;
+        for (int q = 0; q < nsub; ++q) {
+          for (int side = 0; side < 2; ++side) {
+            const EllPlan& E = side == 0 ? P.L : P.U;
+            for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
+              const size_t nr = E.lev_nr[l], K = E.lev_K[l];
+              const size_t o_l = total + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
+                           o_c = o_v + a16(K * nr * vb), end = o_c + a16(2 * K * nr);
+              if (pass == 1) {
+                rec_off16.push_back(static_cast<uint32_t>(total / 16));
+                rec_bytes.push_back(static_cast<uint32_t>(end - total));
+                uint32_t* dp = side == 0 ? dinvposL.data() : dinvposU.data();
+                uint32_t* vp = side == 0 ? valposL.data() : valposU.data();
+                for (size_t t = 0; t < nr; ++t) dp[E.lev_start[l] + t] = static_cast<uint32_t>((o_d + t * vb) / vb);
+                for (size_t t = 0; t < K * nr; ++t) vp[E.lev_off[l] + t] = static_cast<uint32_t>((o_v + t * vb) / vb);
+              }
+              total = end;
+            }
+          }
+          if (pass == 1) rec_ptr[q + 1] = static_cast<int>(rec_off16.size());
+        }
+        if (total / 16 >= (size_t(1) << 32) || total / vb >= (size_t(1) << 32)) {
+          set_error("factor stream too large"); return GDSW_ERR_UNSUPPORTED;
+        }
+      }
+      std::vector<uint8_t> host(total, 0);
+      size_t stage = 16;
+      for (int q = 0, rr = 0; q < nsub; ++q) {
+        for (int side = 0; side < 2; ++side) {
+          const EllPlan& E = side == 0 ? P.L : P.U;
+          for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l, ++rr) {
+            const size_t nr = E.lev_nr[l], K = E.lev_K[l];
+            const size_t base = size_t(rec_off16[rr]) * 16;
+            const int hdr[4] = {static_cast<int>(nr), static_cast<int>(K), 0, 0};
+            std::memcpy(&host[base], hdr, 16);
+            const size_t o_l = base + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
+                         o_c = o_v + a16(K * nr * vb);
+            std::memcpy(&host[o_l], &E.lrows[E.lev_start[l]], 2 * nr);
+            std::memcpy(&host[o_c], &E.col[E.lev_off[l]], 2 * K * nr);
+            stage = std::max<size_t>(stage, rec_bytes[rr]);
+          }
+        }
+      }
+      uint8_t* d_stream;
+      GDSW_TRY(upload(c, &d_stream, host, s));
+      c->rec_stream = d_stream;
+      GDSW_TRY(upload(c, &c->rec_ptr, rec_ptr, s));
+      GDSW_TRY(upload(c, &c->rec_off16, rec_off16, s));
+      GDSW_TRY(upload(c, &c->rec_bytes, rec_bytes, s));
+      c->rec_stage_bytes = static_cast<int>(stage);
+      c->rec_total_bytes = static_cast<int64_t>(total);
+      for (int side = 0; side < 2; ++side) {
+        const EllPlan& E = side == 0 ? P.L : P.U;
+        uint32_t *d_vp, *d_dp;
+        int *d_src, *d_dsrc;
+        GDSW_TRY(sc.put(&d_vp, side == 0 ? valposL : valposU, s));
+        GDSW_TRY(sc.put(&d_dp, side == 0 ? dinvposL : dinvposU, s));
+        GDSW_TRY(sc.put(&d_src, E.src, s));
+        GDSW_TRY(sc.put(&d_dsrc, E.dsrc, s));
+        if (c->fp32)
+          k_fill_records<float><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                      reinterpret_cast<float*>(d_stream));
+        else
+          k_fill_records<double><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                       reinterpret_cast<double*>(d_stream));
+        GDSW_CK(cudaGetLastError());
+      }
+    }
     GDSW_CK(cudaStreamSynchronize(s));   // scratch of this stage is released below
   }
   c->stats.setup_phase_seconds[1] = now_s() - t0;
@@ -818,7 +920,13 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   GDSW_TRY(upload(c, &c->cs_idx, C.cs_idx, s));
   GDSW_TRY(upload(c, &c->pull_ptr, C.pull_ptr, s));
   GDSW_TRY(upload(c, &c->pull_pos, C.pull_pos, s));
-  c->n_slots = C.bcol_ptr[C.nblk];
+  GDSW_TRY(upload(c, &c->pos_blk, C.pos_blk, s));
+  GDSW_TRY(upload(c, &c->chunk_blk, C.chunk_blk, s));
+  GDSW_TRY(upload(c, &c->chunk_r0, C.chunk_r0, s));
+  GDSW_TRY(upload(c, &c->chunk_r1, C.chunk_r1, s));
+  GDSW_TRY(upload(c, &c->chunk_slot, C.chunk_slot, s));
+  c->n_chunks = static_cast<int>(C.chunk_blk.size());
+  c->n_slots = C.n_slots;
   c->stats.nnz_phi = C.phi_len;
   c->max_bcols = 0;
   for (int b = 0; b < C.nblk; ++b) c->max_bcols = std::max(c->max_bcols, C.bcol_ptr[b + 1] - C.bcol_ptr[b]);

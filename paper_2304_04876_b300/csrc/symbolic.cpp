@@ -449,15 +449,35 @@ gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, 
       C->dof_blk[C->brow_dof[q]] = b;
       C->dof_blkrow[C->brow_dof[q]] = q - C->brow_ptr[b];
     }
-  // partial slots per coarse column, ascending block order
-  C->cs_ptr.assign(n0 + 1, 0);
-  for (int q = 0; q < C->bcol_ptr[nblk]; ++q) C->cs_ptr[C->bcol[q] + 1]++;
-  for (int l = 0; l < n0; ++l) C->cs_ptr[l + 1] += C->cs_ptr[l];
-  C->cs_idx.resize(C->bcol_ptr[nblk]);
-  {
-    std::vector<int> pos(C->cs_ptr.begin(), C->cs_ptr.end() - 1);
-    for (int q = 0; q < C->bcol_ptr[nblk]; ++q) C->cs_idx[pos[C->bcol[q]]++] = q;
+  // Phi^T r chunks of at most kChunkRows rows; partial slots per (chunk, column)
+  constexpr int kChunkRows = 1024;
+  C->chunk_blk.clear(); C->chunk_r0.clear(); C->chunk_r1.clear(); C->chunk_slot.clear();
+  int nslot = 0;
+  std::vector<std::vector<int>> col_slots(n0);
+  for (int b = 0; b < nblk; ++b) {
+    const int rows = C->brow_ptr[b + 1] - C->brow_ptr[b];
+    const int k = C->bcol_ptr[b + 1] - C->bcol_ptr[b];
+    if (k == 0) continue;
+    for (int r0 = 0; r0 < rows; r0 += kChunkRows) {
+      C->chunk_blk.push_back(b);
+      C->chunk_r0.push_back(r0);
+      C->chunk_r1.push_back(std::min(rows, r0 + kChunkRows));
+      C->chunk_slot.push_back(nslot);
+      for (int u = 0; u < k; ++u) col_slots[C->bcol[C->bcol_ptr[b] + u]].push_back(nslot + u);
+      nslot += k;
+    }
   }
+  C->n_slots = nslot;
+  // slots of every coarse column in ascending (block, chunk) order
+  C->cs_ptr.assign(n0 + 1, 0);
+  C->cs_idx.clear();
+  for (int l = 0; l < n0; ++l) {
+    C->cs_idx.insert(C->cs_idx.end(), col_slots[l].begin(), col_slots[l].end());
+    C->cs_ptr[l + 1] = static_cast<int>(C->cs_idx.size());
+  }
+  C->pos_blk.assign(n, 0);
+  for (int b = 0; b < nblk; ++b)
+    for (int q = C->brow_ptr[b]; q < C->brow_ptr[b + 1]; ++q) C->pos_blk[q] = b;
   // scatter lists in block-row order
   C->pull_ptr.assign(n + 1, 0);
   C->pull_pos.clear();
