@@ -118,7 +118,55 @@ __global__ void __launch_bounds__(256) k_local_tri(const double* __restrict__ r,
 // for the copies still in flight, and ends the CTA without writing z_s.
 constexpr long long kWaitLimit = 2000000000LL;   // cycles, about 1 s
 
-template <class T, int S>
+// Row update of one level: TPR threads per row split the row's entries and
+// add their partial sums with shuffles; short rows (TPR = 1) are unrolled.
+template <class T, int TPR>
+__device__ __forceinline__ void level_rows(const unsigned char* rec, T* v) {
+  const int4 hdr = *reinterpret_cast<const int4*>(rec);
+  const int nr = hdr.x, K = hdr.y;
+  const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 16);
+  const T* dinv = reinterpret_cast<const T*>(rec + 16 + ((2 * nr + 15) & ~15));
+  const T* vals = reinterpret_cast<const T*>(rec + hdr.z);
+  const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + hdr.w);
+  if (TPR == 1) {
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const int row = lrows[t];
+      T acc = v[row];
+      if (K <= 4) {
+        T a[4];
+        int cidx[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          cidx[k] = k < K ? cols[k * nr + t] : row;
+          a[k] = k < K ? vals[k * nr + t] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc = fma(-a[k], v[cidx[k]], acc);
+      } else {
+        for (int k = 0; k < K; ++k) acc = fma(-vals[k * nr + t], v[cols[k * nr + t]], acc);
+      }
+      v[row] = acc * dinv[t];
+    }
+  } else {
+    const int sub = threadIdx.x % TPR;
+    const int groups = blockDim.x / TPR;
+    // every thread runs the same number of rounds, so the shuffles stay convergent
+    for (int round = 0; round < nr; round += groups) {
+      const int t = round + threadIdx.x / TPR;
+      T part = T(0);
+      if (t < nr)
+        for (int k = sub; k < K; k += TPR) part = fma(vals[k * nr + t], v[cols[k * nr + t]], part);
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, TPR);
+      if (t < nr && sub == 0) {
+        const int row = lrows[t];
+        v[row] = (v[row] - part) * dinv[t];
+      }
+    }
+  }
+}
+
+template <class T, int S, int TPR>
 __global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r,
                                                     const int* __restrict__ om_ptr,
                                                     const int* __restrict__ om_dofs,
@@ -153,7 +201,10 @@ __global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r
   for (int i = 0; i < nrec; ++i) {
     const int st = i % S;
     const unsigned parity = (i / S) & 1;
+    // each thread waits for the record itself; the one barrier per level
+    // below also carries a timed-out wait to every thread
     const bool ok = mbar_wait_bounded(&bar[st], parity, kWaitLimit);
+    if (ok) level_rows<T, TPR>(stages + size_t(st) * stage_bytes, v);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(err, 1);
@@ -162,23 +213,6 @@ __global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r
       }
       return;
     }
-    const unsigned char* rec = stages + size_t(st) * stage_bytes;
-    const int4 hdr = *reinterpret_cast<const int4*>(rec);
-    const int nr = hdr.x, K = hdr.y;
-    const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 16);
-    const size_t o_d = 16 + ((size_t(2) * nr + 15) & ~size_t(15));
-    const T* dinv = reinterpret_cast<const T*>(rec + o_d);
-    const size_t o_v = o_d + ((size_t(nr) * sizeof(T) + 15) & ~size_t(15));
-    const T* vals = reinterpret_cast<const T*>(rec + o_v);
-    const size_t o_c = o_v + ((size_t(K) * nr * sizeof(T) + 15) & ~size_t(15));
-    const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + o_c);
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-      const int row = lrows[t];
-      T acc = v[row];
-      for (int k = 0; k < K; ++k) acc -= vals[k * nr + t] * v[cols[k * nr + t]];
-      v[row] = acc * dinv[t];
-    }
-    __syncthreads();
     if (threadIdx.x == 0 && i + S < nrec) {
       fence_proxy_async_smem();
       const unsigned nb = rec_bytes[r0 + i + S];
@@ -222,7 +256,7 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
 }
 
 // Partial products Phi_b^T r_b over one chunk of at most 1024 rows of a
-// block (one CTA per chunk, up to four rows per thread, 8 columns per pass).
+// block (one CTA per chunk, 8 columns per pass, four rows per trip).
 template <class T>
 __global__ void __launch_bounds__(256) k_phiT(const double* __restrict__ r,
                                               const int* __restrict__ brow_ptr,
@@ -236,7 +270,7 @@ __global__ void __launch_bounds__(256) k_phiT(const double* __restrict__ r,
                                               const int* __restrict__ chunk_slot,
                                               double* __restrict__ partial,
                                               const KrylovScalars* __restrict__ ks) {
-  __shared__ T sh[32];
+  __shared__ T red8[8][256];
   if (ks != nullptr && ks->done) return;
   const int q = blockIdx.x;
   const int b = chunk_blk[q];
@@ -244,32 +278,45 @@ __global__ void __launch_bounds__(256) k_phiT(const double* __restrict__ r,
   const int i0 = chunk_r0[q], i1 = chunk_r1[q];
   const int k = bcol_ptr[b + 1] - bcol_ptr[b];
   const T* Ph = phi + phi_off[b];
-  // r of this thread's (up to) four rows, loaded once
-  T rv[4];
-  int ri[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int i = i0 + threadIdx.x + j * 256;
-    ri[j] = i;
-    rv[j] = i < i1 ? T(r[brow_dof[p0 + i]]) : T(0);
-  }
   for (int c0 = 0; c0 < k; c0 += 8) {
     const int kc = min(8, k - c0);
     T acc[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] = T(0);
+    for (int ib = i0 + threadIdx.x; ib < i1; ib += 4 * 256) {
+      // four rows per trip, all loads issued before the FMAs
+      T rv[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (ri[j] >= i1) continue;
-      const T* col = Ph + int64_t(c0) * nr + ri[j];
+      for (int j = 0; j < 4; ++j) {
+        const int i = ib + j * 256;
+        rv[j] = i < i1 ? T(r[brow_dof[p0 + i]]) : T(0);
+      }
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (u < kc) acc[u] += col[int64_t(u) * nr] * rv[j];
+      for (int j = 0; j < 4; ++j) {
+        const int i = ib + j * 256;
+        if (i >= i1) continue;
+        const T* col = Ph + int64_t(c0) * nr + i;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < kc) acc[u] = fma(col[int64_t(u) * nr], rv[j], acc[u]);
+      }
     }
-    for (int u = 0; u < kc; ++u) {
-      const T t = block_sum(acc[u], sh);
-      if (threadIdx.x == 0) partial[chunk_slot[q] + c0 + u] = double(t);
+    // reduce the kc accumulators: transpose through shared memory, then warp u
+    // sums column u (8 values per lane and one shuffle tree), which costs far
+    // fewer FP64 adds than a shuffle tree per column in every warp
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < kc) red8[u][threadIdx.x] = acc[u];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < kc) {
+      T t = T(0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t += red8[w][lane * 8 + j];
+      t = warp_sum(t);
+      if (lane == 0) partial[chunk_slot[q] + c0 + w] = double(t);
     }
+    __syncthreads();
   }
 }
 
@@ -298,8 +345,18 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
   const int warps = gridDim.x * (blockDim.x >> 5);
   for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n0; row += warps) {
     const double* Ar = Ainv + int64_t(row) * n0;
-    double acc = 0.0;
-    for (int j = lane; j < n0; j += 32) acc += Ar[j] * cs[j];
+    // four independent FMA chains per lane (FP64 latency), loads issued first
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = lane;
+    for (; j + 96 < n0; j += 128) {
+      const double m0 = Ar[j], m1 = Ar[j + 32], m2 = Ar[j + 64], m3 = Ar[j + 96];
+      a0 = fma(m0, cs[j], a0);
+      a1 = fma(m1, cs[j + 32], a1);
+      a2 = fma(m2, cs[j + 64], a2);
+      a3 = fma(m3, cs[j + 96], a3);
+    }
+    for (; j < n0; j += 32) a0 = fma(Ar[j], cs[j], a0);
+    double acc = (a0 + a1) + (a2 + a3);
     acc = warp_sum(acc);
     if (lane == 0) y[row] = acc;
   }
@@ -320,20 +377,19 @@ __device__ __forceinline__ double combine_one(int p, const int* __restrict__ pos
                                               const int* __restrict__ pull_ptr,
                                               const int* __restrict__ pull_pos,
                                               const T* __restrict__ zloc) {
-  double acc = 0.0;
+  // summed in the preconditioner's precision T, converted once
+  T acc = T(0);
   const int q0 = pull_ptr[p], q1 = pull_ptr[p + 1];
-  for (int q = q0; q < q1; ++q) acc += double(zloc[pull_pos[q]]);
+  for (int q = q0; q < q1; ++q) acc += zloc[pull_pos[q]];
   const int b = pos_blk[p];
   const int c0 = bcol_ptr[b], k = bcol_ptr[b + 1] - c0;
   if (k > 0) {
     const int p0 = brow_ptr[b];
     const int nr = brow_ptr[b + 1] - p0;
     const T* Ph = phi + phi_off[b] + (p - p0);
-    T py = T(0);
-    for (int u = 0; u < k; ++u) py += Ph[int64_t(u) * nr] * T(y[bcol[c0 + u]]);
-    acc += double(py);
+    for (int u = 0; u < k; ++u) acc = fma(Ph[int64_t(u) * nr], T(y[bcol[c0 + u]]), acc);
   }
-  return acc;
+  return double(acc);
 }
 
 template <class T>
@@ -357,11 +413,11 @@ __global__ void __launch_bounds__(256) k_combine(
     const double a2 = p2 < n ? combine_one(p2, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc) : 0.0;
     if (dots) {
       const double rg = r[g];
-      d_old = fma(rg, z[g], d_old);
+      if (dots > 1) d_old = fma(rg, z[g], d_old);
       d_new = fma(rg, a, d_new);
       if (p2 < n) {
         const double rg2 = r[g2];
-        d_old = fma(rg2, z[g2], d_old);
+        if (dots > 1) d_old = fma(rg2, z[g2], d_old);
         d_new = fma(rg2, a2, d_new);
       }
     }
@@ -384,7 +440,7 @@ __global__ void __launch_bounds__(256) k_combine(
     sn = block_sum(sn, sh);
     so = block_sum(so, sh);
     if (threadIdx.x == 0) {
-      const double num = ks->flexible ? (sn - so) : sn;
+      const double num = dots > 1 ? (sn - so) : sn;
       ks->beta = num / ks->rz;
       ks->rz_oldz = so;
       ks->rz_new = sn;
@@ -416,12 +472,22 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
                                             c->ainv_off, zl, ks);
   } else if (c->rec_stages > 0) {
     const size_t shm = size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * sizeof(T);
-    switch (c->rec_stages) {
-      case 2: k_local_pipe<T, 2><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
-      case 3: k_local_pipe<T, 3><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
-      case 4: k_local_pipe<T, 4><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
-      default: k_local_pipe<T, 6><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, ks, c->derr); break;
+#define GDSW_PIPE_LAUNCH(SS, TP)                                                                     \
+  k_local_pipe<T, SS, TP><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, \
+                                                    c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, \
+                                                    ks, c->derr)
+    const int key = c->rec_stages * 100 + c->rec_tpr;
+    switch (key) {
+      case 201: GDSW_PIPE_LAUNCH(2, 1); break;
+      case 301: GDSW_PIPE_LAUNCH(3, 1); break;
+      case 401: GDSW_PIPE_LAUNCH(4, 1); break;
+      case 601: GDSW_PIPE_LAUNCH(6, 1); break;
+      case 208: GDSW_PIPE_LAUNCH(2, 8); break;
+      case 308: GDSW_PIPE_LAUNCH(3, 8); break;
+      case 408: GDSW_PIPE_LAUNCH(4, 8); break;
+      default: GDSW_PIPE_LAUNCH(6, 8); break;
     }
+#undef GDSW_PIPE_LAUNCH
   } else {
     const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
     const size_t shm = size_t(c->max_m) * sizeof(T) * (jac ? 3 : 1);
@@ -458,7 +524,7 @@ gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, b
   k_combine<T><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
                                     c->bcol, c->phi_off, static_cast<const T*>(c->phi), c->yvec,
                                     c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),
-                                    dots ? 1 : 0, c->red, dots ? c->ks : nullptr);
+                                    dots ? (c->flexible ? 2 : 1) : 0, c->red, dots ? c->ks : nullptr);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -466,6 +532,20 @@ gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, b
 template <class T>
 gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, cudaEvent_t* ev) {
   const KrylovScalars* ks = dots ? c->ks : nullptr;
+  if (ev == nullptr && c->n0 > 0 && c->aux_stream != nullptr) {
+    // The one-level and coarse branches of Eq. 1 are independent until the
+    // final sum: the coarse branch (Phi^T r, c, A0^-1 c) runs on a second
+    // stream beside the local solves and joins before the scatter-add.
+    GDSW_CK(cudaEventRecord(c->ev_fork, s));
+    GDSW_CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
+    GDSW_TRY(launch_phiT<T>(c, r, c->aux_stream, ks));
+    GDSW_TRY(launch_coarse(c, c->aux_stream, ks));
+    GDSW_CK(cudaEventRecord(c->ev_join, c->aux_stream));
+    GDSW_TRY(launch_local<T>(c, r, s, ks));
+    GDSW_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+    GDSW_TRY(launch_combine<T>(c, r, z, s, dots));
+    return GDSW_OK;
+  }
   if (ev) GDSW_CK(cudaEventRecord(ev[0], s));
   GDSW_TRY(launch_local<T>(c, r, s, ks));
   if (ev) GDSW_CK(cudaEventRecord(ev[1], s));
@@ -481,6 +561,12 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
 }  // namespace
 
 gdsw_status apply_configure(Ctx* c) {
+  const char* two = getenv("GDSW_APPLY_STREAMS");
+  if (c->aux_stream == nullptr && (two == nullptr || two[0] != '1')) {
+    GDSW_CK(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    GDSW_CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    GDSW_CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
   if (c->derr == nullptr) {
     GDSW_TRY(dalloc(c, &c->derr, 4));
     GDSW_CK(cudaMemset(c->derr, 0, 4 * sizeof(int)));
@@ -513,12 +599,16 @@ gdsw_status apply_configure(Ctx* c) {
       }
     }
   }
+  c->rec_tpr = c->rec_max_width > 8 ? 8 : 1;
   if (c->rec_stages > 0) {
     const int shm = int(size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * es);
-#define GDSW_PIPE_ATTR(TT, SS)                                                                     \
-  GDSW_CK(cudaFuncSetAttribute(k_local_pipe<TT, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-    if (c->fp32) { GDSW_PIPE_ATTR(float, 2) GDSW_PIPE_ATTR(float, 3) GDSW_PIPE_ATTR(float, 4) GDSW_PIPE_ATTR(float, 6) }
-    else { GDSW_PIPE_ATTR(double, 2) GDSW_PIPE_ATTR(double, 3) GDSW_PIPE_ATTR(double, 4) GDSW_PIPE_ATTR(double, 6) }
+#define GDSW_PIPE_ATTR(TT, SS, TP)                                                                     \
+  GDSW_CK(cudaFuncSetAttribute(k_local_pipe<TT, SS, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+#define GDSW_PIPE_ATTRS(TT) \
+  GDSW_PIPE_ATTR(TT, 2, 1) GDSW_PIPE_ATTR(TT, 3, 1) GDSW_PIPE_ATTR(TT, 4, 1) GDSW_PIPE_ATTR(TT, 6, 1) \
+  GDSW_PIPE_ATTR(TT, 2, 8) GDSW_PIPE_ATTR(TT, 3, 8) GDSW_PIPE_ATTR(TT, 4, 8) GDSW_PIPE_ATTR(TT, 6, 8)
+    if (c->fp32) { GDSW_PIPE_ATTRS(float) } else { GDSW_PIPE_ATTRS(double) }
+#undef GDSW_PIPE_ATTRS
 #undef GDSW_PIPE_ATTR
   }
   if (c->fp32) {

@@ -25,6 +25,9 @@ void release(Ctx* c) {
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
   if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->ks_host) cudaFreeHost(c->ks_host);
@@ -115,6 +118,7 @@ gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const doub
   c->max_m = P.max_m;
   c->sum_m = P.sum_m;
   c->fp32 = o.precision == GDSW_PREC_FP32;
+  c->flexible = o.flexible < 0 ? c->fp32 : (o.flexible != 0);
   c->stats.setup_phase_seconds[0] = t_sym;
   st = numeric_setup(c, P, A, Z, nn, s);
   if (st == GDSW_OK) st = c->fp32 ? dalloc(c, reinterpret_cast<float**>(&c->zloc), P.sum_m)

@@ -152,6 +152,7 @@ struct Ctx {
   int max_m = 0;
   int64_t sum_m = 0;
   bool fp32 = false;
+  bool flexible = false;            // PCG uses the flexible beta (needs (r, z_old))
   std::vector<void*> allocs;
   size_t bytes = 0;
   gdsw_stats stats{};
@@ -177,6 +178,8 @@ struct Ctx {
   int rec_stage_bytes = 0;
   int64_t rec_total_bytes = 0;
   int rec_stages = 0;                // ring depth chosen at setup (0 = not used)
+  int rec_max_width = 0;             // widest level (off-diagonal entries per row)
+  int rec_tpr = 1;                   // threads per row in the pipelined solve
   int* derr = nullptr;               // device error flags (bounded waits that ran out)
   // exact local solver: dense inverses
   void* ainv = nullptr;
@@ -213,6 +216,8 @@ struct Ctx {
   cudaGraph_t pcg_graph = nullptr;
   cudaGraphExec_t pcg_exec = nullptr;
   cudaStream_t graph_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;     // coarse branch of the apply
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // host staging for gdsw_solve_host
   double* hpin = nullptr;
   // events for timed apply

@@ -102,14 +102,15 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
     ri.x -= alpha * qi.x; ri.y -= alpha * qi.y;
     x2[i] = xi;
     r2[i] = ri;
-    rr += ri.x * ri.x + ri.y * ri.y;
+    rr = fma(ri.x, ri.x, rr);
+    rr = fma(ri.y, ri.y, rr);
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int i = n - 1;
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
-    rr += ri * ri;
+    rr = fma(ri, ri, rr);
   }
   const double t = block_sum(rr, sh);
   if (threadIdx.x == 0) red[blockIdx.x] = t;
@@ -371,7 +372,7 @@ gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
   GDSW_CK(cudaMemcpyAsync(c->x, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   KrylovScalars init = {};
   init.maxit = c->opt.maxit;
-  init.flexible = c->opt.flexible < 0 ? (c->fp32 ? 1 : 0) : c->opt.flexible;
+  init.flexible = c->flexible ? 1 : 0;
   init.rz = 1.0;
   GDSW_CK(cudaMemcpyAsync(c->ks, &init, sizeof(KrylovScalars), cudaMemcpyHostToDevice, s));
   // r = b - A x0

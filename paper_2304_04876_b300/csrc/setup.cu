@@ -49,89 +49,73 @@ __global__ void k_extract_local(const double* __restrict__ val, const int* __res
   }
 }
 
-// Synchronous IC(0) sweeps (Sec. V-B3) on the lower pattern, one CTA per
-// subdomain, double-buffered: every entry of sweep k+1 reads sweep-k values.
+// One synchronous IC(0) sweep (Sec. V-B3) over every lower entry of every
+// subdomain (one thread per entry; one launch per sweep, so every entry of
+// sweep k+1 reads sweep-k values):
 //   s_ij = a~_ij - sum_{k<j} l_ik l_jk;  l_ij = s_ij / l_jj (i>j),  l_jj = sqrt(s_jj).
-__global__ void k_ic0_sweeps(const int* __restrict__ om_ptr, const int* __restrict__ lm_sub_ent,
-                             const int* __restrict__ lm_rowptr, const int* __restrict__ lm_col,
-                             const uint16_t* __restrict__ lm_row, const int* __restrict__ lm_diag,
-                             const double* __restrict__ at, double* F0, double* F1, int sweeps,
-                             int* err) {
-  const int s = blockIdx.x;
-  const int base = om_ptr[s];
-  const int e0 = lm_sub_ent[s], e1 = lm_sub_ent[s + 1];
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) F0[e] = at[e];
-  __syncthreads();
-  double* Fo = F0;
-  double* Fn = F1;
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int i = lm_row[e], j = lm_col[e];
-      if (j > i) { Fn[e] = Fo[e]; continue; }
-      // merge row i and row j over columns k < j
-      int a = lm_rowptr[base + i], ae = lm_rowptr[base + i + 1];
-      int b = lm_rowptr[base + j], be = lm_diag[base + j];
-      double acc = 0.0;
-      while (a < ae && b < be) {
-        const int ca = lm_col[a], cb = lm_col[b];
-        if (ca >= j) break;
-        if (ca == cb) { acc = fma(Fo[a], Fo[b], acc); ++a; ++b; }
-        else if (ca < cb) ++a;
-        else ++b;
-      }
-      const double sv = at[e] - acc;
-      if (i == j) {
-        if (!(sv > 0.0)) { atomicOr(err, ERR_BREAKDOWN); Fn[e] = 1.0; }
-        else Fn[e] = sqrt(sv);
-      } else {
-        Fn[e] = sv / Fo[lm_diag[base + j]];
-      }
+// The sum merges row i and row j of the local pattern over columns k < j.
+__global__ void k_ic0_sweep(int nent, const int* __restrict__ ebase, const int* __restrict__ lm_rowptr,
+                            const int* __restrict__ lm_col, const uint16_t* __restrict__ lm_row,
+                            const int* __restrict__ lm_diag, const double* __restrict__ at,
+                            const double* __restrict__ Fo, double* __restrict__ Fn, int* err) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
+    const int base = ebase[e];
+    const int i = lm_row[e], j = lm_col[e];
+    if (j > i) { Fn[e] = Fo[e]; continue; }
+    int a = lm_rowptr[base + i];
+    const int ae = lm_rowptr[base + i + 1];
+    int b = lm_rowptr[base + j];
+    const int be = lm_diag[base + j];
+    double acc = 0.0;
+    while (a < ae && b < be) {
+      const int ca = lm_col[a], cb = lm_col[b];
+      if (ca >= j) break;
+      if (ca == cb) { acc = fma(Fo[a], Fo[b], acc); ++a; ++b; }
+      else if (ca < cb) ++a;
+      else ++b;
     }
-    __syncthreads();
-    double* t = Fo; Fo = Fn; Fn = t;
+    const double sv = at[e] - acc;
+    if (i == j) {
+      if (!(sv > 0.0)) { atomicOr(err, ERR_BREAKDOWN); Fn[e] = 1.0; }
+      else Fn[e] = sqrt(sv);
+    } else {
+      Fn[e] = sv / Fo[lm_diag[base + j]];
+    }
   }
 }
 
-// Synchronous ILU(0) sweeps on the full pattern (L unit lower, U upper):
+// One synchronous ILU(0) sweep over the full pattern (L unit lower, U upper):
 //   l_ij = (a~_ij - sum_{k<j} l_ik u_kj) / u_jj  (i>j),   u_ij = a~_ij - sum_{k<i} l_ik u_kj.
 // u_kj is read from the entry (k, j) reached through the transposed position of (j, k).
-__global__ void k_ilu0_sweeps(const int* __restrict__ om_ptr, const int* __restrict__ lm_sub_ent,
-                              const int* __restrict__ lm_rowptr, const int* __restrict__ lm_col,
-                              const uint16_t* __restrict__ lm_row, const int* __restrict__ lm_diag,
-                              const int* __restrict__ lm_tpos, const double* __restrict__ at,
-                              double* F0, double* F1, int sweeps, int* err) {
-  const int s = blockIdx.x;
-  const int base = om_ptr[s];
-  const int e0 = lm_sub_ent[s], e1 = lm_sub_ent[s + 1];
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) F0[e] = at[e];
-  __syncthreads();
-  double* Fo = F0;
-  double* Fn = F1;
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int i = lm_row[e], j = lm_col[e];
-      const int kmax = min(i, j);
-      int a = lm_rowptr[base + i], ae = lm_rowptr[base + i + 1];
-      int b = lm_rowptr[base + j], be = lm_rowptr[base + j + 1];
-      double acc = 0.0;
-      while (a < ae && b < be) {
-        const int ca = lm_col[a], cb = lm_col[b];
-        if (ca >= kmax || cb >= kmax) break;
-        if (ca == cb) { acc = fma(Fo[a], Fo[lm_tpos[b]], acc); ++a; ++b; }
-        else if (ca < cb) ++a;
-        else ++b;
-      }
-      const double sv = at[e] - acc;
-      if (i > j) {
-        const double u = Fo[lm_diag[base + j]];
-        if (u == 0.0) { atomicOr(err, ERR_BREAKDOWN); Fn[e] = 0.0; }
-        else Fn[e] = sv / u;
-      } else {
-        Fn[e] = sv;
-      }
+__global__ void k_ilu0_sweep(int nent, const int* __restrict__ ebase, const int* __restrict__ lm_rowptr,
+                             const int* __restrict__ lm_col, const uint16_t* __restrict__ lm_row,
+                             const int* __restrict__ lm_diag, const int* __restrict__ lm_tpos,
+                             const double* __restrict__ at, const double* __restrict__ Fo,
+                             double* __restrict__ Fn, int* err) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
+    const int base = ebase[e];
+    const int i = lm_row[e], j = lm_col[e];
+    const int kmax = min(i, j);
+    int a = lm_rowptr[base + i];
+    const int ae = lm_rowptr[base + i + 1];
+    int b = lm_rowptr[base + j];
+    const int be = lm_rowptr[base + j + 1];
+    double acc = 0.0;
+    while (a < ae && b < be) {
+      const int ca = lm_col[a], cb = lm_col[b];
+      if (ca >= kmax || cb >= kmax) break;
+      if (ca == cb) { acc = fma(Fo[a], Fo[lm_tpos[b]], acc); ++a; ++b; }
+      else if (ca < cb) ++a;
+      else ++b;
     }
-    __syncthreads();
-    double* t = Fo; Fo = Fn; Fn = t;
+    const double sv = at[e] - acc;
+    if (i > j) {
+      const double u = Fo[lm_diag[base + j]];
+      if (u == 0.0) { atomicOr(err, ERR_BREAKDOWN); Fn[e] = 0.0; }
+      else Fn[e] = sv / u;
+    } else {
+      Fn[e] = sv;
+    }
   }
 }
 
@@ -744,22 +728,29 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     GDSW_TRY(sc.get(&F0, nent));
     GDSW_TRY(sc.get(&F1, nent));
     GDSW_TRY(sc.get(&G, nent));
-    const int sw = std::max(0, o.sweeps_factor);
-    if (ilu)
-      k_ilu0_sweeps<<<nsub, 256, 0, s>>>(c->om_ptr, d_lm_sub_ent, d_lm_rowptr, d_lm_col, d_lm_row,
-                                         d_lm_diag, d_lm_tpos, d_at, F0, F1, sw, d_err);
-    else
-      k_ic0_sweeps<<<nsub, 256, 0, s>>>(c->om_ptr, d_lm_sub_ent, d_lm_rowptr, d_lm_col, d_lm_row,
-                                        d_lm_diag, d_at, F0, F1, sw, d_err);
-    GDSW_CK(cudaGetLastError());
-    GDSW_TRY(read_err(d_err, s, ilu ? "ILU(0) sweeps" : "IC(0) sweeps"));
-    double* F = (sw % 2 == 0) ? F0 : F1;
     // subdomain row base of every entry
     std::vector<int> ebase(nent);
     for (int q = 0; q < nsub; ++q)
       for (int e = P.lm_sub_ent[q]; e < P.lm_sub_ent[q + 1]; ++e) ebase[e] = P.om_ptr[q];
     int* d_ebase;
     GDSW_TRY(sc.put(&d_ebase, ebase, s));
+    const int sw = std::max(0, o.sweeps_factor);
+    GDSW_CK(cudaMemcpyAsync(F0, d_at, nent * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double* Fo = F0;
+    double* Fn = F1;
+    const int ne = static_cast<int>(nent);
+    for (int q = 0; q < sw; ++q) {
+      if (ilu)
+        k_ilu0_sweep<<<grid_for(nent, 256), 256, 0, s>>>(ne, d_ebase, d_lm_rowptr, d_lm_col, d_lm_row,
+                                                         d_lm_diag, d_lm_tpos, d_at, Fo, Fn, d_err);
+      else
+        k_ic0_sweep<<<grid_for(nent, 256), 256, 0, s>>>(ne, d_ebase, d_lm_rowptr, d_lm_col, d_lm_row,
+                                                        d_lm_diag, d_at, Fo, Fn, d_err);
+      GDSW_CK(cudaGetLastError());
+      std::swap(Fo, Fn);
+    }
+    GDSW_TRY(read_err(d_err, s, ilu ? "ILU(0) sweeps" : "IC(0) sweeps"));
+    double* F = Fo;
     k_unscale<<<grid_for(nent, 256), 256, 0, s>>>(static_cast<int>(nent), ilu ? 1 : 0, nullptr,
                                                   d_lm_row, d_lm_col, d_ebase, d_sc, F, G);
     GDSW_CK(cudaGetLastError());
@@ -799,7 +790,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     c->max_levels = std::max(P.L.max_levels, P.U.max_levels);
     // Per-level records for the pipelined level-scheduled solve: for every
     // subdomain its L levels then its U levels, each record 16-byte aligned:
-    //   int4 {rows, width, 0, 0} | rows x uint16 local row | rows x T inverse
+    //   int4 {rows, width, values offset, columns offset} | rows x uint16 local row | rows x T inverse
     //   diagonal | width*rows x T values | width*rows x uint16 columns,
     // every section padded to 16 bytes so a record is one bulk copy.
     {
@@ -844,10 +835,12 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
           for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l, ++rr) {
             const size_t nr = E.lev_nr[l], K = E.lev_K[l];
             const size_t base = size_t(rec_off16[rr]) * 16;
-            const int hdr[4] = {static_cast<int>(nr), static_cast<int>(K), 0, 0};
-            std::memcpy(&host[base], hdr, 16);
             const size_t o_l = base + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
                          o_c = o_v + a16(K * nr * vb);
+            // header: rows, width, and the byte offsets of the values and columns
+            const int hdr[4] = {static_cast<int>(nr), static_cast<int>(K), static_cast<int>(o_v - base),
+                                static_cast<int>(o_c - base)};
+            std::memcpy(&host[base], hdr, 16);
             std::memcpy(&host[o_l], &E.lrows[E.lev_start[l]], 2 * nr);
             std::memcpy(&host[o_c], &E.col[E.lev_off[l]], 2 * K * nr);
             stage = std::max<size_t>(stage, rec_bytes[rr]);
@@ -861,6 +854,10 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       GDSW_TRY(upload(c, &c->rec_off16, rec_off16, s));
       GDSW_TRY(upload(c, &c->rec_bytes, rec_bytes, s));
       c->rec_stage_bytes = static_cast<int>(stage);
+      int maxK = 0;
+      for (int kk : P.L.lev_K) maxK = std::max(maxK, kk);
+      for (int kk : P.U.lev_K) maxK = std::max(maxK, kk);
+      c->rec_max_width = maxK;
       c->rec_total_bytes = static_cast<int64_t>(total);
       for (int side = 0; side < 2; ++side) {
         const EllPlan& E = side == 0 ? P.L : P.U;

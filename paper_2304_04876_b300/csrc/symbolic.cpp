@@ -449,7 +449,7 @@ gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, 
       C->dof_blk[C->brow_dof[q]] = b;
       C->dof_blkrow[C->brow_dof[q]] = q - C->brow_ptr[b];
     }
-  // Phi^T r chunks of at most kChunkRows rows; partial slots per (chunk, column)
+  // Phi^T r chunks of at most kChunkRows rows (4 per thread of a 256-thread CTA); partial slots per (chunk, column)
   constexpr int kChunkRows = 1024;
   C->chunk_blk.clear(); C->chunk_r0.clear(); C->chunk_r1.clear(); C->chunk_slot.clear();
   int nslot = 0;
