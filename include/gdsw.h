@@ -123,6 +123,7 @@ typedef struct {
   int64_t dense_local;    /* entries of the exact solver's dense inverses   */
   int64_t n_blocks;       /* Phi blocks: interiors + interface components   */
   int64_t device_bytes;   /* device memory held by the handle               */
+  int64_t n_problems;     /* independent problems (gdsw_setup_batch)        */
   double setup_seconds;
   double setup_phase_seconds[8]; /* [0] symbolic [1] local factors [2] Phi_Gamma
                                     [3] Phi_I [4] A0 [5] A0^-1 [6] exact local
@@ -146,6 +147,24 @@ GDSW_API void gdsw_default_options(gdsw_options* opt);
  * solver beyond its memory cap). */
 GDSW_API gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const double* Z,
                        int32_t nn, const gdsw_options* opt, void* stream, gdsw_handle* out);
+
+/* Batch of `count` independent problems in one handle (one block-diagonal
+ * system): A[p], parts[p] and, when nn[p] > 0, Z[p] (A[p].n x nn[p],
+ * column-major, host) describe member p; Z or nn may be NULL for constants.
+ * All members need the same dofs_per_node.  Every launch of the apply and of
+ * the SpMV covers all members' subdomains; A0 is one dense block per member.
+ * Vectors of this handle are the members' vectors concatenated in order.
+ * Only PCG is supported (GDSW_ERR_UNSUPPORTED otherwise).  Sizes: the merged
+ * system must fit 32-bit indices. */
+GDSW_API gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gdsw_partition* parts,
+                                      const double* const* Z, const int32_t* nn,
+                                      const gdsw_options* opt, void* stream, gdsw_handle* out);
+
+/* Batched PCG on a batch handle: each member converges on its own
+ * ||b_p - A_p x_p|| <= tol ||b_p||; info[p] (count entries) per member.
+ * gdsw_solve on a batch handle does the same and summarises info. */
+GDSW_API gdsw_status gdsw_solve_batch(gdsw_handle h, const double* b, double* x,
+                                      gdsw_solve_info* info, void* stream);
 
 /* z = M^-1 r (Eq. 1), device vectors. */
 GDSW_API gdsw_status gdsw_apply(gdsw_handle h, const double* r, double* z, void* stream);

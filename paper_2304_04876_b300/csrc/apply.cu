@@ -331,31 +331,40 @@ __global__ void k_coarse_c(int n0, const int* __restrict__ cs_ptr, const int* __
   }
 }
 
-// y = A0^-1 c, warp per row of the explicit inverse, c staged in shared memory.
+// y = A0^-1 c, warp per row of the explicit inverse (one dense block per
+// problem; c staged in shared memory when there is a single problem).
 __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __restrict__ Ainv,
+                                                     const int* __restrict__ coarse_prob,
+                                                     const int* __restrict__ prob_c0,
+                                                     const int64_t* __restrict__ a0_off, int staged,
                                                      const double* __restrict__ c,
                                                      double* __restrict__ y,
                                                      const KrylovScalars* __restrict__ ks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ks != nullptr && ks->done) return;
   double* cs = reinterpret_cast<double*>(smem_raw);
-  for (int l = threadIdx.x; l < n0; l += blockDim.x) cs[l] = c[l];
-  __syncthreads();
+  if (staged) {
+    for (int l = threadIdx.x; l < n0; l += blockDim.x) cs[l] = c[l];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (blockDim.x >> 5);
   for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n0; row += warps) {
-    const double* Ar = Ainv + int64_t(row) * n0;
+    const int pr = coarse_prob[row];
+    const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;
+    const double* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
+    const double* cv = staged ? cs + cp : c + cp;
     // four independent FMA chains per lane (FP64 latency), loads issued first
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int j = lane;
-    for (; j + 96 < n0; j += 128) {
+    for (; j + 96 < np; j += 128) {
       const double m0 = Ar[j], m1 = Ar[j + 32], m2 = Ar[j + 64], m3 = Ar[j + 96];
-      a0 = fma(m0, cs[j], a0);
-      a1 = fma(m1, cs[j + 32], a1);
-      a2 = fma(m2, cs[j + 64], a2);
-      a3 = fma(m3, cs[j + 96], a3);
+      a0 = fma(m0, cv[j], a0);
+      a1 = fma(m1, cv[j + 32], a1);
+      a2 = fma(m2, cv[j + 64], a2);
+      a3 = fma(m3, cv[j + 96], a3);
     }
-    for (; j < n0; j += 32) a0 = fma(Ar[j], cs[j], a0);
+    for (; j < np; j += 32) a0 = fma(Ar[j], cv[j], a0);
     double acc = (a0 + a1) + (a2 + a3);
     acc = warp_sum(acc);
     if (lane == 0) y[row] = acc;
@@ -513,7 +522,9 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
   if (c->n0 == 0) return GDSW_OK;
   k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, ks);
   const int grid = std::min((c->n0 + 7) / 8, kNumSMs * 4);
-  k_coarse_gemv<<<grid, 256, size_t(c->n0) * sizeof(double), s>>>(c->n0, c->A0inv, c->cvec, c->yvec, ks);
+  const int staged = c->nprob == 1;
+  k_coarse_gemv<<<grid, 256, staged ? size_t(c->n0) * sizeof(double) : 16, s>>>(
+      c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, staged, c->cvec, c->yvec, ks);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -579,7 +590,7 @@ gdsw_status apply_configure(Ctx* c) {
     set_error("subdomain of %d unknowns does not fit the local solve's shared memory", c->max_m);
     return GDSW_ERR_UNSUPPORTED;
   }
-  const size_t shm_coarse = size_t(c->n0) * sizeof(double);
+  const size_t shm_coarse = c->nprob == 1 ? size_t(c->n0) * sizeof(double) : 16;
   if (shm_coarse > 227 * 1024) { set_error("coarse dimension too large"); return GDSW_ERR_UNSUPPORTED; }
   // pipelined level-scheduled solve: deepest ring (6, 4, 3, 2 stages) that fits
   // next to the subdomain vector; otherwise the plain kernel

@@ -1,0 +1,338 @@
+// Batched PCG over independent problems merged into one handle.
+//
+// The merged handle holds the block-diagonal union of the problems (one CSR,
+// one set of subdomains, one coarse block per problem), so the SpMV and every
+// phase of the preconditioner run as one launch for all problems.  The Krylov
+// scalars are per problem: vectors are cut into tiles that never straddle two
+// problems, every tile writes its partial dot products, and one warp per
+// problem adds its tiles in order (deterministic).  Each problem stops updating
+// once it has converged; the iteration runs in a CUDA graph behind a device-side
+// while node until every problem has stopped.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gdsw {
+
+namespace {
+
+constexpr int kTileRows = 4096;
+constexpr int kThreads = 256;
+
+// per-tile partial of (a, b) into part[2 t + slot] (tiles of stopped problems skip)
+__global__ void __launch_bounds__(kThreads) k_bdot(const int* __restrict__ tile_prob,
+                                                   const int* __restrict__ tile_r0,
+                                                   const int* __restrict__ tile_r1,
+                                                   const double* __restrict__ a,
+                                                   const double* __restrict__ b,
+                                                   const BatchScalars* __restrict__ bs,
+                                                   double* __restrict__ part, int slot) {
+  __shared__ double sh[32];
+  const int t = blockIdx.x;
+  if (bs[tile_prob[t]].done) return;
+  double ab = 0.0;
+  for (int i = tile_r0[t] + threadIdx.x; i < tile_r1[t]; i += blockDim.x) ab = fma(a[i], b[i], ab);
+  ab = block_sum(ab, sh);
+  if (threadIdx.x == 0) part[2 * t + slot] = ab;
+}
+
+enum { RED_PQ = 0, RED_RR = 1, RED_RZ = 2 };
+
+// One warp per problem adds its tiles' partials in order and advances the
+// problem's PCG state:
+//   RED_PQ:   alpha = rz / pq
+//   RED_RR:   count the iteration, stop on ||r||^2 <= tol^2 ||b||^2, maxit or breakdown
+//   RED_RZ:   beta = (r, z)_new / (r, z)_old, or with `flexible` the
+//             flexible beta ((r, z)_new - (r, z_old)) / (r, z)_old
+__global__ void k_breduce(int nprob, const int* __restrict__ prob_tile_ptr,
+                          const double* __restrict__ part, BatchScalars* bs, int which,
+                          BatchControl* ctl, int flexible, cudaGraphConditionalHandle handle,
+                          int use_handle) {
+  const int lane = threadIdx.x & 31;
+  const int pr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (pr >= nprob) return;
+  BatchScalars& S = bs[pr];
+  if (S.done) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int t = prob_tile_ptr[pr] + lane; t < prob_tile_ptr[pr + 1]; t += 32) {
+    s0 += part[2 * t];
+    if (which == RED_RZ && flexible) s1 += part[2 * t + 1];
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  if (lane != 0) return;
+  if (which == RED_PQ) {
+    S.pq = s0;
+    S.alpha = S.rz / s0;
+    if (!(s0 > 0.0) || !isfinite(S.alpha)) { S.bad = 1; S.alpha = 0.0; }
+  } else if (which == RED_RZ) {
+    S.beta = (flexible ? s0 - s1 : s0) / S.rz;
+    S.rz = s0;
+  } else {  // RED_RR
+    S.rr = s0;
+    S.iter += 1;
+    int stop = 0;
+    if (S.bad || !isfinite(s0)) { S.bad = 1; stop = 1; }
+    else if (s0 <= S.tol2) stop = 1;
+    else if (S.iter >= ctl->maxit) stop = 1;
+    if (stop) {
+      S.done = 1;
+      const unsigned int nd = atomicAdd(&ctl->ndone, 1u) + 1;
+      if (nd == static_cast<unsigned int>(nprob)) {
+        ctl->all_done = 1;
+        if (use_handle) cudaGraphSetConditional(handle, 0);
+      }
+    }
+  }
+}
+
+// the loop must end even when entered with every problem already stopped
+__global__ void k_bguard(BatchControl* ctl, cudaGraphConditionalHandle handle, int use_handle) {
+  if (threadIdx.x == 0 && ctl->all_done && use_handle) cudaGraphSetConditional(handle, 0);
+}
+
+// x += alpha_p p, r -= alpha_p q; partial ||r||^2 per tile (stopped problems skip)
+__global__ void __launch_bounds__(kThreads) k_bupdate(const int* __restrict__ tile_prob,
+                                                      const int* __restrict__ tile_r0,
+                                                      const int* __restrict__ tile_r1,
+                                                      double* __restrict__ x, double* __restrict__ r,
+                                                      const double* __restrict__ p,
+                                                      const double* __restrict__ q,
+                                                      const BatchScalars* __restrict__ bs,
+                                                      double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int t = blockIdx.x;
+  const BatchScalars& S = bs[tile_prob[t]];
+  if (S.done) return;
+  const double alpha = S.alpha;
+  double rr = 0.0;
+  for (int i = tile_r0[t] + threadIdx.x; i < tile_r1[t]; i += blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  rr = block_sum(rr, sh);
+  if (threadIdx.x == 0) part[2 * t] = rr;
+}
+
+// p = z + beta_p p (stopped problems skip); with init, p = z
+__global__ void __launch_bounds__(kThreads) k_bpupdate(const int* __restrict__ tile_prob,
+                                                       const int* __restrict__ tile_r0,
+                                                       const int* __restrict__ tile_r1,
+                                                       const double* __restrict__ z,
+                                                       double* __restrict__ p,
+                                                       const BatchScalars* __restrict__ bs, int init) {
+  const int t = blockIdx.x;
+  const BatchScalars& S = bs[tile_prob[t]];
+  if (S.done) return;
+  const double beta = init ? 0.0 : S.beta;
+  for (int i = tile_r0[t] + threadIdx.x; i < tile_r1[t]; i += blockDim.x)
+    p[i] = init ? z[i] : fma(beta, p[i], z[i]);
+}
+
+// r = b - q
+__global__ void k_bresidual(int n, const double* __restrict__ b, const double* __restrict__ q,
+                            double* __restrict__ r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = b[i] - q[i];
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+gdsw_status batch_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
+  const int nt = c->n_tiles, np = c->nprob;
+  const int rgrid = (np + 7) / 8;
+  k_bguard<<<1, 32, 0, s>>>(c->bctl, h, use_handle);
+  GDSW_TRY(spmv_enqueue(c, c->p, c->q, s));
+  const int flex = c->flexible ? 1 : 0;
+  k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->p, c->q, c->bks, c->red, 0);
+  k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_PQ, c->bctl, flex, h, 0);
+  k_bupdate<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->x, c->r, c->p, c->q, c->bks, c->red);
+  k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_RR, c->bctl, flex, h, use_handle);
+  if (flex) k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 1);
+  GDSW_TRY(apply_enqueue(c, c->r, c->z, s, false));
+  k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 0);
+  k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_RZ, c->bctl, flex, h, 0);
+  k_bpupdate<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->z, c->p, c->bks, 0);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+}  // namespace
+
+gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, cudaStream_t s) {
+  const int np = static_cast<int>(prob_dof_ptr.size()) - 1;
+  std::vector<int> tp, t0, t1, ptp(np + 1, 0);
+  for (int q = 0; q < np; ++q) {
+    for (int r0 = prob_dof_ptr[q]; r0 < prob_dof_ptr[q + 1]; r0 += kTileRows) {
+      tp.push_back(q);
+      t0.push_back(r0);
+      t1.push_back(std::min(prob_dof_ptr[q + 1], r0 + kTileRows));
+    }
+    ptp[q + 1] = static_cast<int>(tp.size());
+  }
+  c->n_tiles = static_cast<int>(tp.size());
+  GDSW_TRY(upload(c, &c->tile_prob, tp, s));
+  GDSW_TRY(upload(c, &c->tile_r0, t0, s));
+  GDSW_TRY(upload(c, &c->tile_r1, t1, s));
+  GDSW_TRY(upload(c, &c->prob_tile_ptr, ptp, s));
+  c->prob_dof_host = prob_dof_ptr;
+  GDSW_TRY(dalloc(c, &c->bks, np));
+  GDSW_TRY(dalloc(c, &c->bctl, 1));
+  if (c->red_len < 4 * c->n_tiles + 64) {        // the initial residual uses two partial arrays
+    GDSW_TRY(dalloc(c, &c->red, 4 * c->n_tiles + 64));
+    c->red_len = 4 * c->n_tiles + 64;
+  }
+  const char* env = getenv("GDSW_PCG_GRAPH");
+  if (env != nullptr && env[0] == '0') return GDSW_OK;
+  GDSW_CK(cudaStreamCreateWithFlags(&c->bgraph_stream, cudaStreamNonBlocking));
+  GDSW_CK(cudaGraphCreate(&c->bgraph, 0));
+  cudaGraphConditionalHandle h;
+  GDSW_CK(cudaGraphConditionalHandleCreate(&h, c->bgraph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams nparams = {};
+  nparams.type = cudaGraphNodeTypeConditional;
+  nparams.conditional.handle = h;
+  nparams.conditional.type = cudaGraphCondTypeWhile;
+  nparams.conditional.size = 1;
+  cudaGraphNode_t node;
+  GDSW_CK(cudaGraphAddNode(&node, c->bgraph, nullptr, nullptr, 0, &nparams));
+  cudaGraph_t body = nparams.conditional.phGraph_out[0];
+  GDSW_CK(cudaStreamBeginCaptureToGraph(c->bgraph_stream, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  gdsw_status st = batch_body(c, c->bgraph_stream, h, 1);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->bgraph_stream, &captured);
+  if (st != GDSW_OK) return st;
+  GDSW_CK(e);
+  GDSW_CK(cudaGraphInstantiate(&c->bgraph_exec, c->bgraph, 0));
+  return GDSW_OK;
+}
+
+// Batched PCG: every problem of the merged handle solved at once, each with its
+// own alpha, beta and stopping test; info[p] per problem.
+gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
+                            cudaStream_t s) {
+  const double t0 = now_s();
+  const int n = c->n, np = c->nprob, nt = c->n_tiles;
+  const int rgrid = (np + 7) / 8;
+  GDSW_CK(cudaMemcpyAsync(c->b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->x, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemsetAsync(c->bks, 0, sizeof(BatchScalars) * np, s));
+  BatchControl ctl = {};
+  ctl.maxit = c->opt.maxit;
+  GDSW_CK(cudaMemcpyAsync(c->bctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+  const int vg = std::min(kNumSMs * 8, (n + kThreads - 1) / kThreads);
+  // initial residual r = b - A x0, rr and bb per problem
+  GDSW_TRY(spmv_enqueue(c, c->x, c->q, s));
+  k_bresidual<<<vg, kThreads, 0, s>>>(n, c->b, c->q, c->r);
+  k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->b, c->b, c->bks, c->red, 0);
+  k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->r, c->bks, c->red + 2 * nt, 0);
+  GDSW_CK(cudaGetLastError());
+  std::vector<double> part(4 * size_t(nt));
+  GDSW_CK(cudaMemcpyAsync(part.data(), c->red, sizeof(double) * 4 * nt, cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  std::vector<int> tile_ptr(np + 1, 0);
+  {
+    int t = 0;
+    for (int q = 0; q < np; ++q) {
+      for (int r0 = c->prob_dof_host[q]; r0 < c->prob_dof_host[q + 1]; r0 += kTileRows) ++t;
+      tile_ptr[q + 1] = t;
+    }
+  }
+  std::vector<BatchScalars> hs(np);
+  std::vector<double> bb(np, 0.0), rr(np, 0.0);
+  int ndone = 0;
+  for (int q = 0; q < np; ++q) {
+    for (int t = tile_ptr[q]; t < tile_ptr[q + 1]; ++t) { bb[q] += part[2 * t]; rr[q] += part[2 * nt + 2 * t]; }
+    hs[q] = BatchScalars{};
+    hs[q].bb = bb[q];
+    hs[q].rr = rr[q];
+    hs[q].tol2 = c->opt.tol * c->opt.tol * bb[q];
+    hs[q].rz = 1.0;
+    if (bb[q] == 0.0 || rr[q] <= hs[q].tol2) { hs[q].done = 1; ++ndone; }
+  }
+  ctl.ndone = ndone;
+  ctl.all_done = ndone == np;
+  GDSW_CK(cudaMemcpyAsync(c->bks, hs.data(), sizeof(BatchScalars) * np, cudaMemcpyHostToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->bctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+  std::vector<int> final_iters(np, 0);
+  std::vector<double> final_rr(rr);
+  for (int round = 0; round < 64 && ndone < np; ++round) {
+    // z = M r, (r, z), p = z (first round) or p = z + beta p (continuation)
+    const int flex = (c->flexible && round > 0) ? 1 : 0;
+    if (flex) k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 1);
+    GDSW_TRY(apply_enqueue(c, c->r, c->z, s, false));
+    k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 0);
+    k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_RZ, c->bctl, flex,
+                                    cudaGraphConditionalHandle{}, 0);
+    k_bpupdate<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->z, c->p, c->bks, round == 0);
+    GDSW_CK(cudaGetLastError());
+    if (c->bgraph_exec != nullptr) {
+      GDSW_CK(cudaGraphLaunch(c->bgraph_exec, s));
+    } else {
+      for (;;) {
+        GDSW_TRY(batch_body(c, s, cudaGraphConditionalHandle{}, 0));
+        BatchControl hc;
+        GDSW_CK(cudaMemcpyAsync(&hc, c->bctl, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        GDSW_CK(cudaStreamSynchronize(s));
+        if (hc.all_done) break;
+      }
+    }
+    // true residual of every problem that stopped on the recurrence
+    GDSW_TRY(spmv_enqueue(c, c->x, c->q, s));
+    k_bresidual<<<vg, kThreads, 0, s>>>(n, c->b, c->q, c->r);
+    GDSW_CK(cudaMemcpyAsync(hs.data(), c->bks, sizeof(BatchScalars) * np, cudaMemcpyDeviceToHost, s));
+    GDSW_CK(cudaStreamSynchronize(s));
+    // partial (r, r) for all tiles: mark everyone active for the dot, restore after
+    std::vector<BatchScalars> act(hs);
+    for (auto& v : act) v.done = 0;
+    GDSW_CK(cudaMemcpyAsync(c->bks, act.data(), sizeof(BatchScalars) * np, cudaMemcpyHostToDevice, s));
+    k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->r, c->bks, c->red, 0);
+    GDSW_CK(cudaGetLastError());
+    GDSW_CK(cudaMemcpyAsync(part.data(), c->red, sizeof(double) * 2 * nt, cudaMemcpyDeviceToHost, s));
+    GDSW_CK(cudaStreamSynchronize(s));
+    ndone = 0;
+    for (int q = 0; q < np; ++q) {
+      double t_rr = 0.0;
+      for (int t = tile_ptr[q]; t < tile_ptr[q + 1]; ++t) t_rr += part[2 * t];
+      final_rr[q] = t_rr;
+      final_iters[q] = hs[q].iter;
+      const bool ok = t_rr <= hs[q].tol2 || bb[q] == 0.0;
+      const bool give_up = hs[q].bad || hs[q].iter >= c->opt.maxit || !std::isfinite(t_rr);
+      if (ok || give_up) { hs[q].done = 1; ++ndone; }
+      else hs[q].done = 0;           // continue this problem from its true residual
+    }
+    ctl.ndone = ndone;
+    ctl.all_done = ndone == np;
+    GDSW_CK(cudaMemcpyAsync(c->bks, hs.data(), sizeof(BatchScalars) * np, cudaMemcpyHostToDevice, s));
+    GDSW_CK(cudaMemcpyAsync(c->bctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+    if (ndone == np) break;
+    // continuation: p = z + beta p happens at the top of the next round (round > 0)
+  }
+  GDSW_CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  GDSW_TRY(check_device_errors(c, s));
+  bool all_ok = true;
+  const double el = now_s() - t0;
+  for (int q = 0; q < np; ++q) {
+    const bool ok = bb[q] == 0.0 || final_rr[q] <= c->opt.tol * c->opt.tol * bb[q];
+    all_ok = all_ok && ok;
+    if (info) {
+      info[q].iters = final_iters[q];
+      info[q].converged = ok ? 1 : 0;
+      info[q].true_relres = bb[q] == 0.0 ? 0.0 : std::sqrt(final_rr[q] / bb[q]);
+      info[q].seconds = el;
+    }
+  }
+  if (!all_ok) { set_error("batched PCG: some problems did not converge"); return GDSW_ERR_NOT_CONVERGED; }
+  return GDSW_OK;
+}
+
+}  // namespace gdsw

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -22,6 +23,9 @@ double now_s() {
 }
 
 void release(Ctx* c) {
+  if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
+  if (c->bgraph) cudaGraphDestroy(c->bgraph);
+  if (c->bgraph_stream) cudaStreamDestroy(c->bgraph_stream);
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
   if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
@@ -52,6 +56,26 @@ void set_error(const char* fmt, ...) {
 }
 
 gdsw_status apply_configure(Ctx* c);
+
+// One solve on any handle; for a batch, info summarises every member (largest
+// iteration count and residual, converged only if all converged).
+gdsw_status solve_any(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s) {
+  if (c->nprob > 1) {
+    std::vector<gdsw_solve_info> all(c->nprob);
+    gdsw_status st = solve_pcg_batch(c, b, x, all.data(), s);
+    if (info) {
+      *info = gdsw_solve_info{0, 1, 0.0, 0.0};
+      for (const auto& a : all) {
+        info->iters = std::max(info->iters, a.iters);
+        info->converged = info->converged && a.converged;
+        info->true_relres = std::max(info->true_relres, a.true_relres);
+        info->seconds = a.seconds;
+      }
+    }
+    return st;
+  }
+  return c->opt.krylov == GDSW_KRYLOV_GMRES ? solve_gmres(c, b, x, info, s) : solve_pcg(c, b, x, info, s);
+}
 
 }  // namespace gdsw
 
@@ -91,20 +115,15 @@ const char* gdsw_status_string(gdsw_status s) {
 
 const char* gdsw_last_error(void) { return g_err; }
 
-gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const double* Z, int32_t nn,
-                       const gdsw_options* opt, void* stream, gdsw_handle* out) {
-  if (!out) { set_error("null output handle"); return GDSW_ERR_INVALID_ARG; }
-  *out = nullptr;
-  gdsw_options o;
-  if (opt) o = *opt; else gdsw_default_options(&o);
-  if (!valid_options(&o)) { set_error("invalid options"); return GDSW_ERR_INVALID_ARG; }
-  if (nn < 0 || (nn > 0 && !Z)) { set_error("null space: nn=%d with Z=%p", nn, (const void*)Z); return GDSW_ERR_INVALID_ARG; }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const double t0 = now_s();
-  Plan P;
-  gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
-  if (st != GDSW_OK) return st;
-  const double t_sym = now_s() - t0;
+}  // extern "C"
+
+namespace {
+
+// Numeric setup, apply/SpMV configuration and Krylov workspace for a plan
+// (one problem, or the merged plan of a batch); the handle on success.
+gdsw_status setup_from_plan(Plan& P, const gdsw_csr* A, const double* Z, int32_t nn,
+                            const gdsw_options& o, cudaStream_t s, double t0, double t_sym,
+                            gdsw_handle* out) {
   gdsw_ctx* h = new (std::nothrow) gdsw_ctx();
   if (!h) { set_error("host allocation failed"); return GDSW_ERR_OUT_OF_MEMORY; }
   Ctx* c = &h->c;
@@ -117,16 +136,18 @@ gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const doub
   c->dpn = P.dpn;
   c->max_m = P.max_m;
   c->sum_m = P.sum_m;
+  c->nprob = P.nprob;
   c->fp32 = o.precision == GDSW_PREC_FP32;
   c->flexible = o.flexible < 0 ? c->fp32 : (o.flexible != 0);
   c->stats.setup_phase_seconds[0] = t_sym;
-  st = numeric_setup(c, P, A, Z, nn, s);
+  gdsw_status st = numeric_setup(c, P, A, Z, nn, s);
   if (st == GDSW_OK) st = c->fp32 ? dalloc(c, reinterpret_cast<float**>(&c->zloc), P.sum_m)
                                   : dalloc(c, reinterpret_cast<double**>(&c->zloc), P.sum_m);
   if (st == GDSW_OK) st = apply_configure(c);
   if (st == GDSW_OK) st = spmv_configure(c, A->rowptr);
   const double t1 = now_s();
   if (st == GDSW_OK) st = krylov_init(c, s);
+  if (st == GDSW_OK && P.nprob > 1) st = batch_init(c, P.prob_dof_ptr, s);
   if (st == GDSW_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { set_error("setup: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; }
@@ -154,9 +175,89 @@ gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const doub
   S.max_levels = c->max_levels;
   S.n_blocks = c->nblk;
   S.device_bytes = static_cast<int64_t>(c->bytes);
+  S.n_problems = P.nprob;
   S.setup_seconds = now_s() - t0;
   *out = h;
   return GDSW_OK;
+}
+
+bool prepare_options(const gdsw_options* opt, gdsw_options* o) {
+  if (opt) *o = *opt; else gdsw_default_options(o);
+  if (!valid_options(o)) { set_error("invalid options"); return false; }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const double* Z, int32_t nn,
+                       const gdsw_options* opt, void* stream, gdsw_handle* out) {
+  if (!out) { set_error("null output handle"); return GDSW_ERR_INVALID_ARG; }
+  *out = nullptr;
+  gdsw_options o;
+  if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
+  if (nn < 0 || (nn > 0 && !Z)) { set_error("null space: nn=%d with Z=%p", nn, (const void*)Z); return GDSW_ERR_INVALID_ARG; }
+  const double t0 = now_s();
+  Plan P;
+  gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
+  if (st != GDSW_OK) return st;
+  return setup_from_plan(P, A, Z, nn, o, static_cast<cudaStream_t>(stream), t0, now_s() - t0, out);
+}
+
+gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gdsw_partition* parts,
+                             const double* const* Z, const int32_t* nn, const gdsw_options* opt,
+                             void* stream, gdsw_handle* out) {
+  if (!out) { set_error("null output handle"); return GDSW_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (count < 1 || !A || !parts) { set_error("batch needs count >= 1 matrices and partitions"); return GDSW_ERR_INVALID_ARG; }
+  gdsw_options o;
+  if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
+  if (o.krylov != GDSW_KRYLOV_PCG) { set_error("batched solves use PCG"); return GDSW_ERR_UNSUPPORTED; }
+  const double t0 = now_s();
+  std::vector<Plan> plans(count);
+  int nnmax = 1;
+  int64_t n = 0, nnz = 0;
+  for (int p = 0; p < count; ++p) {
+    const int np_ = nn ? nn[p] : 0;
+    if (np_ < 0 || (np_ > 0 && (!Z || !Z[p]))) { set_error("null space of member %d", p); return GDSW_ERR_INVALID_ARG; }
+    nnmax = std::max(nnmax, np_);
+    gdsw_status st = build_plan(&A[p], &parts[p], &o, o.local_solver != GDSW_LOCAL_EXACT, &plans[p]);
+    if (st != GDSW_OK) return st;
+    n += A[p].n;
+    nnz += A[p].rowptr[A[p].n];
+  }
+  if (n >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31)) { set_error("batch too large"); return GDSW_ERR_UNSUPPORTED; }
+  // block-diagonal union: CSR and null space (missing columns stay zero and are
+  // dropped by the orthonormalisation)
+  std::vector<int> rp(n + 1, 0), ci;
+  std::vector<double> va;
+  ci.reserve(nnz);
+  va.reserve(nnz);
+  std::vector<double> Zm(size_t(n) * nnmax, 0.0);
+  int64_t off = 0;
+  for (int p = 0; p < count; ++p) {
+    const gdsw_csr& a = A[p];
+    for (int i = 0; i < a.n; ++i) {
+      for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+        ci.push_back(static_cast<int>(a.colind[e] + off));
+        va.push_back(a.val[e]);
+      }
+      rp[off + i + 1] = static_cast<int>(ci.size());
+    }
+    const int np_ = nn ? nn[p] : 0;
+    for (int col = 0; col < nnmax; ++col)
+      for (int i = 0; i < a.n; ++i)
+        Zm[size_t(col) * n + off + i] = np_ == 0 ? (col == 0 ? 1.0 : 0.0)
+                                                 : (col < np_ ? Z[p][size_t(col) * a.n + i] : 0.0);
+    off += a.n;
+  }
+  Plan M;
+  gdsw_status st = merge_plans(plans, &M);
+  if (st != GDSW_OK) return st;
+  gdsw_csr merged{static_cast<int32_t>(n), rp.data(), ci.data(), va.data()};
+  return setup_from_plan(M, &merged, Zm.data(), nnmax, o, static_cast<cudaStream_t>(stream), t0,
+                         now_s() - t0, out);
 }
 
 gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st) {
@@ -184,9 +285,15 @@ gdsw_status gdsw_spmv(gdsw_handle h, const double* x, double* y, void* stream) {
 gdsw_status gdsw_solve(gdsw_handle h, const double* b, double* x, gdsw_solve_info* info,
                        void* stream) {
   if (!h || !b || !x) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  return solve_any(&h->c, b, x, info, static_cast<cudaStream_t>(stream));
+}
+
+gdsw_status gdsw_solve_batch(gdsw_handle h, const double* b, double* x, gdsw_solve_info* info,
+                             void* stream) {
+  if (!h || !b || !x) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
   Ctx* c = &h->c;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return c->opt.krylov == GDSW_KRYLOV_GMRES ? solve_gmres(c, b, x, info, s) : solve_pcg(c, b, x, info, s);
+  if (c->nprob == 1) return solve_any(c, b, x, info, static_cast<cudaStream_t>(stream));
+  return solve_pcg_batch(c, b, x, info, static_cast<cudaStream_t>(stream));
 }
 
 gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
@@ -203,8 +310,7 @@ gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
   GDSW_CK(cudaMemcpyAsync(c->p, x_host, bytes, cudaMemcpyHostToDevice, s));
   double* bd = c->q;
   double* xd = c->p;
-  gdsw_status st = c->opt.krylov == GDSW_KRYLOV_GMRES ? solve_gmres(c, bd, xd, info, s)
-                                                      : solve_pcg(c, bd, xd, info, s);
+  gdsw_status st = solve_any(c, bd, xd, info, s);
   if (st != GDSW_OK && st != GDSW_ERR_NOT_CONVERGED) return st;
   GDSW_CK(cudaMemcpyAsync(x_host, c->x, bytes, cudaMemcpyDeviceToHost, s));
   GDSW_CK(cudaStreamSynchronize(s));

@@ -85,6 +85,10 @@ struct Plan {
   // scatter lists: per dof, the positions in the concatenated local vectors,
   // ascending subdomain order
   std::vector<int> pull_dof_ptr, pull_dof_pos;
+  // independent problems of a batch (one problem unless merged)
+  int nprob = 1;
+  std::vector<int> prob_dof_ptr;          // nprob+1: unknowns of each problem
+  std::vector<int> comp_prob;             // problem of each interface component
 };
 
 // Coarse-space layout once the rank of every component is known.
@@ -106,12 +110,18 @@ struct CoarsePlan {
   // chunk_blk; its partial products go to slots chunk_slot[q] .. + block columns
   std::vector<int> chunk_blk, chunk_r0, chunk_r1, chunk_slot;
   int n_slots = 0;
+  // coarse columns of each problem (A0 is block diagonal over problems)
+  std::vector<int> prob_c0;               // nprob+1
 };
 
 gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
                        bool need_levels, Plan* P);
 gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, bool coarse,
                               CoarsePlan* C);
+// Block-diagonal union of independent problems: every index is offset so the
+// merged plan describes all problems as one (their subdomains, components and
+// levels side by side).
+gdsw_status merge_plans(std::vector<Plan>& parts, Plan* out);
 
 // ---------------------------------------------------------------------------
 // Device context
@@ -143,6 +153,19 @@ struct KrylovScalars {
 };
 
 constexpr int kNumSMsForCtx = 148;
+
+// Per-problem PCG state of a batched handle.
+struct BatchScalars {
+  double rz, pq, rr, bb, tol2, alpha, beta;
+  int iter, done, bad, pad;
+};
+
+struct BatchControl {
+  unsigned int ndone;
+  int all_done;
+  int maxit;
+  int pad;
+};
 
 struct Ctx {
   int device = 0;
@@ -200,7 +223,12 @@ struct Ctx {
   double* partial = nullptr;     // per (block, column) slot
   double* cvec = nullptr;
   double* yvec = nullptr;
-  double* A0inv = nullptr;
+  double* A0inv = nullptr;        // one dense block per problem
+  int* coarse_prob = nullptr;     // problem of each coarse column
+  int* prob_c0 = nullptr;         // coarse column range of each problem
+  int64_t* a0_off = nullptr;      // offset of each problem's block
+  int coarse_max_block = 0;
+  int nprob = 1;
   void* zloc = nullptr;          // local solutions, sum_m
   // Krylov workspace
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
@@ -223,6 +251,15 @@ struct Ctx {
   // events for timed apply
   cudaEvent_t ev[8] = {};
   int red_grid = 0;
+  // batched handle (several independent problems)
+  int n_tiles = 0;
+  int *tile_prob = nullptr, *tile_r0 = nullptr, *tile_r1 = nullptr, *prob_tile_ptr = nullptr;
+  std::vector<int> prob_dof_host;
+  BatchScalars* bks = nullptr;
+  BatchControl* bctl = nullptr;
+  cudaGraph_t bgraph = nullptr;
+  cudaGraphExec_t bgraph_exec = nullptr;
+  cudaStream_t bgraph_stream = nullptr;
   int spmv_R = 256, spmv_maxne = 1, spmv_tiles = 1, spmv_grid = kNumSMsForCtx;
 };
 
@@ -268,6 +305,9 @@ gdsw_status spmv_configure(Ctx* c, const int* rowptr_host);
 gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
 gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
                         cudaStream_t s);
+// batch.cu
+gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, cudaStream_t s);
+gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
 
 constexpr int kNumSMs = 148;
 

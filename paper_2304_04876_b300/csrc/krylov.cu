@@ -340,7 +340,7 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   // the PCG iteration as a graph: while (cond) { body }, cond cleared on device
   const char* env = getenv("GDSW_PCG_GRAPH");
   const bool use_graph = env == nullptr || env[0] != '0';
-  if (c->opt.krylov == GDSW_KRYLOV_PCG && use_graph) {
+  if (c->opt.krylov == GDSW_KRYLOV_PCG && use_graph && c->nprob == 1) {
     GDSW_CK(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     GDSW_CK(cudaGraphCreate(&c->pcg_graph, 0));
     cudaGraphConditionalHandle h;

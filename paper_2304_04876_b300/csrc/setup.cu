@@ -418,8 +418,10 @@ __global__ void k_convert(int64_t len, const double* __restrict__ a, T* __restri
 // One CTA (one warp) per coarse row k, owned by one interface component:
 //   A0[k, :] = sum_{g in Gamma_i} Phi[g, k] sum_j A[g, j] Phi[j, :]
 // accumulated in shared memory in a fixed order (deterministic).
-__global__ void k_coarse_rows(int n0, int nsub, const int* __restrict__ coarse_comp,
-                              const int* __restrict__ comp_c0, const int* __restrict__ rowptr,
+__global__ void k_coarse_rows(int nsub, const int* __restrict__ coarse_comp,
+                              const int* __restrict__ comp_c0, const int* __restrict__ coarse_prob,
+                              const int* __restrict__ prob_c0, const int64_t* __restrict__ a0_off,
+                              const int* __restrict__ rowptr,
                               const int* __restrict__ colind, const double* __restrict__ val,
                               const int* __restrict__ brow_ptr, const int* __restrict__ brow_dof,
                               const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
@@ -431,9 +433,11 @@ __global__ void k_coarse_rows(int n0, int nsub, const int* __restrict__ coarse_c
   const int comp = coarse_comp[k];
   const int b = nsub + comp;
   const int t = k - comp_c0[comp];
+  const int pr = coarse_prob[k];
+  const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;   // this problem's coarse block
   const int R = brow_ptr[b + 1] - brow_ptr[b];
   const double* Pk = phi + phi_off[b] + int64_t(t) * R;
-  for (int l = threadIdx.x; l < n0; l += blockDim.x) acc[l] = 0.0;
+  for (int l = threadIdx.x; l < np; l += blockDim.x) acc[l] = 0.0;
   __syncwarp();
   for (int r = 0; r < R; ++r) {
     const int g = brow_dof[brow_ptr[b] + r];
@@ -445,11 +449,12 @@ __global__ void k_coarse_rows(int n0, int nsub, const int* __restrict__ coarse_c
       const int nr = brow_ptr[bj + 1] - brow_ptr[bj];
       const int c0 = bcol_ptr[bj], kc = bcol_ptr[bj + 1] - c0;
       const double* Pj = phi + phi_off[bj] + rj;
-      for (int u = threadIdx.x; u < kc; u += 32) acc[bcol[c0 + u]] += coef * Pj[int64_t(u) * nr];
+      for (int u = threadIdx.x; u < kc; u += 32) acc[bcol[c0 + u] - cp] += coef * Pj[int64_t(u) * nr];
       __syncwarp();
     }
   }
-  for (int l = threadIdx.x; l < n0; l += blockDim.x) A0[int64_t(k) * n0 + l] = acc[l];
+  double* row = A0 + a0_off[pr] + int64_t(k - cp) * np;
+  for (int l = threadIdx.x; l < np; l += blockDim.x) row[l] = acc[l];
 }
 
 // ---------------------------------------------------------------------------
@@ -983,46 +988,67 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   }
   c->stats.setup_phase_seconds[3] = now_s() - t0;
 
-  // ---- A0 = Phi^T A Phi and its inverse ----
+  // ---- A0 = Phi^T A Phi (one dense block per problem) and its inverse ----
   t0 = now_s();
   if (C.n0 > 0) {
     const int n0 = C.n0;
-    std::vector<int> coarse_comp(n0);
+    const int np_ = P.nprob;
+    std::vector<int> coarse_comp(n0), coarse_prob(n0);
     for (int q = 0; q < P.ncomp; ++q)
-      for (int t = 0; t < C.comp_k[q]; ++t) coarse_comp[C.comp_c0[q] + t] = q;
+      for (int t = 0; t < C.comp_k[q]; ++t) {
+        coarse_comp[C.comp_c0[q] + t] = q;
+        coarse_prob[C.comp_c0[q] + t] = P.comp_prob[q];
+      }
+    std::vector<int64_t> a0_off(np_ + 1, 0);
+    int maxb = 0;
+    for (int q = 0; q < np_; ++q) {
+      const int64_t nb = C.prob_c0[q + 1] - C.prob_c0[q];
+      a0_off[q + 1] = a0_off[q] + nb * nb;
+      maxb = std::max<int>(maxb, static_cast<int>(nb));
+    }
     int *d_cc, *d_c0b, *d_dof_blk, *d_dof_blkrow;
     GDSW_TRY(sc.put(&d_cc, coarse_comp, s));
     GDSW_TRY(sc.put(&d_c0b, C.comp_c0, s));
     GDSW_TRY(sc.put(&d_dof_blk, C.dof_blk, s));
     GDSW_TRY(sc.put(&d_dof_blkrow, C.dof_blkrow, s));
+    GDSW_TRY(upload(c, &c->coarse_prob, coarse_prob, s));
+    GDSW_TRY(upload(c, &c->prob_c0, C.prob_c0, s));
+    GDSW_TRY(upload(c, &c->a0_off, a0_off, s));
+    c->coarse_max_block = maxb;
     double* d_A0;
-    GDSW_TRY(sc.get(&d_A0, size_t(n0) * n0));
-    const size_t shm = size_t(n0) * sizeof(double);
-    if (shm > 227 * 1024) { set_error("coarse dimension %d too large for the A0 kernel", n0); return GDSW_ERR_UNSUPPORTED; }
+    GDSW_TRY(sc.get(&d_A0, a0_off[np_]));
+    const size_t shm = size_t(maxb) * sizeof(double);
+    if (shm > 227 * 1024) { set_error("coarse dimension %d too large for the A0 kernel", maxb); return GDSW_ERR_UNSUPPORTED; }
     if (shm > 48 * 1024)
       GDSW_CK(cudaFuncSetAttribute(k_coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
-    k_coarse_rows<<<n0, 32, shm, s>>>(n0, nsub, d_cc, d_c0b, c->rowptr, c->colind, c->val, c->brow_ptr,
-                                      c->brow_dof, c->bcol_ptr, c->bcol, c->phi_off, phi64, d_dof_blk,
-                                      d_dof_blkrow, d_A0);
+    k_coarse_rows<<<n0, 32, std::max<size_t>(shm, 8), s>>>(nsub, d_cc, d_c0b, c->coarse_prob, c->prob_c0,
+                                                          c->a0_off, c->rowptr, c->colind, c->val,
+                                                          c->brow_ptr, c->brow_dof, c->bcol_ptr, c->bcol,
+                                                          c->phi_off, phi64, d_dof_blk, d_dof_blkrow, d_A0);
     GDSW_CK(cudaGetLastError());
     c->stats.setup_phase_seconds[4] = now_s() - t0;
     t0 = now_s();
-    const int nbk = (n0 + NB - 1) / NB;
-    for (int J = 0; J < nbk; ++J) {
-      k_potrf_diag<<<1, 256, 0, s>>>(d_A0, n0, J, d_err);
-      const int rest = nbk - J - 1;
-      if (rest > 0) {
-        k_trsm_panel<<<rest, 32, 0, s>>>(d_A0, n0, J);
-        k_syrk_update<<<dim3(rest, rest), 256, 0, s>>>(d_A0, n0, J);
+    GDSW_TRY(dalloc(c, &c->A0inv, a0_off[np_]));
+    double* d_W;
+    const int maxnbk = (maxb + NB - 1) / NB;
+    GDSW_TRY(sc.get(&d_W, size_t(maxnbk) * NB * maxb));
+    for (int q = 0; q < np_; ++q) {
+      const int nb0 = C.prob_c0[q + 1] - C.prob_c0[q];
+      if (nb0 == 0) continue;
+      double* Aq = d_A0 + a0_off[q];
+      const int nbk = (nb0 + NB - 1) / NB;
+      for (int J = 0; J < nbk; ++J) {
+        k_potrf_diag<<<1, 256, 0, s>>>(Aq, nb0, J, d_err);
+        const int rest = nbk - J - 1;
+        if (rest > 0) {
+          k_trsm_panel<<<rest, 32, 0, s>>>(Aq, nb0, J);
+          k_syrk_update<<<dim3(rest, rest), 256, 0, s>>>(Aq, nb0, J);
+        }
       }
+      k_chol_inverse<<<nbk, 256, 0, s>>>(Aq, nb0, d_W, c->A0inv + a0_off[q]);
     }
     GDSW_CK(cudaGetLastError());
     GDSW_TRY(read_err(d_err, s, "coarse Cholesky"));
-    double* d_W;
-    GDSW_TRY(sc.get(&d_W, size_t(nbk) * NB * n0));
-    GDSW_TRY(dalloc(c, &c->A0inv, size_t(n0) * n0));
-    k_chol_inverse<<<nbk, 256, 0, s>>>(d_A0, n0, d_W, c->A0inv);
-    GDSW_CK(cudaGetLastError());
     // Phi in the apply precision
     if (c->fp32) {
       float* pf;

@@ -397,6 +397,106 @@ gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw
     std::vector<int> pos(P->pull_dof_ptr.begin(), P->pull_dof_ptr.end() - 1);
     for (int64_t q = 0; q < P->sum_m; ++q) P->pull_dof_pos[pos[P->om_dofs[q]]++] = static_cast<int>(q);
   }
+  P->nprob = 1;
+  P->prob_dof_ptr = {0, n};
+  P->comp_prob.assign(P->ncomp, 0);
+  return GDSW_OK;
+}
+
+gdsw_status merge_plans(std::vector<Plan>& parts, Plan* M) {
+  if (parts.empty()) { set_error("empty batch"); return GDSW_ERR_INVALID_ARG; }
+  Plan& o = *M;
+  o = Plan();
+  o.dpn = parts[0].dpn;
+  o.nprob = static_cast<int>(parts.size());
+  o.prob_dof_ptr.assign(o.nprob + 1, 0);
+  int64_t n = 0, nnodes = 0, nnz = 0, sum_m = 0, nent = 0, nsub = 0, ncomp = 0;
+  int64_t levL = 0, levU = 0, slotsL = 0, slotsU = 0;
+  for (const Plan& p : parts) {
+    if (p.dpn != o.dpn) { set_error("batch members must have the same unknowns per node"); return GDSW_ERR_INVALID_ARG; }
+    n += p.n; nnodes += p.nnodes; nnz += p.nnz; sum_m += p.sum_m; nent += p.lm_col.size();
+    nsub += p.nsub; ncomp += p.ncomp;
+    levL += p.L.lev_nr.size(); levU += p.U.lev_nr.size(); slotsL += p.L.slots; slotsU += p.U.slots;
+  }
+  if (n >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31) || nent >= (int64_t(1) << 31) ||
+      sum_m >= (int64_t(1) << 31) || slotsL >= (int64_t(1) << 31) || slotsU >= (int64_t(1) << 31)) {
+    set_error("batch too large for 32-bit indices"); return GDSW_ERR_UNSUPPORTED;
+  }
+  o.n = static_cast<int>(n); o.nnodes = static_cast<int>(nnodes); o.nnz = nnz;
+  o.nsub = static_cast<int>(nsub); o.ncomp = static_cast<int>(ncomp); o.sum_m = sum_m;
+  o.om_ptr.assign(1, 0); o.int_ptr.assign(1, 0); o.comp_ptr.assign(1, 0);
+  o.lm_rowptr.assign(1, 0); o.lm_sub_ent.assign(1, 0); o.pull_dof_ptr.assign(1, 0);
+  for (EllPlan* E : {&o.L, &o.U}) E->sub_lev.assign(1, 0);
+  int doff = 0, noff = 0, soff = 0, coff = 0, moff = 0, eoff = 0, goff = 0;
+  int lvL = 0, lvU = 0, slL = 0, slU = 0;
+  for (int pi = 0; pi < o.nprob; ++pi) {
+    Plan& p = parts[pi];
+    auto add = [](std::vector<int>& dst, const std::vector<int>& src, int off, bool keep_neg) {
+      for (int v : src) dst.push_back((keep_neg && v < 0) ? v : v + off);
+    };
+    add(o.node_sub, p.node_sub, soff, false);
+    add(o.node_comp, p.node_comp, coff, true);
+    o.comp_type.insert(o.comp_type.end(), p.comp_type.begin(), p.comp_type.end());
+    add(o.comp_dofs, p.comp_dofs, doff, false);
+    add(o.int_dofs, p.int_dofs, doff, false);
+    add(o.om_dofs, p.om_dofs, doff, false);
+    add(o.dof_comp, p.dof_comp, coff, true);
+    o.dof_comprow.insert(o.dof_comprow.end(), p.dof_comprow.begin(), p.dof_comprow.end());
+    o.dof_introw.insert(o.dof_introw.end(), p.dof_introw.begin(), p.dof_introw.end());
+    for (int q = 1; q < static_cast<int>(p.lm_rowptr.size()); ++q) o.lm_rowptr.push_back(p.lm_rowptr[q] + eoff);
+    o.lm_col.insert(o.lm_col.end(), p.lm_col.begin(), p.lm_col.end());
+    o.lm_row.insert(o.lm_row.end(), p.lm_row.begin(), p.lm_row.end());
+    add(o.lm_gent, p.lm_gent, goff, false);
+    add(o.lm_tpos, p.lm_tpos, eoff, false);
+    add(o.lm_diag, p.lm_diag, eoff, false);
+    for (int q = 1; q < static_cast<int>(p.lm_sub_ent.size()); ++q) o.lm_sub_ent.push_back(p.lm_sub_ent[q] + eoff);
+    struct Side { EllPlan* dst; EllPlan* src; int* lv; int* sl; };
+    Side sides[2] = {{&o.L, &p.L, &lvL, &slL}, {&o.U, &p.U, &lvU, &slU}};
+    for (Side& sd : sides) {
+      EllPlan& D = *sd.dst;
+      EllPlan& S = *sd.src;
+      for (size_t q = 1; q < S.sub_lev.size(); ++q) D.sub_lev.push_back(S.sub_lev[q] + *sd.lv);
+      add(D.lev_start, S.lev_start, moff, false);
+      D.lev_nr.insert(D.lev_nr.end(), S.lev_nr.begin(), S.lev_nr.end());
+      D.lev_K.insert(D.lev_K.end(), S.lev_K.begin(), S.lev_K.end());
+      add(D.lev_off, S.lev_off, *sd.sl, false);
+      D.lrows.insert(D.lrows.end(), S.lrows.begin(), S.lrows.end());
+      D.col.insert(D.col.end(), S.col.begin(), S.col.end());
+      add(D.src, S.src, eoff, true);
+      add(D.dsrc, S.dsrc, eoff, true);
+      D.nnz += S.nnz;
+      D.slots += S.slots;
+      D.max_levels = std::max(D.max_levels, S.max_levels);
+      *sd.lv += static_cast<int>(S.lev_nr.size());
+      *sd.sl += static_cast<int>(S.slots);
+    }
+    for (const std::vector<int>& adj : p.int_adj) {
+      std::vector<int> a;
+      for (int c : adj) a.push_back(c + coff);
+      o.int_adj.push_back(a);
+    }
+    o.int_bw.insert(o.int_bw.end(), p.int_bw.begin(), p.int_bw.end());
+    o.om_bw.insert(o.om_bw.end(), p.om_bw.begin(), p.om_bw.end());
+    for (int g = 1; g <= p.n; ++g) o.pull_dof_ptr.push_back(p.pull_dof_ptr[g] + o.pull_dof_ptr[doff]);
+    add(o.pull_dof_pos, p.pull_dof_pos, moff, false);
+    o.comp_prob.insert(o.comp_prob.end(), p.ncomp, pi);
+    o.max_m = std::max(o.max_m, p.max_m);
+    // pointer arrays from sizes
+    for (int q = 0; q < p.nsub; ++q) {
+      o.om_ptr.push_back(o.om_ptr.back() + p.om_ptr[q + 1] - p.om_ptr[q]);
+      o.int_ptr.push_back(o.int_ptr.back() + p.int_ptr[q + 1] - p.int_ptr[q]);
+    }
+    doff += p.n; noff += p.nnodes; soff += p.nsub; coff += p.ncomp;
+    moff += static_cast<int>(p.sum_m); eoff += static_cast<int>(p.lm_col.size()); goff += static_cast<int>(p.nnz);
+    o.prob_dof_ptr[pi + 1] = doff;
+    p = Plan();   // release the member's memory as soon as it is merged
+  }
+  // component pointers from the merged component dof lists
+  o.comp_ptr.assign(o.ncomp + 1, 0);
+  for (int g = 0; g < o.n; ++g)
+    if (o.dof_comp[g] >= 0) o.comp_ptr[o.dof_comp[g] + 1]++;
+  for (int c = 0; c < o.ncomp; ++c) o.comp_ptr[c + 1] += o.comp_ptr[c];
+  (void)noff;
   return GDSW_OK;
 }
 
@@ -412,6 +512,9 @@ gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, 
     n0 += C->comp_k[c];
   }
   C->n0 = n0;
+  C->prob_c0.assign(P.nprob + 1, 0);
+  for (int c = 0; c < ncomp; ++c) C->prob_c0[P.comp_prob[c] + 1] += C->comp_k[c];
+  for (int q = 0; q < P.nprob; ++q) C->prob_c0[q + 1] += C->prob_c0[q];
   C->nblk = nsub + ncomp;
   const int nblk = C->nblk;
   C->brow_ptr.assign(nblk + 1, 0);

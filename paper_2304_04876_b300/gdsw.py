@@ -49,7 +49,7 @@ class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in (
         "n", "nnz", "n_sub", "n0", "n_comp", "sum_omega", "max_omega", "nnz_L", "nnz_U", "ell_L",
         "ell_U", "nnz_phi", "n_levels_L", "n_levels_U", "max_levels", "dense_local", "n_blocks",
-        "device_bytes")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8)]
+        "device_bytes", "n_problems")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "setup_phase_seconds"}
@@ -70,6 +70,9 @@ SIGNATURES = {
     "gdsw_default_options": (None, [C.POINTER(Options)]),
     "gdsw_setup": (C.c_int, [C.POINTER(CSRStruct), C.POINTER(PartitionStruct), C.c_void_p, C.c_int32,
                              C.POINTER(Options), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "gdsw_setup_batch": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(Options), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "gdsw_solve_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_apply_timed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "gdsw_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -140,8 +143,11 @@ def _stream(stream) -> Optional[int]:
 class Handle:
     """One set-up problem: factors, Phi and A0^-1 resident on the device."""
 
-    def __init__(self, A, part, Z: Optional[np.ndarray] = None, stream=None, **options):
+    def __init__(self, A, part, Z: Optional[np.ndarray] = None, stream=None, _batch=None, **options):
         lib = load()
+        if _batch is not None:
+            self._init_batch(_batch, stream, options)
+            return
         rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
         colind = np.ascontiguousarray(A.colind, dtype=np.int32)
         val = np.ascontiguousarray(A.val, dtype=np.float64)
@@ -162,6 +168,55 @@ class Handle:
                               _stream(stream) if stream is not False else None, C.byref(h)), "gdsw_setup")
         self._h = h
         self.n = int(A.n)
+
+    def _init_batch(self, members, stream, options):
+        """members: list of (A, part, Z or None)."""
+        lib = load()
+        count = len(members)
+        keep = []
+        csrs = (CSRStruct * count)()
+        parts = (PartitionStruct * count)()
+        zs = (C.c_void_p * count)()
+        nns = (C.c_int32 * count)()
+        for i, (A, part, Z) in enumerate(members):
+            rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+            ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+            va = np.ascontiguousarray(A.val, dtype=np.float64)
+            keep += [rp, ci, va]
+            csrs[i] = CSRStruct(int(A.n), rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+            cuts = [np.ascontiguousarray(c, dtype=np.int32) for c in part.cuts]
+            keep += cuts
+            parts[i] = PartitionStruct(int(part.nx), int(part.ny), int(part.nz), int(part.dpn))
+            for a in range(3):
+                parts[i].ncut[a] = len(cuts[a])
+                parts[i].cut[a] = cuts[a].ctypes.data if len(cuts[a]) else None
+            if Z is None:
+                zs[i], nns[i] = None, 0
+            else:
+                Zc = np.asfortranarray(np.asarray(Z, dtype=np.float64).reshape(A.n, -1))
+                keep.append(Zc)
+                zs[i], nns[i] = Zc.ctypes.data, Zc.shape[1]
+        self.options = make_options(**options)
+        h = C.c_void_p()
+        _check(lib.gdsw_setup_batch(count, C.cast(csrs, C.c_void_p), C.cast(parts, C.c_void_p),
+                                    C.cast(zs, C.c_void_p), C.cast(nns, C.c_void_p), C.byref(self.options),
+                                    _stream(stream) if stream is not False else None, C.byref(h)),
+               "gdsw_setup_batch")
+        self._h = h
+        self.count = count
+        self.n = sum(int(m[0].n) for m in members)
+
+    @classmethod
+    def batch(cls, members, stream=None, **options):
+        """One handle for independent problems [(A, part, Z), ...] (block-diagonal union)."""
+        return cls(None, None, None, stream=stream, _batch=members, **options)
+
+    def solve_batch(self, b, x, stream=None, raise_on_nonconvergence=True):
+        infos = (SolveInfo * self.count)()
+        st = load().gdsw_solve_batch(self._handle(), _ptr(b), _ptr(x), C.cast(infos, C.c_void_p), _stream(stream))
+        if st != ERR_NOT_CONVERGED or raise_on_nonconvergence:
+            _check(st, "gdsw_solve_batch")
+        return list(infos)
 
     def _handle(self):
         if self._h is None:

@@ -36,6 +36,16 @@ def main():
                 key = f"{name}/{local}/{trsv}/seed{seed}"
                 res[key] = {"iters": info.iters, "relres": info.relres, "converged": bool(info.converged)}
                 print(key, res[key], f"{time.time() - t0:.1f}s", flush=True)
+    # Q1 elasticity 48^3 elements, 4^3 subdomains, ILU(0) 3 sweeps, right-preconditioned GMRES(30)
+    prob = P.config_problem(3)
+    t0 = time.time()
+    M = O.GDSW(prob.A, prob.part, prob.Z, local=O.ILU0)
+    for trsv in ("levelsched", "jacobi"):
+        M.trsv = trsv
+        x, info = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=30)
+        key = f"elasticity_48_se12/ilu0/{trsv}/gmres30/body_force"
+        res[key] = {"iters": info.iters, "relres": info.relres, "converged": bool(info.converged)}
+        print(key, res[key], f"{time.time() - t0:.1f}s", flush=True)
     json.dump(res, open(OUT, "w"), indent=1, sort_keys=True)
 
 

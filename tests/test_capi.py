@@ -94,4 +94,15 @@ def test_structs_match_header(lib):
     fields = re.findall(r"(?:int32_t|double)\s+(\w+);", body)
     assert fields == [f for f, _ in G.Options._fields_]
     assert C.sizeof(G.Options) == 11 * 4 + 4 + 8
-    assert C.sizeof(G.Stats) == 18 * 8 + 9 * 8
+    assert C.sizeof(G.Stats) == 19 * 8 + 9 * 8
+
+
+def test_batch_rejects_bad_members_on_host(lib):
+    a = P.poisson_problem(6, 3)
+    e = P.elasticity_problem(2, 1)
+    with pytest.raises(G.GdswError) as ex:      # different unknowns per node
+        G.Handle.batch([(a.A, a.part, None), (e.A, e.part, None)], stream=False)
+    assert ex.value.status == G.ERR_INVALID_ARG
+    with pytest.raises(G.GdswError) as ex:      # GMRES is not batched
+        G.Handle.batch([(a.A, a.part, None)], stream=False, krylov="gmres")
+    assert ex.value.status == G.ERR_UNSUPPORTED

@@ -1,0 +1,75 @@
+"""Full-size parity in the launch configuration bench.py times: Poisson 128^3 with 512
+subdomains (IC(0), both triangular solves, FP64 and FP32 preconditioner) and Q1
+elasticity 48^3 with 64 subdomains (ILU(0), GMRES(30)).
+
+The apply is compared with the oracle on the whole vector (relative 2-norm error
+<= 1e-10 in FP64); iteration counts are compared with the oracle's, stored in
+tests/golden/oracle_pcg.json by tests/golden/make_golden.py (oracle only), within +-1."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2304_04876_b300 import problems as P
+from tests.gpu_util import gpu_apply, gpu_handle, gpu_solve, oracle_for, relerr
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_pcg.json")))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2304_04876_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+@pytest.fixture(scope="module")
+def poisson128():
+    prob = P.config_problem(2, seed=0)
+    return prob, oracle_for(prob, local="ic0")
+
+
+@pytest.mark.parametrize("trsv", ["levelsched", "jacobi"])
+def test_poisson128_apply_matches_oracle(poisson128, trsv):
+    prob, M = poisson128
+    M.trsv = {"levelsched": "levelsched", "jacobi": "jacobi"}[trsv]
+    h = gpu_handle(prob, local_solver="ic0", trsv=trsv)
+    r = P.rhs_uniform(prob.A.n, 11)
+    assert relerr(gpu_apply(h, r), M.apply(r)) <= 1e-10
+    h.close()
+
+
+@pytest.mark.parametrize("trsv,precision", [("levelsched", "fp64"), ("jacobi", "fp64"),
+                                            ("levelsched", "fp32"), ("jacobi", "fp32")])
+def test_poisson128_pcg_iterations(trsv, precision):
+    prob = P.config_problem(2, seed=0)
+    ref = GOLD[f"poisson_128_s16/ic0/{trsv}/seed0"]["iters"]
+    h = gpu_handle(prob, local_solver="ic0", trsv=trsv, precision=precision)
+    x, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    if precision == "fp64":
+        assert abs(info.iters - ref) <= 1, (info.iters, ref)
+    else:
+        # FP32 preconditioner inside FP64 PCG: at most two extra iterations (Table VII behaviour)
+        assert info.iters <= ref + 2, (info.iters, ref)
+    assert np.linalg.norm(prob.b - prob.A.to_scipy() @ x) / np.linalg.norm(prob.b) <= 1e-8
+    h.close()
+
+
+def test_elasticity48_apply_and_gmres():
+    prob = P.config_problem(3)
+    M = oracle_for(prob, local="ilu0")
+    h = gpu_handle(prob, local_solver="ilu0", krylov="gmres", restart=30)
+    st = h.stats()
+    assert st["n0"] == M.n0 == 1485
+    r = np.random.default_rng(2).uniform(-1, 1, prob.A.n)
+    assert relerr(gpu_apply(h, r), M.apply(r)) <= 1e-10
+    ref = GOLD["elasticity_48_se12/ilu0/levelsched/gmres30/body_force"]["iters"]
+    x, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    assert abs(info.iters - ref) <= 1, (info.iters, ref)
+    h.close()
