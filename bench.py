@@ -21,7 +21,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 # the CPU oracle legs run single-threaded; set before numpy loads its BLAS
@@ -40,11 +39,35 @@ VARIANTS = {
     "fp64_jacobi": dict(local_solver="ic0", trsv="jacobi", precision="fp64"),
     "fp32_levelsched": dict(local_solver="ic0", trsv="levelsched", precision="fp32"),
     "fp32_jacobi": dict(local_solver="ic0", trsv="jacobi", precision="fp32"),
+    "fp16_levelsched": dict(local_solver="ic0", trsv="levelsched", precision="fp16"),
+    "fp64_levelsched_rgdsw": dict(local_solver="ic0", trsv="levelsched", precision="fp64", coarse="rgdsw"),
+    "fp32_levelsched_rgdsw": dict(local_solver="ic0", trsv="levelsched", precision="fp32", coarse="rgdsw"),
 }
-DEFAULT_VARIANT = "fp64_levelsched"
+DEFAULT_VARIANT = "fp32_levelsched"
 METRIC = "PCG solves/s to 1e-8 relative residual (time-to-residual = 1/value)"
 WORKLOAD = "poisson7_128^3_512sub16^3_gdsw_ic0"
 
+# the other fixed workloads (python bench.py --config N); config 2 is the default line
+CONFIGS = {
+    1: dict(workload="poisson7_16^3_8sub8^3_gdsw_exact", metric=METRIC, make=lambda: P.config_problem(1),
+            variants={"fp64_exact": dict(local_solver="exact", precision="fp64"),
+                      "fp32_exact": dict(local_solver="exact", precision="fp32")},
+            default="fp64_exact", Z=False),
+    2: dict(workload=WORKLOAD, metric=METRIC, make=lambda: P.config_problem(2), variants=VARIANTS,
+            default=DEFAULT_VARIANT, Z=False),
+    3: dict(workload="elasticity_q1_48^3_64sub12^3_gdsw_rbm_ilu0_gmres30",
+            metric="GMRES(30) solves/s to 1e-8 relative residual (time-to-residual = 1/value)",
+            make=lambda: P.config_problem(3),
+            variants={"fp64_levelsched": dict(local_solver="ilu0", krylov="gmres", restart=30),
+                      "fp32_levelsched": dict(local_solver="ilu0", krylov="gmres", restart=30, precision="fp32"),
+                      "fp64_jacobi": dict(local_solver="ilu0", krylov="gmres", restart=30, trsv="jacobi"),
+                      "fp32_jacobi": dict(local_solver="ilu0", krylov="gmres", restart=30, trsv="jacobi",
+                                          precision="fp32"),
+                      "fp16_levelsched": dict(local_solver="ilu0", krylov="gmres", restart=30, precision="fp16"),
+                      "fp32_levelsched_rgdsw": dict(local_solver="ilu0", krylov="gmres", restart=30,
+                                                    precision="fp32", coarse="rgdsw")},
+            default="fp32_levelsched", Z=True),
+}
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -137,41 +160,52 @@ class ClockSampler:
 # CPU oracle baseline (rank 0, N = 1): bounded sample, single thread
 # ---------------------------------------------------------------------------
 
-def golden_iters(variant: str) -> int | None:
+def golden_iters(cfg: int, variant: str) -> int | None:
     path = os.path.join(ROOT, "tests", "golden", "oracle_pcg.json")
     if not os.path.exists(path):
         return None
     g = json.load(open(path))
     trsv = "jacobi" if "jacobi" in variant else "levelsched"
-    e = g.get(f"poisson_128_s16/ic0/{trsv}/seed0")
+    key = {1: f"poisson_16_s8/exact/levelsched/seed0", 2: f"poisson_128_s16/ic0/{trsv}/seed0",
+           3: f"elasticity_48_se12/ilu0/{trsv}/gmres30/body_force"}.get(cfg)
+    e = g.get(key)
     return None if e is None else int(e["iters"])
 
 
-def oracle_sample(prob, variant: str, iters_for_metric: int, n_iter: int = 2) -> dict:
-    """Time the oracle's PCG iteration (SpMV + M^-1 apply + vector updates) on the full
-    workload after its setup; solves/s = 1 / (t_iteration * iterations of a solve)."""
+def oracle_for_variant(prob, cfg: int, variant: str):
     from oracle import gdsw_oracle as O
+    local = {1: O.EXACT, 2: O.IC0, 3: O.ILU0}.get(cfg, O.IC0)
     trsv = O.JACOBI if "jacobi" in variant else O.LEVELSCHED
-    if True:
-        t0 = time.perf_counter()
-        M = O.GDSW(prob.A, prob.part, prob.Z, local=O.IC0, trsv=trsv)
-        setup_s = time.perf_counter() - t0
-        b = prob.b
-        r = b.copy()
-        p = M.apply(r)
-        times = []
-        for _ in range(n_iter):
-            t1 = time.perf_counter()
-            q = M.spmv(p)
-            alpha = (r @ p) / (p @ q)
-            r = r - alpha * q
-            z = M.apply(r)
-            beta = (r @ z) / (r @ r + 1.0)
-            p = z + beta * p
-            times.append(time.perf_counter() - t1)
-    t_it = statistics.median(times)
+    Z = prob.Z if cfg == 3 else None
+    return O.GDSW(prob.A, prob.part, Z, local=local, trsv=trsv)
+
+
+def oracle_iteration_time(M, b, n_iter: int) -> float:
+    """Median time of one oracle Krylov iteration: SpMV + M^-1 apply + vector updates."""
+    r = b.copy()
+    p = M.apply(r)
+    times = []
+    for _ in range(n_iter):
+        t1 = time.perf_counter()
+        q = M.spmv(p)
+        alpha = (r @ p) / (p @ q)
+        r = r - alpha * q
+        z = M.apply(r)
+        beta = (r @ z) / (r @ r + 1.0)
+        p = z + beta * p
+        times.append(time.perf_counter() - t1)
+    return statistics.median(times)
+
+
+def oracle_sample(prob, cfg: int, variant: str, iters_for_metric: int, n_iter: int = 2) -> dict:
+    """The oracle (single thread) on the full workload after its setup: solves/s =
+    1 / (seconds per Krylov iteration * iterations of a solve)."""
+    t0 = time.perf_counter()
+    M = oracle_for_variant(prob, cfg, variant)
+    setup_s = time.perf_counter() - t0
+    t_it = oracle_iteration_time(M, prob.b, n_iter)
     return {"value": 1.0 / (t_it * iters_for_metric), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_iter} oracle PCG iterations (SpMV + M^-1 apply + updates) on the full workload, "
+            "sample": f"{n_iter} oracle Krylov iterations (SpMV + M^-1 apply + updates) on the full workload, "
                       f"median {t_it:.3f} s/iteration x {iters_for_metric} iterations per solve; "
                       f"oracle setup {setup_s:.1f} s not counted",
             "seconds_per_iteration": t_it, "oracle_setup_s": setup_s}
@@ -184,35 +218,33 @@ def oracle_sample(prob, variant: str, iters_for_metric: int, n_iter: int = 2) ->
 def run_reference(args, rank: int):
     if rank != 0:
         return
-    prob = P.config_problem(2, seed=0)
-    variant = args.variant
-    iters = golden_iters(variant) or 40
-    from oracle import gdsw_oracle as O
-    trsv = O.JACOBI if "jacobi" in variant else O.LEVELSCHED
-    if True:
-        M = O.GDSW(prob.A, prob.part, prob.Z, local=O.IC0, trsv=trsv)
+    cfg = args.config if args.config in CONFIGS else 2
+    C = CONFIGS[cfg]
+    variant = args.variant or C["default"]
+    prob = C["make"]()
+    iters = golden_iters(cfg, variant) or 40
+    M = oracle_for_variant(prob, cfg, variant)
 
-        def step():
-            # one bounded sample: one PCG iteration of the oracle on the full workload
-            q = M.spmv(prob.b)
-            z = M.apply(prob.b - 1e-3 * q)
-            return float(z[0])
+    def step():
+        # one bounded sample: one oracle Krylov iteration on the full workload
+        q = M.spmv(prob.b)
+        z = M.apply(prob.b - 1e-3 * q)
+        return float(z[0])
 
-        for _ in range(args.warmup):
-            step()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step()
-        el = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
     t_it = el / args.steps
     value = 1.0 / (t_it * iters)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": C["metric"], "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_it * iters,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "variant": variant, "n": prob.A.n,
-                                            "subdomains": 512},
+            "data": "synthetic", "config": {"workload": C["workload"], "variant": variant, "n": prob.A.n},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step = one oracle PCG iteration (SpMV + apply) on the full "
+                             "sample": f"each step = one oracle Krylov iteration (SpMV + apply) on the full "
                                        f"workload; solves/s = 1/(s per iteration x {iters} iterations)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -222,18 +254,329 @@ def run_reference(args, rank: int):
 # our arm
 # ---------------------------------------------------------------------------
 
+def timed_solves(h, bs, x, steps, warmup, stream, barrier, solve=None):
+    import torch
+    solve = solve or (lambda b, xx: h.solve(b, xx))
+    for k in range(warmup):
+        x.zero_()
+        solve(bs[k % len(bs)], x)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for k in range(steps):
+        x.zero_()
+        infos.append(solve(bs[k % len(bs)], x))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / 1e3, infos
+
+
+def kernel_measurements(h, st, vb, stream, v0):
+    """Per-phase apply times (CUDA events on the launching stream), the apply as
+    the solver runs it (branches overlapped) and the SpMV."""
+    import torch
+    rr = v0.clone()
+    zz = torch.empty_like(rr)
+    reps = 20
+    for _ in range(3):
+        h.apply_timed(rr, zz)
+    phases = np.zeros(4)
+    for _ in range(reps):
+        phases += np.array(h.apply_timed(rr, zz))
+    phases /= reps
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(reps):
+        h.apply(rr, zz)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    overlapped = ea.elapsed_time(eb) / reps
+    for _ in range(3):
+        h.spmv(rr, zz)
+    ea.record(stream)
+    for _ in range(reps):
+        h.spmv(rr, zz)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = ea.elapsed_time(eb) / reps
+    hbm, src = peaks()
+    names = ["local", "phiT", "coarse", "combine"]
+    phase_ms = dict(zip(names, phases.tolist()))
+    ab = apply_bytes(st, vb)
+    dom = max(names, key=lambda k: phase_ms[k])
+    achieved = ab[dom] / (phase_ms[dom] * 1e-3) / 1e9
+    return {
+        "apply_ms": float(phases.sum()), "apply_phase_ms": phase_ms,
+        "apply_gbs": sum(ab.values()) / (phases.sum() * 1e-3) / 1e9,
+        "apply_overlapped_ms": overlapped,
+        "apply_overlapped_gbs": sum(ab.values()) / (overlapped * 1e-3) / 1e9,
+        "spmv_ms": spmv_ms, "spmv_gbs": spmv_bytes(st) / (spmv_ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                     "algorithmic_bytes_per_launch": ab[dom]},
+    }
+
+
+def launches_per_solve(iters, krylov="pcg"):
+    # prologue (SpMV, residual, 5 apply kernels) + 8 per PCG iteration + true residual
+    return sum(9 + 8 * it for it in iters) if krylov == "pcg" else None
+
+
+def run_single(args, world, rank, dist, barrier):
+    import torch
+    from paper_2304_04876_b300 import gdsw
+    cfg = args.config
+    C = CONFIGS[cfg]
+    variant = args.variant or C["default"]
+    opts = C["variants"][variant]
+    prob = C["make"]()
+    Z = prob.Z if C["Z"] else None
+    t0 = time.perf_counter()
+    h = gdsw.Handle(prob.A, prob.part, Z, **opts)
+    setup_s = time.perf_counter() - t0
+    st = h.stats()
+    n = prob.A.n
+    if cfg == 3:
+        bs = [torch.tensor(prob.b, dtype=torch.float64, device="cuda")]
+    else:
+        bs = [torch.tensor(P.rhs_uniform(n, (rank * 5 + k) % 997), dtype=torch.float64, device="cuda")
+              for k in range(5)]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    el, infos = timed_solves(h, bs, x, args.steps, args.warmup, stream, barrier)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    iters = [i.iters for i in infos]
+    # end to end through the C ABI with host (page-locked) buffers
+    bh = bs[0].cpu().pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    h.solve_host(bh, xh)
+    barrier()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        xh.zero_()
+        h.solve_host(bh, xh)
+    e2e_el = time.perf_counter() - te
+    if dist is not None:
+        t = torch.tensor([e2e_el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_el = float(t.item())
+    vb = 4 if opts.get("precision") == "fp32" else 8
+    km = kernel_measurements(h, st, vb, stream, bs[0])
+    line = {
+        "metric": C["metric"], "value": world * args.steps / el, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if vb == 4 else "f64", "data": "synthetic",
+        "config": {"workload": C["workload"], "variant": variant, "n": n, "nnz": st["nnz"],
+                   "subdomains": st["n_sub"], "n0": st["n0"], "overlap": 1, "tol": 1e-8,
+                   "l2": "per-iteration working set larger than the 126 MB L2; no flush" if n > 1e6 else
+                         "small workload: L2-resident, launch-latency bound",
+                   "parallelism": f"replicas{world}"},
+        "time_to_residual_ms": 1e3 * el / args.steps, "iters": iters,
+        "true_relres_max": max(i.true_relres for i in infos),
+        "setup_s": setup_s, "setup_phase_s": st["setup_phase_seconds"],
+        **{k: v for k, v in km.items() if k != "roofline"},
+        "roofline": km["roofline"],
+        "e2e": {"value": world * args.steps / e2e_el, "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches_per_solve(iters, opts.get("krylov", "pcg")),
+        "clocks": clk,
+    }
+    if not args.no_variants and rank == 0:
+        var = {}
+        for name, vo in C["variants"].items():
+            if name == variant:
+                continue
+            hv = gdsw.Handle(prob.A, prob.part, Z, **vo)
+            el_v, inf = timed_solves(hv, bs, x, 3, 2, stream, lambda: None)
+            var[name] = {"ms_per_solve": 1e3 * el_v / 3, "iters": [i.iters for i in inf],
+                         "true_relres_max": max(i.true_relres for i in inf)}
+            hv.close()
+        line["variants"] = var
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        it_ref = golden_iters(cfg, variant) or int(np.median(iters))
+        line["cpu_baseline"] = oracle_sample(prob, cfg, variant, it_ref)
+    h.close()
+    return line
+
+
+def run_batch(args, world, rank, dist, barrier):
+    """Config 4: 256 independent heterogeneous diffusion problems in one batched handle;
+    a step is one batched PCG solve of all of them (FP32 local solves, FP64 outer)."""
+    import torch
+    from paper_2304_04876_b300 import gdsw
+    count = args.batch_count
+    mem = P.diffusion_batch(count, seed=rank)
+    opts = dict(local_solver="ic0", trsv="levelsched", precision="fp32")
+    t0 = time.perf_counter()
+    h = gdsw.Handle.batch([(m.A, m.part, None) for m in mem], **opts)
+    setup_s = time.perf_counter() - t0
+    st = h.stats()
+    n = st["n"]
+    b = torch.tensor(np.concatenate([m.b for m in mem]), dtype=torch.float64, device="cuda")
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    el, infos = timed_solves(h, [b], x, args.steps, args.warmup, stream, barrier,
+                             solve=lambda bb, xx: h.solve_batch(bb, xx))
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    iters = [i.iters for i in infos[-1]]
+    relres = max(i.true_relres for inf in infos for i in inf)
+    # one problem at a time with its own handle (same options), on a sample
+    sample = list(range(0, count, max(1, count // 8)))[:8]
+    t_one = 0.0
+    for i in sample:
+        m = mem[i]
+        h1 = gdsw.Handle(m.A, m.part, None, **opts)
+        b1 = torch.tensor(m.b, dtype=torch.float64, device="cuda")
+        x1 = torch.zeros_like(b1)
+        e1, _ = timed_solves(h1, [b1], x1, 2, 1, stream, lambda: None)
+        t_one += e1 / 2
+        h1.close()
+    seq_per_problem = t_one / len(sample)
+    # end to end with host buffers
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    h.solve_host(bh, xh)
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        xh.zero_()
+        h.solve_host(bh, xh)
+    e2e_el = time.perf_counter() - te
+    km = kernel_measurements(h, st, 4, stream, b)
+    line = {
+        "metric": "batched PCG problems solved/s to 1e-8 (256 diffusion problems per step)",
+        "value": world * count * args.steps / el, "unit": "problems/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"batch_{count}_diffusion7_edge16-64_sub8-16_k1e-2..1e2", "n": n,
+                   "nnz": st["nnz"], "subdomains": st["n_sub"], "n0": st["n0"], "problems": count,
+                   "parallelism": f"replicas{world}"},
+        "iters_min_max": [min(iters), max(iters)], "true_relres_max": relres, "setup_s": setup_s,
+        "one_at_a_time_ms_per_problem": 1e3 * seq_per_problem,
+        "one_at_a_time_problems_per_s": 1.0 / seq_per_problem,
+        **{k: v for k, v in km.items() if k != "roofline"},
+        "roofline": km["roofline"],
+        "e2e": {"value": world * count * args.steps / e2e_el, "unit": "problems/s",
+                "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample: the two smallest members, full PCG solves
+        from oracle import gdsw_oracle as O
+        small = sorted(range(count), key=lambda i: mem[i].A.n)[:2]
+        t_cpu, n_cpu = 0.0, 0
+        for i in small:
+            m = mem[i]
+            M = O.GDSW(m.A, m.part, None, local=O.IC0)
+            tt = time.perf_counter()
+            O.pcg(M.spmv, M.apply, m.b, tol=1e-8)
+            t_cpu += time.perf_counter() - tt
+            n_cpu += m.A.n
+        per_unknown = t_cpu / n_cpu
+        line["cpu_baseline"] = {"value": 1.0 / (per_unknown * n / count), "unit": "problems/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"full oracle PCG solves of the two smallest members ({n_cpu} unknowns), "
+                                          f"scaled by unknowns to the batch's mean problem"}
+    h.close()
+    return line
+
+
+def run_serving(args, world, rank, dist, barrier):
+    """Config 5: Poisson-arrival stream of mixed Poisson / Q1 elasticity requests served
+    continuously (resident handles under a memory budget, concurrent streams); p50/p99
+    latency and solves/s per arrival rate."""
+    import torch
+    from paper_2304_04876_b300 import gdsw
+    from paper_2304_04876_b300 import serving as S
+    pool = P.serving_pool(args.pool, seed=rank)
+    byname = {p.name: p for p in pool}
+    opts = dict(local_solver="ic0", trsv="levelsched", precision="fp32")
+
+    def make(key, stream):
+        pr = byname[key]
+        return gdsw.Handle(pr.A, pr.part, pr.Z if pr.part.dpn == 3 else None, stream=stream, **opts)
+
+    def estimate(key):
+        pr = byname[key]
+        return int(pr.A.n * (600 if pr.part.dpn == 1 else 4500))
+
+    free, _total = torch.cuda.mem_get_info()
+    budget = int(args.serving_budget_gb * (1 << 30)) if args.serving_budget_gb else int(0.8 * free)
+    srv = S.Server(make, estimate, budget, workers=args.workers)
+    # warm: set every pool problem up once (resident factors), reported separately
+    t0 = time.perf_counter()
+    warm = srv.run([S.Request(0.0, i, p.name, P.rhs_uniform(p.A.n, 7)) for i, p in enumerate(pool)])
+    warm_s = time.perf_counter() - t0
+    rates = {}
+    rng = np.random.default_rng(rank)
+    for lam in args.rates:
+        arr = S.poisson_arrivals(lam, args.requests, seed=int(lam))
+        reqs = []
+        for i, t in enumerate(arr):
+            pr = pool[int(rng.integers(len(pool)))]
+            reqs.append(S.Request(float(t), i, pr.name, P.rhs_uniform(pr.A.n, 1000 + i)))
+        res = srv.run(reqs)
+        rates[str(lam)] = S.summarize(res)
+    top = rates[str(max(args.rates))]
+    sizes = sorted(p.A.n for p in pool)
+    line = {
+        "metric": "served solves/s (saturated) with p50/p99 latency, mixed Poisson / Q1 elasticity",
+        "value": world * top["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.requests,
+        "warmup": len(pool), "ms_per_step": 1e3 / top["solves_per_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"serving_pool{len(pool)}_poisson+elasticity_32^3-160^3", "pool_unknowns": sizes,
+                   "workers": args.workers, "budget_bytes": budget, "rates_req_per_s": args.rates,
+                   "requests_per_rate": args.requests, "parallelism": f"replicas{world}"},
+        "rates": rates, "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+        "warm_setup_s": warm_s, "setups": srv.setups, "evictions": srv.evictions,
+        "e2e": {"value": world * top["solves_per_s"], "unit": "solves/s",
+                "h2d_bytes_per_step": int(np.mean([8 * n for n in sizes])),
+                "d2h_bytes_per_step": int(np.mean([8 * n for n in sizes]))},
+        "gpu_launches": None, "roofline": None,
+    }
+    srv.close()
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default=DEFAULT_VARIANT, choices=sorted(VARIANTS))
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--variant", default=None)
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--pool", type=int, default=8, help="serving: distinct problems")
+    ap.add_argument("--requests", type=int, default=60, help="serving: requests per rate")
+    ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
+    ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--serving-budget-gb", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.config in CONFIGS and args.variant is not None and args.variant not in CONFIGS[args.config]["variants"]:
+        ap.error(f"variant must be one of {sorted(CONFIGS[args.config]['variants'])}")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -253,156 +596,19 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     else:
         torch.cuda.set_device(0)
-    dev = torch.cuda.current_device()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    prob = P.config_problem(2, seed=0)
-    opts = VARIANTS[args.variant]
-    t0 = time.perf_counter()
-    h = gdsw.Handle(prob.A, prob.part, None, **opts)
-    setup_s = time.perf_counter() - t0
-    st = h.stats()
-    n = prob.A.n
-    bs = [torch.tensor(P.rhs_uniform(n, (rank * 5 + k) % 997), dtype=torch.float64, device="cuda")
-          for k in range(5)]
-    x = torch.zeros(n, dtype=torch.float64, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    infos = []
-    for k in range(args.warmup):
-        x.zero_()
-        h.solve(bs[k % 5], x)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(dev)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.steps):
-        x.zero_()
-        infos.append(h.solve(bs[k % 5], x))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    el = e0.elapsed_time(e1) / 1e3
-    if dist is not None:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    iters = [i.iters for i in infos]
-    relres = max(i.true_relres for i in infos)
-    value = world * args.steps / el
-    launches = sum(9 + 8 * it for it in iters)
-
-    # end to end through the C ABI with host (page-locked) buffers
-    bh = torch.tensor(P.rhs_uniform(n, rank * 5), dtype=torch.float64).pin_memory()
-    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-    h.solve_host(bh, xh)
-    barrier()
-    torch.cuda.synchronize()
-    te = time.perf_counter()
-    for k in range(args.steps):
-        xh.zero_()
-        h.solve_host(bh, xh)
-    torch.cuda.synchronize()
-    e2e_el = time.perf_counter() - te
-    if dist is not None:
-        t = torch.tensor([e2e_el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_el = float(t.item())
-
-    # per-phase apply times and SpMV (CUDA events on the launching stream)
-    vb = 4 if opts["precision"] == "fp32" else 8
-    rr = bs[0].clone()
-    zz = torch.empty_like(rr)
-    phases = np.zeros(4)
-    reps = 20
-    for _ in range(3):
-        h.apply_timed(rr, zz)
-    for _ in range(reps):
-        phases += np.array(h.apply_timed(rr, zz))
-    phases /= reps
-    ab = apply_bytes(st, vb)
-    # the apply as the solver runs it (branches overlapped), CUDA events
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ea.record(stream)
-    for _ in range(reps):
-        h.apply(rr, zz)
-    eb.record(stream)
-    torch.cuda.synchronize()
-    apply_overlapped_ms = ea.elapsed_time(eb) / reps
-    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(3):
-        h.spmv(rr, zz)
-    es.record(stream)
-    for _ in range(reps):
-        h.spmv(rr, zz)
-    ee.record(stream)
-    torch.cuda.synchronize()
-    spmv_ms = es.elapsed_time(ee) / reps
-    hbm, src = peaks()
-    names = ["local", "phiT", "coarse", "combine"]
-    phase_ms = dict(zip(names, phases.tolist()))
-    dom = max(names, key=lambda k: phase_ms[k])
-    achieved = ab[dom] / (phase_ms[dom] * 1e-3) / 1e9
-    apply_ms = float(phases.sum())
-    apply_gbs = sum(ab.values()) / (apply_ms * 1e-3) / 1e9
-
-    line = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if vb == 4 else "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": args.variant, "n": n, "nnz": st["nnz"],
-                   "subdomains": st["n_sub"], "n0": st["n0"], "overlap": 1, "tol": 1e-8,
-                   "l2": "per-iteration working set ~0.9 GB >> 126 MB L2; no flush",
-                   "parallelism": f"replicas{world}"},
-        "time_to_residual_ms": 1e3 * el / args.steps, "iters": iters, "true_relres_max": relres,
-        "setup_s": setup_s, "setup_phase_s": st["setup_phase_seconds"],
-        "apply_ms": apply_ms, "apply_phase_ms": phase_ms, "apply_gbs": apply_gbs,
-        "apply_overlapped_ms": apply_overlapped_ms,
-        "apply_overlapped_gbs": sum(ab.values()) / (apply_overlapped_ms * 1e-3) / 1e9,
-        "apply_frac_of_measured_hbm": apply_gbs / hbm,
-        "spmv_ms": spmv_ms, "spmv_gbs": spmv_bytes(st) / (spmv_ms * 1e-3) / 1e9,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": src,
-                     "algorithmic_bytes_per_launch": ab[dom]},
-        "e2e": {"value": world * args.steps / e2e_el, "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * n,
-                "d2h_bytes_per_step": 8 * n},
-        "gpu_launches": launches,
-        "clocks": clk,
-    }
-    if not args.no_variants and rank == 0:
-        var = {}
-        for name, vo in VARIANTS.items():
-            if name == args.variant:
-                continue
-            hv = gdsw.Handle(prob.A, prob.part, None, **vo)
-            for k in range(2):
-                x.zero_()
-                hv.solve(bs[0], x)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            inf = []
-            for k in range(3):
-                x.zero_()
-                inf.append(hv.solve(bs[k], x))
-            torch.cuda.synchronize()
-            var[name] = {"ms_per_solve": 1e3 * (time.perf_counter() - t1) / 3, "iters": [i.iters for i in inf],
-                         "true_relres_max": max(i.true_relres for i in inf)}
-            hv.close()
-        line["variants"] = var
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        it_ref = golden_iters(args.variant) or int(np.median(iters))
-        line["cpu_baseline"] = oracle_sample(prob, args.variant, it_ref)
+    if args.config == 4:
+        line = run_batch(args, world, rank, dist, barrier)
+    elif args.config == 5:
+        line = run_serving(args, world, rank, dist, barrier)
+    else:
+        line = run_single(args, world, rank, dist, barrier)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     if dist is not None:
         dist.destroy_process_group()
 

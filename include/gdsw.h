@@ -59,10 +59,16 @@ enum { GDSW_LOCAL_EXACT = 0, /* Cholesky of A_s, applied as its dense inverse   
 /* triangular solves of IC(0)/ILU(0) factors (Sec. V-B2, V-B3) */
 enum { GDSW_TRSV_LEVELSCHED = 0, GDSW_TRSV_JACOBI = 1 };
 /* storage/compute precision of the preconditioner (Sec. V-A2); the Krylov
- * vectors, dot products, residual and the coarse solve stay FP64 */
-enum { GDSW_PREC_FP64 = 0, GDSW_PREC_FP32 = 1 };
+ * vectors, dot products, residual and the coarse solve stay FP64.
+ * FP16: level-scheduled IC(0)/ILU(0) factors stored in half precision and
+ * applied in FP32 (everything else as FP32). */
+enum { GDSW_PREC_FP64 = 0, GDSW_PREC_FP32 = 1, GDSW_PREC_FP16 = 2 };
 enum { GDSW_KRYLOV_PCG = 0, GDSW_KRYLOV_GMRES = 1 };
-enum { GDSW_COARSE_GDSW = 0, GDSW_COARSE_NONE = 1 };
+/* coarse space: GDSW (Eq. 2, one function per interface component and null-space
+ * vector), none (one-level), or reduced GDSW (Sec. III: vertex functions only,
+ * each 1 on its vertex and 1/N_c on the edges and faces whose closure holds N_c
+ * vertices) */
+enum { GDSW_COARSE_GDSW = 0, GDSW_COARSE_NONE = 1, GDSW_COARSE_RGDSW = 2 };
 
 /* Square sparse matrix, CSR, host memory.  rowptr[n+1], colind[nnz] (0-based,
  * strictly increasing within each row, diagonal stored), val[nnz].  The
@@ -100,6 +106,10 @@ typedef struct {
   int32_t flexible;       /* PCG beta (r, z - z_old)/(r_old, z_old): 1 = on,
                              0 = off, -1 = on exactly when precision != FP64 */
   double tol;             /* relative residual target     (1e-8)          */
+  int64_t wait_budget_cycles; /* bound on every device-side wait (the local
+                             solve's waits for its bulk copies), SM clock
+                             cycles; 0 = about one second (2e9).  A wait that
+                             runs out ends the call with GDSW_ERR_TIMEOUT.    */
 } gdsw_options;
 
 typedef struct {
@@ -190,6 +200,30 @@ GDSW_API gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double
                             gdsw_solve_info* info, void* stream);
 
 GDSW_API gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st);
+
+/* Numeric phase again for new matrix values on the same sparsity pattern
+ * (Sec. V-A1: the symbolic phase is kept when only the values change, as in a
+ * time step or a Newton iteration).  `val` (host, read during the call) holds
+ * the nnz values in the CSR order given to gdsw_setup; for a handle from
+ * gdsw_setup_batch, the members' values concatenated in member order.  The
+ * null space and options given at setup are kept.  Local factors, Phi_Gamma,
+ * Phi_I, A0 and A0^-1 are recomputed on the device; on success the handle is
+ * what gdsw_setup with the new values would have built (bitwise), and
+ * gdsw_stats.setup_seconds is the numeric phase alone.  On failure (e.g.
+ * GDSW_ERR_BREAKDOWN for an indefinite new matrix) the handle keeps its
+ * previous state and stays usable.  Synchronises the stream. */
+GDSW_API gdsw_status gdsw_refactor(gdsw_handle h, const double* val, void* stream);
+
+/* Device memory that gdsw_setup with these arguments would use, from the
+ * symbolic phase alone (host work, no device call): *resident = the bytes the
+ * handle keeps (what gdsw_stats.device_bytes reports after setup) and
+ * *setup_scratch = the bytes the numeric setup holds on top of that while it
+ * runs.  Both are upper bounds: the coarse space is sized as if no
+ * null-space column were dropped.  Either output pointer may be NULL.  Meant
+ * for admission control under a device-memory budget. */
+GDSW_API gdsw_status gdsw_bytes_required(const gdsw_csr* A, const gdsw_partition* part, const double* Z,
+                                         int32_t nn, const gdsw_options* opt, int64_t* resident,
+                                         int64_t* setup_scratch);
 
 /* Frees every device allocation of the handle.  NULL is accepted. */
 GDSW_API gdsw_status gdsw_destroy(gdsw_handle h);

@@ -127,6 +127,7 @@ class Decomposition:
     comp_nodes: List[np.ndarray]
     sub_interior_nodes: List[np.ndarray]
     sub_nodes: List[np.ndarray]
+    comp_key: np.ndarray = None     # (ncomp, 3, 2): per axis (on_plane, plane or block index)
 
 
 def decompose(part) -> Decomposition:
@@ -176,8 +177,39 @@ def decompose(part) -> Decomposition:
     bounds = np.searchsorted(node_sub[srt], np.arange(n_sub + 1))
     sub_nodes = [srt[bounds[s]:bounds[s + 1]] for s in range(n_sub)]
     sub_interior = [nodes[~gamma[nodes]] for nodes in sub_nodes]
+    comp_key = np.zeros((len(order), 3, 2), dtype=np.int64)
+    if len(gnodes):
+        first_node = np.array([nodes[0] for nodes in comp_nodes])
+        for a, (bb, pp) in enumerate(((bx, px), (by, py), (bz, pz))):
+            comp_key[:, a, 0] = pp[first_node]
+            comp_key[:, a, 1] = bb[first_node]
     return Decomposition(n_sub, node_sub, gamma, node_comp, comp_type, comp_nodes,
-                         sub_interior, sub_nodes)
+                         sub_interior, sub_nodes, comp_key)
+
+
+def vertex_closure(dec: Decomposition, part) -> List[np.ndarray]:
+    """For every interface component, the vertex components in its closure.
+
+    A vertex lies in the closure of component c when, on every axis, it sits on
+    c's plane if c lies on a plane there, and on one of the two planes bounding
+    c's block otherwise (block b is bounded by planes b-1 and b).
+    """
+    ncut = [len(part.cuts[a]) for a in range(3)]
+    verts = np.nonzero(dec.comp_type == 3)[0]
+    vkey = {tuple(dec.comp_key[v, :, 1]): v for v in verts}
+    out = []
+    for c in range(len(dec.comp_nodes)):
+        if dec.comp_type[c] == 3:
+            out.append(np.array([c]))
+            continue
+        choices = []
+        for a in range(3):
+            on, idx = dec.comp_key[c, a]
+            choices.append([idx] if on else [q for q in (idx - 1, idx) if 0 <= q < ncut[a]])
+        vs = sorted(vkey[(x, y, z)] for x in choices[0] for y in choices[1] for z in choices[2]
+                    if (x, y, z) in vkey)
+        out.append(np.array(vs, dtype=np.int64))
+    return out
 
 
 def node_dofs(nodes: np.ndarray, dpn: int) -> np.ndarray:
@@ -255,13 +287,17 @@ class Coarse:
     comp_cols: List[np.ndarray]  # coarse columns of each component
 
 
-def coarse_space(A, part, dec: Decomposition, Z: np.ndarray) -> Coarse:
+def coarse_space(A, part, dec: Decomposition, Z: np.ndarray, variant: str = "gdsw") -> Coarse:
     """GDSW coarse basis (Eq. 2) and coarse matrix A0 = Phi^T A Phi.
 
-    Phi_Gamma = [R_Gamma_1^T Phi_Gamma_1, ...] with Phi_Gamma_i an orthonormal
-    basis of the null space restricted to component i (D_Gamma_i = I);
-    Phi_I = -A_II^-1 A_IGamma Phi_Gamma, solved exactly per interior block
-    since A_II is block diagonal (Sec. III).
+    variant "gdsw": Phi_Gamma = [R_Gamma_1^T Phi_Gamma_1, ...] with Phi_Gamma_i an
+    orthonormal basis of the null space restricted to component i (D_Gamma_i = I).
+    variant "rgdsw" (reduced: coarse functions for vertices only, Sec. III): the
+    function of vertex v and null-space vector z is z on v and z / N_c on every
+    edge or face c whose closure holds N_c vertices, v among them (a partition of
+    unity on Gamma); each vertex's functions are orthonormalised over their support.
+    Phi_I = -A_II^-1 A_IGamma Phi_Gamma, solved exactly per interior block since
+    A_II is block diagonal (Sec. III).
     """
     n = A.n
     dpn = part.dpn
@@ -269,9 +305,25 @@ def coarse_space(A, part, dec: Decomposition, Z: np.ndarray) -> Coarse:
     rows, cols, vals = [], [], []
     comp_cols = []
     n0 = 0
-    for nodes in dec.comp_nodes:
-        dofs = node_dofs(nodes, dpn)
-        Q = mgs_basis(Z[dofs, :])
+    if variant == "gdsw":
+        supports = [(node_dofs(nodes, dpn), np.ones(len(nodes) * dpn)) for nodes in dec.comp_nodes]
+    elif variant == "rgdsw":
+        closure = vertex_closure(dec, part)
+        owners = {v: [] for v in np.nonzero(dec.comp_type == 3)[0]}
+        for c, vs in enumerate(closure):
+            if len(vs) == 0:
+                raise ValueError("rGDSW needs a vertex in the closure of every interface component")
+            for v in vs:
+                owners[v].append((c, 1.0 / len(vs)))
+        supports = []
+        for v in sorted(owners):
+            dofs = np.concatenate([node_dofs(dec.comp_nodes[c], dpn) for c, _ in owners[v]])
+            w = np.concatenate([np.full(len(dec.comp_nodes[c]) * dpn, wt) for c, wt in owners[v]])
+            supports.append((dofs, w))
+    else:
+        raise ValueError(variant)
+    for dofs, w in supports:
+        Q = mgs_basis(w[:, None] * Z[dofs, :])
         k = Q.shape[1]
         cc = np.arange(n0, n0 + k)
         comp_cols.append(cc)
@@ -283,6 +335,7 @@ def coarse_space(A, part, dec: Decomposition, Z: np.ndarray) -> Coarse:
         return Coarse(0, sp.csr_matrix((n, 0)), np.zeros((0, 0)), comp_cols)
     PhiG = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(n, n0))
+    PhiG.sum_duplicates()
     irows, icols, ivals = [], [], []
     for inodes in dec.sub_interior_nodes:
         I = node_dofs(inodes, dpn)
@@ -474,11 +527,12 @@ class GDSW:
 
     local: EXACT (Cholesky of A_s), IC0 or ILU0 (Chow-Patel sweeps);
     trsv: LEVELSCHED (exact substitution) or JACOBI (fixed sweeps).
-    coarse=False gives the one-level additive Schwarz operator.
+    coarse=False gives the one-level additive Schwarz operator; coarse_variant
+    "rgdsw" the reduced (vertex) coarse space.
     """
 
     def __init__(self, A, part, Z=None, local=EXACT, trsv=LEVELSCHED, sweeps_factor=3,
-                 sweeps_trsv=5, overlap=1, coarse=True):
+                 sweeps_trsv=5, overlap=1, coarse=True, coarse_variant="gdsw"):
         self.A = A
         self.part = part
         self.n = A.n
@@ -490,7 +544,7 @@ class GDSW:
         if Z is None:
             Z = np.ones((A.n, 1))
         self.Asp = _csr(A.n, A.rowptr, A.colind, A.val)
-        self.coarse = coarse_space(A, part, self.dec, Z) if coarse else None
+        self.coarse = coarse_space(A, part, self.dec, Z, coarse_variant) if coarse else None
         if self.coarse is not None and self.coarse.n0:
             self.A0fac = sla.cho_factor(self.coarse.A0, lower=True)
         self.factors = [self._factor(dofs) for dofs in self.omega]

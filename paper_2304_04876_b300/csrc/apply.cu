@@ -15,6 +15,9 @@
 //              the prolongation (Phi y)_g, optionally fusing the PCG dots.
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
+
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -114,19 +117,25 @@ __global__ void __launch_bounds__(256) k_local_tri(const double* __restrict__ r,
 // flight with TMA bulk copies into a ring of stages, each stage tracked by an
 // mbarrier, while all threads compute the current level from shared memory:
 //     v[row] = (v[row] - sum_k val_k v[col_k]) * dinv
-// Every wait is bounded; a wait that runs out sets err[0], waits (bounded)
-// for the copies still in flight, and ends the CTA without writing z_s.
-constexpr long long kWaitLimit = 2000000000LL;   // cycles, about 1 s
+// Every wait is bounded by `wait_cycles`; a wait that runs out sets err[0],
+// waits (bounded again) for the copies still in flight, and ends the CTA
+// without writing z_s.
+
+template <class T, class TS>
+__device__ __forceinline__ T load_as(const TS* p, int i) { return T(p[i]); }
+template <>
+__device__ __forceinline__ float load_as<float, __half>(const __half* p, int i) { return __half2float(p[i]); }
 
 // Row update of one level: TPR threads per row split the row's entries and
 // add their partial sums with shuffles; short rows (TPR = 1) are unrolled.
-template <class T, int TPR>
+// TS is the storage type of the record values (T, or FP16 applied in FP32).
+template <class T, class TS, int TPR>
 __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v) {
   const int4 hdr = *reinterpret_cast<const int4*>(rec);
   const int nr = hdr.x, K = hdr.y;
   const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 16);
-  const T* dinv = reinterpret_cast<const T*>(rec + 16 + ((2 * nr + 15) & ~15));
-  const T* vals = reinterpret_cast<const T*>(rec + hdr.z);
+  const TS* dinv = reinterpret_cast<const TS*>(rec + 16 + ((2 * nr + 15) & ~15));
+  const TS* vals = reinterpret_cast<const TS*>(rec + hdr.z);
   const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + hdr.w);
   if (TPR == 1) {
     for (int t = threadIdx.x; t < nr; t += blockDim.x) {
@@ -138,14 +147,14 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           cidx[k] = k < K ? cols[k * nr + t] : row;
-          a[k] = k < K ? vals[k * nr + t] : T(0);
+          a[k] = k < K ? load_as<T, TS>(vals, k * nr + t) : T(0);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc = fma(-a[k], v[cidx[k]], acc);
       } else {
-        for (int k = 0; k < K; ++k) acc = fma(-vals[k * nr + t], v[cols[k * nr + t]], acc);
+        for (int k = 0; k < K; ++k) acc = fma(-load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], acc);
       }
-      v[row] = acc * dinv[t];
+      v[row] = acc * load_as<T, TS>(dinv, t);
     }
   } else {
     const int sub = threadIdx.x % TPR;
@@ -155,18 +164,18 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v) {
       const int t = round + threadIdx.x / TPR;
       T part = T(0);
       if (t < nr)
-        for (int k = sub; k < K; k += TPR) part = fma(vals[k * nr + t], v[cols[k * nr + t]], part);
+        for (int k = sub; k < K; k += TPR) part = fma(load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], part);
 #pragma unroll
       for (int o = TPR / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, TPR);
       if (t < nr && sub == 0) {
         const int row = lrows[t];
-        v[row] = (v[row] - part) * dinv[t];
+        v[row] = (v[row] - part) * load_as<T, TS>(dinv, t);
       }
     }
   }
 }
 
-template <class T, int S, int TPR>
+template <class T, class TS, int S, int TPR>
 __global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r,
                                                     const int* __restrict__ om_ptr,
                                                     const int* __restrict__ om_dofs,
@@ -175,7 +184,8 @@ __global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r
                                                     const uint32_t* __restrict__ rec_bytes,
                                                     const uint8_t* __restrict__ stream, int stage_bytes,
                                                     T* __restrict__ zloc,
-                                                    const KrylovScalars* __restrict__ ks, int* err) {
+                                                    const KrylovScalars* __restrict__ ks, int* err,
+                                                    long long wait_cycles) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[S];
   if (ks != nullptr && ks->done) return;
@@ -203,13 +213,13 @@ __global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r
     const unsigned parity = (i / S) & 1;
     // each thread waits for the record itself; the one barrier per level
     // below also carries a timed-out wait to every thread
-    const bool ok = mbar_wait_bounded(&bar[st], parity, kWaitLimit);
-    if (ok) level_rows<T, TPR>(stages + size_t(st) * stage_bytes, v);
+    const bool ok = mbar_wait_bounded(&bar[st], parity, wait_cycles);
+    if (ok) level_rows<T, TS, TPR>(stages + size_t(st) * stage_bytes, v);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(err, 1);
         // let the copies already issued land before the CTA's shared memory goes away
-        for (int j = i; j < nrec && j < i + S; ++j) mbar_wait_bounded(&bar[j % S], (j / S) & 1, kWaitLimit);
+        for (int j = i; j < nrec && j < i + S; ++j) mbar_wait_bounded(&bar[j % S], (j / S) & 1, wait_cycles);
       }
       return;
     }
@@ -481,20 +491,41 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
                                             c->ainv_off, zl, ks);
   } else if (c->rec_stages > 0) {
     const size_t shm = size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * sizeof(T);
-#define GDSW_PIPE_LAUNCH(SS, TP)                                                                     \
-  k_local_pipe<T, SS, TP><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, \
-                                                    c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, \
-                                                    ks, c->derr)
     const int key = c->rec_stages * 100 + c->rec_tpr;
-    switch (key) {
-      case 201: GDSW_PIPE_LAUNCH(2, 1); break;
-      case 301: GDSW_PIPE_LAUNCH(3, 1); break;
-      case 401: GDSW_PIPE_LAUNCH(4, 1); break;
-      case 601: GDSW_PIPE_LAUNCH(6, 1); break;
-      case 208: GDSW_PIPE_LAUNCH(2, 8); break;
-      case 308: GDSW_PIPE_LAUNCH(3, 8); break;
-      case 408: GDSW_PIPE_LAUNCH(4, 8); break;
-      default: GDSW_PIPE_LAUNCH(6, 8); break;
+    if (c->fp16) {
+      if constexpr (std::is_same<T, float>::value) {
+#define GDSW_PIPE_LAUNCH(SS, TP)                                                                            \
+  k_local_pipe<T, __half, SS, TP><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr,            \
+                                                            c->rec_off16, c->rec_bytes, c->rec_stream,       \
+                                                            c->rec_stage_bytes, zl, ks, c->derr,             \
+                                                            c->wait_cycles)
+        switch (key) {
+          case 201: GDSW_PIPE_LAUNCH(2, 1); break;
+          case 301: GDSW_PIPE_LAUNCH(3, 1); break;
+          case 401: GDSW_PIPE_LAUNCH(4, 1); break;
+          case 601: GDSW_PIPE_LAUNCH(6, 1); break;
+          case 208: GDSW_PIPE_LAUNCH(2, 8); break;
+          case 308: GDSW_PIPE_LAUNCH(3, 8); break;
+          case 408: GDSW_PIPE_LAUNCH(4, 8); break;
+          default: GDSW_PIPE_LAUNCH(6, 8); break;
+        }
+#undef GDSW_PIPE_LAUNCH
+      }
+    } else {
+#define GDSW_PIPE_LAUNCH(SS, TP)                                                                     \
+  k_local_pipe<T, T, SS, TP><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, \
+                                                       c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, \
+                                                       ks, c->derr, c->wait_cycles)
+      switch (key) {
+        case 201: GDSW_PIPE_LAUNCH(2, 1); break;
+        case 301: GDSW_PIPE_LAUNCH(3, 1); break;
+        case 401: GDSW_PIPE_LAUNCH(4, 1); break;
+        case 601: GDSW_PIPE_LAUNCH(6, 1); break;
+        case 208: GDSW_PIPE_LAUNCH(2, 8); break;
+        case 308: GDSW_PIPE_LAUNCH(3, 8); break;
+        case 408: GDSW_PIPE_LAUNCH(4, 8); break;
+        default: GDSW_PIPE_LAUNCH(6, 8); break;
+      }
     }
 #undef GDSW_PIPE_LAUNCH
   } else {
@@ -613,24 +644,24 @@ gdsw_status apply_configure(Ctx* c) {
   c->rec_tpr = c->rec_max_width > 8 ? 8 : 1;
   if (c->rec_stages > 0) {
     const int shm = int(size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * es);
-#define GDSW_PIPE_ATTR(TT, SS, TP)                                                                     \
-  GDSW_CK(cudaFuncSetAttribute(k_local_pipe<TT, SS, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
-#define GDSW_PIPE_ATTRS(TT) \
-  GDSW_PIPE_ATTR(TT, 2, 1) GDSW_PIPE_ATTR(TT, 3, 1) GDSW_PIPE_ATTR(TT, 4, 1) GDSW_PIPE_ATTR(TT, 6, 1) \
-  GDSW_PIPE_ATTR(TT, 2, 8) GDSW_PIPE_ATTR(TT, 3, 8) GDSW_PIPE_ATTR(TT, 4, 8) GDSW_PIPE_ATTR(TT, 6, 8)
-    if (c->fp32) { GDSW_PIPE_ATTRS(float) } else { GDSW_PIPE_ATTRS(double) }
+#define GDSW_PIPE_ATTR(TT, TS, SS, TP)                                                                     \
+  GDSW_CK(allow_max_dynamic_smem(k_local_pipe<TT, TS, SS, TP>));
+#define GDSW_PIPE_ATTRS(TT, TS) \
+  GDSW_PIPE_ATTR(TT, TS, 2, 1) GDSW_PIPE_ATTR(TT, TS, 3, 1) GDSW_PIPE_ATTR(TT, TS, 4, 1) GDSW_PIPE_ATTR(TT, TS, 6, 1) \
+  GDSW_PIPE_ATTR(TT, TS, 2, 8) GDSW_PIPE_ATTR(TT, TS, 3, 8) GDSW_PIPE_ATTR(TT, TS, 4, 8) GDSW_PIPE_ATTR(TT, TS, 6, 8)
+    if (c->fp16) { GDSW_PIPE_ATTRS(float, __half) }
+    else if (c->fp32) { GDSW_PIPE_ATTRS(float, float) } else { GDSW_PIPE_ATTRS(double, double) }
 #undef GDSW_PIPE_ATTRS
 #undef GDSW_PIPE_ATTR
   }
   if (c->fp32) {
-    GDSW_CK(cudaFuncSetAttribute(k_local_tri<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
-    GDSW_CK(cudaFuncSetAttribute(k_local_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
+    GDSW_CK(allow_max_dynamic_smem(k_local_tri<float>));
+    GDSW_CK(allow_max_dynamic_smem(k_local_dense<float>));
   } else {
-    GDSW_CK(cudaFuncSetAttribute(k_local_tri<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
-    GDSW_CK(cudaFuncSetAttribute(k_local_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_local)));
+    GDSW_CK(allow_max_dynamic_smem(k_local_tri<double>));
+    GDSW_CK(allow_max_dynamic_smem(k_local_dense<double>));
   }
-  GDSW_CK(cudaFuncSetAttribute(k_coarse_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(std::max<size_t>(shm_coarse, 8))));
+  GDSW_CK(allow_max_dynamic_smem(k_coarse_gemv));
   return GDSW_OK;
 }
 

@@ -11,6 +11,11 @@
 
 struct gdsw_ctx {
   gdsw::Ctx c;
+  // kept for gdsw_refactor: the symbolic plan, the CSR pattern and the null space
+  gdsw::Plan plan;
+  std::vector<int> rowptr, colind;
+  std::vector<double> Z;
+  int32_t nn = 0;
 };
 
 namespace gdsw {
@@ -43,8 +48,8 @@ void release(Ctx* c) {
 bool valid_options(const gdsw_options* o) {
   return o->local_solver >= 0 && o->local_solver <= 2 && o->trsv >= 0 && o->trsv <= 1 &&
          o->sweeps_factor >= 0 && o->sweeps_trsv >= 0 && o->overlap >= 0 && o->precision >= 0 &&
-         o->precision <= 1 && o->krylov >= 0 && o->krylov <= 1 && o->restart >= 1 &&
-         o->maxit >= 1 && o->coarse >= 0 && o->coarse <= 1 && o->tol > 0.0;
+         o->precision <= 2 && o->krylov >= 0 && o->krylov <= 1 && o->restart >= 1 &&
+         o->maxit >= 1 && o->coarse >= 0 && o->coarse <= 2 && o->tol > 0.0 && o->wait_budget_cycles >= 0;
 }
 }  // namespace
 
@@ -97,6 +102,7 @@ void gdsw_default_options(gdsw_options* o) {
   o->coarse = GDSW_COARSE_GDSW;
   o->flexible = -1;
   o->tol = 1e-8;
+  o->wait_budget_cycles = 0;
 }
 
 const char* gdsw_status_string(gdsw_status s) {
@@ -121,7 +127,7 @@ namespace {
 
 // Numeric setup, apply/SpMV configuration and Krylov workspace for a plan
 // (one problem, or the merged plan of a batch); the handle on success.
-gdsw_status setup_from_plan(Plan& P, const gdsw_csr* A, const double* Z, int32_t nn,
+gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, int32_t nn,
                             const gdsw_options& o, cudaStream_t s, double t0, double t_sym,
                             gdsw_handle* out) {
   gdsw_ctx* h = new (std::nothrow) gdsw_ctx();
@@ -137,8 +143,10 @@ gdsw_status setup_from_plan(Plan& P, const gdsw_csr* A, const double* Z, int32_t
   c->max_m = P.max_m;
   c->sum_m = P.sum_m;
   c->nprob = P.nprob;
-  c->fp32 = o.precision == GDSW_PREC_FP32;
+  c->fp32 = o.precision == GDSW_PREC_FP32 || o.precision == GDSW_PREC_FP16;
+  c->fp16 = o.precision == GDSW_PREC_FP16;
   c->flexible = o.flexible < 0 ? c->fp32 : (o.flexible != 0);
+  c->wait_cycles = o.wait_budget_cycles > 0 ? o.wait_budget_cycles : kDefaultWaitCycles;
   c->stats.setup_phase_seconds[0] = t_sym;
   gdsw_status st = numeric_setup(c, P, A, Z, nn, s);
   if (st == GDSW_OK) st = c->fp32 ? dalloc(c, reinterpret_cast<float**>(&c->zloc), P.sum_m)
@@ -181,6 +189,16 @@ gdsw_status setup_from_plan(Plan& P, const gdsw_csr* A, const double* Z, int32_t
   return GDSW_OK;
 }
 
+// The handle remembers what gdsw_refactor needs to rerun the numeric phase.
+void keep_for_refactor(gdsw_handle h, Plan&& P, std::vector<int>&& rp, std::vector<int>&& ci, const double* Z,
+                       int32_t nn) {
+  h->plan = std::move(P);
+  h->rowptr = std::move(rp);
+  h->colind = std::move(ci);
+  if (Z && nn > 0) h->Z.assign(Z, Z + int64_t(h->plan.n) * nn);
+  h->nn = Z ? nn : 0;
+}
+
 bool prepare_options(const gdsw_options* opt, gdsw_options* o) {
   if (opt) *o = *opt; else gdsw_default_options(o);
   if (!valid_options(o)) { set_error("invalid options"); return false; }
@@ -202,7 +220,41 @@ gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const doub
   Plan P;
   gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
   if (st != GDSW_OK) return st;
-  return setup_from_plan(P, A, Z, nn, o, static_cast<cudaStream_t>(stream), t0, now_s() - t0, out);
+  st = setup_from_plan(P, A, Z, nn, o, static_cast<cudaStream_t>(stream), t0, now_s() - t0, out);
+  if (st == GDSW_OK)
+    keep_for_refactor(*out, std::move(P), std::vector<int>(A->rowptr, A->rowptr + A->n + 1),
+                      std::vector<int>(A->colind, A->colind + A->rowptr[A->n]), Z, nn);
+  return st;
+}
+
+gdsw_status gdsw_bytes_required(const gdsw_csr* A, const gdsw_partition* part, const double* Z, int32_t nn,
+                                const gdsw_options* opt, int64_t* resident, int64_t* setup_scratch) {
+  gdsw_options o;
+  if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
+  if (nn < 0 || (nn > 0 && !Z)) { set_error("null space: nn=%d with Z=%p", nn, (const void*)Z); return GDSW_ERR_INVALID_ARG; }
+  Plan P;
+  gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
+  if (st != GDSW_OK) return st;
+  int64_t r = 0, sc = 0;
+  st = estimate_footprint(P, o, Z ? nn : 0, &r, &sc);
+  if (st != GDSW_OK) return st;
+  if (resident) *resident = r;
+  if (setup_scratch) *setup_scratch = sc;
+  return GDSW_OK;
+}
+
+gdsw_status gdsw_refactor(gdsw_handle h, const double* val, void* stream) {
+  if (!h || !val) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  const double t0 = now_s();
+  gdsw_csr A{h->plan.n, h->rowptr.data(), h->colind.data(), val};
+  gdsw_handle fresh = nullptr;
+  gdsw_status st = setup_from_plan(h->plan, &A, h->Z.empty() ? nullptr : h->Z.data(), h->nn, h->c.opt,
+                                   static_cast<cudaStream_t>(stream), t0, 0.0, &fresh);
+  if (st != GDSW_OK) return st;           // the handle keeps its previous factors
+  std::swap(h->c, fresh->c);
+  release(&fresh->c);
+  delete fresh;
+  return GDSW_OK;
 }
 
 gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gdsw_partition* parts,
@@ -256,8 +308,9 @@ gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gdsw_partit
   gdsw_status st = merge_plans(plans, &M);
   if (st != GDSW_OK) return st;
   gdsw_csr merged{static_cast<int32_t>(n), rp.data(), ci.data(), va.data()};
-  return setup_from_plan(M, &merged, Zm.data(), nnmax, o, static_cast<cudaStream_t>(stream), t0,
-                         now_s() - t0, out);
+  st = setup_from_plan(M, &merged, Zm.data(), nnmax, o, static_cast<cudaStream_t>(stream), t0, now_s() - t0, out);
+  if (st == GDSW_OK) keep_for_refactor(*out, std::move(M), std::move(rp), std::move(ci), Zm.data(), nnmax);
+  return st;
 }
 
 gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st) {

@@ -7,6 +7,31 @@
 
 namespace gdsw {
 
+// The largest shared memory a block may opt in to on this device.
+inline int max_block_smem_optin() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    v = optin;
+  }
+  return v;
+}
+
+// The launch limit on dynamic shared memory belongs to the kernel, not to a
+// handle, so every opt-in kernel is raised once to the most it can take (the
+// opt-in maximum less its static shared memory) and each launch asks for what
+// it needs: handles with different needs then never conflict.
+template <class K>
+cudaError_t allow_max_dynamic_smem(K* kernel) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              max_block_smem_optin() - static_cast<int>(fa.sharedSizeBytes));
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

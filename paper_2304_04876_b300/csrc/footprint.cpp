@@ -1,0 +1,116 @@
+// Device memory a handle will need, from its symbolic plan alone (no device
+// work): every array the numeric setup keeps, with the sizes the setup gives
+// it, plus the scratch the setup holds on the way.  The coarse space is sized
+// as if every owner kept all of its null-space columns, so the figures are
+// upper bounds (equal when no column is dropped).
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+namespace gdsw {
+
+namespace {
+inline int64_t a16(int64_t x) { return (x + 15) & ~int64_t(15); }
+inline int64_t arr(int64_t count, int64_t elem) { return std::max<int64_t>(count, 1) * elem; }
+}  // namespace
+
+// Bytes of the per-level record stream of both triangles (the layout the
+// numeric setup packs for the pipelined level-scheduled solve).
+int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec) {
+  int64_t total = 0, count = 0;
+  for (int q = 0; q < P.nsub; ++q)
+    for (int side = 0; side < 2; ++side) {
+      const EllPlan& E = side == 0 ? P.L : P.U;
+      if (E.sub_lev.empty()) continue;
+      for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
+        const int64_t nr = E.lev_nr[l], K = E.lev_K[l];
+        total += 16 + a16(2 * nr) + a16(nr * vb) + a16(K * nr * vb) + a16(2 * K * nr);
+        ++count;
+      }
+    }
+  if (nrec) *nrec = count;
+  return total;
+}
+
+gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
+                               int64_t* scratch_peak) {
+  const bool exact = o.local_solver == GDSW_LOCAL_EXACT;
+  const bool low = o.precision != GDSW_PREC_FP64;
+  const int64_t v = low ? 4 : 8;                        // apply precision of Phi, inverses, ELL
+  const int64_t vrec = o.precision == GDSW_PREC_FP16 ? 2 : v;
+  const int64_t n = P.n, nsub = P.nsub, sum_m = P.sum_m, nnz = P.nnz;
+  const int64_t nent = static_cast<int64_t>(P.lm_col.size());
+  int64_t R = 0, S = 0;
+
+  // matrix, overlap, local solution buffer, device error word
+  R += arr(n + 1, 4) + arr(nnz, 4) + arr(nnz, 8) + arr(nsub + 1, 4) + arr(sum_m, 4) + arr(sum_m, v) + 4;
+  // local matrices and fixed-point sweeps (scratch)
+  S += arr(nsub + 1, 4) + arr(sum_m + 1, 4) + 4 * arr(nent, 4) + arr(nent, 2) + arr(sum_m, 8) + 2 * arr(nent, 8);
+  if (!exact) {
+    S += arr(nent, 4) + 3 * arr(nent, 8) + arr(nent, 4);
+    for (const EllPlan* E : {&P.L, &P.U}) {
+      R += arr(static_cast<int64_t>(E->sub_lev.size()), 4) + arr(static_cast<int64_t>(E->lev_nr.size()), 16) +
+           arr(static_cast<int64_t>(E->lrows.size()), 2) + arr(static_cast<int64_t>(E->col.size()), 2) +
+           arr(E->slots, v) + arr(sum_m, v);
+      S += arr(static_cast<int64_t>(E->src.size()), 4) + arr(static_cast<int64_t>(E->dsrc.size()), 4);
+    }
+    int64_t nrec = 0;
+    R += arr(record_stream_bytes(P, vrec, &nrec), 1) + arr(nsub + 1, 4) + 2 * arr(nrec, 4);
+  } else {
+    int64_t dense = 0, band = 0;
+    for (int q = 0; q < P.nsub; ++q) {
+      const int64_t m = P.om_ptr[q + 1] - P.om_ptr[q];
+      dense += m * m;
+      band += m * (int64_t(P.om_bw[q]) + 1);
+    }
+    R += arr(nsub + 1, 8) + arr(dense, v);
+    S += arr(dense, 8) + std::min<int64_t>(band * 8, int64_t(4) << 30) + 4 * arr(nsub + 1, 8);
+  }
+
+  // coarse space
+  const bool coarse = (o.coarse == GDSW_COARSE_GDSW || o.coarse == GDSW_COARSE_RGDSW) && P.ncomp > 0;
+  SupportPlan SP;
+  GDSW_TRY(build_supports(P, &SP));
+  const int nown = static_cast<int>(SP.owners.size());
+  const int zcols = nn > 0 ? nn : 1;
+  std::vector<int> rank(P.ncomp, 0);
+  for (int q = 0; q < nown; ++q)
+    rank[SP.owners[q]] = std::min(zcols, SP.supp_ptr[q + 1] - SP.supp_ptr[q]);
+  CoarsePlan C;
+  GDSW_TRY(build_coarse_plan(P, SP, rank, coarse && nown > 0, &C));
+  auto vb = [](const std::vector<int>& x) { return arr(static_cast<int64_t>(x.size()), 4); };
+  R += vb(C.brow_ptr) + vb(C.brow_dof) + vb(C.bcol_ptr) + vb(C.bcol) +
+       arr(static_cast<int64_t>(C.phi_off.size()), 8) + vb(C.cs_ptr) + vb(C.cs_idx) + vb(C.pull_ptr) +
+       vb(C.pull_pos) + vb(C.pos_blk) + vb(C.chunk_blk) + vb(C.chunk_r0) + vb(C.chunk_r1) + vb(C.chunk_slot) +
+       arr(C.n_slots, 8) + 2 * arr(C.n0, 8);
+  if (coarse && nown > 0) {
+    const int64_t sup = SP.supp_ptr[nown];
+    S += arr(n * zcols, 8) + 4 * arr(sup, 4) + arr(sup, 8) + arr(sup * zcols, 8) + arr(nown, 4) +
+         2 * arr(sup, 4);
+  }
+  if (C.n0 > 0) {
+    int64_t a0 = 0, maxb = 0, band = 0;
+    for (int q = 0; q < P.nprob; ++q) {
+      const int64_t nb = C.prob_c0[q + 1] - C.prob_c0[q];
+      a0 += nb * nb;
+      maxb = std::max(maxb, nb);
+    }
+    for (int q = 0; q < P.nsub; ++q) band += int64_t(P.int_ptr[q + 1] - P.int_ptr[q]) * (int64_t(P.int_bw[q]) + 1);
+    R += arr(C.n0, 4) + arr(P.nprob + 1, 4) + arr(P.nprob + 1, 8) + arr(a0, 8) + arr(C.phi_len, v);
+    S += arr(C.phi_len, 8) + arr(a0, 8) + arr((maxb + 63) / 64 * 64 * maxb, 8) +
+         std::min<int64_t>(band * 8, int64_t(6) << 30) + 8 * arr(nsub + 1, 8) + 6 * arr(n, 4) + 2 * arr(C.n0, 4);
+  }
+
+  // Krylov workspace: six vectors, the reduction buffer, scalars; GMRES basis
+  R += 6 * arr(n, 8) + arr(2 * (nsub + int64_t(P.ncomp)) + 4096, 8) + 256;
+  if (o.krylov == GDSW_KRYLOV_GMRES)
+    R += (2 * int64_t(o.restart) + 1) * arr(n, 8) + arr(o.restart + 2, 8) + (int64_t(o.restart) + 2) * 10000;
+  if (P.nprob > 1) R += 4 * arr(n / 4096 + 2 * P.nprob + 1, 4) + arr(P.nprob, 256) + arr(4 * (n / 4096 + P.nprob) + 64, 8);
+  *resident = R;
+  *scratch_peak = S;
+  return GDSW_OK;
+}
+
+}  // namespace gdsw

@@ -85,6 +85,11 @@ struct Plan {
   // scatter lists: per dof, the positions in the concatenated local vectors,
   // ascending subdomain order
   std::vector<int> pull_dof_ptr, pull_dof_pos;
+  // coarse-space owners (Sec. III): the components whose coarse columns appear
+  // on component c, with the weight of that component in their functions.
+  // GDSW: c itself, weight 1; reduced GDSW: the vertices in c's closure, 1/N_c.
+  std::vector<int> own_ptr, own_comp;
+  std::vector<double> own_w;
   // independent problems of a batch (one problem unless merged)
   int nprob = 1;
   std::vector<int> prob_dof_ptr;          // nprob+1: unknowns of each problem
@@ -92,10 +97,21 @@ struct Plan {
 };
 
 // Coarse-space layout once the rank of every component is known.
+// Support of each coarse-space owner: the interface rows its functions cover
+// (owner o: entries supp_ptr[o] .. supp_ptr[o+1]).
+struct SupportPlan {
+  std::vector<int> owners;                // owner components, ascending
+  std::vector<int> supp_ptr;              // per owner
+  std::vector<int> supp_dof, supp_comp, supp_row;
+  std::vector<double> supp_w;
+};
+gdsw_status build_supports(const Plan& P, SupportPlan* S);
+
 struct CoarsePlan {
   int n0 = 0;
-  std::vector<int> comp_c0;               // first coarse column of each component
-  std::vector<int> comp_k;
+  std::vector<int> comp_c0;               // first coarse column of each owner component
+  std::vector<int> comp_k;                // columns of each owner component (0 for others)
+  std::vector<int> supp_colpos;           // per support entry: first column of its owner in the block
   // Phi blocks: b < nsub is the interior of subdomain b, b >= nsub component b-nsub.
   int nblk = 0;
   std::vector<int> brow_ptr, brow_dof;    // every dof exactly once
@@ -114,10 +130,16 @@ struct CoarsePlan {
   std::vector<int> prob_c0;               // nprob+1
 };
 
+// Device bytes of a handle built from this plan and of the setup's scratch
+// (upper bounds; host work only).
+gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
+                               int64_t* scratch_peak);
+int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec);
+
 gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
                        bool need_levels, Plan* P);
-gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, bool coarse,
-                              CoarsePlan* C);
+gdsw_status build_coarse_plan(const Plan& P, const SupportPlan& S, const std::vector<int>& comp_rank,
+                              bool coarse, CoarsePlan* C);
 // Block-diagonal union of independent problems: every index is offset so the
 // merged plan describes all problems as one (their subdomains, components and
 // levels side by side).
@@ -167,6 +189,9 @@ struct BatchControl {
   int pad;
 };
 
+// Default bound on a device-side wait: about one second at the B300 SM clock.
+constexpr long long kDefaultWaitCycles = 2000000000LL;
+
 struct Ctx {
   int device = 0;
   gdsw_options opt;
@@ -174,7 +199,8 @@ struct Ctx {
   int64_t nnz = 0;
   int max_m = 0;
   int64_t sum_m = 0;
-  bool fp32 = false;
+  bool fp32 = false;                // preconditioner computes in FP32
+  bool fp16 = false;                // level records store the factors in FP16
   bool flexible = false;            // PCG uses the flexible beta (needs (r, z_old))
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -204,6 +230,7 @@ struct Ctx {
   int rec_max_width = 0;             // widest level (off-diagonal entries per row)
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int* derr = nullptr;               // device error flags (bounded waits that ran out)
+  long long wait_cycles = 0;         // bound on each device-side wait, SM clock cycles
   // exact local solver: dense inverses
   void* ainv = nullptr;
   int64_t* ainv_off = nullptr;

@@ -293,8 +293,7 @@ gdsw_status spmv_configure(Ctx* c, const int* rowptr) {
   switch (R) {
 #define GDSW_SPMV_CFG(RR)                                                                         \
   case RR:                                                                                         \
-    GDSW_CK(cudaFuncSetAttribute(k_spmv_stream<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 int(std::max<size_t>(shm, 16))));                                 \
+    GDSW_CK(allow_max_dynamic_smem(k_spmv_stream<RR>));                                 \
     GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_stream<RR>, RR, shm));  \
     break;
     GDSW_SPMV_CFG(256)

@@ -12,6 +12,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -162,6 +164,11 @@ __global__ void k_pack_dinv(int64_t nrows, const int* __restrict__ dsrc, const d
 // level-sliced ELL goes to element valpos[q] of the stream, the inverse
 // diagonal of level-ordered row i to element dinvpos[i].
 template <class T>
+__device__ __forceinline__ T from_double(double v) { return T(v); }
+template <>
+__device__ __forceinline__ __half from_double<__half>(double v) { return __double2half(v); }
+
+template <class T>
 __global__ void k_fill_records(int64_t nslots, const int* __restrict__ src,
                                const uint32_t* __restrict__ valpos, int64_t nrows,
                                const int* __restrict__ dsrc, const uint32_t* __restrict__ dinvpos,
@@ -169,11 +176,11 @@ __global__ void k_fill_records(int64_t nslots, const int* __restrict__ src,
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nslots; q += stride) {
     const int e = src[q];
-    stream[valpos[q]] = e >= 0 ? T(G[e]) : T(0);
+    stream[valpos[q]] = from_double<T>(e >= 0 ? G[e] : 0.0);
   }
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nrows; q += stride) {
     const int e = dsrc[q];
-    stream[dinvpos[q]] = e >= 0 ? T(1.0 / G[e]) : T(1);
+    stream[dinvpos[q]] = from_double<T>(e >= 0 ? 1.0 / G[e] : 1.0);
   }
 }
 
@@ -181,24 +188,25 @@ __global__ void k_fill_records(int64_t nslots, const int* __restrict__ src,
 // Phi_Gamma: orthonormal basis of the null space on each component
 // ---------------------------------------------------------------------------
 
-// One CTA per component: modified Gram-Schmidt over the nn columns of
-// R_Gamma_i Z in order, dropping a column whose remaining norm is below
-// kDropTol of its original norm.  Q[(comp_ptr[c])*nn + k*R + r] holds kept
-// column k; rank[c] the number kept.
-__global__ void k_mgs(const int* __restrict__ comp_ptr, const int* __restrict__ comp_dofs,
-                      const double* __restrict__ Z, int n, int nn, double* __restrict__ Q,
-                      int* __restrict__ rank) {
+// One CTA per coarse-space owner: modified Gram-Schmidt over the nn columns of
+// the null space restricted to the owner's support and scaled by the support
+// weights, in column order, dropping a column whose remaining norm is below
+// kDropTol of its original norm.  Kept column k of owner o sits at
+// Q[supp_ptr[o]*nn + k*R + r]; rank[o] counts the kept columns.
+__global__ void k_mgs(const int* __restrict__ supp_ptr, const int* __restrict__ supp_dof,
+                      const double* __restrict__ supp_w, const double* __restrict__ Z, int n, int nn,
+                      double* __restrict__ Q, int* __restrict__ rank) {
   __shared__ double sh[32];
   __shared__ double bc;
-  const int c = blockIdx.x;
-  const int r0 = comp_ptr[c], R = comp_ptr[c + 1] - r0;
+  const int o = blockIdx.x;
+  const int r0 = supp_ptr[o], R = supp_ptr[o + 1] - r0;
   double* Qc = Q + int64_t(r0) * nn;
   int kept = 0;
   for (int col = 0; col < nn; ++col) {
     double* v = Qc + int64_t(kept) * R;
     double loc = 0.0;
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
-      const double z = Z[int64_t(col) * n + comp_dofs[r0 + r]];
+      const double z = Z[int64_t(col) * n + supp_dof[r0 + r]] * supp_w[r0 + r];
       v[r] = z;
       loc += z * z;
     }
@@ -232,19 +240,27 @@ __global__ void k_mgs(const int* __restrict__ comp_ptr, const int* __restrict__ 
     __syncthreads();
     ++kept;
   }
-  if (threadIdx.x == 0) rank[c] = kept;
+  if (threadIdx.x == 0) rank[o] = kept;
 }
 
-// Copy the kept MGS columns into the component blocks of Phi (column-major).
-__global__ void k_copy_phig(int nsub, const int* __restrict__ comp_ptr, int nn,
-                            const double* __restrict__ Q, const int* __restrict__ bcol_ptr,
+// Scatter each owner's kept columns into the interface-component blocks of Phi
+// (column-major): support entry e lies in component supp_comp[e], row
+// supp_row[e], and the owner's columns start at supp_colpos[e] in that block.
+__global__ void k_copy_phig(int nsub, const int* __restrict__ supp_ptr,
+                            const int* __restrict__ supp_comp, const int* __restrict__ supp_row,
+                            const int* __restrict__ supp_colpos, const int* __restrict__ owner_k,
+                            int nn, const double* __restrict__ Q, const int* __restrict__ brow_ptr,
                             const int64_t* __restrict__ phi_off, double* __restrict__ phi) {
-  const int c = blockIdx.x;
-  const int b = nsub + c;
-  const int R = comp_ptr[c + 1] - comp_ptr[c];
-  const int k = bcol_ptr[b + 1] - bcol_ptr[b];
-  const double* Qc = Q + int64_t(comp_ptr[c]) * nn;
-  for (int q = threadIdx.x; q < R * k; q += blockDim.x) phi[phi_off[b] + q] = Qc[q];
+  const int o = blockIdx.x;
+  const int r0 = supp_ptr[o], R = supp_ptr[o + 1] - r0;
+  const int k = owner_k[o];
+  const double* Qc = Q + int64_t(r0) * nn;
+  for (int q = threadIdx.x; q < R * k; q += blockDim.x) {
+    const int t = q / R, e = q - t * R;
+    const int b = nsub + supp_comp[r0 + e];
+    const int nr = brow_ptr[b + 1] - brow_ptr[b];
+    phi[phi_off[b] + int64_t(supp_colpos[r0 + e] + t) * nr + supp_row[r0 + e]] = Qc[q];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -344,7 +360,6 @@ __global__ void k_assemble_interior(int s0, const int* __restrict__ rowptr,
                                     const int* __restrict__ dof_comp,
                                     const int* __restrict__ dof_comprow,
                                     const int* __restrict__ dof_introw,
-                                    const int* __restrict__ comp_c0, const int* __restrict__ comp_k,
                                     int nsub, const int* __restrict__ brow_ptr,
                                     const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
                                     const int64_t* __restrict__ phi_off, double* __restrict__ phi,
@@ -367,17 +382,20 @@ __global__ void k_assemble_interior(int s0, const int* __restrict__ rowptr,
         if (j <= i) B[int64_t(j) * W + (i - j)] = val[e];
         continue;
       }
-      const int kc = comp_k[comp];
-      if (kc == 0) continue;
       const int b = nsub + comp;
+      const int kc = bcol_ptr[b + 1] - bcol_ptr[b];
+      if (kc == 0) continue;
       const int Rc = brow_ptr[b + 1] - brow_ptr[b];
       const double* Pc = phi + phi_off[b];
       const int rr = dof_comprow[c];
-      // the component's columns are contiguous in the block's sorted list
-      const int l0 = comp_c0[comp];
-      int lo = 0, hi = ncols;
-      while (lo < hi) { const int mid = (lo + hi) >> 1; if (cols[mid] < l0) lo = mid + 1; else hi = mid; }
-      for (int t = 0; t < kc; ++t) Ph[int64_t(lo + t) * ns + i] -= val[e] * Pc[int64_t(t) * Rc + rr];
+      const int* ccols = bcol + bcol_ptr[b];
+      for (int t = 0; t < kc; ++t) {
+        // position of the component's column in the interior block's sorted list
+        const int l = ccols[t];
+        int lo = 0, hi = ncols;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (cols[mid] < l) lo = mid + 1; else hi = mid; }
+        Ph[int64_t(lo) * ns + i] -= val[e] * Pc[int64_t(t) * Rc + rr];
+      }
     }
   }
 }
@@ -415,33 +433,34 @@ __global__ void k_convert(int64_t len, const double* __restrict__ a, T* __restri
 // ---------------------------------------------------------------------------
 // Coarse matrix A0 = Phi^T A Phi = Phi_Gamma^T (A Phi)_Gamma  ((A Phi)_I = 0 by Eq. 2)
 // ---------------------------------------------------------------------------
-// One CTA (one warp) per coarse row k, owned by one interface component:
-//   A0[k, :] = sum_{g in Gamma_i} Phi[g, k] sum_j A[g, j] Phi[j, :]
+// One CTA (one warp) per coarse row k, whose function lives on its owner's support:
+//   A0[k, :] = sum_{g in supp(k)} Phi[g, k] sum_j A[g, j] Phi[j, :]
 // accumulated in shared memory in a fixed order (deterministic).
-__global__ void k_coarse_rows(int nsub, const int* __restrict__ coarse_comp,
-                              const int* __restrict__ comp_c0, const int* __restrict__ coarse_prob,
+__global__ void k_coarse_rows(int nsub, const int* __restrict__ coarse_owner,
+                              const int* __restrict__ owner_c0, const int* __restrict__ coarse_prob,
                               const int* __restrict__ prob_c0, const int64_t* __restrict__ a0_off,
                               const int* __restrict__ rowptr,
                               const int* __restrict__ colind, const double* __restrict__ val,
-                              const int* __restrict__ brow_ptr, const int* __restrict__ brow_dof,
+                              const int* __restrict__ brow_ptr, const int* __restrict__ supp_ptr,
+                              const int* __restrict__ supp_dof, const int* __restrict__ supp_comp,
+                              const int* __restrict__ supp_row, const int* __restrict__ supp_colpos,
                               const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
                               const int64_t* __restrict__ phi_off, const double* __restrict__ phi,
                               const int* __restrict__ dof_blk, const int* __restrict__ dof_blkrow,
                               double* __restrict__ A0) {
   extern __shared__ double acc[];
   const int k = blockIdx.x;
-  const int comp = coarse_comp[k];
-  const int b = nsub + comp;
-  const int t = k - comp_c0[comp];
+  const int o = coarse_owner[k];                  // owner index (support range)
+  const int t = k - owner_c0[o];
   const int pr = coarse_prob[k];
   const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;   // this problem's coarse block
-  const int R = brow_ptr[b + 1] - brow_ptr[b];
-  const double* Pk = phi + phi_off[b] + int64_t(t) * R;
   for (int l = threadIdx.x; l < np; l += blockDim.x) acc[l] = 0.0;
   __syncwarp();
-  for (int r = 0; r < R; ++r) {
-    const int g = brow_dof[brow_ptr[b] + r];
-    const double pk = Pk[r];
+  for (int sidx = supp_ptr[o]; sidx < supp_ptr[o + 1]; ++sidx) {
+    const int g = supp_dof[sidx];
+    const int b = nsub + supp_comp[sidx];
+    const int R = brow_ptr[b + 1] - brow_ptr[b];
+    const double pk = phi[phi_off[b] + int64_t(supp_colpos[sidx] + t) * R + supp_row[sidx]];
     for (int e = rowptr[g]; e < rowptr[g + 1]; ++e) {
       const int j = colind[e];
       const double coef = pk * val[e];
@@ -671,8 +690,7 @@ gdsw_status band_batches(int np, const std::vector<int>& bn, const std::vector<i
     const size_t shm = std::max<size_t>(sizeof(double), size_t(maxw) * sizeof(double));
     if (shm > 200 * 1024) { set_error("band width %d too large for the banded Cholesky", maxw); return GDSW_ERR_UNSUPPORTED; }
     if (shm > 48 * 1024)
-      GDSW_CK(cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(shm)));
+      GDSW_CK(allow_max_dynamic_smem(k_band_cholesky));
     k_band_cholesky<<<p1 - p0, 512, shm, s>>>(band, d_boff, d_bn, d_bw, p0, d_err);
     GDSW_CK(cudaGetLastError());
     GDSW_TRY(after(p0, p1, band, d_boff, d_bn, d_bw));
@@ -799,7 +817,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     //   diagonal | width*rows x T values | width*rows x uint16 columns,
     // every section padded to 16 bytes so a record is one bulk copy.
     {
-      const size_t vb = c->fp32 ? sizeof(float) : sizeof(double);
+      const size_t vb = c->fp16 ? sizeof(__half) : c->fp32 ? sizeof(float) : sizeof(double);
       auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
       std::vector<int> rec_ptr(nsub + 1, 0);
       std::vector<uint32_t> rec_off16, rec_bytes;
@@ -872,7 +890,10 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         GDSW_TRY(sc.put(&d_dp, side == 0 ? dinvposL : dinvposU, s));
         GDSW_TRY(sc.put(&d_src, E.src, s));
         GDSW_TRY(sc.put(&d_dsrc, E.dsrc, s));
-        if (c->fp32)
+        if (c->fp16)
+          k_fill_records<__half><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                       reinterpret_cast<__half*>(d_stream));
+        else if (c->fp32)
           k_fill_records<float><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
                                                                       reinterpret_cast<float*>(d_stream));
         else
@@ -885,32 +906,48 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   }
   c->stats.setup_phase_seconds[1] = now_s() - t0;
 
-  // ---- Phi_Gamma: MGS per component ----
+  // ---- Phi_Gamma: MGS per coarse-space owner over its weighted support ----
+  // (GDSW: every interface component owns itself with weight 1; rGDSW: the
+  // vertices own the edges and faces of their closure with weight 1/N_c.)
   t0 = now_s();
   std::vector<int> comp_rank(P.ncomp, 0);
   double* d_Q = nullptr;
-  int* d_comp_ptr = nullptr;
-  int* d_comp_dofs = nullptr;
   int zcols = nn;
-  const bool coarse = o.coarse == GDSW_COARSE_GDSW && P.ncomp > 0;
-  if (coarse) {
+  const bool coarse = (o.coarse == GDSW_COARSE_GDSW || o.coarse == GDSW_COARSE_RGDSW) && P.ncomp > 0;
+  SupportPlan S;
+  GDSW_TRY(build_supports(P, &S));
+  const int nown = static_cast<int>(S.owners.size());
+  int *d_supp_ptr = nullptr, *d_supp_dof = nullptr, *d_supp_comp = nullptr, *d_supp_row = nullptr;
+  if (coarse && nown > 0) {
     double* d_Z;
     std::vector<double> zh;
     if (Z == nullptr || nn == 0) { zh.assign(P.n, 1.0); zcols = 1; }
     else zh.assign(Z, Z + int64_t(P.n) * nn);
     GDSW_TRY(sc.put(&d_Z, zh, s));
-    GDSW_TRY(sc.put(&d_comp_ptr, P.comp_ptr, s));
-    GDSW_TRY(sc.put(&d_comp_dofs, P.comp_dofs, s));
-    GDSW_TRY(sc.get(&d_Q, size_t(P.comp_ptr[P.ncomp]) * zcols));
+    double* d_supp_w;
+    GDSW_TRY(sc.put(&d_supp_ptr, S.supp_ptr, s));
+    GDSW_TRY(sc.put(&d_supp_dof, S.supp_dof, s));
+    GDSW_TRY(sc.put(&d_supp_comp, S.supp_comp, s));
+    GDSW_TRY(sc.put(&d_supp_row, S.supp_row, s));
+    GDSW_TRY(sc.put(&d_supp_w, S.supp_w, s));
+    GDSW_TRY(sc.get(&d_Q, size_t(S.supp_ptr[nown]) * zcols));
     int* d_rank;
-    GDSW_TRY(sc.get(&d_rank, P.ncomp));
-    k_mgs<<<P.ncomp, 128, 0, s>>>(d_comp_ptr, d_comp_dofs, d_Z, P.n, zcols, d_Q, d_rank);
+    GDSW_TRY(sc.get(&d_rank, nown));
+    k_mgs<<<nown, 128, 0, s>>>(d_supp_ptr, d_supp_dof, d_supp_w, d_Z, P.n, zcols, d_Q, d_rank);
     GDSW_CK(cudaGetLastError());
-    GDSW_CK(cudaMemcpyAsync(comp_rank.data(), d_rank, P.ncomp * sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int> orank(nown);
+    GDSW_CK(cudaMemcpyAsync(orank.data(), d_rank, nown * sizeof(int), cudaMemcpyDeviceToHost, s));
     GDSW_CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < nown; ++q) comp_rank[S.owners[q]] = orank[q];
   }
   CoarsePlan C;
-  GDSW_TRY(build_coarse_plan(P, comp_rank, coarse, &C));
+  GDSW_TRY(build_coarse_plan(P, S, comp_rank, coarse && nown > 0, &C));
+  // per owner: first coarse column and column count
+  std::vector<int> owner_c0(std::max(nown, 1), 0), owner_k(std::max(nown, 1), 0);
+  for (int q = 0; q < nown; ++q) {
+    owner_c0[q] = C.comp_c0[S.owners[q]];
+    owner_k[q] = C.comp_k[S.owners[q]];
+  }
   c->n0 = C.n0;
   c->nblk = C.nblk;
   GDSW_TRY(upload(c, &c->brow_ptr, C.brow_ptr, s));
@@ -939,8 +976,11 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   if (C.n0 > 0) {
     GDSW_TRY(sc.get(&phi64, C.phi_len));
     GDSW_CK(cudaMemsetAsync(phi64, 0, C.phi_len * sizeof(double), s));
-    int* d_bcol_ptr = c->bcol_ptr;
-    k_copy_phig<<<P.ncomp, 256, 0, s>>>(nsub, d_comp_ptr, zcols, d_Q, d_bcol_ptr, c->phi_off, phi64);
+    int *d_colpos, *d_owner_k;
+    GDSW_TRY(sc.put(&d_colpos, C.supp_colpos, s));
+    GDSW_TRY(sc.put(&d_owner_k, owner_k, s));
+    k_copy_phig<<<nown, 256, 0, s>>>(nsub, d_supp_ptr, d_supp_comp, d_supp_row, d_colpos, d_owner_k, zcols, d_Q,
+                                     c->brow_ptr, c->phi_off, phi64);
     GDSW_CK(cudaGetLastError());
   }
   c->stats.setup_phase_seconds[2] = now_s() - t0;
@@ -948,14 +988,12 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   // ---- Phi_I = -A_II^-1 A_IGamma Phi_Gamma (Eq. 2), banded Cholesky per interior ----
   t0 = now_s();
   if (C.n0 > 0) {
-    int *d_int_ptr, *d_int_dofs, *d_dof_comp, *d_dof_comprow, *d_dof_introw, *d_c0, *d_ck;
+    int *d_int_ptr, *d_int_dofs, *d_dof_comp, *d_dof_comprow, *d_dof_introw;
     GDSW_TRY(sc.put(&d_int_ptr, P.int_ptr, s));
     GDSW_TRY(sc.put(&d_int_dofs, P.int_dofs, s));
     GDSW_TRY(sc.put(&d_dof_comp, P.dof_comp, s));
     GDSW_TRY(sc.put(&d_dof_comprow, P.dof_comprow, s));
     GDSW_TRY(sc.put(&d_dof_introw, P.dof_introw, s));
-    GDSW_TRY(sc.put(&d_c0, C.comp_c0, s));
-    GDSW_TRY(sc.put(&d_ck, C.comp_k, s));
     std::vector<int> bn(nsub), bwv(nsub), rk(nsub);
     std::vector<int64_t> roff(nsub);
     for (int q = 0; q < nsub; ++q) {
@@ -973,7 +1011,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     auto fill = [&](int p0, int p1, double* band, int64_t* d_boff) -> gdsw_status {
       k_assemble_interior<<<p1 - p0, 256, 0, s>>>(
           p0, c->rowptr, c->colind, c->val, d_int_ptr, d_int_dofs, d_dof_comp, d_dof_comprow,
-          d_dof_introw, d_c0, d_ck, nsub, c->brow_ptr, c->bcol_ptr, c->bcol, c->phi_off, phi64,
+          d_dof_introw, nsub, c->brow_ptr, c->bcol_ptr, c->bcol, c->phi_off, phi64,
           band, d_boff, d_bw_full);
       GDSW_CK(cudaGetLastError());
       return GDSW_OK;
@@ -993,11 +1031,11 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   if (C.n0 > 0) {
     const int n0 = C.n0;
     const int np_ = P.nprob;
-    std::vector<int> coarse_comp(n0), coarse_prob(n0);
-    for (int q = 0; q < P.ncomp; ++q)
-      for (int t = 0; t < C.comp_k[q]; ++t) {
-        coarse_comp[C.comp_c0[q] + t] = q;
-        coarse_prob[C.comp_c0[q] + t] = P.comp_prob[q];
+    std::vector<int> coarse_owner(n0), coarse_prob(n0);
+    for (int q = 0; q < nown; ++q)
+      for (int t = 0; t < owner_k[q]; ++t) {
+        coarse_owner[owner_c0[q] + t] = q;
+        coarse_prob[owner_c0[q] + t] = P.comp_prob[S.owners[q]];
       }
     std::vector<int64_t> a0_off(np_ + 1, 0);
     int maxb = 0;
@@ -1006,9 +1044,10 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       a0_off[q + 1] = a0_off[q] + nb * nb;
       maxb = std::max<int>(maxb, static_cast<int>(nb));
     }
-    int *d_cc, *d_c0b, *d_dof_blk, *d_dof_blkrow;
-    GDSW_TRY(sc.put(&d_cc, coarse_comp, s));
-    GDSW_TRY(sc.put(&d_c0b, C.comp_c0, s));
+    int *d_cc, *d_c0b, *d_dof_blk, *d_dof_blkrow, *d_colpos2;
+    GDSW_TRY(sc.put(&d_cc, coarse_owner, s));
+    GDSW_TRY(sc.put(&d_c0b, owner_c0, s));
+    GDSW_TRY(sc.put(&d_colpos2, C.supp_colpos, s));
     GDSW_TRY(sc.put(&d_dof_blk, C.dof_blk, s));
     GDSW_TRY(sc.put(&d_dof_blkrow, C.dof_blkrow, s));
     GDSW_TRY(upload(c, &c->coarse_prob, coarse_prob, s));
@@ -1020,10 +1059,11 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     const size_t shm = size_t(maxb) * sizeof(double);
     if (shm > 227 * 1024) { set_error("coarse dimension %d too large for the A0 kernel", maxb); return GDSW_ERR_UNSUPPORTED; }
     if (shm > 48 * 1024)
-      GDSW_CK(cudaFuncSetAttribute(k_coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
+      GDSW_CK(allow_max_dynamic_smem(k_coarse_rows));
     k_coarse_rows<<<n0, 32, std::max<size_t>(shm, 8), s>>>(nsub, d_cc, d_c0b, c->coarse_prob, c->prob_c0,
                                                           c->a0_off, c->rowptr, c->colind, c->val,
-                                                          c->brow_ptr, c->brow_dof, c->bcol_ptr, c->bcol,
+                                                          c->brow_ptr, d_supp_ptr, d_supp_dof, d_supp_comp,
+                                                          d_supp_row, d_colpos2, c->bcol_ptr, c->bcol,
                                                           c->phi_off, phi64, d_dof_blk, d_dof_blkrow, d_A0);
     GDSW_CK(cudaGetLastError());
     c->stats.setup_phase_seconds[4] = now_s() - t0;

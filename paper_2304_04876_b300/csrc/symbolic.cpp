@@ -178,6 +178,7 @@ gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw
   P->node_comp.assign(nn, -1);
   const int64_t nkeys = int64_t(8) * P->nb[0] * P->nb[1] * P->nb[2];
   std::vector<int> key2comp(nkeys, -1);
+  std::vector<int> comp_key;   // per component and axis: 2*index + on_plane
   for (int k = 0; k < dims[2]; ++k)
     for (int j = 0; j < dims[1]; ++j)
       for (int i = 0; i < dims[0]; ++i) {
@@ -192,6 +193,9 @@ gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw
         if (c < 0) {
           c = key2comp[key] = P->ncomp++;
           P->comp_type.push_back(np);
+          comp_key.push_back(2 * blk[0][i] + onp[0][i]);
+          comp_key.push_back(2 * blk[1][j] + onp[1][j]);
+          comp_key.push_back(2 * blk[2][k] + onp[2][k]);
         }
         P->node_comp[u] = c;
       }
@@ -227,6 +231,50 @@ gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw
           P->int_dofs[ipos[s]++] = g;
         }
       }
+    }
+  }
+
+  // ---- coarse-space owners ----
+  // A vertex lies in the closure of component c when, on every axis, it is on
+  // c's plane if c lies on a plane there, and on one of the two planes bounding
+  // c's block otherwise (block b lies between planes b-1 and b).
+  P->own_ptr.assign(ncomp + 1, 0);
+  P->own_comp.clear();
+  P->own_w.clear();
+  {
+    std::vector<int> vert_of(int64_t(part->ncut[0]) * part->ncut[1] * part->ncut[2] + 1, -1);
+    for (int c = 0; c < ncomp; ++c)
+      if (P->comp_type[c] == 3)
+        vert_of[(comp_key[3 * c] / 2) + int64_t(part->ncut[0]) * ((comp_key[3 * c + 1] / 2) +
+                                                                 int64_t(part->ncut[1]) * (comp_key[3 * c + 2] / 2))] = c;
+    const bool reduced = opt->coarse == GDSW_COARSE_RGDSW;
+    for (int c = 0; c < ncomp; ++c) {
+      if (!reduced || P->comp_type[c] == 3) {
+        P->own_comp.push_back(c);
+        P->own_w.push_back(1.0);
+      } else {
+        std::vector<int> ch[3];
+        for (int a = 0; a < 3; ++a) {
+          const int key = comp_key[3 * c + a], idx = key / 2;
+          if (key & 1) ch[a].push_back(idx);
+          else for (int q : {idx - 1, idx}) if (q >= 0 && q < part->ncut[a]) ch[a].push_back(q);
+        }
+        std::vector<int> vs;
+        for (int x : ch[0]) for (int y : ch[1]) for (int z : ch[2]) {
+          const int v = vert_of[x + int64_t(part->ncut[0]) * (y + int64_t(part->ncut[1]) * z)];
+          if (v >= 0) vs.push_back(v);
+        }
+        if (vs.empty()) {
+          set_error("reduced GDSW needs a vertex in the closure of every interface component");
+          return GDSW_ERR_UNSUPPORTED;
+        }
+        std::sort(vs.begin(), vs.end());
+        for (int v : vs) {
+          P->own_comp.push_back(v);
+          P->own_w.push_back(1.0 / vs.size());
+        }
+      }
+      P->own_ptr[c + 1] = static_cast<int>(P->own_comp.size());
     }
   }
 
@@ -480,6 +528,13 @@ gdsw_status merge_plans(std::vector<Plan>& parts, Plan* M) {
     for (int g = 1; g <= p.n; ++g) o.pull_dof_ptr.push_back(p.pull_dof_ptr[g] + o.pull_dof_ptr[doff]);
     add(o.pull_dof_pos, p.pull_dof_pos, moff, false);
     o.comp_prob.insert(o.comp_prob.end(), p.ncomp, pi);
+    if (o.own_ptr.empty()) o.own_ptr.push_back(0);
+    {
+      const int oo = static_cast<int>(o.own_comp.size());
+      for (size_t q = 1; q < p.own_ptr.size(); ++q) o.own_ptr.push_back(p.own_ptr[q] + oo);
+    }
+    add(o.own_comp, p.own_comp, coff, false);
+    o.own_w.insert(o.own_w.end(), p.own_w.begin(), p.own_w.end());
     o.max_m = std::max(o.max_m, p.max_m);
     // pointer arrays from sizes
     for (int q = 0; q < p.nsub; ++q) {
@@ -500,13 +555,38 @@ gdsw_status merge_plans(std::vector<Plan>& parts, Plan* M) {
   return GDSW_OK;
 }
 
-gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, bool coarse,
-                              CoarsePlan* C) {
+gdsw_status build_supports(const Plan& P, SupportPlan* S) {
+  const int ncomp = P.ncomp;
+  std::vector<std::vector<std::pair<int, double>>> sup(ncomp);   // owner -> (component, weight)
+  for (int c = 0; c < ncomp; ++c)
+    for (int q = P.own_ptr[c]; q < P.own_ptr[c + 1]; ++q) sup[P.own_comp[q]].push_back({c, P.own_w[q]});
+  S->owners.clear();
+  S->supp_ptr.assign(1, 0);
+  S->supp_dof.clear(); S->supp_comp.clear(); S->supp_row.clear(); S->supp_w.clear();
+  for (int o = 0; o < ncomp; ++o) {
+    if (sup[o].empty()) continue;
+    S->owners.push_back(o);
+    for (const auto& cw : sup[o]) {
+      const int c = cw.first;
+      for (int q = P.comp_ptr[c]; q < P.comp_ptr[c + 1]; ++q) {
+        S->supp_dof.push_back(P.comp_dofs[q]);
+        S->supp_comp.push_back(c);
+        S->supp_row.push_back(q - P.comp_ptr[c]);
+        S->supp_w.push_back(cw.second);
+      }
+    }
+    S->supp_ptr.push_back(static_cast<int>(S->supp_dof.size()));
+  }
+  return GDSW_OK;
+}
+
+gdsw_status build_coarse_plan(const Plan& P, const SupportPlan& S, const std::vector<int>& comp_rank,
+                              bool coarse, CoarsePlan* C) {
   const int nsub = P.nsub, ncomp = P.ncomp, n = P.n;
   C->comp_c0.assign(ncomp, 0);
   C->comp_k.assign(ncomp, 0);
   int n0 = 0;
-  for (int c = 0; c < ncomp; ++c) {
+  for (int c = 0; c < ncomp; ++c) {      // owners in component order (problem-major)
     C->comp_c0[c] = n0;
     C->comp_k[c] = coarse ? comp_rank[c] : 0;
     n0 += C->comp_k[c];
@@ -515,6 +595,24 @@ gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, 
   C->prob_c0.assign(P.nprob + 1, 0);
   for (int c = 0; c < ncomp; ++c) C->prob_c0[P.comp_prob[c] + 1] += C->comp_k[c];
   for (int q = 0; q < P.nprob; ++q) C->prob_c0[q + 1] += C->prob_c0[q];
+  // columns of each component block: its owners' columns, owners ascending
+  std::vector<std::vector<int>> comp_cols(ncomp);
+  for (int c = 0; c < ncomp; ++c)
+    for (int q = P.own_ptr[c]; q < P.own_ptr[c + 1]; ++q) {
+      const int o = P.own_comp[q];
+      for (int t = 0; t < C->comp_k[o]; ++t) comp_cols[c].push_back(C->comp_c0[o] + t);
+    }
+  // first column of owner o inside component c's block, for every support entry
+  C->supp_colpos.assign(S.supp_dof.size(), 0);
+  for (size_t oi = 0; oi < S.owners.size(); ++oi) {
+    const int o = S.owners[oi];
+    for (int e = S.supp_ptr[oi]; e < S.supp_ptr[oi + 1]; ++e) {
+      const int c = S.supp_comp[e];
+      int pos = 0;
+      for (int q = P.own_ptr[c]; q < P.own_ptr[c + 1] && P.own_comp[q] != o; ++q) pos += C->comp_k[P.own_comp[q]];
+      C->supp_colpos[e] = pos;
+    }
+  }
   C->nblk = nsub + ncomp;
   const int nblk = C->nblk;
   C->brow_ptr.assign(nblk + 1, 0);
@@ -527,13 +625,16 @@ gdsw_status build_coarse_plan(const Plan& P, const std::vector<int>& comp_rank, 
     if (b < nsub) {
       C->brow_dof.insert(C->brow_dof.end(), P.int_dofs.begin() + P.int_ptr[b],
                          P.int_dofs.begin() + P.int_ptr[b + 1]);
-      for (int c : P.int_adj[b])
-        for (int t = 0; t < C->comp_k[c]; ++t) C->bcol.push_back(C->comp_c0[c] + t);
+      std::vector<int> cols;
+      for (int c : P.int_adj[b]) cols.insert(cols.end(), comp_cols[c].begin(), comp_cols[c].end());
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      C->bcol.insert(C->bcol.end(), cols.begin(), cols.end());
     } else {
       const int c = b - nsub;
       C->brow_dof.insert(C->brow_dof.end(), P.comp_dofs.begin() + P.comp_ptr[c],
                          P.comp_dofs.begin() + P.comp_ptr[c + 1]);
-      for (int t = 0; t < C->comp_k[c]; ++t) C->bcol.push_back(C->comp_c0[c] + t);
+      C->bcol.insert(C->bcol.end(), comp_cols[c].begin(), comp_cols[c].end());
     }
     C->brow_ptr[b + 1] = static_cast<int>(C->brow_dof.size());
     C->bcol_ptr[b + 1] = static_cast<int>(C->bcol.size());

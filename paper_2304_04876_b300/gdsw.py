@@ -19,9 +19,9 @@ OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TI
     ERR_UNSUPPORTED = range(8)
 LOCAL = {"exact": 0, "ic0": 1, "ilu0": 2}
 TRSV = {"levelsched": 0, "jacobi": 1}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2}
 KRYLOV = {"pcg": 0, "gmres": 1}
-COARSE = {"gdsw": 0, "none": 1}
+COARSE = {"gdsw": 0, "none": 1, "rgdsw": 2}
 
 
 class CSRStruct(C.Structure):
@@ -37,7 +37,8 @@ class Options(C.Structure):
     _fields_ = [("local_solver", C.c_int32), ("trsv", C.c_int32), ("sweeps_factor", C.c_int32),
                 ("sweeps_trsv", C.c_int32), ("overlap", C.c_int32), ("precision", C.c_int32),
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32),
-                ("coarse", C.c_int32), ("flexible", C.c_int32), ("tol", C.c_double)]
+                ("coarse", C.c_int32), ("flexible", C.c_int32), ("tol", C.c_double),
+                ("wait_budget_cycles", C.c_int64)]
 
 
 class SolveInfo(C.Structure):
@@ -80,6 +81,9 @@ SIGNATURES = {
     "gdsw_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
     "gdsw_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "gdsw_destroy": (C.c_int, [C.c_void_p]),
+    "gdsw_refactor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gdsw_bytes_required": (C.c_int, [C.POINTER(CSRStruct), C.POINTER(PartitionStruct), C.c_void_p, C.c_int32,
+                                      C.POINTER(Options), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "gdsw_spmv_dot_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_status_string": (C.c_char_p, [C.c_int]),
@@ -148,24 +152,12 @@ class Handle:
         if _batch is not None:
             self._init_batch(_batch, stream, options)
             return
-        rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
-        colind = np.ascontiguousarray(A.colind, dtype=np.int32)
-        val = np.ascontiguousarray(A.val, dtype=np.float64)
-        csr = CSRStruct(int(A.n), rowptr.ctypes.data, colind.ctypes.data, val.ctypes.data)
-        cuts = [np.ascontiguousarray(c, dtype=np.int32) for c in part.cuts]
-        ps = PartitionStruct(int(part.nx), int(part.ny), int(part.nz), int(part.dpn))
-        for a in range(3):
-            ps.ncut[a] = len(cuts[a])
-            ps.cut[a] = cuts[a].ctypes.data if len(cuts[a]) else None
-        if Z is None:
-            zp, nn = None, 0
-        else:
-            Zc = np.asfortranarray(np.asarray(Z, dtype=np.float64).reshape(A.n, -1))
-            zp, nn = Zc.ctypes.data, Zc.shape[1]
+        csr, ps, zp, nn, keep = _marshal(A, part, Z)
         self.options = make_options(**options)
         h = C.c_void_p()
         _check(lib.gdsw_setup(C.byref(csr), C.byref(ps), zp, nn, C.byref(self.options),
                               _stream(stream) if stream is not False else None, C.byref(h)), "gdsw_setup")
+        del keep                      # the library copied the matrix, partition and null space
         self._h = h
         self.n = int(A.n)
 
@@ -253,6 +245,11 @@ class Handle:
             _check(st, "gdsw_solve_host")
         return info
 
+    def refactor(self, val: np.ndarray, stream=None):
+        """New matrix values on the setup's pattern (host float64, CSR order): numeric phase only."""
+        v = np.ascontiguousarray(val, dtype=np.float64)
+        _check(load().gdsw_refactor(self._handle(), v.ctypes.data, _stream(stream)), "gdsw_refactor")
+
     def stats(self) -> dict:
         s = Stats()
         _check(load().gdsw_get_stats(self._handle(), C.byref(s)), "gdsw_get_stats")
@@ -268,6 +265,39 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+def _marshal(A, part, Z):
+    """C structs for a CSR matrix, its partition and null space; the last item
+    keeps the numpy buffers alive while the structs are in use."""
+    rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    colind = np.ascontiguousarray(A.colind, dtype=np.int32)
+    val = np.ascontiguousarray(A.val, dtype=np.float64)
+    csr = CSRStruct(int(A.n), rowptr.ctypes.data, colind.ctypes.data, val.ctypes.data)
+    cuts = [np.ascontiguousarray(c, dtype=np.int32) for c in part.cuts]
+    ps = PartitionStruct(int(part.nx), int(part.ny), int(part.nz), int(part.dpn))
+    for a in range(3):
+        ps.ncut[a] = len(cuts[a])
+        ps.cut[a] = cuts[a].ctypes.data if len(cuts[a]) else None
+    keep = [rowptr, colind, val] + cuts
+    if Z is None:
+        zp, nn = None, 0
+    else:
+        Zc = np.asfortranarray(np.asarray(Z, dtype=np.float64).reshape(A.n, -1))
+        keep.append(Zc)
+        zp, nn = Zc.ctypes.data, Zc.shape[1]
+    return csr, ps, zp, nn, keep
+
+
+def bytes_required(A, part, Z: Optional[np.ndarray] = None, **options):
+    """(resident, setup_scratch) device bytes of gdsw_setup on these arguments (host work only)."""
+    csr, ps, zp, nn, keep = _marshal(A, part, Z)
+    o = make_options(**options)
+    res, scr = C.c_int64(), C.c_int64()
+    _check(load().gdsw_bytes_required(C.byref(csr), C.byref(ps), zp, nn, C.byref(o), C.byref(res), C.byref(scr)),
+           "gdsw_bytes_required")
+    del keep
+    return int(res.value), int(scr.value)
 
 
 def _host_ptr(a) -> int:

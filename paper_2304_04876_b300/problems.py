@@ -221,42 +221,31 @@ def elasticity_q1(ne: int, E: float = 1.0, nu: float = 0.3,
             off = (d[0] + 1) + 3 * ((d[1] + 1) + 3 * (d[2] + 1))
             blocks[ua, off] += Ke[3 * a:3 * a + 3, 3 * b:3 * b + 3]
     # free-node numbering
-    I, J, K = np.meshgrid(np.arange(nn1), np.arange(nn1), np.arange(nn1), indexing="ij")
-    full_id = (I + nn1 * (J + nn1 * K))
     nx, ny, nz = ne, nn1, nn1
-    free_of_full = -np.ones(nfull, dtype=np.int64)
-    free_mask = I >= 1
-    free_of_full[full_id[free_mask]] = ((I - 1) + nx * (J + ny * K))[free_mask]
     nfree = nx * ny * nz
-    # rows of free nodes, neighbours sorted by offset (dz, dy, dx) => ascending id
     fr = np.arange(nfree)
     fi, fj, fk = fr % nx + 1, (fr // nx) % ny, fr // (nx * ny)
     ufull = fi + nn1 * (fj + nn1 * fk)
-    rows, cols, vals = [], [], []
-    for dz in (-1, 0, 1):
-        for dy in (-1, 0, 1):
-            for dx in (-1, 0, 1):
-                off = (dx + 1) + 3 * ((dy + 1) + 3 * (dz + 1))
-                vi, vj, vk = fi + dx, fj + dy, fk + dz
-                ok = (vi >= 1) & (vi <= ne) & (vj >= 0) & (vj <= ne) & (vk >= 0) & (vk <= ne)
-                u = fr[ok]
-                v = free_of_full[(vi + nn1 * (vj + nn1 * vk))[ok]]
-                blk = blocks[ufull[ok], off]            # (m, 3, 3)
-                for p in range(3):
-                    for q in range(3):
-                        rows.append(3 * u + p)
-                        cols.append(3 * v + q)
-                        vals.append(blk[:, p, q])
-    rows = np.concatenate(rows)
-    cols = np.concatenate(cols)
-    vals = np.concatenate(vals)
+    # neighbour offsets in (dz, dy, dx) order give ascending neighbour ids, so the
+    # rows come out sorted: row (u, p) lists, per valid offset, the 3 dofs q of v
+    offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    valid = np.empty((nfree, 27), dtype=bool)
+    vid = np.empty((nfree, 27), dtype=np.int64)
+    for t, (dx, dy, dz) in enumerate(offs):
+        vi, vj, vk = fi + dx, fj + dy, fk + dz
+        valid[:, t] = (vi >= 1) & (vi <= ne) & (vj >= 0) & (vj <= ne) & (vk >= 0) & (vk <= ne)
+        vid[:, t] = (vi - 1) + nx * (vj + ny * vk)
+    off_idx = np.array([(dx + 1) + 3 * ((dy + 1) + 3 * (dz + 1)) for dx, dy, dz in offs])
+    blk = blocks[ufull][:, off_idx]                      # (nfree, 27, 3, 3) in offset order
+    del blocks
+    vals4 = np.transpose(blk, (0, 2, 1, 3))             # (u, p, offset, q)
+    cols4 = 3 * vid[:, None, :, None] + np.arange(3)[None, None, None, :]
+    mask4 = np.broadcast_to(valid[:, None, :, None], vals4.shape)
+    vals = vals4[mask4]
+    cols = np.broadcast_to(cols4, vals4.shape)[mask4]
     n = 3 * nfree
-    # keep explicit zeros structurally: build the pattern with coo -> csr without pruning
-    order = np.lexsort((cols, rows))
-    rows, cols, vals = rows[order], cols[order], vals[order]
-    rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(rowptr, rows + 1, 1)
-    rowptr = np.cumsum(rowptr)
+    per_row = np.repeat(3 * valid.sum(axis=1), 3)
+    rowptr = np.concatenate([[0], np.cumsum(per_row)])
     A = CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals.astype(np.float64))
     # consistent load of a uniform body force: h^3/8 per element corner
     load = np.zeros((nfull, 3))
@@ -321,6 +310,27 @@ def diffusion_batch(count: int = 256, seed: int = 0, nmin: int = 16, nmax: int =
         part = Partition(n, n, n, 1, [list(cuts), list(cuts), list(cuts)])
         b = rng.uniform(-1.0, 1.0, A.n)
         out.append(Problem(f"diffusion_{p}_n{n}_s{s}", A, part, np.ones((A.n, 1)), b))
+    return out
+
+
+def serving_pool(count: int = 8, seed: int = 0, dofs_min: int = 32 ** 3, dofs_max: int = 160 ** 3,
+                 poisson_sub: int = 16, elasticity_sub: int = 12) -> List[Problem]:
+    """Half Poisson 7-point, half Q1 elasticity, total unknowns log-uniform in
+    [dofs_min, dofs_max]: Poisson edge cbrt(N) with subdomains of poisson_sub nodes
+    per axis, elasticity element edge cbrt(N/3) - 1 with subdomains of
+    elasticity_sub elements per axis."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = float(np.exp(rng.uniform(np.log(dofs_min), np.log(dofs_max))))
+        if i % 2 == 0:
+            n = max(4, int(round(N ** (1.0 / 3.0))))
+            prob = poisson_problem(n, min(poisson_sub, n), seed=seed * 1000 + i)
+        else:
+            ne = max(2, int(round((N / 3.0) ** (1.0 / 3.0) - 1)))
+            prob = elasticity_problem(ne, min(elasticity_sub, ne))
+        prob.name = f"{prob.name}_pool{i}"
+        out.append(prob)
     return out
 
 

@@ -13,7 +13,7 @@ def oracle_for(prob, local="ic0", trsv="levelsched", sweeps_factor=3, sweeps_trs
                coarse="gdsw"):
     return O.GDSW(prob.A, prob.part, prob.Z, local=LOCAL[local], trsv=TRSV[trsv],
                   sweeps_factor=sweeps_factor, sweeps_trsv=sweeps_trsv, overlap=overlap,
-                  coarse=(coarse == "gdsw"))
+                  coarse=(coarse != "none"), coarse_variant=("rgdsw" if coarse == "rgdsw" else "gdsw"))
 
 
 def gpu_handle(prob, **opts):

@@ -38,7 +38,7 @@ def test_default_options_and_status_strings(lib):
     o = G.default_options()
     assert (o.local_solver, o.trsv, o.sweeps_factor, o.sweeps_trsv, o.overlap) == (1, 0, 3, 5, 1)
     assert (o.precision, o.krylov, o.restart, o.maxit, o.coarse, o.flexible) == (0, 0, 30, 2000, 0, -1)
-    assert o.tol == 1e-8
+    assert o.tol == 1e-8 and o.wait_budget_cycles == 0
     for s in range(8):
         assert lib.gdsw_status_string(s)
     assert lib.gdsw_status_string(99) == b"unknown status"
@@ -91,9 +91,9 @@ def test_structs_match_header(lib):
     text = open(HEADER).read()
     body = text[text.index("typedef struct {\n  int32_t local_solver"):]
     body = body[:body.index("} gdsw_options;")]
-    fields = re.findall(r"(?:int32_t|double)\s+(\w+);", body)
+    fields = re.findall(r"(?:int32_t|int64_t|double)\s+(\w+);", body)
     assert fields == [f for f, _ in G.Options._fields_]
-    assert C.sizeof(G.Options) == 11 * 4 + 4 + 8
+    assert C.sizeof(G.Options) == 11 * 4 + 4 + 8 + 8
     assert C.sizeof(G.Stats) == 19 * 8 + 9 * 8
 
 
@@ -106,3 +106,35 @@ def test_batch_rejects_bad_members_on_host(lib):
     with pytest.raises(G.GdswError) as ex:      # GMRES is not batched
         G.Handle.batch([(a.A, a.part, None)], stream=False, krylov="gmres")
     assert ex.value.status == G.ERR_UNSUPPORTED
+
+
+def test_refactor_rejects_null_arguments(lib):
+    v = np.zeros(4)
+    assert lib.gdsw_refactor(None, v.ctypes.data, None) == G.ERR_INVALID_ARG
+
+
+def test_bytes_required_from_the_symbolic_phase(lib):
+    """The footprint estimate needs no device: it grows with the problem, counts the
+    matrix and Krylov vectors at least, and follows the storage precision."""
+    small, big = P.poisson_problem(12, 4), P.poisson_problem(24, 4)
+    r_s, s_s = G.bytes_required(small.A, small.part)
+    r_b, _ = G.bytes_required(big.A, big.part)
+    assert 0 < r_s < r_b and s_s > 0
+    A = small.A
+    assert r_s >= 12 * len(A.colind) + 6 * 8 * A.n
+    r32, _ = G.bytes_required(small.A, small.part, precision="fp32")
+    r16, _ = G.bytes_required(small.A, small.part, precision="fp16")
+    assert r16 < r32 < r_s
+    # no coarse space: less than with one
+    r1, _ = G.bytes_required(small.A, small.part, coarse="none")
+    assert r1 < r_s
+    # rGDSW keeps one function per vertex: a smaller A0 than GDSW
+    e = P.elasticity_problem(6, 2)
+    rg, _ = G.bytes_required(e.A, e.part, e.Z, local_solver="ilu0")
+    rr, _ = G.bytes_required(e.A, e.part, e.Z, local_solver="ilu0", coarse="rgdsw")
+    assert rr < rg
+    # GMRES(30) adds 61 basis vectors of n doubles
+    rgm, _ = G.bytes_required(e.A, e.part, e.Z, local_solver="ilu0", krylov="gmres")
+    assert rgm - rg >= 61 * 8 * e.A.n
+    with pytest.raises(G.GdswError):
+        G.bytes_required(small.A, P.Partition(12, 12, 11, 1, small.part.cuts))

@@ -49,6 +49,11 @@ APPLY_CASES = [
     ("single_subdomain", lambda: P.poisson_problem(6, 6), dict(local="exact")),
     ("overlap2", lambda: P.poisson_problem(12, 4), dict(local="ic0", overlap=2)),
     ("sweeps7", lambda: P.poisson_problem(12, 4), dict(local="ic0", trsv="jacobi", sweeps_factor=7, sweeps_trsv=2)),
+    ("rgdsw_poisson12_exact", lambda: P.poisson_problem(12, 4), dict(local="exact", coarse="rgdsw")),
+    ("rgdsw_ragged13_ic0", _ragged, dict(local="ic0", coarse="rgdsw")),
+    ("rgdsw_diffusion10_ic0", _diffusion, dict(local="ic0", coarse="rgdsw")),
+    ("rgdsw_elast6_ilu0", lambda: P.elasticity_problem(6, 2), dict(local="ilu0", coarse="rgdsw")),
+    ("rgdsw_two_blocks", lambda: P.poisson_problem(8, 4), dict(local="exact", coarse="rgdsw")),
 ]
 
 
@@ -101,6 +106,8 @@ PCG_CASES = [
     ("ragged13_ilu0", _ragged, dict(local="ilu0")),
     ("diffusion10_ic0", _diffusion, dict(local="ic0")),
     ("elast6_exact", lambda: P.elasticity_problem(6, 2), dict(local="exact")),
+    ("rgdsw_poisson12_ic0", lambda: P.poisson_problem(12, 4), dict(local="ic0", coarse="rgdsw")),
+    ("rgdsw_elast6_exact", lambda: P.elasticity_problem(6, 2), dict(local="exact", coarse="rgdsw")),
 ]
 
 
@@ -183,3 +190,101 @@ def test_host_made_faults():
     b[3] = np.nan
     x, info = gpu_solve(h, b, raise_on_nonconvergence=False)
     assert not info.converged
+
+
+@pytest.mark.parametrize("make,opts", [
+    (lambda: P.poisson_problem(12, 4), dict(local_solver="ic0")),
+    (lambda: P.elasticity_problem(6, 2), dict(local_solver="ilu0", krylov="gmres", restart=30)),
+], ids=["poisson12_ic0", "elast6_ilu0_gmres"])
+def test_fp16_factor_storage(make, opts):
+    """Factors stored in FP16 and applied in FP32: the apply stays within FP16's
+    rounding of the FP64 one and the FP64 Krylov solve still reaches 1e-8."""
+    prob = make()
+    local = opts["local_solver"]
+    M = oracle_for(prob, local=local)
+    h16 = gpu_handle(prob, precision="fp16", **opts)
+    h64 = gpu_handle(prob, **opts)
+    r = np.random.default_rng(0).uniform(-1, 1, prob.A.n)
+    assert relerr(gpu_apply(h16, r), M.apply(r)) <= 5e-3
+    _, i64 = gpu_solve(h64, prob.b)
+    x, i16 = gpu_solve(h16, prob.b)
+    assert i16.converged and i16.true_relres <= 1e-8
+    assert i16.iters <= i64.iters + 5
+
+
+def test_handles_with_different_shared_memory_needs_interleave():
+    """Kernel launch limits are per kernel, not per handle: a handle created later with
+    smaller needs must not break an earlier one with larger needs."""
+    big = P.poisson_problem(20, 20)            # one subdomain of 8000 unknowns
+    small = P.poisson_problem(8, 4)
+    Mb = oracle_for(big, local="ic0")
+    hb = gpu_handle(big, local_solver="ic0")
+    hs = gpu_handle(small, local_solver="ic0")
+    r = np.random.default_rng(1).uniform(-1, 1, big.A.n)
+    assert relerr(gpu_apply(hb, r), Mb.apply(r)) <= 1e-10
+    hs2 = gpu_handle(small, local_solver="ic0", precision="fp32")
+    assert relerr(gpu_apply(hb, r), Mb.apply(r)) <= 1e-10
+    for h in (hb, hs, hs2):
+        h.close()
+
+
+def _diffusion_k(seed):
+    k = 10 ** np.random.default_rng(seed).uniform(-2, 2, (10, 10, 10))
+    A = P.diffusion7(k)
+    cuts = P.uniform_cuts(10, 4)
+    part = P.Partition(10, 10, 10, 1, [cuts, cuts, cuts])
+    return P.Problem("diff10", A, part, np.ones((A.n, 1)), P.rhs_uniform(A.n, 1))
+
+
+@pytest.mark.parametrize("opts", [dict(local_solver="ic0"), dict(local_solver="exact", coarse="rgdsw"),
+                                  dict(local_solver="ilu0", precision="fp32")])
+def test_refactor_equals_fresh_setup(opts):
+    """New values on the same pattern: the numeric phase alone gives what a fresh
+    setup gives, bit for bit; a matrix that breaks the factorization leaves the
+    handle as it was."""
+    p1, p2 = _diffusion_k(7), _diffusion_k(8)
+    assert np.array_equal(p1.A.colind, p2.A.colind) and np.array_equal(p1.A.rowptr, p2.A.rowptr)
+    h = gpu_handle(p1, **opts)
+    r = np.random.default_rng(3).uniform(-1, 1, p1.A.n)
+    z1 = gpu_apply(h, r)
+    h.refactor(p2.A.val)
+    fresh = gpu_handle(p2, **opts)
+    z2 = gpu_apply(h, r)
+    assert np.array_equal(z2, gpu_apply(fresh, r))
+    assert h.stats()["n0"] == fresh.stats()["n0"]
+    if opts.get("precision", "fp64") == "fp64":
+        local = {"local_solver": "local"}
+        M = oracle_for(p2, **{local.get(k, k): v for k, v in opts.items()})
+        assert relerr(z2, M.apply(r)) <= TOL_FP64
+    x, info = gpu_solve(h, p2.b)
+    assert info.converged and info.true_relres <= 1e-8
+    # an indefinite matrix (negated) fails in the numeric phase; the handle keeps the p2 factors
+    from paper_2304_04876_b300 import gdsw as G
+    with pytest.raises(G.GdswError):
+        h.refactor(-p2.A.val)
+    assert np.array_equal(gpu_apply(h, r), z2)
+    assert not np.array_equal(z1, z2)
+    h.close()
+    fresh.close()
+
+
+@pytest.mark.parametrize("make,opts", [
+    (lambda: P.config_problem(1), dict(local_solver="exact")),
+    (lambda: P.poisson_problem(12, 4), dict(local_solver="ic0")),
+    (lambda: P.poisson_problem(12, 4), dict(local_solver="ic0", precision="fp16", trsv="jacobi")),
+    (lambda: P.elasticity_problem(6, 2), dict(local_solver="ilu0", krylov="gmres")),
+    (lambda: P.elasticity_problem(6, 2), dict(local_solver="ilu0", coarse="rgdsw", precision="fp32")),
+])
+def test_bytes_required_bounds_the_handle(make, opts):
+    """The host-only footprint estimate is an upper bound of what setup allocates,
+    and a tight one (no null-space column is dropped for these problems except
+    the elasticity edges, rank 5 of 6)."""
+    from paper_2304_04876_b300 import gdsw as G
+    prob = make()
+    Z = None if prob.Z is None or prob.Z.shape[1] == 1 and np.all(prob.Z == 1) else prob.Z
+    resident, scratch = G.bytes_required(prob.A, prob.part, Z, **opts)
+    h = gpu_handle(prob, **opts)
+    held = h.stats()["device_bytes"]
+    h.close()
+    assert held <= resident <= 1.15 * held + (1 << 20), (held, resident)
+    assert scratch > 0

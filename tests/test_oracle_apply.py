@@ -107,3 +107,20 @@ def test_ic0_apply_matches_factor_definition():
     r = np.random.default_rng(4).standard_normal(len(s))
     ref = s * np.linalg.solve(L.T, np.linalg.solve(L, s * r))
     assert np.allclose(M.local_solve(2, r), ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("name,make", [("poisson12_s4", lambda: P.poisson_problem(12, 4)),
+                                       ("elasticity6_s2", lambda: P.elasticity_problem(6, 2))])
+def test_rgdsw_apply_equals_brute_force_and_converges(name, make):
+    prob = make()
+    M = O.GDSW(prob.A, prob.part, prob.Z, local=O.EXACT, coarse_variant="rgdsw")
+    Ad = prob.A.to_scipy().toarray()
+    Mb = _brute_force_M(M, Ad)
+    R = np.random.default_rng(0).standard_normal((prob.A.n, 2))
+    Z = np.column_stack([M.apply(R[:, j]) for j in range(2)])
+    assert np.abs(Z - Mb @ R).max() <= 1e-12 * np.abs(Mb @ R).max()
+    assert np.linalg.eigvalsh(0.5 * (Mb + Mb.T)).min() > 0
+    x, info = O.pcg(M.spmv, M.apply, prob.b)
+    assert info.converged
+    Mg = O.GDSW(prob.A, prob.part, prob.Z, local=O.EXACT)
+    assert M.n0 < Mg.n0

@@ -118,3 +118,68 @@ def test_edges_vertices_do_not_extend_for_7pt():
     for t, cc in zip(dec.comp_type, cs.comp_cols):
         nz = PhiI[:, cc].nnz
         assert (nz > 0) == (t == 1)
+
+
+def test_rgdsw_vertex_closure_and_sizes():
+    """Reduced GDSW: one coarse function per vertex and null-space vector; every edge
+    of a 3^3 decomposition has 2 vertices in its closure and every interior face 4,
+    faces and edges touching the outer boundary fewer."""
+    prob = P.poisson_problem(12, 4)
+    dec = O.decompose(prob.part)
+    clo = O.vertex_closure(dec, prob.part)
+    counts = {1: [], 2: []}
+    for c, vs in enumerate(clo):
+        if dec.comp_type[c] in counts:
+            counts[int(dec.comp_type[c])].append(len(vs))
+    # 2 planes per axis: vertices 8; faces have 1, 2 or 4 vertices, edges 1 or 2
+    assert int((dec.comp_type == 3).sum()) == 8
+    assert set(counts[1]) <= {1, 2, 4} and 4 in counts[1]
+    assert set(counts[2]) <= {1, 2} and 2 in counts[2]
+    cs = O.coarse_space(prob.A, prob.part, dec, prob.Z, "rgdsw")
+    assert cs.n0 == 8
+    # closed form: the central face of the 3^3 split touches the 4 vertices of its plane
+    for c, vs in enumerate(clo):
+        if dec.comp_type[c] == 1 and len(vs) == 4:
+            xs = set(int(k) for k in dec.comp_key[vs][:, :, 1].ravel())
+            assert xs <= {0, 1}
+
+
+def test_rgdsw_partition_of_unity_and_extension():
+    prob = P.poisson_problem(12, 4)
+    dec = O.decompose(prob.part)
+    cs = O.coarse_space(prob.A, prob.part, dec, prob.Z, "rgdsw")
+    G = np.nonzero(dec.node_gamma)[0]
+    # weights: the norm of each vertex's unnormalised function (sum of its squared weights)
+    clo = O.vertex_closure(dec, prob.part)
+    verts = sorted(np.nonzero(dec.comp_type == 3)[0])
+    wsq = {v: 0.0 for v in verts}
+    for c, vs in enumerate(clo):
+        for v in vs:
+            wsq[v] += len(dec.comp_nodes[c]) / len(vs) ** 2
+    w = np.array([np.sqrt(wsq[v]) for v in verts])
+    u = cs.Phi @ w
+    assert np.allclose(u[G], 1.0, atol=1e-13)
+    A = prob.A.to_scipy()
+    I = O.node_dofs(np.concatenate(dec.sub_interior_nodes), 1)
+    AP = (A @ cs.Phi).toarray()
+    assert np.abs(AP[I]).max() <= 1e-12 * np.abs(AP).max()
+    assert np.allclose(u[dec.sub_interior_nodes[13]], 1.0, atol=1e-12)   # floating block
+
+
+def test_rgdsw_rigid_body_modes():
+    """Elasticity: six functions per vertex (rotations are independent on the support),
+    and every rigid-body mode reproduced on subdomains away from the clamp."""
+    prob = P.elasticity_problem(6, 2)
+    dec = O.decompose(prob.part)
+    cs = O.coarse_space(prob.A, prob.part, dec, prob.Z, "rgdsw")
+    assert cs.n0 == 6 * int((dec.comp_type == 3).sum())
+    A = prob.A.to_scipy()
+    G = O.node_dofs(np.nonzero(dec.node_gamma)[0], 3)
+    PhiG = cs.Phi[G].toarray()
+    C, *_ = np.linalg.lstsq(PhiG, prob.Z[G], rcond=None)
+    assert np.linalg.norm(PhiG @ C - prob.Z[G]) < 1e-11 * np.linalg.norm(prob.Z[G])
+    PZ = cs.Phi @ C
+    for inodes in dec.sub_interior_nodes:
+        I = O.node_dofs(inodes, 3)
+        if np.abs(A[I] @ prob.Z).max() < 1e-12:
+            assert np.abs(PZ[I] - prob.Z[I]).max() < 1e-10
