@@ -514,9 +514,15 @@ def run_serving(args, world, rank, dist, barrier):
         pr = byname[key]
         return gdsw.Handle(pr.A, pr.part, pr.Z if pr.part.dpn == 3 else None, stream=stream, **opts)
 
+    est = {}
+
     def estimate(key):
-        pr = byname[key]
-        return int(pr.A.n * (600 if pr.part.dpn == 1 else 4500))
+        # resident handle plus the setup's transient scratch, from the symbolic phase
+        if key not in est:
+            pr = byname[key]
+            r, sc = gdsw.bytes_required(pr.A, pr.part, pr.Z if pr.part.dpn == 3 else None, **opts)
+            est[key] = r + sc
+        return est[key]
 
     free, _total = torch.cuda.mem_get_info()
     budget = int(args.serving_budget_gb * (1 << 30)) if args.serving_budget_gb else int(0.8 * free)

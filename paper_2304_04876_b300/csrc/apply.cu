@@ -602,6 +602,39 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
 
 }  // namespace
 
+// Resident CTAs per SM of the pipelined local solve for this handle's types,
+// ring depth S and dynamic shared memory (0 when it does not fit).  Raises the
+// kernel's dynamic shared memory limit first.
+template <class TT, class TS, int TP>
+gdsw_status pipe_occupancy_t(int S, size_t shm, int* per_sm) {
+  *per_sm = 0;
+  auto one = [&](auto kernel) -> gdsw_status {
+    GDSW_CK(allow_max_dynamic_smem(kernel));
+    cudaFuncAttributes fa;
+    GDSW_CK(cudaFuncGetAttributes(&fa, kernel));
+    if (shm + fa.sharedSizeBytes > size_t(max_block_smem_optin())) return GDSW_OK;
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, 256, shm));
+    return GDSW_OK;
+  };
+  switch (S) {
+    case 2: return one(k_local_pipe<TT, TS, 2, TP>);
+    case 3: return one(k_local_pipe<TT, TS, 3, TP>);
+    case 4: return one(k_local_pipe<TT, TS, 4, TP>);
+    default: return one(k_local_pipe<TT, TS, 6, TP>);
+  }
+}
+
+gdsw_status pipe_occupancy(const Ctx* c, int S, size_t shm, int* per_sm) {
+  if (c->fp16)
+    return c->rec_tpr == 8 ? pipe_occupancy_t<float, __half, 8>(S, shm, per_sm)
+                           : pipe_occupancy_t<float, __half, 1>(S, shm, per_sm);
+  if (c->fp32)
+    return c->rec_tpr == 8 ? pipe_occupancy_t<float, float, 8>(S, shm, per_sm)
+                           : pipe_occupancy_t<float, float, 1>(S, shm, per_sm);
+  return c->rec_tpr == 8 ? pipe_occupancy_t<double, double, 8>(S, shm, per_sm)
+                         : pipe_occupancy_t<double, double, 1>(S, shm, per_sm);
+}
+
 gdsw_status apply_configure(Ctx* c) {
   const char* two = getenv("GDSW_APPLY_STREAMS");
   if (c->aux_stream == nullptr && (two == nullptr || two[0] != '1')) {
@@ -623,36 +656,34 @@ gdsw_status apply_configure(Ctx* c) {
   }
   const size_t shm_coarse = c->nprob == 1 ? size_t(c->n0) * sizeof(double) : 16;
   if (shm_coarse > 227 * 1024) { set_error("coarse dimension too large"); return GDSW_ERR_UNSUPPORTED; }
-  // pipelined level-scheduled solve: deepest ring (6, 4, 3, 2 stages) that fits
-  // next to the subdomain vector; otherwise the plain kernel
+  // pipelined level-scheduled solve: the ring depth (6, 4, 3 or 2 stages)
+  // that runs all subdomains in the fewest waves of resident CTAs (one CTA per
+  // subdomain; the local solve is latency-bound, so a wave that is only partly
+  // filled costs as much as a full one), the deepest ring among those
   c->rec_stages = 0;
+  c->rec_tpr = c->rec_max_width > 8 ? 8 : 1;
   const char* env = getenv("GDSW_LOCAL_PIPE");
   const bool pipe_ok = (env == nullptr || env[0] != '0') && c->rec_stream != nullptr &&
                        c->opt.local_solver != GDSW_LOCAL_EXACT && !jac;
   if (pipe_ok) {
+    int dev = 0, sms = 148;
+    GDSW_CK(cudaGetDevice(&dev));
+    GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int depth_env = getenv("GDSW_PIPE_STAGES") ? atoi(getenv("GDSW_PIPE_STAGES")) : 0;
     const int cand[4] = {6, 4, 3, 2};
+    int64_t best_waves = INT64_MAX;
     for (int q = 0; q < 4; ++q) {
       if (depth_env > 0 && cand[q] != depth_env) continue;
       const size_t shm = size_t(cand[q]) * c->rec_stage_bytes + size_t(c->max_m) * es;
-      if (shm <= 200 * 1024 && (depth_env > 0 || shm <= 112 * 1024 || cand[q] == 2)) {
+      int per_sm = 0;
+      GDSW_TRY(pipe_occupancy(c, cand[q], shm, &per_sm));
+      if (per_sm == 0) continue;
+      const int64_t waves = (int64_t(c->nsub) + int64_t(sms) * per_sm - 1) / (int64_t(sms) * per_sm);
+      if (waves < best_waves) {
+        best_waves = waves;
         c->rec_stages = cand[q];
-        break;
       }
     }
-  }
-  c->rec_tpr = c->rec_max_width > 8 ? 8 : 1;
-  if (c->rec_stages > 0) {
-    const int shm = int(size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * es);
-#define GDSW_PIPE_ATTR(TT, TS, SS, TP)                                                                     \
-  GDSW_CK(allow_max_dynamic_smem(k_local_pipe<TT, TS, SS, TP>));
-#define GDSW_PIPE_ATTRS(TT, TS) \
-  GDSW_PIPE_ATTR(TT, TS, 2, 1) GDSW_PIPE_ATTR(TT, TS, 3, 1) GDSW_PIPE_ATTR(TT, TS, 4, 1) GDSW_PIPE_ATTR(TT, TS, 6, 1) \
-  GDSW_PIPE_ATTR(TT, TS, 2, 8) GDSW_PIPE_ATTR(TT, TS, 3, 8) GDSW_PIPE_ATTR(TT, TS, 4, 8) GDSW_PIPE_ATTR(TT, TS, 6, 8)
-    if (c->fp16) { GDSW_PIPE_ATTRS(float, __half) }
-    else if (c->fp32) { GDSW_PIPE_ATTRS(float, float) } else { GDSW_PIPE_ATTRS(double, double) }
-#undef GDSW_PIPE_ATTRS
-#undef GDSW_PIPE_ATTR
   }
   if (c->fp32) {
     GDSW_CK(allow_max_dynamic_smem(k_local_tri<float>));
