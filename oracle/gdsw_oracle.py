@@ -41,6 +41,7 @@ cases, finite termination).
 """
 from __future__ import annotations
 
+import heapq
 from dataclasses import dataclass
 from typing import List, Optional
 
@@ -449,6 +450,61 @@ def ilu0_sweeps(ptr, col, val, sweeps: int):
     return (ptr, col, F), s
 
 
+def level_fill_pattern(ptr, col, k: int):
+    """Pattern of the level-of-fill incomplete factorisation ILU(k) (Sec. V-B:
+    the KokkosKernels ILU(k) and the fixed-point FastILU(k) of Table I).
+
+    Entries of A have level 0.  Eliminating row i with pivot p (in increasing
+    column order, fill included) creates or lowers entry (i, j), j > p, to level
+    lev(i, p) + lev(p, j) + 1, where lev(p, j) is the final level of row p; the
+    pattern keeps every entry of level <= k.  Returns (ptr, col, level), rows
+    sorted by column.
+    """
+    m = len(ptr) - 1
+    upper = []                       # finished rows: [(j, level)] for j > row
+    out_ptr = [0]
+    out_col, out_lev = [], []
+    for i in range(m):
+        lev = {int(j): 0 for j in col[ptr[i]:ptr[i + 1]]}
+        heap = [j for j in lev if j < i]
+        heapq.heapify(heap)
+        seen = set()
+        while heap:
+            p = heapq.heappop(heap)
+            if p in seen:
+                continue
+            seen.add(p)
+            lip = lev[p]
+            for j, lpj in upper[p]:
+                new = lip + lpj + 1
+                if new > k:
+                    continue
+                if j not in lev:
+                    lev[j] = new
+                    if j < i:
+                        heapq.heappush(heap, j)
+                elif new < lev[j]:
+                    lev[j] = new
+        cols = sorted(lev)
+        upper.append([(j, lev[j]) for j in cols if j > i])
+        out_col.extend(cols)
+        out_lev.extend(lev[j] for j in cols)
+        out_ptr.append(len(out_col))
+    return (np.asarray(out_ptr, dtype=np.int64), np.asarray(out_col, dtype=np.int64),
+            np.asarray(out_lev, dtype=np.int64))
+
+
+def pad_to_pattern(ptr, col, val, fptr, fcol):
+    """Values of (ptr, col, val) on the larger pattern (fptr, fcol), zero on fill."""
+    m = len(ptr) - 1
+    out = np.zeros(len(fcol))
+    for i in range(m):
+        pos = {int(j): q for q, j in enumerate(fcol[fptr[i]:fptr[i + 1]], start=int(fptr[i]))}
+        for e in range(ptr[i], ptr[i + 1]):
+            out[pos[int(col[e])]] = val[e]
+    return out
+
+
 def ic0_sequential(ptr, col, val):
     """Textbook IC(0) (row-by-row, in place on the pattern of tril(A)); small cases.
 
@@ -532,8 +588,9 @@ class GDSW:
     """
 
     def __init__(self, A, part, Z=None, local=EXACT, trsv=LEVELSCHED, sweeps_factor=3,
-                 sweeps_trsv=5, overlap=1, coarse=True, coarse_variant="gdsw"):
+                 sweeps_trsv=5, overlap=1, coarse=True, coarse_variant="gdsw", fill_level=0):
         self.A = A
+        self.fill_level = fill_level
         self.part = part
         self.n = A.n
         self.local, self.trsv = local, trsv
@@ -562,6 +619,11 @@ class GDSW:
         if self.local == EXACT:
             As = _csr(m, ptr, col, val)
             return ("exact", As)
+        if self.fill_level > 0:
+            # IC(k)/ILU(k): the same sweeps over the level-k pattern, zero on fill
+            fptr, fcol, _ = level_fill_pattern(ptr, col, self.fill_level)
+            val = pad_to_pattern(ptr, col, val, fptr, fcol)
+            ptr, col = fptr, fcol
         if self.local == IC0:
             (lp, lc, lv), s = ic0_sweeps(ptr, col, val, self.sweeps_factor)
             Lm = _csr(m, lp, lc, lv)
