@@ -42,6 +42,8 @@ VARIANTS = {
     "fp16_levelsched": dict(local_solver="ic0", trsv="levelsched", precision="fp16"),
     "fp64_levelsched_rgdsw": dict(local_solver="ic0", trsv="levelsched", precision="fp64", coarse="rgdsw"),
     "fp32_levelsched_rgdsw": dict(local_solver="ic0", trsv="levelsched", precision="fp32", coarse="rgdsw"),
+    "fp32_levelsched_ic1": dict(local_solver="ic0", trsv="levelsched", precision="fp32", fill_level=1),
+    "fp32_levelsched_ic2": dict(local_solver="ic0", trsv="levelsched", precision="fp32", fill_level=2),
 }
 DEFAULT_VARIANT = "fp32_levelsched"
 METRIC = "PCG solves/s to 1e-8 relative residual (time-to-residual = 1/value)"
@@ -65,7 +67,9 @@ CONFIGS = {
                                           precision="fp32"),
                       "fp16_levelsched": dict(local_solver="ilu0", krylov="gmres", restart=30, precision="fp16"),
                       "fp32_levelsched_rgdsw": dict(local_solver="ilu0", krylov="gmres", restart=30,
-                                                    precision="fp32", coarse="rgdsw")},
+                                                    precision="fp32", coarse="rgdsw"),
+                      "fp32_levelsched_ilu1": dict(local_solver="ilu0", krylov="gmres", restart=30,
+                                                   precision="fp32", fill_level=1)},
             default="fp32_levelsched", Z=True),
 }
 

@@ -70,6 +70,13 @@ enum { GDSW_KRYLOV_PCG = 0, GDSW_KRYLOV_GMRES = 1 };
  * vertices) */
 enum { GDSW_COARSE_GDSW = 0, GDSW_COARSE_NONE = 1, GDSW_COARSE_RGDSW = 2 };
 
+/* Gram-Schmidt of the GMRES Arnoldi process: classical Gram-Schmidt applied
+ * twice (two fused reductions per step), or the single-reduce form (one
+ * reduction of V^T w and (w, w), the norm by Pythagoras, a second pass only
+ * when that cancels).  The single-reduce form loses orthogonality faster, so
+ * its least-squares residual can lag the true one and take more steps. */
+enum { GDSW_GMRES_ORTH_CGS2 = 0, GDSW_GMRES_ORTH_SINGLE = 1 };
+
 /* Square sparse matrix, CSR, host memory.  rowptr[n+1], colind[nnz] (0-based,
  * strictly increasing within each row, diagonal stored), val[nnz].  The
  * pattern must be structurally symmetric (it is the pattern of the
@@ -103,6 +110,14 @@ typedef struct {
   int32_t restart;        /* GMRES restart length         (30)            */
   int32_t maxit;          /* iteration cap                (2000)          */
   int32_t coarse;         /* GDSW_COARSE_*                (GDSW)          */
+  int32_t fill_level;     /* k of IC(k)/ILU(k): level-of-fill pattern of the
+                             local factors (Sec. V-B); 0 = IC(0)/ILU(0).  Only
+                             with the IC0/ILU0 local solvers            (0)   */
+  int32_t autotune;       /* 1: the local solve's shape (ring depth, consumer
+                             threads) is timed at setup and the fastest kept;
+                             0: chosen from occupancy alone.  Results do not
+                             depend on it                               (1)   */
+  int32_t gmres_orth;     /* GDSW_GMRES_ORTH_*: Gram-Schmidt of GMRES  (CGS2) */
   int32_t flexible;       /* PCG beta (r, z - z_old)/(r_old, z_old): 1 = on,
                              0 = off, -1 = on exactly when precision != FP64 */
   double tol;             /* relative residual target     (1e-8)          */

@@ -26,18 +26,43 @@ namespace gdsw {
 
 namespace {
 
+// v = R_s r for one subdomain (m entries from base) by `nt` threads (this
+// thread is `tid`): eight indices, then eight values, in flight per thread.
+template <class T>
+__device__ __forceinline__ void gather_sub(const double* __restrict__ r, const int* __restrict__ om_dofs,
+                                           int base, int m, T* v, int tid, int nt) {
+  for (int i0 = tid; i0 < m; i0 += 8 * nt) {
+    int idx[8];
+    double rv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) idx[u] = i0 + u * nt < m ? om_dofs[base + i0 + u * nt] : -1;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) rv[u] = idx[u] >= 0 ? r[idx[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (i0 + u * nt < m) v[i0 + u * nt] = T(rv[u]);
+  }
+}
+
+// Level-scheduled substitution: the rows of a level are independent except
+// within a node's group of E.grp consecutive rows, which one thread solves in
+// the stored order.
 template <class T>
 __device__ __forceinline__ void tri_levels(const EllDev<T>& E, int s, T* v) {
   const int l0 = E.sub_lev[s], l1 = E.sub_lev[s + 1];
+  const int G = E.grp;
   for (int l = l0; l < l1; ++l) {
     const int4 lv = E.lev[l];   // (first row, rows, width, first slot)
-    for (int t = threadIdx.x; t < lv.y; t += blockDim.x) {
-      const int row = E.lrows[lv.x + t];
-      T acc = v[row];
-      const T* vals = E.val + lv.w + t;
-      const uint16_t* cols = E.col + lv.w + t;
-      for (int k = 0; k < lv.z; ++k) acc -= vals[int64_t(k) * lv.y] * v[cols[int64_t(k) * lv.y]];
-      v[row] = acc * E.dinv[lv.x + t];
+    for (int gt = threadIdx.x; gt * G < lv.y; gt += blockDim.x) {
+      for (int d = 0; d < G; ++d) {
+        const int t = gt * G + d;
+        const int row = E.lrows[lv.x + t];
+        T acc = v[row];
+        const T* vals = E.val + lv.w + t;
+        const uint16_t* cols = E.col + lv.w + t;
+        for (int k = 0; k < lv.z; ++k) acc -= vals[int64_t(k) * lv.y] * v[cols[int64_t(k) * lv.y]];
+        v[row] = acc * E.dinv[lv.x + t];
+      }
     }
     __syncthreads();
   }
@@ -86,7 +111,7 @@ __device__ __forceinline__ void tri_jacobi(const EllDev<T>& E, int s, int sweeps
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_local_tri(const double* __restrict__ r,
+__global__ void __launch_bounds__(1024) k_local_tri(const double* __restrict__ r,
                                                    const int* __restrict__ om_ptr,
                                                    const int* __restrict__ om_dofs, EllDev<T> L,
                                                    EllDev<T> U, int jacobi, int sweeps,
@@ -97,7 +122,7 @@ __global__ void __launch_bounds__(256) k_local_tri(const double* __restrict__ r,
   T* v = reinterpret_cast<T*>(smem_raw);
   const int s = blockIdx.x;
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = T(r[om_dofs[base + i]]);
+  gather_sub(r, om_dofs, base, m, v, threadIdx.x, blockDim.x);
   __syncthreads();
   if (!jacobi) {
     tri_levels(L, s, v);
@@ -113,9 +138,10 @@ __global__ void __launch_bounds__(256) k_local_tri(const double* __restrict__ r,
 
 // Level-scheduled triangular solves streamed through shared memory.  The L
 // levels and then the U levels of subdomain s are a sequence of records (one
-// per level, 16-byte aligned, see the setup); thread 0 keeps S records in
-// flight with TMA bulk copies into a ring of stages, each stage tracked by an
-// mbarrier, while all threads compute the current level from shared memory:
+// per level, 16-byte aligned, see the setup); a producer warp keeps S records
+// in flight with bulk copies into a ring of stages, each stage tracked by
+// mbarriers, while the consumer threads compute the current level from
+// shared memory:
 //     v[row] = (v[row] - sum_k val_k v[col_k]) * dinv
 // Every wait is bounded by `wait_cycles`; a wait that runs out sets err[0],
 // waits (bounded again) for the copies still in flight, and ends the CTA
@@ -130,15 +156,26 @@ __device__ __forceinline__ float load_as<float, __half>(const __half* p, int i) 
 // add their partial sums with shuffles; short rows (TPR = 1) are unrolled.
 // TS is the storage type of the record values (T, or FP16 applied in FP32).
 template <class T, class TS, int TPR>
-__device__ __forceinline__ void level_rows(const unsigned char* rec, T* v) {
+__device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const int NT, const int G) {
   const int4 hdr = *reinterpret_cast<const int4*>(rec);
   const int nr = hdr.x, K = hdr.y;
   const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 16);
   const TS* dinv = reinterpret_cast<const TS*>(rec + 16 + ((2 * nr + 15) & ~15));
   const TS* vals = reinterpret_cast<const TS*>(rec + hdr.z);
   const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + hdr.w);
-  if (TPR == 1) {
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+  if (TPR == 1 && G > 1) {
+    // a node's rows in order by one thread
+    for (int gt = threadIdx.x; gt * G < nr; gt += NT) {
+      for (int d = 0; d < G; ++d) {
+        const int t = gt * G + d;
+        const int row = lrows[t];
+        T acc = v[row];
+        for (int k = 0; k < K; ++k) acc = fma(-load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], acc);
+        v[row] = acc * load_as<T, TS>(dinv, t);
+      }
+    }
+  } else if (TPR == 1) {
+    for (int t = threadIdx.x; t < nr; t += NT) {
       const int row = lrows[t];
       T acc = v[row];
       if (K <= 4) {
@@ -158,36 +195,68 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v) {
     }
   } else {
     const int sub = threadIdx.x % TPR;
-    const int groups = blockDim.x / TPR;
-    // every thread runs the same number of rounds, so the shuffles stay convergent
-    for (int round = 0; round < nr; round += groups) {
-      const int t = round + threadIdx.x / TPR;
-      T part = T(0);
-      if (t < nr)
-        for (int k = sub; k < K; k += TPR) part = fma(load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], part);
+    const int groups = NT / TPR;
+    const int ngr = nr / G;
+    // every thread runs the same number of rounds, so the shuffles stay
+    // convergent; a node's G rows go in order, each one's update visible to the
+    // next through the warp barrier
+    for (int round = 0; round < ngr; round += groups) {
+      const int gt = round + threadIdx.x / TPR;
+      for (int d = 0; d < G; ++d) {
+        const int t = gt * G + d;
+        T part = T(0);
+        if (gt < ngr)
+          for (int k = sub; k < K; k += TPR) part = fma(load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], part);
 #pragma unroll
-      for (int o = TPR / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, TPR);
-      if (t < nr && sub == 0) {
-        const int row = lrows[t];
-        v[row] = (v[row] - part) * load_as<T, TS>(dinv, t);
+        for (int o = TPR / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, TPR);
+        if (gt < ngr && sub == 0) {
+          const int row = lrows[t];
+          v[row] = (v[row] - part) * load_as<T, TS>(dinv, t);
+        }
+        if (G > 1) __syncwarp();
       }
     }
   }
 }
 
+// The pipelined local solve runs NT consumer threads (128 to 992, chosen at
+// setup) that update the rows, plus one producer warp that only streams the
+// level records into the ring.
+constexpr int kPipeMaxThreads = 1024;
+
+// Barrier of the `nt` consumer threads only (named barrier 1), returning the
+// OR of `pred` over them.
+__device__ __forceinline__ bool consumers_sync_or(bool pred, int nt) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.cta.red.or.pred p, 1, %2, q;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(out)
+      : "r"(static_cast<uint32_t>(pred)), "r"(nt)
+      : "memory");
+  return out != 0;
+}
+
+// z_s = (L U)^-1 r_s for every subdomain s (one CTA each), level by level.
+// The producer warp copies the records of subdomain s, one per level, with
+// bulk copies into a ring of S stages (full[st] completes when a record has
+// landed, empty[st] when the consumers are done with it); the consumers wait
+// for a record, update its rows in shared memory, meet at one barrier per
+// level and release the stage.  The copy issue is off the consumers' path.
 template <class T, class TS, int S, int TPR>
-__global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r,
-                                                    const int* __restrict__ om_ptr,
-                                                    const int* __restrict__ om_dofs,
-                                                    const int* __restrict__ rec_ptr,
-                                                    const uint32_t* __restrict__ rec_off16,
-                                                    const uint32_t* __restrict__ rec_bytes,
-                                                    const uint8_t* __restrict__ stream, int stage_bytes,
-                                                    T* __restrict__ zloc,
-                                                    const KrylovScalars* __restrict__ ks, int* err,
-                                                    long long wait_cycles) {
+__global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __restrict__ r,
+                                                             const int* __restrict__ om_ptr,
+                                                             const int* __restrict__ om_dofs,
+                                                             const int* __restrict__ rec_ptr,
+                                                             const uint32_t* __restrict__ rec_off16,
+                                                             const uint32_t* __restrict__ rec_bytes,
+                                                             const uint8_t* __restrict__ stream, int stage_bytes,
+                                                             T* __restrict__ zloc,
+                                                             const KrylovScalars* __restrict__ ks, int* err,
+                                                             long long wait_cycles, int grp) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar[S];
+  __shared__ __align__(8) uint64_t full[S];
+  __shared__ __align__(8) uint64_t empty[S];
   if (ks != nullptr && ks->done) return;
   const int s = blockIdx.x;
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
@@ -195,42 +264,54 @@ __global__ void __launch_bounds__(256) k_local_pipe(const double* __restrict__ r
   unsigned char* stages = smem_raw;
   T* v = reinterpret_cast<T*>(smem_raw + size_t(S) * stage_bytes);
   if (threadIdx.x == 0) {
-    for (int j = 0; j < S; ++j) mbar_init(&bar[j], 1);
+    for (int j = 0; j < S; ++j) {
+      mbar_init(&full[j], 1);
+      mbar_init(&empty[j], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < S && j < nrec; ++j) {
+  const int nt = blockDim.x - 32;            // consumer threads
+  if (int(threadIdx.x) >= nt) {
+    // ---- producer warp (one lane issues) ----
+    if (int(threadIdx.x) != nt) return;
+    int last[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) last[j] = -1;
+    for (int j = 0; j < nrec; ++j) {
+      const int st = j % S;
+      if (j >= S && !mbar_wait_bounded(&empty[st], ((j / S) - 1) & 1, wait_cycles)) {
+        atomicOr(err, 1);      // the consumers stopped (their own wait ran out)
+        break;
+      }
+      fence_proxy_async_smem();
       const unsigned nb = rec_bytes[r0 + j];
-      mbar_expect_tx(&bar[j], nb);
-      bulk_g2s(stages + size_t(j) * stage_bytes, stream + size_t(rec_off16[r0 + j]) * 16, nb, &bar[j]);
+      mbar_expect_tx(&full[st], nb);
+      bulk_g2s(stages + size_t(st) * stage_bytes, stream + size_t(rec_off16[r0 + j]) * 16, nb, &full[st]);
+      last[st] = j;
     }
+    // every copy issued has landed before the CTA's shared memory can go away
+#pragma unroll
+    for (int st = 0; st < S; ++st)
+      if (last[st] >= 0) mbar_wait_bounded(&full[st], (last[st] / S) & 1, wait_cycles);
+    return;
   }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = T(r[om_dofs[base + i]]);
-  __syncthreads();
+  // ---- consumer warps ----
+  gather_sub(r, om_dofs, base, m, v, threadIdx.x, nt);
+  consumers_sync_or(false, nt);
   for (int i = 0; i < nrec; ++i) {
     const int st = i % S;
-    const unsigned parity = (i / S) & 1;
-    // each thread waits for the record itself; the one barrier per level
-    // below also carries a timed-out wait to every thread
-    const bool ok = mbar_wait_bounded(&bar[st], parity, wait_cycles);
-    if (ok) level_rows<T, TS, TPR>(stages + size_t(st) * stage_bytes, v);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        atomicOr(err, 1);
-        // let the copies already issued land before the CTA's shared memory goes away
-        for (int j = i; j < nrec && j < i + S; ++j) mbar_wait_bounded(&bar[j % S], (j / S) & 1, wait_cycles);
-      }
+    // each thread waits for the record itself; the barrier below carries a
+    // wait that ran out to every consumer
+    const bool ok = mbar_wait_bounded(&full[st], (i / S) & 1, wait_cycles);
+    if (ok) level_rows<T, TS, TPR>(stages + size_t(st) * stage_bytes, v, nt, grp);
+    if (consumers_sync_or(!ok, nt)) {
+      if (threadIdx.x == 0) atomicOr(err, 1);
       return;
     }
-    if (threadIdx.x == 0 && i + S < nrec) {
-      fence_proxy_async_smem();
-      const unsigned nb = rec_bytes[r0 + i + S];
-      mbar_expect_tx(&bar[st], nb);
-      bulk_g2s(stages + size_t(st) * stage_bytes, stream + size_t(rec_off16[r0 + i + S]) * 16, nb, &bar[st]);
-    }
+    if (threadIdx.x == 0 && i + S < nrec) mbar_arrive(&empty[st]);
   }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) zloc[base + i] = v[i];
+  for (int i = threadIdx.x; i < m; i += nt) zloc[base + i] = v[i];
 }
 
 // Exact local solver: z_s = A_s^-1 r_s with the stored dense inverse
@@ -250,7 +331,7 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
   const int row0 = blockIdx.x * 32;
   if (row0 >= m) return;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) rs[i] = T(r[om_dofs[base + i]]);
+  gather_sub(r, om_dofs, base, m, rs, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const T* A = ainv + ainv_off[s];
@@ -265,10 +346,52 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
   }
 }
 
-// Partial products Phi_b^T r_b over one chunk of at most 1024 rows of a
-// block (one CTA per chunk, 8 columns per pass, four rows per trip).
+// Partial products Phi_b^T r_b.  The first n_cta chunks (more than 256 rows,
+// at most 1024, of a block) take one CTA each: 8 columns per pass, four rows
+// per trip, a transpose reduction through shared memory.  The small chunks
+// (interface components) take one warp each, eight per CTA, with shuffle sums.
 template <class T>
-__global__ void __launch_bounds__(256) k_phiT(const double* __restrict__ r,
+__device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict__ r,
+                                                const int* __restrict__ brow_ptr,
+                                                const int* __restrict__ brow_dof,
+                                                const int* __restrict__ bcol_ptr,
+                                                const int64_t* __restrict__ phi_off,
+                                                const T* __restrict__ phi,
+                                                const int* __restrict__ chunk_blk,
+                                                const int* __restrict__ chunk_r0,
+                                                const int* __restrict__ chunk_r1,
+                                                const int* __restrict__ chunk_slot,
+                                                double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31;
+  const int b = chunk_blk[q];
+  const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
+  const int i0 = chunk_r0[q], i1 = chunk_r1[q];
+  const int k = bcol_ptr[b + 1] - bcol_ptr[b];
+  const T* Ph = phi + phi_off[b];
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    const int kc = min(8, k - c0);
+    T acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = T(0);
+    for (int i = i0 + lane; i < i1; i += 32) {
+      const T rv = T(r[brow_dof[p0 + i]]);
+      const T* col = Ph + int64_t(c0) * nr + i;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u < kc) acc[u] = fma(col[int64_t(u) * nr], rv, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u < kc) {
+        const T t = warp_sum(acc[u]);
+        if (lane == 0) partial[chunk_slot[q] + c0 + u] = double(t);
+      }
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, 6) k_phiT(int n_chunks, int n_cta, const double* __restrict__ r,
                                               const int* __restrict__ brow_ptr,
                                               const int* __restrict__ brow_dof,
                                               const int* __restrict__ bcol_ptr,
@@ -282,6 +405,14 @@ __global__ void __launch_bounds__(256) k_phiT(const double* __restrict__ r,
                                               const KrylovScalars* __restrict__ ks) {
   __shared__ T red8[8][256];
   if (ks != nullptr && ks->done) return;
+  if (int(blockIdx.x) >= n_cta) {
+    // warp path: no CTA-wide barrier below
+    const int q = n_cta + (int(blockIdx.x) - n_cta) * 8 + (threadIdx.x >> 5);
+    if (q < n_chunks)
+      phiT_warp_chunk<T>(q, r, brow_ptr, brow_dof, bcol_ptr, phi_off, phi, chunk_blk, chunk_r0, chunk_r1,
+                         chunk_slot, partial);
+    return;
+  }
   const int q = blockIdx.x;
   const int b = chunk_blk[q];
   const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
@@ -348,7 +479,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
                                                      const int* __restrict__ prob_c0,
                                                      const int64_t* __restrict__ a0_off, int staged,
                                                      const double* __restrict__ c,
-                                                     double* __restrict__ y,
+                                                     double* __restrict__ y, float* __restrict__ y32,
                                                      const KrylovScalars* __restrict__ ks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ks != nullptr && ks->done) return;
@@ -377,7 +508,10 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
     for (; j < np; j += 32) a0 = fma(Ar[j], cv[j], a0);
     double acc = (a0 + a1) + (a2 + a3);
     acc = warp_sum(acc);
-    if (lane == 0) y[row] = acc;
+    if (lane == 0) {
+      y[row] = acc;
+      if (y32 != nullptr) y32[row] = float(acc);   // converted once, not per scatter position
+    }
   }
 }
 
@@ -392,7 +526,7 @@ __device__ __forceinline__ double combine_one(int p, const int* __restrict__ pos
                                               const int* __restrict__ bcol_ptr,
                                               const int* __restrict__ bcol,
                                               const int64_t* __restrict__ phi_off,
-                                              const T* __restrict__ phi, const double* __restrict__ y,
+                                              const T* __restrict__ phi, const T* __restrict__ y,
                                               const int* __restrict__ pull_ptr,
                                               const int* __restrict__ pull_pos,
                                               const T* __restrict__ zloc) {
@@ -406,17 +540,17 @@ __device__ __forceinline__ double combine_one(int p, const int* __restrict__ pos
     const int p0 = brow_ptr[b];
     const int nr = brow_ptr[b + 1] - p0;
     const T* Ph = phi + phi_off[b] + (p - p0);
-    for (int u = 0; u < k; ++u) acc = fma(Ph[int64_t(u) * nr], T(y[bcol[c0 + u]]), acc);
+    for (int u = 0; u < k; ++u) acc = fma(Ph[int64_t(u) * nr], y[bcol[c0 + u]], acc);
   }
   return double(acc);
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_combine(
+__global__ void __launch_bounds__(256, 6) k_combine(
     int n, const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_dof,
     const int* __restrict__ pos_blk, const int* __restrict__ brow_ptr,
     const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
-    const int64_t* __restrict__ phi_off, const T* __restrict__ phi, const double* __restrict__ y,
+    const int64_t* __restrict__ phi_off, const T* __restrict__ phi, const T* __restrict__ y,
     const int* __restrict__ pull_ptr, const int* __restrict__ pull_pos, const T* __restrict__ zloc,
     int dots, double* __restrict__ red, KrylovScalars* ks) {
   __shared__ double sh[32];
@@ -478,6 +612,7 @@ EllDev<T> ell(const Ctx* c, bool lower) {
     e.sub_lev = c->U_sub_lev; e.lev = c->U_lev; e.lrows = c->U_lrows; e.col = c->U_col;
     e.val = static_cast<const T*>(c->U_val); e.dinv = static_cast<const T*>(c->U_dinv);
   }
+  e.grp = c->dpn;
   return e;
 }
 
@@ -495,10 +630,10 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
     if (c->fp16) {
       if constexpr (std::is_same<T, float>::value) {
 #define GDSW_PIPE_LAUNCH(SS, TP)                                                                            \
-  k_local_pipe<T, __half, SS, TP><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr,            \
+  k_local_pipe<T, __half, SS, TP><<<c->nsub, c->rec_consumers + 32, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr,            \
                                                             c->rec_off16, c->rec_bytes, c->rec_stream,       \
                                                             c->rec_stage_bytes, zl, ks, c->derr,             \
-                                                            c->wait_cycles)
+                                                            c->wait_cycles, c->dpn)
         switch (key) {
           case 201: GDSW_PIPE_LAUNCH(2, 1); break;
           case 301: GDSW_PIPE_LAUNCH(3, 1); break;
@@ -513,9 +648,9 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
       }
     } else {
 #define GDSW_PIPE_LAUNCH(SS, TP)                                                                     \
-  k_local_pipe<T, T, SS, TP><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, \
+  k_local_pipe<T, T, SS, TP><<<c->nsub, c->rec_consumers + 32, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, \
                                                        c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, \
-                                                       ks, c->derr, c->wait_cycles)
+                                                       ks, c->derr, c->wait_cycles, c->dpn)
       switch (key) {
         case 201: GDSW_PIPE_LAUNCH(2, 1); break;
         case 301: GDSW_PIPE_LAUNCH(3, 1); break;
@@ -531,7 +666,7 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
   } else {
     const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
     const size_t shm = size_t(c->max_m) * sizeof(T) * (jac ? 3 : 1);
-    k_local_tri<T><<<c->nsub, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, ell<T>(c, true),
+    k_local_tri<T><<<c->nsub, c->tri_threads, shm, s>>>(r, c->om_ptr, c->om_dofs, ell<T>(c, true),
                                              ell<T>(c, false), jac, c->opt.sweeps_trsv, zl, ks);
   }
   GDSW_CK(cudaGetLastError());
@@ -542,7 +677,9 @@ template <class T>
 gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
   if (c->n0 == 0) return GDSW_OK;
   if (c->n_chunks == 0) return GDSW_OK;
-  k_phiT<T><<<c->n_chunks, 256, 0, s>>>(r, c->brow_ptr, c->brow_dof, c->bcol_ptr, c->phi_off,
+  const int grid = c->n_cta_chunks + (c->n_chunks - c->n_cta_chunks + 7) / 8;
+  k_phiT<T><<<grid, 256, 0, s>>>(c->n_chunks, c->n_cta_chunks, r, c->brow_ptr, c->brow_dof, c->bcol_ptr,
+                                 c->phi_off,
                                         static_cast<const T*>(c->phi), c->chunk_blk, c->chunk_r0,
                                         c->chunk_r1, c->chunk_slot, c->partial, ks);
   GDSW_CK(cudaGetLastError());
@@ -555,25 +692,28 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
   const int grid = std::min((c->n0 + 7) / 8, kNumSMs * 4);
   const int staged = c->nprob == 1;
   k_coarse_gemv<<<grid, 256, staged ? size_t(c->n0) * sizeof(double) : 16, s>>>(
-      c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, staged, c->cvec, c->yvec, ks);
+      c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, staged, c->cvec, c->yvec, c->yvec32, ks);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
 
 template <class T>
-gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots) {
-  const int grid = std::min(kNumSMs * 8, (c->n + 511) / 512);
+gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated) {
+  const int grid = std::max(1, std::min(c->combine_grid, (c->n + 511) / 512));
   k_combine<T><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
-                                    c->bcol, c->phi_off, static_cast<const T*>(c->phi), c->yvec,
+                                    c->bcol, c->phi_off, static_cast<const T*>(c->phi),
+                                    c->fp32 ? reinterpret_cast<const T*>(c->yvec32) : reinterpret_cast<const T*>(c->yvec),
                                     c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),
-                                    dots ? (c->flexible ? 2 : 1) : 0, c->red, dots ? c->ks : nullptr);
+                                    dots ? (c->flexible ? 2 : 1) : 0, c->red, (dots || gated) ? c->ks : nullptr);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
 
+// dots: the PCG form (z, (r, z) and beta into the Krylov scalars); gated:
+// every kernel returns at once when the Krylov loop has set its stop flag.
 template <class T>
-gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, cudaEvent_t* ev) {
-  const KrylovScalars* ks = dots ? c->ks : nullptr;
+gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated, cudaEvent_t* ev) {
+  const KrylovScalars* ks = (dots || gated) ? c->ks : nullptr;
   if (ev == nullptr && c->n0 > 0 && c->aux_stream != nullptr) {
     // The one-level and coarse branches of Eq. 1 are independent until the
     // final sum: the coarse branch (Phi^T r, c, A0^-1 c) runs on a second
@@ -585,7 +725,7 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
     GDSW_CK(cudaEventRecord(c->ev_join, c->aux_stream));
     GDSW_TRY(launch_local<T>(c, r, s, ks));
     GDSW_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
-    GDSW_TRY(launch_combine<T>(c, r, z, s, dots));
+    GDSW_TRY(launch_combine<T>(c, r, z, s, dots, gated));
     return GDSW_OK;
   }
   if (ev) GDSW_CK(cudaEventRecord(ev[0], s));
@@ -595,7 +735,7 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
   if (ev) GDSW_CK(cudaEventRecord(ev[2], s));
   GDSW_TRY(launch_coarse(c, s, ks));
   if (ev) GDSW_CK(cudaEventRecord(ev[3], s));
-  GDSW_TRY(launch_combine<T>(c, r, z, s, dots));
+  GDSW_TRY(launch_combine<T>(c, r, z, s, dots, gated));
   if (ev) GDSW_CK(cudaEventRecord(ev[4], s));
   return GDSW_OK;
 }
@@ -606,14 +746,14 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
 // ring depth S and dynamic shared memory (0 when it does not fit).  Raises the
 // kernel's dynamic shared memory limit first.
 template <class TT, class TS, int TP>
-gdsw_status pipe_occupancy_t(int S, size_t shm, int* per_sm) {
+gdsw_status pipe_occupancy_t(int S, size_t shm, int threads, int* per_sm) {
   *per_sm = 0;
   auto one = [&](auto kernel) -> gdsw_status {
     GDSW_CK(allow_max_dynamic_smem(kernel));
     cudaFuncAttributes fa;
     GDSW_CK(cudaFuncGetAttributes(&fa, kernel));
     if (shm + fa.sharedSizeBytes > size_t(max_block_smem_optin())) return GDSW_OK;
-    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, 256, shm));
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, shm));
     return GDSW_OK;
   };
   switch (S) {
@@ -626,13 +766,88 @@ gdsw_status pipe_occupancy_t(int S, size_t shm, int* per_sm) {
 
 gdsw_status pipe_occupancy(const Ctx* c, int S, size_t shm, int* per_sm) {
   if (c->fp16)
-    return c->rec_tpr == 8 ? pipe_occupancy_t<float, __half, 8>(S, shm, per_sm)
-                           : pipe_occupancy_t<float, __half, 1>(S, shm, per_sm);
+    return c->rec_tpr == 8 ? pipe_occupancy_t<float, __half, 8>(S, shm, c->rec_consumers + 32, per_sm)
+                           : pipe_occupancy_t<float, __half, 1>(S, shm, c->rec_consumers + 32, per_sm);
   if (c->fp32)
-    return c->rec_tpr == 8 ? pipe_occupancy_t<float, float, 8>(S, shm, per_sm)
-                           : pipe_occupancy_t<float, float, 1>(S, shm, per_sm);
-  return c->rec_tpr == 8 ? pipe_occupancy_t<double, double, 8>(S, shm, per_sm)
-                         : pipe_occupancy_t<double, double, 1>(S, shm, per_sm);
+    return c->rec_tpr == 8 ? pipe_occupancy_t<float, float, 8>(S, shm, c->rec_consumers + 32, per_sm)
+                           : pipe_occupancy_t<float, float, 1>(S, shm, c->rec_consumers + 32, per_sm);
+  return c->rec_tpr == 8 ? pipe_occupancy_t<double, double, 8>(S, shm, c->rec_consumers + 32, per_sm)
+                         : pipe_occupancy_t<double, double, 1>(S, shm, c->rec_consumers + 32, per_sm);
+}
+
+// Measured choice of the pipelined local solve's shape: every ring depth that
+// fits, with 128 to 992 consumer threads, timed over three launches each
+// (CUDA events, after one warm-up launch) on a zero right-hand side, and the
+// unpipelined level-scheduled kernel beside them; the fastest is kept.  Every
+// candidate computes the same values in the same order, so the choice changes
+// the speed only, never the result.
+gdsw_status tune_local(Ctx* c) {
+  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  cudaStream_t s;
+  GDSW_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  double* r = nullptr;
+  cudaEvent_t e0, e1;
+  gdsw_status st = GDSW_OK;
+  auto fail = [&](cudaError_t e) { set_error("local-solve tuning: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; };
+  cudaError_t e = cudaMalloc(&r, sizeof(double) * std::max(1, c->n));
+  if (e == cudaSuccess) e = cudaMemsetAsync(r, 0, sizeof(double) * std::max(1, c->n), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) fail(e);
+  const int keep_s = c->rec_stages, keep_nt = c->rec_consumers;
+  float best = 3.4e38f;
+  int best_s = keep_s, best_nt = keep_nt;
+  const int cand[4] = {6, 4, 3, 2};
+  for (int q = 0; q < 4 && st == GDSW_OK; ++q) {
+    for (int nt : {128, 256, 512, 992}) {
+      if (c->rec_tpr == 8 && nt < 256) continue;
+      c->rec_stages = cand[q];
+      c->rec_consumers = nt;
+      const size_t shm = size_t(cand[q]) * c->rec_stage_bytes + size_t(c->max_m) * es;
+      int per_sm = 0;
+      st = pipe_occupancy(c, cand[q], shm, &per_sm);
+      if (st != GDSW_OK) break;
+      if (per_sm == 0) continue;
+      st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+      if (st != GDSW_OK) break;
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep)
+        st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+      cudaEventRecord(e1, s);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) { fail(e); break; }
+      if (ms < best) { best = ms; best_s = cand[q]; best_nt = nt; }
+    }
+  }
+  // the unpipelined level-scheduled kernel (factors read through L2), with
+  // 256 to 1024 threads, as further candidates
+  int best_tri = c->tri_threads;
+  for (int tt : {256, 512, 1024}) {
+    if (st != GDSW_OK) break;
+    c->rec_stages = 0;
+    c->tri_threads = tt;
+    st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep)
+      st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { fail(e); break; }
+    if (ms < best) { best = ms; best_s = 0; best_tri = tt; }
+  }
+  c->rec_stages = best_s;
+  c->rec_consumers = best_nt;
+  c->tri_threads = best_s == 0 ? best_tri : 256;
+  if (r) cudaFree(r);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (st == GDSW_OK) st = check_device_errors(c, nullptr);
+  return st;
 }
 
 gdsw_status apply_configure(Ctx* c) {
@@ -662,6 +877,10 @@ gdsw_status apply_configure(Ctx* c) {
   // filled costs as much as a full one), the deepest ring among those
   c->rec_stages = 0;
   c->rec_tpr = c->rec_max_width > 8 ? 8 : 1;
+  // consumer threads: 128 when a level has at most 256 rows to update (two per
+  // thread at most), which halves the instructions that idle threads spend per
+  // level; 256 for wider levels or threads-per-row groups
+  c->rec_consumers = (c->rec_tpr == 1 && c->rec_max_rows <= 256) ? 128 : 256;
   const char* env = getenv("GDSW_LOCAL_PIPE");
   const bool pipe_ok = (env == nullptr || env[0] != '0') && c->rec_stream != nullptr &&
                        c->opt.local_solver != GDSW_LOCAL_EXACT && !jac;
@@ -693,6 +912,16 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(allow_max_dynamic_smem(k_local_dense<double>));
   }
   GDSW_CK(allow_max_dynamic_smem(k_coarse_gemv));
+  if (c->rec_stages > 0 && c->opt.autotune) GDSW_TRY(tune_local(c));
+  // the scatter-add is a grid-stride loop: exactly the CTAs that are resident at once
+  {
+    int dev = 0, sms = kNumSMs, per_sm = 1;
+    GDSW_CK(cudaGetDevice(&dev));
+    GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (c->fp32) GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<float>, 256, 0));
+    else GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<double>, 256, 0));
+    c->combine_grid = std::max(1, per_sm) * sms;
+  }
   return GDSW_OK;
 }
 
@@ -711,12 +940,18 @@ gdsw_status check_device_errors(Ctx* c, cudaStream_t s) {
 }
 
 gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bool rz_dots) {
-  return c->fp32 ? apply_t<float>(c, r, z, s, rz_dots, nullptr)
-                 : apply_t<double>(c, r, z, s, rz_dots, nullptr);
+  return c->fp32 ? apply_t<float>(c, r, z, s, rz_dots, false, nullptr)
+                 : apply_t<double>(c, r, z, s, rz_dots, false, nullptr);
+}
+
+gdsw_status apply_enqueue_gated(Ctx* c, const double* r, double* z, cudaStream_t s) {
+  return c->fp32 ? apply_t<float>(c, r, z, s, false, true, nullptr)
+                 : apply_t<double>(c, r, z, s, false, true, nullptr);
 }
 
 gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms) {
-  GDSW_TRY(c->fp32 ? apply_t<float>(c, r, z, s, false, c->ev) : apply_t<double>(c, r, z, s, false, c->ev));
+  GDSW_TRY(c->fp32 ? apply_t<float>(c, r, z, s, false, false, c->ev)
+                   : apply_t<double>(c, r, z, s, false, false, c->ev));
   GDSW_CK(cudaEventSynchronize(c->ev[4]));
   GDSW_TRY(check_device_errors(c, s));
   for (int q = 0; q < 4; ++q) {

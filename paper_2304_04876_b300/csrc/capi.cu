@@ -31,6 +31,8 @@ void release(Ctx* c) {
   if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
   if (c->bgraph) cudaGraphDestroy(c->bgraph);
   if (c->bgraph_stream) cudaStreamDestroy(c->bgraph_stream);
+  if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
+  if (c->gm_graph) cudaGraphDestroy(c->gm_graph);
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
   if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
@@ -49,7 +51,9 @@ bool valid_options(const gdsw_options* o) {
   return o->local_solver >= 0 && o->local_solver <= 2 && o->trsv >= 0 && o->trsv <= 1 &&
          o->sweeps_factor >= 0 && o->sweeps_trsv >= 0 && o->overlap >= 0 && o->precision >= 0 &&
          o->precision <= 2 && o->krylov >= 0 && o->krylov <= 1 && o->restart >= 1 &&
-         o->maxit >= 1 && o->coarse >= 0 && o->coarse <= 2 && o->tol > 0.0 && o->wait_budget_cycles >= 0;
+         o->maxit >= 1 && o->coarse >= 0 && o->coarse <= 2 && o->tol > 0.0 && o->wait_budget_cycles >= 0 &&
+         o->fill_level >= 0 && (o->fill_level == 0 || o->local_solver != GDSW_LOCAL_EXACT) &&
+         (o->autotune == 0 || o->autotune == 1) && (o->gmres_orth == 0 || o->gmres_orth == 1);
 }
 }  // namespace
 
@@ -100,6 +104,9 @@ void gdsw_default_options(gdsw_options* o) {
   o->restart = 30;
   o->maxit = 2000;
   o->coarse = GDSW_COARSE_GDSW;
+  o->fill_level = 0;
+  o->autotune = 1;
+  o->gmres_orth = GDSW_GMRES_ORTH_CGS2;
   o->flexible = -1;
   o->tol = 1e-8;
   o->wait_budget_cycles = 0;

@@ -25,9 +25,13 @@ int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec) {
       const EllPlan& E = side == 0 ? P.L : P.U;
       if (E.sub_lev.empty()) continue;
       for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
-        const int64_t nr = E.lev_nr[l], K = E.lev_K[l];
-        total += 16 + a16(2 * nr) + a16(nr * vb) + a16(K * nr * vb) + a16(2 * K * nr);
-        ++count;
+        const int K = E.lev_K[l];
+        const int piece = record_piece_rows(E.lev_nr[l], K, P.dpn, size_t(vb));
+        for (int t0 = 0; t0 < E.lev_nr[l]; t0 += piece) {
+          const int64_t nr = std::min(piece, E.lev_nr[l] - t0);
+          total += 16 + a16(2 * nr) + a16(nr * vb) + a16(K * nr * vb) + a16(2 * K * nr);
+          ++count;
+        }
       }
     }
   if (nrec) *nrec = count;

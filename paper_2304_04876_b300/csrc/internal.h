@@ -125,10 +125,23 @@ struct CoarsePlan {
   // Phi^T r work split: chunk q covers rows [chunk_r0, chunk_r1) of block
   // chunk_blk; its partial products go to slots chunk_slot[q] .. + block columns
   std::vector<int> chunk_blk, chunk_r0, chunk_r1, chunk_slot;
+  int n_cta_chunks = 0;                   // the first n_cta_chunks take a CTA each, the rest a warp
   int n_slots = 0;
   // coarse columns of each problem (A0 is block diagonal over problems)
   std::vector<int> prob_c0;               // nprob+1
 };
+
+// Rows per record when a level of nr rows and width K is split so that one
+// record (header, rows, inverse diagonal, values, columns; vb bytes per value)
+// stays within kRecordCap bytes; a multiple of the node group g.
+constexpr size_t kRecordCap = 32 * 1024;
+inline int record_piece_rows(int nr, int K, int g, size_t vb) {
+  const size_t per_row = 2 + vb + size_t(K) * (vb + 2);
+  size_t rows = (kRecordCap - 80) / per_row;
+  rows = rows / size_t(g) * size_t(g);
+  if (rows < size_t(g)) rows = g;
+  return rows >= size_t(nr) ? nr : static_cast<int>(rows);
+}
 
 // Device bytes of a handle built from this plan and of the setup's scratch
 // (upper bounds; host work only).
@@ -158,6 +171,7 @@ struct EllDev {
   const uint16_t* col;
   const T* val;
   const T* dinv;
+  int grp;                  // rows per node, solved in order by one thread
 };
 
 // Scalars of the Krylov loop, in device memory.  Reductions write partial sums
@@ -170,7 +184,7 @@ struct KrylovScalars {
   double tol2;                   // tol^2 * ||b||^2
   int iter, done, maxit, flexible;
   int bad;                       // NaN / Inf seen
-  int pad;
+  int gm_mode;                   // GMRES: 1 = one Gram-Schmidt pass, 2 = a second pass
   unsigned int ticket[8];        // last-block reduction counters
 };
 
@@ -229,6 +243,9 @@ struct Ctx {
   int rec_stages = 0;                // ring depth chosen at setup (0 = not used)
   int rec_max_width = 0;             // widest level (off-diagonal entries per row)
   int rec_tpr = 1;                   // threads per row in the pipelined solve
+  int rec_max_rows = 0;              // most rows in one level
+  int rec_consumers = 256;           // consumer threads of the pipelined solve
+  int tri_threads = 256;             // threads of the unpipelined level / Jacobi solve
   int* derr = nullptr;               // device error flags (bounded waits that ran out)
   long long wait_cycles = 0;         // bound on each device-side wait, SM clock cycles
   // exact local solver: dense inverses
@@ -244,12 +261,14 @@ struct Ctx {
   int* pull_ptr = nullptr; int* pull_pos = nullptr;
   int* pos_blk = nullptr;
   int* chunk_blk = nullptr; int* chunk_r0 = nullptr; int* chunk_r1 = nullptr; int* chunk_slot = nullptr;
-  int n_chunks = 0;
+  int n_chunks = 0, n_cta_chunks = 0;
+  int combine_grid = 0;              // resident CTAs of the scatter-add (grid-stride)
   int max_bcols = 0;
   int n_slots = 0;
   double* partial = nullptr;     // per (block, column) slot
   double* cvec = nullptr;
   double* yvec = nullptr;
+  float* yvec32 = nullptr;           // A0^-1 c rounded once for the FP32 scatter (n0)
   double* A0inv = nullptr;        // one dense block per problem
   int* coarse_prob = nullptr;     // problem of each coarse column
   int* prob_c0 = nullptr;         // coarse column range of each problem
@@ -267,6 +286,10 @@ struct Ctx {
   double* V = nullptr;           // (restart+1) x n
   double* Zk = nullptr;          // restart x n (right-preconditioned directions)
   double* hcol = nullptr;        // restart+2 doubles
+  double* gm = nullptr;          // GMRES state on the device (GmresLayout)
+  cudaGraphExec_t gm_exec = nullptr;  // one restart cycle of GMRES
+  cudaGraph_t gm_graph = nullptr;
+  double gm_keep = 1e-4;         // second Gram-Schmidt pass when ||w - V h||^2 < gm_keep (w, w)
   // graphs
   cudaGraph_t pcg_graph = nullptr;
   cudaGraphExec_t pcg_exec = nullptr;
@@ -323,6 +346,8 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
 // (r, z_new) and (r, z_old) into the Krylov scalars (z_old read before it is
 // overwritten).  Kernels return at once when ks->done is set.
 gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bool rz_dots);
+// The apply with every kernel gated on the Krylov stop flag (no dots).
+gdsw_status apply_enqueue_gated(Ctx* c, const double* r, double* z, cudaStream_t s);
 gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms);
 gdsw_status check_device_errors(Ctx* c, cudaStream_t s);
 // krylov.cu

@@ -178,36 +178,145 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, const double* __re
 // ---- GMRES helpers -------------------------------------------------------
 
 // h[j] = (V_j, w) for j < k (one CTA row of partials per j), CGS.
-__global__ void __launch_bounds__(kThreads) k_multidot(int n, int k, const double* __restrict__ V,
-                                                       const double* __restrict__ w,
-                                                       double* __restrict__ red) {
+// ---- single-reduce GMRES (device-resident Arnoldi and Givens) ----
+// Layout of the GMRES state in one device array of doubles (restart m):
+// H (m+1) x m row-major | cs m | sn m | g m+1 | h1 m+2 | h2 m+2 | beta 2.
+struct GmLayout {
+  int m;
+  __host__ __device__ explicit GmLayout(int m_) : m(m_) {}
+  __host__ __device__ int cs() const { return (m + 1) * m; }
+  __host__ __device__ int sn() const { return cs() + m; }
+  __host__ __device__ int g() const { return sn() + m; }
+  __host__ __device__ int h1() const { return g() + m + 1; }
+  __host__ __device__ int h2() const { return h1() + m + 2; }
+  __host__ __device__ int beta() const { return h2() + m + 2; }
+  __host__ __device__ int total() const { return beta() + 2; }
+};
+
+// Partial sums of (V_i, w) for the k basis vectors and of (w, w) (slot k), in
+// one pass over w: the single global reduction of an Arnoldi step.  Columns
+// go 8 at a time.  Gated on the stop flag and, for the second pass, on mode 2.
+__global__ void __launch_bounds__(kThreads) k_gs_dots(int n, int k, const double* __restrict__ V,
+                                                      const double* __restrict__ w,
+                                                      double* __restrict__ red,
+                                                      const KrylovScalars* __restrict__ ks, int need_mode) {
   __shared__ double sh[32];
-  for (int j = 0; j < k; ++j) {
-    const double* v = V + int64_t(j) * n;
-    double acc = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += v[i] * w[i];
-    const double t = block_sum(acc, sh);
-    if (threadIdx.x == 0) red[int64_t(j) * gridDim.x + blockIdx.x] = t;
+  if (ks->done || (need_mode != 0 && ks->gm_mode != need_mode)) return;
+  for (int c0 = 0; c0 <= k; c0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int col = c0 + u;
+        if (col < k) acc[u] = fma(V[int64_t(col) * n + i], wi, acc[u]);
+        else if (col == k) acc[u] = fma(wi, wi, acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (c0 + u <= k) {
+        const double t = block_sum(acc[u], sh);
+        if (threadIdx.x == 0) red[int64_t(c0 + u) * gridDim.x + blockIdx.x] = t;
+      }
+    }
   }
 }
 
-__global__ void k_reduce_rows(int k, int parts, const double* __restrict__ red, double* __restrict__ out,
-                              int accumulate) {
+// h[j] = the sum of the partials of dot j (one CTA per dot, fixed order).
+__global__ void k_gs_reduce(int parts, const double* __restrict__ red, double* __restrict__ h,
+                            const KrylovScalars* __restrict__ ks, int need_mode) {
   __shared__ double sh[32];
-  const int j = blockIdx.x;
-  if (j >= k) return;
-  const double s = sum_partials(red + int64_t(j) * parts, parts, sh);
-  if (threadIdx.x == 0) out[j] = accumulate ? out[j] + s : s;
+  if (ks->done || (need_mode != 0 && ks->gm_mode != need_mode)) return;
+  const double v = sum_partials(red + int64_t(blockIdx.x) * parts, parts, sh);
+  if (threadIdx.x == 0) h[blockIdx.x] = v;
 }
 
-// w -= V h (k columns)
-__global__ void k_subtract_basis(int n, int k, const double* __restrict__ V, const double* __restrict__ h,
-                                 double* __restrict__ w) {
+// After the first pass: ||w - V h||^2 = (w, w) - ||h||^2 when V is
+// orthonormal.  If that keeps less than `keep` of (w, w) the subtraction
+// cancels too much for the formula, and a second pass (mode 2) follows;
+// keep > 1 asks for the second pass at every step (CGS2).
+__global__ void k_gs_norm1(int k, const double* __restrict__ h1, double* __restrict__ beta,
+                           KrylovScalars* ks, double keep) {
+  if (threadIdx.x != 0 || ks->done) return;
+  double sq = 0.0;
+  for (int i = 0; i < k; ++i) sq = fma(h1[i], h1[i], sq);
+  const double ww = h1[k], b2 = ww - sq;
+  if (b2 > keep * ww) {
+    ks->gm_mode = 1;
+    beta[0] = sqrt(b2);
+  } else {
+    ks->gm_mode = 2;
+    beta[0] = 0.0;
+  }
+}
+
+__global__ void k_gs_norm2(int k, const double* __restrict__ h2, double* __restrict__ beta, KrylovScalars* ks) {
+  if (threadIdx.x != 0 || ks->done || ks->gm_mode != 2) return;
+  double sq = 0.0;
+  for (int i = 0; i < k; ++i) sq = fma(h2[i], h2[i], sq);
+  const double b2 = h2[k] - sq;
+  beta[1] = b2 > 0.0 ? sqrt(b2) : 0.0;
+}
+
+// w -= V h (k columns); the pass that completes the orthogonalisation also
+// divides by beta (a zero beta, an exact breakdown, leaves w unscaled).
+__global__ void __launch_bounds__(kThreads) k_gs_orth(int n, int k, const double* __restrict__ V,
+                                                      const double* __restrict__ h,
+                                                      const double* __restrict__ beta, double* __restrict__ w,
+                                                      const KrylovScalars* __restrict__ ks, int pass) {
+  if (ks->done) return;
+  const int mode = ks->gm_mode;
+  if (pass == 2 && mode != 2) return;
+  const bool last = pass == 2 || mode == 1;
+  const double b = last ? beta[pass - 1] : 1.0;
+  const double inv = b > 0.0 ? 1.0 / b : 1.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc = w[i];
-    for (int j = 0; j < k; ++j) acc -= h[j] * V[int64_t(j) * n + i];
-    w[i] = acc;
+    for (int j = 0; j < k; ++j) acc = fma(-h[j], V[int64_t(j) * n + i], acc);
+    w[i] = last ? acc * inv : acc;
   }
+}
+
+// Column j of the Hessenberg matrix (the Gram-Schmidt coefficients of both
+// passes and beta), the earlier rotations applied to it, the new rotation,
+// and the least-squares residual |g_{j+1}|, which ends the cycle (and the
+// solve) when it is at most tol ||b||, or at maxit, or on breakdown.
+__global__ void k_givens(int j, int m, double* __restrict__ gm, KrylovScalars* ks) {
+  if (threadIdx.x != 0 || ks->done) return;
+  const GmLayout L(m);
+  double* H = gm;
+  double* cs = gm + L.cs();
+  double* sn = gm + L.sn();
+  double* g = gm + L.g();
+  const double* h1 = gm + L.h1();
+  const double* h2 = gm + L.h2();
+  const bool two = ks->gm_mode == 2;
+  for (int i = 0; i <= j; ++i) H[i * m + j] = two ? h1[i] + h2[i] : h1[i];
+  const double hn = gm[L.beta() + (two ? 1 : 0)];
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * m + j], b = H[(i + 1) * m + j];
+    H[i * m + j] = cs[i] * a + sn[i] * b;
+    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+  }
+  const double d = H[j * m + j];
+  const double den = hypot(d, hn);
+  if (den == 0.0) {                      // singular: stop, the host sees it as not converged
+    ks->bad = 1;
+    ks->done = 1;
+    return;
+  }
+  cs[j] = d / den;
+  sn[j] = hn / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  ks->iter += 1;
+  if (!isfinite(g[j + 1])) ks->bad = 1;
+  if (!(g[j + 1] * g[j + 1] > ks->tol2) || ks->iter >= ks->maxit || hn == 0.0 || ks->bad) ks->done = 1;
 }
 
 // b = a * (*scal); a and b may be the same vector
@@ -310,6 +419,8 @@ gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s) {
   return launch_spmv(c, x, y, s, nullptr);
 }
 
+gdsw_status gmres_cycle(Ctx* c, cudaStream_t s);
+
 gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   const int n = c->n;
   c->red_grid = kNumSMs * 8;
@@ -333,6 +444,7 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
     GDSW_TRY(dalloc(c, &c->V, size_t(m + 1) * n));
     GDSW_TRY(dalloc(c, &c->Zk, size_t(m) * n));
     GDSW_TRY(dalloc(c, &c->hcol, m + 2));
+    GDSW_TRY(dalloc(c, &c->gm, GmLayout(m).total()));
   }
   for (int q = 0; q < 8; ++q) GDSW_CK(cudaEventCreate(&c->ev[q]));
   GDSW_CK(cudaStreamSynchronize(s));
@@ -360,6 +472,16 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
     if (st != GDSW_OK) return st;
     GDSW_CK(e);
     GDSW_CK(cudaGraphInstantiate(&c->pcg_exec, c->pcg_graph, 0));
+  }
+  // one GMRES restart cycle as a graph (the kernels are gated on the stop flag)
+  if (c->opt.krylov == GDSW_KRYLOV_GMRES && use_graph && c->nprob == 1) {
+    if (c->graph_stream == nullptr) GDSW_CK(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    GDSW_CK(cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal));
+    gdsw_status st = gmres_cycle(c, c->graph_stream);
+    cudaError_t e = cudaStreamEndCapture(c->graph_stream, &c->gm_graph);
+    if (st != GDSW_OK) return st;
+    GDSW_CK(e);
+    GDSW_CK(cudaGraphInstantiate(&c->gm_exec, c->gm_graph, 0));
   }
   return GDSW_OK;
 }
@@ -439,21 +561,61 @@ gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
   return GDSW_OK;
 }
 
-// Right-preconditioned restarted GMRES(m): Arnoldi on A M^-1 with classical
-// Gram-Schmidt applied twice (one multi-dot reduction per pass), Givens
-// rotations and the small least-squares problem on the host; the true
-// residual is recomputed at every restart.
+// One restart cycle of GMRES(m): m Arnoldi steps, each z_j = M^-1 v_j,
+// w = A z_j, one fused reduction for V^T w and (w, w), the orthogonalisation
+// (a second pass only when the first cancelled), and the Givens update; every
+// kernel is gated on the stop flag, so the cycle can be enqueued (or captured)
+// whole and ends early on convergence without a host round trip.
+gdsw_status gmres_cycle(Ctx* c, cudaStream_t s) {
+  const int n = c->n;
+  // two passes always (CGS2), or one pass with a second only where the
+  // Pythagorean norm cancels (single reduction per step)
+  c->gm_keep = c->opt.gmres_orth == GDSW_GMRES_ORTH_SINGLE ? 1e-4 : 2.0;
+  const int m = std::max(1, c->opt.restart);
+  const int G = vec_grid(c);
+  const GmLayout L(m);
+  double* h1 = c->gm + L.h1();
+  double* h2 = c->gm + L.h2();
+  double* bt = c->gm + L.beta();
+  for (int j = 0; j < m; ++j) {
+    const int k = j + 1;
+    double* vj = c->V + int64_t(j) * n;
+    double* zj = c->Zk + int64_t(j) * n;
+    double* w = c->V + int64_t(k) * n;
+    GDSW_TRY(apply_enqueue_gated(c, vj, zj, s));
+    GDSW_TRY(launch_spmv(c, zj, w, s, c->ks));
+    k_gs_dots<<<G, kThreads, 0, s>>>(n, k, c->V, w, c->red, c->ks, 0);
+    k_gs_reduce<<<k + 1, kThreads, 0, s>>>(G, c->red, h1, c->ks, 0);
+    k_gs_norm1<<<1, 32, 0, s>>>(k, h1, bt, c->ks, c->gm_keep);
+    k_gs_orth<<<G, kThreads, 0, s>>>(n, k, c->V, h1, bt, w, c->ks, 1);
+    k_gs_dots<<<G, kThreads, 0, s>>>(n, k, c->V, w, c->red, c->ks, 2);
+    k_gs_reduce<<<k + 1, kThreads, 0, s>>>(G, c->red, h2, c->ks, 2);
+    k_gs_norm2<<<1, 32, 0, s>>>(k, h2, bt, c->ks);
+    k_gs_orth<<<G, kThreads, 0, s>>>(n, k, c->V, h2, bt, w, c->ks, 2);
+    k_givens<<<1, 32, 0, s>>>(j, m, c->gm, c->ks);
+    GDSW_CK(cudaGetLastError());
+  }
+  return GDSW_OK;
+}
+
+// Right-preconditioned restarted GMRES(m) (Sec. VII) with the Arnoldi
+// process, the Hessenberg matrix and the Givens rotations on the device: each
+// Gram-Schmidt pass is one fused reduction (V^T w together with (w, w)); two
+// passes (CGS2) by default, or the single-reduce form (one pass, a second
+// only on cancellation).  One host round trip per restart cycle, where the
+// true residual is recomputed and the small triangular system is solved.
 gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s) {
   const double t0 = now_s();
   const int n = c->n;
   const int m = std::max(1, c->opt.restart);
   const int G = vec_grid(c);
+  const GmLayout L(m);
   GDSW_CK(cudaMemcpyAsync(c->b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GDSW_CK(cudaMemcpyAsync(c->x, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   KrylovScalars init = {};
   init.maxit = c->opt.maxit;
   GDSW_CK(cudaMemcpyAsync(c->ks, &init, sizeof(KrylovScalars), cudaMemcpyHostToDevice, s));
-  std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), hv(m + 2);
+  std::vector<double> gmh(L.total());
   int it = 0;
   double bb = 0.0, rr = 0.0;
   bool converged = false;
@@ -474,74 +636,48 @@ gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* inf
     const double tolabs = c->opt.tol * std::sqrt(bb);
     const double beta = std::sqrt(rr);
     if (beta <= tolabs) { converged = true; break; }
-    if (it >= c->opt.maxit || !std::isfinite(beta)) break;
-    // V_0 = r / beta
+    if (it >= c->opt.maxit || !std::isfinite(beta) || c->ks_host->bad) break;
+    // V_0 = r / beta; g = (beta, 0, ...); the cycle's stop flag cleared
     const double inv = 1.0 / beta;
     GDSW_CK(cudaMemcpyAsync(c->hcol, &inv, sizeof(double), cudaMemcpyHostToDevice, s));
     k_scale_copy<<<G, kThreads, 0, s>>>(n, c->r, c->hcol, c->V);
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jdone = 0;
-    for (int j = 0; j < m; ++j) {
-      double* vj = c->V + int64_t(j) * n;
-      double* zj = c->Zk + int64_t(j) * n;
-      double* w = c->V + int64_t(j + 1) * n;
-      GDSW_TRY(apply_enqueue(c, vj, zj, s, false));
-      GDSW_TRY(launch_spmv(c, zj, w, s, nullptr));
-      // two passes of classical Gram-Schmidt
-      std::fill(hv.begin(), hv.end(), 0.0);
-      GDSW_CK(cudaMemsetAsync(c->hcol, 0, sizeof(double) * (m + 2), s));
-      for (int pass = 0; pass < 2; ++pass) {
-        k_multidot<<<G, kThreads, 0, s>>>(n, j + 1, c->V, w, c->red);
-        k_reduce_rows<<<j + 1, kThreads, 0, s>>>(j + 1, G, c->red, c->q, 0);
-        k_subtract_basis<<<G, kThreads, 0, s>>>(n, j + 1, c->V, c->q, w);
-        // accumulate h += pass coefficients (kept on host)
-        std::vector<double> hp(j + 1);
-        GDSW_CK(cudaMemcpyAsync(hp.data(), c->q, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
-        GDSW_CK(cudaStreamSynchronize(s));
-        for (int i = 0; i <= j; ++i) hv[i] += hp[i];
+    std::fill(gmh.begin(), gmh.end(), 0.0);
+    gmh[L.g()] = beta;
+    GDSW_CK(cudaMemcpyAsync(c->gm, gmh.data(), sizeof(double) * L.total(), cudaMemcpyHostToDevice, s));
+    KrylovScalars* kh = c->ks_host;
+    kh->done = 0;
+    kh->iter = it;
+    kh->tol2 = tolabs * tolabs;
+    kh->gm_mode = 1;
+    GDSW_CK(cudaMemcpyAsync(c->ks, kh, sizeof(KrylovScalars), cudaMemcpyHostToDevice, s));
+    if (c->gm_exec != nullptr) GDSW_CK(cudaGraphLaunch(c->gm_exec, s));
+    else GDSW_TRY(gmres_cycle(c, s));
+    GDSW_CK(cudaMemcpyAsync(gmh.data(), c->gm, sizeof(double) * L.total(), cudaMemcpyDeviceToHost, s));
+    GDSW_TRY(read_scalars(c, s));
+    const int jdone = c->ks_host->iter - it;
+    it = c->ks_host->iter;
+    if (jdone > 0) {
+      // y = R^-1 g, x += Z y
+      std::vector<double> yv(jdone);
+      for (int i = jdone - 1; i >= 0; --i) {
+        double v = gmh[L.g() + i];
+        for (int k = i + 1; k < jdone; ++k) v -= gmh[size_t(i) * m + k] * yv[k];
+        yv[i] = v / gmh[size_t(i) * m + i];
       }
-      // ||w||
-      k_multidot<<<G, kThreads, 0, s>>>(n, 1, w, w, c->red);
-      k_reduce_rows<<<1, kThreads, 0, s>>>(1, G, c->red, c->hcol, 0);
-      double ww = 0.0;
-      GDSW_CK(cudaMemcpyAsync(&ww, c->hcol, sizeof(double), cudaMemcpyDeviceToHost, s));
-      GDSW_CK(cudaStreamSynchronize(s));
-      const double hn = std::sqrt(ww);
-      if (hn > 0.0) {
-        const double ih = 1.0 / hn;
-        GDSW_CK(cudaMemcpyAsync(c->hcol, &ih, sizeof(double), cudaMemcpyHostToDevice, s));
-        k_scale_copy<<<G, kThreads, 0, s>>>(n, w, c->hcol, w);
-      }
-      for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] = hv[i];
-      H[size_t(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * H[size_t(i) * m + j] + sn[i] * H[size_t(i + 1) * m + j];
-        H[size_t(i + 1) * m + j] = -sn[i] * H[size_t(i) * m + j] + cs[i] * H[size_t(i + 1) * m + j];
-        H[size_t(i) * m + j] = t;
-      }
-      const double den = std::hypot(H[size_t(j) * m + j], H[size_t(j + 1) * m + j]);
-      cs[j] = H[size_t(j) * m + j] / den;
-      sn[j] = H[size_t(j + 1) * m + j] / den;
-      H[size_t(j) * m + j] = den;
-      H[size_t(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++it;
-      jdone = j + 1;
-      if (std::fabs(g[j + 1]) <= tolabs || it >= c->opt.maxit) break;
+      GDSW_CK(cudaMemcpyAsync(c->hcol, yv.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
+      k_update_x<<<G, kThreads, 0, s>>>(n, jdone, c->Zk, c->hcol, c->x);
+      GDSW_CK(cudaGetLastError());
     }
-    // back substitution and x += Z y
-    std::vector<double> yv(jdone);
-    for (int i = jdone - 1; i >= 0; --i) {
-      double v = g[i];
-      for (int k = i + 1; k < jdone; ++k) v -= H[size_t(i) * m + k] * yv[k];
-      yv[i] = v / H[size_t(i) * m + i];
+    if (c->ks_host->bad || jdone == 0) {
+      // breakdown without progress: recompute the residual once more and stop
+      GDSW_TRY(launch_spmv(c, c->x, c->q, s, nullptr));
+      k_residual<<<G, kThreads, 0, s>>>(n, c->b, c->q, c->r, c->red, c->ks);
+      GDSW_CK(cudaGetLastError());
+      GDSW_TRY(read_scalars(c, s));
+      rr = c->ks_host->rr;
+      converged = std::sqrt(rr) <= tolabs;
+      break;
     }
-    GDSW_CK(cudaMemcpyAsync(c->hcol, yv.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
-    k_update_x<<<G, kThreads, 0, s>>>(n, jdone, c->Zk, c->hcol, c->x);
-    GDSW_CK(cudaGetLastError());
   }
   GDSW_CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GDSW_CK(cudaStreamSynchronize(s));

@@ -45,7 +45,8 @@ __global__ void k_extract_local(const double* __restrict__ val, const int* __res
   }
   __syncthreads();
   for (int e = lm_sub_ent[s] + threadIdx.x; e < lm_sub_ent[s + 1]; e += blockDim.x) {
-    const double a = val[lm_gent[e]];
+    const int g = lm_gent[e];
+    const double a = g >= 0 ? val[g] : 0.0;      // fill of IC(k)/ILU(k) starts at zero
     araw[e] = a;
     at[e] = a * sc[base + lm_row[e]] * sc[base + lm_col[e]];
   }
@@ -821,6 +822,8 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
       std::vector<int> rec_ptr(nsub + 1, 0);
       std::vector<uint32_t> rec_off16, rec_bytes;
+      std::vector<int> rec_lev, rec_t0;            // level and first row of every record
+      std::vector<char> rec_is_L;
       std::vector<uint32_t> valposL(P.L.slots), valposU(P.U.slots), dinvposL(P.sum_m), dinvposU(P.sum_m);
       size_t total = 0;
       for (int pass = 0; pass < 2; ++pass) {      // pass 0 sizes, pass 1 fills
@@ -830,18 +833,30 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
           for (int side = 0; side < 2; ++side) {
             const EllPlan& E = side == 0 ? P.L : P.U;
             for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
-              const size_t nr = E.lev_nr[l], K = E.lev_K[l];
-              const size_t o_l = total + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
-                           o_c = o_v + a16(K * nr * vb), end = o_c + a16(2 * K * nr);
-              if (pass == 1) {
-                rec_off16.push_back(static_cast<uint32_t>(total / 16));
-                rec_bytes.push_back(static_cast<uint32_t>(end - total));
-                uint32_t* dp = side == 0 ? dinvposL.data() : dinvposU.data();
-                uint32_t* vp = side == 0 ? valposL.data() : valposU.data();
-                for (size_t t = 0; t < nr; ++t) dp[E.lev_start[l] + t] = static_cast<uint32_t>((o_d + t * vb) / vb);
-                for (size_t t = 0; t < K * nr; ++t) vp[E.lev_off[l] + t] = static_cast<uint32_t>((o_v + t * vb) / vb);
+              // a wide level becomes several records (rows are independent
+              // within a level, node groups kept whole)
+              const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
+              const size_t piece = record_piece_rows(E.lev_nr[l], E.lev_K[l], P.dpn, vb);
+              for (size_t t0 = 0; t0 < L_nr; t0 += piece) {
+                const size_t nr = std::min(piece, L_nr - t0);
+                const size_t o_l = total + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
+                             o_c = o_v + a16(K * nr * vb), end = o_c + a16(2 * K * nr);
+                if (pass == 1) {
+                  rec_off16.push_back(static_cast<uint32_t>(total / 16));
+                  rec_bytes.push_back(static_cast<uint32_t>(end - total));
+                  rec_lev.push_back(l);
+                  rec_t0.push_back(static_cast<int>(t0));
+                  rec_is_L.push_back(side == 0);
+                  uint32_t* dp = side == 0 ? dinvposL.data() : dinvposU.data();
+                  uint32_t* vp = side == 0 ? valposL.data() : valposU.data();
+                  for (size_t t = 0; t < nr; ++t)
+                    dp[E.lev_start[l] + t0 + t] = static_cast<uint32_t>((o_d + t * vb) / vb);
+                  for (size_t k = 0; k < K; ++k)
+                    for (size_t t = 0; t < nr; ++t)
+                      vp[E.lev_off[l] + k * L_nr + t0 + t] = static_cast<uint32_t>((o_v + (k * nr + t) * vb) / vb);
+                }
+                total = end;
               }
-              total = end;
             }
           }
           if (pass == 1) rec_ptr[q + 1] = static_cast<int>(rec_off16.size());
@@ -852,23 +867,23 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       }
       std::vector<uint8_t> host(total, 0);
       size_t stage = 16;
-      for (int q = 0, rr = 0; q < nsub; ++q) {
-        for (int side = 0; side < 2; ++side) {
-          const EllPlan& E = side == 0 ? P.L : P.U;
-          for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l, ++rr) {
-            const size_t nr = E.lev_nr[l], K = E.lev_K[l];
-            const size_t base = size_t(rec_off16[rr]) * 16;
-            const size_t o_l = base + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
-                         o_c = o_v + a16(K * nr * vb);
-            // header: rows, width, and the byte offsets of the values and columns
-            const int hdr[4] = {static_cast<int>(nr), static_cast<int>(K), static_cast<int>(o_v - base),
-                                static_cast<int>(o_c - base)};
-            std::memcpy(&host[base], hdr, 16);
-            std::memcpy(&host[o_l], &E.lrows[E.lev_start[l]], 2 * nr);
-            std::memcpy(&host[o_c], &E.col[E.lev_off[l]], 2 * K * nr);
-            stage = std::max<size_t>(stage, rec_bytes[rr]);
-          }
-        }
+      for (size_t rr = 0; rr < rec_off16.size(); ++rr) {
+        const EllPlan& E = rec_is_L[rr] ? P.L : P.U;
+        const int l = rec_lev[rr];
+        const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
+        const size_t t0 = rec_t0[rr];
+        const size_t nr = std::min(size_t(record_piece_rows(E.lev_nr[l], E.lev_K[l], P.dpn, vb)), L_nr - t0);
+        const size_t base = size_t(rec_off16[rr]) * 16;
+        const size_t o_l = base + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
+                     o_c = o_v + a16(K * nr * vb);
+        // header: rows, width, and the byte offsets of the values and columns
+        const int hdr[4] = {static_cast<int>(nr), static_cast<int>(K), static_cast<int>(o_v - base),
+                            static_cast<int>(o_c - base)};
+        std::memcpy(&host[base], hdr, 16);
+        std::memcpy(&host[o_l], &E.lrows[E.lev_start[l] + t0], 2 * nr);
+        for (size_t k = 0; k < K; ++k)
+          std::memcpy(&host[o_c + 2 * k * nr], &E.col[E.lev_off[l] + k * L_nr + t0], 2 * nr);
+        stage = std::max<size_t>(stage, rec_bytes[rr]);
       }
       uint8_t* d_stream;
       GDSW_TRY(upload(c, &d_stream, host, s));
@@ -881,6 +896,10 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       for (int kk : P.L.lev_K) maxK = std::max(maxK, kk);
       for (int kk : P.U.lev_K) maxK = std::max(maxK, kk);
       c->rec_max_width = maxK;
+      int maxR = 0;
+      for (int nr : P.L.lev_nr) maxR = std::max(maxR, nr);
+      for (int nr : P.U.lev_nr) maxR = std::max(maxR, nr);
+      c->rec_max_rows = maxR;
       c->rec_total_bytes = static_cast<int64_t>(total);
       for (int side = 0; side < 2; ++side) {
         const EllPlan& E = side == 0 ? P.L : P.U;
@@ -965,6 +984,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   GDSW_TRY(upload(c, &c->chunk_r1, C.chunk_r1, s));
   GDSW_TRY(upload(c, &c->chunk_slot, C.chunk_slot, s));
   c->n_chunks = static_cast<int>(C.chunk_blk.size());
+  c->n_cta_chunks = C.n_cta_chunks;
   c->n_slots = C.n_slots;
   c->stats.nnz_phi = C.phi_len;
   c->max_bcols = 0;
@@ -972,6 +992,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   GDSW_TRY(dalloc(c, &c->partial, std::max(1, c->n_slots)));
   GDSW_TRY(dalloc(c, &c->cvec, std::max(1, C.n0)));
   GDSW_TRY(dalloc(c, &c->yvec, std::max(1, C.n0)));
+  if (c->fp32) GDSW_TRY(dalloc(c, &c->yvec32, std::max(1, C.n0)));
   double* phi64 = nullptr;
   if (C.n0 > 0) {
     GDSW_TRY(sc.get(&phi64, C.phi_len));

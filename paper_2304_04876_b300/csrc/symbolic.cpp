@@ -14,6 +14,8 @@
 //  * once the component ranks are known, the layout of the GDSW basis (Eq. 2)
 //    as dense per-block column panels.
 #include <algorithm>
+#include <climits>
+#include <queue>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -28,37 +30,40 @@ namespace {
 
 bool fits_i32(int64_t v) { return v >= 0 && v < (int64_t(1) << 31); }
 
-// Levels of a triangle of one subdomain's local CSR.  lower: entries j < i, in
-// increasing row order; upper: entries j > i, in decreasing row order.
+// Levels of a triangle of one subdomain's local CSR, by node: the dpn rows of
+// a node (consecutive local rows) form one group that a single thread (or
+// thread group) updates in order, so only couplings between different nodes
+// create levels.  lower: entries j < i, rows of a node in increasing order;
+// upper: entries j > i, rows of a node in decreasing order.
 void build_ell(const Plan& P, int s, bool lower, int local_solver, EllPlan* E) {
   const int base = P.om_ptr[s];
   const int m = P.om_ptr[s + 1] - base;
-  std::vector<int> lev(m, 0);
+  const int G = P.dpn;
+  const int ng = m / G;
+  std::vector<int> glev(ng, 0);
   int nlev = 0;
   auto off_entries = [&](int i, int& first, int& last) {
     const int r0 = P.lm_rowptr[base + i], r1 = P.lm_rowptr[base + i + 1];
     const int d = P.lm_diag[base + i];
     if (lower) { first = r0; last = d; } else { first = d + 1; last = r1; }
   };
-  if (lower) {
-    for (int i = 0; i < m; ++i) {
+  auto group_level = [&](int g) {
+    int l = 0;
+    for (int d = 0; d < G; ++d) {
       int a, b;
-      off_entries(i, a, b);
-      int l = 0;
-      for (int e = a; e < b; ++e) l = std::max(l, lev[P.lm_col[e]] + 1);
-      lev[i] = l;
-      nlev = std::max(nlev, l + 1);
+      off_entries(g * G + d, a, b);
+      for (int e = a; e < b; ++e) {
+        const int gj = P.lm_col[e] / G;
+        if (gj != g) l = std::max(l, glev[gj] + 1);
+      }
     }
-  } else {
-    for (int i = m - 1; i >= 0; --i) {
-      int a, b;
-      off_entries(i, a, b);
-      int l = 0;
-      for (int e = a; e < b; ++e) l = std::max(l, lev[P.lm_col[e]] + 1);
-      lev[i] = l;
-      nlev = std::max(nlev, l + 1);
-    }
-  }
+    glev[g] = l;
+    nlev = std::max(nlev, l + 1);
+  };
+  if (lower) for (int g = 0; g < ng; ++g) group_level(g);
+  else for (int g = ng - 1; g >= 0; --g) group_level(g);
+  std::vector<int> lev(m);
+  for (int i = 0; i < m; ++i) lev[i] = glev[i / G];
   if (m == 0) nlev = 0;
   // bucket rows by level, ascending row inside a level
   std::vector<int> cnt(nlev + 1, 0);
@@ -66,8 +71,10 @@ void build_ell(const Plan& P, int s, bool lower, int local_solver, EllPlan* E) {
   for (int l = 0; l < nlev; ++l) cnt[l + 1] += cnt[l];
   std::vector<int> order(m);
   {
+    // rows of one node stay together, in the order they are solved
     std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    for (int i = 0; i < m; ++i) order[pos[lev[i]]++] = i;
+    for (int g = 0; g < ng; ++g)
+      for (int d = 0; d < G; ++d) order[pos[glev[g]]++] = g * G + (lower ? d : G - 1 - d);
   }
   E->max_levels = std::max(E->max_levels, nlev);
   for (int l = 0; l < nlev; ++l) {
@@ -112,6 +119,77 @@ void build_ell(const Plan& P, int s, bool lower, int local_solver, EllPlan* E) {
 }
 
 }  // namespace
+
+// Level-of-fill pattern of every local matrix (ILU(k), Sec. V-B): entries of
+// A_s have level 0; eliminating row i with pivot p (increasing column order,
+// fill included) gives (i, j), j > p, the level lev(i,p) + lev(p,j) + 1, with
+// lev(p, j) the final level of row p; entries of level <= k are kept.  Fill
+// entries get lm_gent = -1 (value zero before the factorisation sweeps).
+gdsw_status add_level_fill(Plan* P, int k) {
+  const int nsub = P->nsub;
+  std::vector<int> nrowptr(P->sum_m + 1, 0), ncol, ngent, ndiag(P->sum_m, -1), nsub_ent(nsub + 1, 0);
+  std::vector<uint16_t> nrow;
+  ncol.reserve(P->lm_col.size() * 2);
+  ngent.reserve(P->lm_col.size() * 2);
+  nrow.reserve(P->lm_col.size() * 2);
+  constexpr int kNone = INT32_MAX;
+  std::vector<int> lev(P->max_m, kNone), orig(P->max_m, -1);
+  int64_t ent = 0;
+  for (int s = 0; s < nsub; ++s) {
+    const int base = P->om_ptr[s], m = P->om_ptr[s + 1] - base;
+    std::vector<std::vector<std::pair<int, int>>> upper(m);   // finished rows: (column > row, level)
+    std::vector<int> cols;
+    for (int i = 0; i < m; ++i) {
+      cols.clear();
+      std::priority_queue<int, std::vector<int>, std::greater<int>> heap;
+      for (int e = P->lm_rowptr[base + i]; e < P->lm_rowptr[base + i + 1]; ++e) {
+        const int j = P->lm_col[e];
+        lev[j] = 0;
+        orig[j] = P->lm_gent[e];
+        cols.push_back(j);
+        if (j < i) heap.push(j);
+      }
+      while (!heap.empty()) {
+        const int piv = heap.top();
+        heap.pop();
+        const int lp = lev[piv];
+        for (const auto& jl : upper[piv]) {
+          const int nl = lp + jl.second + 1;
+          if (nl > k) continue;
+          const int j = jl.first;
+          if (lev[j] == kNone) {
+            lev[j] = nl;
+            cols.push_back(j);
+            if (j < i) heap.push(j);
+          } else if (nl < lev[j]) {
+            lev[j] = nl;
+          }
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      for (int j : cols) {
+        if (j == i) ndiag[base + i] = static_cast<int>(ent);
+        if (j > i) upper[i].push_back({j, lev[j]});
+        ncol.push_back(j);
+        nrow.push_back(static_cast<uint16_t>(i));
+        ngent.push_back(orig[j]);
+        ++ent;
+        lev[j] = kNone;
+        orig[j] = -1;
+      }
+      if (!fits_i32(ent)) { set_error("local factors with fill too large"); return GDSW_ERR_UNSUPPORTED; }
+      nrowptr[base + i + 1] = static_cast<int>(ent);
+    }
+    nsub_ent[s + 1] = static_cast<int>(ent);
+  }
+  P->lm_rowptr.swap(nrowptr);
+  P->lm_col.swap(ncol);
+  P->lm_row.swap(nrow);
+  P->lm_gent.swap(ngent);
+  P->lm_diag.swap(ndiag);
+  P->lm_sub_ent.swap(nsub_ent);
+  return GDSW_OK;
+}
 
 gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
                        bool need_levels, Plan* P) {
@@ -399,6 +477,8 @@ gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw
       P->int_bw[s] = bw;
     }
   }
+  // IC(k)/ILU(k): widen the local patterns by the level-k fill
+  if (opt->fill_level > 0 && opt->local_solver != GDSW_LOCAL_EXACT) GDSW_TRY(add_level_fill(P, opt->fill_level));
   // transposed positions (structural symmetry is required)
   P->lm_tpos.assign(P->lm_col.size(), -1);
   for (int s = 0; s < nsub; ++s) {
@@ -494,7 +574,7 @@ gdsw_status merge_plans(std::vector<Plan>& parts, Plan* M) {
     for (int q = 1; q < static_cast<int>(p.lm_rowptr.size()); ++q) o.lm_rowptr.push_back(p.lm_rowptr[q] + eoff);
     o.lm_col.insert(o.lm_col.end(), p.lm_col.begin(), p.lm_col.end());
     o.lm_row.insert(o.lm_row.end(), p.lm_row.begin(), p.lm_row.end());
-    add(o.lm_gent, p.lm_gent, goff, false);
+    add(o.lm_gent, p.lm_gent, goff, true);
     add(o.lm_tpos, p.lm_tpos, eoff, false);
     add(o.lm_diag, p.lm_diag, eoff, false);
     for (int q = 1; q < static_cast<int>(p.lm_sub_ent.size()); ++q) o.lm_sub_ent.push_back(p.lm_sub_ent[q] + eoff);
@@ -654,7 +734,8 @@ gdsw_status build_coarse_plan(const Plan& P, const SupportPlan& S, const std::ve
       C->dof_blkrow[C->brow_dof[q]] = q - C->brow_ptr[b];
     }
   // Phi^T r chunks of at most kChunkRows rows (4 per thread of a 256-thread CTA); partial slots per (chunk, column)
-  constexpr int kChunkRows = 1024;
+  int kChunkRows = 1024;
+  if (const char* e = std::getenv("GDSW_PHIT_CHUNK")) kChunkRows = std::max(256, std::atoi(e));
   C->chunk_blk.clear(); C->chunk_r0.clear(); C->chunk_r1.clear(); C->chunk_slot.clear();
   int nslot = 0;
   std::vector<std::vector<int>> col_slots(n0);
@@ -672,6 +753,24 @@ gdsw_status build_coarse_plan(const Plan& P, const SupportPlan& S, const std::ve
     }
   }
   C->n_slots = nslot;
+  // processing order: chunks of more than kWarpRows rows first (a CTA each),
+  // then the small ones (a warp each); slots keep the (block, chunk) order, so
+  // the order of the sums does not change
+  {
+    constexpr int kWarpRows = 256;
+    std::vector<int> order(C->chunk_blk.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = static_cast<int>(q);
+    std::stable_partition(order.begin(), order.end(),
+                          [&](int q) { return C->chunk_r1[q] - C->chunk_r0[q] > kWarpRows; });
+    C->n_cta_chunks = 0;
+    for (int q : order) C->n_cta_chunks += C->chunk_r1[q] - C->chunk_r0[q] > kWarpRows;
+    auto permute = [&](std::vector<int>& v) {
+      std::vector<int> t(v.size());
+      for (size_t q = 0; q < order.size(); ++q) t[q] = v[order[q]];
+      v.swap(t);
+    };
+    permute(C->chunk_blk); permute(C->chunk_r0); permute(C->chunk_r1); permute(C->chunk_slot);
+  }
   // slots of every coarse column in ascending (block, chunk) order
   C->cs_ptr.assign(n0 + 1, 0);
   C->cs_idx.clear();

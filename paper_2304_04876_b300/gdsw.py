@@ -22,6 +22,7 @@ TRSV = {"levelsched": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2}
 KRYLOV = {"pcg": 0, "gmres": 1}
 COARSE = {"gdsw": 0, "none": 1, "rgdsw": 2}
+GMRES_ORTH = {"cgs2": 0, "single": 1}
 
 
 class CSRStruct(C.Structure):
@@ -37,7 +38,8 @@ class Options(C.Structure):
     _fields_ = [("local_solver", C.c_int32), ("trsv", C.c_int32), ("sweeps_factor", C.c_int32),
                 ("sweeps_trsv", C.c_int32), ("overlap", C.c_int32), ("precision", C.c_int32),
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32),
-                ("coarse", C.c_int32), ("flexible", C.c_int32), ("tol", C.c_double),
+                ("coarse", C.c_int32), ("fill_level", C.c_int32), ("autotune", C.c_int32),
+                ("gmres_orth", C.c_int32), ("flexible", C.c_int32), ("tol", C.c_double),
                 ("wait_budget_cycles", C.c_int64)]
 
 
@@ -124,7 +126,7 @@ def make_options(**kw) -> Options:
     o = default_options()
     for k, v in kw.items():
         table = {"local_solver": LOCAL, "trsv": TRSV, "precision": PRECISION, "krylov": KRYLOV,
-                 "coarse": COARSE}.get(k)
+                 "coarse": COARSE, "gmres_orth": GMRES_ORTH}.get(k)
         if table is not None and isinstance(v, str):
             v = table[v]
         setattr(o, k, v)

@@ -10,10 +10,11 @@ TRSV = {"levelsched": O.LEVELSCHED, "jacobi": O.JACOBI}
 
 
 def oracle_for(prob, local="ic0", trsv="levelsched", sweeps_factor=3, sweeps_trsv=5, overlap=1,
-               coarse="gdsw"):
+               coarse="gdsw", fill_level=0):
     return O.GDSW(prob.A, prob.part, prob.Z, local=LOCAL[local], trsv=TRSV[trsv],
                   sweeps_factor=sweeps_factor, sweeps_trsv=sweeps_trsv, overlap=overlap,
-                  coarse=(coarse != "none"), coarse_variant=("rgdsw" if coarse == "rgdsw" else "gdsw"))
+                  coarse=(coarse != "none"), coarse_variant=("rgdsw" if coarse == "rgdsw" else "gdsw"),
+                  fill_level=fill_level)
 
 
 def gpu_handle(prob, **opts):

@@ -38,6 +38,7 @@ def test_default_options_and_status_strings(lib):
     o = G.default_options()
     assert (o.local_solver, o.trsv, o.sweeps_factor, o.sweeps_trsv, o.overlap) == (1, 0, 3, 5, 1)
     assert (o.precision, o.krylov, o.restart, o.maxit, o.coarse, o.flexible) == (0, 0, 30, 2000, 0, -1)
+    assert o.fill_level == 0 and o.autotune == 1 and o.gmres_orth == 0
     assert o.tol == 1e-8 and o.wait_budget_cycles == 0
     for s in range(8):
         assert lib.gdsw_status_string(s)
@@ -84,6 +85,8 @@ def test_rejects_malformed_input_on_host(lib):
     # invalid options
     _expect(G.ERR_INVALID_ARG, A, part, local_solver=7)
     _expect(G.ERR_INVALID_ARG, A, part, tol=0.0)
+    _expect(G.ERR_INVALID_ARG, A, part, local_solver="exact", fill_level=1)
+    _expect(G.ERR_INVALID_ARG, A, part, fill_level=-1)
 
 
 def test_structs_match_header(lib):
@@ -93,7 +96,7 @@ def test_structs_match_header(lib):
     body = body[:body.index("} gdsw_options;")]
     fields = re.findall(r"(?:int32_t|int64_t|double)\s+(\w+);", body)
     assert fields == [f for f, _ in G.Options._fields_]
-    assert C.sizeof(G.Options) == 11 * 4 + 4 + 8 + 8
+    assert C.sizeof(G.Options) == 14 * 4 + 8 + 8
     assert C.sizeof(G.Stats) == 19 * 8 + 9 * 8
 
 
@@ -133,6 +136,9 @@ def test_bytes_required_from_the_symbolic_phase(lib):
     rg, _ = G.bytes_required(e.A, e.part, e.Z, local_solver="ilu0")
     rr, _ = G.bytes_required(e.A, e.part, e.Z, local_solver="ilu0", coarse="rgdsw")
     assert rr < rg
+    # level-1 fill widens the local factors
+    rf, _ = G.bytes_required(small.A, small.part, fill_level=1)
+    assert rf > r_s
     # GMRES(30) adds 61 basis vectors of n doubles
     rgm, _ = G.bytes_required(e.A, e.part, e.Z, local_solver="ilu0", krylov="gmres")
     assert rgm - rg >= 61 * 8 * e.A.n

@@ -54,6 +54,11 @@ APPLY_CASES = [
     ("rgdsw_diffusion10_ic0", _diffusion, dict(local="ic0", coarse="rgdsw")),
     ("rgdsw_elast6_ilu0", lambda: P.elasticity_problem(6, 2), dict(local="ilu0", coarse="rgdsw")),
     ("rgdsw_two_blocks", lambda: P.poisson_problem(8, 4), dict(local="exact", coarse="rgdsw")),
+    ("poisson12_ic1", lambda: P.poisson_problem(12, 4), dict(local="ic0", fill_level=1)),
+    ("poisson12_ic2_jac", lambda: P.poisson_problem(12, 4), dict(local="ic0", trsv="jacobi", fill_level=2)),
+    ("ragged13_ilu1", _ragged, dict(local="ilu0", fill_level=1)),
+    ("diffusion10_ic2", _diffusion, dict(local="ic0", fill_level=2)),
+    ("elast6_ilu1", lambda: P.elasticity_problem(6, 2), dict(local="ilu0", fill_level=1)),
 ]
 
 
@@ -64,6 +69,9 @@ def test_apply_matches_oracle(name, make, opts):
     h = gpu_handle(prob, **{("local_solver" if k == "local" else k): v for k, v in opts.items()})
     st = h.stats()
     assert st["n0"] == M.n0 and st["sum_omega"] == sum(len(o) for o in M.omega)
+    if opts.get("local", "ic0") != "exact":
+        # the factor pattern (fill included) is the oracle's, entry for entry in count
+        assert st["nnz_L"] == sum(f[1].nnz for f in M.factors)
     for seed in range(3):
         r = np.random.default_rng(seed).uniform(-1, 1, prob.A.n)
         z = gpu_apply(h, r)
@@ -108,6 +116,8 @@ PCG_CASES = [
     ("elast6_exact", lambda: P.elasticity_problem(6, 2), dict(local="exact")),
     ("rgdsw_poisson12_ic0", lambda: P.poisson_problem(12, 4), dict(local="ic0", coarse="rgdsw")),
     ("rgdsw_elast6_exact", lambda: P.elasticity_problem(6, 2), dict(local="exact", coarse="rgdsw")),
+    ("poisson12_ic1", lambda: P.poisson_problem(12, 4), dict(local="ic0", fill_level=1)),
+    ("elast6_ilu2", lambda: P.elasticity_problem(6, 2), dict(local="ilu0", fill_level=2)),
 ]
 
 
@@ -153,6 +163,31 @@ def test_gmres_matches_oracle():
     xo2, io2 = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=5)
     x2, info2 = gpu_solve(h2, prob.b)
     assert info2.converged and abs(info2.iters - io2.iters) <= 2
+
+
+def test_gmres_exact_preconditioner_one_step_and_poisson():
+    """One subdomain with the exact local solve makes A M^-1 = I: the first Arnoldi
+    vector is already in the basis (the second Gram-Schmidt pass finds a zero
+    remainder) and GMRES stops after one step.  GMRES on a Poisson problem with
+    fill and FP32 factors matches the oracle's count."""
+    from oracle import gdsw_oracle as O
+    one = P.poisson_problem(6, 6)
+    h = gpu_handle(one, local_solver="exact", krylov="gmres")
+    x, info = gpu_solve(h, one.b)
+    assert info.converged and info.iters == 1 and info.true_relres <= 1e-8
+    prob = P.poisson_problem(12, 4)
+    M = oracle_for(prob, local="ic0", fill_level=1)
+    _, io = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=30)
+    h = gpu_handle(prob, local_solver="ic0", fill_level=1, krylov="gmres")
+    x, info = gpu_solve(h, prob.b)
+    assert info.converged and abs(info.iters - io.iters) <= 1 and info.true_relres <= 1e-8
+    h32 = gpu_handle(prob, local_solver="ic0", fill_level=1, krylov="gmres", precision="fp32")
+    _, info32 = gpu_solve(h32, prob.b)
+    assert info32.converged and abs(info32.iters - io.iters) <= 1
+    # the single-reduce orthogonalisation still converges to the true residual
+    h1 = gpu_handle(prob, local_solver="ic0", fill_level=1, krylov="gmres", gmres_orth="single")
+    _, info1 = gpu_solve(h1, prob.b)
+    assert info1.converged and info1.true_relres <= 1e-8 and info1.iters >= io.iters - 1
 
 
 def test_fp32_pcg_iteration_inflation_and_fp64_residual():
