@@ -85,18 +85,20 @@ def peaks():
 # algorithmic bytes (each array touched once per launch)
 # ---------------------------------------------------------------------------
 
-def apply_bytes(st: dict, vbytes: int) -> dict:
-    """Algorithmic bytes of the four apply phases for value size `vbytes`."""
+def apply_bytes(st: dict, vbytes: int, fbytes: int = None) -> dict:
+    """Algorithmic bytes of the four apply phases: `vbytes` per value of Phi, the
+    local vectors and inverses, `fbytes` per stored factor value (default vbytes)."""
+    fbytes = vbytes if fbytes is None else fbytes
     n, sum_m, n0, nblk = st["n"], st["sum_omega"], st["n0"], st["n_blocks"]
     tri = 0
     for nnz, lev in ((st["nnz_L"], st["n_levels_L"]), (st["nnz_U"], st["n_levels_U"])):
         off = nnz - sum_m
-        tri += off * (vbytes + 2) + sum_m * (vbytes + 2) + lev * 16
+        tri += off * (fbytes + 2) + sum_m * (fbytes + 2) + lev * 16
     if st["dense_local"]:
         tri = st["dense_local"] * vbytes
     local = sum_m * (8 + 4) + tri + sum_m * vbytes + st["n_sub"] * 8
     phit = st["nnz_phi"] * vbytes + n * (8 + 4) + (nblk + 1) * 12 if n0 else 0
-    coarse = n0 * n0 * 8 + n0 * 8 * 3 if n0 else 0
+    coarse = st.get("a0_entries", n0 * n0) * 8 + n0 * 8 * 3 if n0 else 0
     combine = (sum_m * 4 + (n + 1) * 4 + sum_m * vbytes + n * 4 + st["nnz_phi"] * vbytes
                + n * 8 + nblk * 16)
     return {"local": local, "phiT": phit, "coarse": coarse, "combine": combine}
@@ -279,7 +281,7 @@ def timed_solves(h, bs, x, steps, warmup, stream, barrier, solve=None):
     return e0.elapsed_time(e1) / 1e3, infos
 
 
-def kernel_measurements(h, st, vb, stream, v0):
+def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=None):
     """Per-phase apply times (CUDA events on the launching stream), the apply as
     the solver runs it (branches overlapped) and the SpMV."""
     import torch
@@ -310,7 +312,7 @@ def kernel_measurements(h, st, vb, stream, v0):
     hbm, src = peaks()
     names = ["local", "phiT", "coarse", "combine"]
     phase_ms = dict(zip(names, phases.tolist()))
-    ab = apply_bytes(st, vb)
+    ab = apply_bytes(st, vb, fb)
     dom = max(names, key=lambda k: phase_ms[k])
     achieved = ab[dom] / (phase_ms[dom] * 1e-3) / 1e9
     return {
@@ -320,9 +322,39 @@ def kernel_measurements(h, st, vb, stream, v0):
         "apply_overlapped_gbs": sum(ab.values()) / (overlapped * 1e-3) / 1e9,
         "spmv_ms": spmv_ms, "spmv_gbs": spmv_bytes(st) / (spmv_ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                     "frac": achieved / hbm, "traffic": profiled_traffic(dom, workload, variant),
+                     "peak_source": src,
                      "algorithmic_bytes_per_launch": ab[dom]},
     }
+
+
+KERNEL_SOURCE = {"local": "apply.cu", "phiT": "apply.cu", "coarse": "apply.cu", "combine": "apply.cu",
+                 "spmv": "krylov.cu"}
+
+
+def source_digest(name):
+    """First 16 hex digits of the SHA-256 of a kernel source file."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_2304_04876_b300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(phase, workload, variant):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+    phase's kernel, from the ncu summary table in profiles/traffic.md, or None when
+    no capture exists for it or the kernel's source has changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path) or phase not in KERNEL_SOURCE:
+        return None
+    want = source_digest(KERNEL_SOURCE[phase])
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 5 and cells[0] == phase and cells[1] == workload and cells[2] == variant:
+            try:
+                return int(cells[3]) if cells[4] == want else None
+            except ValueError:
+                return None
+    return None
 
 
 def launches_per_solve(iters, krylov="pcg"):
@@ -375,8 +407,9 @@ def run_single(args, world, rank, dist, barrier):
         t = torch.tensor([e2e_el], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_el = float(t.item())
-    vb = 4 if opts.get("precision") == "fp32" else 8
-    km = kernel_measurements(h, st, vb, stream, bs[0])
+    vb = 4 if opts.get("precision") in ("fp32", "fp16") else 8
+    fb = 2 if opts.get("precision") == "fp16" else vb
+    km = kernel_measurements(h, st, vb, stream, bs[0], C["workload"], variant, fb)
     line = {
         "metric": C["metric"], "value": world * args.steps / el, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -384,6 +417,7 @@ def run_single(args, world, rank, dist, barrier):
         "dtype": "f32+f64" if vb == 4 else "f64", "data": "synthetic",
         "config": {"workload": C["workload"], "variant": variant, "n": n, "nnz": st["nnz"],
                    "subdomains": st["n_sub"], "n0": st["n0"], "overlap": 1, "tol": 1e-8,
+                   "local_shape": [int(st["local_stages"]), int(st["local_threads"])],
                    "l2": "per-iteration working set larger than the 126 MB L2; no flush" if n > 1e6 else
                          "small workload: L2-resident, launch-latency bound",
                    "parallelism": f"replicas{world}"},
@@ -463,7 +497,8 @@ def run_batch(args, world, rank, dist, barrier):
         xh.zero_()
         h.solve_host(bh, xh)
     e2e_el = time.perf_counter() - te
-    km = kernel_measurements(h, st, 4, stream, b)
+    km = kernel_measurements(h, st, 4, stream, b, f"batch_{count}_diffusion7_edge16-64_sub8-16_k1e-2..1e2",
+                             "fp32_levelsched")
     line = {
         "metric": "batched PCG problems solved/s to 1e-8 (256 diffusion problems per step)",
         "value": world * count * args.steps / el, "unit": "problems/s", "n_gpus": world, "steps": args.steps,
@@ -471,6 +506,7 @@ def run_batch(args, world, rank, dist, barrier):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"batch_{count}_diffusion7_edge16-64_sub8-16_k1e-2..1e2", "n": n,
                    "nnz": st["nnz"], "subdomains": st["n_sub"], "n0": st["n0"], "problems": count,
+                   "local_shape": [int(st["local_stages"]), int(st["local_threads"])],
                    "parallelism": f"replicas{world}"},
         "iters_min_max": [min(iters), max(iters)], "true_relres_max": relres, "setup_s": setup_s,
         "one_at_a_time_ms_per_problem": 1e3 * seq_per_problem,

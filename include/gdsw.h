@@ -149,6 +149,10 @@ typedef struct {
   int64_t n_blocks;       /* Phi blocks: interiors + interface components   */
   int64_t device_bytes;   /* device memory held by the handle               */
   int64_t n_problems;     /* independent problems (gdsw_setup_batch)        */
+  int64_t a0_entries;     /* entries of the dense A0^-1 blocks (one per problem) */
+  int64_t local_stages;   /* ring depth of the pipelined local solve chosen at
+                             setup (0: the unpipelined level/Jacobi kernel)   */
+  int64_t local_threads;  /* its consumer threads (or threads per CTA)      */
   double setup_seconds;
   double setup_phase_seconds[8]; /* [0] symbolic [1] local factors [2] Phi_Gamma
                                     [3] Phi_I [4] A0 [5] A0^-1 [6] exact local

@@ -14,6 +14,7 @@
 //              (the deterministic scatter-add of sum_s R_s^T z_s) and adds
 //              the prolongation (Phi y)_g, optionally fusing the PCG dots.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <type_traits>
 
@@ -152,6 +153,30 @@ __device__ __forceinline__ T load_as(const TS* p, int i) { return T(p[i]); }
 template <>
 __device__ __forceinline__ float load_as<float, __half>(const __half* p, int i) { return __half2float(p[i]); }
 
+// The four values of row t of a row-major record (16-byte aligned rows for
+// FP32, 32 for FP64, 8 for FP16), widened to T.
+template <class T, class TS>
+__device__ __forceinline__ void load4(const TS* vals, int t, T* a);
+template <>
+__device__ __forceinline__ void load4<float, float>(const float* vals, int t, float* a) {
+  const float4 q = reinterpret_cast<const float4*>(vals)[t];
+  a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load4<double, double>(const double* vals, int t, double* a) {
+  const double2 q0 = reinterpret_cast<const double2*>(vals)[2 * t];
+  const double2 q1 = reinterpret_cast<const double2*>(vals)[2 * t + 1];
+  a[0] = q0.x; a[1] = q0.y; a[2] = q1.x; a[3] = q1.y;
+}
+template <>
+__device__ __forceinline__ void load4<float, __half>(const __half* vals, int t, float* a) {
+  const uint2 q = reinterpret_cast<const uint2*>(vals)[t];
+  const __half2 h0 = *reinterpret_cast<const __half2*>(&q.x);
+  const __half2 h1 = *reinterpret_cast<const __half2*>(&q.y);
+  const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+  a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
+}
+
 // Row update of one level: TPR threads per row split the row's entries and
 // add their partial sums with shuffles; short rows (TPR = 1) are unrolled.
 // TS is the storage type of the record values (T, or FP16 applied in FP32).
@@ -163,6 +188,9 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
   const TS* dinv = reinterpret_cast<const TS*>(rec + 16 + ((2 * nr + 15) & ~15));
   const TS* vals = reinterpret_cast<const TS*>(rec + hdr.z);
   const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + hdr.w);
+  // entry k of row t: row-major padded to 4 for widths 1-4, else column-major
+  const bool packed = K > 0 && K <= 4;
+  auto at = [&](int t, int k) { return packed ? t * 4 + k : k * nr + t; };
   if (TPR == 1 && G > 1) {
     // a node's rows in order by one thread
     for (int gt = threadIdx.x; gt * G < nr; gt += NT) {
@@ -170,7 +198,7 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
         const int t = gt * G + d;
         const int row = lrows[t];
         T acc = v[row];
-        for (int k = 0; k < K; ++k) acc = fma(-load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], acc);
+        for (int k = 0; k < K; ++k) acc = fma(-load_as<T, TS>(vals, at(t, k)), v[cols[at(t, k)]], acc);
         v[row] = acc * load_as<T, TS>(dinv, t);
       }
     }
@@ -178,16 +206,15 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
     for (int t = threadIdx.x; t < nr; t += NT) {
       const int row = lrows[t];
       T acc = v[row];
-      if (K <= 4) {
+      if (packed) {
+        // one vector load of the four columns and one of the four values
+        const ushort4 c4 = reinterpret_cast<const ushort4*>(cols)[t];
         T a[4];
-        int cidx[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          cidx[k] = k < K ? cols[k * nr + t] : row;
-          a[k] = k < K ? load_as<T, TS>(vals, k * nr + t) : T(0);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc = fma(-a[k], v[cidx[k]], acc);
+        load4<T, TS>(vals, t, a);
+        acc = fma(-a[0], v[c4.x], acc);
+        acc = fma(-a[1], v[c4.y], acc);
+        acc = fma(-a[2], v[c4.z], acc);
+        acc = fma(-a[3], v[c4.w], acc);
       } else {
         for (int k = 0; k < K; ++k) acc = fma(-load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], acc);
       }
@@ -206,7 +233,7 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
         const int t = gt * G + d;
         T part = T(0);
         if (gt < ngr)
-          for (int k = sub; k < K; k += TPR) part = fma(load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], part);
+          for (int k = sub; k < K; k += TPR) part = fma(load_as<T, TS>(vals, at(t, k)), v[cols[at(t, k)]], part);
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, TPR);
         if (gt < ngr && sub == 0) {
@@ -347,9 +374,11 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
 }
 
 // Partial products Phi_b^T r_b.  The first n_cta chunks (more than 256 rows,
-// at most 1024, of a block) take one CTA each: 8 columns per pass, four rows
-// per trip, a transpose reduction through shared memory.  The small chunks
-// (interface components) take one warp each, eight per CTA, with shuffle sums.
+// at most 1024, of a block) take one CTA each: the chunk's r is staged in
+// shared memory, then each warp takes whole columns, which are contiguous in
+// the column-major panel.  The small chunks (interface components) take one
+// warp each, eight per CTA, with shuffle sums; their CTAs are placed first in
+// the grid.
 template <class T>
 __device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict__ r,
                                                 const int* __restrict__ brow_ptr,
@@ -373,12 +402,22 @@ __device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict_
     T acc[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] = T(0);
-    for (int i = i0 + lane; i < i1; i += 32) {
-      const T rv = T(r[brow_dof[p0 + i]]);
-      const T* col = Ph + int64_t(c0) * nr + i;
+    // four rows per lane and trip: indices, then values, then the products
+    for (int ib = i0 + lane; ib < i1; ib += 4 * 32) {
+      int g[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (u < kc) acc[u] = fma(col[int64_t(u) * nr], rv, acc[u]);
+      for (int j = 0; j < 4; ++j) g[j] = ib + 32 * j < i1 ? brow_dof[p0 + ib + 32 * j] : -1;
+      T rv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rv[j] = g[j] >= 0 ? T(r[g[j]]) : T(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (g[j] < 0) continue;
+        const T* col = Ph + int64_t(c0) * nr + ib + 32 * j;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < kc) acc[u] = fma(col[int64_t(u) * nr], rv[j], acc[u]);
+      }
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -391,7 +430,7 @@ __device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict_
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 6) k_phiT(int n_chunks, int n_cta, const double* __restrict__ r,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chunks, int n_cta, const double* __restrict__ r,
                                               const int* __restrict__ brow_ptr,
                                               const int* __restrict__ brow_dof,
                                               const int* __restrict__ bcol_ptr,
@@ -403,61 +442,47 @@ __global__ void __launch_bounds__(256, 6) k_phiT(int n_chunks, int n_cta, const 
                                               const int* __restrict__ chunk_slot,
                                               double* __restrict__ partial,
                                               const KrylovScalars* __restrict__ ks) {
-  __shared__ T red8[8][256];
+  __shared__ T rs[kPhiChunkRows];          // r of a chunk
   if (ks != nullptr && ks->done) return;
-  if (int(blockIdx.x) >= n_cta) {
+  // the small chunks' CTAs come first in the grid, so that their longer
+  // chains of dependent loads overlap the big chunks instead of trailing them
+  const int n_warp_ctas = (n_chunks - n_cta + 7) / 8;
+  if (int(blockIdx.x) < n_warp_ctas) {
     // warp path: no CTA-wide barrier below
-    const int q = n_cta + (int(blockIdx.x) - n_cta) * 8 + (threadIdx.x >> 5);
+    const int q = n_cta + int(blockIdx.x) * 8 + (threadIdx.x >> 5);
     if (q < n_chunks)
       phiT_warp_chunk<T>(q, r, brow_ptr, brow_dof, bcol_ptr, phi_off, phi, chunk_blk, chunk_r0, chunk_r1,
                          chunk_slot, partial);
     return;
   }
-  const int q = blockIdx.x;
+  const int q = int(blockIdx.x) - n_warp_ctas;
   const int b = chunk_blk[q];
   const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
-  const int i0 = chunk_r0[q], i1 = chunk_r1[q];
+  const int i0 = chunk_r0[q], rows = chunk_r1[q] - i0;
   const int k = bcol_ptr[b + 1] - bcol_ptr[b];
-  const T* Ph = phi + phi_off[b];
-  for (int c0 = 0; c0 < k; c0 += 8) {
-    const int kc = min(8, k - c0);
-    T acc[8];
+  // r of the chunk's rows into shared memory (four rows per thread in flight)
+  for (int ib = threadIdx.x; ib < rows; ib += 4 * 256) {
+    int g[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = T(0);
-    for (int ib = i0 + threadIdx.x; ib < i1; ib += 4 * 256) {
-      // four rows per trip, all loads issued before the FMAs
-      T rv[4];
+    for (int j = 0; j < 4; ++j) g[j] = ib + 256 * j < rows ? brow_dof[p0 + i0 + ib + 256 * j] : -1;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i = ib + j * 256;
-        rv[j] = i < i1 ? T(r[brow_dof[p0 + i]]) : T(0);
-      }
+    for (int j = 0; j < 4; ++j)
+      if (g[j] >= 0) rs[ib + 256 * j] = T(r[g[j]]);
+  }
+  __syncthreads();
+  // one warp per column: the column is contiguous in the block's panel
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int u = w; u < k; u += 8) {
+    const T* col = phi + phi_off[b] + int64_t(u) * nr + i0;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    int i = lane;
+    for (; i + 96 < rows; i += 128) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i = ib + j * 256;
-        if (i >= i1) continue;
-        const T* col = Ph + int64_t(c0) * nr + i;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u < kc) acc[u] = fma(col[int64_t(u) * nr], rv[j], acc[u]);
-      }
+      for (int j = 0; j < 4; ++j) acc[j] = fma(col[i + 32 * j], rs[i + 32 * j], acc[j]);
     }
-    // reduce the kc accumulators: transpose through shared memory, then warp u
-    // sums column u (8 values per lane and one shuffle tree), which costs far
-    // fewer FP64 adds than a shuffle tree per column in every warp
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (u < kc) red8[u][threadIdx.x] = acc[u];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (w < kc) {
-      T t = T(0);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) t += red8[w][lane * 8 + j];
-      t = warp_sum(t);
-      if (lane == 0) partial[chunk_slot[q] + c0 + w] = double(t);
-    }
-    __syncthreads();
+    for (; i < rows; i += 32) acc[0] = fma(col[i], rs[i], acc[0]);
+    const T t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+    if (lane == 0) partial[chunk_slot[q] + u] = double(t);
   }
 }
 
@@ -472,8 +497,10 @@ __global__ void k_coarse_c(int n0, const int* __restrict__ cs_ptr, const int* __
   }
 }
 
-// y = A0^-1 c, warp per row of the explicit inverse (one dense block per
-// problem; c staged in shared memory when there is a single problem).
+// y = A0^-1 c with the explicit inverse (one dense block per problem; c staged
+// in shared memory when there is a single problem).  Two warps per row, each
+// over half of the columns with eight independent FMA chains per lane (FP64
+// latency); the halves are added in a fixed order.
 __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __restrict__ Ainv,
                                                      const int* __restrict__ coarse_prob,
                                                      const int* __restrict__ prob_c0,
@@ -482,36 +509,47 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
                                                      double* __restrict__ y, float* __restrict__ y32,
                                                      const KrylovScalars* __restrict__ ks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double half_sum[4][2];
   if (ks != nullptr && ks->done) return;
   double* cs = reinterpret_cast<double*>(smem_raw);
   if (staged) {
     for (int l = threadIdx.x; l < n0; l += blockDim.x) cs[l] = c[l];
     __syncthreads();
   }
-  const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n0; row += warps) {
-    const int pr = coarse_prob[row];
-    const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;
-    const double* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
-    const double* cv = staged ? cs + cp : c + cp;
-    // four independent FMA chains per lane (FP64 latency), loads issued first
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int j = lane;
-    for (; j + 96 < np; j += 128) {
-      const double m0 = Ar[j], m1 = Ar[j + 32], m2 = Ar[j + 64], m3 = Ar[j + 96];
-      a0 = fma(m0, cv[j], a0);
-      a1 = fma(m1, cv[j + 32], a1);
-      a2 = fma(m2, cv[j + 64], a2);
-      a3 = fma(m3, cv[j + 96], a3);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int slot = w >> 1, h = w & 1;                  // row slot in the CTA, half of the row
+  for (int row0 = blockIdx.x * 4; row0 < n0; row0 += gridDim.x * 4) {
+    const int row = row0 + slot;
+    double acc = 0.0;
+    if (row < n0) {
+      const int pr = coarse_prob[row];
+      const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;
+      const double* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
+      const double* cv = staged ? cs + cp : c + cp;
+      const int j0 = h == 0 ? 0 : np / 2, j1 = h == 0 ? np / 2 : np;
+      double a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = 0.0;
+      int j = j0 + lane;
+      for (; j + 7 * 32 < j1; j += 8 * 32) {
+        double m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m[u] = Ar[j + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = fma(m[u], cv[j + 32 * u], a[u]);
+      }
+      for (; j < j1; j += 32) a[0] = fma(Ar[j], cv[j], a[0]);
+      acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+      acc = warp_sum(acc);
     }
-    for (; j < np; j += 32) a0 = fma(Ar[j], cv[j], a0);
-    double acc = (a0 + a1) + (a2 + a3);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      y[row] = acc;
-      if (y32 != nullptr) y32[row] = float(acc);   // converted once, not per scatter position
+    if (lane == 0) half_sum[slot][h] = acc;
+    __syncthreads();
+    if (h == 0 && lane == 0 && row < n0) {
+      const double v = half_sum[slot][0] + half_sum[slot][1];
+      y[row] = v;
+      if (y32 != nullptr) y32[row] = float(v);   // converted once, not per scatter position
     }
+    __syncthreads();
   }
 }
 
@@ -546,7 +584,7 @@ __device__ __forceinline__ double combine_one(int p, const int* __restrict__ pos
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 6) k_combine(
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_combine(
     int n, const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_dof,
     const int* __restrict__ pos_blk, const int* __restrict__ brow_ptr,
     const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
@@ -557,25 +595,29 @@ __global__ void __launch_bounds__(256, 6) k_combine(
   if (ks != nullptr && ks->done) return;
   double d_new = 0.0, d_old = 0.0;
   const int stride = gridDim.x * blockDim.x;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += 2 * stride) {
-    // two independent positions per trip keep more loads in flight
-    const int p2 = p + stride;
-    const int g = brow_dof[p];
-    const int g2 = p2 < n ? brow_dof[p2] : 0;
-    const double a = combine_one(p, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc);
-    const double a2 = p2 < n ? combine_one(p2, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc) : 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += 4 * stride) {
+    // four independent positions per trip keep more loads in flight
+    int g[4];
+    double a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int pj = p + j * stride;
+      g[j] = pj < n ? brow_dof[pj] : -1;
+      a[j] = pj < n ? combine_one(pj, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc)
+                    : 0.0;
+    }
     if (dots) {
-      const double rg = r[g];
-      if (dots > 1) d_old = fma(rg, z[g], d_old);
-      d_new = fma(rg, a, d_new);
-      if (p2 < n) {
-        const double rg2 = r[g2];
-        if (dots > 1) d_old = fma(rg2, z[g2], d_old);
-        d_new = fma(rg2, a2, d_new);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (g[j] < 0) continue;
+        const double rg = r[g[j]];
+        if (dots > 1) d_old = fma(rg, z[g[j]], d_old);
+        d_new = fma(rg, a[j], d_new);
       }
     }
-    z[g] = a;
-    if (p2 < n) z[g2] = a2;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (g[j] >= 0) z[g[j]] = a[j];
   }
   if (!dots) return;
   const double tn = block_sum(d_new, sh);
@@ -689,7 +731,7 @@ gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovSca
 gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
   if (c->n0 == 0) return GDSW_OK;
   k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, ks);
-  const int grid = std::min((c->n0 + 7) / 8, kNumSMs * 4);
+  const int grid = std::min((c->n0 + 3) / 4, kNumSMs * 8);
   const int staged = c->nprob == 1;
   k_coarse_gemv<<<grid, 256, staged ? size_t(c->n0) * sizeof(double) : 16, s>>>(
       c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, staged, c->cvec, c->yvec, c->yvec32, ks);
@@ -699,7 +741,7 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
 
 template <class T>
 gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated) {
-  const int grid = std::max(1, std::min(c->combine_grid, (c->n + 511) / 512));
+  const int grid = std::max(1, std::min(c->combine_grid, (c->n + 255) / 256));
   k_combine<T><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
                                     c->bcol, c->phi_off, static_cast<const T*>(c->phi),
                                     c->fp32 ? reinterpret_cast<const T*>(c->yvec32) : reinterpret_cast<const T*>(c->yvec),
@@ -912,7 +954,20 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(allow_max_dynamic_smem(k_local_dense<double>));
   }
   GDSW_CK(allow_max_dynamic_smem(k_coarse_gemv));
-  if (c->rec_stages > 0 && c->opt.autotune) GDSW_TRY(tune_local(c));
+  if (c->rec_stages > 0 && c->opt.autotune) {
+    // GDSW_LOCAL_SHAPE="stages,threads" fixes the shape instead of timing it
+    // (for profilers, under which the timings mean nothing)
+    if (const char* e = getenv("GDSW_LOCAL_SHAPE")) {
+      int st = 0, nt = 0;
+      if (sscanf(e, "%d,%d", &st, &nt) == 2 && (st == 0 || st == 2 || st == 3 || st == 4 || st == 6) &&
+          (nt == 128 || nt == 256 || nt == 512 || nt == 992 || nt == 1024)) {
+        c->rec_stages = st;
+        if (st > 0) c->rec_consumers = nt == 1024 ? 992 : nt; else c->tri_threads = nt == 992 ? 1024 : nt;
+      }
+    } else {
+      GDSW_TRY(tune_local(c));
+    }
+  }
   // the scatter-add is a grid-stride loop: exactly the CTAs that are resident at once
   {
     int dev = 0, sms = kNumSMs, per_sm = 1;

@@ -191,6 +191,8 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
   S.n_blocks = c->nblk;
   S.device_bytes = static_cast<int64_t>(c->bytes);
   S.n_problems = P.nprob;
+  S.local_stages = c->rec_stages;
+  S.local_threads = c->rec_stages > 0 ? c->rec_consumers : c->tri_threads;
   S.setup_seconds = now_s() - t0;
   *out = h;
   return GDSW_OK;

@@ -27,9 +27,10 @@ int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec) {
       for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
         const int K = E.lev_K[l];
         const int piece = record_piece_rows(E.lev_nr[l], K, P.dpn, size_t(vb));
+        const int64_t Kp = record_width(K);
         for (int t0 = 0; t0 < E.lev_nr[l]; t0 += piece) {
           const int64_t nr = std::min(piece, E.lev_nr[l] - t0);
-          total += 16 + a16(2 * nr) + a16(nr * vb) + a16(K * nr * vb) + a16(2 * K * nr);
+          total += 16 + a16(2 * nr) + a16(nr * vb) + a16(Kp * nr * vb) + a16(2 * Kp * nr);
           ++count;
         }
       }

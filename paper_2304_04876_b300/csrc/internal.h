@@ -107,6 +107,9 @@ struct SupportPlan {
 };
 gdsw_status build_supports(const Plan& P, SupportPlan* S);
 
+// Rows of one Phi^T r chunk (the kernel stages a chunk's r in shared memory).
+constexpr int kPhiChunkRows = 1024;
+
 struct CoarsePlan {
   int n0 = 0;
   std::vector<int> comp_c0;               // first coarse column of each owner component
@@ -131,12 +134,17 @@ struct CoarsePlan {
   std::vector<int> prob_c0;               // nprob+1
 };
 
+// Stored width of a level record: levels of width 1-4 are stored row-major
+// with each row padded to 4 entries (one vector load of values and one of
+// columns per row); wider levels column-major with their own width.
+inline int record_width(int K) { return K == 0 ? 0 : (K <= 4 ? 4 : K); }
+
 // Rows per record when a level of nr rows and width K is split so that one
 // record (header, rows, inverse diagonal, values, columns; vb bytes per value)
 // stays within kRecordCap bytes; a multiple of the node group g.
 constexpr size_t kRecordCap = 32 * 1024;
 inline int record_piece_rows(int nr, int K, int g, size_t vb) {
-  const size_t per_row = 2 + vb + size_t(K) * (vb + 2);
+  const size_t per_row = 2 + vb + size_t(record_width(K)) * (vb + 2);
   size_t rows = (kRecordCap - 80) / per_row;
   rows = rows / size_t(g) * size_t(g);
   if (rows < size_t(g)) rows = g;
@@ -311,6 +319,7 @@ struct Ctx {
   cudaGraphExec_t bgraph_exec = nullptr;
   cudaStream_t bgraph_stream = nullptr;
   int spmv_R = 256, spmv_maxne = 1, spmv_tiles = 1, spmv_grid = kNumSMsForCtx;
+  int spmv_W = 0;                    // lanes per row for long rows (0: the tiled kernel)
 };
 
 template <class T>

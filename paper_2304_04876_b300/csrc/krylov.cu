@@ -72,6 +72,44 @@ __global__ void __launch_bounds__(R) k_spmv_stream(int n, int ntiles, const int*
   }
 }
 
+// y = A x and (x, y) for matrices with long rows: W lanes per row stride over
+// its entries (coalesced values and columns), the partial sums meet in a
+// shuffle tree of width W; the dot product as in k_spmv_stream.
+template <int W>
+__global__ void __launch_bounds__(256) k_spmv_rows(int n, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ colind,
+                                                   const double* __restrict__ val,
+                                                   const double* __restrict__ x, double* __restrict__ y,
+                                                   double* __restrict__ red, KrylovScalars* ks) {
+  __shared__ double sh[32];
+  if (ks != nullptr && ks->done) return;
+  const int lane = threadIdx.x % W;
+  constexpr int kRows = 256 / W;
+  double dot = 0.0;
+  for (int base = blockIdx.x * kRows; base < n; base += gridDim.x * kRows) {
+    const int row = base + threadIdx.x / W;
+    const bool valid = row < n;
+    double acc = 0.0;
+    if (valid) {
+      const int e1 = rowptr[row + 1];
+      for (int e = rowptr[row] + lane; e < e1; e += W) acc = fma(val[e], x[colind[e]], acc);
+    }
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, W);
+    if (valid && lane == 0) {
+      y[row] = acc;
+      dot = fma(x[row], acc, dot);
+    }
+  }
+  if (ks == nullptr) return;
+  const double t = block_sum(dot, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = t;
+  if (arrive_last(&ks->ticket[0])) {
+    const double s2 = sum_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) ks->pq = s2;
+  }
+}
+
 // alpha = (r,z)/(p,q); x += alpha p; r -= alpha q; rr = ||r||^2; then the
 // last CTA counts the iteration and decides whether the loop ends.
 __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restrict__ x,
@@ -336,6 +374,17 @@ __global__ void k_update_x(int n, int k, const double* __restrict__ Zk, const do
 }
 
 gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, KrylovScalars* ks) {
+  if (c->spmv_W > 0) {
+    const int grid = std::max(1, std::min(c->spmv_grid, (c->n + 256 / c->spmv_W - 1) / (256 / c->spmv_W)));
+    switch (c->spmv_W) {
+      case 4: k_spmv_rows<4><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+      case 8: k_spmv_rows<8><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+      case 16: k_spmv_rows<16><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+      default: k_spmv_rows<32><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    }
+    GDSW_CK(cudaGetLastError());
+    return GDSW_OK;
+  }
   const int grid = std::min(c->spmv_grid, c->spmv_tiles);
   const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
   switch (c->spmv_R) {
@@ -384,6 +433,25 @@ gdsw_status set_done(Ctx* c, cudaStream_t s, int v) {
 // number of CTAs that fit on the SMs at once.
 gdsw_status spmv_configure(Ctx* c, const int* rowptr) {
   const int n = c->n;
+  // long rows (more than 16 entries on average): W lanes per row, W the power
+  // of two nearest to a tenth of the mean row length, within 4..32
+  const double mean = n > 0 ? double(rowptr[n]) / n : 0.0;
+  c->spmv_W = 0;
+  if (mean > 16.0) {
+    int W = 4;
+    while (W < 32 && W * 10 < mean) W *= 2;
+    c->spmv_W = W;
+    int per_sm = 1;
+    switch (W) {
+      case 4: GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_rows<4>, 256, 0)); break;
+      case 8: GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_rows<8>, 256, 0)); break;
+      case 16: GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_rows<16>, 256, 0)); break;
+      default: GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_rows<32>, 256, 0)); break;
+    }
+    c->spmv_grid = std::max(1, per_sm) * kNumSMs;
+    c->spmv_tiles = 1;
+    return GDSW_OK;
+  }
   int R = 256, maxne = 0;
   for (; R >= 32; R >>= 1) {
     maxne = 0;

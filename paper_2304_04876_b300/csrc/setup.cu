@@ -835,12 +835,13 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
             for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
               // a wide level becomes several records (rows are independent
               // within a level, node groups kept whole)
-              const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
+              const size_t L_nr = E.lev_nr[l], K = E.lev_K[l], Kp = record_width(E.lev_K[l]);
+              const bool packed = Kp == 4;      // row-major, 4 entries per row
               const size_t piece = record_piece_rows(E.lev_nr[l], E.lev_K[l], P.dpn, vb);
               for (size_t t0 = 0; t0 < L_nr; t0 += piece) {
                 const size_t nr = std::min(piece, L_nr - t0);
                 const size_t o_l = total + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
-                             o_c = o_v + a16(K * nr * vb), end = o_c + a16(2 * K * nr);
+                             o_c = o_v + a16(Kp * nr * vb), end = o_c + a16(2 * Kp * nr);
                 if (pass == 1) {
                   rec_off16.push_back(static_cast<uint32_t>(total / 16));
                   rec_bytes.push_back(static_cast<uint32_t>(end - total));
@@ -853,7 +854,8 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
                     dp[E.lev_start[l] + t0 + t] = static_cast<uint32_t>((o_d + t * vb) / vb);
                   for (size_t k = 0; k < K; ++k)
                     for (size_t t = 0; t < nr; ++t)
-                      vp[E.lev_off[l] + k * L_nr + t0 + t] = static_cast<uint32_t>((o_v + (k * nr + t) * vb) / vb);
+                      vp[E.lev_off[l] + k * L_nr + t0 + t] =
+                          static_cast<uint32_t>((o_v + (packed ? t * 4 + k : k * nr + t) * vb) / vb);
                 }
                 total = end;
               }
@@ -870,19 +872,27 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       for (size_t rr = 0; rr < rec_off16.size(); ++rr) {
         const EllPlan& E = rec_is_L[rr] ? P.L : P.U;
         const int l = rec_lev[rr];
-        const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
+        const size_t L_nr = E.lev_nr[l], K = E.lev_K[l], Kp = record_width(E.lev_K[l]);
         const size_t t0 = rec_t0[rr];
         const size_t nr = std::min(size_t(record_piece_rows(E.lev_nr[l], E.lev_K[l], P.dpn, vb)), L_nr - t0);
         const size_t base = size_t(rec_off16[rr]) * 16;
         const size_t o_l = base + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
-                     o_c = o_v + a16(K * nr * vb);
+                     o_c = o_v + a16(Kp * nr * vb);
         // header: rows, width, and the byte offsets of the values and columns
         const int hdr[4] = {static_cast<int>(nr), static_cast<int>(K), static_cast<int>(o_v - base),
                             static_cast<int>(o_c - base)};
         std::memcpy(&host[base], hdr, 16);
         std::memcpy(&host[o_l], &E.lrows[E.lev_start[l] + t0], 2 * nr);
-        for (size_t k = 0; k < K; ++k)
-          std::memcpy(&host[o_c + 2 * k * nr], &E.col[E.lev_off[l] + k * L_nr + t0], 2 * nr);
+        if (Kp == 4) {
+          // row-major, padded to 4 with the row itself (value zero)
+          uint16_t* cc = reinterpret_cast<uint16_t*>(&host[o_c]);
+          for (size_t t = 0; t < nr; ++t)
+            for (size_t k = 0; k < 4; ++k)
+              cc[t * 4 + k] = k < K ? E.col[E.lev_off[l] + k * L_nr + t0 + t] : E.lrows[E.lev_start[l] + t0 + t];
+        } else {
+          for (size_t k = 0; k < K; ++k)
+            std::memcpy(&host[o_c + 2 * k * nr], &E.col[E.lev_off[l] + k * L_nr + t0], 2 * nr);
+        }
         stage = std::max<size_t>(stage, rec_bytes[rr]);
       }
       uint8_t* d_stream;
@@ -1090,6 +1100,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     c->stats.setup_phase_seconds[4] = now_s() - t0;
     t0 = now_s();
     GDSW_TRY(dalloc(c, &c->A0inv, a0_off[np_]));
+    c->stats.a0_entries = a0_off[np_];
     double* d_W;
     const int maxnbk = (maxb + NB - 1) / NB;
     GDSW_TRY(sc.get(&d_W, size_t(maxnbk) * NB * maxb));

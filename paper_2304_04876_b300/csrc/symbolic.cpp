@@ -733,9 +733,8 @@ gdsw_status build_coarse_plan(const Plan& P, const SupportPlan& S, const std::ve
       C->dof_blk[C->brow_dof[q]] = b;
       C->dof_blkrow[C->brow_dof[q]] = q - C->brow_ptr[b];
     }
-  // Phi^T r chunks of at most kChunkRows rows (4 per thread of a 256-thread CTA); partial slots per (chunk, column)
-  int kChunkRows = 1024;
-  if (const char* e = std::getenv("GDSW_PHIT_CHUNK")) kChunkRows = std::max(256, std::atoi(e));
+  // Phi^T r chunks of at most kPhiChunkRows rows; partial slots per (chunk, column)
+  constexpr int kChunkRows = kPhiChunkRows;
   C->chunk_blk.clear(); C->chunk_r0.clear(); C->chunk_r1.clear(); C->chunk_slot.clear();
   int nslot = 0;
   std::vector<std::vector<int>> col_slots(n0);
