@@ -290,15 +290,15 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
   const int r0 = rec_ptr[s], nrec = rec_ptr[s + 1] - r0;
   unsigned char* stages = smem_raw;
   T* v = reinterpret_cast<T*>(smem_raw + size_t(S) * stage_bytes);
+  const int nt = blockDim.x - 32;            // consumer threads
   if (threadIdx.x == 0) {
     for (int j = 0; j < S; ++j) {
       mbar_init(&full[j], 1);
-      mbar_init(&empty[j], 1);
+      mbar_init(&empty[j], nt / 32);         // one arrival per consumer warp
     }
     fence_mbar_init();
   }
   __syncthreads();
-  const int nt = blockDim.x - 32;            // consumer threads
   if (int(threadIdx.x) >= nt) {
     // ---- producer warp (one lane issues) ----
     if (int(threadIdx.x) != nt) return;
@@ -332,11 +332,16 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
     // wait that ran out to every consumer
     const bool ok = mbar_wait_bounded(&full[st], (i / S) & 1, wait_cycles);
     if (ok) level_rows<T, TS, TPR>(stages + size_t(st) * stage_bytes, v, nt, grp);
+    // each warp releases the stage as soon as its lanes are done reading it,
+    // before the level barrier, so the next copy into it starts earlier
+    // (a warp whose wait ran out releases nothing: the producer's own bounded
+    // wait then ends it too)
+    const bool all_ok = __all_sync(0xffffffffu, ok);
+    if (all_ok && (threadIdx.x & 31) == 0 && i + S < nrec) mbar_arrive(&empty[st]);
     if (consumers_sync_or(!ok, nt)) {
       if (threadIdx.x == 0) atomicOr(err, 1);
       return;
     }
-    if (threadIdx.x == 0 && i + S < nrec) mbar_arrive(&empty[st]);
   }
   for (int i = threadIdx.x; i < m; i += nt) zloc[base + i] = v[i];
 }
