@@ -183,30 +183,61 @@ __device__ __forceinline__ void load4<float, __half>(const __half* vals, int t, 
 template <class T, class TS, int TPR>
 __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const int NT, const int G) {
   const int4 hdr = *reinterpret_cast<const int4*>(rec);
-  const int nr = hdr.x, K = hdr.y;
-  const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 16);
-  const TS* dinv = reinterpret_cast<const TS*>(rec + 16 + ((2 * nr + 15) & ~15));
+  const int4 hdr1 = *reinterpret_cast<const int4*>(rec + 16);
+  const int nr = hdr.x, K = hdr.y;          // rows, stored width
+  const int layout = hdr1.y;                // 0 column-major, 1 row-major by 4, 2 by node
+  const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 32);
+  const TS* dinv = reinterpret_cast<const TS*>(rec + 32 + ((2 * nr + 15) & ~15));
   const TS* vals = reinterpret_cast<const TS*>(rec + hdr.z);
   const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + hdr.w);
-  // entry k of row t: row-major padded to 4 for widths 1-4, else column-major
-  const bool packed = K > 0 && K <= 4;
-  auto at = [&](int t, int k) { return packed ? t * 4 + k : k * nr + t; };
-  if (TPR == 1 && G > 1) {
-    // a node's rows in order by one thread
-    for (int gt = threadIdx.x; gt * G < nr; gt += NT) {
-      for (int d = 0; d < G; ++d) {
-        const int t = gt * G + d;
-        const int row = lrows[t];
-        T acc = v[row];
-        for (int k = 0; k < K; ++k) acc = fma(-load_as<T, TS>(vals, at(t, k)), v[cols[at(t, k)]], acc);
-        v[row] = acc * load_as<T, TS>(dinv, t);
+  const TS* inn = reinterpret_cast<const TS*>(rec + hdr1.x);
+  if (layout == 2) {
+    // by node: the G rows' couplings to other nodes summed at once, then the
+    // rows of the node solved in order with the in-node coefficients
+    const int sub = TPR == 1 ? 0 : threadIdx.x % TPR;
+    const int groups = NT / TPR;
+    const int ngr = nr / G;
+    for (int round = 0; round < ngr; round += groups) {
+      const int gt = round + threadIdx.x / TPR;
+      const bool valid = gt < ngr;
+      T part[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        part[d] = T(0);
+        if (valid && d < G) {
+          const int t = gt * G + d;
+          for (int k = sub; k < K; k += TPR)
+            part[d] = fma(load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], part[d]);
+        }
+      }
+      if (TPR > 1) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+          for (int o = TPR / 2; o > 0; o >>= 1) part[d] += __shfl_down_sync(0xffffffffu, part[d], o, TPR);
+      }
+      if (valid && sub == 0) {
+        T y[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          if (d < G) {
+            const int t = gt * G + d;
+            const int row = lrows[t];
+            T acc = v[row] - part[d];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < d) acc = fma(-load_as<T, TS>(inn, t * (G - 1) + q), y[q], acc);
+            y[d] = acc * load_as<T, TS>(dinv, t);
+            v[row] = y[d];
+          }
+        }
       }
     }
   } else if (TPR == 1) {
     for (int t = threadIdx.x; t < nr; t += NT) {
       const int row = lrows[t];
       T acc = v[row];
-      if (packed) {
+      if (layout == 1) {
         // one vector load of the four columns and one of the four values
         const ushort4 c4 = reinterpret_cast<const ushort4*>(cols)[t];
         T a[4];
@@ -223,24 +254,22 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
   } else {
     const int sub = threadIdx.x % TPR;
     const int groups = NT / TPR;
-    const int ngr = nr / G;
-    // every thread runs the same number of rounds, so the shuffles stay
-    // convergent; a node's G rows go in order, each one's update visible to the
-    // next through the warp barrier
-    for (int round = 0; round < ngr; round += groups) {
-      const int gt = round + threadIdx.x / TPR;
-      for (int d = 0; d < G; ++d) {
-        const int t = gt * G + d;
-        T part = T(0);
-        if (gt < ngr)
-          for (int k = sub; k < K; k += TPR) part = fma(load_as<T, TS>(vals, at(t, k)), v[cols[at(t, k)]], part);
-#pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, TPR);
-        if (gt < ngr && sub == 0) {
-          const int row = lrows[t];
-          v[row] = (v[row] - part) * load_as<T, TS>(dinv, t);
+    // every thread runs the same number of rounds, so the shuffles stay convergent
+    for (int round = 0; round < nr; round += groups) {
+      const int t = round + threadIdx.x / TPR;
+      T part = T(0);
+      if (t < nr) {
+        if (layout == 1) {
+          for (int k = sub; k < 4; k += TPR) part = fma(load_as<T, TS>(vals, t * 4 + k), v[cols[t * 4 + k]], part);
+        } else {
+          for (int k = sub; k < K; k += TPR) part = fma(load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], part);
         }
-        if (G > 1) __syncwarp();
+      }
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, TPR);
+      if (t < nr && sub == 0) {
+        const int row = lrows[t];
+        v[row] = (v[row] - part) * load_as<T, TS>(dinv, t);
       }
     }
   }

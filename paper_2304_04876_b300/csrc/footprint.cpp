@@ -30,7 +30,8 @@ int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec) {
         const int64_t Kp = record_width(K);
         for (int t0 = 0; t0 < E.lev_nr[l]; t0 += piece) {
           const int64_t nr = std::min(piece, E.lev_nr[l] - t0);
-          total += 16 + a16(2 * nr) + a16(nr * vb) + a16(Kp * nr * vb) + a16(2 * Kp * nr);
+          total += 32 + a16(2 * nr) + a16(nr * vb) + a16(Kp * nr * vb) + a16(2 * Kp * nr) +
+                   (P.dpn > 1 ? a16((int64_t(P.dpn - 1) * nr + 1) * vb) : 0);
           ++count;
         }
       }

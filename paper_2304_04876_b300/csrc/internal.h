@@ -144,7 +144,7 @@ inline int record_width(int K) { return K == 0 ? 0 : (K <= 4 ? 4 : K); }
 // stays within kRecordCap bytes; a multiple of the node group g.
 constexpr size_t kRecordCap = 32 * 1024;
 inline int record_piece_rows(int nr, int K, int g, size_t vb) {
-  const size_t per_row = 2 + vb + size_t(record_width(K)) * (vb + 2);
+  const size_t per_row = 2 + vb + size_t(record_width(K)) * (vb + 2) + size_t(g - 1) * vb;
   size_t rows = (kRecordCap - 80) / per_row;
   rows = rows / size_t(g) * size_t(g);
   if (rows < size_t(g)) rows = g;

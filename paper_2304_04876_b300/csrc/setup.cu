@@ -813,13 +813,55 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     }
     c->max_levels = std::max(P.L.max_levels, P.U.max_levels);
     // Per-level records for the pipelined level-scheduled solve: for every
-    // subdomain its L levels then its U levels, each record 16-byte aligned:
-    //   int4 {rows, width, values offset, columns offset} | rows x uint16 local row | rows x T inverse
-    //   diagonal | width*rows x T values | width*rows x uint16 columns,
-    // every section padded to 16 bytes so a record is one bulk copy.
-    {
+    // subdomain its L levels then its U levels (wide levels split into pieces),
+    // each record 16-byte aligned and one bulk copy:
+    //   int4 {rows, stored width, values offset, columns offset} | int4 {in-node
+    //   offset, layout, 0, 0} | rows x uint16 local row | rows x T inverse
+    //   diagonal | width*rows x T values | width*rows x uint16 columns
+    //   [| (dpn-1)*rows + 1 x T in-node coefficients]
+    // every section padded to 16 bytes.  Layouts: 0 column-major; 1 row-major
+    // padded to 4 (widths 1-4, one unknown per node); 2 by node (several
+    // unknowns per node): the entries coupling a row to other nodes
+    // column-major, those to earlier-solved rows of its own node as
+    // coefficients by solve step (row t, step q at t*(dpn-1)+q; one trailing
+    // zero absorbs the padding).  More than 4 unknowns per node: no records
+    // (the unpipelined kernel solves).
+    if (P.dpn <= 4) {
       const size_t vb = c->fp16 ? sizeof(__half) : c->fp32 ? sizeof(float) : sizeof(double);
+      const int Gn = P.dpn;
       auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+      struct RecLayout { int layout; size_t K, o_l, o_d, o_v, o_c, o_i, end; };
+      // solve step of local column `col` inside its node (L: increasing, U: decreasing)
+      auto step_of = [&](bool lower, int col) { return lower ? col % Gn : Gn - 1 - col % Gn; };
+      auto layout_of = [&](const EllPlan& E, bool lower, int l, size_t t0, size_t nr) {
+        RecLayout R;
+        const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
+        if (Gn > 1) {
+          size_t koff = 0;
+          for (size_t t = 0; t < nr; ++t) {
+            const int row = E.lrows[E.lev_start[l] + t0 + t];
+            size_t cnt = 0;
+            for (size_t k = 0; k < K; ++k) {
+              const int64_t slot = E.lev_off[l] + int64_t(k) * L_nr + t0 + t;
+              if (E.src[slot] >= 0 && E.col[slot] / Gn != row / Gn) ++cnt;
+            }
+            koff = std::max(koff, cnt);
+          }
+          R.layout = 2;
+          R.K = koff;
+        } else {
+          R.layout = record_width(E.lev_K[l]) == 4 ? 1 : 0;
+          R.K = record_width(E.lev_K[l]);
+        }
+        (void)lower;
+        R.o_l = 32;
+        R.o_d = R.o_l + a16(2 * nr);
+        R.o_v = R.o_d + a16(nr * vb);
+        R.o_c = R.o_v + a16(R.K * nr * vb);
+        R.o_i = R.o_c + a16(2 * R.K * nr);
+        R.end = R.layout == 2 ? R.o_i + a16((size_t(Gn - 1) * nr + 1) * vb) : R.o_i;
+        return R;
+      };
       std::vector<int> rec_ptr(nsub + 1, 0);
       std::vector<uint32_t> rec_off16, rec_bytes;
       std::vector<int> rec_lev, rec_t0;            // level and first row of every record
@@ -827,37 +869,47 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       std::vector<uint32_t> valposL(P.L.slots), valposU(P.U.slots), dinvposL(P.sum_m), dinvposU(P.sum_m);
       size_t total = 0;
       for (int pass = 0; pass < 2; ++pass) {      // pass 0 sizes, pass 1 fills
-        std::vector<uint8_t> dummy;
         total = 0;
         for (int q = 0; q < nsub; ++q) {
           for (int side = 0; side < 2; ++side) {
             const EllPlan& E = side == 0 ? P.L : P.U;
+            const bool lower = side == 0;
             for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
               // a wide level becomes several records (rows are independent
               // within a level, node groups kept whole)
-              const size_t L_nr = E.lev_nr[l], K = E.lev_K[l], Kp = record_width(E.lev_K[l]);
-              const bool packed = Kp == 4;      // row-major, 4 entries per row
-              const size_t piece = record_piece_rows(E.lev_nr[l], E.lev_K[l], P.dpn, vb);
+              const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
+              const size_t piece = record_piece_rows(E.lev_nr[l], E.lev_K[l], Gn, vb);
               for (size_t t0 = 0; t0 < L_nr; t0 += piece) {
                 const size_t nr = std::min(piece, L_nr - t0);
-                const size_t o_l = total + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
-                             o_c = o_v + a16(Kp * nr * vb), end = o_c + a16(2 * Kp * nr);
+                const RecLayout R = layout_of(E, lower, l, t0, nr);
                 if (pass == 1) {
                   rec_off16.push_back(static_cast<uint32_t>(total / 16));
-                  rec_bytes.push_back(static_cast<uint32_t>(end - total));
+                  rec_bytes.push_back(static_cast<uint32_t>(R.end));
                   rec_lev.push_back(l);
                   rec_t0.push_back(static_cast<int>(t0));
-                  rec_is_L.push_back(side == 0);
-                  uint32_t* dp = side == 0 ? dinvposL.data() : dinvposU.data();
-                  uint32_t* vp = side == 0 ? valposL.data() : valposU.data();
+                  rec_is_L.push_back(lower);
+                  uint32_t* dp = lower ? dinvposL.data() : dinvposU.data();
+                  uint32_t* vp = lower ? valposL.data() : valposU.data();
                   for (size_t t = 0; t < nr; ++t)
-                    dp[E.lev_start[l] + t0 + t] = static_cast<uint32_t>((o_d + t * vb) / vb);
-                  for (size_t k = 0; k < K; ++k)
-                    for (size_t t = 0; t < nr; ++t)
-                      vp[E.lev_off[l] + k * L_nr + t0 + t] =
-                          static_cast<uint32_t>((o_v + (packed ? t * 4 + k : k * nr + t) * vb) / vb);
+                    dp[E.lev_start[l] + t0 + t] = static_cast<uint32_t>((total + R.o_d + t * vb) / vb);
+                  for (size_t t = 0; t < nr; ++t) {
+                    const int row = E.lrows[E.lev_start[l] + t0 + t];
+                    size_t koff = 0;
+                    for (size_t k = 0; k < K; ++k) {
+                      const int64_t slot = E.lev_off[l] + int64_t(k) * L_nr + t0 + t;
+                      size_t pos;
+                      if (R.layout == 0) pos = R.o_v + (k * nr + t) * vb;
+                      else if (R.layout == 1) pos = R.o_v + (t * 4 + k) * vb;
+                      else if (E.src[slot] < 0) pos = R.o_i + size_t(Gn - 1) * nr * vb;     // padding: the zero
+                      else if (E.col[slot] / Gn == row / Gn)
+                        pos = R.o_i + (t * (Gn - 1) + step_of(lower, E.col[slot])) * vb;
+                      else
+                        pos = R.o_v + (koff++ * nr + t) * vb;
+                      vp[slot] = static_cast<uint32_t>((total + pos) / vb);
+                    }
+                  }
                 }
-                total = end;
+                total += R.end;
               }
             }
           }
@@ -870,28 +922,37 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       std::vector<uint8_t> host(total, 0);
       size_t stage = 16;
       for (size_t rr = 0; rr < rec_off16.size(); ++rr) {
-        const EllPlan& E = rec_is_L[rr] ? P.L : P.U;
+        const bool lower = rec_is_L[rr];
+        const EllPlan& E = lower ? P.L : P.U;
         const int l = rec_lev[rr];
-        const size_t L_nr = E.lev_nr[l], K = E.lev_K[l], Kp = record_width(E.lev_K[l]);
+        const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
         const size_t t0 = rec_t0[rr];
-        const size_t nr = std::min(size_t(record_piece_rows(E.lev_nr[l], E.lev_K[l], P.dpn, vb)), L_nr - t0);
+        const size_t nr = std::min(size_t(record_piece_rows(E.lev_nr[l], E.lev_K[l], Gn, vb)), L_nr - t0);
+        const RecLayout R = layout_of(E, lower, l, t0, nr);
         const size_t base = size_t(rec_off16[rr]) * 16;
-        const size_t o_l = base + 16, o_d = o_l + a16(2 * nr), o_v = o_d + a16(nr * vb),
-                     o_c = o_v + a16(Kp * nr * vb);
-        // header: rows, width, and the byte offsets of the values and columns
-        const int hdr[4] = {static_cast<int>(nr), static_cast<int>(K), static_cast<int>(o_v - base),
-                            static_cast<int>(o_c - base)};
-        std::memcpy(&host[base], hdr, 16);
-        std::memcpy(&host[o_l], &E.lrows[E.lev_start[l] + t0], 2 * nr);
-        if (Kp == 4) {
-          // row-major, padded to 4 with the row itself (value zero)
-          uint16_t* cc = reinterpret_cast<uint16_t*>(&host[o_c]);
-          for (size_t t = 0; t < nr; ++t)
-            for (size_t k = 0; k < 4; ++k)
-              cc[t * 4 + k] = k < K ? E.col[E.lev_off[l] + k * L_nr + t0 + t] : E.lrows[E.lev_start[l] + t0 + t];
-        } else {
-          for (size_t k = 0; k < K; ++k)
-            std::memcpy(&host[o_c + 2 * k * nr], &E.col[E.lev_off[l] + k * L_nr + t0], 2 * nr);
+        const int hdr[8] = {static_cast<int>(nr), static_cast<int>(R.K), static_cast<int>(R.o_v),
+                            static_cast<int>(R.o_c), static_cast<int>(R.o_i), R.layout, 0, 0};
+        std::memcpy(&host[base], hdr, 32);
+        std::memcpy(&host[base + R.o_l], &E.lrows[E.lev_start[l] + t0], 2 * nr);
+        uint16_t* cc = reinterpret_cast<uint16_t*>(&host[base + R.o_c]);
+        for (size_t t = 0; t < nr; ++t) {
+          const int row = E.lrows[E.lev_start[l] + t0 + t];
+          size_t koff = 0;
+          for (size_t k = 0; k < R.K; ++k) {
+            if (R.layout == 1) {
+              cc[t * 4 + k] = k < K ? E.col[E.lev_off[l] + k * L_nr + t0 + t] : static_cast<uint16_t>(row);
+            } else if (R.layout == 0) {
+              cc[k * nr + t] = E.col[E.lev_off[l] + k * L_nr + t0 + t];
+            }
+          }
+          if (R.layout == 2) {
+            // off-node columns in entry order, then the row itself as padding
+            for (size_t k = 0; k < K; ++k) {
+              const int64_t slot = E.lev_off[l] + int64_t(k) * L_nr + t0 + t;
+              if (E.src[slot] >= 0 && E.col[slot] / Gn != row / Gn) cc[koff++ * nr + t] = E.col[slot];
+            }
+            for (; koff < R.K; ++koff) cc[koff * nr + t] = static_cast<uint16_t>(row);
+          }
         }
         stage = std::max<size_t>(stage, rec_bytes[rr]);
       }
