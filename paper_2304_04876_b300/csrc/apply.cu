@@ -28,19 +28,21 @@ namespace gdsw {
 namespace {
 
 // v = R_s r for one subdomain (m entries from base) by `nt` threads (this
-// thread is `tid`): eight indices, then eight values, in flight per thread.
+// thread is `tid`): sixteen indices, then sixteen values, in flight per thread
+// (each round costs two dependent global-memory latencies).
 template <class T>
 __device__ __forceinline__ void gather_sub(const double* __restrict__ r, const int* __restrict__ om_dofs,
                                            int base, int m, T* v, int tid, int nt) {
-  for (int i0 = tid; i0 < m; i0 += 8 * nt) {
-    int idx[8];
-    double rv[8];
+  constexpr int U = 16;
+  for (int i0 = tid; i0 < m; i0 += U * nt) {
+    int idx[U];
+    double rv[U];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) idx[u] = i0 + u * nt < m ? om_dofs[base + i0 + u * nt] : -1;
+    for (int u = 0; u < U; ++u) idx[u] = i0 + u * nt < m ? om_dofs[base + i0 + u * nt] : -1;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) rv[u] = idx[u] >= 0 ? r[idx[u]] : 0.0;
+    for (int u = 0; u < U; ++u) rv[u] = idx[u] >= 0 ? r[idx[u]] : 0.0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+    for (int u = 0; u < U; ++u)
       if (i0 + u * nt < m) v[i0 + u * nt] = T(rv[u]);
   }
 }
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
                                                              const uint8_t* __restrict__ stream, int stage_bytes,
                                                              T* __restrict__ zloc,
                                                              const KrylovScalars* __restrict__ ks, int* err,
-                                                             long long wait_cycles, int grp) {
+                                                             long long wait_cycles, int grp, int stall_test) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[S];
   __shared__ __align__(8) uint64_t empty[S];
@@ -340,6 +342,9 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
         atomicOr(err, 1);      // the consumers stopped (their own wait ran out)
         break;
       }
+      // failure test: record 1 is never copied, so the consumers' wait for it
+      // runs out (its `full` barrier is a flag that nothing sets)
+      if (stall_test && j == 1) continue;
       fence_proxy_async_smem();
       const unsigned nb = rec_bytes[r0 + j];
       mbar_expect_tx(&full[st], nb);
@@ -347,9 +352,11 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
       last[st] = j;
     }
     // every copy issued has landed before the CTA's shared memory can go away
+    // (waited for with at least the default bound, however short the caller's)
+    const long long drain = wait_cycles > kDefaultWaitCycles ? wait_cycles : kDefaultWaitCycles;
 #pragma unroll
     for (int st = 0; st < S; ++st)
-      if (last[st] >= 0) mbar_wait_bounded(&full[st], (last[st] / S) & 1, wait_cycles);
+      if (last[st] >= 0) mbar_wait_bounded(&full[st], (last[st] / S) & 1, drain);
     return;
   }
   // ---- consumer warps ----
@@ -709,7 +716,7 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
   k_local_pipe<T, __half, SS, TP><<<c->nsub, c->rec_consumers + 32, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr,            \
                                                             c->rec_off16, c->rec_bytes, c->rec_stream,       \
                                                             c->rec_stage_bytes, zl, ks, c->derr,             \
-                                                            c->wait_cycles, c->dpn)
+                                                            c->wait_cycles, c->dpn, c->stall_test)
         switch (key) {
           case 201: GDSW_PIPE_LAUNCH(2, 1); break;
           case 301: GDSW_PIPE_LAUNCH(3, 1); break;
@@ -726,7 +733,7 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
 #define GDSW_PIPE_LAUNCH(SS, TP)                                                                     \
   k_local_pipe<T, T, SS, TP><<<c->nsub, c->rec_consumers + 32, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, \
                                                        c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, \
-                                                       ks, c->derr, c->wait_cycles, c->dpn)
+                                                       ks, c->derr, c->wait_cycles, c->dpn, c->stall_test)
       switch (key) {
         case 201: GDSW_PIPE_LAUNCH(2, 1); break;
         case 301: GDSW_PIPE_LAUNCH(3, 1); break;
@@ -859,6 +866,9 @@ gdsw_status pipe_occupancy(const Ctx* c, int S, size_t shm, int* per_sm) {
 // the speed only, never the result.
 gdsw_status tune_local(Ctx* c) {
   const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  // timed with the default wait bound, whatever the handle's
+  const long long keep_wait = c->wait_cycles;
+  c->wait_cycles = kDefaultWaitCycles;
   cudaStream_t s;
   GDSW_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   double* r = nullptr;
@@ -918,6 +928,7 @@ gdsw_status tune_local(Ctx* c) {
   c->rec_stages = best_s;
   c->rec_consumers = best_nt;
   c->tri_threads = best_s == 0 ? best_tri : 256;
+  c->wait_cycles = keep_wait;
   if (r) cudaFree(r);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -988,7 +999,9 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(allow_max_dynamic_smem(k_local_dense<double>));
   }
   GDSW_CK(allow_max_dynamic_smem(k_coarse_gemv));
-  if (c->rec_stages > 0 && c->opt.autotune) {
+  // GDSW_TEST_STALL=1: the failure test of the bounded waits (see k_local_pipe)
+  if (const char* e = getenv("GDSW_TEST_STALL")) c->stall_test = e[0] == '1';
+  if (c->rec_stages > 0 && c->opt.autotune && !c->stall_test) {
     // GDSW_LOCAL_SHAPE="stages,threads" fixes the shape instead of timing it
     // (for profilers, under which the timings mean nothing)
     if (const char* e = getenv("GDSW_LOCAL_SHAPE")) {

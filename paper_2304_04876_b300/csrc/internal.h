@@ -256,6 +256,7 @@ struct Ctx {
   int tri_threads = 256;             // threads of the unpipelined level / Jacobi solve
   int* derr = nullptr;               // device error flags (bounded waits that ran out)
   long long wait_cycles = 0;         // bound on each device-side wait, SM clock cycles
+  int stall_test = 0;                // failure test: one record copy withheld
   // exact local solver: dense inverses
   void* ainv = nullptr;
   int64_t* ainv_off = nullptr;

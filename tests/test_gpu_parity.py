@@ -323,3 +323,29 @@ def test_bytes_required_bounds_the_handle(make, opts):
     h.close()
     assert held <= resident <= 1.15 * held + (1 << 20), (held, resident)
     assert scratch > 0
+
+
+def test_bounded_wait_that_runs_out_reports_timeout(monkeypatch):
+    """A local-solve wait that can never complete (GDSW_TEST_STALL=1 withholds one
+    level record's copy, so its barrier is a flag that nothing sets) runs out after
+    its budget (here about 10 ms): the kernel records it, lets the copies it did issue
+    land and returns, and the host reports GDSW_ERR_TIMEOUT.  The context stays usable:
+    a handle without the stall computes normally afterwards."""
+    from paper_2304_04876_b300 import gdsw as G
+    import torch
+    prob = P.poisson_problem(12, 4)
+    monkeypatch.setenv("GDSW_TEST_STALL", "1")
+    h = gpu_handle(prob, local_solver="ic0", wait_budget_cycles=20_000_000)
+    monkeypatch.delenv("GDSW_TEST_STALL")
+    if h.stats()["local_stages"] == 0:
+        pytest.skip("the pipelined local solve is not used for this problem")
+    r = np.random.default_rng(0).uniform(-1, 1, prob.A.n)
+    rt = torch.tensor(r, dtype=torch.float64, device="cuda")
+    zt = torch.empty_like(rt)
+    with pytest.raises(G.GdswError) as e:
+        h.apply_timed(rt, zt)
+    assert e.value.status == G.ERR_TIMEOUT
+    h.close()
+    M = oracle_for(prob, local="ic0")
+    h2 = gpu_handle(prob, local_solver="ic0")
+    assert relerr(gpu_apply(h2, r), M.apply(r)) <= TOL_FP64
