@@ -54,9 +54,10 @@ typedef enum {
 
 /* local solver A_s^-1 (Sec. V-B) */
 enum { GDSW_LOCAL_EXACT = 0, /* Cholesky of A_s, applied as its dense inverse   */
-       GDSW_LOCAL_IC0 = 1,   /* IC(0) by synchronous fixed-point sweeps          */
-       GDSW_LOCAL_ILU0 = 2   /* ILU(0) by synchronous fixed-point sweeps         */ };
-/* triangular solves of IC(0)/ILU(0) factors (Sec. V-B2, V-B3) */
+       GDSW_LOCAL_IC0 = 1,   /* IC(k) by synchronous fixed-point sweeps (k =
+                                gdsw_options.fill_level, 0 by default)         */
+       GDSW_LOCAL_ILU0 = 2   /* ILU(k) likewise                                 */ };
+/* triangular solves of the IC(k)/ILU(k) factors (Sec. V-B2, V-B3) */
 enum { GDSW_TRSV_LEVELSCHED = 0, GDSW_TRSV_JACOBI = 1 };
 /* storage/compute precision of the preconditioner (Sec. V-A2); the Krylov
  * vectors, dot products, residual and the coarse solve stay FP64.

@@ -1,15 +1,18 @@
-// The preconditioner apply z = M^-1 r (Sec. III, Eq. 1) as four launches:
+// The preconditioner apply z = M^-1 r (Sec. III, Eq. 1) as four phases, the
+// one-level branch and the coarse branch on two streams:
 //
 //  1. local:   one CTA per overlapping subdomain gathers r_s = R_s r into
-//              shared memory and solves A_s z_s = r_s there (level-scheduled
-//              or Jacobi-sweep triangular solves of the IC(0)/ILU(0) factor,
-//              or the dense inverse of the exact solver); z_s goes to the
-//              concatenated local-solution buffer.
-//  2. phiT:    one CTA per Phi block (subdomain interior or interface
-//              component) forms the partial products Phi_b^T r_b.
+//              shared memory and solves A_s z_s = r_s there: level-scheduled
+//              substitution with the IC(k)/ILU(k) factors streamed as
+//              per-level records by a producer warp (bulk copies into a ring),
+//              the same from L2 without the ring, Jacobi sweeps, or the dense
+//              inverse of the exact solver; z_s goes to the concatenated
+//              local-solution buffer.
+//  2. phiT:    partial products Phi_b^T r_b per chunk of a Phi block (a
+//              subdomain interior or an interface component).
 //  3. coarse:  c = sum of partials per coarse column (fixed order), then
 //              y = A0^-1 c as a dense FP64 GEMV with the explicit inverse.
-//  4. combine: every unknown is owned by exactly one Phi block; its CTA sums
+//  4. combine: every unknown is owned by exactly one Phi block; its thread sums
 //              the overlapping local solutions in ascending subdomain order
 //              (the deterministic scatter-add of sum_s R_s^T z_s) and adds
 //              the prolongation (Phi y)_g, optionally fusing the PCG dots.
@@ -331,26 +334,38 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
   }
   __syncthreads();
   if (int(threadIdx.x) >= nt) {
-    // ---- producer warp (one lane issues) ----
-    if (int(threadIdx.x) != nt) return;
+    // ---- producer warp: the lanes fetch the record offsets and sizes 32 at a
+    // time, lane 0 waits for free stages and issues the copies ----
+    const int lane = threadIdx.x & 31;
     int last[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) last[j] = -1;
+    uint32_t my_off = 0, my_nb = 0;
     for (int j = 0; j < nrec; ++j) {
-      const int st = j % S;
-      if (j >= S && !mbar_wait_bounded(&empty[st], ((j / S) - 1) & 1, wait_cycles)) {
-        atomicOr(err, 1);      // the consumers stopped (their own wait ran out)
-        break;
+      if ((j & 31) == 0 && j + lane < nrec) {
+        my_off = rec_off16[r0 + j + lane];
+        my_nb = rec_bytes[r0 + j + lane];
       }
-      // failure test: record 1 is never copied, so the consumers' wait for it
-      // runs out (its `full` barrier is a flag that nothing sets)
-      if (stall_test && j == 1) continue;
-      fence_proxy_async_smem();
-      const unsigned nb = rec_bytes[r0 + j];
-      mbar_expect_tx(&full[st], nb);
-      bulk_g2s(stages + size_t(st) * stage_bytes, stream + size_t(rec_off16[r0 + j]) * 16, nb, &full[st]);
-      last[st] = j;
+      const uint32_t off16 = __shfl_sync(0xffffffffu, my_off, j & 31);
+      const uint32_t nb = __shfl_sync(0xffffffffu, my_nb, j & 31);
+      const int st = j % S;
+      int stop = 0;
+      if (lane == 0) {
+        if (j >= S && !mbar_wait_bounded(&empty[st], ((j / S) - 1) & 1, wait_cycles)) {
+          atomicOr(err, 1);    // the consumers stopped (their own wait ran out)
+          stop = 1;
+        } else if (!(stall_test && j == 1)) {
+          // (failure test: record 1 is never copied, so the consumers' wait
+          // for it runs out; its `full` barrier is a flag that nothing sets)
+          fence_proxy_async_smem();
+          mbar_expect_tx(&full[st], nb);
+          bulk_g2s(stages + size_t(st) * stage_bytes, stream + size_t(off16) * 16, nb, &full[st]);
+          last[st] = j;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, stop, 0)) break;
     }
+    if (lane != 0) return;
     // every copy issued has landed before the CTA's shared memory can go away
     // (waited for with at least the default bound, however short the caller's)
     const long long drain = wait_cycles > kDefaultWaitCycles ? wait_cycles : kDefaultWaitCycles;

@@ -1,7 +1,9 @@
-// Krylov loops around the preconditioner: CSR SpMV, fused vector updates with
-// deterministic reductions, PCG with its iteration captured in a CUDA graph
-// behind a device-side while condition, and right-preconditioned GMRES(m)
-// (Sec. VII) with classical Gram-Schmidt applied twice.
+// Krylov loops around the preconditioner: CSR SpMV (row tiles for short rows,
+// W lanes per row for long ones), fused vector updates with deterministic
+// reductions, PCG with its iteration captured in a CUDA graph behind a
+// device-side while condition, and right-preconditioned GMRES(m) (Sec. VII)
+// with the Arnoldi process, Hessenberg matrix and Givens rotations on the
+// device (classical Gram-Schmidt twice, or the single-reduce form).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
