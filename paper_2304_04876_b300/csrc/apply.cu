@@ -553,25 +553,21 @@ __global__ void k_coarse_c(int n0, const int* __restrict__ cs_ptr, const int* __
   }
 }
 
-// y = A0^-1 c with the explicit inverse (one dense block per problem; c staged
-// in shared memory when there is a single problem).  Two warps per row, each
-// over half of the columns with eight independent FMA chains per lane (FP64
-// latency); the halves are added in a fixed order.
+// y = A0^-1 c with the explicit inverse (one dense block per problem).  Two
+// warps per row, each over half of the columns with eight independent FMA
+// chains per lane (FP64 latency); the halves are added in a fixed order.  c is
+// read through L1/L2, not staged in shared memory, so the CTAs need almost
+// none and fit beside the local solve's CTAs on the same SMs (the two branches
+// of the apply overlap).
 __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __restrict__ Ainv,
                                                      const int* __restrict__ coarse_prob,
                                                      const int* __restrict__ prob_c0,
-                                                     const int64_t* __restrict__ a0_off, int staged,
+                                                     const int64_t* __restrict__ a0_off,
                                                      const double* __restrict__ c,
                                                      double* __restrict__ y, float* __restrict__ y32,
                                                      const KrylovScalars* __restrict__ ks) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double half_sum[4][2];
   if (ks != nullptr && ks->done) return;
-  double* cs = reinterpret_cast<double*>(smem_raw);
-  if (staged) {
-    for (int l = threadIdx.x; l < n0; l += blockDim.x) cs[l] = c[l];
-    __syncthreads();
-  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int slot = w >> 1, h = w & 1;                  // row slot in the CTA, half of the row
   for (int row0 = blockIdx.x * 4; row0 < n0; row0 += gridDim.x * 4) {
@@ -581,7 +577,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
       const int pr = coarse_prob[row];
       const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;
       const double* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
-      const double* cv = staged ? cs + cp : c + cp;
+      const double* cv = c + cp;
       const int j0 = h == 0 ? 0 : np / 2, j1 = h == 0 ? np / 2 : np;
       double a[8];
 #pragma unroll
@@ -788,9 +784,9 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
   if (c->n0 == 0) return GDSW_OK;
   k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, ks);
   const int grid = std::min((c->n0 + 3) / 4, kNumSMs * 8);
-  const int staged = c->nprob == 1;
-  k_coarse_gemv<<<grid, 256, staged ? size_t(c->n0) * sizeof(double) : 16, s>>>(
-      c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, staged, c->cvec, c->yvec, c->yvec32, ks);
+
+  k_coarse_gemv<<<grid, 256, 0, s>>>(c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, c->cvec, c->yvec,
+                                      c->yvec32, ks);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -971,8 +967,6 @@ gdsw_status apply_configure(Ctx* c) {
     set_error("subdomain of %d unknowns does not fit the local solve's shared memory", c->max_m);
     return GDSW_ERR_UNSUPPORTED;
   }
-  const size_t shm_coarse = c->nprob == 1 ? size_t(c->n0) * sizeof(double) : 16;
-  if (shm_coarse > 227 * 1024) { set_error("coarse dimension too large"); return GDSW_ERR_UNSUPPORTED; }
   // pipelined level-scheduled solve: the ring depth (6, 4, 3 or 2 stages)
   // that runs all subdomains in the fewest waves of resident CTAs (one CTA per
   // subdomain; the local solve is latency-bound, so a wave that is only partly
@@ -1013,7 +1007,6 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(allow_max_dynamic_smem(k_local_tri<double>));
     GDSW_CK(allow_max_dynamic_smem(k_local_dense<double>));
   }
-  GDSW_CK(allow_max_dynamic_smem(k_coarse_gemv));
   // GDSW_TEST_STALL=1: the failure test of the bounded waits (see k_local_pipe)
   if (const char* e = getenv("GDSW_TEST_STALL")) c->stall_test = e[0] == '1';
   if (c->rec_stages > 0 && c->opt.autotune && !c->stall_test) {
