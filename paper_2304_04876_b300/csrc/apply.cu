@@ -299,11 +299,12 @@ __device__ __forceinline__ bool consumers_sync_or(bool pred, int nt) {
 }
 
 // z_s = (L U)^-1 r_s for every subdomain s (one CTA each), level by level.
-// The producer warp copies the records of subdomain s, one per level, with
-// bulk copies into a ring of S stages (full[st] completes when a record has
-// landed, empty[st] when the consumers are done with it); the consumers wait
-// for a record, update its rows in shared memory, meet at one barrier per
-// level and release the stage.  The copy issue is off the consumers' path.
+// The producer warp copies the level records of subdomain s, several small
+// consecutive ones packed into one bulk copy, into a ring of S stages
+// (full[st] completes when a pack has landed, empty[st] when every consumer
+// warp is done with it); the consumers wait for a pack, update the rows of its
+// levels in shared memory with one barrier per level, and release the stage.
+// The copy issue is off the consumers' path.
 template <class T, class TS, int S, int TPR>
 __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __restrict__ r,
                                                              const int* __restrict__ om_ptr,
@@ -379,19 +380,28 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
   consumers_sync_or(false, nt);
   for (int i = 0; i < nrec; ++i) {
     const int st = i % S;
-    // each thread waits for the record itself; the barrier below carries a
-    // wait that ran out to every consumer
+    // each thread waits for the pack itself, then all agree that it has
+    // landed before any reads it (the barrier carries a wait that ran out to
+    // every consumer)
     const bool ok = mbar_wait_bounded(&full[st], (i / S) & 1, wait_cycles);
-    if (ok) level_rows<T, TS, TPR>(stages + size_t(st) * stage_bytes, v, nt, grp);
-    // each warp releases the stage as soon as its lanes are done reading it,
-    // before the level barrier, so the next copy into it starts earlier
-    // (a warp whose wait ran out releases nothing: the producer's own bounded
-    // wait then ends it too)
-    const bool all_ok = __all_sync(0xffffffffu, ok);
-    if (all_ok && (threadIdx.x & 31) == 0 && i + S < nrec) mbar_arrive(&empty[st]);
     if (consumers_sync_or(!ok, nt)) {
       if (threadIdx.x == 0) atomicOr(err, 1);
       return;
+    }
+    // the stage holds a pack of consecutive level records (their count in the
+    // first header, each record's size in its own); one barrier per level
+    const unsigned char* rec = stages + size_t(st) * stage_bytes;
+    const int count = reinterpret_cast<const int*>(rec)[7];
+    for (int q = 0; q < count; ++q) {
+      const unsigned char* next = rec + reinterpret_cast<const int*>(rec)[6];
+      level_rows<T, TS, TPR>(rec, v, nt, grp);
+      // each warp releases the stage as soon as its lanes are done reading it
+      if (q + 1 == count) {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0 && i + S < nrec) mbar_arrive(&empty[st]);
+      }
+      consumers_sync_or(false, nt);
+      rec = next;
     }
   }
   for (int i = threadIdx.x; i < m; i += nt) zloc[base + i] = v[i];

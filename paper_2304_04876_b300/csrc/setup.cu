@@ -931,7 +931,8 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         const RecLayout R = layout_of(E, lower, l, t0, nr);
         const size_t base = size_t(rec_off16[rr]) * 16;
         const int hdr[8] = {static_cast<int>(nr), static_cast<int>(R.K), static_cast<int>(R.o_v),
-                            static_cast<int>(R.o_c), static_cast<int>(R.o_i), R.layout, 0, 0};
+                            static_cast<int>(R.o_c), static_cast<int>(R.o_i), R.layout,
+                            static_cast<int>(R.end), 1};
         std::memcpy(&host[base], hdr, 32);
         std::memcpy(&host[base + R.o_l], &E.lrows[E.lev_start[l] + t0], 2 * nr);
         uint16_t* cc = reinterpret_cast<uint16_t*>(&host[base + R.o_c]);
@@ -956,12 +957,32 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         }
         stage = std::max<size_t>(stage, rec_bytes[rr]);
       }
+      // Consecutive records of a subdomain are contiguous in the stream: pack
+      // them greedily into one bulk copy while the pack stays within the largest
+      // single record (so a ring stage still holds any pack).  The first record
+      // of a pack carries the pack's record count (header word 7); every record
+      // its own size (word 6), so the consumers step through the pack.
+      std::vector<int> pk_ptr(nsub + 1, 0);
+      std::vector<uint32_t> pk_off16, pk_bytes;
+      for (int q = 0; q < nsub; ++q) {
+        for (int rr = rec_ptr[q]; rr < rec_ptr[q + 1];) {
+          size_t bytes = rec_bytes[rr];
+          int cnt = 1;
+          while (rr + cnt < rec_ptr[q + 1] && bytes + rec_bytes[rr + cnt] <= stage) bytes += rec_bytes[rr + cnt++];
+          int* first = reinterpret_cast<int*>(&host[size_t(rec_off16[rr]) * 16]);
+          first[7] = cnt;
+          pk_off16.push_back(rec_off16[rr]);
+          pk_bytes.push_back(static_cast<uint32_t>(bytes));
+          rr += cnt;
+        }
+        pk_ptr[q + 1] = static_cast<int>(pk_off16.size());
+      }
       uint8_t* d_stream;
       GDSW_TRY(upload(c, &d_stream, host, s));
       c->rec_stream = d_stream;
-      GDSW_TRY(upload(c, &c->rec_ptr, rec_ptr, s));
-      GDSW_TRY(upload(c, &c->rec_off16, rec_off16, s));
-      GDSW_TRY(upload(c, &c->rec_bytes, rec_bytes, s));
+      GDSW_TRY(upload(c, &c->rec_ptr, pk_ptr, s));
+      GDSW_TRY(upload(c, &c->rec_off16, pk_off16, s));
+      GDSW_TRY(upload(c, &c->rec_bytes, pk_bytes, s));
       c->rec_stage_bytes = static_cast<int>(stage);
       int maxK = 0;
       for (int kk : P.L.lev_K) maxK = std::max(maxK, kk);
