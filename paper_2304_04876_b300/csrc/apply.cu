@@ -588,7 +588,9 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
       const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;
       const double* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
       const double* cv = c + cp;
-      const int j0 = h == 0 ? 0 : np / 2, j1 = h == 0 ? np / 2 : np;
+      // short rows (small problems of a batch) go whole to the first warp
+      const int split = np >= 1024 ? np / 2 : np;
+      const int j0 = h == 0 ? 0 : split, j1 = h == 0 ? split : np;
       double a[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) a[u] = 0.0;
@@ -906,7 +908,7 @@ gdsw_status tune_local(Ctx* c) {
   int best_s = keep_s, best_nt = keep_nt;
   const int cand[4] = {6, 4, 3, 2};
   for (int q = 0; q < 4 && st == GDSW_OK; ++q) {
-    for (int nt : {128, 256, 512, 992}) {
+    for (int nt : {64, 128, 256, 512, 992}) {
       if (c->rec_tpr == 8 && nt < 256) continue;
       c->rec_stages = cand[q];
       c->rec_consumers = nt;
@@ -1025,7 +1027,7 @@ gdsw_status apply_configure(Ctx* c) {
     if (const char* e = getenv("GDSW_LOCAL_SHAPE")) {
       int st = 0, nt = 0;
       if (sscanf(e, "%d,%d", &st, &nt) == 2 && (st == 0 || st == 2 || st == 3 || st == 4 || st == 6) &&
-          (nt == 128 || nt == 256 || nt == 512 || nt == 992 || nt == 1024)) {
+          (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 992 || nt == 1024)) {
         c->rec_stages = st;
         if (st > 0) c->rec_consumers = nt == 1024 ? 992 : nt; else c->tri_threads = nt == 992 ? 1024 : nt;
       }
