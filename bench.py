@@ -33,6 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2304_04876_b300 import problems as P  # noqa: E402
+from paper_2304_04876_b300 import replicas as R  # noqa: E402
 
 VARIANTS = {
     "fp64_levelsched": dict(local_solver="ic0", trsv="levelsched", precision="fp64"),
@@ -379,7 +380,7 @@ def run_single(args, world, rank, dist, barrier):
     if cfg == 3:
         bs = [torch.tensor(prob.b, dtype=torch.float64, device="cuda")]
     else:
-        bs = [torch.tensor(P.rhs_uniform(n, (rank * 5 + k) % 997), dtype=torch.float64, device="cuda")
+        bs = [torch.tensor(P.rhs_uniform(n, R.rhs_seed(rank, k)), dtype=torch.float64, device="cuda")
               for k in range(5)]
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -387,10 +388,7 @@ def run_single(args, world, rank, dist, barrier):
     clocks.start()
     el, infos = timed_solves(h, bs, x, args.steps, args.warmup, stream, barrier)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = R.max_over_ranks(el, dist, "cuda")
     iters = [i.iters for i in infos]
     # end to end through the C ABI with host (page-locked) buffers
     bh = bs[0].cpu().pin_memory()
@@ -402,16 +400,12 @@ def run_single(args, world, rank, dist, barrier):
     for _ in range(args.steps):
         xh.zero_()
         h.solve_host(bh, xh)
-    e2e_el = time.perf_counter() - te
-    if dist is not None:
-        t = torch.tensor([e2e_el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_el = float(t.item())
+    e2e_el = R.max_over_ranks(time.perf_counter() - te, dist, "cuda")
     vb = 4 if opts.get("precision") in ("fp32", "fp16") else 8
     fb = 2 if opts.get("precision") == "fp16" else vb
     km = kernel_measurements(h, st, vb, stream, bs[0], C["workload"], variant, fb)
     line = {
-        "metric": C["metric"], "value": world * args.steps / el, "unit": "solves/s", "n_gpus": world,
+        "metric": C["metric"], "value": R.job_rate(args.steps, el, world), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if vb == 4 else "f64", "data": "synthetic",
@@ -426,7 +420,7 @@ def run_single(args, world, rank, dist, barrier):
         "setup_s": setup_s, "setup_phase_s": st["setup_phase_seconds"],
         **{k: v for k, v in km.items() if k != "roofline"},
         "roofline": km["roofline"],
-        "e2e": {"value": world * args.steps / e2e_el, "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * n,
+        "e2e": {"value": R.job_rate(args.steps, e2e_el, world), "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches_per_solve(iters, opts.get("krylov", "pcg")),
         "clocks": clk,
@@ -470,10 +464,7 @@ def run_batch(args, world, rank, dist, barrier):
     el, infos = timed_solves(h, [b], x, args.steps, args.warmup, stream, barrier,
                              solve=lambda bb, xx: h.solve_batch(bb, xx))
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = R.max_over_ranks(el, dist, "cuda")
     iters = [i.iters for i in infos[-1]]
     relres = max(i.true_relres for inf in infos for i in inf)
     # one problem at a time with its own handle (same options), on a sample
@@ -496,12 +487,13 @@ def run_batch(args, world, rank, dist, barrier):
     for _ in range(args.steps):
         xh.zero_()
         h.solve_host(bh, xh)
-    e2e_el = time.perf_counter() - te
+    e2e_el = R.max_over_ranks(time.perf_counter() - te, dist, "cuda")
     km = kernel_measurements(h, st, 4, stream, b, f"batch_{count}_diffusion7_edge16-64_sub8-16_k1e-2..1e2",
                              "fp32_levelsched")
     line = {
         "metric": "batched PCG problems solved/s to 1e-8 (256 diffusion problems per step)",
-        "value": world * count * args.steps / el, "unit": "problems/s", "n_gpus": world, "steps": args.steps,
+        "value": R.job_rate(count * args.steps, el, world), "unit": "problems/s", "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"batch_{count}_diffusion7_edge16-64_sub8-16_k1e-2..1e2", "n": n,
@@ -513,7 +505,7 @@ def run_batch(args, world, rank, dist, barrier):
         "one_at_a_time_problems_per_s": 1.0 / seq_per_problem,
         **{k: v for k, v in km.items() if k != "roofline"},
         "roofline": km["roofline"],
-        "e2e": {"value": world * count * args.steps / e2e_el, "unit": "problems/s",
+        "e2e": {"value": R.job_rate(count * args.steps, e2e_el, world), "unit": "problems/s",
                 "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": None,
         "clocks": clk,
