@@ -59,6 +59,10 @@ APPLY_CASES = [
     ("ragged13_ilu1", _ragged, dict(local="ilu0", fill_level=1)),
     ("diffusion10_ic2", _diffusion, dict(local="ic0", fill_level=2)),
     ("elast6_ilu1", lambda: P.elasticity_problem(6, 2), dict(local="ilu0", fill_level=1)),
+    ("overlap0_block_jacobi", lambda: P.poisson_problem(12, 4), dict(local="ic0", overlap=0)),
+    ("tiny_subdomains", lambda: P.poisson_problem(9, 3), dict(local="ilu0")),
+    ("elast_ragged7", lambda: P.elasticity_problem(7, 3), dict(local="ilu0")),
+    ("elast_ragged7_rgdsw_exact", lambda: P.elasticity_problem(7, 3), dict(local="exact", coarse="rgdsw")),
 ]
 
 
@@ -230,13 +234,14 @@ def test_host_made_faults():
 @pytest.mark.parametrize("make,opts", [
     (lambda: P.poisson_problem(12, 4), dict(local_solver="ic0")),
     (lambda: P.elasticity_problem(6, 2), dict(local_solver="ilu0", krylov="gmres", restart=30)),
-], ids=["poisson12_ic0", "elast6_ilu0_gmres"])
+    (lambda: P.poisson_problem(13, 4), dict(local_solver="ilu0", fill_level=1)),
+], ids=["poisson12_ic0", "elast6_ilu0_gmres", "ragged13_ilu1"])
 def test_fp16_factor_storage(make, opts):
     """Factors stored in FP16 and applied in FP32: the apply stays within FP16's
     rounding of the FP64 one and the FP64 Krylov solve still reaches 1e-8."""
     prob = make()
     local = opts["local_solver"]
-    M = oracle_for(prob, local=local)
+    M = oracle_for(prob, local=local, fill_level=opts.get("fill_level", 0))
     h16 = gpu_handle(prob, precision="fp16", **opts)
     h64 = gpu_handle(prob, **opts)
     r = np.random.default_rng(0).uniform(-1, 1, prob.A.n)
