@@ -45,6 +45,8 @@ VARIANTS = {
     "fp32_levelsched_rgdsw": dict(local_solver="ic0", trsv="levelsched", precision="fp32", coarse="rgdsw"),
     "fp32_levelsched_ic1": dict(local_solver="ic0", trsv="levelsched", precision="fp32", fill_level=1),
     "fp32_levelsched_ic2": dict(local_solver="ic0", trsv="levelsched", precision="fp32", fill_level=2),
+    "fp32_exact": dict(local_solver="exact", precision="fp32"),
+    "fp64_exact": dict(local_solver="exact", precision="fp64"),
 }
 DEFAULT_VARIANT = "fp32_levelsched"
 METRIC = "PCG solves/s to 1e-8 relative residual (time-to-residual = 1/value)"
@@ -96,7 +98,8 @@ def apply_bytes(st: dict, vbytes: int, fbytes: int = None) -> dict:
         off = nnz - sum_m
         tri += off * (fbytes + 2) + sum_m * (fbytes + 2) + lev * 16
     if st["dense_local"]:
-        tri = st["dense_local"] * vbytes
+        # dense inverses are read once; multifrontal panels once per sweep
+        tri = st["dense_local"] * vbytes * (2 if st.get("mf_supernodes") else 1)
     local = sum_m * (8 + 4) + tri + sum_m * vbytes + st["n_sub"] * 8
     phit = st["nnz_phi"] * vbytes + n * (8 + 4) + (nblk + 1) * 12 if n0 else 0
     coarse = st.get("a0_entries", n0 * n0) * 8 + n0 * 8 * 3 if n0 else 0

@@ -146,7 +146,8 @@ typedef struct {
   int64_t nnz_phi;        /* stored entries of Phi (interior blocks + Gamma) */
   int64_t n_levels_L, n_levels_U; /* summed over subdomains                 */
   int64_t max_levels;     /* per subdomain                                  */
-  int64_t dense_local;    /* entries of the exact solver's dense inverses   */
+  int64_t dense_local;    /* entries of the exact solver's factors: the dense
+                             inverses, or the multifrontal panels           */
   int64_t n_blocks;       /* Phi blocks: interiors + interface components   */
   int64_t device_bytes;   /* device memory held by the handle               */
   int64_t n_problems;     /* independent problems (gdsw_setup_batch)        */
@@ -154,6 +155,11 @@ typedef struct {
   int64_t local_stages;   /* ring depth of the pipelined local solve chosen at
                              setup (0: the unpipelined level/Jacobi kernel)   */
   int64_t local_threads;  /* its consumer threads (or threads per CTA)      */
+  int64_t mf_supernodes;  /* supernodes of the multifrontal exact solver,
+                             summed over subdomains (0: dense inverses or an
+                             incomplete factor)                             */
+  int64_t mf_levels;      /* tree levels of the multifrontal solve, summed
+                             over subdomains                                */
   double setup_seconds;
   double setup_phase_seconds[8]; /* [0] symbolic [1] local factors [2] Phi_Gamma
                                     [3] Phi_I [4] A0 [5] A0^-1 [6] exact local

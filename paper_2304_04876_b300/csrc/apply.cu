@@ -725,6 +725,7 @@ EllDev<T> ell(const Ctx* c, bool lower) {
 template <class T>
 gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
   T* zl = static_cast<T*>(c->zloc);
+  if (c->mf) return mf_launch_local(c, r, s, ks);
   if (c->opt.local_solver == GDSW_LOCAL_EXACT) {
     const size_t shm = size_t(c->max_m) * sizeof(T);
     dim3 grid((c->max_m + 31) / 32, c->nsub);

@@ -64,6 +64,16 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
     }
     int64_t nrec = 0;
     R += arr(record_stream_bytes(P, vrec, &nrec), 1) + arr(nsub + 1, 4) + 2 * arr(nrec, 4);
+  } else if (P.max_m > exact_dense_max() || [&] {
+               int64_t d = 0;
+               for (int q = 0; q < P.nsub; ++q) d += int64_t(P.om_ptr[q + 1] - P.om_ptr[q]) * (P.om_ptr[q + 1] - P.om_ptr[q]);
+               return d > (int64_t(1) << 31);
+             }()) {
+    // multifrontal exact solver: panels, solve lists, arena; factor work areas
+    MfPlan M;
+    GDSW_TRY(build_mf_plan(P, mf_leaf_size(), kMfBufBytes / int(v), &M));
+    R += mf_resident_bytes(M, P.nsub, sum_m, v);
+    S += mf_scratch_bytes(M, P.nsub);
   } else {
     int64_t dense = 0, band = 0;
     for (int q = 0; q < P.nsub; ++q) {

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -151,6 +152,81 @@ inline int record_piece_rows(int nr, int K, int g, size_t vb) {
   return rows >= size_t(nr) ? nr : static_cast<int>(rows);
 }
 
+// Multifrontal exact local solver (nested dissection, supernodal fronts, the
+// partitioned inverse of each diagonal block).  Positions are ND positions
+// inside a subdomain; supernode ids are global (subdomain q owns ids
+// sub_sn[q] .. sub_sn[q+1]) and local ones (in rows / task words) are
+// relative to sub_sn[q].
+struct MfSn {
+  int64_t panel;      // first element of [Linv_SS; L_BS], column-major trapezoid:
+                      // entry (i, j), i >= j, at panel + j*(ns+nb) - j*(j-1)/2 + (i-j)
+  int pos0, ns, nb;   // first ND position, |S|, |B(S)|
+  int uoff;           // update vector u_S in the subdomain's arena
+  int brow;           // first B row (indexes bidx, pullB_ptr, relF)
+  int stage;          // first row of S among the rows of its level
+  int nchild;
+};
+struct MfLevel {
+  int rows;           // first entry of the level in rows (ND positions of its unknowns)
+  int st, xt, ut;     // first task of the level in stasks / xtasks / utasks
+  int br;             // first entry in brows (unknowns of its large supernodes)
+  int flags;          // bit 0: some supernode of the level has children;
+                      // bit 1: the level has a large supernode
+};
+// A supernode is small (one warp solves it from a staged copy of its panel)
+// when it has at most kMfSmall unknowns, at most kMfSmallNb B rows and its
+// panel fits the warp's kMfBufBytes buffer.
+constexpr int kMfSmall = 32;
+constexpr int kMfSmallNb = 128;
+constexpr int kMfBufBytes = 3584;
+constexpr int kMfTaskWords = 5;
+struct MfPlan {
+  int leaf = 0;
+  std::vector<MfSn> sn;
+  std::vector<int64_t> sub_panel;         // nsub: first panel element of each subdomain
+  std::vector<int> sub_brow;              // nsub: first B row of each subdomain
+  std::vector<int> sub_sn, sub_lv;        // nsub+1
+  std::vector<MfLevel> lv;                // levels of every subdomain, leaves first, plus an end marker
+  std::vector<uint16_t> rows;             // per level: ND positions of its unknowns
+  std::vector<uint16_t> brows;            // per level: those of its large supernodes, stage order
+  // per level, kMfTaskWords per task (see build_mf_plan): small supernodes,
+  // 32-row pieces of S and of B(S) of the large ones
+  std::vector<uint32_t> stasks, xtasks, utasks;
+  std::vector<int> nd_dof;                // sum_m: global unknown of each ND position
+  std::vector<uint16_t> nd_loc;           // sum_m: local unknown of each ND position
+  std::vector<int> pullS_ptr;             // sum_m+1, into pullS_ent
+  std::vector<int> pullB_ptr;             // B rows + 1, into pullB_ent
+  std::vector<uint16_t> pullS_ent, pullB_ent;   // arena entries of the children's update vectors
+  std::vector<uint16_t> bidx;             // ND position of every B row
+  std::vector<uint16_t> relF;             // row of every B row in the parent's front
+  std::vector<int> ch_ptr, ch_list;       // children of each supernode (global ids)
+  std::vector<int> asm_ptr, asm_ent;      // entries of A_s assembled into each front
+  std::vector<uint32_t> asm_rc;           // front row | front column << 16
+  std::vector<int64_t> stack_off;         // update matrix of each supernode in its subdomain's stack
+  std::vector<int64_t> sub_stack;         // stack doubles of each subdomain
+  int64_t panel_total = 0;
+  int arena_max = 0, stage_max = 0, max_front = 0, max_ns = 0, max_nb = 0, max_levels = 0;
+};
+// small_cap: panel entries a warp's staging buffer holds.
+gdsw_status build_mf_plan(const Plan& P, int leaf, int small_cap, MfPlan* M);
+// Device memory for the fronts, inverse blocks and update stacks of the
+// subdomains factored at once.
+constexpr int64_t kMfWorkBudgetBytes = int64_t(3) << 30;
+// Work doubles of subdomain q's factorisation: front, inverse block, update stack.
+int64_t mf_work_need(const MfPlan& M, int q);
+// Consecutive subdomain batches whose work fits the budget; returns the
+// doubles of the largest batch.
+int64_t mf_batches(const MfPlan& M, int nsub, std::vector<std::pair<int, int>>* batches);
+// Device bytes the solve keeps (vb bytes per factor value) and the setup's scratch.
+int64_t mf_resident_bytes(const MfPlan& M, int nsub, int64_t sum_m, int64_t vb);
+int64_t mf_scratch_bytes(const MfPlan& M, int nsub);
+// Nested-dissection leaf size (unknowns); GDSW_MF_LEAF overrides it.
+inline int mf_leaf_size() {
+  const char* e = getenv("GDSW_MF_LEAF");
+  const int v = e ? atoi(e) : 16;
+  return v < 1 ? 1 : v;
+}
+
 // Device bytes of a handle built from this plan and of the setup's scratch
 // (upper bounds; host work only).
 gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
@@ -257,6 +333,20 @@ struct Ctx {
   int* derr = nullptr;               // device error flags (bounded waits that ran out)
   long long wait_cycles = 0;         // bound on each device-side wait, SM clock cycles
   int stall_test = 0;                // failure test: one record copy withheld
+  // exact local solver, multifrontal (see MfPlan)
+  bool mf = false;
+  MfSn* mf_sn = nullptr;
+  int* mf_sub_sn = nullptr; int* mf_sub_lv = nullptr;
+  MfLevel* mf_lv = nullptr;
+  uint16_t* mf_rows = nullptr; uint32_t* mf_xt = nullptr; uint32_t* mf_ut = nullptr;
+  int* mf_nd_dof = nullptr; uint16_t* mf_nd_loc = nullptr;
+  int* mf_pullS_ptr = nullptr; int* mf_pullB_ptr = nullptr;
+  uint16_t* mf_pullS = nullptr; uint16_t* mf_pullB = nullptr; uint16_t* mf_bidx = nullptr;
+  void* mf_panel = nullptr;
+  void* mf_arena_buf = nullptr;      // update vectors, mf_arena entries per subdomain
+  int64_t* mf_sub_panel = nullptr; int* mf_sub_brow = nullptr;
+  uint32_t* mf_st = nullptr; uint16_t* mf_brows = nullptr;
+  int mf_arena = 0, mf_stage = 0, mf_threads = 256;
   // exact local solver: dense inverses
   void* ainv = nullptr;
   int64_t* ainv_off = nullptr;
@@ -360,6 +450,16 @@ gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bo
 gdsw_status apply_enqueue_gated(Ctx* c, const double* r, double* z, cudaStream_t s);
 gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms);
 gdsw_status check_device_errors(Ctx* c, cudaStream_t s);
+// multifrontal.cu: the exact local solver for subdomains too large for dense inverses
+gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaStream_t s);
+gdsw_status mf_launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks);
+gdsw_status mf_configure(Ctx* c);
+// Largest subdomain (unknowns) whose exact solve uses a dense inverse; larger
+// ones use the multifrontal factor.  GDSW_EXACT_DENSE_MAX overrides it.
+inline int exact_dense_max() {
+  const char* e = getenv("GDSW_EXACT_DENSE_MAX");
+  return e ? atoi(e) : 1536;
+}
 // krylov.cu
 gdsw_status krylov_init(Ctx* c, cudaStream_t s);
 gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s);

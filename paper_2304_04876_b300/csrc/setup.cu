@@ -1220,7 +1220,9 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     c->stats.setup_phase_seconds[5] = now_s() - t0;
   }
 
-  // ---- exact local solver: dense inverse of each A_s ----
+  // ---- exact local solver: dense inverse of each A_s, or the multifrontal
+  // factor when a subdomain is larger than exact_dense_max() or the inverses
+  // would hold more than 2^31 entries ----
   t0 = now_s();
   if (exact) {
     GDSW_TRY(read_err(d_err, s, "local matrix"));
@@ -1231,10 +1233,10 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
       xoff[q + 1] = xoff[q] + int64_t(mn[q]) * mn[q];
     }
     const int64_t total = xoff[nsub];
-    if (total > (int64_t(1) << 31)) {
-      set_error("exact local solver needs %lld dense entries; use IC0/ILU0 for subdomains this large",
-                (long long)total);
-      return GDSW_ERR_UNSUPPORTED;
+    if (P.max_m > exact_dense_max() || total > (int64_t(1) << 31)) {
+      GDSW_TRY(mf_numeric_setup(c, P, d_araw, s));
+      c->stats.setup_phase_seconds[6] = now_s() - t0;
+      return GDSW_OK;
     }
     double* X;
     GDSW_TRY(sc.get(&X, total));

@@ -52,7 +52,7 @@ class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in (
         "n", "nnz", "n_sub", "n0", "n_comp", "sum_omega", "max_omega", "nnz_L", "nnz_U", "ell_L",
         "ell_U", "nnz_phi", "n_levels_L", "n_levels_U", "max_levels", "dense_local", "n_blocks",
-        "device_bytes", "n_problems", "a0_entries", "local_stages", "local_threads")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8)]
+        "device_bytes", "n_problems", "a0_entries", "local_stages", "local_threads", "mf_supernodes", "mf_levels")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "setup_phase_seconds"}

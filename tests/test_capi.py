@@ -97,7 +97,7 @@ def test_structs_match_header(lib):
     fields = re.findall(r"(?:int32_t|int64_t|double)\s+(\w+);", body)
     assert fields == [f for f, _ in G.Options._fields_]
     assert C.sizeof(G.Options) == 14 * 4 + 8 + 8
-    assert C.sizeof(G.Stats) == 22 * 8 + 9 * 8
+    assert C.sizeof(G.Stats) == 24 * 8 + 9 * 8
 
 
 def test_batch_rejects_bad_members_on_host(lib):
