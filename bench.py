@@ -46,6 +46,7 @@ VARIANTS = {
     "fp32_levelsched_ic1": dict(local_solver="ic0", trsv="levelsched", precision="fp32", fill_level=1),
     "fp32_levelsched_ic2": dict(local_solver="ic0", trsv="levelsched", precision="fp32", fill_level=2),
     "fp32_exact": dict(local_solver="exact", precision="fp32"),
+    "fp16_exact": dict(local_solver="exact", precision="fp16"),
     "fp64_exact": dict(local_solver="exact", precision="fp64"),
 }
 DEFAULT_VARIANT = "fp32_levelsched"
@@ -72,7 +73,8 @@ CONFIGS = {
                       "fp32_levelsched_rgdsw": dict(local_solver="ilu0", krylov="gmres", restart=30,
                                                     precision="fp32", coarse="rgdsw"),
                       "fp32_levelsched_ilu1": dict(local_solver="ilu0", krylov="gmres", restart=30,
-                                                   precision="fp32", fill_level=1)},
+                                                   precision="fp32", fill_level=1),
+                      "fp32_exact": dict(local_solver="exact", krylov="gmres", restart=30, precision="fp32")},
             default="fp32_levelsched", Z=True),
 }
 
@@ -99,7 +101,7 @@ def apply_bytes(st: dict, vbytes: int, fbytes: int = None) -> dict:
         tri += off * (fbytes + 2) + sum_m * (fbytes + 2) + lev * 16
     if st["dense_local"]:
         # dense inverses are read once; multifrontal panels once per sweep
-        tri = st["dense_local"] * vbytes * (2 if st.get("mf_supernodes") else 1)
+        tri = (st["dense_local"] * fbytes * 2 if st.get("mf_supernodes") else st["dense_local"] * vbytes)
     local = sum_m * (8 + 4) + tri + sum_m * vbytes + st["n_sub"] * 8
     phit = st["nnz_phi"] * vbytes + n * (8 + 4) + (nblk + 1) * 12 if n0 else 0
     coarse = st.get("a0_entries", n0 * n0) * 8 + n0 * 8 * 3 if n0 else 0

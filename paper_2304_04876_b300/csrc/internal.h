@@ -217,8 +217,9 @@ int64_t mf_work_need(const MfPlan& M, int q);
 // Consecutive subdomain batches whose work fits the budget; returns the
 // doubles of the largest batch.
 int64_t mf_batches(const MfPlan& M, int nsub, std::vector<std::pair<int, int>>* batches);
-// Device bytes the solve keeps (vb bytes per factor value) and the setup's scratch.
-int64_t mf_resident_bytes(const MfPlan& M, int nsub, int64_t sum_m, int64_t vb);
+// Device bytes the solve keeps (pb bytes per panel value, vb per vector
+// value) and the setup's scratch.
+int64_t mf_resident_bytes(const MfPlan& M, int nsub, int64_t sum_m, int64_t pb, int64_t vb);
 int64_t mf_scratch_bytes(const MfPlan& M, int nsub);
 // Nested-dissection leaf size (unknowns); GDSW_MF_LEAF overrides it.
 inline int mf_leaf_size() {

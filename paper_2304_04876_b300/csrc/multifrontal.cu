@@ -21,6 +21,8 @@
 #include <cstdlib>
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -29,6 +31,17 @@ namespace gdsw {
 namespace {
 
 enum { MF_ERR_BREAKDOWN = 1 };
+
+template <class T>
+__device__ __forceinline__ T to_storage(double x) { return T(x); }
+template <>
+__device__ __forceinline__ __half to_storage<__half>(double x) { return __double2half(x); }
+
+template <class T>
+__device__ __forceinline__ float ld_f(const T* p) { return float(*p); }
+__device__ __forceinline__ double ld_f(const double* p) { return *p; }
+template <>
+__device__ __forceinline__ float ld_f<__half>(const __half* p) { return __half2float(*p); }
 
 __device__ __forceinline__ int64_t mf_col(int nf, int j) {
   return int64_t(j) * nf - int64_t(j) * (j - 1) / 2;
@@ -135,8 +148,8 @@ __global__ void __launch_bounds__(512) k_mf_factor(MfFactorArgs a, T* __restrict
     T* Pn = panel + d.panel;
     for (int j = wid; j < ns; j += nw) {
       T* col = Pn + mf_col(nf, j) - j;
-      for (int i = j + lane; i < ns; i += 32) col[i] = T(X[int64_t(j) * ns + i]);
-      for (int r = lane; r < nb; r += 32) col[ns + r] = T(F[int64_t(j) * nf + ns + r]);
+      for (int i = j + lane; i < ns; i += 32) col[i] = to_storage<T>(X[int64_t(j) * ns + i]);
+      for (int r = lane; r < nb; r += 32) col[ns + r] = to_storage<T>(F[int64_t(j) * nf + ns + r]);
     }
     __syncthreads();
   }
@@ -175,12 +188,23 @@ struct MfTask {
   int pos0, ns, nb, stage, uoff, c0;
 };
 
-__device__ __forceinline__ MfTask mf_task(const uint32_t* T5, int t) {
+struct MfWords {
+  uint32_t w[kMfTaskWords];
+};
+
+__device__ __forceinline__ MfWords mf_words(const uint32_t* T5, int t) {
+  MfWords x;
   const uint32_t* w = T5 + size_t(t) * kMfTaskWords;
+#pragma unroll
+  for (int k = 0; k < kMfTaskWords; ++k) x.w[k] = __ldg(w + k);
+  return x;
+}
+
+__device__ __forceinline__ MfTask mf_decode(const MfWords& x) {
   MfTask d;
-  d.panel = __ldg(w);
-  d.brow = __ldg(w + 1);
-  const uint32_t w2 = __ldg(w + 2), w3 = __ldg(w + 3), w4 = __ldg(w + 4);
+  d.panel = x.w[0];
+  d.brow = x.w[1];
+  const uint32_t w2 = x.w[2], w3 = x.w[3], w4 = x.w[4];
   d.pos0 = int(w2 & 0xffffu);
   d.ns = int(w2 >> 16);
   d.nb = int(w3 & 0xffffu);
@@ -189,6 +213,8 @@ __device__ __forceinline__ MfTask mf_task(const uint32_t* T5, int t) {
   d.c0 = int(w4 >> 16);
   return d;
 }
+
+__device__ __forceinline__ MfTask mf_task(const uint32_t* T5, int t) { return mf_decode(mf_words(T5, t)); }
 
 // Offset of entry (i, j) of a trapezoid panel with nf rows, less i:
 // column j starts at j*nf - j(j-1)/2 and holds rows j .. nf-1.
@@ -201,7 +227,7 @@ constexpr int kMfK = kMfSmallNb / 32;   // B rows per lane of a small supernode
 template <class T>
 __device__ __forceinline__ void mf_fetch(const T* src, int entries, T* buf, uint64_t* bar) {
   if ((threadIdx.x & 31) == 0) {
-    const unsigned bytes = unsigned((entries + 3) & ~3) * sizeof(T);
+    const unsigned bytes = unsigned((entries + 7) & ~7) * sizeof(T);
     fence_proxy_async_smem();
     mbar_expect_tx(bar, bytes);
     bulk_g2s(buf, src, bytes, bar);
@@ -218,26 +244,28 @@ __device__ __forceinline__ void mf_wait(uint64_t* bar, unsigned& phase, const Mf
   phase ^= 1u;
 }
 
-template <class T>
+template <class T, class TS>
 __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ r, MfSolveArgs a,
-                                                  const T* __restrict__ panel_all, T* __restrict__ arena_all,
-                                                  T* __restrict__ zloc, const KrylovScalars* __restrict__ ks) {
+                                                     const TS* __restrict__ panel_all, T* __restrict__ arena_all,
+                                                     T* __restrict__ zloc, const KrylovScalars* __restrict__ ks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ks != nullptr && ks->done) return;
-  constexpr int kBuf = kMfBufBytes / int(sizeof(T));
+  constexpr int kBufT = kMfBufBytes / int(sizeof(T));    // x_B gathers
+
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   T* v = reinterpret_cast<T*>(smem_raw + 64 * sizeof(uint64_t));
   T* stage = v + a.vlen;
-  T* buf = stage + a.stage + wid * kBuf;          // this warp's panel buffer
+  TS* buf = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(stage + a.stage) + wid * kMfBufBytes);
+  T* bufT = reinterpret_cast<T*>(buf);             // the same buffer for x_B gathers
   uint64_t* bar = bars + wid;
   if (lane == 0) mbar_init(bar, 1);
   fence_mbar_init();
   unsigned phase = 0;
   const int q = blockIdx.x;
   const int base = a.om_ptr[q], m = a.om_ptr[q + 1] - base;
-  const T* panel = panel_all + a.sub_panel[q];
+  const TS* panel = panel_all + a.sub_panel[q];
   const uint16_t* bidx = a.bidx + a.sub_brow[q];
   const int* pullB_ptr = a.pullB_ptr + a.sub_brow[q];
   T* arena = arena_all + int64_t(q) * a.arena;
@@ -258,10 +286,13 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
       __syncthreads();
     }
     // small supernodes, one warp each: y_S = Linv_SS f_S, u_S = pulls - L_BS y_S
+    MfWords nx;
+    if (L.st + wid < E.st) nx = mf_words(a.st, L.st + wid);
     for (int t = L.st + wid; t < E.st; t += nw) {
-      const MfTask d = mf_task(a.st, t);
+      const MfTask d = mf_decode(nx);
       const int nf = d.ns + d.nb;
       mf_fetch(panel + d.panel, d.ns * nf - d.ns * (d.ns - 1) / 2, buf, bar);
+      if (t + nw < E.st) nx = mf_words(a.st, t + nw);     // the next task's layout, early
       const T f = lane < d.ns ? v[d.pos0 + lane] : T(0);
       T u[kMfK];
 #pragma unroll
@@ -276,11 +307,11 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
       int c = 0;                                   // column j starts at buf + c + j
       for (int j = 0; j < d.ns; ++j) {
         const T fj = __shfl_sync(0xffffffffu, f, j);
-        if (lane >= j && lane < d.ns) y += buf[c + lane] * fj;
+        if (lane >= j && lane < d.ns) y += T(ld_f(buf + c + lane)) * fj;
         const T yj = __shfl_sync(0xffffffffu, y, j);   // row j is complete after column j
 #pragma unroll
         for (int k = 0; k < kMfK; ++k)
-          if (lane + 32 * k < d.nb) u[k] -= buf[c + d.ns + lane + 32 * k] * yj;
+          if (lane + 32 * k < d.nb) u[k] -= T(ld_f(buf + c + d.ns + lane + 32 * k)) * yj;
         c += nf - 1 - j;
       }
       if (lane < d.ns) v[d.pos0 + lane] = y;
@@ -295,19 +326,19 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
       const int i0 = d.c0, i = i0 + lane;
       const int nf = d.ns + d.nb, jend = min(i0 + 32, d.ns);
       const bool row = i < d.ns;
-      const T* p = panel + d.panel + i;
+      const TS* p = panel + d.panel + i;
       const T* f = v + d.pos0;
       T acc = T(0);
       int j = 0;
       for (; j + kMfUnroll <= jend; j += kMfUnroll) {
         T x[kMfUnroll];
 #pragma unroll
-        for (int k = 0; k < kMfUnroll; ++k) x[k] = (row && j + k <= i) ? p[mf_cofs(nf, j + k)] : T(0);
+        for (int k = 0; k < kMfUnroll; ++k) x[k] = (row && j + k <= i) ? T(ld_f(p + mf_cofs(nf, j + k))) : T(0);
 #pragma unroll
         for (int k = 0; k < kMfUnroll; ++k) acc += x[k] * f[j + k];
       }
       for (; j < jend; ++j)
-        if (row && j <= i) acc += p[mf_cofs(nf, j)] * f[j];
+        if (row && j <= i) acc += T(ld_f(p + mf_cofs(nf, j))) * f[j];
       if (row) stage[d.stage + i] = acc;
     }
     if (L.flags & 2) {
@@ -319,19 +350,19 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
         const bool row = rr < d.nb;
         const int nf = d.ns + d.nb;
         const int k0 = row ? pullB_ptr[d.brow + rr] : 0, k1 = row ? pullB_ptr[d.brow + rr + 1] : 0;
-        const T* p = panel + d.panel + d.ns + rr;
+        const TS* p = panel + d.panel + d.ns + rr;
         const T* y = stage + d.stage;
         T acc = T(0);
         int j = 0;
         for (; j + 2 * kMfUnroll <= d.ns; j += 2 * kMfUnroll) {   // sixteen loads in flight
           T x[2 * kMfUnroll];
 #pragma unroll
-          for (int k = 0; k < 2 * kMfUnroll; ++k) x[k] = row ? p[mf_cofs(nf, j + k)] : T(0);
+          for (int k = 0; k < 2 * kMfUnroll; ++k) x[k] = row ? T(ld_f(p + mf_cofs(nf, j + k))) : T(0);
 #pragma unroll
           for (int k = 0; k < 2 * kMfUnroll; ++k) acc -= x[k] * y[j + k];
         }
         for (; j < d.ns; ++j)
-          if (row) acc -= p[mf_cofs(nf, j)] * y[j];
+          if (row) acc -= T(ld_f(p + mf_cofs(nf, j))) * y[j];
         T pulled = T(0);
         for (int k = k0; k < k1; ++k) pulled += arena[a.pullB[k]];
         if (row) arena[d.uoff + rr] = pulled + acc;
@@ -344,10 +375,13 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
   for (int l = l1 - 1; l >= l0; --l) {
     const MfLevel L = a.lv[l], E = a.lv[l + 1];
     // small supernodes: g_S = y_S - L_BS^T x_B, x_S = Linv_SS^T g_S, one column per lane
+    MfWords nx;
+    if (L.st + wid < E.st) nx = mf_words(a.st, L.st + wid);
     for (int t = L.st + wid; t < E.st; t += nw) {
-      const MfTask d = mf_task(a.st, t);
+      const MfTask d = mf_decode(nx);
       const int nf = d.ns + d.nb;
       mf_fetch(panel + d.panel, d.ns * nf - d.ns * (d.ns - 1) / 2, buf, bar);
+      if (t + nw < E.st) nx = mf_words(a.st, t + nw);
       T xv[kMfK];
 #pragma unroll
       for (int k = 0; k < kMfK; ++k) {
@@ -362,16 +396,16 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
       for (int k = 0; k < kMfK; ++k) {
         if (32 * k >= d.nb) break;
         const int rend = min(32, d.nb - 32 * k);
-        const T* pc = buf + cl + d.ns + 32 * k;
+        const TS* pc = buf + cl + d.ns + 32 * k;
         for (int r2 = 0; r2 < rend; ++r2) {
           const T xr = __shfl_sync(0xffffffffu, xv[k], r2);
-          if (col) g -= pc[r2] * xr;
+          if (col) g -= T(ld_f(pc + r2)) * xr;
         }
       }
       T x = T(0);
       for (int i = 0; i < d.ns; ++i) {
         const T gi = __shfl_sync(0xffffffffu, g, i);
-        if (col && lane <= i) x += buf[cl + i] * gi;
+        if (col && lane <= i) x += T(ld_f(buf + cl + i)) * gi;
       }
       if (col) v[d.pos0 + lane] = x;
       __syncwarp();
@@ -382,34 +416,34 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
       const MfTask d = mf_task(a.xt, t);
       if (d.nb == 0) continue;
       const int i0 = d.c0, iend = min(i0 + 32, d.ns), nf = d.ns + d.nb;
-      const bool staged = d.nb <= kBuf;
+      const bool staged = d.nb <= kBufT;
       if (staged)
-        for (int rr = lane; rr < d.nb; rr += 32) buf[rr] = v[bidx[d.brow + rr]];
+        for (int rr = lane; rr < d.nb; rr += 32) bufT[rr] = v[bidx[d.brow + rr]];
       __syncwarp();
       for (int i = i0; i < iend; i += kMfUnroll) {
         T acc[kMfUnroll];
 #pragma unroll
         for (int k = 0; k < kMfUnroll; ++k) acc[k] = T(0);
-        const T* p = panel + d.panel + d.ns;
+        const TS* p = panel + d.panel + d.ns;
         int rr = lane;
         for (; rr + 32 < d.nb; rr += 64) {    // two rows per lane in flight
           T x[kMfUnroll], x2[kMfUnroll];
 #pragma unroll
           for (int k = 0; k < kMfUnroll; ++k) {
             const bool c = i + k < iend;
-            x[k] = c ? p[mf_cofs(nf, i + k) + rr] : T(0);
-            x2[k] = c ? p[mf_cofs(nf, i + k) + rr + 32] : T(0);
+            x[k] = c ? T(ld_f(p + mf_cofs(nf, i + k) + rr)) : T(0);
+            x2[k] = c ? T(ld_f(p + mf_cofs(nf, i + k) + rr + 32)) : T(0);
           }
-          const T xv = staged ? buf[rr] : v[bidx[d.brow + rr]];
-          const T xv2 = staged ? buf[rr + 32] : v[bidx[d.brow + rr + 32]];
+          const T xv = staged ? bufT[rr] : v[bidx[d.brow + rr]];
+          const T xv2 = staged ? bufT[rr + 32] : v[bidx[d.brow + rr + 32]];
 #pragma unroll
           for (int k = 0; k < kMfUnroll; ++k) acc[k] += x[k] * xv + x2[k] * xv2;
         }
         if (rr < d.nb) {
           T x[kMfUnroll];
 #pragma unroll
-          for (int k = 0; k < kMfUnroll; ++k) x[k] = (i + k < iend) ? p[mf_cofs(nf, i + k) + rr] : T(0);
-          const T xv = staged ? buf[rr] : v[bidx[d.brow + rr]];
+          for (int k = 0; k < kMfUnroll; ++k) x[k] = (i + k < iend) ? T(ld_f(p + mf_cofs(nf, i + k) + rr)) : T(0);
+          const T xv = staged ? bufT[rr] : v[bidx[d.brow + rr]];
 #pragma unroll
           for (int k = 0; k < kMfUnroll; ++k) acc[k] += x[k] * xv;
         }
@@ -432,15 +466,15 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
           T acc[kMfUnroll];
 #pragma unroll
           for (int k = 0; k < kMfUnroll; ++k) acc[k] = T(0);
-          const T* p = panel + d.panel;
+          const TS* p = panel + d.panel;
           int i = j + lane;
           for (; i + 32 < d.ns; i += 64) {      // two rows per lane in flight
             T x[kMfUnroll], x2[kMfUnroll];
 #pragma unroll
             for (int k = 0; k < kMfUnroll; ++k) {
               const bool c = j + k < jend;
-              x[k] = (c && i >= j + k) ? p[mf_cofs(nf, j + k) + i] : T(0);
-              x2[k] = c ? p[mf_cofs(nf, j + k) + i + 32] : T(0);
+              x[k] = (c && i >= j + k) ? T(ld_f(p + mf_cofs(nf, j + k) + i)) : T(0);
+              x2[k] = c ? T(ld_f(p + mf_cofs(nf, j + k) + i + 32)) : T(0);
             }
             const T gi = g[i], gi2 = g[i + 32];
 #pragma unroll
@@ -449,7 +483,7 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
           if (i < d.ns) {
             T x[kMfUnroll];
 #pragma unroll
-            for (int k = 0; k < kMfUnroll; ++k) x[k] = (j + k < jend && i >= j + k) ? p[mf_cofs(nf, j + k) + i] : T(0);
+            for (int k = 0; k < kMfUnroll; ++k) x[k] = (j + k < jend && i >= j + k) ? T(ld_f(p + mf_cofs(nf, j + k) + i)) : T(0);
             const T gi = g[i];
 #pragma unroll
             for (int k = 0; k < kMfUnroll; ++k) acc[k] += x[k] * gi;
@@ -511,19 +545,26 @@ gdsw_status mf_configure(Ctx* c) {
     set_error("subdomain of %d unknowns does not fit the multifrontal solve's shared memory", c->max_m);
     return GDSW_ERR_UNSUPPORTED;
   }
-  if (c->fp32) GDSW_CK(allow_max_dynamic_smem(k_local_mf<float>));
-  else GDSW_CK(allow_max_dynamic_smem(k_local_mf<double>));
+  if (c->fp16) GDSW_CK(allow_max_dynamic_smem(k_local_mf<float, __half>));
+  else if (c->fp32) GDSW_CK(allow_max_dynamic_smem(k_local_mf<float, float>));
+  else GDSW_CK(allow_max_dynamic_smem(k_local_mf<double, double>));
   return GDSW_OK;
 }
 
+// Panels are stored in FP16 (FP16 precision), FP32 or FP64; the solve
+// computes in FP32 or FP64.
 gdsw_status mf_launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
   const MfSolveArgs a = solve_args(c);
-  if (c->fp32) {
-    k_local_mf<float><<<c->nsub, c->mf_threads, solve_smem(c, sizeof(float)), s>>>(
+  if (c->fp16) {
+    k_local_mf<float, __half><<<c->nsub, c->mf_threads, solve_smem(c, sizeof(float)), s>>>(
+        r, a, static_cast<const __half*>(c->mf_panel), static_cast<float*>(c->mf_arena_buf),
+        static_cast<float*>(c->zloc), ks);
+  } else if (c->fp32) {
+    k_local_mf<float, float><<<c->nsub, c->mf_threads, solve_smem(c, sizeof(float)), s>>>(
         r, a, static_cast<const float*>(c->mf_panel), static_cast<float*>(c->mf_arena_buf),
         static_cast<float*>(c->zloc), ks);
   } else {
-    k_local_mf<double><<<c->nsub, c->mf_threads, solve_smem(c, sizeof(double)), s>>>(
+    k_local_mf<double, double><<<c->nsub, c->mf_threads, solve_smem(c, sizeof(double)), s>>>(
         r, a, static_cast<const double*>(c->mf_panel), static_cast<double*>(c->mf_arena_buf),
         static_cast<double*>(c->zloc), ks);
   }
@@ -533,9 +574,10 @@ gdsw_status mf_launch_local(Ctx* c, const double* r, cudaStream_t s, const Krylo
 
 gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaStream_t s) {
   MfPlan M;
-  GDSW_TRY(build_mf_plan(P, mf_leaf_size(), kMfBufBytes / int(c->fp32 ? sizeof(float) : sizeof(double)), &M));
-  const bool f32 = c->fp32;
-  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  const bool f32 = c->fp32, f16 = c->fp16;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);     // vectors
+  const size_t ps = f16 ? sizeof(__half) : es;                // panels
+  GDSW_TRY(build_mf_plan(P, mf_leaf_size(), kMfBufBytes / int(ps), &M));
   // resident solve data
   GDSW_TRY(upload(c, &c->mf_sn, M.sn, s));
   GDSW_TRY(upload(c, &c->mf_sub_panel, M.sub_panel, s));
@@ -557,22 +599,29 @@ gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaSt
   GDSW_TRY(upload(c, &c->mf_bidx, M.bidx, s));
   c->mf_arena = std::max(1, M.arena_max);
   c->mf_stage = (M.stage_max + 3) & ~3;
-  if (f32) {
+  if (f16) {
+    __half* p;
+    GDSW_TRY(dalloc(c, &p, size_t(M.panel_total)));
+    c->mf_panel = p;
+  } else if (f32) {
     float* p;
     GDSW_TRY(dalloc(c, &p, size_t(M.panel_total)));
     c->mf_panel = p;
-    float* ar;
-    GDSW_TRY(dalloc(c, &ar, size_t(c->nsub) * c->mf_arena));
-    c->mf_arena_buf = ar;
   } else {
     double* p;
     GDSW_TRY(dalloc(c, &p, size_t(M.panel_total)));
     c->mf_panel = p;
+  }
+  if (f32) {
+    float* ar;
+    GDSW_TRY(dalloc(c, &ar, size_t(c->nsub) * c->mf_arena));
+    c->mf_arena_buf = ar;
+  } else {
     double* ar;
     GDSW_TRY(dalloc(c, &ar, size_t(c->nsub) * c->mf_arena));
     c->mf_arena_buf = ar;
   }
-  GDSW_CK(cudaMemsetAsync(c->mf_panel, 0, size_t(M.panel_total) * es, s));
+  GDSW_CK(cudaMemsetAsync(c->mf_panel, 0, size_t(M.panel_total) * ps, s));
 
   // factorisation, in batches of subdomains whose work areas fit the budget
   struct Tmp {
@@ -626,7 +675,8 @@ gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaSt
   fa.work_off = d_off;
   const size_t shm = size_t(std::max(1, M.max_front)) * sizeof(double);
   if (shm > size_t(max_block_smem_optin())) { set_error("front of %d rows too large", M.max_front); return GDSW_ERR_UNSUPPORTED; }
-  if (f32) GDSW_CK(allow_max_dynamic_smem(k_mf_factor<float>));
+  if (f16) GDSW_CK(allow_max_dynamic_smem(k_mf_factor<__half>));
+  else if (f32) GDSW_CK(allow_max_dynamic_smem(k_mf_factor<float>));
   else GDSW_CK(allow_max_dynamic_smem(k_mf_factor<double>));
   std::vector<int64_t> off;
   for (const auto& b : batches) {
@@ -635,7 +685,8 @@ gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaSt
     for (int q = b.first; q < b.second; ++q) { off.push_back(tot); tot += mf_work_need(M, q); }
     GDSW_CK(cudaMemcpyAsync(d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
     fa.q0 = b.first;
-    if (f32) k_mf_factor<float><<<b.second - b.first, 512, shm, s>>>(fa, static_cast<float*>(c->mf_panel));
+    if (f16) k_mf_factor<__half><<<b.second - b.first, 512, shm, s>>>(fa, static_cast<__half*>(c->mf_panel));
+    else if (f32) k_mf_factor<float><<<b.second - b.first, 512, shm, s>>>(fa, static_cast<float*>(c->mf_panel));
     else k_mf_factor<double><<<b.second - b.first, 512, shm, s>>>(fa, static_cast<double*>(c->mf_panel));
     GDSW_CK(cudaGetLastError());
     GDSW_CK(cudaStreamSynchronize(s));   // the work areas and offsets are reused by the next batch

@@ -262,7 +262,7 @@ void build_sub(const Plan& P, int q, int leaf, int small_cap, SubMf* R) {
   R->small.assign(nsn, 0);
   for (int S = 0; S < nsn; ++S)
     R->small[S] = R->ns[S] <= kMfSmall && R->nb[S] <= kMfSmallNb &&
-                  (panel_entries(R->ns[S], R->nb[S]) + 3) / 4 * 4 <= small_cap;
+                  (panel_entries(R->ns[S], R->nb[S]) + 7) / 8 * 8 <= small_cap;
   // stage offsets (rows of the large supernodes of a level, in order) and the
   // arena: u_S lives from its own level to its parent's; first fit over
   // address-ordered free blocks
@@ -413,7 +413,7 @@ gdsw_status build_mf_plan(const Plan& P, int leaf, int small_cap, MfPlan* M) {
       }
       M->max_nb = std::max(M->max_nb, d.nb);
       M->stack_off.push_back(R.stack_off[S]);
-      panel += (panel_entries(R.ns[S], R.nb[S]) + 3) / 4 * 4;
+      panel += (panel_entries(R.ns[S], R.nb[S]) + 7) / 8 * 8;   // 16-byte starts for every storage type
       for (int t : R.bset[S]) M->bidx.push_back(static_cast<uint16_t>(t));
       brow += R.nb[S];
     }
@@ -530,9 +530,9 @@ int64_t mf_batches(const MfPlan& M, int nsub, std::vector<std::pair<int, int>>* 
   return cap;
 }
 
-int64_t mf_resident_bytes(const MfPlan& M, int nsub, int64_t sum_m, int64_t vb) {
+int64_t mf_resident_bytes(const MfPlan& M, int nsub, int64_t sum_m, int64_t pb, int64_t vb) {
   const int64_t brows = static_cast<int64_t>(M.bidx.size());
-  return M.panel_total * vb + int64_t(M.sn.size()) * int64_t(sizeof(MfSn)) + int64_t(M.lv.size()) * 16 +
+  return M.panel_total * pb + int64_t(M.sn.size()) * int64_t(sizeof(MfSn)) + int64_t(M.lv.size()) * 16 +
          int64_t(M.rows.size() + M.brows.size()) * 2 +
          int64_t(M.stasks.size() + M.xtasks.size() + M.utasks.size()) * 4 + sum_m * (4 + 2 + 4) + 4 +
          (brows + 1) * 4 + int64_t(M.pullS_ent.size() + M.pullB_ent.size()) * 2 + brows * 2 +

@@ -151,3 +151,20 @@ def test_bytes_required_bounds_the_handle(prec):
     h.close()
     assert held <= resident <= 1.15 * held + (1 << 20), (held, resident)
     assert scratch > 0
+
+
+def test_fp16_panels():
+    """FP16 precision stores the exact factor panels in half precision (computed in
+    FP32): the apply is the exact solve to about the panels' rounding, and PCG still
+    reaches the FP64 true residual within a few more iterations than the oracle's."""
+    from oracle import gdsw_oracle as O
+    prob = P.poisson_problem(12, 4)
+    M = oracle_for(prob, local="exact")
+    h = gpu_handle(prob, local_solver="exact", precision="fp16")
+    r = np.random.default_rng(0).uniform(-1, 1, prob.A.n)
+    assert relerr(gpu_apply(h, r), M.apply(r)) <= 1e-2
+    h32 = gpu_handle(prob, local_solver="exact", precision="fp32")
+    assert h.stats()["device_bytes"] < h32.stats()["device_bytes"]
+    _, io = O.pcg(M.spmv, M.apply, prob.b, tol=1e-8)
+    _, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8 and io.iters - 1 <= info.iters <= io.iters + 3
