@@ -8,6 +8,7 @@ HBM.  The per-iteration working set (~0.9 GB) is far larger than the 126 MB L2,
 so no explicit flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--variant NAME] [--impl reference]
+    python bench.py --profile {solve,apply} [--profile-count C]   (untimed, for ncu)
 
 One JSON line is printed by rank 0.  Under torchrun every rank solves its own
 replica (independent problems, no collective on the data path).
@@ -599,6 +600,32 @@ def run_serving(args, world, rank, dist, barrier):
     return line
 
 
+def run_profile(args):
+    """Untimed work for profiler captures (ncu): set up the config's variant, then run
+    `--profile-count` solves (`--profile solve`) or preconditioner applies
+    (`--profile apply`) on the first right-hand side, and print nothing but a summary.
+    No number from such a run is a bench value."""
+    import torch
+    from paper_2304_04876_b300 import gdsw
+    C = CONFIGS[args.config]
+    variant = args.variant or C["default"]
+    prob = C["make"]()
+    h = gdsw.Handle(prob.A, prob.part, prob.Z if C["Z"] else None, **C["variants"][variant])
+    b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    for _ in range(args.profile_count):
+        if args.profile == "solve":
+            x.zero_()
+            h.solve(b, x)
+        else:
+            h.apply(b, x)
+    torch.cuda.synchronize()
+    st = h.stats()
+    print(f"profile run: config {args.config} variant {variant}, {args.profile_count} {args.profile} calls, "
+          f"n {st['n']}, subdomains {st['n_sub']}", flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -615,6 +642,9 @@ def main():
     ap.add_argument("--serving-budget-gb", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["solve", "apply"],
+                    help="untimed solves or applies for profiler captures (configs 1-3)")
+    ap.add_argument("--profile-count", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -644,6 +674,11 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.profile is not None:
+        if args.config not in (1, 2, 3):
+            ap.error("--profile runs configs 1-3")
+        run_profile(args)
+        return
     if args.config == 4:
         line = run_batch(args, world, rank, dist, barrier)
     elif args.config == 5:

@@ -53,7 +53,13 @@ typedef enum {
 } gdsw_status;
 
 /* local solver A_s^-1 (Sec. V-B) */
-enum { GDSW_LOCAL_EXACT = 0, /* Cholesky of A_s, applied as its dense inverse   */
+enum { GDSW_LOCAL_EXACT = 0, /* exact Cholesky of A_s: applied as its dense
+                                inverse for subdomains of at most 1536 unknowns;
+                                larger ones are factored multifrontally in a
+                                nested-dissection order and applied through the
+                                inverted diagonal blocks of the supernodes (the
+                                partitioned inverse, Sec. V-B2); the panels are
+                                stored in FP16 / FP32 / FP64 by precision       */
        GDSW_LOCAL_IC0 = 1,   /* IC(k) by synchronous fixed-point sweeps (k =
                                 gdsw_options.fill_level, 0 by default)         */
        GDSW_LOCAL_ILU0 = 2   /* ILU(k) likewise                                 */ };
@@ -61,8 +67,9 @@ enum { GDSW_LOCAL_EXACT = 0, /* Cholesky of A_s, applied as its dense inverse   
 enum { GDSW_TRSV_LEVELSCHED = 0, GDSW_TRSV_JACOBI = 1 };
 /* storage/compute precision of the preconditioner (Sec. V-A2); the Krylov
  * vectors, dot products, residual and the coarse solve stay FP64.
- * FP16: level-scheduled IC(0)/ILU(0) factors stored in half precision and
- * applied in FP32 (everything else as FP32). */
+ * FP16: level-scheduled IC(k)/ILU(k) factors, or the exact solver's
+ * multifrontal panels, stored in half precision and applied in FP32
+ * (everything else as FP32). */
 enum { GDSW_PREC_FP64 = 0, GDSW_PREC_FP32 = 1, GDSW_PREC_FP16 = 2 };
 enum { GDSW_KRYLOV_PCG = 0, GDSW_KRYLOV_GMRES = 1 };
 /* coarse space: GDSW (Eq. 2, one function per interface component and null-space
