@@ -258,6 +258,23 @@ GDSW_API gdsw_status gdsw_bytes_required(const gdsw_csr* A, const gdsw_partition
                                          int32_t nn, const gdsw_options* opt, int64_t* resident,
                                          int64_t* setup_scratch);
 
+/* The nested-dissection plan of the exact solver's multifrontal path for one
+ * subdomain (the symbolic phase alone, host work, no device call), for
+ * inspection and tests.  Returns *m (unknowns of the subdomain), *nsn
+ * (supernodes, postorder) and *nb_total (sum of |B(S)|); each array argument
+ * may be NULL (query the sizes first), else it must hold: nd_dof[m] the global
+ * unknown at each nested-dissection position; sn_ptr[nsn+1] the positions of
+ * each supernode; parent[nsn] its parent supernode (-1 for a root);
+ * b_ptr[nsn+1] and b_pos[nb_total] the positions B(S) of the ancestor unknowns
+ * coupled to the subtree of S (ascending).  The factor of A_s in this order
+ * has its nonzeros of column j within S u B(S) for the supernode S holding j.
+ * Errors: INVALID_ARG (inputs, subdomain out of range), UNSUPPORTED. */
+GDSW_API gdsw_status gdsw_mf_plan_export(const gdsw_csr* A, const gdsw_partition* part,
+                                         const gdsw_options* opt, int32_t subdomain, int32_t* m,
+                                         int32_t* nsn, int64_t* nb_total, int32_t* nd_dof,
+                                         int32_t* sn_ptr, int32_t* parent, int64_t* b_ptr,
+                                         int32_t* b_pos);
+
 /* Frees every device allocation of the handle.  NULL is accepted. */
 GDSW_API gdsw_status gdsw_destroy(gdsw_handle h);
 

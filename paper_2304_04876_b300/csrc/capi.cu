@@ -252,6 +252,53 @@ gdsw_status gdsw_bytes_required(const gdsw_csr* A, const gdsw_partition* part, c
   return GDSW_OK;
 }
 
+gdsw_status gdsw_mf_plan_export(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
+                                int32_t subdomain, int32_t* m, int32_t* nsn, int64_t* nb_total,
+                                int32_t* nd_dof, int32_t* sn_ptr, int32_t* parent, int64_t* b_ptr,
+                                int32_t* b_pos) {
+  gdsw_options o;
+  if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
+  if (!m || !nsn || !nb_total) { set_error("null size output"); return GDSW_ERR_INVALID_ARG; }
+  Plan P;
+  gdsw_status st = build_plan(A, part, &o, false, &P);
+  if (st != GDSW_OK) return st;
+  if (subdomain < 0 || subdomain >= P.nsub) {
+    set_error("subdomain %d outside [0, %d)", subdomain, P.nsub);
+    return GDSW_ERR_INVALID_ARG;
+  }
+  MfPlan M;
+  st = build_mf_plan(P, mf_leaf_size(), kMfBufBytes / 4, &M);
+  if (st != GDSW_OK) return st;
+  const int q = subdomain, base = P.om_ptr[q];
+  const int s0 = M.sub_sn[q], s1 = M.sub_sn[q + 1];
+  *m = P.om_ptr[q + 1] - base;
+  *nsn = s1 - s0;
+  int64_t nb = 0;
+  for (int S = s0; S < s1; ++S) nb += M.sn[S].nb;
+  *nb_total = nb;
+  if (nd_dof)
+    for (int p = 0; p < *m; ++p) nd_dof[p] = M.nd_dof[base + p];
+  if (sn_ptr) {
+    for (int S = s0; S < s1; ++S) sn_ptr[S - s0] = M.sn[S].pos0;
+    sn_ptr[s1 - s0] = *m;
+  }
+  if (parent) {
+    for (int S = s0; S < s1; ++S) parent[S - s0] = -1;
+    for (int S = s0; S < s1; ++S)
+      for (int t = M.ch_ptr[S]; t < M.ch_ptr[S + 1]; ++t) parent[M.ch_list[t] - s0] = S - s0;
+  }
+  if (b_ptr || b_pos) {
+    int64_t k = 0;
+    for (int S = s0; S < s1; ++S) {
+      if (b_ptr) b_ptr[S - s0] = k;
+      for (int r = 0; r < M.sn[S].nb; ++r, ++k)
+        if (b_pos) b_pos[k] = M.bidx[M.sn[S].brow + r];
+    }
+    if (b_ptr) b_ptr[s1 - s0] = k;
+  }
+  return GDSW_OK;
+}
+
 gdsw_status gdsw_refactor(gdsw_handle h, const double* val, void* stream) {
   if (!h || !val) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
   const double t0 = now_s();

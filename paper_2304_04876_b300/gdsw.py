@@ -86,6 +86,10 @@ SIGNATURES = {
     "gdsw_refactor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_bytes_required": (C.c_int, [C.POINTER(CSRStruct), C.POINTER(PartitionStruct), C.c_void_p, C.c_int32,
                                       C.POINTER(Options), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "gdsw_mf_plan_export": (C.c_int, [C.POINTER(CSRStruct), C.POINTER(PartitionStruct), C.POINTER(Options),
+                                      C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "gdsw_spmv_dot_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_status_string": (C.c_char_p, [C.c_int]),
@@ -300,6 +304,25 @@ def bytes_required(A, part, Z: Optional[np.ndarray] = None, **options):
            "gdsw_bytes_required")
     del keep
     return int(res.value), int(scr.value)
+
+
+def mf_plan(A, part, subdomain: int, **options) -> dict:
+    """The nested-dissection plan of the multifrontal exact solver for one subdomain
+    (gdsw_mf_plan_export; host work only): nd_dof, sn_ptr, parent, b_ptr, b_pos."""
+    csr, ps, _, _, keep = _marshal(A, part, None)
+    o = make_options(**options)
+    m, nsn, nbt = C.c_int32(), C.c_int32(), C.c_int64()
+    lib = load()
+    args = (C.byref(csr), C.byref(ps), C.byref(o), int(subdomain), C.byref(m), C.byref(nsn), C.byref(nbt))
+    _check(lib.gdsw_mf_plan_export(*args, None, None, None, None, None), "gdsw_mf_plan_export")
+    out = dict(nd_dof=np.zeros(m.value, np.int32), sn_ptr=np.zeros(nsn.value + 1, np.int32),
+               parent=np.zeros(nsn.value, np.int32), b_ptr=np.zeros(nsn.value + 1, np.int64),
+               b_pos=np.zeros(max(nbt.value, 1), np.int32))
+    _check(lib.gdsw_mf_plan_export(*args, *(out[k].ctypes.data for k in ("nd_dof", "sn_ptr", "parent", "b_ptr",
+                                                                          "b_pos"))), "gdsw_mf_plan_export")
+    out["b_pos"] = out["b_pos"][:nbt.value]
+    del keep
+    return out
 
 
 def _host_ptr(a) -> int:
