@@ -234,14 +234,19 @@ __device__ __forceinline__ void mf_fetch(const T* src, int entries, T* buf, uint
   }
 }
 
-// Wait for the warp's staged panel; a wait that runs out is recorded and
-// followed by one more bounded wait so no copy is left in flight.
-__device__ __forceinline__ void mf_wait(uint64_t* bar, unsigned& phase, const MfSolveArgs& a) {
+// Wait for the warp's staged panel.  A wait that runs out is recorded (the
+// host reports GDSW_ERR_TIMEOUT), followed by one more bounded wait for the copy
+// to land, and returns false: the warp then issues no further copy, so none is
+// left in flight when the CTA ends.
+__device__ __forceinline__ bool mf_wait(uint64_t* bar, unsigned& phase, const MfSolveArgs& a) {
+  bool ok = true;
   if (!mbar_wait_bounded(bar, phase, a.wait_cycles)) {
     if ((threadIdx.x & 31) == 0) atomicOr(a.err, 1);
     mbar_wait_bounded(bar, phase, kDefaultWaitCycles);
+    ok = false;
   }
   phase ^= 1u;
+  return ok;
 }
 
 template <class T, class TS>
@@ -263,6 +268,7 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
   if (lane == 0) mbar_init(bar, 1);
   fence_mbar_init();
   unsigned phase = 0;
+  bool copies_ok = true;                           // false once a copy wait ran out
   const int q = blockIdx.x;
   const int base = a.om_ptr[q], m = a.om_ptr[q + 1] - base;
   const TS* panel = panel_all + a.sub_panel[q];
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
     // small supernodes, one warp each: y_S = Linv_SS f_S, u_S = pulls - L_BS y_S
     MfWords nx;
     if (L.st + wid < E.st) nx = mf_words(a.st, L.st + wid);
-    for (int t = L.st + wid; t < E.st; t += nw) {
+    for (int t = L.st + wid; t < E.st && copies_ok; t += nw) {
       const MfTask d = mf_decode(nx);
       const int nf = d.ns + d.nb;
       mf_fetch(panel + d.panel, d.ns * nf - d.ns * (d.ns - 1) / 2, buf, bar);
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
         if (rr < d.nb)
           for (int e = pullB_ptr[d.brow + rr]; e < pullB_ptr[d.brow + rr + 1]; ++e) u[k] += arena[a.pullB[e]];
       }
-      mf_wait(bar, phase, a);
+      copies_ok = mf_wait(bar, phase, a) && copies_ok;
       T y = T(0);
       int c = 0;                                   // column j starts at buf + c + j
       for (int j = 0; j < d.ns; ++j) {
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
     // small supernodes: g_S = y_S - L_BS^T x_B, x_S = Linv_SS^T g_S, one column per lane
     MfWords nx;
     if (L.st + wid < E.st) nx = mf_words(a.st, L.st + wid);
-    for (int t = L.st + wid; t < E.st; t += nw) {
+    for (int t = L.st + wid; t < E.st && copies_ok; t += nw) {
       const MfTask d = mf_decode(nx);
       const int nf = d.ns + d.nb;
       mf_fetch(panel + d.panel, d.ns * nf - d.ns * (d.ns - 1) / 2, buf, bar);
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ 
       const bool col = lane < d.ns;
       T g = col ? v[d.pos0 + lane] : T(0);
       const int cl = col ? mf_cofs(nf, lane) : 0;   // this lane's column
-      mf_wait(bar, phase, a);
+      copies_ok = mf_wait(bar, phase, a) && copies_ok;
 #pragma unroll
       for (int k = 0; k < kMfK; ++k) {
         if (32 * k >= d.nb) break;

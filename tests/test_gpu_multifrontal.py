@@ -210,3 +210,17 @@ def test_batched_handle():
     for i, m in enumerate(mem):
         zi = oracle_for(m, local="exact").apply(r[offs[i]:offs[i + 1]])
         assert relerr(z[offs[i]:offs[i + 1]], zi) <= TOL_FP64, i
+
+
+def test_gmres_with_multifrontal_local_solves():
+    """GMRES(30) with the exact multifrontal local solves (the elasticity setting of
+    config 3 at small size) takes the oracle's GMRES iteration count, +-1."""
+    from oracle import gdsw_oracle as O
+    prob = P.elasticity_problem(6, 2)
+    M = oracle_for(prob, local="exact")
+    _, io = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=30)
+    h = gpu_handle(prob, local_solver="exact", krylov="gmres", restart=30, precision="fp32")
+    assert h.stats()["mf_supernodes"] > 0
+    _, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    assert abs(info.iters - io.iters) <= 1, (info.iters, io.iters)
