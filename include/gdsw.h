@@ -232,6 +232,12 @@ GDSW_API gdsw_status gdsw_solve(gdsw_handle h, const double* b, double* x, gdsw_
 GDSW_API gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
                             gdsw_solve_info* info, void* stream);
 
+/* As gdsw_solve_host from the zero initial guess: only b is copied to the
+ * device (x0 = 0 is set there), x_host is written with the solution and never
+ * read.  Saves the caller zeroing x_host and one host-to-device copy per solve. */
+GDSW_API gdsw_status gdsw_solve_host_zero_guess(gdsw_handle h, const double* b_host, double* x_host,
+                                                gdsw_solve_info* info, void* stream);
+
 GDSW_API gdsw_status gdsw_get_stats(gdsw_handle h, gdsw_stats* st);
 
 /* Numeric phase again for new matrix values on the same sparsity pattern

@@ -427,6 +427,24 @@ gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,
   return st;
 }
 
+gdsw_status gdsw_solve_host_zero_guess(gdsw_handle h, const double* b_host, double* x_host,
+                                       gdsw_solve_info* info, void* stream) {
+  if (!h || !b_host || !x_host) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  Ctx* c = &h->c;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double t0 = now_s();
+  const size_t bytes = sizeof(double) * c->n;
+  // as gdsw_solve_host, with the initial guess set to zero on the device
+  GDSW_CK(cudaMemcpyAsync(c->q, b_host, bytes, cudaMemcpyHostToDevice, s));
+  GDSW_CK(cudaMemsetAsync(c->p, 0, bytes, s));
+  gdsw_status st = solve_any(c, c->q, c->p, info, s);
+  if (st != GDSW_OK && st != GDSW_ERR_NOT_CONVERGED) return st;
+  GDSW_CK(cudaMemcpyAsync(x_host, c->x, bytes, cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (info) info->seconds = now_s() - t0;
+  return st;
+}
+
 gdsw_status gdsw_destroy(gdsw_handle h) {
   if (!h) return GDSW_OK;
   release(&h->c);

@@ -81,6 +81,8 @@ SIGNATURES = {
     "gdsw_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
     "gdsw_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
+    "gdsw_solve_host_zero_guess": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo),
+                                             C.c_void_p]),
     "gdsw_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "gdsw_destroy": (C.c_int, [C.c_void_p]),
     "gdsw_refactor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -242,13 +244,16 @@ class Handle:
             _check(st, "gdsw_solve")
         return info
 
-    def solve_host(self, b: np.ndarray, x: np.ndarray, stream=None, raise_on_nonconvergence=True) -> SolveInfo:
-        """b, x: host float64 arrays (page-locked memory makes the copies asynchronous)."""
+    def solve_host(self, b: np.ndarray, x: np.ndarray, stream=None, raise_on_nonconvergence=True,
+                   zero_guess: bool = False) -> SolveInfo:
+        """b, x: host float64 arrays (page-locked memory makes the copies asynchronous).
+        x holds the initial guess, or with zero_guess=True is only written (x0 = 0)."""
         info = SolveInfo()
-        st = load().gdsw_solve_host(self._handle(), C.c_void_p(_host_ptr(b)), C.c_void_p(_host_ptr(x)),
-                                    C.byref(info), _stream(stream))
+        name = "gdsw_solve_host_zero_guess" if zero_guess else "gdsw_solve_host"
+        st = getattr(load(), name)(self._handle(), C.c_void_p(_host_ptr(b)), C.c_void_p(_host_ptr(x)),
+                                   C.byref(info), _stream(stream))
         if st != ERR_NOT_CONVERGED or raise_on_nonconvergence:
-            _check(st, "gdsw_solve_host")
+            _check(st, name)
         return info
 
     def refactor(self, val: np.ndarray, stream=None):

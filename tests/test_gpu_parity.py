@@ -211,6 +211,27 @@ def test_solve_host_matches_device_solve():
     xh = np.zeros(prob.A.n)
     infoh = h.solve_host(np.ascontiguousarray(prob.b), xh)
     assert infoh.iters == infod.iters and np.array_equal(xh, xd)
+    # from the zero initial guess: x_host is only written (its contents are ignored),
+    # twice in a row with the same result
+    for _ in range(2):
+        xz = np.full(prob.A.n, 7.0)
+        infoz = h.solve_host(np.ascontiguousarray(prob.b), xz, zero_guess=True)
+        assert infoz.iters == infod.iters and np.array_equal(xz, xd)
+
+
+def test_solve_host_zero_guess_on_a_batch():
+    """The zero-guess host solve on a batched handle equals the batched device solve."""
+    from paper_2304_04876_b300 import gdsw as G
+    import torch
+    mem = [P.poisson_problem(8, 4), P.poisson_problem(12, 4)]
+    h = G.Handle.batch([(m.A, m.part, None) for m in mem], local_solver="ic0")
+    b = np.concatenate([m.b for m in mem])
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.zeros_like(bt)
+    h.solve_batch(bt, xt)
+    xz = np.full(b.size, -1.0)
+    info = h.solve_host(np.ascontiguousarray(b), xz, zero_guess=True)
+    assert info.converged and np.array_equal(xz, xt.cpu().numpy())
 
 
 def test_host_made_faults():
