@@ -88,7 +88,7 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes (each array touched once per launch; see DESIGN.md)
+# algorithmic bytes (each array touched once per launch)
 # ---------------------------------------------------------------------------
 
 def apply_bytes(st: dict, vbytes: int, fbytes: int = None) -> dict:
@@ -130,15 +130,19 @@ class ClockSampler:
         self.path = None
 
     def start(self):
-        outdir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
-        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv", dir=outdir)
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # the timed region starts once sampling has (the tool takes a moment to start)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.proc is None:
