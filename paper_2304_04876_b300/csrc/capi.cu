@@ -267,7 +267,7 @@ gdsw_status gdsw_mf_plan_export(const gdsw_csr* A, const gdsw_partition* part, c
     return GDSW_ERR_INVALID_ARG;
   }
   MfPlan M;
-  st = build_mf_plan(P, mf_leaf_size(), kMfBufBytes / 4, &M);
+  st = build_mf_plan(P, mf_leaf_size(), mf_buf_bytes(4) / 4, &M);
   if (st != GDSW_OK) return st;
   const int q = subdomain, base = P.om_ptr[q];
   const int s0 = M.sub_sn[q], s1 = M.sub_sn[q + 1];

@@ -71,7 +71,7 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
              }()) {
     // multifrontal exact solver: panels, solve lists, arena; factor work areas
     MfPlan M;
-    GDSW_TRY(build_mf_plan(P, mf_leaf_size(), kMfBufBytes / int(vrec), &M));
+    GDSW_TRY(build_mf_plan(P, mf_leaf_size(), mf_buf_bytes(int(v)) / int(vrec), &M));
     R += mf_resident_bytes(M, P.nsub, sum_m, vrec, v);
     S += mf_scratch_bytes(M, P.nsub);
   } else {

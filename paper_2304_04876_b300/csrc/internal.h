@@ -175,10 +175,11 @@ struct MfLevel {
 };
 // A supernode is small (one warp solves it from a staged copy of its panel)
 // when it has at most kMfSmall unknowns, at most kMfSmallNb B rows and its
-// panel fits the warp's kMfBufBytes buffer.
+// panel fits the warp's buffer of mf_buf_bytes(es) bytes, es the solve's value
+// size (FP64 solves run 2 CTAs per SM, so their buffers are twice as large).
 constexpr int kMfSmall = 32;
 constexpr int kMfSmallNb = 128;
-constexpr int kMfBufBytes = 3584;
+constexpr int mf_buf_bytes(int es) { return es == 8 ? 7168 : 3584; }
 constexpr int kMfTaskWords = 5;
 struct MfPlan {
   int leaf = 0;

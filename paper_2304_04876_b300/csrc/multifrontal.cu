@@ -250,19 +250,20 @@ __device__ __forceinline__ bool mf_wait(uint64_t* bar, unsigned& phase, const Mf
 }
 
 template <class T, class TS>
-__global__ void __launch_bounds__(256, 4) k_local_mf(const double* __restrict__ r, MfSolveArgs a,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_local_mf(const double* __restrict__ r, MfSolveArgs a,
                                                      const TS* __restrict__ panel_all, T* __restrict__ arena_all,
                                                      T* __restrict__ zloc, const KrylovScalars* __restrict__ ks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ks != nullptr && ks->done) return;
-  constexpr int kBufT = kMfBufBytes / int(sizeof(T));    // x_B gathers
+  constexpr int kBufBytes = mf_buf_bytes(int(sizeof(T)));   // this warp's panel buffer
+  constexpr int kBufT = kBufBytes / int(sizeof(T));         // x_B gathers
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   T* v = reinterpret_cast<T*>(smem_raw + 64 * sizeof(uint64_t));
   T* stage = v + a.vlen;
-  TS* buf = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(stage + a.stage) + wid * kMfBufBytes);
+  TS* buf = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(stage + a.stage) + wid * kBufBytes);
   T* bufT = reinterpret_cast<T*>(buf);             // the same buffer for x_B gathers
   uint64_t* bar = bars + wid;
   if (lane == 0) mbar_init(bar, 1);
@@ -540,7 +541,7 @@ MfSolveArgs solve_args(const Ctx* c) {
 // large supernodes' stage and one panel buffer per warp.
 size_t solve_smem(const Ctx* c, size_t es) {
   return 64 * sizeof(uint64_t) + size_t((c->max_m + 3) & ~3) * es + size_t(c->mf_stage) * es +
-         size_t(c->mf_threads / 32) * kMfBufBytes;
+         size_t(c->mf_threads / 32) * mf_buf_bytes(int(es));
 }
 
 }  // namespace
@@ -583,7 +584,7 @@ gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaSt
   const bool f32 = c->fp32, f16 = c->fp16;
   const size_t es = f32 ? sizeof(float) : sizeof(double);     // vectors
   const size_t ps = f16 ? sizeof(__half) : es;                // panels
-  GDSW_TRY(build_mf_plan(P, mf_leaf_size(), kMfBufBytes / int(ps), &M));
+  GDSW_TRY(build_mf_plan(P, mf_leaf_size(), mf_buf_bytes(int(es)) / int(ps), &M));
   // resident solve data
   GDSW_TRY(upload(c, &c->mf_sn, M.sn, s));
   GDSW_TRY(upload(c, &c->mf_sub_panel, M.sub_panel, s));
