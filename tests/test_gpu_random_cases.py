@@ -12,7 +12,7 @@ from tests.gpu_util import gpu_apply, gpu_handle, oracle_for, relerr
 
 pytestmark = pytest.mark.gpu
 
-SEEDS = list(range(16))
+SEEDS = list(range(40))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -60,4 +60,23 @@ def test_random_problem_apply(seed, monkeypatch):
     for rs in range(2):
         r = np.random.default_rng(rs).uniform(-1, 1, prob.A.n)
         assert relerr(gpu_apply(h, r), M.apply(r)) <= 1e-10, (seed, local, opts)
+    h.close()
+
+
+@pytest.mark.parametrize("seed", SEEDS[:12])
+def test_random_problem_pcg(seed, monkeypatch):
+    """PCG on the same random problems: the oracle's iteration count +-1 and the FP64
+    true residual."""
+    from oracle import gdsw_oracle as O
+    from tests.gpu_util import gpu_solve
+    prob, local, opts = _case(seed)
+    if local == "exact_mf":
+        monkeypatch.setenv("GDSW_EXACT_DENSE_MAX", "0")
+        local = "exact"
+    M = oracle_for(prob, local=local, **opts)
+    _, io = O.pcg(M.spmv, M.apply, prob.b, tol=1e-8)
+    h = gpu_handle(prob, local_solver=local, **opts)
+    x, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    assert abs(info.iters - io.iters) <= 1, (seed, info.iters, io.iters)
     h.close()
