@@ -80,3 +80,31 @@ def test_random_problem_pcg(seed, monkeypatch):
     assert info.converged and info.true_relres <= 1e-8
     assert abs(info.iters - io.iters) <= 1, (seed, info.iters, io.iters)
     h.close()
+
+
+ELAST_SEEDS = list(range(8))
+
+
+@pytest.mark.parametrize("seed", ELAST_SEEDS)
+def test_random_elasticity_apply(seed, monkeypatch):
+    """Q1 elasticity (three unknowns per node, rigid-body null space) with random element
+    counts and block sizes, ragged last blocks included, every local solver."""
+    rng = np.random.default_rng(2000 + seed)
+    ne = int(rng.integers(4, 8))
+    se = int(rng.integers(2, 4))
+    prob = P.elasticity_problem(ne, se)
+    local = ["exact", "exact_mf", "ilu0", "ic0"][seed % 4]
+    opts = dict(overlap=int(rng.integers(0, 2)))
+    if rng.random() < 0.5:
+        opts["coarse"] = "rgdsw"
+    if local in ("ic0", "ilu0"):
+        opts["fill_level"] = int(rng.integers(0, 2))
+    if local == "exact_mf":
+        monkeypatch.setenv("GDSW_EXACT_DENSE_MAX", "0")
+        local = "exact"
+    M = oracle_for(prob, local=local, **opts)
+    h = gpu_handle(prob, local_solver=local, **opts)
+    assert h.stats()["n0"] == M.n0
+    r = np.random.default_rng(seed).uniform(-1, 1, prob.A.n)
+    assert relerr(gpu_apply(h, r), M.apply(r)) <= 1e-10, (seed, ne, se, local, opts)
+    h.close()
