@@ -10,8 +10,9 @@
  * with the GDSW coarse basis of Eq. 2, Phi = [-A_II^-1 A_IGamma; I] Phi_Gamma.
  *
  * Conventions shared by every entry point:
- *  - Matrices and partitions passed to gdsw_setup are HOST memory; the library
- *    copies what it needs and never keeps the caller's pointers.
+ *  - Partitions passed to gdsw_setup are HOST memory, matrices host or device
+ *    memory (gdsw_csr.mem); the library copies what it needs and never keeps
+ *    the caller's pointers.
  *  - Vector arguments of gdsw_apply / gdsw_spmv / gdsw_solve are DEVICE
  *    pointers to n doubles, borrowed for the duration of the call; work is
  *    enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy
@@ -85,15 +86,21 @@ enum { GDSW_COARSE_GDSW = 0, GDSW_COARSE_NONE = 1, GDSW_COARSE_RGDSW = 2 };
  * its least-squares residual can lag the true one and take more steps. */
 enum { GDSW_GMRES_ORTH_CGS2 = 0, GDSW_GMRES_ORTH_SINGLE = 1 };
 
-/* Square sparse matrix, CSR, host memory.  rowptr[n+1], colind[nnz] (0-based,
- * strictly increasing within each row, diagonal stored), val[nnz].  The
- * pattern must be structurally symmetric (it is the pattern of the
- * incomplete factors). */
+/* Where the arrays of a gdsw_csr live. */
+enum { GDSW_MEM_HOST = 0, GDSW_MEM_DEVICE = 1 };
+
+/* Square sparse matrix, CSR.  rowptr[n+1], colind[nnz] (0-based, strictly
+ * increasing within each row, diagonal stored), val[nnz].  The pattern must be
+ * structurally symmetric (it is the pattern of the incomplete factors).
+ * mem = GDSW_MEM_HOST (0, so a zero-initialised struct means host arrays) or
+ * GDSW_MEM_DEVICE: device arrays, which the call copies to the host for the
+ * symbolic phase (a synchronous copy; a failed copy returns GDSW_ERR_CUDA). */
 typedef struct {
   int32_t n;
   const int32_t* rowptr;
   const int32_t* colind;
   const double* val;
+  int32_t mem;
 } gdsw_csr;
 
 /* Structured nonoverlapping decomposition.  Unknown d of node (i,j,k) is

@@ -214,6 +214,31 @@ bool prepare_options(const gdsw_options* opt, gdsw_options* o) {
   return true;
 }
 
+// A host view of a CSR matrix: the caller's arrays for GDSW_MEM_HOST, host
+// copies of device arrays for GDSW_MEM_DEVICE.
+struct HostCsr {
+  gdsw_csr view{};
+  std::vector<int32_t> rp, ci;
+  std::vector<double> va;
+};
+
+gdsw_status host_csr(const gdsw_csr* A, HostCsr* H) {
+  if (!A) { set_error("null matrix"); return GDSW_ERR_INVALID_ARG; }
+  if (A->mem == GDSW_MEM_HOST) { H->view = *A; return GDSW_OK; }
+  if (A->mem != GDSW_MEM_DEVICE) { set_error("gdsw_csr.mem = %d is neither host nor device", A->mem); return GDSW_ERR_INVALID_ARG; }
+  if (A->n <= 0 || !A->rowptr || !A->colind || !A->val) { set_error("null or empty device CSR"); return GDSW_ERR_INVALID_ARG; }
+  H->rp.resize(size_t(A->n) + 1);
+  GDSW_CK(cudaMemcpy(H->rp.data(), A->rowptr, H->rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  const int64_t nnz = H->rp[A->n];
+  if (H->rp[0] != 0 || nnz < A->n || nnz >= (int64_t(1) << 31)) { set_error("device rowptr is not a CSR row pointer"); return GDSW_ERR_INVALID_ARG; }
+  H->ci.resize(nnz);
+  H->va.resize(nnz);
+  GDSW_CK(cudaMemcpy(H->ci.data(), A->colind, size_t(nnz) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  GDSW_CK(cudaMemcpy(H->va.data(), A->val, size_t(nnz) * sizeof(double), cudaMemcpyDeviceToHost));
+  H->view = gdsw_csr{A->n, H->rp.data(), H->ci.data(), H->va.data(), GDSW_MEM_HOST};
+  return GDSW_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -226,6 +251,9 @@ gdsw_status gdsw_setup(const gdsw_csr* A, const gdsw_partition* part, const doub
   if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
   if (nn < 0 || (nn > 0 && !Z)) { set_error("null space: nn=%d with Z=%p", nn, (const void*)Z); return GDSW_ERR_INVALID_ARG; }
   const double t0 = now_s();
+  HostCsr H;
+  GDSW_TRY(host_csr(A, &H));
+  A = &H.view;
   Plan P;
   gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
   if (st != GDSW_OK) return st;
@@ -241,6 +269,9 @@ gdsw_status gdsw_bytes_required(const gdsw_csr* A, const gdsw_partition* part, c
   gdsw_options o;
   if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
   if (nn < 0 || (nn > 0 && !Z)) { set_error("null space: nn=%d with Z=%p", nn, (const void*)Z); return GDSW_ERR_INVALID_ARG; }
+  HostCsr H;
+  GDSW_TRY(host_csr(A, &H));
+  A = &H.view;
   Plan P;
   gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
   if (st != GDSW_OK) return st;
@@ -259,6 +290,9 @@ gdsw_status gdsw_mf_plan_export(const gdsw_csr* A, const gdsw_partition* part, c
   gdsw_options o;
   if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
   if (!m || !nsn || !nb_total) { set_error("null size output"); return GDSW_ERR_INVALID_ARG; }
+  HostCsr H;
+  GDSW_TRY(host_csr(A, &H));
+  A = &H.view;
   Plan P;
   gdsw_status st = build_plan(A, part, &o, false, &P);
   if (st != GDSW_OK) return st;
@@ -323,6 +357,11 @@ gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gdsw_partit
   if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
   if (o.krylov != GDSW_KRYLOV_PCG) { set_error("batched solves use PCG"); return GDSW_ERR_UNSUPPORTED; }
   const double t0 = now_s();
+  std::vector<HostCsr> hosts(count);
+  for (int p = 0; p < count; ++p) GDSW_TRY(host_csr(&A[p], &hosts[p]));
+  std::vector<gdsw_csr> views(count);
+  for (int p = 0; p < count; ++p) views[p] = hosts[p].view;
+  A = views.data();
   std::vector<Plan> plans(count);
   int nnmax = 1;
   int64_t n = 0, nnz = 0;

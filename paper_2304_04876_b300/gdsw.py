@@ -26,7 +26,25 @@ GMRES_ORTH = {"cgs2": 0, "single": 1}
 
 
 class CSRStruct(C.Structure):
-    _fields_ = [("n", C.c_int32), ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("val", C.c_void_p)]
+    _fields_ = [("n", C.c_int32), ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("val", C.c_void_p),
+                ("mem", C.c_int32)]
+
+
+MEM_HOST, MEM_DEVICE = 0, 1
+
+
+def _csr_struct(A):
+    """CSRStruct for A (problems.CSR with numpy arrays, or any object with n and CUDA
+    tensors rowptr/colind (int32) and val (float64)) and the buffers it borrows."""
+    if getattr(A.rowptr, "is_cuda", False):
+        rp, ci, va = A.rowptr, A.colind, A.val
+        assert rp.dtype == ci.dtype and str(rp.dtype) == "torch.int32" and str(va.dtype) == "torch.float64"
+        assert rp.is_contiguous() and ci.is_contiguous() and va.is_contiguous()
+        return CSRStruct(int(A.n), rp.data_ptr(), ci.data_ptr(), va.data_ptr(), MEM_DEVICE), [rp, ci, va]
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+    va = np.ascontiguousarray(A.val, dtype=np.float64)
+    return CSRStruct(int(A.n), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, MEM_HOST), [rp, ci, va]
 
 
 class PartitionStruct(C.Structure):
@@ -179,11 +197,8 @@ class Handle:
         zs = (C.c_void_p * count)()
         nns = (C.c_int32 * count)()
         for i, (A, part, Z) in enumerate(members):
-            rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
-            ci = np.ascontiguousarray(A.colind, dtype=np.int32)
-            va = np.ascontiguousarray(A.val, dtype=np.float64)
-            keep += [rp, ci, va]
-            csrs[i] = CSRStruct(int(A.n), rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+            csrs[i], bufs = _csr_struct(A)
+            keep += bufs
             cuts = [np.ascontiguousarray(c, dtype=np.int32) for c in part.cuts]
             keep += cuts
             parts[i] = PartitionStruct(int(part.nx), int(part.ny), int(part.nz), int(part.dpn))
@@ -281,16 +296,13 @@ class Handle:
 def _marshal(A, part, Z):
     """C structs for a CSR matrix, its partition and null space; the last item
     keeps the numpy buffers alive while the structs are in use."""
-    rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
-    colind = np.ascontiguousarray(A.colind, dtype=np.int32)
-    val = np.ascontiguousarray(A.val, dtype=np.float64)
-    csr = CSRStruct(int(A.n), rowptr.ctypes.data, colind.ctypes.data, val.ctypes.data)
+    csr, keep = _csr_struct(A)
     cuts = [np.ascontiguousarray(c, dtype=np.int32) for c in part.cuts]
     ps = PartitionStruct(int(part.nx), int(part.ny), int(part.nz), int(part.dpn))
     for a in range(3):
         ps.ncut[a] = len(cuts[a])
         ps.cut[a] = cuts[a].ctypes.data if len(cuts[a]) else None
-    keep = [rowptr, colind, val] + cuts
+    keep = keep + cuts
     if Z is None:
         zp, nn = None, 0
     else:

@@ -97,6 +97,7 @@ def test_structs_match_header(lib):
     fields = re.findall(r"(?:int32_t|int64_t|double)\s+(\w+);", body)
     assert fields == [f for f, _ in G.Options._fields_]
     assert C.sizeof(G.Options) == 14 * 4 + 8 + 8
+    assert C.sizeof(G.CSRStruct) == 40          # n, three pointers, mem (padded)
     assert C.sizeof(G.Stats) == 24 * 8 + 9 * 8
 
 
@@ -144,3 +145,20 @@ def test_bytes_required_from_the_symbolic_phase(lib):
     assert rgm - rg >= 61 * 8 * e.A.n
     with pytest.raises(G.GdswError):
         G.bytes_required(small.A, P.Partition(12, 12, 11, 1, small.part.cuts))
+
+
+def test_csr_memory_kind_is_checked(lib):
+    """gdsw_csr.mem must be GDSW_MEM_HOST or GDSW_MEM_DEVICE; any other value is an
+    invalid argument (checked before any device call)."""
+    import ctypes as C
+    from paper_2304_04876_b300 import problems as P
+    prob = P.poisson_problem(6, 3)
+    csr, ps, zp, nn, keep = G._marshal(prob.A, prob.part, None)
+    csr.mem = 7
+    o = G.make_options()
+    res, scr = C.c_int64(), C.c_int64()
+    st = lib.gdsw_bytes_required(C.byref(csr), C.byref(ps), zp, nn, C.byref(o), C.byref(res), C.byref(scr))
+    assert st == 1 and b"mem" in lib.gdsw_last_error()
+    csr.mem = G.MEM_HOST
+    st = lib.gdsw_bytes_required(C.byref(csr), C.byref(ps), zp, nn, C.byref(o), C.byref(res), C.byref(scr))
+    assert st == 0 and res.value > 0
