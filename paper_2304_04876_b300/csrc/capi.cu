@@ -136,10 +136,11 @@ namespace {
 // (one problem, or the merged plan of a batch); the handle on success.
 gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, int32_t nn,
                             const gdsw_options& o, cudaStream_t s, double t0, double t_sym,
-                            gdsw_handle* out) {
+                            gdsw_handle* out, std::shared_ptr<const MfPlan> mf_plan = nullptr) {
   gdsw_ctx* h = new (std::nothrow) gdsw_ctx();
   if (!h) { set_error("host allocation failed"); return GDSW_ERR_OUT_OF_MEMORY; }
   Ctx* c = &h->c;
+  c->mf_plan_host = std::move(mf_plan);
   cudaGetDevice(&c->device);
   c->opt = o;
   c->n = P.n;
@@ -339,7 +340,7 @@ gdsw_status gdsw_refactor(gdsw_handle h, const double* val, void* stream) {
   gdsw_csr A{h->plan.n, h->rowptr.data(), h->colind.data(), val};
   gdsw_handle fresh = nullptr;
   gdsw_status st = setup_from_plan(h->plan, &A, h->Z.empty() ? nullptr : h->Z.data(), h->nn, h->c.opt,
-                                   static_cast<cudaStream_t>(stream), t0, 0.0, &fresh);
+                                   static_cast<cudaStream_t>(stream), t0, 0.0, &fresh, h->c.mf_plan_host);
   if (st != GDSW_OK) return st;           // the handle keeps its previous factors
   std::swap(h->c, fresh->c);
   release(&fresh->c);

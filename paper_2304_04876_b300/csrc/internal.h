@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <cstdlib>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -346,6 +347,7 @@ struct Ctx {
   uint16_t* mf_pullS = nullptr; uint16_t* mf_pullB = nullptr; uint16_t* mf_bidx = nullptr;
   void* mf_panel = nullptr;
   void* mf_arena_buf = nullptr;      // update vectors, mf_arena entries per subdomain
+  std::shared_ptr<const MfPlan> mf_plan_host;   // host plan, kept for gdsw_refactor
   int64_t* mf_sub_panel = nullptr; int* mf_sub_brow = nullptr;
   uint32_t* mf_st = nullptr; uint16_t* mf_brows = nullptr;
   int mf_arena = 0, mf_stage = 0, mf_threads = 256;

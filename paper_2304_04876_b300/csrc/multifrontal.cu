@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <memory>
 #include <type_traits>
 
 #include <cuda_fp16.h>
@@ -580,11 +581,16 @@ gdsw_status mf_launch_local(Ctx* c, const double* r, cudaStream_t s, const Krylo
 }
 
 gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaStream_t s) {
-  MfPlan M;
   const bool f32 = c->fp32, f16 = c->fp16;
   const size_t es = f32 ? sizeof(float) : sizeof(double);     // vectors
   const size_t ps = f16 ? sizeof(__half) : es;                // panels
-  GDSW_TRY(build_mf_plan(P, mf_leaf_size(), mf_buf_bytes(int(es)) / int(ps), &M));
+  // the plan depends on the pattern alone: a refactor reuses the setup's
+  if (!c->mf_plan_host) {
+    auto plan = std::make_shared<MfPlan>();
+    GDSW_TRY(build_mf_plan(P, mf_leaf_size(), mf_buf_bytes(int(es)) / int(ps), plan.get()));
+    c->mf_plan_host = std::move(plan);
+  }
+  const MfPlan& M = *c->mf_plan_host;
   // resident solve data
   GDSW_TRY(upload(c, &c->mf_sn, M.sn, s));
   GDSW_TRY(upload(c, &c->mf_sub_panel, M.sub_panel, s));
