@@ -108,3 +108,39 @@ def test_random_elasticity_apply(seed, monkeypatch):
     r = np.random.default_rng(seed).uniform(-1, 1, prob.A.n)
     assert relerr(gpu_apply(h, r), M.apply(r)) <= 1e-10, (seed, ne, se, local, opts)
     h.close()
+
+
+@pytest.mark.parametrize("seed", SEEDS[12:20])
+def test_random_problem_gmres(seed, monkeypatch):
+    """GMRES on the random problems, with a random restart length: the oracle's GMRES
+    iteration count within +-2 (short restarts amplify rounding differences between
+    the device's CGS2 and the oracle's MGS) and the FP64 true residual."""
+    from oracle import gdsw_oracle as O
+    from tests.gpu_util import gpu_solve
+    prob, local, opts = _case(seed)
+    if local == "exact_mf":
+        monkeypatch.setenv("GDSW_EXACT_DENSE_MAX", "0")
+        local = "exact"
+    restart = int(np.random.default_rng(3000 + seed).integers(5, 31))
+    M = oracle_for(prob, local=local, **opts)
+    _, io = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=restart)
+    h = gpu_handle(prob, local_solver=local, krylov="gmres", restart=restart, **opts)
+    x, info = gpu_solve(h, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    assert abs(info.iters - io.iters) <= 2, (seed, restart, info.iters, io.iters)
+    h.close()
+
+
+@pytest.mark.parametrize("seed", SEEDS[20:28])
+def test_random_problem_fp32_preconditioner(seed, monkeypatch):
+    """The FP32 preconditioner on the random problems: the apply within 2e-5 of the
+    oracle's FP64 one (factors, Phi and the scatter rounded to FP32)."""
+    prob, local, opts = _case(seed)
+    if local == "exact_mf":
+        monkeypatch.setenv("GDSW_EXACT_DENSE_MAX", "0")
+        local = "exact"
+    M = oracle_for(prob, local=local, **opts)
+    h = gpu_handle(prob, local_solver=local, precision="fp32", **opts)
+    r = np.random.default_rng(seed).uniform(-1, 1, prob.A.n)
+    assert relerr(gpu_apply(h, r), M.apply(r)) <= 2e-5, (seed, local, opts)
+    h.close()
