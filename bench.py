@@ -24,7 +24,8 @@ import sys
 import tempfile
 import time
 
-# the CPU oracle legs run single-threaded; set before numpy loads its BLAS
+# the CPU oracle legs spread their local solves over processes (one BLAS thread
+# each); set before numpy loads its BLAS
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -115,6 +116,47 @@ def spmv_bytes(st: dict) -> int:
     return st["nnz"] * 12 + (st["n"] + 1) * 4 + st["n"] * 16
 
 
+def iteration_work(st: dict, vb: int, fb: int, flexible: bool) -> dict:
+    """Algorithmic bytes and FP64 FMAs per launch of each kernel of a PCG iteration
+    (the apply in its PCG form, dots fused into the scatter-add); FP32 or FP16
+    preconditioners do their own arithmetic in FP32, which is not counted."""
+    n, nnz = st["n"], st["nnz"]
+    ab = apply_bytes(st, vb, fb)
+    dots = 2 if flexible else 1
+    fp64_pre = vb == 8
+    tri = st["nnz_L"] + st["nnz_U"] - 2 * st["sum_omega"]
+    return {
+        "spmv": {"bytes": spmv_bytes(st), "fma64": nnz + n},
+        "update": {"bytes": 48 * n, "fma64": 3 * n},
+        "local": {"bytes": ab["local"], "fma64": tri if fp64_pre and not st["dense_local"] else 0},
+        "phiT": {"bytes": ab["phiT"], "fma64": st["nnz_phi"] if fp64_pre else 0},
+        "coarse": {"bytes": ab["coarse"], "fma64": st.get("a0_entries", st["n0"] ** 2)},
+        "combine": {"bytes": ab["combine"] + 8 * dots * n,
+                    "fma64": dots * n + (st["nnz_phi"] if fp64_pre else 0)},
+        "pupdate": {"bytes": 24 * n, "fma64": n},
+    }
+
+
+def rooflines(kernel_ms: dict, work: dict, hbm: float, src: str, fp64_rate: float | None) -> dict:
+    """Per kernel: algorithmic GB/s against the measured HBM peak and, where the
+    kernel works in FP64, FMA/s against the measured FP64 FMA rate; `bound` is the
+    resource with the larger fraction (max(bytes / BW, FMAs / FP64 rate))."""
+    out = {}
+    for k, ms in kernel_ms.items():
+        if k not in work or ms <= 0:
+            continue
+        w = work[k]
+        gbs = w["bytes"] / (ms * 1e-3) / 1e9
+        e = {"us": 1e3 * ms, "algorithmic_bytes": int(w["bytes"]), "gbs": gbs, "hbm_frac": gbs / hbm,
+             "hbm_peak_source": src}
+        if fp64_rate and w["fma64"]:
+            rate = w["fma64"] / (ms * 1e-3)
+            e.update(fma64=int(w["fma64"]), fma64_per_s=rate, fp64_frac=rate / fp64_rate)
+        e["bound"] = "fp64" if e.get("fp64_frac", 0.0) > e["hbm_frac"] else "hbm"
+        out[k] = e
+    return out
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -197,34 +239,125 @@ def oracle_for_variant(prob, cfg: int, variant: str):
     return O.GDSW(prob.A, prob.part, Z, local=local, trsv=trsv)
 
 
-def oracle_iteration_time(M, b, n_iter: int) -> float:
-    """Median time of one oracle Krylov iteration: SpMV + M^-1 apply + vector updates."""
+class OracleCores:
+    """The oracle's preconditioner apply spread over the host cores: worker processes,
+    forked after the oracle is built (so they share its factors) and before any CUDA
+    call, each run the oracle's own `local_solve` for a slice of the subdomains into a
+    shared buffer; the parent then sums the local terms in ascending subdomain order
+    and adds the coarse term exactly as `GDSW.apply` does, so the result is the
+    oracle's, value for value.  SpMV is the oracle's own (one core)."""
+
+    def __init__(self, M, workers: int):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        self.M = M
+        sizes = [len(d) for d in M.omega]
+        self.offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self._shm = [shared_memory.SharedMemory(create=True, size=max(8, 8 * M.n)),
+                     shared_memory.SharedMemory(create=True, size=max(8, 8 * int(self.offs[-1])))]
+        self.r = np.ndarray((M.n,), np.float64, buffer=self._shm[0].buf)
+        self.zl = np.ndarray((int(self.offs[-1]),), np.float64, buffer=self._shm[1].buf)
+        ns = len(M.omega)
+        self.workers = max(1, min(workers, ns))
+        # contiguous slices of subdomains, about equal in unknowns
+        cuts = np.searchsorted(self.offs, np.linspace(0, self.offs[-1], self.workers + 1))
+        cuts[0], cuts[-1] = 0, ns
+        self.slices = [(int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        global _ORACLE_CORES
+        _ORACLE_CORES = self
+        self.pool = mp.get_context("fork").Pool(self.workers) if self.workers > 1 else None
+
+    def apply(self, r):
+        M = self.M
+        self.r[:] = r
+        if self.pool is None:
+            _oracle_local_slice((0, len(M.omega)))
+        else:
+            self.pool.map(_oracle_local_slice, self.slices)
+        z = np.zeros(M.n)
+        for s, dofs in enumerate(M.omega):
+            z[dofs] += self.zl[self.offs[s]:self.offs[s + 1]]
+        if M.n0:
+            import scipy.linalg as sla
+            c = M.coarse.Phi.T @ r
+            y = sla.cho_solve(M.A0fac, c)
+            z += M.coarse.Phi @ y
+        return z
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.terminate()
+            self.pool.join()
+        for m in self._shm:
+            m.close()
+            m.unlink()
+
+
+_ORACLE_CORES = None
+
+
+def _oracle_local_slice(bounds):
+    oc = _ORACLE_CORES
+    for s in range(bounds[0], bounds[1]):
+        oc.zl[oc.offs[s]:oc.offs[s + 1]] = oc.M.local_solve(s, oc.r[oc.M.omega[s]])
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_iteration(M, apply, r, p):
+    """One oracle Krylov iteration: SpMV, step, residual update, M^-1 apply, new direction."""
+    q = M.spmv(p)
+    alpha = (r @ p) / (p @ q)
+    r = r - alpha * q
+    z = apply(r)
+    beta = (r @ z) / (r @ r + 1.0)
+    return r, z + beta * p
+
+
+def oracle_iteration_time(M, apply, b, n_iter: int) -> float:
+    """Median time of one oracle Krylov iteration."""
     r = b.copy()
-    p = M.apply(r)
+    p = apply(r)
     times = []
     for _ in range(n_iter):
         t1 = time.perf_counter()
-        q = M.spmv(p)
-        alpha = (r @ p) / (p @ q)
-        r = r - alpha * q
-        z = M.apply(r)
-        beta = (r @ z) / (r @ r + 1.0)
-        p = z + beta * p
+        r, p = oracle_iteration(M, apply, r, p)
         times.append(time.perf_counter() - t1)
     return statistics.median(times)
 
 
-def oracle_sample(prob, cfg: int, variant: str, iters_for_metric: int, n_iter: int = 2) -> dict:
-    """The oracle (single thread) on the full workload after its setup: solves/s =
-    1 / (seconds per Krylov iteration * iterations of a solve)."""
+def oracle_sample(prob, cfg: int, variant: str, iters_for_metric: int, n_iter: int = 3) -> dict:
+    """The oracle on the full workload after its setup, its local solves on all host
+    cores: solves/s = 1 / (seconds per Krylov iteration * iterations of a solve).
+    Must run before the process makes its first CUDA call (the pool is forked)."""
     t0 = time.perf_counter()
     M = oracle_for_variant(prob, cfg, variant)
     setup_s = time.perf_counter() - t0
-    t_it = oracle_iteration_time(M, prob.b, n_iter)
-    return {"value": 1.0 / (t_it * iters_for_metric), "unit": "solves/s", "cores": 1, "kind": "oracle",
+    oc = OracleCores(M, host_cores())
+    try:
+        t_it = oracle_iteration_time(M, oc.apply, prob.b, n_iter)
+    finally:
+        oc.close()
+    return {"value": 1.0 / (t_it * iters_for_metric), "unit": "solves/s", "cores": oc.workers, "kind": "oracle",
+            "cpu": cpu_model(), "host_cores": host_cores(),
             "sample": f"{n_iter} oracle Krylov iterations (SpMV + M^-1 apply + updates) on the full workload, "
-                      f"median {t_it:.3f} s/iteration x {iters_for_metric} iterations per solve; "
-                      f"oracle setup {setup_s:.1f} s not counted",
+                      f"local solves in {oc.workers} processes; median {t_it:.3f} s/iteration x "
+                      f"{iters_for_metric} iterations per solve; oracle setup {setup_s:.1f} s not counted",
             "seconds_per_iteration": t_it, "oracle_setup_s": setup_s}
 
 
@@ -241,28 +374,35 @@ def run_reference(args, rank: int):
     prob = C["make"]()
     iters = golden_iters(cfg, variant) or 40
     M = oracle_for_variant(prob, cfg, variant)
+    oc = OracleCores(M, host_cores())
+    state = {"r": prob.b.copy(), "p": oc.apply(prob.b)}
 
     def step():
-        # one bounded sample: one oracle Krylov iteration on the full workload
-        q = M.spmv(prob.b)
-        z = M.apply(prob.b - 1e-3 * q)
-        return float(z[0])
+        # one bounded sample of the workload: one oracle Krylov iteration
+        state["r"], state["p"] = oracle_iteration(M, oc.apply, state["r"], state["p"])
 
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t0
+    try:
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        el = time.perf_counter() - t0
+    finally:
+        oc.close()
     t_it = el / args.steps
     value = 1.0 / (t_it * iters)
     line = {"impl": "reference", "metric": C["metric"], "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_it * iters,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_it,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": C["workload"], "variant": variant, "n": prob.A.n},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step = one oracle Krylov iteration (SpMV + apply) on the full "
-                                       f"workload; solves/s = 1/(s per iteration x {iters} iterations)"},
+            "step": f"one oracle Krylov iteration (SpMV + M^-1 apply + updates) on the full workload; "
+                    f"value = solves/s = 1/(s per step x {iters} iterations of a solve)",
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oc.workers, "kind": "oracle",
+                             "cpu": cpu_model(), "host_cores": host_cores(),
+                             "sample": f"each step = one oracle Krylov iteration on the full workload, local "
+                                       f"solves in {oc.workers} processes; solves/s = 1/(s per iteration x "
+                                       f"{iters} iterations)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -292,7 +432,8 @@ def timed_solves(h, bs, x, steps, warmup, stream, barrier, solve=None):
     return e0.elapsed_time(e1) / 1e3, infos
 
 
-def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=None):
+def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=None, flexible=False,
+                        fp64_rate=None, krylov="pcg"):
     """Per-phase apply times (CUDA events on the launching stream), the apply as
     the solver runs it (branches overlapped) and the SpMV."""
     import torch
@@ -324,18 +465,43 @@ def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=N
     names = ["local", "phiT", "coarse", "combine"]
     phase_ms = dict(zip(names, phases.tolist()))
     ab = apply_bytes(st, vb, fb)
-    dom = max(names, key=lambda k: phase_ms[k])
-    achieved = ab[dom] / (phase_ms[dom] * 1e-3) / 1e9
+    # every kernel of a PCG iteration, timed one by one (CUDA events on the
+    # launching stream); the dominant kernel is the slowest of them all
+    work = iteration_work(st, vb, fb if fb is not None else vb, flexible)
+    if st.get("n_problems", 1) == 1:
+        acc = {}
+        for _ in range(3):
+            h.pcg_iteration_timed(v0)
+        for _ in range(reps):
+            for k, v in h.pcg_iteration_timed(v0).items():
+                acc[k] = acc.get(k, 0.0) + v / reps
+        kernel_ms = acc
+        if krylov != "pcg":
+            # GMRES has its own vector kernels; keep the SpMV and the apply's phases
+            kernel_ms = {k: v for k, v in acc.items() if k not in ("update", "pupdate")}
+    else:
+        kernel_ms = {**phase_ms, "spmv": spmv_ms}
+    per_kernel = rooflines(kernel_ms, work, hbm, src, fp64_rate)
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["us"])
+    achieved = per_kernel[dom]["gbs"]
+    dom_entry = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                 "frac": achieved / hbm, "traffic": profiled_traffic(dom, workload, variant),
+                 "peak_source": src, "algorithmic_bytes_per_launch": per_kernel[dom]["algorithmic_bytes"],
+                 "launch_us": per_kernel[dom]["us"]}
+    if "fp64_frac" in per_kernel[dom]:
+        dom_entry["fp64"] = {"fma_per_launch": per_kernel[dom]["fma64"],
+                             "achieved_fma_per_s": per_kernel[dom]["fma64_per_s"], "peak_fma_per_s": fp64_rate,
+                             "frac": per_kernel[dom]["fp64_frac"], "peak_source": "measured live "
+                             "(gdsw_measure_fma_rate)"}
     return {
         "apply_ms": float(phases.sum()), "apply_phase_ms": phase_ms,
         "apply_gbs": sum(ab.values()) / (phases.sum() * 1e-3) / 1e9,
         "apply_overlapped_ms": overlapped,
         "apply_overlapped_gbs": sum(ab.values()) / (overlapped * 1e-3) / 1e9,
         "spmv_ms": spmv_ms, "spmv_gbs": spmv_bytes(st) / (spmv_ms * 1e-3) / 1e9,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": profiled_traffic(dom, workload, variant),
-                     "peak_source": src,
-                     "algorithmic_bytes_per_launch": ab[dom]},
+        "iteration_kernel_us": {k: 1e3 * v for k, v in kernel_ms.items()},
+        "rooflines": per_kernel,
+        "roofline": dom_entry,
     }
 
 
@@ -373,7 +539,7 @@ def launches_per_solve(iters, krylov="pcg"):
     return sum(9 + 8 * it for it in iters) if krylov == "pcg" else None
 
 
-def run_single(args, world, rank, dist, barrier):
+def run_single(args, world, rank, dist, barrier, cpu_baseline=None):
     import torch
     from paper_2304_04876_b300 import gdsw
     cfg = args.config
@@ -413,7 +579,9 @@ def run_single(args, world, rank, dist, barrier):
     e2e_el = R.max_over_ranks(time.perf_counter() - te, dist, "cuda")
     vb = 4 if opts.get("precision") in ("fp32", "fp16") else 8
     fb = 2 if opts.get("precision") == "fp16" else vb
-    km = kernel_measurements(h, st, vb, stream, bs[0], C["workload"], variant, fb)
+    fp64_rate = gdsw.measure_fma_rate("fp64")
+    km = kernel_measurements(h, st, vb, stream, bs[0], C["workload"], variant, fb, flexible=vb < 8,
+                             fp64_rate=fp64_rate, krylov=opts.get("krylov", "pcg"))
     line = {
         "metric": C["metric"], "value": R.job_rate(args.steps, el, world), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -434,6 +602,7 @@ def run_single(args, world, rank, dist, barrier):
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches_per_solve(iters, opts.get("krylov", "pcg")),
         "clocks": clk,
+        "fp64_fma_per_s": fp64_rate,
     }
     if not args.no_variants and rank == 0:
         var = {}
@@ -446,9 +615,8 @@ def run_single(args, world, rank, dist, barrier):
                          "true_relres_max": max(i.true_relres for i in inf)}
             hv.close()
         line["variants"] = var
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        it_ref = golden_iters(cfg, variant) or int(np.median(iters))
-        line["cpu_baseline"] = oracle_sample(prob, cfg, variant, it_ref)
+    if cpu_baseline is not None:
+        line["cpu_baseline"] = cpu_baseline
     h.close()
     return line
 
@@ -542,65 +710,116 @@ def run_batch(args, world, rank, dist, barrier):
 
 def run_serving(args, world, rank, dist, barrier):
     """Config 5: Poisson-arrival stream of mixed Poisson / Q1 elasticity requests served
-    continuously (resident handles under a memory budget, concurrent streams); p50/p99
-    latency and solves/s per arrival rate."""
+    with continuous batching (resident solve slots of batched handles chosen under a
+    memory budget; the iterations of all running requests are shared launches, and
+    requests join and leave between iterations); p50/p99 latency and solves/s per
+    arrival rate, beside the plain FP64 one-at-a-time solve of the same stream."""
     import torch
     from paper_2304_04876_b300 import gdsw
     from paper_2304_04876_b300 import serving as S
     pool = P.serving_pool(args.pool, seed=rank)
     byname = {p.name: p for p in pool}
     opts = dict(local_solver="ic0", trsv="levelsched", precision="fp32")
-
-    def make(key, stream):
-        pr = byname[key]
-        return gdsw.Handle(pr.A, pr.part, pr.Z if pr.part.dpn == 3 else None, stream=stream, **opts)
-
-    est = {}
-
-    def estimate(key):
-        # resident handle plus the setup's transient scratch, from the symbolic phase
-        if key not in est:
-            pr = byname[key]
-            r, sc = gdsw.bytes_required(pr.A, pr.part, pr.Z if pr.part.dpn == 3 else None, **opts)
-            est[key] = r + sc
-        return est[key]
-
+    zof = lambda pr: pr.Z if pr.part.dpn == 3 else None  # noqa: E731
     free, _total = torch.cuda.mem_get_info()
-    budget = int(args.serving_budget_gb * (1 << 30)) if args.serving_budget_gb else int(0.8 * free)
-    srv = S.Server(make, estimate, budget, workers=args.workers)
-    # warm: set every pool problem up once (resident factors), reported separately
+    budget = int(args.serving_budget_gb * (1 << 30)) if args.serving_budget_gb else int(0.6 * free)
+    est = [(p.name, p.part.dpn, gdsw.bytes_required(p.A, p.part, zof(p), **opts)[0]) for p in pool]
+    plan = S.plan_slots(est, budget, max_copies=args.serving_copies)
+    problems = {p.name: (p.A, p.part, zof(p)) for p in pool}
     t0 = time.perf_counter()
-    warm = srv.run([S.Request(0.0, i, p.name, P.rhs_uniform(p.A.n, 7)) for i, p in enumerate(pool)])
+    pools, slots = S.build_pools(problems, plan, **opts)
     warm_s = time.perf_counter() - t0
-    rates = {}
-    rng = np.random.default_rng(rank)
-    for lam in args.rates:
-        arr = S.poisson_arrivals(lam, args.requests, seed=int(lam))
+    # every result is read back to the host, as a client would receive it
+    srv = S.BatchServer(pools, slots, iterations=args.serving_iters, keep_x=True)
+    # warm-up: every slot once
+    srv.run([S.Request(0.0, i, sl.key, P.rhs_uniform(sl.n, 7)) for i, sl in enumerate(slots)])
+    admitted = sorted({sl.key for sl in slots})
+
+    def stream(lam, count):
+        rng = np.random.default_rng(int(lam) + 17 * rank)
+        arr = S.poisson_arrivals(lam, count, seed=int(lam))
         reqs = []
         for i, t in enumerate(arr):
-            pr = pool[int(rng.integers(len(pool)))]
+            pr = byname[admitted[int(rng.integers(len(admitted)))]]
             reqs.append(S.Request(float(t), i, pr.name, P.rhs_uniform(pr.A.n, 1000 + i)))
-        res = srv.run(reqs)
+        return reqs
+
+    rates = {}
+    for lam in args.rates:
+        res = srv.run(stream(lam, args.requests))
         rates[str(lam)] = S.summarize(res)
     top = rates[str(max(args.rates))]
+    # the plain FP64 one-problem-at-a-time solve of the same (saturated) stream:
+    # one resident FP64 handle per problem, one solve at a time on one stream
+    plain_opts = dict(local_solver="ic0", trsv="levelsched", precision="fp64")
+    plain = S.Server(lambda key, st: gdsw.Handle(byname[key].A, byname[key].part, zof(byname[key]), stream=st,
+                                                 **plain_opts),
+                     lambda key: 0, budget_bytes=1 << 62, workers=1, keep_x=True)
+    plain.run([S.Request(0.0, i, k, P.rhs_uniform(byname[k].A.n, 7)) for i, k in enumerate(admitted)])
+    plain_top = S.summarize(plain.run(stream(max(args.rates), args.requests)))
+    plain.close()
     sizes = sorted(p.A.n for p in pool)
     line = {
-        "metric": "served solves/s (saturated) with p50/p99 latency, mixed Poisson / Q1 elasticity",
+        "metric": "served solves/s (saturated) with p50/p99 latency, mixed Poisson / Q1 elasticity, "
+                  "continuous batching",
         "value": world * top["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.requests,
-        "warmup": len(pool), "ms_per_step": 1e3 / top["solves_per_s"], "higher_is_better": True,
+        "warmup": len(slots), "ms_per_step": 1e3 / top["solves_per_s"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"serving_pool{len(pool)}_poisson+elasticity_32^3-160^3", "pool_unknowns": sizes,
-                   "workers": args.workers, "budget_bytes": budget, "rates_req_per_s": args.rates,
+                   "slots": len(slots), "admitted_problems": len(admitted), "budget_bytes": budget,
+                   "iterations_per_round": args.serving_iters, "rates_req_per_s": args.rates,
                    "requests_per_rate": args.requests, "parallelism": f"replicas{world}"},
         "rates": rates, "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
-        "warm_setup_s": warm_s, "setups": srv.setups, "evictions": srv.evictions,
+        "plain_fp64_one_at_a_time": plain_top,
+        "served_over_plain": top["solves_per_s"] / plain_top["solves_per_s"],
+        "warm_setup_s": warm_s, "rounds": srv.rounds, "rejected": srv.rejected,
         "e2e": {"value": world * top["solves_per_s"], "unit": "solves/s",
                 "h2d_bytes_per_step": int(np.mean([8 * n for n in sizes])),
                 "d2h_bytes_per_step": int(np.mean([8 * n for n in sizes]))},
         "gpu_launches": None, "roofline": None,
     }
-    srv.close()
+    for h in pools:
+        h.close()
     return line
+
+
+def config_summaries(args, world, rank, dist, barrier) -> dict:
+    """Bounded runs of the other workloads for the default line (configs 1, 3, 4, 5),
+    each reduced to its headline numbers; the full lines come from --config N."""
+    import copy
+    out = {}
+    keep = ("metric", "value", "unit", "ms_per_step", "iters", "iters_min_max", "true_relres_max", "setup_s",
+            "one_at_a_time_problems_per_s", "p50_ms", "p99_ms", "plain_fp64_one_at_a_time", "served_over_plain",
+            "rates", "slots", "roofline", "apply_phase_ms", "spmv_ms", "variants")
+    for cfg, extra in ((1, dict(steps=20, warmup=3)), (3, dict(steps=3, warmup=3)),
+                       (4, dict(steps=2, warmup=3)), (5, dict(requests=40, rates=[100.0, 1000.0]))):
+        a = copy.copy(args)
+        a.config, a.variant, a.no_cpu_baseline = cfg, None, True
+        for k, v in extra.items():
+            setattr(a, k, v)
+        a.no_variants = True
+        t0 = time.perf_counter()
+        try:
+            if cfg == 4:
+                line = run_batch(a, world, rank, dist, barrier)
+            elif cfg == 5:
+                line = run_serving(a, world, rank, dist, barrier)
+            else:
+                line = run_single(a, world, rank, dist, barrier)
+        except Exception as e:                      # reported, not fatal to the headline
+            out[str(cfg)] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        d = {k: line[k] for k in keep if k in line}
+        d["workload"] = line["config"]["workload"]
+        d["steps"] = line.get("steps")
+        if isinstance(d.get("roofline"), dict):
+            r = d["roofline"]
+            d["roofline"] = {k: r.get(k) for k in ("kernel", "achieved", "peak", "frac", "launch_us")}
+        if "iters" in d and isinstance(d["iters"], list):
+            d["iters"] = [min(d["iters"]), max(d["iters"])]
+        d["wall_s"] = time.perf_counter() - t0
+        out[str(cfg)] = d
+    return out
 
 
 def run_profile(args):
@@ -638,13 +857,17 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--variant", default=None)
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--pool", type=int, default=8, help="serving: distinct problems")
+    ap.add_argument("--pool", type=int, default=16, help="serving: distinct problems")
+    ap.add_argument("--serving-copies", type=int, default=2, help="serving: most slots per problem")
+    ap.add_argument("--serving-iters", type=int, default=4, help="serving: PCG iterations per round")
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per rate")
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
     ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--serving-budget-gb", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default line without the bounded runs of configs 1, 3, 4, 5")
     ap.add_argument("--profile", default=None, choices=["solve", "apply"],
                     help="untimed solves or applies for profiler captures (configs 1-3)")
     ap.add_argument("--profile-count", type=int, default=1)
@@ -660,6 +883,15 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+
+    # the oracle's CPU baseline first: its worker processes are forked, which must
+    # happen before this process makes any CUDA call
+    cpu_baseline = None
+    if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.profile is None
+            and args.config in (1, 2, 3)):
+        C = CONFIGS[args.config]
+        variant = args.variant or C["default"]
+        cpu_baseline = oracle_sample(C["make"](), args.config, variant, golden_iters(args.config, variant) or 73)
 
     import torch
     from paper_2304_04876_b300 import build, gdsw
@@ -687,7 +919,9 @@ def main():
     elif args.config == 5:
         line = run_serving(args, world, rank, dist, barrier)
     else:
-        line = run_single(args, world, rank, dist, barrier)
+        line = run_single(args, world, rank, dist, barrier, cpu_baseline)
+        if args.config == 2 and not args.no_configs and world == 1:
+            line["configs"] = config_summaries(args, world, rank, dist, barrier)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -216,6 +216,49 @@ GDSW_API gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gd
 GDSW_API gdsw_status gdsw_solve_batch(gdsw_handle h, const double* b, double* x,
                                       gdsw_solve_info* info, void* stream);
 
+/* ---- Continuous batching on a batched handle (gdsw_setup_batch) ----------
+ * The paper runs many subdomains per GPU through several MPI ranks per GPU
+ * (Sec. VI); here the members of a batched handle are solve slots that start,
+ * iterate together in shared launches, and finish independently, so a request
+ * that arrives while others are on the GPU joins them between iterations.
+ * A member's arithmetic never mixes with another's (block-diagonal operator,
+ * per-member scalars and reductions in a fixed order), so its result is the
+ * same bit for bit whichever other members are active.  All calls take the
+ * caller's stream; do not mix them with gdsw_solve_batch on the same handle
+ * (a whole-batch solve ends every started member). */
+
+/* Starts member `member` (0-based, in the order given to gdsw_setup_batch) on
+ * right-hand side b (DEVICE vector of that member's n entries, copied; the
+ * initial guess is x = 0).  The next iteration performs its PCG prologue
+ * (z = M^-1 b, p = z); the one after it is its first counted iteration.  A
+ * member that is still iterating is restarted.  The first call on a handle
+ * marks every member idle.  Errors: INVALID_ARG (not batched, member out of
+ * range, NULL b), CUDA. */
+GDSW_API gdsw_status gdsw_batch_start(gdsw_handle h, int32_t member, const double* b, void* stream);
+
+/* Enqueues `iterations` PCG iterations (Sec. II's loop around Eq. 1) of every
+ * started member that has not stopped; stopped and idle members cost only the
+ * check of their flag.  Asynchronous.  Errors: INVALID_ARG (not batched, no
+ * member started, iterations < 0), CUDA. */
+GDSW_API gdsw_status gdsw_batch_iterate(gdsw_handle h, int32_t iterations, void* stream);
+
+/* Waits for `stream` and reports every member (arrays of count entries, any
+ * may be NULL): done[m] = 1 when member m has stopped (its recurrence residual
+ * met the tolerance, maxit, a breakdown, or it is idle), iters[m] its
+ * iteration count, relres[m] its recurrence residual ||r|| / ||b||.
+ * Errors: INVALID_ARG, TIMEOUT (a bounded device wait ran out), CUDA. */
+GDSW_API gdsw_status gdsw_batch_status(gdsw_handle h, int32_t* done, int32_t* iters, double* relres,
+                                       void* stream);
+
+/* For a stopped member: recomputes its true residual b - A x in FP64.  If it
+ * meets the tolerance (or the member hit maxit or broke down) the member's x is
+ * copied to `x` (DEVICE, n entries; NULL skips the copy), *info is filled and
+ * *continued = 0; otherwise the member continues from its true residual (as
+ * gdsw_solve does) and *continued = 1.  Waits for `stream`.  Errors:
+ * INVALID_ARG (member still iterating, out of range), CUDA. */
+GDSW_API gdsw_status gdsw_batch_finish(gdsw_handle h, int32_t member, double* x, gdsw_solve_info* info,
+                                       int32_t* continued, void* stream);
+
 /* z = M^-1 r (Eq. 1), device vectors. */
 GDSW_API gdsw_status gdsw_apply(gdsw_handle h, const double* r, double* z, void* stream);
 
@@ -224,6 +267,19 @@ GDSW_API gdsw_status gdsw_apply(gdsw_handle h, const double* r, double* z, void*
  * [2] coarse solve, [3] scatter-add + prolongation. */
 GDSW_API gdsw_status gdsw_apply_timed(gdsw_handle h, const double* r, double* z, void* stream,
                              double* phase_ms);
+
+/* Measurement of one PCG iteration (Sec. II's Krylov loop around Eq. 1),
+ * kernel by kernel: sets up the PCG state for right-hand side b (device
+ * vector, n entries; x0 = 0, r = b, z = M^-1 r, p = z), runs one iteration
+ * with every kernel on `stream` in order (the apply's two branches are not
+ * overlapped) and CUDA events between them, waits, and writes the device times
+ * in ms to kernel_ms[7]: [0] SpMV with (p, Ap), [1] x, r update with ||r||^2,
+ * [2] gather + local solve, [3] Phi^T r, [4] coarse solve, [5] scatter-add +
+ * prolongation with the PCG dots, [6] new direction p.  Overwrites the
+ * handle's Krylov workspace.  Errors: INVALID_ARG (NULL), UNSUPPORTED
+ * (batched handle), TIMEOUT, CUDA. */
+GDSW_API gdsw_status gdsw_pcg_iteration_timed(gdsw_handle h, const double* b, void* stream,
+                                              double* kernel_ms);
 
 /* y = A x with the CSR matrix given at setup, device vectors. */
 GDSW_API gdsw_status gdsw_spmv(gdsw_handle h, const double* x, double* y, void* stream);
@@ -304,12 +360,24 @@ GDSW_API gdsw_status gdsw_destroy(gdsw_handle h);
  * 5-10 entries, 0.5 million rows of more than 24): larger n returns
  * GDSW_ERR_UNSUPPORTED with the limit in gdsw_last_error().  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call on a device
+ * make that first call before any stream capture; the cached address assumes
+ * the device's primary context lives as long as the process (no
+ * cudaDeviceReset between calls).  Every call on a device
  * shares the array: calls whose kernels may overlap on the GPU race and must
  * be ordered by the caller.  Work is enqueued on `stream`. */
 GDSW_API gdsw_status gdsw_spmv_dot_noalloc(int32_t n, int64_t nnz, const int32_t* rowptr,
                                            const int32_t* colind, const double* val,
                                            const double* x, double* y, double* dot, void* stream);
+
+/* Measures the device's FMA throughput in FP64 (GDSW_PREC_FP64) or FP32
+ * (GDSW_PREC_FP32): eight independent FMA chains per thread on every SM, the
+ * best of four timed launches (CUDA events), written to *fma_per_second.  The
+ * paper has no counterpart: it is the arithmetic denominator of the rooflines
+ * of the FP64 Krylov kernels (SpMV, vector updates, coarse GEMV), whose bound
+ * on B300 is max(bytes / HBM bandwidth, FMAs / FP64 rate).  Allocates and
+ * frees a few KB of device memory; runs about 0.1 s on `stream`, then
+ * synchronises.  Errors: INVALID_ARG (precision, NULL output), CUDA. */
+GDSW_API gdsw_status gdsw_measure_fma_rate(int32_t precision, double* fma_per_second, void* stream);
 
 GDSW_API const char* gdsw_status_string(gdsw_status s);
 GDSW_API const char* gdsw_last_error(void);

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgdsw.so")
 
-SOURCES = ["symbolic.cpp", "supernodal.cpp", "footprint.cpp", "setup.cu", "apply.cu", "krylov.cu", "capi.cu", "noalloc.cu", "batch.cu", "multifrontal.cu"]
+SOURCES = ["symbolic.cpp", "supernodal.cpp", "footprint.cpp", "setup.cu", "apply.cu", "krylov.cu", "capi.cu", "noalloc.cu", "batch.cu", "multifrontal.cu", "peak.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -122,11 +122,12 @@ __global__ void __launch_bounds__(1024) k_local_tri(const double* __restrict__ r
                                                    const int* __restrict__ om_dofs, EllDev<T> L,
                                                    EllDev<T> U, int jacobi, int sweeps,
                                                    T* __restrict__ zloc,
-                                                   const KrylovScalars* __restrict__ ks) {
+                                                   const KrylovScalars* __restrict__ ks, BatchGate gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ks != nullptr && ks->done) return;
   T* v = reinterpret_cast<T*>(smem_raw);
   const int s = blockIdx.x;
+  if (gate_sub_off(gate, s)) return;
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
   gather_sub(r, om_dofs, base, m, v, threadIdx.x, blockDim.x);
   __syncthreads();
@@ -190,7 +191,7 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
   const int4 hdr = *reinterpret_cast<const int4*>(rec);
   const int4 hdr1 = *reinterpret_cast<const int4*>(rec + 16);
   const int nr = hdr.x, K = hdr.y;          // rows, stored width
-  const int layout = hdr1.y;                // 0 column-major, 1 row-major by 4, 2 by node
+  const int layout = hdr1.y & 0xff;         // 0 column-major, 1 row-major by 4, 2 by node
   const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 32);
   const TS* dinv = reinterpret_cast<const TS*>(rec + 32 + ((2 * nr + 15) & ~15));
   const TS* vals = reinterpret_cast<const TS*>(rec + hdr.z);
@@ -298,6 +299,114 @@ __device__ __forceinline__ bool consumers_sync_or(bool pred, int nt) {
   return out != 0;
 }
 
+// v = R_s r from indices already staged in shared memory (`idx`: this
+// subdomain's slice of the overlap map), sixteen values in flight per thread.
+// For FP32 vectors `idx` and `v` share their words: each thread reads and
+// writes only its own positions.  For FP64 `idx` sits in the upper half of
+// the vector's space, and a barrier between the index reads and the value
+// writes of each round keeps a value from overwriting an index still to be
+// read (the values of a round land below the indices of every later round).
+template <class T>
+__device__ __forceinline__ void gather_staged(const double* __restrict__ r, const int* idx, T* v, int m,
+                                              int nt) {
+  constexpr int U = 16;
+  const int tid = threadIdx.x;
+  for (int i0 = 0; i0 < m; i0 += U * nt) {
+    double rv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + tid + u * nt;
+      rv[u] = i < m ? r[idx[i]] : 0.0;
+    }
+    if (sizeof(T) == 8) consumers_sync_or(false, nt);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + tid + u * nt;
+      if (i < m) v[i] = T(rv[u]);
+    }
+  }
+}
+
+// Shared memory of the pipelined solve's local vector: m values plus the room
+// the staged overlap indices need (an aligned start and up to three words on
+// either side of the subdomain's slice).
+inline size_t pipe_vector_bytes(int max_m, size_t es) { return (size_t(max_m) * es + 48 + 15) & ~size_t(15); }
+
+// Producer warp of the pipelined local solves: lane 0 first copies the
+// subdomain's overlap indices (om_dofs[first, first + cnt), one bulk copy into
+// idx_dst, completing on gbar); the lanes fetch the pack offsets and sizes 32
+// at a time, lane 0 waits for free stages and issues the copies, and keeps
+// `prefetch_bytes` of the subdomain's records beyond the ring on their way
+// into L2.  Every copy issued has landed before it returns.
+template <int S>
+__device__ __forceinline__ void pipe_producer(const int* __restrict__ om_dofs, int first, int cnt,
+                                              unsigned char* idx_dst, uint64_t* gbar,
+                                              const uint32_t* __restrict__ rec_off16,
+                                              const uint32_t* __restrict__ rec_bytes, int r0, int nrec,
+                                              const uint8_t* __restrict__ stream, unsigned char* stages,
+                                              int stage_bytes, uint64_t* full, uint64_t* empty, int* err,
+                                              long long wait_cycles, int stall_test, int prefetch_bytes) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0 && cnt > 0) {
+    mbar_expect_tx(gbar, unsigned(cnt) * 4u);
+    bulk_g2s(idx_dst, om_dofs + first, unsigned(cnt) * 4u, gbar);
+  }
+  int last[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) last[j] = -1;
+  uint32_t my_off = 0, my_nb = 0;
+  // end of the subdomain's record bytes, and how far the L2 prefetch reached
+  size_t pf_end = 0, pf = 0;
+  if (nrec > 0 && prefetch_bytes > 0) {
+    pf_end = size_t(rec_off16[r0 + nrec - 1]) * 16 + rec_bytes[r0 + nrec - 1];
+    pf = size_t(rec_off16[r0]) * 16;
+  }
+  for (int j = 0; j < nrec; ++j) {
+    if ((j & 31) == 0 && j + lane < nrec) {
+      my_off = rec_off16[r0 + j + lane];
+      my_nb = rec_bytes[r0 + j + lane];
+    }
+    const uint32_t off16 = __shfl_sync(0xffffffffu, my_off, j & 31);
+    const uint32_t nb = __shfl_sync(0xffffffffu, my_nb, j & 31);
+    const int st = j % S;
+    int stop = 0;
+    if (lane == 0) {
+      if (j >= S && !mbar_wait_bounded(&empty[st], ((j / S) - 1) & 1, wait_cycles)) {
+        atomicOr(err, 1);    // the consumers stopped (their own wait ran out)
+        stop = 1;
+      } else if (!(stall_test && j == 1)) {
+        // (failure test: record 1 is never copied, so the consumers' wait
+        // for it runs out; its `full` barrier is a flag that nothing sets)
+        fence_proxy_async_smem();
+        mbar_expect_tx(&full[st], nb);
+        bulk_g2s(stages + size_t(st) * stage_bytes, stream + size_t(off16) * 16, nb, &full[st]);
+        last[st] = j;
+      }
+      if (prefetch_bytes > 0 && !stop) {
+        // records up to `prefetch_bytes` past this pack, in pieces of at
+        // most 16 KB, start their way into L2 (16-byte aligned: records are)
+        const size_t here = size_t(off16) * 16 + nb;
+        if (pf < here) pf = here;
+        const size_t want = here + size_t(prefetch_bytes) < pf_end ? here + size_t(prefetch_bytes) : pf_end;
+        while (pf < want) {
+          const size_t piece = want - pf < 16384 ? want - pf : 16384;
+          bulk_prefetch_l2(stream + pf, static_cast<unsigned>(piece));
+          pf += piece;
+        }
+      }
+    }
+    if (__shfl_sync(0xffffffffu, stop, 0)) break;
+  }
+  if (lane != 0) return;
+  // every copy issued has landed before the CTA's shared memory can go away
+  // (waited for with at least the default bound, however short the caller's)
+  const long long drain = wait_cycles > kDefaultWaitCycles ? wait_cycles : kDefaultWaitCycles;
+#pragma unroll
+  for (int st = 0; st < S; ++st)
+    if (last[st] >= 0) mbar_wait_bounded(&full[st], (last[st] / S) & 1, drain);
+  if (cnt > 0) mbar_wait_bounded(gbar, 0, drain);
+}
+
 // z_s = (L U)^-1 r_s for every subdomain s (one CTA each), level by level.
 // The producer warp copies the level records of subdomain s, several small
 // consecutive ones packed into one bulk copy, into a ring of S stages
@@ -315,68 +424,52 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
                                                              const uint8_t* __restrict__ stream, int stage_bytes,
                                                              T* __restrict__ zloc,
                                                              const KrylovScalars* __restrict__ ks, int* err,
-                                                             long long wait_cycles, int grp, int stall_test) {
+                                                             long long wait_cycles, int grp, int stall_test,
+                                                             int prefetch_bytes, BatchGate gate) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[S];
   __shared__ __align__(8) uint64_t empty[S];
+  __shared__ __align__(8) uint64_t gbar;    // the staged overlap indices have landed
   if (ks != nullptr && ks->done) return;
   const int s = blockIdx.x;
+  if (gate_sub_off(gate, s)) return;
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
   const int r0 = rec_ptr[s], nrec = rec_ptr[s + 1] - r0;
   unsigned char* stages = smem_raw;
-  T* v = reinterpret_cast<T*>(smem_raw + size_t(S) * stage_bytes);
+  unsigned char* vreg = smem_raw + size_t(S) * stage_bytes;
+  // the overlap indices om_dofs[base - off, base - off + cnt) arrive by one
+  // bulk copy (16-byte aligned source and size); position i's index is then
+  // word off + i of the staged slice
+  const int off = base & 3;
+  const int cnt = m > 0 ? (off + m + 3) & ~3 : 0;
+  const int m4 = (m + 3) & ~3;
+  unsigned char* idx_dst = sizeof(T) == 4 ? vreg : vreg + size_t(4) * m4;
+  const int* idx = reinterpret_cast<const int*>(idx_dst) + off;
+  T* v = sizeof(T) == 4 ? reinterpret_cast<T*>(vreg) + off : reinterpret_cast<T*>(vreg);
   const int nt = blockDim.x - 32;            // consumer threads
   if (threadIdx.x == 0) {
     for (int j = 0; j < S; ++j) {
       mbar_init(&full[j], 1);
       mbar_init(&empty[j], nt / 32);         // one arrival per consumer warp
     }
+    mbar_init(&gbar, 1);
     fence_mbar_init();
   }
   __syncthreads();
   if (int(threadIdx.x) >= nt) {
-    // ---- producer warp: the lanes fetch the record offsets and sizes 32 at a
-    // time, lane 0 waits for free stages and issues the copies ----
-    const int lane = threadIdx.x & 31;
-    int last[S];
-#pragma unroll
-    for (int j = 0; j < S; ++j) last[j] = -1;
-    uint32_t my_off = 0, my_nb = 0;
-    for (int j = 0; j < nrec; ++j) {
-      if ((j & 31) == 0 && j + lane < nrec) {
-        my_off = rec_off16[r0 + j + lane];
-        my_nb = rec_bytes[r0 + j + lane];
-      }
-      const uint32_t off16 = __shfl_sync(0xffffffffu, my_off, j & 31);
-      const uint32_t nb = __shfl_sync(0xffffffffu, my_nb, j & 31);
-      const int st = j % S;
-      int stop = 0;
-      if (lane == 0) {
-        if (j >= S && !mbar_wait_bounded(&empty[st], ((j / S) - 1) & 1, wait_cycles)) {
-          atomicOr(err, 1);    // the consumers stopped (their own wait ran out)
-          stop = 1;
-        } else if (!(stall_test && j == 1)) {
-          // (failure test: record 1 is never copied, so the consumers' wait
-          // for it runs out; its `full` barrier is a flag that nothing sets)
-          fence_proxy_async_smem();
-          mbar_expect_tx(&full[st], nb);
-          bulk_g2s(stages + size_t(st) * stage_bytes, stream + size_t(off16) * 16, nb, &full[st]);
-          last[st] = j;
-        }
-      }
-      if (__shfl_sync(0xffffffffu, stop, 0)) break;
-    }
-    if (lane != 0) return;
-    // every copy issued has landed before the CTA's shared memory can go away
-    // (waited for with at least the default bound, however short the caller's)
-    const long long drain = wait_cycles > kDefaultWaitCycles ? wait_cycles : kDefaultWaitCycles;
-#pragma unroll
-    for (int st = 0; st < S; ++st)
-      if (last[st] >= 0) mbar_wait_bounded(&full[st], (last[st] / S) & 1, drain);
+    pipe_producer<S>(om_dofs, base - off, cnt, idx_dst, &gbar, rec_off16, rec_bytes, r0, nrec, stream, stages,
+                     stage_bytes, full, empty, err, wait_cycles, stall_test, prefetch_bytes);
     return;
   }
   // ---- consumer warps ----
-  gather_sub(r, om_dofs, base, m, v, threadIdx.x, nt);
+  {
+    const bool ok = m == 0 || mbar_wait_bounded(&gbar, 0, wait_cycles);
+    if (consumers_sync_or(!ok, nt)) {
+      if (threadIdx.x == 0) atomicOr(err, 1);
+      return;
+    }
+  }
+  gather_staged(r, idx, v, m, nt);
   consumers_sync_or(false, nt);
   for (int i = 0; i < nrec; ++i) {
     const int st = i % S;
@@ -389,21 +482,247 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
       return;
     }
     // the stage holds a pack of consecutive level records (their count in the
-    // first header, each record's size in its own); one barrier per level
+    // first header, each record's size in its own); one barrier per level,
+    // after its last record
     const unsigned char* rec = stages + size_t(st) * stage_bytes;
     const int count = reinterpret_cast<const int*>(rec)[7];
     for (int q = 0; q < count; ++q) {
       const unsigned char* next = rec + reinterpret_cast<const int*>(rec)[6];
+      const bool level_end = (reinterpret_cast<const int*>(rec)[5] & kRecLevelEnd) != 0;
       level_rows<T, TS, TPR>(rec, v, nt, grp);
       // each warp releases the stage as soon as its lanes are done reading it
       if (q + 1 == count) {
         __syncwarp();
         if ((threadIdx.x & 31) == 0 && i + S < nrec) mbar_arrive(&empty[st]);
       }
-      consumers_sync_or(false, nt);
+      if (level_end) consumers_sync_or(false, nt);
       rec = next;
     }
   }
+  for (int i = threadIdx.x; i < m; i += nt) zloc[base + i] = v[i];
+}
+
+// ---- level-scheduled solve without a barrier per level ----
+//
+// The same records and producer as k_local_pipe, but the consumers meet at no
+// barrier between levels: every row waits only for the rows it reads.  A byte
+// per local row (in shared memory) says how far that row's value has got: 0
+// the right-hand side, 1 final after the L sweep, 2 final after the U sweep.
+// A row of sweep `phase` spins until every column it reads is flagged
+// `phase`, updates its value, fences (CTA scope) and sets its own flag.  Each
+// thread takes its rows in record order, and a row reads only rows of earlier
+// records, so the earliest unfinished row can always proceed.  One barrier
+// separates the two sweeps (the U sweep overwrites values the L sweep reads).
+// Every spin is bounded; a wait that runs out sets the CTA's failure flag and
+// err[0], after which every thread skips the remaining work but still meets
+// the two barriers, and z_s is not written.
+
+__device__ __forceinline__ void fence_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
+
+// Barrier of the `nt` consumer threads (named barrier 1), not .aligned: the
+// threads of a warp may arrive from different places (a thread whose wait ran
+// out meets the sweep barrier at the end of its loop).
+__device__ __forceinline__ void consumers_sync(int nt) {
+  asm volatile("barrier.cta.sync 1, %0;" ::"r"(nt) : "memory");
+}
+
+// Spins until flags[c] >= phase; false when `cycles` pass first or the CTA
+// has failed.
+__device__ __forceinline__ bool wait_row(const volatile unsigned char* flags, int c, int phase,
+                                         long long cycles, const volatile int* fail) {
+  if (flags[c] >= phase) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (flags[c] >= phase) return true;
+    if (*fail) return false;
+    if (clock64() - t0 > cycles) return false;
+  }
+}
+
+// The rows of one level record for sweep `phase`; false when a wait ran out.
+template <class T, class TS>
+__device__ __forceinline__ bool sf_record(const unsigned char* rec, T* v, unsigned char* flags, int phase, int nt,
+                                          int G, long long cycles, const volatile int* fail) {
+  const int4 hdr = *reinterpret_cast<const int4*>(rec);
+  const int4 hdr1 = *reinterpret_cast<const int4*>(rec + 16);
+  const int nr = hdr.x, K = hdr.y;
+  const int layout = hdr1.y & 0xff;
+  const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 32);
+  const TS* dinv = reinterpret_cast<const TS*>(rec + 32 + ((2 * nr + 15) & ~15));
+  const TS* vals = reinterpret_cast<const TS*>(rec + hdr.z);
+  const uint16_t* cols = reinterpret_cast<const uint16_t*>(rec + hdr.w);
+  const TS* inn = reinterpret_cast<const TS*>(rec + hdr1.x);
+  volatile unsigned char* vf = flags;
+  if (layout == 1) {
+    for (int t = threadIdx.x; t < nr; t += nt) {
+      const int row = lrows[t];
+      const ushort4 c4 = reinterpret_cast<const ushort4*>(cols)[t];
+      // padding entries point at the row itself (value 0): nothing to wait for
+      if ((c4.x != row && !wait_row(vf, c4.x, phase, cycles, fail)) ||
+          (c4.y != row && !wait_row(vf, c4.y, phase, cycles, fail)) ||
+          (c4.z != row && !wait_row(vf, c4.z, phase, cycles, fail)) ||
+          (c4.w != row && !wait_row(vf, c4.w, phase, cycles, fail)))
+        return false;
+      fence_cta();
+      T a[4];
+      load4<T, TS>(vals, t, a);
+      T acc = v[row];
+      acc = fma(-a[0], v[c4.x], acc);
+      acc = fma(-a[1], v[c4.y], acc);
+      acc = fma(-a[2], v[c4.z], acc);
+      acc = fma(-a[3], v[c4.w], acc);
+      v[row] = acc * load_as<T, TS>(dinv, t);
+      fence_cta();
+      vf[row] = static_cast<unsigned char>(phase);
+    }
+  } else if (layout == 0) {
+    for (int t = threadIdx.x; t < nr; t += nt) {
+      const int row = lrows[t];
+      for (int k = 0; k < K; ++k) {
+        const int c = cols[k * nr + t];
+        if (c != row && !wait_row(vf, c, phase, cycles, fail)) return false;
+      }
+      fence_cta();
+      T acc = v[row];
+      for (int k = 0; k < K; ++k) acc = fma(-load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], acc);
+      v[row] = acc * load_as<T, TS>(dinv, t);
+      fence_cta();
+      vf[row] = static_cast<unsigned char>(phase);
+    }
+  } else {
+    // by node: the G rows' couplings to other nodes (padding points at the
+    // row itself), then the in-node triangle in order by this thread
+    const int ngr = nr / G;
+    for (int gt = threadIdx.x; gt < ngr; gt += nt) {
+      for (int d = 0; d < G; ++d) {
+        const int t = gt * G + d;
+        const int row = lrows[t];
+        for (int k = 0; k < K; ++k) {
+          const int c = cols[k * nr + t];
+          if (c != row && !wait_row(vf, c, phase, cycles, fail)) return false;
+        }
+      }
+      fence_cta();
+      T y[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        if (d < G) {
+          const int t = gt * G + d;
+          const int row = lrows[t];
+          T part = T(0);
+          for (int k = 0; k < K; ++k) part = fma(load_as<T, TS>(vals, k * nr + t), v[cols[k * nr + t]], part);
+          T acc = v[row] - part;
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            if (q < d) acc = fma(-load_as<T, TS>(inn, t * (G - 1) + q), y[q], acc);
+          y[d] = acc * load_as<T, TS>(dinv, t);
+          v[row] = y[d];
+        }
+      }
+      fence_cta();
+      for (int d = 0; d < G; ++d) vf[lrows[gt * G + d]] = static_cast<unsigned char>(phase);
+    }
+  }
+  return true;
+}
+
+// Shared memory of the per-row flags (one byte per local row, 16-byte padded).
+inline size_t sf_flag_bytes(int max_m) { return (size_t(max_m) + 15) & ~size_t(15); }
+
+template <class T, class TS, int S>
+__global__ void __launch_bounds__(kPipeMaxThreads) k_local_sf(const double* __restrict__ r,
+                                                           const int* __restrict__ om_ptr,
+                                                           const int* __restrict__ om_dofs,
+                                                           const int* __restrict__ rec_ptr,
+                                                           const uint32_t* __restrict__ rec_off16,
+                                                           const uint32_t* __restrict__ rec_bytes,
+                                                           const uint8_t* __restrict__ stream, int stage_bytes,
+                                                           int vec_bytes, T* __restrict__ zloc,
+                                                           const KrylovScalars* __restrict__ ks, int* err,
+                                                           long long wait_cycles, int grp, int stall_test,
+                                                           int prefetch_bytes, BatchGate gate) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[S];
+  __shared__ __align__(8) uint64_t empty[S];
+  __shared__ __align__(8) uint64_t gbar;
+  __shared__ int s_fail;
+  if (ks != nullptr && ks->done) return;
+  const int s = blockIdx.x;
+  if (gate_sub_off(gate, s)) return;
+  const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+  const int r0 = rec_ptr[s], nrec = rec_ptr[s + 1] - r0;
+  unsigned char* stages = smem_raw;
+  unsigned char* vreg = smem_raw + size_t(S) * stage_bytes;
+  unsigned char* flags = vreg + vec_bytes;
+  const int off = base & 3;
+  const int cnt = m > 0 ? (off + m + 3) & ~3 : 0;
+  const int m4 = (m + 3) & ~3;
+  unsigned char* idx_dst = sizeof(T) == 4 ? vreg : vreg + size_t(4) * m4;
+  const int* idx = reinterpret_cast<const int*>(idx_dst) + off;
+  T* v = sizeof(T) == 4 ? reinterpret_cast<T*>(vreg) + off : reinterpret_cast<T*>(vreg);
+  const int nt = blockDim.x - 32;            // consumer threads
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < S; ++j) {
+      mbar_init(&full[j], 1);
+      mbar_init(&empty[j], nt / 32);
+    }
+    mbar_init(&gbar, 1);
+    s_fail = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (int(threadIdx.x) >= nt) {
+    pipe_producer<S>(om_dofs, base - off, cnt, idx_dst, &gbar, rec_off16, rec_bytes, r0, nrec, stream, stages,
+                     stage_bytes, full, empty, err, wait_cycles, stall_test, prefetch_bytes);
+    return;
+  }
+  volatile int* fail = &s_fail;
+  auto set_fail = [&]() {
+    if (!*fail) {
+      *fail = 1;
+      atomicOr(err, 1);
+    }
+  };
+  // ---- consumer warps: indices, gather, flags cleared ----
+  {
+    const bool ok = m == 0 || mbar_wait_bounded(&gbar, 0, wait_cycles);
+    if (consumers_sync_or(!ok, nt)) {
+      if (threadIdx.x == 0) atomicOr(err, 1);
+      return;
+    }
+  }
+  gather_staged(r, idx, v, m, nt);
+  for (int i = threadIdx.x; i < m; i += nt) flags[i] = 0;
+  consumers_sync_or(false, nt);
+  int phase = 1;
+  bool switched = false;          // met the barrier between the sweeps
+  for (int i = 0; i < nrec; ++i) {
+    const int st = i % S;
+    bool ok = !*fail && mbar_wait_bounded(&full[st], (i / S) & 1, wait_cycles);
+    if (!ok) set_fail();
+    if (ok) {
+      const unsigned char* rec = stages + size_t(st) * stage_bytes;
+      const int count = reinterpret_cast<const int*>(rec)[7];
+      for (int q = 0; q < count && ok; ++q) {
+        const unsigned char* next = rec + reinterpret_cast<const int*>(rec)[6];
+        if ((reinterpret_cast<const int*>(rec)[5] & kRecUpper) && !switched) {
+          consumers_sync(nt);              // the L sweep is complete
+          switched = true;
+          phase = 2;
+        }
+        ok = sf_record<T, TS>(rec, v, flags, phase, nt, grp, wait_cycles, fail);
+        if (!ok) set_fail();
+        rec = next;
+      }
+    }
+    // the warp releases the stage once all its lanes are done with it (never
+    // after a failure: the producer then stops on its own bounded wait)
+    const bool warp_ok = __all_sync(0xffffffffu, ok);
+    if (warp_ok && (threadIdx.x & 31) == 0 && i + S < nrec) mbar_arrive(&empty[st]);
+  }
+  if (!switched) consumers_sync(nt);
+  consumers_sync(nt);
+  if (*fail) return;
   for (int i = threadIdx.x; i < m; i += nt) zloc[base + i] = v[i];
 }
 
@@ -416,11 +735,12 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
                                                      const T* __restrict__ ainv,
                                                      const int64_t* __restrict__ ainv_off,
                                                      T* __restrict__ zloc,
-                                                     const KrylovScalars* __restrict__ ks) {
+                                                     const KrylovScalars* __restrict__ ks, BatchGate gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (ks != nullptr && ks->done) return;
   T* rs = reinterpret_cast<T*>(smem_raw);
   const int s = blockIdx.y;
+  if (gate_sub_off(gate, s)) return;
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
   const int row0 = blockIdx.x * 32;
   if (row0 >= m) return;
@@ -507,7 +827,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
                                               const int* __restrict__ chunk_r1,
                                               const int* __restrict__ chunk_slot,
                                               double* __restrict__ partial,
-                                              const KrylovScalars* __restrict__ ks) {
+                                              const KrylovScalars* __restrict__ ks, BatchGate gate) {
   __shared__ T rs[kPhiChunkRows];          // r of a chunk
   if (ks != nullptr && ks->done) return;
   // the small chunks' CTAs come first in the grid, so that their longer
@@ -516,13 +836,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
   if (int(blockIdx.x) < n_warp_ctas) {
     // warp path: no CTA-wide barrier below
     const int q = n_cta + int(blockIdx.x) * 8 + (threadIdx.x >> 5);
-    if (q < n_chunks)
+    if (q < n_chunks && !gate_blk_off(gate, chunk_blk[q]))
       phiT_warp_chunk<T>(q, r, brow_ptr, brow_dof, bcol_ptr, phi_off, phi, chunk_blk, chunk_r0, chunk_r1,
                          chunk_slot, partial);
     return;
   }
   const int q = int(blockIdx.x) - n_warp_ctas;
   const int b = chunk_blk[q];
+  if (gate_blk_off(gate, b)) return;
   const int p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
   const int i0 = chunk_r0[q], rows = chunk_r1[q] - i0;
   const int k = bcol_ptr[b + 1] - bcol_ptr[b];
@@ -554,9 +875,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
 
 __global__ void k_coarse_c(int n0, const int* __restrict__ cs_ptr, const int* __restrict__ cs_idx,
                            const double* __restrict__ partial, double* __restrict__ c,
-                           const KrylovScalars* __restrict__ ks) {
+                           const KrylovScalars* __restrict__ ks, BatchGate gate) {
   if (ks != nullptr && ks->done) return;
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n0; l += gridDim.x * blockDim.x) {
+    if (gate_col_off(gate, l)) continue;
     double v = 0.0;
     for (int q = cs_ptr[l]; q < cs_ptr[l + 1]; ++q) v += partial[cs_idx[q]];
     c[l] = v;
@@ -575,7 +897,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
                                                      const int64_t* __restrict__ a0_off,
                                                      const double* __restrict__ c,
                                                      double* __restrict__ y, float* __restrict__ y32,
-                                                     const KrylovScalars* __restrict__ ks) {
+                                                     const KrylovScalars* __restrict__ ks, BatchGate gate) {
   __shared__ double half_sum[4][2];
   if (ks != nullptr && ks->done) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -583,7 +905,8 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
   for (int row0 = blockIdx.x * 4; row0 < n0; row0 += gridDim.x * 4) {
     const int row = row0 + slot;
     double acc = 0.0;
-    if (row < n0) {
+    const bool live = row < n0 && !gate_col_off(gate, row);
+    if (live) {
       const int pr = coarse_prob[row];
       const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;
       const double* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
@@ -608,7 +931,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
     }
     if (lane == 0) half_sum[slot][h] = acc;
     __syncthreads();
-    if (h == 0 && lane == 0 && row < n0) {
+    if (h == 0 && lane == 0 && live) {
       const double v = half_sum[slot][0] + half_sum[slot][1];
       y[row] = v;
       if (y32 != nullptr) y32[row] = float(v);   // converted once, not per scatter position
@@ -654,7 +977,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_combine(
     const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
     const int64_t* __restrict__ phi_off, const T* __restrict__ phi, const T* __restrict__ y,
     const int* __restrict__ pull_ptr, const int* __restrict__ pull_pos, const T* __restrict__ zloc,
-    int dots, double* __restrict__ red, KrylovScalars* ks) {
+    int dots, double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
   double d_new = 0.0, d_old = 0.0;
@@ -666,9 +989,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_combine(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int pj = p + j * stride;
-      g[j] = pj < n ? brow_dof[pj] : -1;
-      a[j] = pj < n ? combine_one(pj, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc)
-                    : 0.0;
+      const bool live = pj < n && !gate_blk_off(gate, pos_blk[pj]);
+      g[j] = live ? brow_dof[pj] : -1;
+      a[j] = live ? combine_one(pj, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc)
+                  : 0.0;
     }
     if (dots) {
 #pragma unroll
@@ -723,16 +1047,42 @@ EllDev<T> ell(const Ctx* c, bool lower) {
 }
 
 template <class T>
-gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
+gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks, const BatchGate& gate) {
   T* zl = static_cast<T*>(c->zloc);
   if (c->mf) return mf_launch_local(c, r, s, ks);
   if (c->opt.local_solver == GDSW_LOCAL_EXACT) {
     const size_t shm = size_t(c->max_m) * sizeof(T);
     dim3 grid((c->max_m + 31) / 32, c->nsub);
     k_local_dense<T><<<grid, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
-                                            c->ainv_off, zl, ks);
+                                            c->ainv_off, zl, ks, gate);
+  } else if (c->rec_stages > 0 && c->rec_sf) {
+    // without a barrier per level (one unknown per row group of at most 4, rows of up to 8 entries)
+    const int vb = static_cast<int>(pipe_vector_bytes(c->max_m, sizeof(T)));
+    const size_t shm = size_t(c->rec_stages) * c->rec_stage_bytes + vb + sf_flag_bytes(c->max_m);
+#define GDSW_SF_LAUNCH(TS, SS)                                                                             \
+  k_local_sf<T, TS, SS><<<c->nsub, c->rec_consumers + 32, shm, s>>>(                                      \
+      r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, c->rec_bytes, c->rec_stream, c->rec_stage_bytes, \
+      vb, zl, ks, c->derr, c->wait_cycles, c->dpn, c->stall_test, c->rec_prefetch, gate)
+    if (c->fp16) {
+      if constexpr (std::is_same<T, float>::value) {
+        switch (c->rec_stages) {
+          case 2: GDSW_SF_LAUNCH(__half, 2); break;
+          case 4: GDSW_SF_LAUNCH(__half, 4); break;
+          case 8: GDSW_SF_LAUNCH(__half, 8); break;
+          default: GDSW_SF_LAUNCH(__half, 16); break;
+        }
+      }
+    } else {
+      switch (c->rec_stages) {
+        case 2: GDSW_SF_LAUNCH(T, 2); break;
+        case 4: GDSW_SF_LAUNCH(T, 4); break;
+        case 8: GDSW_SF_LAUNCH(T, 8); break;
+        default: GDSW_SF_LAUNCH(T, 16); break;
+      }
+    }
+#undef GDSW_SF_LAUNCH
   } else if (c->rec_stages > 0) {
-    const size_t shm = size_t(c->rec_stages) * c->rec_stage_bytes + size_t(c->max_m) * sizeof(T);
+    const size_t shm = size_t(c->rec_stages) * c->rec_stage_bytes + pipe_vector_bytes(c->max_m, sizeof(T));
     const int key = c->rec_stages * 100 + c->rec_tpr;
     if (c->fp16) {
       if constexpr (std::is_same<T, float>::value) {
@@ -740,16 +1090,17 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
   k_local_pipe<T, __half, SS, TP><<<c->nsub, c->rec_consumers + 32, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr,            \
                                                             c->rec_off16, c->rec_bytes, c->rec_stream,       \
                                                             c->rec_stage_bytes, zl, ks, c->derr,             \
-                                                            c->wait_cycles, c->dpn, c->stall_test)
+                                                            c->wait_cycles, c->dpn, c->stall_test,           \
+                                                            c->rec_prefetch, gate)
         switch (key) {
           case 201: GDSW_PIPE_LAUNCH(2, 1); break;
-          case 301: GDSW_PIPE_LAUNCH(3, 1); break;
           case 401: GDSW_PIPE_LAUNCH(4, 1); break;
-          case 601: GDSW_PIPE_LAUNCH(6, 1); break;
+          case 801: GDSW_PIPE_LAUNCH(8, 1); break;
+          case 1601: GDSW_PIPE_LAUNCH(16, 1); break;
           case 208: GDSW_PIPE_LAUNCH(2, 8); break;
-          case 308: GDSW_PIPE_LAUNCH(3, 8); break;
           case 408: GDSW_PIPE_LAUNCH(4, 8); break;
-          default: GDSW_PIPE_LAUNCH(6, 8); break;
+          case 808: GDSW_PIPE_LAUNCH(8, 8); break;
+          default: GDSW_PIPE_LAUNCH(16, 8); break;
         }
 #undef GDSW_PIPE_LAUNCH
       }
@@ -757,16 +1108,17 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
 #define GDSW_PIPE_LAUNCH(SS, TP)                                                                     \
   k_local_pipe<T, T, SS, TP><<<c->nsub, c->rec_consumers + 32, shm, s>>>(r, c->om_ptr, c->om_dofs, c->rec_ptr, c->rec_off16, \
                                                        c->rec_bytes, c->rec_stream, c->rec_stage_bytes, zl, \
-                                                       ks, c->derr, c->wait_cycles, c->dpn, c->stall_test)
+                                                       ks, c->derr, c->wait_cycles, c->dpn, c->stall_test,  \
+                                                       c->rec_prefetch, gate)
       switch (key) {
         case 201: GDSW_PIPE_LAUNCH(2, 1); break;
-        case 301: GDSW_PIPE_LAUNCH(3, 1); break;
         case 401: GDSW_PIPE_LAUNCH(4, 1); break;
-        case 601: GDSW_PIPE_LAUNCH(6, 1); break;
+        case 801: GDSW_PIPE_LAUNCH(8, 1); break;
+        case 1601: GDSW_PIPE_LAUNCH(16, 1); break;
         case 208: GDSW_PIPE_LAUNCH(2, 8); break;
-        case 308: GDSW_PIPE_LAUNCH(3, 8); break;
         case 408: GDSW_PIPE_LAUNCH(4, 8); break;
-        default: GDSW_PIPE_LAUNCH(6, 8); break;
+        case 808: GDSW_PIPE_LAUNCH(8, 8); break;
+        default: GDSW_PIPE_LAUNCH(16, 8); break;
       }
     }
 #undef GDSW_PIPE_LAUNCH
@@ -774,44 +1126,45 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
     const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
     const size_t shm = size_t(c->max_m) * sizeof(T) * (jac ? 3 : 1);
     k_local_tri<T><<<c->nsub, c->tri_threads, shm, s>>>(r, c->om_ptr, c->om_dofs, ell<T>(c, true),
-                                             ell<T>(c, false), jac, c->opt.sweeps_trsv, zl, ks);
+                                             ell<T>(c, false), jac, c->opt.sweeps_trsv, zl, ks, gate);
   }
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
 
 template <class T>
-gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks) {
+gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovScalars* ks, const BatchGate& gate) {
   if (c->n0 == 0) return GDSW_OK;
   if (c->n_chunks == 0) return GDSW_OK;
   const int grid = c->n_cta_chunks + (c->n_chunks - c->n_cta_chunks + 7) / 8;
   k_phiT<T><<<grid, 256, 0, s>>>(c->n_chunks, c->n_cta_chunks, r, c->brow_ptr, c->brow_dof, c->bcol_ptr,
                                  c->phi_off,
                                         static_cast<const T*>(c->phi), c->chunk_blk, c->chunk_r0,
-                                        c->chunk_r1, c->chunk_slot, c->partial, ks);
+                                        c->chunk_r1, c->chunk_slot, c->partial, ks, gate);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
 
-gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks) {
+gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const BatchGate& gate) {
   if (c->n0 == 0) return GDSW_OK;
-  k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, ks);
+  k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, ks, gate);
   const int grid = std::min((c->n0 + 3) / 4, kNumSMs * 8);
 
   k_coarse_gemv<<<grid, 256, 0, s>>>(c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, c->cvec, c->yvec,
-                                      c->yvec32, ks);
+                                      c->yvec32, ks, gate);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
 
 template <class T>
-gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated) {
+gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated,
+                           const BatchGate& gate) {
   const int grid = std::max(1, std::min(c->combine_grid, (c->n + 255) / 256));
   k_combine<T><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
                                     c->bcol, c->phi_off, static_cast<const T*>(c->phi),
                                     c->fp32 ? reinterpret_cast<const T*>(c->yvec32) : reinterpret_cast<const T*>(c->yvec),
                                     c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),
-                                    dots ? (c->flexible ? 2 : 1) : 0, c->red, (dots || gated) ? c->ks : nullptr);
+                                    dots ? (c->flexible ? 2 : 1) : 0, c->red, (dots || gated) ? c->ks : nullptr, gate);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -819,30 +1172,32 @@ gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, b
 // dots: the PCG form (z, (r, z) and beta into the Krylov scalars); gated:
 // every kernel returns at once when the Krylov loop has set its stop flag.
 template <class T>
-gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated, cudaEvent_t* ev) {
+gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated, cudaEvent_t* ev,
+                    bool batch = false) {
   const KrylovScalars* ks = (dots || gated) ? c->ks : nullptr;
+  const BatchGate gate = batch ? batch_gate(c) : BatchGate{};
   if (ev == nullptr && c->n0 > 0 && c->aux_stream != nullptr) {
     // The one-level and coarse branches of Eq. 1 are independent until the
     // final sum: the coarse branch (Phi^T r, c, A0^-1 c) runs on a second
     // stream beside the local solves and joins before the scatter-add.
     GDSW_CK(cudaEventRecord(c->ev_fork, s));
     GDSW_CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
-    GDSW_TRY(launch_phiT<T>(c, r, c->aux_stream, ks));
-    GDSW_TRY(launch_coarse(c, c->aux_stream, ks));
+    GDSW_TRY(launch_phiT<T>(c, r, c->aux_stream, ks, gate));
+    GDSW_TRY(launch_coarse(c, c->aux_stream, ks, gate));
     GDSW_CK(cudaEventRecord(c->ev_join, c->aux_stream));
-    GDSW_TRY(launch_local<T>(c, r, s, ks));
+    GDSW_TRY(launch_local<T>(c, r, s, ks, gate));
     GDSW_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
-    GDSW_TRY(launch_combine<T>(c, r, z, s, dots, gated));
+    GDSW_TRY(launch_combine<T>(c, r, z, s, dots, gated, gate));
     return GDSW_OK;
   }
   if (ev) GDSW_CK(cudaEventRecord(ev[0], s));
-  GDSW_TRY(launch_local<T>(c, r, s, ks));
+  GDSW_TRY(launch_local<T>(c, r, s, ks, gate));
   if (ev) GDSW_CK(cudaEventRecord(ev[1], s));
-  GDSW_TRY(launch_phiT<T>(c, r, s, ks));
+  GDSW_TRY(launch_phiT<T>(c, r, s, ks, gate));
   if (ev) GDSW_CK(cudaEventRecord(ev[2], s));
-  GDSW_TRY(launch_coarse(c, s, ks));
+  GDSW_TRY(launch_coarse(c, s, ks, gate));
   if (ev) GDSW_CK(cudaEventRecord(ev[3], s));
-  GDSW_TRY(launch_combine<T>(c, r, z, s, dots, gated));
+  GDSW_TRY(launch_combine<T>(c, r, z, s, dots, gated, gate));
   if (ev) GDSW_CK(cudaEventRecord(ev[4], s));
   return GDSW_OK;
 }
@@ -853,7 +1208,7 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
 // ring depth S and dynamic shared memory (0 when it does not fit).  Raises the
 // kernel's dynamic shared memory limit first.
 template <class TT, class TS, int TP>
-gdsw_status pipe_occupancy_t(int S, size_t shm, int threads, int* per_sm) {
+gdsw_status pipe_occupancy_t(int S, bool sf, size_t shm, int threads, int* per_sm) {
   *per_sm = 0;
   auto one = [&](auto kernel) -> gdsw_status {
     GDSW_CK(allow_max_dynamic_smem(kernel));
@@ -863,23 +1218,39 @@ gdsw_status pipe_occupancy_t(int S, size_t shm, int threads, int* per_sm) {
     GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, shm));
     return GDSW_OK;
   };
+  if (sf) {
+    switch (S) {
+      case 2: return one(k_local_sf<TT, TS, 2>);
+      case 4: return one(k_local_sf<TT, TS, 4>);
+      case 8: return one(k_local_sf<TT, TS, 8>);
+      default: return one(k_local_sf<TT, TS, 16>);
+    }
+  }
   switch (S) {
     case 2: return one(k_local_pipe<TT, TS, 2, TP>);
-    case 3: return one(k_local_pipe<TT, TS, 3, TP>);
     case 4: return one(k_local_pipe<TT, TS, 4, TP>);
-    default: return one(k_local_pipe<TT, TS, 6, TP>);
+    case 8: return one(k_local_pipe<TT, TS, 8, TP>);
+    default: return one(k_local_pipe<TT, TS, 16, TP>);
   }
 }
 
-gdsw_status pipe_occupancy(const Ctx* c, int S, size_t shm, int* per_sm) {
+// Dynamic shared memory of the pipelined local solve with ring depth S.
+size_t pipe_smem(const Ctx* c, int S, bool sf) {
+  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  return size_t(S) * c->rec_stage_bytes + pipe_vector_bytes(c->max_m, es) + (sf ? sf_flag_bytes(c->max_m) : 0);
+}
+
+gdsw_status pipe_occupancy(const Ctx* c, int S, bool sf, int* per_sm) {
+  const size_t shm = pipe_smem(c, S, sf);
+  const int th = c->rec_consumers + 32;
   if (c->fp16)
-    return c->rec_tpr == 8 ? pipe_occupancy_t<float, __half, 8>(S, shm, c->rec_consumers + 32, per_sm)
-                           : pipe_occupancy_t<float, __half, 1>(S, shm, c->rec_consumers + 32, per_sm);
+    return c->rec_tpr == 8 ? pipe_occupancy_t<float, __half, 8>(S, sf, shm, th, per_sm)
+                           : pipe_occupancy_t<float, __half, 1>(S, sf, shm, th, per_sm);
   if (c->fp32)
-    return c->rec_tpr == 8 ? pipe_occupancy_t<float, float, 8>(S, shm, c->rec_consumers + 32, per_sm)
-                           : pipe_occupancy_t<float, float, 1>(S, shm, c->rec_consumers + 32, per_sm);
-  return c->rec_tpr == 8 ? pipe_occupancy_t<double, double, 8>(S, shm, c->rec_consumers + 32, per_sm)
-                         : pipe_occupancy_t<double, double, 1>(S, shm, c->rec_consumers + 32, per_sm);
+    return c->rec_tpr == 8 ? pipe_occupancy_t<float, float, 8>(S, sf, shm, th, per_sm)
+                           : pipe_occupancy_t<float, float, 1>(S, sf, shm, th, per_sm);
+  return c->rec_tpr == 8 ? pipe_occupancy_t<double, double, 8>(S, sf, shm, th, per_sm)
+                         : pipe_occupancy_t<double, double, 1>(S, sf, shm, th, per_sm);
 }
 
 // Measured choice of the pipelined local solve's shape: every ring depth that
@@ -907,30 +1278,35 @@ gdsw_status tune_local(Ctx* c) {
   const int keep_s = c->rec_stages, keep_nt = c->rec_consumers;
   float best = 3.4e38f;
   int best_s = keep_s, best_nt = keep_nt;
-  const int cand[4] = {6, 4, 3, 2};
+  bool best_sf = false;
+  const int cand[4] = {16, 8, 4, 2};
+  // the barrier-free kernel takes rows of up to 8 entries (one thread per row)
+  const int n_kinds = c->rec_tpr == 1 ? 2 : 1;
+  for (int kind = 0; kind < n_kinds && st == GDSW_OK; ++kind)
   for (int q = 0; q < 4 && st == GDSW_OK; ++q) {
     for (int nt : {64, 128, 256, 512, 992}) {
       if (c->rec_tpr == 8 && nt < 256) continue;
       c->rec_stages = cand[q];
       c->rec_consumers = nt;
-      const size_t shm = size_t(cand[q]) * c->rec_stage_bytes + size_t(c->max_m) * es;
+      c->rec_sf = kind == 1;
       int per_sm = 0;
-      st = pipe_occupancy(c, cand[q], shm, &per_sm);
+      st = pipe_occupancy(c, cand[q], c->rec_sf, &per_sm);
       if (st != GDSW_OK) break;
       if (per_sm == 0) continue;
-      st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+      st = c->fp32 ? launch_local<float>(c, r, s, nullptr, BatchGate{}) : launch_local<double>(c, r, s, nullptr, BatchGate{});
       if (st != GDSW_OK) break;
       cudaEventRecord(e0, s);
       for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep)
-        st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+        st = c->fp32 ? launch_local<float>(c, r, s, nullptr, BatchGate{}) : launch_local<double>(c, r, s, nullptr, BatchGate{});
       cudaEventRecord(e1, s);
       e = cudaEventSynchronize(e1);
       float ms = 0.f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       if (e != cudaSuccess) { fail(e); break; }
-      if (ms < best) { best = ms; best_s = cand[q]; best_nt = nt; }
+      if (ms < best) { best = ms; best_s = cand[q]; best_nt = nt; best_sf = c->rec_sf; }
     }
   }
+  c->rec_sf = false;
   // the unpipelined level-scheduled kernel (factors read through L2), with
   // 256 to 1024 threads, as further candidates
   int best_tri = c->tri_threads;
@@ -938,10 +1314,10 @@ gdsw_status tune_local(Ctx* c) {
     if (st != GDSW_OK) break;
     c->rec_stages = 0;
     c->tri_threads = tt;
-    st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+    st = c->fp32 ? launch_local<float>(c, r, s, nullptr, BatchGate{}) : launch_local<double>(c, r, s, nullptr, BatchGate{});
     cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep)
-      st = c->fp32 ? launch_local<float>(c, r, s, nullptr) : launch_local<double>(c, r, s, nullptr);
+      st = c->fp32 ? launch_local<float>(c, r, s, nullptr, BatchGate{}) : launch_local<double>(c, r, s, nullptr, BatchGate{});
     cudaEventRecord(e1, s);
     e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -951,6 +1327,7 @@ gdsw_status tune_local(Ctx* c) {
   }
   c->rec_stages = best_s;
   c->rec_consumers = best_nt;
+  c->rec_sf = best_s > 0 && best_sf;
   c->tri_threads = best_s == 0 ? best_tri : 256;
   c->wait_cycles = keep_wait;
   if (r) cudaFree(r);
@@ -980,7 +1357,7 @@ gdsw_status apply_configure(Ctx* c) {
     set_error("subdomain of %d unknowns does not fit the local solve's shared memory", c->max_m);
     return GDSW_ERR_UNSUPPORTED;
   }
-  // pipelined level-scheduled solve: the ring depth (6, 4, 3 or 2 stages)
+  // pipelined level-scheduled solve: the ring depth (16, 8, 4 or 2 stages)
   // that runs all subdomains in the fewest waves of resident CTAs (one CTA per
   // subdomain; the local solve is latency-bound, so a wave that is only partly
   // filled costs as much as a full one), the deepest ring among those
@@ -998,13 +1375,12 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(cudaGetDevice(&dev));
     GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int depth_env = getenv("GDSW_PIPE_STAGES") ? atoi(getenv("GDSW_PIPE_STAGES")) : 0;
-    const int cand[4] = {6, 4, 3, 2};
+    const int cand[4] = {16, 8, 4, 2};
     int64_t best_waves = INT64_MAX;
     for (int q = 0; q < 4; ++q) {
       if (depth_env > 0 && cand[q] != depth_env) continue;
-      const size_t shm = size_t(cand[q]) * c->rec_stage_bytes + size_t(c->max_m) * es;
       int per_sm = 0;
-      GDSW_TRY(pipe_occupancy(c, cand[q], shm, &per_sm));
+      GDSW_TRY(pipe_occupancy(c, cand[q], false, &per_sm));
       if (per_sm == 0) continue;
       const int64_t waves = (int64_t(c->nsub) + int64_t(sms) * per_sm - 1) / (int64_t(sms) * per_sm);
       if (waves < best_waves) {
@@ -1020,21 +1396,34 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(allow_max_dynamic_smem(k_local_tri<double>));
     GDSW_CK(allow_max_dynamic_smem(k_local_dense<double>));
   }
+  // records prefetched into L2 ahead of the ring (bytes per subdomain);
+  // GDSW_PIPE_PREFETCH overrides the default
+  c->rec_prefetch = 0;
+  if (const char* e = getenv("GDSW_PIPE_PREFETCH")) c->rec_prefetch = std::max(0, atoi(e)) & ~15;
   // GDSW_TEST_STALL=1: the failure test of the bounded waits (see k_local_pipe)
   if (const char* e = getenv("GDSW_TEST_STALL")) c->stall_test = e[0] == '1';
-  if (c->rec_stages > 0 && c->opt.autotune && !c->stall_test) {
-    // GDSW_LOCAL_SHAPE="stages,threads" fixes the shape instead of timing it
-    // (for profilers, under which the timings mean nothing)
-    if (const char* e = getenv("GDSW_LOCAL_SHAPE")) {
-      int st = 0, nt = 0;
-      if (sscanf(e, "%d,%d", &st, &nt) == 2 && (st == 0 || st == 2 || st == 3 || st == 4 || st == 6) &&
-          (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 992 || nt == 1024)) {
-        c->rec_stages = st;
-        if (st > 0) c->rec_consumers = nt == 1024 ? 992 : nt; else c->tri_threads = nt == 992 ? 1024 : nt;
+  // GDSW_LOCAL_SHAPE="stages,threads[,barrier_free]" fixes the shape instead
+  // of timing it (for profilers, under which the timings mean nothing, and for
+  // the failure tests); barrier_free 1 selects the solve without a barrier
+  // per level
+  const char* shape = getenv("GDSW_LOCAL_SHAPE");
+  if (c->rec_stages > 0 && shape != nullptr) {
+    int st = 0, nt = 0, sf = 0;
+    const int got = sscanf(shape, "%d,%d,%d", &st, &nt, &sf);
+    if (got >= 2 && (st == 0 || st == 2 || st == 4 || st == 8 || st == 16) &&
+        (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 992 || nt == 1024)) {
+      c->rec_stages = st;
+      if (st > 0) c->rec_consumers = nt == 1024 ? 992 : nt; else c->tri_threads = nt == 992 ? 1024 : nt;
+      c->rec_sf = st > 0 && got == 3 && sf == 1 && c->rec_tpr == 1;
+      int per_sm = 0;
+      if (st > 0) GDSW_TRY(pipe_occupancy(c, st, c->rec_sf, &per_sm));
+      if (st > 0 && per_sm == 0) {
+        set_error("GDSW_LOCAL_SHAPE=%s does not fit the shared memory", shape);
+        return GDSW_ERR_UNSUPPORTED;
       }
-    } else {
-      GDSW_TRY(tune_local(c));
     }
+  } else if (c->rec_stages > 0 && c->opt.autotune && !c->stall_test) {
+    GDSW_TRY(tune_local(c));
   }
   // the scatter-add is a grid-stride loop: exactly the CTAs that are resident at once
   {
@@ -1067,9 +1456,31 @@ gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bo
                  : apply_t<double>(c, r, z, s, rz_dots, false, nullptr);
 }
 
+BatchGate batch_gate(const Ctx* c) {
+  BatchGate g{};
+  if (c->nprob > 1 && c->bks != nullptr && c->sub_prob != nullptr) {
+    g.bs = c->bks;
+    g.sub_prob = c->sub_prob;
+    g.blk_prob = c->blk_prob;
+    g.col_prob = c->coarse_prob;
+    g.row_ptr = c->prob_rows;
+    g.nprob = c->nprob;
+  }
+  return g;
+}
+
+gdsw_status apply_enqueue_batch(Ctx* c, const double* r, double* z, cudaStream_t s) {
+  return c->fp32 ? apply_t<float>(c, r, z, s, false, false, nullptr, true)
+                 : apply_t<double>(c, r, z, s, false, false, nullptr, true);
+}
+
 gdsw_status apply_enqueue_gated(Ctx* c, const double* r, double* z, cudaStream_t s) {
   return c->fp32 ? apply_t<float>(c, r, z, s, false, true, nullptr)
                  : apply_t<double>(c, r, z, s, false, true, nullptr);
+}
+
+gdsw_status apply_timed_dots(Ctx* c, const double* r, double* z, cudaStream_t s, cudaEvent_t* ev) {
+  return c->fp32 ? apply_t<float>(c, r, z, s, true, false, ev) : apply_t<double>(c, r, z, s, true, false, ev);
 }
 
 gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms) {

@@ -66,6 +66,27 @@ __global__ void k_breduce(int nprob, const int* __restrict__ prob_tile_ptr,
   s0 = warp_sum(s0);
   s1 = warp_sum(s1);
   if (lane != 0) return;
+  if (S.start) {
+    // the prologue of a started problem: no step (p = 0), r kept, then
+    // z = M r and p = z
+    if (which == RED_PQ) {
+      S.pq = s0;
+      S.alpha = 0.0;
+    } else if (which == RED_RR) {
+      S.rr = s0;
+      if (S.start == 1) {
+        S.bb = s0;
+        S.tol2 = ctl->tol * ctl->tol * s0;
+        if (!isfinite(s0)) { S.bad = 1; S.done = 1; }
+        else if (s0 == 0.0) S.done = 1;            // b = 0: x = 0 is the solution
+      }
+    } else {
+      S.beta = 0.0;
+      S.rz = s0;
+      S.start = 0;
+    }
+    return;
+  }
   if (which == RED_PQ) {
     S.pq = s0;
     S.alpha = S.rz / s0;
@@ -142,6 +163,61 @@ __global__ void k_bresidual(int n, const double* __restrict__ b, const double* _
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = b[i] - q[i];
 }
 
+// Continuous batching: a member's state set for a new right-hand side
+// (mode 1) or for a continuation from its true residual (mode 2); every
+// member idle (stopped) before the first start.
+__global__ void k_bstart(BatchScalars* bs, int member, int mode) {
+  BatchScalars& S = bs[member];
+  S.start = mode;
+  S.done = 0;
+  S.bad = 0;
+  S.alpha = 0.0;
+  S.beta = 0.0;
+  if (mode == 1) {
+    S.iter = 0;
+    S.rz = 1.0;
+    S.rr = 0.0;
+    S.bb = 0.0;
+    S.tol2 = 0.0;
+  }
+}
+
+__global__ void k_bidle(BatchScalars* bs, int nprob) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nprob; q += gridDim.x * blockDim.x) {
+    BatchScalars S = {};
+    S.done = 1;
+    bs[q] = S;
+  }
+}
+
+// r = b - A x on rows [row0, row1) (one thread per row, grid-stride), partial
+// ||r||^2 per CTA into part[blockIdx.x].
+__global__ void __launch_bounds__(kThreads) k_bresid_rows(int row0, int row1, const int* __restrict__ rowptr,
+                                                          const int* __restrict__ colind,
+                                                          const double* __restrict__ val,
+                                                          const double* __restrict__ x,
+                                                          const double* __restrict__ b, double* __restrict__ r,
+                                                          double* __restrict__ part) {
+  __shared__ double sh[32];
+  double rr = 0.0;
+  for (int i = row0 + blockIdx.x * blockDim.x + threadIdx.x; i < row1; i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc = fma(val[e], x[colind[e]], acc);
+    const double ri = b[i] - acc;
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  rr = block_sum(rr, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = rr;
+}
+
+// The member's true ||r||^2: the partials added in order by one CTA.
+__global__ void k_bsum_rr(const double* __restrict__ part, int count, BatchScalars* bs, int member) {
+  __shared__ double sh[32];
+  const double v = sum_partials(part, count, sh);
+  if (threadIdx.x == 0) bs[member].rr = v;
+}
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -150,14 +226,14 @@ gdsw_status batch_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int
   const int nt = c->n_tiles, np = c->nprob;
   const int rgrid = (np + 7) / 8;
   k_bguard<<<1, 32, 0, s>>>(c->bctl, h, use_handle);
-  GDSW_TRY(spmv_enqueue(c, c->p, c->q, s));
+  GDSW_TRY(spmv_enqueue_batch(c, c->p, c->q, s));
   const int flex = c->flexible ? 1 : 0;
   k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->p, c->q, c->bks, c->red, 0);
   k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_PQ, c->bctl, flex, h, 0);
   k_bupdate<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->x, c->r, c->p, c->q, c->bks, c->red);
   k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_RR, c->bctl, flex, h, use_handle);
   if (flex) k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 1);
-  GDSW_TRY(apply_enqueue(c, c->r, c->z, s, false));
+  GDSW_TRY(apply_enqueue_batch(c, c->r, c->z, s));
   k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 0);
   k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_RZ, c->bctl, flex, h, 0);
   k_bpupdate<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->z, c->p, c->bks, 0);
@@ -167,8 +243,12 @@ gdsw_status batch_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int
 
 }  // namespace
 
-gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, cudaStream_t s) {
+gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, const std::vector<int>& sub_prob,
+                       const std::vector<int>& blk_prob, cudaStream_t s) {
   const int np = static_cast<int>(prob_dof_ptr.size()) - 1;
+  GDSW_TRY(upload(c, &c->prob_rows, prob_dof_ptr, s));
+  GDSW_TRY(upload(c, &c->sub_prob, sub_prob, s));
+  GDSW_TRY(upload(c, &c->blk_prob, blk_prob, s));
   std::vector<int> tp, t0, t1, ptp(np + 1, 0);
   for (int q = 0; q < np; ++q) {
     for (int r0 = prob_dof_ptr[q]; r0 < prob_dof_ptr[q + 1]; r0 += kTileRows) {
@@ -215,6 +295,113 @@ gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, cudaStream_
   return GDSW_OK;
 }
 
+// ---- continuous batching ----------------------------------------------------
+
+namespace {
+
+gdsw_status serving_init(Ctx* c, cudaStream_t s) {
+  if (c->serving) return GDSW_OK;
+  k_bidle<<<(c->nprob + 255) / 256, 256, 0, s>>>(c->bks, c->nprob);
+  BatchControl ctl = {};
+  ctl.maxit = c->opt.maxit;
+  ctl.tol = c->opt.tol;
+  GDSW_CK(cudaMemcpyAsync(c->bctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (c->bks_host == nullptr) GDSW_CK(cudaMallocHost(&c->bks_host, sizeof(BatchScalars) * c->nprob));
+  const char* env = getenv("GDSW_PCG_GRAPH");
+  if (c->sgraph_exec == nullptr && (env == nullptr || env[0] != '0')) {
+    // one batched iteration as a graph (no device-side loop: the host admits
+    // and retires members between rounds)
+    cudaStream_t cs = c->bgraph_stream;
+    if (cs == nullptr) {
+      GDSW_CK(cudaStreamCreateWithFlags(&c->bgraph_stream, cudaStreamNonBlocking));
+      cs = c->bgraph_stream;
+    }
+    GDSW_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    gdsw_status st = batch_body(c, cs, cudaGraphConditionalHandle{}, 0);
+    cudaError_t e = cudaStreamEndCapture(cs, &c->sgraph);
+    if (st != GDSW_OK) return st;
+    GDSW_CK(e);
+    GDSW_CK(cudaGraphInstantiate(&c->sgraph_exec, c->sgraph, 0));
+  }
+  c->serving = true;
+  return GDSW_OK;
+}
+
+}  // namespace
+
+gdsw_status batch_start(Ctx* c, int member, const double* b, cudaStream_t s) {
+  GDSW_TRY(serving_init(c, s));
+  const int off = c->prob_dof_host[member], nm = c->prob_dof_host[member + 1] - off;
+  GDSW_CK(cudaMemcpyAsync(c->b + off, b, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->r + off, b, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemsetAsync(c->x + off, 0, sizeof(double) * nm, s));
+  GDSW_CK(cudaMemsetAsync(c->p + off, 0, sizeof(double) * nm, s));
+  k_bstart<<<1, 1, 0, s>>>(c->bks, member, 1);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+gdsw_status batch_iterate(Ctx* c, int iterations, cudaStream_t s) {
+  if (!c->serving) { set_error("gdsw_batch_iterate: no member has been started"); return GDSW_ERR_INVALID_ARG; }
+  for (int k = 0; k < iterations; ++k) {
+    if (c->sgraph_exec != nullptr) GDSW_CK(cudaGraphLaunch(c->sgraph_exec, s));
+    else GDSW_TRY(batch_body(c, s, cudaGraphConditionalHandle{}, 0));
+  }
+  return GDSW_OK;
+}
+
+gdsw_status batch_status(Ctx* c, int32_t* done, int32_t* iters, double* relres, cudaStream_t s) {
+  if (!c->serving) GDSW_TRY(serving_init(c, s));
+  GDSW_CK(cudaMemcpyAsync(c->bks_host, c->bks, sizeof(BatchScalars) * c->nprob, cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  GDSW_TRY(check_device_errors(c, s));
+  for (int q = 0; q < c->nprob; ++q) {
+    const BatchScalars& S = c->bks_host[q];
+    if (done) done[q] = S.done;
+    if (iters) iters[q] = S.iter;
+    if (relres) relres[q] = S.bb > 0.0 ? std::sqrt(S.rr / S.bb) : 0.0;
+  }
+  return GDSW_OK;
+}
+
+gdsw_status batch_finish(Ctx* c, int member, double* x, gdsw_solve_info* info, int32_t* continued,
+                         cudaStream_t s) {
+  if (!c->serving) { set_error("gdsw_batch_finish: no member has been started"); return GDSW_ERR_INVALID_ARG; }
+  const int off = c->prob_dof_host[member], nm = c->prob_dof_host[member + 1] - off;
+  BatchScalars S;
+  GDSW_CK(cudaMemcpyAsync(&S, c->bks + member, sizeof(S), cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (!S.done) { set_error("gdsw_batch_finish: member %d is still iterating", member); return GDSW_ERR_INVALID_ARG; }
+  // the true residual r = b - A x of the member, and its norm
+  const int grid = std::max(1, std::min(1024, (nm + kThreads - 1) / kThreads));
+  k_bresid_rows<<<grid, kThreads, 0, s>>>(off, off + nm, c->rowptr, c->colind, c->val, c->x, c->b, c->r, c->red);
+  k_bsum_rr<<<1, 256, 0, s>>>(c->red, grid, c->bks, member);
+  GDSW_CK(cudaGetLastError());
+  GDSW_CK(cudaMemcpyAsync(&S, c->bks + member, sizeof(S), cudaMemcpyDeviceToHost, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  const bool ok = S.bb == 0.0 || S.rr <= S.tol2;
+  const bool give_up = S.bad || S.iter >= c->opt.maxit || !std::isfinite(S.rr);
+  if (!ok && !give_up) {
+    // continue from the true residual (now in r): p = 0, then the prologue
+    GDSW_CK(cudaMemsetAsync(c->p + off, 0, sizeof(double) * nm, s));
+    k_bstart<<<1, 1, 0, s>>>(c->bks, member, 2);
+    GDSW_CK(cudaGetLastError());
+    if (continued) *continued = 1;
+    return GDSW_OK;
+  }
+  if (continued) *continued = 0;
+  if (x) GDSW_CK(cudaMemcpyAsync(x, c->x + off, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = S.iter;
+    info->converged = ok ? 1 : 0;
+    info->true_relres = S.bb > 0.0 ? std::sqrt(S.rr / S.bb) : 0.0;
+    info->seconds = 0.0;
+  }
+  return GDSW_OK;
+}
+
 // Batched PCG: every problem of the merged handle solved at once, each with its
 // own alpha, beta and stopping test; info[p] per problem.
 gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
@@ -224,9 +411,12 @@ gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info*
   const int rgrid = (np + 7) / 8;
   GDSW_CK(cudaMemcpyAsync(c->b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GDSW_CK(cudaMemcpyAsync(c->x, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  // (a whole-batch solve ends any continuous batching on the handle)
+  c->serving = false;
   GDSW_CK(cudaMemsetAsync(c->bks, 0, sizeof(BatchScalars) * np, s));
   BatchControl ctl = {};
   ctl.maxit = c->opt.maxit;
+  ctl.tol = c->opt.tol;
   GDSW_CK(cudaMemcpyAsync(c->bctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
   const int vg = std::min(kNumSMs * 8, (n + kThreads - 1) / kThreads);
   // initial residual r = b - A x0, rr and bb per problem
@@ -268,7 +458,7 @@ gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info*
     // z = M r, (r, z), p = z (first round) or p = z + beta p (continuation)
     const int flex = (c->flexible && round > 0) ? 1 : 0;
     if (flex) k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 1);
-    GDSW_TRY(apply_enqueue(c, c->r, c->z, s, false));
+    GDSW_TRY(apply_enqueue_batch(c, c->r, c->z, s));
     k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->z, c->bks, c->red, 0);
     k_breduce<<<rgrid, 256, 0, s>>>(np, c->prob_tile_ptr, c->red, c->bks, RED_RZ, c->bctl, flex,
                                     cudaGraphConditionalHandle{}, 0);

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 #include <vector>
+#include <thread>
+#include <atomic>
 
 #include "internal.h"
 
@@ -30,6 +32,9 @@ double now_s() {
 void release(Ctx* c) {
   if (c->bgraph_exec) cudaGraphExecDestroy(c->bgraph_exec);
   if (c->bgraph) cudaGraphDestroy(c->bgraph);
+  if (c->sgraph_exec) cudaGraphExecDestroy(c->sgraph_exec);
+  if (c->sgraph) cudaGraphDestroy(c->sgraph);
+  if (c->bks_host) cudaFreeHost(c->bks_host);
   if (c->bgraph_stream) cudaStreamDestroy(c->bgraph_stream);
   if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
   if (c->gm_graph) cudaGraphDestroy(c->gm_graph);
@@ -163,7 +168,24 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
   if (st == GDSW_OK) st = spmv_configure(c, A->rowptr);
   const double t1 = now_s();
   if (st == GDSW_OK) st = krylov_init(c, s);
-  if (st == GDSW_OK && P.nprob > 1) st = batch_init(c, P.prob_dof_ptr, s);
+  if (st == GDSW_OK && P.nprob > 1) {
+    // problem of each subdomain (from its first unknown; subdomains are
+    // concatenated problem by problem) and of each Phi block
+    std::vector<int> sub_prob(P.nsub, 0), blk_prob;
+    for (int q = 0; q < P.nsub; ++q) {
+      if (P.om_ptr[q + 1] > P.om_ptr[q]) {
+        const int dof = P.om_dofs[P.om_ptr[q]];
+        sub_prob[q] = static_cast<int>(std::upper_bound(P.prob_dof_ptr.begin(), P.prob_dof_ptr.end(), dof) -
+                                       P.prob_dof_ptr.begin()) - 1;
+      } else {
+        sub_prob[q] = q > 0 ? sub_prob[q - 1] : 0;
+      }
+    }
+    blk_prob = sub_prob;
+    blk_prob.insert(blk_prob.end(), P.comp_prob.begin(), P.comp_prob.end());
+    blk_prob.resize(std::max(c->nblk, P.nsub + P.ncomp), 0);
+    st = batch_init(c, P.prob_dof_ptr, sub_prob, blk_prob, s);
+  }
   if (st == GDSW_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { set_error("setup: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; }
@@ -370,10 +392,26 @@ gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gdsw_partit
     const int np_ = nn ? nn[p] : 0;
     if (np_ < 0 || (np_ > 0 && (!Z || !Z[p]))) { set_error("null space of member %d", p); return GDSW_ERR_INVALID_ARG; }
     nnmax = std::max(nnmax, np_);
-    gdsw_status st = build_plan(&A[p], &parts[p], &o, o.local_solver != GDSW_LOCAL_EXACT, &plans[p]);
-    if (st != GDSW_OK) return st;
     n += A[p].n;
     nnz += A[p].rowptr[A[p].n];
+  }
+  {
+    // the members' symbolic phases are independent: host threads take them in
+    // turn; a member that fails is built again on this thread, which sets the
+    // error message
+    std::vector<gdsw_status> sts(count, GDSW_OK);
+    std::atomic<int> next{0};
+    const bool levels = o.local_solver != GDSW_LOCAL_EXACT;
+    auto work = [&]() {
+      for (int p = next++; p < count; p = next++) sts[p] = build_plan(&A[p], &parts[p], &o, levels, &plans[p]);
+    };
+    const int nth = std::max(1, std::min<int>(count, static_cast<int>(std::thread::hardware_concurrency())));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+    for (int p = 0; p < count; ++p)
+      if (sts[p] != GDSW_OK) return build_plan(&A[p], &parts[p], &o, levels, &plans[p]);
   }
   if (n >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31)) { set_error("batch too large"); return GDSW_ERR_UNSUPPORTED; }
   // block-diagonal union: CSR and null space (missing columns stay zero and are
@@ -424,6 +462,42 @@ gdsw_status gdsw_apply_timed(gdsw_handle h, const double* r, double* z, void* st
                              double* phase_ms) {
   if (!h || !r || !z || !phase_ms) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
   return apply_timed(&h->c, r, z, static_cast<cudaStream_t>(stream), phase_ms);
+}
+
+gdsw_status gdsw_batch_start(gdsw_handle h, int32_t member, const double* b, void* stream) {
+  if (!h || !b) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  Ctx* c = &h->c;
+  if (c->nprob < 2 || c->bks == nullptr) { set_error("gdsw_batch_start needs a batched handle"); return GDSW_ERR_INVALID_ARG; }
+  if (member < 0 || member >= c->nprob) { set_error("member %d out of range [0, %d)", member, c->nprob); return GDSW_ERR_INVALID_ARG; }
+  return batch_start(c, member, b, static_cast<cudaStream_t>(stream));
+}
+
+gdsw_status gdsw_batch_iterate(gdsw_handle h, int32_t iterations, void* stream) {
+  if (!h || iterations < 0) { set_error("null handle or negative iteration count"); return GDSW_ERR_INVALID_ARG; }
+  Ctx* c = &h->c;
+  if (c->nprob < 2 || c->bks == nullptr) { set_error("gdsw_batch_iterate needs a batched handle"); return GDSW_ERR_INVALID_ARG; }
+  return batch_iterate(c, iterations, static_cast<cudaStream_t>(stream));
+}
+
+gdsw_status gdsw_batch_status(gdsw_handle h, int32_t* done, int32_t* iters, double* relres, void* stream) {
+  if (!h) { set_error("null handle"); return GDSW_ERR_INVALID_ARG; }
+  Ctx* c = &h->c;
+  if (c->nprob < 2 || c->bks == nullptr) { set_error("gdsw_batch_status needs a batched handle"); return GDSW_ERR_INVALID_ARG; }
+  return batch_status(c, done, iters, relres, static_cast<cudaStream_t>(stream));
+}
+
+gdsw_status gdsw_batch_finish(gdsw_handle h, int32_t member, double* x, gdsw_solve_info* info,
+                              int32_t* continued, void* stream) {
+  if (!h) { set_error("null handle"); return GDSW_ERR_INVALID_ARG; }
+  Ctx* c = &h->c;
+  if (c->nprob < 2 || c->bks == nullptr) { set_error("gdsw_batch_finish needs a batched handle"); return GDSW_ERR_INVALID_ARG; }
+  if (member < 0 || member >= c->nprob) { set_error("member %d out of range [0, %d)", member, c->nprob); return GDSW_ERR_INVALID_ARG; }
+  return batch_finish(c, member, x, info, continued, static_cast<cudaStream_t>(stream));
+}
+
+gdsw_status gdsw_pcg_iteration_timed(gdsw_handle h, const double* b, void* stream, double* kernel_ms) {
+  if (!h || !b || !kernel_ms) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
+  return pcg_iteration_timed(&h->c, b, static_cast<cudaStream_t>(stream), kernel_ms);
 }
 
 gdsw_status gdsw_spmv(gdsw_handle h, const double* x, double* y, void* stream) {

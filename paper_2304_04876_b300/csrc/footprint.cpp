@@ -26,7 +26,7 @@ int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec) {
       if (E.sub_lev.empty()) continue;
       for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
         const int K = E.lev_K[l];
-        const int piece = record_piece_rows(E.lev_nr[l], K, P.dpn, size_t(vb));
+        const int piece = record_piece_rows(E.lev_nr[l], K, P.dpn, size_t(vb), record_cap());
         const int64_t Kp = record_width(K);
         for (int t0 = 0; t0 < E.lev_nr[l]; t0 += piece) {
           const int64_t nr = std::min(piece, E.lev_nr[l] - t0);
@@ -51,7 +51,8 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
   int64_t R = 0, S = 0;
 
   // matrix, overlap, local solution buffer, device error word
-  R += arr(n + 1, 4) + arr(nnz, 4) + arr(nnz, 8) + arr(nsub + 1, 4) + arr(sum_m, 4) + arr(sum_m, v) + 4;
+  // (the overlap map padded by four words for the local solve's aligned copies)
+  R += arr(n + 1, 4) + arr(nnz, 4) + arr(nnz, 8) + arr(nsub + 1, 4) + arr(sum_m + 4, 4) + arr(sum_m, v) + 4;
   // local matrices and fixed-point sweeps (scratch)
   S += arr(nsub + 1, 4) + arr(sum_m + 1, 4) + 4 * arr(nent, 4) + arr(nent, 2) + arr(sum_m, 8) + 2 * arr(nent, 8);
   if (!exact) {
@@ -120,10 +121,15 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
   }
 
   // Krylov workspace: six vectors, the reduction buffer, scalars; GMRES basis
-  R += 6 * arr(n, 8) + arr(2 * (nsub + int64_t(P.ncomp)) + 4096, 8) + 256;
+  // (reduction buffer: partials of any SpMV grid, at most 32 CTAs per SM)
+  R += 6 * arr(n, 8) + arr(2 * (nsub + int64_t(P.ncomp)) + 32 * 148 + 64, 8) + 256;
   if (o.krylov == GDSW_KRYLOV_GMRES)
     R += (2 * int64_t(o.restart) + 1) * arr(n, 8) + arr(o.restart + 2, 8) + (int64_t(o.restart) + 2) * 10000;
-  if (P.nprob > 1) R += 4 * arr(n / 4096 + 2 * P.nprob + 1, 4) + arr(P.nprob, 256) + arr(4 * (n / 4096 + P.nprob) + 64, 8);
+  // batched handles: tiles, per-problem states, the problem of each
+  // subdomain, Phi block and unknown range
+  if (P.nprob > 1)
+    R += 4 * arr(n / 4096 + 2 * P.nprob + 1, 4) + arr(P.nprob, 256) + arr(4 * (n / 4096 + P.nprob) + 64, 8) +
+         arr(nsub, 4) + arr(nsub + P.ncomp, 4) + arr(P.nprob + 1, 4);
   *resident = R;
   *scratch_peak = S;
   return GDSW_OK;

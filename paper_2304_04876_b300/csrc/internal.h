@@ -141,13 +141,31 @@ struct CoarsePlan {
 // columns per row); wider levels column-major with their own width.
 inline int record_width(int K) { return K == 0 ? 0 : (K <= 4 ? 4 : K); }
 
+// Header word 5 of a level record holds its layout (low byte), kRecUpper for
+// the records of the second (U) sweep and kRecLevelEnd for the last record of
+// a level (the consumers meet at a barrier only there: the rows of one level
+// are independent, however many records carry them).
+constexpr int kRecUpper = 0x100;
+constexpr int kRecLevelEnd = 0x200;
+
+// Largest level record in bytes (a wide level is split into records of at
+// most this size).  Every copy into the ring has a fixed cost, so fewer,
+// larger records stream faster (measured on B300: 1-4 KB records were 1.2-2.7
+// times slower than 32 KB ones).  GDSW_REC_CAP overrides it.
+constexpr size_t kRecordCapDefault = 32 * 1024;
+inline size_t record_cap() {
+  const char* e = getenv("GDSW_REC_CAP");
+  const long v = e ? atol(e) : static_cast<long>(kRecordCapDefault);
+  return v < 512 ? 512 : static_cast<size_t>(v);
+}
+
 // Rows per record when a level of nr rows and width K is split so that one
 // record (header, rows, inverse diagonal, values, columns; vb bytes per value)
-// stays within kRecordCap bytes; a multiple of the node group g.
-constexpr size_t kRecordCap = 32 * 1024;
-inline int record_piece_rows(int nr, int K, int g, size_t vb) {
+// stays within `cap` bytes (or holds one node group); a multiple of the node
+// group g.
+inline int record_piece_rows(int nr, int K, int g, size_t vb, size_t cap) {
   const size_t per_row = 2 + vb + size_t(record_width(K)) * (vb + 2) + size_t(g - 1) * vb;
-  size_t rows = (kRecordCap - 80) / per_row;
+  size_t rows = cap > 80 + per_row ? (cap - 80) / per_row : 1;
   rows = rows / size_t(g) * size_t(g);
   if (rows < size_t(g)) rows = g;
   return rows >= size_t(nr) ? nr : static_cast<int>(rows);
@@ -277,17 +295,59 @@ struct KrylovScalars {
 
 constexpr int kNumSMsForCtx = 148;
 
-// Per-problem PCG state of a batched handle.
+// Per-problem PCG state of a batched handle.  `start` makes the next
+// iteration the PCG prologue for this problem (step lengths 0: r stays, z = M r,
+// p = z): 1 for a new right-hand side (||r||^2 of that iteration is ||b||^2 and
+// sets the stopping threshold), 2 to continue from a recomputed true residual.
 struct BatchScalars {
   double rz, pq, rr, bb, tol2, alpha, beta;
-  int iter, done, bad, pad;
+  int iter, done, bad, start;
 };
+
+// Per-problem gating of the apply and SpMV kernels of a batched handle: a
+// problem whose PCG has stopped (or an idle serving member) costs only this
+// check.  `bs` is null on single-problem handles (nothing gated).
+struct BatchGate {
+  const BatchScalars* bs;
+  const int* sub_prob;    // problem of each subdomain
+  const int* blk_prob;    // problem of each Phi block
+  const int* col_prob;    // problem of each coarse column
+  const int* row_ptr;     // nprob+1: unknowns of each problem
+  int nprob;
+};
+
+#ifdef __CUDACC__
+// True when problem p of a batched handle is gated off (it has stopped).
+__device__ __forceinline__ bool gate_off(const BatchGate& g, int p) { return g.bs != nullptr && g.bs[p].done; }
+__device__ __forceinline__ bool gate_sub_off(const BatchGate& g, int s) {
+  return g.bs != nullptr && g.bs[g.sub_prob[s]].done;
+}
+__device__ __forceinline__ bool gate_blk_off(const BatchGate& g, int b) {
+  return g.bs != nullptr && g.bs[g.blk_prob[b]].done;
+}
+__device__ __forceinline__ bool gate_col_off(const BatchGate& g, int l) {
+  return g.bs != nullptr && g.bs[g.col_prob[l]].done;
+}
+// True when every problem with unknowns in [r0, r1) is gated off.
+__device__ __forceinline__ bool gate_rows_off(const BatchGate& g, int r0, int r1) {
+  if (g.bs == nullptr) return false;
+  int lo = 0, hi = g.nprob - 1;            // last problem whose first unknown <= r0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.row_ptr[mid] <= r0) lo = mid; else hi = mid - 1;
+  }
+  for (int p = lo; p < g.nprob && g.row_ptr[p] < r1; ++p)
+    if (!g.bs[p].done) return false;
+  return true;
+}
+#endif
 
 struct BatchControl {
   unsigned int ndone;
   int all_done;
   int maxit;
   int pad;
+  double tol;                     // relative tolerance (thresholds of started problems)
 };
 
 // Default bound on a device-side wait: about one second at the B300 SM clock.
@@ -332,6 +392,8 @@ struct Ctx {
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int rec_max_rows = 0;              // most rows in one level
   int rec_consumers = 256;           // consumer threads of the pipelined solve
+  int rec_prefetch = 0;              // bytes of records kept on their way into L2 ahead of the ring
+  bool rec_sf = false;               // pipelined solve without a barrier per level (per-row flags)
   int tri_threads = 256;             // threads of the unpipelined level / Jacobi solve
   int* derr = nullptr;               // device error flags (bounded waits that ran out)
   long long wait_cycles = 0;         // bound on each device-side wait, SM clock cycles
@@ -412,9 +474,17 @@ struct Ctx {
   BatchControl* bctl = nullptr;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bgraph_exec = nullptr;
+  cudaGraph_t sgraph = nullptr;          // one batched iteration (continuous batching)
+  cudaGraphExec_t sgraph_exec = nullptr;
+  BatchScalars* bks_host = nullptr;      // pinned mirror of the per-problem states
+  int* sub_prob = nullptr;               // problem of each subdomain (batched handles)
+  int* blk_prob = nullptr;               // problem of each Phi block
+  int* prob_rows = nullptr;              // nprob+1: unknowns of each problem
+  bool serving = false;                  // members started one by one (gdsw_batch_start)
   cudaStream_t bgraph_stream = nullptr;
   int spmv_R = 256, spmv_maxne = 1, spmv_tiles = 1, spmv_grid = kNumSMsForCtx;
   int spmv_W = 0;                    // lanes per row for long rows (0: the tiled kernel)
+  int spmv_pipe = 0;                 // tiled kernel with the next tile's loads in flight (chosen by timing)
 };
 
 template <class T>
@@ -452,7 +522,14 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
 gdsw_status apply_enqueue(Ctx* c, const double* r, double* z, cudaStream_t s, bool rz_dots);
 // The apply with every kernel gated on the Krylov stop flag (no dots).
 gdsw_status apply_enqueue_gated(Ctx* c, const double* r, double* z, cudaStream_t s);
+// The apply of a batched PCG iteration: problems that have stopped are skipped.
+gdsw_status apply_enqueue_batch(Ctx* c, const double* r, double* z, cudaStream_t s);
+// The gate of the batched handle's iteration (all null on a single problem).
+BatchGate batch_gate(const Ctx* c);
 gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, double* ms);
+// The PCG form of the apply (dots fused) on one stream, events ev[0..4]
+// recorded around its four phases.
+gdsw_status apply_timed_dots(Ctx* c, const double* r, double* z, cudaStream_t s, cudaEvent_t* ev);
 gdsw_status check_device_errors(Ctx* c, cudaStream_t s);
 // multifrontal.cu: the exact local solver for subdomains too large for dense inverses
 gdsw_status mf_numeric_setup(Ctx* c, const Plan& P, const double* d_araw, cudaStream_t s);
@@ -467,13 +544,29 @@ inline int exact_dense_max() {
 // krylov.cu
 gdsw_status krylov_init(Ctx* c, cudaStream_t s);
 gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s);
+// y = A x on the rows of problems that have not stopped (batched iteration).
+gdsw_status spmv_enqueue_batch(Ctx* c, const double* x, double* y, cudaStream_t s);
 gdsw_status spmv_configure(Ctx* c, const int* rowptr_host);
 gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
+// One PCG iteration from x = 0 (after its prologue), kernel by kernel on one
+// stream with CUDA events: ms[0] SpMV, [1] vector update, [2] local solve,
+// [3] Phi^T r, [4] coarse solve, [5] scatter-add (dots fused), [6] direction.
+gdsw_status pcg_iteration_timed(Ctx* c, const double* b, cudaStream_t s, double* ms);
 gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
                         cudaStream_t s);
 // batch.cu
-gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, cudaStream_t s);
+// sub_prob: problem of each subdomain; blk_prob: of each Phi block (subdomain
+// interiors, then interface components).
+gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, const std::vector<int>& sub_prob,
+                       const std::vector<int>& blk_prob, cudaStream_t s);
 gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
+// Continuous batching on a batched handle: members start, iterate together
+// and finish independently (see gdsw_batch_start and the entry points after it).
+gdsw_status batch_start(Ctx* c, int member, const double* b, cudaStream_t s);
+gdsw_status batch_iterate(Ctx* c, int iterations, cudaStream_t s);
+gdsw_status batch_status(Ctx* c, int32_t* done, int32_t* iters, double* relres, cudaStream_t s);
+gdsw_status batch_finish(Ctx* c, int member, double* x, gdsw_solve_info* info, int32_t* continued,
+                         cudaStream_t s);
 
 constexpr int kNumSMs = 148;
 

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <string>
 
 #include "common.cuh"
 #include "internal.h"
@@ -19,58 +20,180 @@ namespace {
 constexpr int kThreads = 256;
 
 // y = A x by row tiles of R rows: the tile's values and the gathered x
-// entries are streamed once, coalesced, into shared memory (several
-// independent loads in flight per thread), then one thread per row forms its
-// sum with one FMA per entry in column order (the FP64 pipe of B300 is narrow,
-// so no separate multiply and add).  With `ks`, also (x, y) into ks->pq.
+// entries are loaded once, coalesced, into shared memory, then one thread per
+// row forms its sum with one FMA per entry in column order (the FP64 pipe of
+// B300 is narrow, so no separate multiply and add).  Every load of a trip is
+// issued before any is used (one memory latency for the columns and values,
+// one for the gathered x), and the next tile's row pointers are fetched
+// before the current tile's sums.  With `ks`, also (x, y) into ks->pq and
+// alpha = (r, z) / (x, y) into ks->alpha (the PCG step length, divided once).
 template <int R>
 __global__ void __launch_bounds__(R) k_spmv_stream(int n, int ntiles, const int* __restrict__ rowptr,
                                                    const int* __restrict__ colind,
                                                    const double* __restrict__ val,
                                                    const double* __restrict__ x, double* __restrict__ y,
-                                                   double* __restrict__ red, KrylovScalars* ks) {
+                                                   double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int rp[R + 1];
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
+  constexpr int U = 8;
   double* va = reinterpret_cast<double*>(smem_raw);
   double dot = 0.0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int t = threadIdx.x;
+  // row pointers of the first tile (thread t: row t; thread 0 also the end)
+  int tile = blockIdx.x;
+  int rp_t = 0, rp_end = 0;
+  if (tile < ntiles) {
+    const int r0 = tile * R, nr = min(R, n - r0);
+    if (t < nr) rp_t = rowptr[r0 + t];
+    if (t == 0) rp_end = rowptr[r0 + nr];
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
     const int r0 = tile * R;
     const int nr = min(R, n - r0);
-    for (int i = threadIdx.x; i <= nr; i += R) rp[i] = rowptr[r0 + i];
+    if (t < nr) rp[t] = rp_t;
+    if (t == 0) rp[nr] = rp_end;
     __syncthreads();
+    // (tiles whose problems have all stopped: nothing to load or sum)
+    const bool off = gate_rows_off(gate, r0, r0 + nr);
     const int e0 = rp[0];
-    const int ne = rp[nr] - e0;
+    const int ne = off ? 0 : rp[nr] - e0;
     double* xa = va + ne;   // gathered x right after the values
     const double* v = val + e0;
     const int* ci = colind + e0;
-    int j = threadIdx.x;
-    for (; j + 3 * R < ne; j += 4 * R) {
-      const int c0 = ci[j], c1 = ci[j + R], c2 = ci[j + 2 * R], c3 = ci[j + 3 * R];
-      const double a0 = v[j], a1 = v[j + R], a2 = v[j + 2 * R], a3 = v[j + 3 * R];
-      const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
-      va[j] = a0; va[j + R] = a1; va[j + 2 * R] = a2; va[j + 3 * R] = a3;
-      xa[j] = x0; xa[j + R] = x1; xa[j + 2 * R] = x2; xa[j + 3 * R] = x3;
+    for (int j0 = t; j0 < ne; j0 += U * R) {
+      int c[U];
+      double a[U], xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u * R;
+        c[u] = j < ne ? ci[j] : -1;
+        a[u] = j < ne ? v[j] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u * R;
+        if (j < ne) { va[j] = a[u]; xa[j] = xv[u]; }
+      }
     }
-    for (; j < ne; j += R) { va[j] = v[j]; xa[j] = x[ci[j]]; }
+    // the next tile's row pointers are in flight during the sums
+    const int nt_ = tile + gridDim.x;
+    if (nt_ < ntiles) {
+      const int q0 = nt_ * R, qn = min(R, n - q0);
+      if (t < qn) rp_t = rowptr[q0 + t];
+      if (t == 0) rp_end = rowptr[q0 + qn];
+    }
     __syncthreads();
-    if (threadIdx.x < nr) {
-      const int a = rp[threadIdx.x] - e0, b = rp[threadIdx.x + 1] - e0;
+    if (t < nr && !off) {
+      const int a = rp[t] - e0, b = rp[t + 1] - e0;
       double acc = 0.0;
       for (int q = a; q < b; ++q) acc = fma(va[q], xa[q], acc);
-      const int row = r0 + threadIdx.x;
+      const int row = r0 + t;
       y[row] = acc;
       dot = fma(x[row], acc, dot);
     }
     __syncthreads();
   }
   if (ks == nullptr) return;
-  const double t = block_sum(dot, sh);
-  if (threadIdx.x == 0) red[blockIdx.x] = t;
+  const double tsum = block_sum(dot, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = tsum;
   if (arrive_last(&ks->ticket[0])) {
     const double s2 = sum_partials(red, gridDim.x, sh);
-    if (threadIdx.x == 0) ks->pq = s2;
+    if (threadIdx.x == 0) {
+      ks->pq = s2;
+      ks->alpha = ks->rz / s2;
+    }
+  }
+}
+
+// The same product with the next tile's columns and values in flight while
+// the current tile's sums run: the FP64 pipe (one DFMA per entry) and the
+// memory stream overlap within a CTA instead of alternating.  Tiles of R rows
+// with at most 8 R entries; row pointers double-buffered in shared memory.
+template <int R>
+__global__ void __launch_bounds__(R, 2048 / R / 2) k_spmv_pipe(int n, int ntiles, const int* __restrict__ rowptr,
+                                                             const int* __restrict__ colind,
+                                                             const double* __restrict__ val,
+                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             double* __restrict__ red, KrylovScalars* ks,
+                                                             BatchGate gate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int rp[2][R + 1];
+  __shared__ double sh[32];
+  if (ks != nullptr && ks->done) return;
+  constexpr int U = 8;
+  double* va = reinterpret_cast<double*>(smem_raw);
+  const int t = threadIdx.x;
+  double dot = 0.0;
+  int tile = blockIdx.x;
+  // row pointers of a tile into buffer b
+  auto load_rp = [&](int tl, int b) {
+    const int r0 = tl * R, nr = min(R, n - r0);
+    if (t < nr) rp[b][t] = rowptr[r0 + t];
+    if (t == 0) rp[b][nr] = rowptr[r0 + nr];
+  };
+  if (tile < ntiles) load_rp(tile, 0);
+  __syncthreads();
+  int c[U];
+  double a[U];
+  // columns and values of the tile whose row pointers are in buffer b
+  auto load_ca = [&](int tl, int b) {
+    const int nr = min(R, n - tl * R);
+    const int e0 = rp[b][0];
+    const int ne = gate_rows_off(gate, tl * R, tl * R + nr) ? 0 : rp[b][nr] - e0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = t + u * R;
+      c[u] = j < ne ? colind[e0 + j] : -1;
+      a[u] = j < ne ? val[e0 + j] : 0.0;
+    }
+  };
+  if (tile < ntiles) load_ca(tile, 0);
+  int buf = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int r0 = tile * R;
+    const int nr = min(R, n - r0);
+    const bool off = gate_rows_off(gate, r0, r0 + nr);
+    const int e0 = rp[buf][0];
+    const int ne = off ? 0 : rp[buf][nr] - e0;
+    double* xa = va + ne;
+    // the gathered x of this tile, then both into shared memory
+    double xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = t + u * R;
+      if (j < ne) { va[j] = a[u]; xa[j] = xv[u]; }
+    }
+    const int next = tile + gridDim.x;
+    if (next < ntiles) load_rp(next, buf ^ 1);
+    __syncthreads();
+    // the next tile's columns and values are in flight during the sums
+    if (next < ntiles) load_ca(next, buf ^ 1);
+    if (t < nr && !off) {
+      const int q0 = rp[buf][t] - e0, q1 = rp[buf][t + 1] - e0;
+      double acc = 0.0;
+      for (int q = q0; q < q1; ++q) acc = fma(va[q], xa[q], acc);
+      const int row = r0 + t;
+      y[row] = acc;
+      dot = fma(x[row], acc, dot);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  if (ks == nullptr) return;
+  const double tsum = block_sum(dot, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = tsum;
+  if (arrive_last(&ks->ticket[0])) {
+    const double s2 = sum_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      ks->pq = s2;
+      ks->alpha = ks->rz / s2;
+    }
   }
 }
 
@@ -82,7 +205,7 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int n, const int* __restrict_
                                                    const int* __restrict__ colind,
                                                    const double* __restrict__ val,
                                                    const double* __restrict__ x, double* __restrict__ y,
-                                                   double* __restrict__ red, KrylovScalars* ks) {
+                                                   double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
   const int lane = threadIdx.x % W;
@@ -90,7 +213,7 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int n, const int* __restrict_
   double dot = 0.0;
   for (int base = blockIdx.x * kRows; base < n; base += gridDim.x * kRows) {
     const int row = base + threadIdx.x / W;
-    const bool valid = row < n;
+    const bool valid = row < n && !gate_rows_off(gate, row, row + 1);
     double acc = 0.0;
     if (valid) {
       const int e1 = rowptr[row + 1];
@@ -108,12 +231,16 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int n, const int* __restrict_
   if (threadIdx.x == 0) red[blockIdx.x] = t;
   if (arrive_last(&ks->ticket[0])) {
     const double s2 = sum_partials(red, gridDim.x, sh);
-    if (threadIdx.x == 0) ks->pq = s2;
+    if (threadIdx.x == 0) {
+      ks->pq = s2;
+      ks->alpha = ks->rz / s2;
+    }
   }
 }
 
-// alpha = (r,z)/(p,q); x += alpha p; r -= alpha q; rr = ||r||^2; then the
-// last CTA counts the iteration and decides whether the loop ends.
+// With alpha = (r,z)/(p,q) (divided once by the SpMV's last CTA): x += alpha p;
+// r -= alpha q; rr = ||r||^2; then the last CTA counts the iteration and
+// decides whether the loop ends.
 __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restrict__ x,
                                                          double* __restrict__ r,
                                                          const double* __restrict__ p,
@@ -127,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
     if (use_handle && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(handle, 0);
     return;
   }
-  const double alpha = ks->rz / ks->pq;
+  const double alpha = ks->alpha;
   double rr = 0.0;
   const int n2 = n >> 1;
   const int stride = gridDim.x * blockDim.x;
@@ -158,7 +285,6 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
     const double s = sum_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
       ks->rr = s;
-      ks->alpha = alpha;
       ks->iter += 1;
       int done = 0;
       if (!isfinite(s) || !isfinite(alpha) || !(ks->pq > 0.0)) { ks->bad = 1; done = 1; }
@@ -375,25 +501,36 @@ __global__ void k_update_x(int n, int k, const double* __restrict__ Zk, const do
   }
 }
 
-gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, KrylovScalars* ks) {
+gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, KrylovScalars* ks,
+                        const BatchGate& gate = BatchGate{}) {
   if (c->spmv_W > 0) {
     const int grid = std::max(1, std::min(c->spmv_grid, (c->n + 256 / c->spmv_W - 1) / (256 / c->spmv_W)));
     switch (c->spmv_W) {
-      case 4: k_spmv_rows<4><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-      case 8: k_spmv_rows<8><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-      case 16: k_spmv_rows<16><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-      default: k_spmv_rows<32><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+      case 4: k_spmv_rows<4><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+      case 8: k_spmv_rows<8><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+      case 16: k_spmv_rows<16><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+      default: k_spmv_rows<32><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
     }
     GDSW_CK(cudaGetLastError());
     return GDSW_OK;
   }
   const int grid = std::min(c->spmv_grid, c->spmv_tiles);
   const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
+  if (c->spmv_pipe) {
+    switch (c->spmv_R) {
+      case 256: k_spmv_pipe<256><<<grid, 256, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+      case 128: k_spmv_pipe<128><<<grid, 128, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+      case 64: k_spmv_pipe<64><<<grid, 64, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+      default: k_spmv_pipe<32><<<grid, 32, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+    }
+    GDSW_CK(cudaGetLastError());
+    return GDSW_OK;
+  }
   switch (c->spmv_R) {
-    case 256: k_spmv_stream<256><<<grid, 256, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-    case 128: k_spmv_stream<128><<<grid, 128, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-    case 64: k_spmv_stream<64><<<grid, 64, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
-    default: k_spmv_stream<32><<<grid, 32, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks); break;
+    case 256: k_spmv_stream<256><<<grid, 256, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+    case 128: k_spmv_stream<128><<<grid, 128, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+    case 64: k_spmv_stream<64><<<grid, 64, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+    default: k_spmv_stream<32><<<grid, 32, shm, s>>>(c->n, c->spmv_tiles, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
   }
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
@@ -485,8 +622,79 @@ gdsw_status spmv_configure(Ctx* c, const int* rowptr) {
   return GDSW_OK;
 }
 
+namespace {
+
+// Resident CTAs of the tiled SpMV kernels for tile height R: the plain one and
+// the one with the next tile's loads in flight.
+template <int RR>
+gdsw_status spmv_grids(size_t shm, int* g_stream, int* g_pipe) {
+  int a = 1, b = 1;
+  GDSW_CK(allow_max_dynamic_smem(k_spmv_stream<RR>));
+  GDSW_CK(allow_max_dynamic_smem(k_spmv_pipe<RR>));
+  GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_spmv_stream<RR>, RR, shm));
+  GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmv_pipe<RR>, RR, shm));
+  *g_stream = std::max(1, a) * kNumSMs;
+  *g_pipe = std::max(1, b) * kNumSMs;
+  return GDSW_OK;
+}
+
+// Measured choice between the two tiled SpMV kernels (three timed launches
+// each after a warm-up, CUDA events, on the Krylov workspace): both compute
+// the same sums in the same order, so the choice changes the speed only.
+// GDSW_SPMV=stream|pipe fixes it instead (for profilers).
+gdsw_status spmv_tune(Ctx* c, cudaStream_t s) {
+  if (c->spmv_W > 0) return GDSW_OK;
+  const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
+  int g[2] = {c->spmv_grid, c->spmv_grid};
+  switch (c->spmv_R) {
+    case 256: GDSW_TRY(spmv_grids<256>(shm, &g[0], &g[1])); break;
+    case 128: GDSW_TRY(spmv_grids<128>(shm, &g[0], &g[1])); break;
+    case 64: GDSW_TRY(spmv_grids<64>(shm, &g[0], &g[1])); break;
+    default: GDSW_TRY(spmv_grids<32>(shm, &g[0], &g[1])); break;
+  }
+  // the pipelined kernel holds eight entries per thread of a tile
+  const bool pipe_ok = c->spmv_maxne <= 8 * c->spmv_R;
+  const char* env = getenv("GDSW_SPMV");
+  if (env != nullptr || !pipe_ok) {
+    c->spmv_pipe = (pipe_ok && env != nullptr && std::string(env) == "pipe") ? 1 : 0;
+    c->spmv_grid = g[c->spmv_pipe];
+    return GDSW_OK;
+  }
+  cudaEvent_t e0, e1;
+  GDSW_CK(cudaEventCreate(&e0));
+  GDSW_CK(cudaEventCreate(&e1));
+  float best = 3.4e38f;
+  int best_k = 0;
+  gdsw_status st = GDSW_OK;
+  for (int k = 0; k < 2 && st == GDSW_OK; ++k) {
+    c->spmv_pipe = k;
+    c->spmv_grid = g[k];
+    st = launch_spmv(c, c->p, c->q, s, nullptr);
+    if (st != GDSW_OK) break;
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep) st = launch_spmv(c, c->p, c->q, s, nullptr);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { set_error("SpMV tuning: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; break; }
+    if (ms < best) { best = ms; best_k = k; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->spmv_pipe = best_k;
+  c->spmv_grid = g[best_k];
+  return st;
+}
+
+}  // namespace
+
 gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s) {
   return launch_spmv(c, x, y, s, nullptr);
+}
+
+gdsw_status spmv_enqueue_batch(Ctx* c, const double* x, double* y, cudaStream_t s) {
+  return launch_spmv(c, x, y, s, nullptr, batch_gate(c));
 }
 
 gdsw_status gmres_cycle(Ctx* c, cudaStream_t s);
@@ -494,7 +702,8 @@ gdsw_status gmres_cycle(Ctx* c, cudaStream_t s);
 gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   const int n = c->n;
   c->red_grid = kNumSMs * 8;
-  c->red_len = std::max(std::max(2 * c->red_grid, 2 * c->nblk), c->spmv_grid) + 64;
+  // (any SpMV grid: at most 32 resident CTAs per SM)
+  c->red_len = std::max(std::max(2 * c->red_grid, 2 * c->nblk), std::max(c->spmv_grid, 32 * kNumSMs)) + 64;
   if (c->opt.krylov == GDSW_KRYLOV_GMRES)
     c->red_len = std::max<int>(c->red_len, (c->opt.restart + 2) * c->red_grid + 64);
   GDSW_TRY(dalloc(c, &c->red, c->red_len));
@@ -517,6 +726,9 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
     GDSW_TRY(dalloc(c, &c->gm, GmLayout(m).total()));
   }
   for (int q = 0; q < 8; ++q) GDSW_CK(cudaEventCreate(&c->ev[q]));
+  GDSW_CK(cudaStreamSynchronize(s));
+  // the SpMV kernel is chosen by timing before the graphs capture it
+  GDSW_TRY(spmv_tune(c, s));
   GDSW_CK(cudaStreamSynchronize(s));
   // the PCG iteration as a graph: while (cond) { body }, cond cleared on device
   const char* env = getenv("GDSW_PCG_GRAPH");
@@ -629,6 +841,56 @@ gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
   }
   if (!converged) { set_error("PCG stopped after %d iterations at relative residual %.3e", iters, std::sqrt(rr / bb)); return GDSW_ERR_NOT_CONVERGED; }
   return GDSW_OK;
+}
+
+gdsw_status pcg_iteration_timed(Ctx* c, const double* b, cudaStream_t s, double* ms) {
+  if (c->nprob != 1) { set_error("timed PCG iteration: batched handles are not supported"); return GDSW_ERR_UNSUPPORTED; }
+  const int n = c->n;
+  KrylovScalars init = {};
+  init.maxit = 1 << 30;
+  init.flexible = c->flexible ? 1 : 0;
+  init.rz = 1.0;
+  init.tol2 = -1.0;                          // never met: the timed iteration runs every kernel
+  GDSW_CK(cudaMemcpyAsync(c->ks, &init, sizeof(KrylovScalars), cudaMemcpyHostToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemsetAsync(c->x, 0, sizeof(double) * n, s));
+  GDSW_CK(cudaMemcpyAsync(c->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_TRY(apply_enqueue(c, c->r, c->z, s, true));
+  GDSW_CK(cudaMemcpyAsync(c->p, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  cudaEvent_t ev[9] = {};
+  gdsw_status st = GDSW_OK;
+  for (int q = 0; q < 9 && st == GDSW_OK; ++q)
+    if (cudaEventCreate(&ev[q]) != cudaSuccess) { set_error("event creation failed"); st = GDSW_ERR_CUDA; }
+  cudaEvent_t* ap = ev + 2;                  // the apply records ap[0..4]
+  if (st == GDSW_OK) {
+    cudaEventRecord(ev[0], s);
+    st = launch_spmv(c, c->p, c->q, s, c->ks);
+  }
+  if (st == GDSW_OK) {
+    cudaEventRecord(ev[1], s);
+    k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(n, c->x, c->r, c->p, c->q, c->red, c->ks,
+                                                   cudaGraphConditionalHandle{}, 0);
+    if (cudaGetLastError() != cudaSuccess) { set_error("vector update launch failed"); st = GDSW_ERR_CUDA; }
+  }
+  if (st == GDSW_OK) st = apply_timed_dots(c, c->r, c->z, s, ap);
+  if (st == GDSW_OK) {
+    k_pupdate<<<vec_grid(c), kThreads, 0, s>>>(n, c->z, c->p, c->ks);
+    cudaEventRecord(ev[7], s);
+    if (cudaEventSynchronize(ev[7]) != cudaSuccess) { set_error("timed iteration failed"); st = GDSW_ERR_CUDA; }
+  }
+  if (st == GDSW_OK) st = check_device_errors(c, s);
+  if (st == GDSW_OK) {
+    // spmv, update, local, phiT, coarse, combine (events ev[1..6]), pupdate
+    const int from[7] = {0, 1, 2, 3, 4, 5, 6}, to[7] = {1, 2, 3, 4, 5, 6, 7};
+    for (int q = 0; q < 7; ++q) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[from[q]], ev[to[q]]);
+      ms[q] = t;
+    }
+  }
+  for (int q = 0; q < 9; ++q)
+    if (ev[q]) cudaEventDestroy(ev[q]);
+  return st;
 }
 
 // One restart cycle of GMRES(m): m Arnoldi steps, each z_j = M^-1 v_j,

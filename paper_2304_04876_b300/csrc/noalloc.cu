@@ -61,7 +61,11 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_spmv_dot_static(
   }
 }
 
-// Device addresses of the two arrays, looked up once per device.
+// Device addresses of the two arrays, looked up once per device.  The cache
+// assumes that the device's primary context (the one the runtime API uses)
+// lives as long as the process: after cudaDeviceReset the module is loaded
+// again, possibly at other addresses, and the cached ones are stale, so a
+// process that resets a device must not call this entry point afterwards.
 struct StaticScratch {
   double* partials = nullptr;
   unsigned int* ticket = nullptr;

@@ -725,7 +725,13 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     GDSW_TRY(upload(c, &c->val, va, s));
   }
   GDSW_TRY(upload(c, &c->om_ptr, P.om_ptr, s));
-  GDSW_TRY(upload(c, &c->om_dofs, P.om_dofs, s));
+  {
+    // padded by four words: the pipelined local solve copies each subdomain's
+    // slice from a 16-byte aligned start in whole 16-byte units
+    std::vector<int> padded(P.om_dofs);
+    padded.resize(P.om_dofs.size() + 4, 0);
+    GDSW_TRY(upload(c, &c->om_dofs, padded, s));
+  }
 
   // ---- local matrices ----
   double t0 = now_s();
@@ -828,6 +834,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     // (the unpipelined kernel solves).
     if (P.dpn <= 4) {
       const size_t vb = c->fp16 ? sizeof(__half) : c->fp32 ? sizeof(float) : sizeof(double);
+      const size_t rcap = record_cap();
       const int Gn = P.dpn;
       auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
       struct RecLayout { int layout; size_t K, o_l, o_d, o_v, o_c, o_i, end; };
@@ -878,7 +885,7 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
               // a wide level becomes several records (rows are independent
               // within a level, node groups kept whole)
               const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
-              const size_t piece = record_piece_rows(E.lev_nr[l], E.lev_K[l], Gn, vb);
+              const size_t piece = record_piece_rows(E.lev_nr[l], E.lev_K[l], Gn, vb, rcap);
               for (size_t t0 = 0; t0 < L_nr; t0 += piece) {
                 const size_t nr = std::min(piece, L_nr - t0);
                 const RecLayout R = layout_of(E, lower, l, t0, nr);
@@ -927,11 +934,15 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         const int l = rec_lev[rr];
         const size_t L_nr = E.lev_nr[l], K = E.lev_K[l];
         const size_t t0 = rec_t0[rr];
-        const size_t nr = std::min(size_t(record_piece_rows(E.lev_nr[l], E.lev_K[l], Gn, vb)), L_nr - t0);
+        const size_t nr = std::min(size_t(record_piece_rows(E.lev_nr[l], E.lev_K[l], Gn, vb, rcap)), L_nr - t0);
         const RecLayout R = layout_of(E, lower, l, t0, nr);
         const size_t base = size_t(rec_off16[rr]) * 16;
+        // word 5: the layout, plus kRecUpper for the records of the U sweep and
+        // kRecLevelEnd for the last record of each level
+        const bool level_end = t0 + nr == L_nr;
         const int hdr[8] = {static_cast<int>(nr), static_cast<int>(R.K), static_cast<int>(R.o_v),
-                            static_cast<int>(R.o_c), static_cast<int>(R.o_i), R.layout,
+                            static_cast<int>(R.o_c), static_cast<int>(R.o_i),
+                            R.layout | (lower ? 0 : kRecUpper) | (level_end ? kRecLevelEnd : 0),
                             static_cast<int>(R.end), 1};
         std::memcpy(&host[base], hdr, 32);
         std::memcpy(&host[base + R.o_l], &E.lrows[E.lev_start[l] + t0], 2 * nr);

@@ -94,9 +94,15 @@ SIGNATURES = {
     "gdsw_setup_batch": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(Options), C.c_void_p, C.POINTER(C.c_void_p)]),
     "gdsw_solve_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gdsw_batch_start": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "gdsw_batch_iterate": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "gdsw_batch_status": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gdsw_batch_finish": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(SolveInfo),
+                                    C.POINTER(C.c_int32), C.c_void_p]),
     "gdsw_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_apply_timed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "gdsw_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gdsw_pcg_iteration_timed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "gdsw_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
     "gdsw_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
     "gdsw_solve_host_zero_guess": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo),
@@ -112,6 +118,7 @@ SIGNATURES = {
                                       C.c_void_p]),
     "gdsw_spmv_dot_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gdsw_measure_fma_rate": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
     "gdsw_status_string": (C.c_char_p, [C.c_int]),
     "gdsw_last_error": (C.c_char_p, []),
 }
@@ -233,6 +240,34 @@ class Handle:
             _check(st, "gdsw_solve_batch")
         return list(infos)
 
+    # ---- continuous batching (members of a batched handle as solve slots) ----
+    def batch_start(self, member: int, b, stream=None):
+        """Start member `member` on right-hand side b (CUDA float64 tensor of its n entries)."""
+        _check(load().gdsw_batch_start(self._handle(), int(member), _ptr(b), _stream(stream)), "gdsw_batch_start")
+
+    def batch_iterate(self, iterations: int, stream=None):
+        """Enqueue `iterations` PCG iterations of every running member (asynchronous)."""
+        _check(load().gdsw_batch_iterate(self._handle(), int(iterations), _stream(stream)), "gdsw_batch_iterate")
+
+    def batch_status(self, stream=None):
+        """(done, iters, relres) arrays over the members (waits for the stream)."""
+        done = np.zeros(self.count, np.int32)
+        iters = np.zeros(self.count, np.int32)
+        rel = np.zeros(self.count, np.float64)
+        _check(load().gdsw_batch_status(self._handle(), done.ctypes.data, iters.ctypes.data, rel.ctypes.data,
+                                        _stream(stream)), "gdsw_batch_status")
+        return done, iters, rel
+
+    def batch_finish(self, member: int, x=None, stream=None):
+        """For a stopped member: (info, continued).  continued = True when its true
+        residual missed the tolerance and it went on iterating; otherwise x (CUDA
+        float64 tensor, or None) receives its solution."""
+        info = SolveInfo()
+        cont = C.c_int32()
+        _check(load().gdsw_batch_finish(self._handle(), int(member), _ptr(x) if x is not None else None,
+                                        C.byref(info), C.byref(cont), _stream(stream)), "gdsw_batch_finish")
+        return info, bool(cont.value)
+
     def _handle(self):
         if self._h is None:
             raise RuntimeError("handle destroyed")
@@ -247,6 +282,15 @@ class Handle:
         _check(load().gdsw_apply_timed(self._handle(), _ptr(r), _ptr(z), _stream(stream), ms),
                "gdsw_apply_timed")
         return list(ms)
+
+    PCG_KERNELS = ("spmv", "update", "local", "phiT", "coarse", "combine", "pupdate")
+
+    def pcg_iteration_timed(self, b, stream=None) -> dict:
+        """Device ms of each kernel of one PCG iteration from right-hand side b (CUDA events)."""
+        ms = (C.c_double * 7)()
+        _check(load().gdsw_pcg_iteration_timed(self._handle(), _ptr(b), _stream(stream), ms),
+               "gdsw_pcg_iteration_timed")
+        return dict(zip(self.PCG_KERNELS, list(ms)))
 
     def spmv(self, x, y, stream=None):
         _check(load().gdsw_spmv(self._handle(), _ptr(x), _ptr(y), _stream(stream)), "gdsw_spmv")
@@ -350,12 +394,31 @@ def _host_ptr(a) -> int:
     return a.ctypes.data
 
 
+def measure_fma_rate(precision: str = "fp64", stream=None) -> float:
+    """FMAs per second of the device in "fp64" or "fp32" (gdsw_measure_fma_rate)."""
+    out = C.c_double()
+    _check(load().gdsw_measure_fma_rate(PRECISION[precision], C.byref(out), _stream(stream)),
+           "gdsw_measure_fma_rate")
+    return out.value
+
+
 def spmv_dot_noalloc(rowptr, colind, val, x, y, dot, nnz: int, stream=None):
     """y = A x and dot[0] = (x, y) through gdsw_spmv_dot_noalloc (no device allocation).
 
-    rowptr/colind (int32) and val, x, y, dot (float64) are CUDA tensors owned by the caller.
+    rowptr/colind (int32) and val, x, y, dot (float64) are CUDA tensors owned by the caller;
+    their dtypes, sizes, layout and device are checked here, since the library reads the
+    raw pointers (a float32 vector or a short index array would be read out of bounds).
     """
+    import torch
     n = x.numel()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for name, t, dtype, size in (("rowptr", rowptr, torch.int32, n + 1), ("colind", colind, torch.int32, nnz),
+                                 ("val", val, torch.float64, nnz), ("x", x, torch.float64, n),
+                                 ("y", y, torch.float64, n), ("dot", dot, torch.float64, 1)):
+        if t.dtype != dtype or not t.is_contiguous() or t.device != dev:
+            raise ValueError(f"{name}: expected a contiguous {dtype} tensor on {dev}, got {t.dtype} on {t.device}")
+        if (t.numel() < size) if name == "dot" else (t.numel() != size):
+            raise ValueError(f"{name}: expected {size} elements, got {t.numel()}")
     _check(load().gdsw_spmv_dot_noalloc(n, int(nnz), rowptr.data_ptr(), colind.data_ptr(), _ptr(val),
                                         _ptr(x), _ptr(y), _ptr(dot), _stream(stream)),
            "gdsw_spmv_dot_noalloc")

@@ -15,6 +15,10 @@ The server admits them while others are on the GPU:
 
 All computation goes through the C ABI (gdsw.Handle); this module only
 schedules.  Latency = completion time - arrival time.
+
+`BatchServer` below goes further (continuous batching): the resident problems
+are solve slots of batched handles, and the iterations of all running requests
+are shared launches, with requests joining and leaving between iterations.
 """
 from __future__ import annotations
 
@@ -216,6 +220,157 @@ class Server:
             for e in self._resident.values():
                 e.handle.close()
             self._resident.clear()
+
+
+# ---------------------------------------------------------------------------
+# Continuous batching: solve slots of batched handles, shared launches
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Slot:
+    pool: int                 # index of the batched handle (problems of one kind share one)
+    member: int               # member of that handle
+    key: str                  # problem it holds (resident factors, Phi, A0^-1)
+    n: int
+
+
+def plan_slots(problems: List[tuple], budget_bytes: int, max_copies: int = 2) -> List[tuple]:
+    """Which problems become resident solve slots, and how many slots each gets.
+
+    problems: [(key, kind, nbytes)] in order of preference (e.g. expected demand);
+    kind groups problems that can share a batched handle (same unknowns per node).
+    First every problem gets one slot while the budget allows (problems that do not
+    fit are not admitted), then further copies round-robin up to `max_copies`, so
+    concurrent requests for one problem need not wait for each other.
+    Returns [(key, kind)] with one entry per slot."""
+    used = 0
+    slots = []
+    admitted = []
+    for key, kind, nb in problems:
+        if used + nb <= budget_bytes:
+            used += nb
+            slots.append((key, kind))
+            admitted.append((key, kind, nb))
+    for _copy in range(1, max_copies):
+        for key, kind, nb in admitted:
+            if used + nb <= budget_bytes:
+                used += nb
+                slots.append((key, kind))
+    return slots
+
+
+class BatchServer:
+    """Continuous batching of GDSW-PCG solves on one GPU.
+
+    The resident problems are the members (solve slots) of a few batched handles,
+    one per kind of problem (the unknowns per node must agree within a handle).
+    Every round, each handle with running members enqueues `iterations` PCG
+    iterations as shared launches (one SpMV and one launch per apply phase cover
+    all its running members; stopped and idle members only check a flag), the
+    handles' rounds run concurrently on their own streams, and between rounds the
+    host retires members that have converged and starts queued requests on free
+    slots.  A request therefore joins the running ones between iterations instead
+    of waiting for them, and its result does not depend on which others run with
+    it (members share no arithmetic).  Latency = completion time - arrival time.
+    """
+
+    def __init__(self, pools, slots: List[Slot], iterations: int = 4, keep_x: bool = False,
+                 stream_factory: Optional[Callable] = None):
+        self.pools = pools                      # gdsw.Handle (batched) per pool
+        self.slots = slots
+        self.iterations = iterations
+        self.keep_x = keep_x
+        self.stream_factory = stream_factory or _cuda_stream
+        self.rounds = 0
+        self.rejected = 0
+
+    def run(self, requests: List[Request]) -> List[Result]:
+        import torch
+        streams = [self.stream_factory() for _ in self.pools]
+        free: Dict[str, List[int]] = {}
+        for i, sl in enumerate(self.slots):
+            free.setdefault(sl.key, []).append(i)
+        for v in free.values():
+            v.reverse()                           # pop() hands out the lowest slot first
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        queue: List[Request] = []
+        active: Dict[int, tuple] = {}           # slot -> (request, admitted at, device b)
+        results: List[Result] = []
+        t0 = time.perf_counter()
+        pi = 0
+        while pi < len(pending) or queue or active:
+            now = time.perf_counter() - t0
+            while pi < len(pending) and pending[pi].arrival <= now:
+                req = pending[pi]
+                pi += 1
+                if req.key in free:
+                    queue.append(req)
+                else:                           # problem not admitted (memory budget)
+                    self.rejected += 1
+                    results.append(Result(req.rid, req.key, req.arrival, now, now, 0.0, 0, float("nan"), False))
+            # first come, first served per problem; a request whose problem has no
+            # free slot does not hold back requests for other problems
+            waiting = []
+            for req in queue:
+                ids = free[req.key]
+                if not ids:
+                    waiting.append(req)
+                    continue
+                sid = ids.pop()
+                sl = self.slots[sid]
+                st = streams[sl.pool]
+                with torch.cuda.stream(st):
+                    bd = torch.from_numpy(np.ascontiguousarray(req.b, dtype=np.float64)).to("cuda", non_blocking=False)
+                self.pools[sl.pool].batch_start(sl.member, bd, stream=st)
+                active[sid] = (req, time.perf_counter() - t0, bd)
+            queue = waiting
+            if not active:
+                if pi < len(pending):
+                    delay = pending[pi].arrival - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                continue
+            busy = sorted({self.slots[sid].pool for sid in active})
+            for p in busy:
+                self.pools[p].batch_iterate(self.iterations, stream=streams[p])
+            self.rounds += 1
+            for p in busy:
+                done, _iters, _rel = self.pools[p].batch_status(stream=streams[p])
+                for sid in [s for s in active if self.slots[s].pool == p]:
+                    sl = self.slots[sid]
+                    if not done[sl.member]:
+                        continue
+                    x = torch.empty(sl.n, dtype=torch.float64, device="cuda") if self.keep_x else None
+                    info, cont = self.pools[p].batch_finish(sl.member, x, stream=streams[p])
+                    if cont:
+                        continue
+                    req, t_adm, _bd = active.pop(sid)
+                    free[sl.key].append(sid)
+                    t_end = time.perf_counter() - t0
+                    results.append(Result(req.rid, req.key, req.arrival, t_adm, t_end, 0.0, info.iters,
+                                          info.true_relres, bool(info.converged),
+                                          x.cpu().numpy() if x is not None else None))
+        results.sort(key=lambda r: r.rid)
+        return results
+
+
+def build_pools(problems: Dict[str, tuple], slot_plan: List[tuple], stream=None, **options):
+    """Batched handles for a slot plan: problems[key] = (A, part, Z or None);
+    slot_plan = [(key, kind)] (plan_slots).  Returns (pools, slots)."""
+    from . import gdsw
+    kinds: Dict[object, List[str]] = {}
+    for key, kind in slot_plan:
+        kinds.setdefault(kind, []).append(key)
+    pools, slots = [], []
+    for kind, keys in kinds.items():
+        if len(keys) == 1:                      # a batched handle has two members at least
+            keys = keys + keys
+        members = [problems[k] for k in keys]
+        h = gdsw.Handle.batch(members, stream=stream, **options)
+        for m, k in enumerate(keys):
+            slots.append(Slot(len(pools), m, k, int(members[m][0].n)))
+        pools.append(h)
+    return pools, slots
 
 
 def _cuda_stream():

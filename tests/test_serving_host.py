@@ -128,3 +128,15 @@ def test_worker_errors_are_raised():
     srv = S.Server(bad_make, lambda k: 1, 10, workers=2, solve_fn=lambda *a: None, stream_factory=lambda: None)
     with pytest.raises(RuntimeError):
         srv.run([S.Request(0.0, 0, "a", np.ones(1))])
+
+
+def test_plan_slots_admits_by_budget_then_adds_copies():
+    """Every problem gets one slot while the budget allows (in order; one that does
+    not fit is left out), then second copies round-robin while they fit."""
+    probs = [("a", 1, 40), ("b", 3, 30), ("c", 1, 50), ("d", 1, 10)]
+    plan = S.plan_slots(probs, budget_bytes=100, max_copies=2)
+    assert plan[:3] == [("a", 1), ("b", 3), ("d", 1)]          # c (50) does not fit after a, b
+    assert plan[3:] == [("d", 1)]                               # 80 used: only d's copy (10) fits
+    assert S.plan_slots(probs, budget_bytes=0) == []
+    big = S.plan_slots(probs, budget_bytes=10 ** 6, max_copies=3)
+    assert [k for k, _ in big].count("a") == 3 and len(big) == 12
