@@ -84,7 +84,7 @@ enum { GDSW_COARSE_GDSW = 0, GDSW_COARSE_NONE = 1, GDSW_COARSE_RGDSW = 2 };
  * reduction of V^T w and (w, w), the norm by Pythagoras, a second pass only
  * when that cancels).  The single-reduce form loses orthogonality faster, so
  * its least-squares residual can lag the true one and take more steps. */
-enum { GDSW_GMRES_ORTH_CGS2 = 0, GDSW_GMRES_ORTH_SINGLE = 1 };
+enum { GDSW_GMRES_ORTH_CGS2 = 0, GDSW_GMRES_ORTH_SINGLE = 1, GDSW_GMRES_ORTH_DCGS2 = 2 };
 
 /* Where the arrays of a gdsw_csr live. */
 enum { GDSW_MEM_HOST = 0, GDSW_MEM_DEVICE = 1 };
@@ -178,6 +178,12 @@ typedef struct {
   double setup_phase_seconds[8]; /* [0] symbolic [1] local factors [2] Phi_Gamma
                                     [3] Phi_I [4] A0 [5] A0^-1 [6] exact local
                                     [7] Krylov workspace and graph            */
+  int64_t local_kernel;   /* local solve chosen at setup: 0 dense inverses,
+                             1 multifrontal, 2 level-sliced ELL read through
+                             L2 (level-scheduled or Jacobi), 3 level records
+                             streamed with a barrier per level, 4 the same
+                             without one (per-row flags), 5 Jacobi sweeps on
+                             blocks resident in shared memory              */
 } gdsw_stats;
 
 typedef struct gdsw_ctx* gdsw_handle;

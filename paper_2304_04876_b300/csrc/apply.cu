@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
 #include <type_traits>
 
 #include <cuda_fp16.h>
@@ -281,10 +282,18 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
   }
 }
 
-// The pipelined local solve runs NT consumer threads (128 to 992, chosen at
+// The pipelined local solve runs NT consumer threads (64 to 512, chosen at
 // setup) that update the rows, plus one producer warp that only streams the
-// level records into the ring.
-constexpr int kPipeMaxThreads = 1024;
+// level records into the ring (at most 544 threads, so a thread may hold up to
+// 112 registers: the gather keeps 32 values in flight and a level's row data
+// is loaded ahead of its barrier).
+constexpr int kPipeMaxThreads = 544;
+
+// Barrier of the `nt` consumer threads only (named barrier 1), every warp
+// arriving whole at the same instruction.
+__device__ __forceinline__ void consumers_sync_aligned(int nt) {
+  asm volatile("barrier.cta.sync.aligned 1, %0;" ::"r"(nt) : "memory");
+}
 
 // Barrier of the `nt` consumer threads only (named barrier 1), returning the
 // OR of `pred` over them.
@@ -300,7 +309,8 @@ __device__ __forceinline__ bool consumers_sync_or(bool pred, int nt) {
 }
 
 // v = R_s r from indices already staged in shared memory (`idx`: this
-// subdomain's slice of the overlap map), sixteen values in flight per thread.
+// subdomain's slice of the overlap map), 32 values in flight per thread (16
+// for FP64 vectors, whose kernels have more live registers).
 // For FP32 vectors `idx` and `v` share their words: each thread reads and
 // writes only its own positions.  For FP64 `idx` sits in the upper half of
 // the vector's space, and a barrier between the index reads and the value
@@ -309,7 +319,7 @@ __device__ __forceinline__ bool consumers_sync_or(bool pred, int nt) {
 template <class T>
 __device__ __forceinline__ void gather_staged(const double* __restrict__ r, const int* idx, T* v, int m,
                                               int nt) {
-  constexpr int U = 16;
+  constexpr int U = sizeof(T) == 4 ? 32 : 16;
   const int tid = threadIdx.x;
   for (int i0 = 0; i0 < m; i0 += U * nt) {
     double rv[U];
@@ -325,6 +335,49 @@ __device__ __forceinline__ void gather_staged(const double* __restrict__ r, cons
       if (i < m) v[i] = T(rv[u]);
     }
   }
+}
+
+// The row-invariant data of one level record whose rows are row-major by 4
+// (layout 1, one thread per row, at most NT rows): loaded before the barrier
+// that precedes the record's level, so that after it only the reads of the
+// solution values remain on the level's critical path.
+template <class T>
+struct RowAhead {
+  int row;
+  ushort4 c;
+  T a[4];
+  T d;
+  bool on;
+};
+
+template <class T, class TS>
+__device__ __forceinline__ bool row_ahead_load(const unsigned char* rec, int nt, RowAhead<T>& p) {
+  const int4 hdr = *reinterpret_cast<const int4*>(rec);
+  const int layout = reinterpret_cast<const int*>(rec)[5] & 0xff;
+  const int nr = hdr.x;
+  if (layout != 1 || nr > nt) return false;
+  const int t = threadIdx.x;
+  p.on = t < nr;
+  if (p.on) {
+    const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 32);
+    const TS* dinv = reinterpret_cast<const TS*>(rec + 32 + ((2 * nr + 15) & ~15));
+    p.row = lrows[t];
+    p.c = reinterpret_cast<const ushort4*>(rec + hdr.w)[t];
+    load4<T, TS>(reinterpret_cast<const TS*>(rec + hdr.z), t, p.a);
+    p.d = load_as<T, TS>(dinv, t);
+  }
+  return true;
+}
+
+template <class T>
+__device__ __forceinline__ void row_ahead_apply(const RowAhead<T>& p, T* v) {
+  if (!p.on) return;
+  T acc = v[p.row];
+  acc = fma(-p.a[0], v[p.c.x], acc);
+  acc = fma(-p.a[1], v[p.c.y], acc);
+  acc = fma(-p.a[2], v[p.c.z], acc);
+  acc = fma(-p.a[3], v[p.c.w], acc);
+  v[p.row] = acc * p.d;
 }
 
 // Shared memory of the pipelined solve's local vector: m values plus the room
@@ -415,7 +468,7 @@ __device__ __forceinline__ void pipe_producer(const int* __restrict__ om_dofs, i
 // levels in shared memory with one barrier per level, and release the stage.
 // The copy issue is off the consumers' path.
 template <class T, class TS, int S, int TPR>
-__global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __restrict__ r,
+__global__ void __launch_bounds__(kPipeMaxThreads, 1) k_local_pipe(const double* __restrict__ r,
                                                              const int* __restrict__ om_ptr,
                                                              const int* __restrict__ om_dofs,
                                                              const int* __restrict__ rec_ptr,
@@ -430,6 +483,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
   __shared__ __align__(8) uint64_t full[S];
   __shared__ __align__(8) uint64_t empty[S];
   __shared__ __align__(8) uint64_t gbar;    // the staged overlap indices have landed
+  __shared__ int s_fail;                     // a consumer's wait ran out
   if (ks != nullptr && ks->done) return;
   const int s = blockIdx.x;
   if (gate_sub_off(gate, s)) return;
@@ -453,6 +507,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
       mbar_init(&empty[j], nt / 32);         // one arrival per consumer warp
     }
     mbar_init(&gbar, 1);
+    s_fail = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -470,14 +525,16 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
     }
   }
   gather_staged(r, idx, v, m, nt);
-  consumers_sync_or(false, nt);
+  consumers_sync_aligned(nt);
+  volatile int* fail = &s_fail;
   for (int i = 0; i < nrec; ++i) {
     const int st = i % S;
     // each thread waits for the pack itself, then all agree that it has
-    // landed before any reads it (the barrier carries a wait that ran out to
-    // every consumer)
-    const bool ok = mbar_wait_bounded(&full[st], (i / S) & 1, wait_cycles);
-    if (consumers_sync_or(!ok, nt)) {
+    // landed before any reads it: a wait that runs out raises the CTA's
+    // failure flag before the barrier, and every thread reads it after
+    if (!mbar_wait_bounded(&full[st], (i / S) & 1, wait_cycles)) *fail = 1;
+    consumers_sync_aligned(nt);
+    if (*fail) {
       if (threadIdx.x == 0) atomicOr(err, 1);
       return;
     }
@@ -486,16 +543,24 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_pipe(const double* __
     // after its last record
     const unsigned char* rec = stages + size_t(st) * stage_bytes;
     const int count = reinterpret_cast<const int*>(rec)[7];
+    RowAhead<T> ahead;
+    bool have_ahead = false;
     for (int q = 0; q < count; ++q) {
       const unsigned char* next = rec + reinterpret_cast<const int*>(rec)[6];
       const bool level_end = (reinterpret_cast<const int*>(rec)[5] & kRecLevelEnd) != 0;
-      level_rows<T, TS, TPR>(rec, v, nt, grp);
+      if (have_ahead) row_ahead_apply(ahead, v);
+      else level_rows<T, TS, TPR>(rec, v, nt, grp);
+      // the next record of this pack: its row data before the barrier
+      have_ahead = false;
+      if constexpr (TPR == 1) {
+        if (q + 1 < count) have_ahead = row_ahead_load<T, TS>(next, nt, ahead);
+      }
       // each warp releases the stage as soon as its lanes are done reading it
       if (q + 1 == count) {
         __syncwarp();
         if ((threadIdx.x & 31) == 0 && i + S < nrec) mbar_arrive(&empty[st]);
       }
-      if (level_end) consumers_sync_or(false, nt);
+      if (level_end) consumers_sync_aligned(nt);
       rec = next;
     }
   }
@@ -626,11 +691,24 @@ __device__ __forceinline__ bool sf_record(const unsigned char* rec, T* v, unsign
   return true;
 }
 
+// Dynamic shared memory of the resident-block Jacobi solve: the slots (one
+// block of each kind in mode 2, the largest block in mode 1) and three vectors.
+inline size_t jac_slot_a(const Ctx* c, int mode) {
+  const size_t a = size_t(mode == 2 ? c->jac_max_bytes[0] : std::max(c->jac_max_bytes[0], c->jac_max_bytes[1]));
+  return (a + 127) & ~size_t(127);
+}
+inline size_t jac_slot_b(const Ctx* c, int mode) {
+  return mode == 2 ? (size_t(c->jac_max_bytes[1]) + 127) & ~size_t(127) : 0;
+}
+inline size_t jac_smem(const Ctx* c, int mode, size_t es) {
+  return jac_slot_a(c, mode) + jac_slot_b(c, mode) + 3 * size_t(c->max_m) * es;
+}
+
 // Shared memory of the per-row flags (one byte per local row, 16-byte padded).
 inline size_t sf_flag_bytes(int max_m) { return (size_t(max_m) + 15) & ~size_t(15); }
 
 template <class T, class TS, int S>
-__global__ void __launch_bounds__(kPipeMaxThreads) k_local_sf(const double* __restrict__ r,
+__global__ void __launch_bounds__(kPipeMaxThreads, 1) k_local_sf(const double* __restrict__ r,
                                                            const int* __restrict__ om_ptr,
                                                            const int* __restrict__ om_dofs,
                                                            const int* __restrict__ rec_ptr,
@@ -724,6 +802,132 @@ __global__ void __launch_bounds__(kPipeMaxThreads) k_local_sf(const double* __re
   consumers_sync(nt);
   if (*fail) return;
   for (int i = threadIdx.x; i < m; i += nt) zloc[base + i] = v[i];
+}
+
+// ---- Jacobi sweeps on resident blocks (Sec. V-B3, FastSpTRSV) ----
+//
+// Persistent CTAs (one per SM) take subdomains blockIdx.x, + gridDim.x, ...
+// For each, r_s is gathered into shared memory, its L block (one bulk copy
+// into slot A, see the setup) is swept from y0 = D^-1 r_s, then its U block
+// from the L result, and z_s is written out.  Mode 2: U_s arrives in slot B
+// while L_s is swept, and the next subdomain's L block in A while U_s is swept,
+// so every factor byte is read from HBM once per apply and its copy overlaps
+// the sweeps.  Mode 1 (two blocks do not fit): one slot takes L_s, U_s, the
+// next L in turn.  Each sweep updates every row from the previous iterate in
+// the order of the unpipelined Jacobi kernel, so the results are the same.
+// Every wait is bounded; a wait that runs out sets err[0], and the copies in
+// flight land before the CTA returns.
+
+// `sweeps` Jacobi sweeps on T y = rhs with the block in shared memory:
+// y0 = D^-1 rhs, y_{k+1} = D^-1 (rhs - (T - D) y_k); returns the buffer
+// holding the result (y0 or y1).
+template <class T, class TS>
+__device__ __forceinline__ T* jac_block_sweeps(const unsigned char* blk, const T* rhs, T* y0, T* y1, int sweeps) {
+  const int4 hdr = *reinterpret_cast<const int4*>(blk);
+  const int m = hdr.x, K = hdr.y;
+  const TS* dinv = reinterpret_cast<const TS*>(blk + 16);
+  const TS* vals = reinterpret_cast<const TS*>(blk + hdr.z);
+  const uint16_t* cols = reinterpret_cast<const uint16_t*>(blk + hdr.w);
+  const int nt = blockDim.x;
+  for (int i = threadIdx.x; i < m; i += nt) y0[i] = rhs[i] * load_as<T, TS>(dinv, i);
+  __syncthreads();
+  T* yo = y0;
+  T* yn = y1;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int i = threadIdx.x; i < m; i += nt) {
+      T acc = rhs[i];
+      for (int k = 0; k < K; ++k) acc -= load_as<T, TS>(vals, k * m + i) * yo[cols[k * m + i]];
+      yn[i] = acc * load_as<T, TS>(dinv, i);
+    }
+    __syncthreads();
+    T* t = yo;
+    yo = yn;
+    yn = t;
+  }
+  return yo;
+}
+
+template <class T, class TS, int MODE>
+__global__ void __launch_bounds__(1024, 1) k_local_jac(const double* __restrict__ r,
+                                                      const int* __restrict__ om_ptr,
+                                                      const int* __restrict__ om_dofs,
+                                                      const uint8_t* __restrict__ stream,
+                                                      const uint32_t* __restrict__ off16,
+                                                      const uint32_t* __restrict__ bytes, int slot_a, int slot_b,
+                                                      int max_m, int nsub, int sweeps, T* __restrict__ zloc,
+                                                      const KrylovScalars* __restrict__ ks, int* err,
+                                                      long long wait_cycles, BatchGate gate, int stall_test) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  if (ks != nullptr && ks->done) return;
+  // slot_a, slot_b: the slots' sizes in bytes (slot_b 0 in mode 1)
+  unsigned char* slot[2] = {smem_raw, MODE == 2 ? smem_raw + slot_a : smem_raw};
+  T* buf0 = reinterpret_cast<T*>(smem_raw + slot_a + slot_b);
+  T* buf1 = buf0 + max_m;
+  T* buf2 = buf1 + max_m;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int su = MODE == 2 ? 1 : 0;            // slot of the U blocks
+  unsigned ph[2] = {0, 0};                     // parity of the next completion of each slot
+  bool pending[2] = {false, false};            // thread 0: a copy into the slot is in flight
+  auto issue = [&](int sl, int q, int side) {  // thread 0
+    const uint32_t nb = bytes[2 * q + side];
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[sl], nb);
+    bulk_g2s(slot[sl], stream + size_t(off16[2 * q + side]) * 16, nb, &bar[sl]);
+    pending[sl] = true;
+  };
+  auto live = [&](int q) {                     // the next subdomain at or after q that is not gated off
+    while (q < nsub && gate_sub_off(gate, q)) q += gridDim.x;
+    return q;
+  };
+  int s = live(blockIdx.x);
+  if (threadIdx.x == 0 && s < nsub) {
+    // (failure test: CTA 0's first copy is never issued, so its wait runs out)
+    if (!(stall_test && blockIdx.x == 0)) issue(0, s, 0);
+    if (MODE == 2) issue(1, s, 1);
+  }
+  bool failed = false;
+  while (s < nsub) {
+    const int nx = live(s + int(gridDim.x));
+    const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+    gather_sub(r, om_dofs, base, m, buf0, threadIdx.x, blockDim.x);
+    bool ok = mbar_wait_bounded(&bar[0], ph[0], wait_cycles);
+    ph[0] ^= 1u;
+    if (threadIdx.x == 0 && ok) pending[0] = false;
+    if (__syncthreads_or(!ok)) { failed = true; break; }
+    T* yl = jac_block_sweeps<T, TS>(slot[0], buf0, buf1, buf2, sweeps);
+    // (the sweeps end with a barrier: slot A is free for its next block)
+    if (threadIdx.x == 0) {
+      if (MODE == 2) { if (nx < nsub) issue(0, nx, 0); }
+      else issue(0, s, 1);
+    }
+    ok = mbar_wait_bounded(&bar[su], ph[su], wait_cycles);
+    ph[su] ^= 1u;
+    if (threadIdx.x == 0 && ok) pending[su] = false;
+    if (__syncthreads_or(!ok)) { failed = true; break; }
+    T* other = yl == buf1 ? buf2 : buf1;
+    const T* yu = jac_block_sweeps<T, TS>(slot[su], yl, buf0, other, sweeps);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) zloc[base + i] = yu[i];
+    __syncthreads();                            // every read of the slot and buffers done
+    if (threadIdx.x == 0 && nx < nsub) {
+      if (MODE == 2) issue(1, nx, 1);
+      else issue(0, nx, 0);
+    }
+    s = nx;
+  }
+  if (threadIdx.x == 0) {
+    if (failed) atomicOr(err, 1);
+    // copies still in flight land before the shared memory goes away (waited
+    // for with at least the default bound)
+    const long long drain = wait_cycles > kDefaultWaitCycles ? wait_cycles : kDefaultWaitCycles;
+    for (int sl = 0; sl < 2; ++sl)
+      if (pending[sl]) mbar_wait_bounded(&bar[sl], ph[sl], drain);
+  }
 }
 
 // Exact local solver: z_s = A_s^-1 r_s with the stored dense inverse
@@ -1122,6 +1326,22 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
       }
     }
 #undef GDSW_PIPE_LAUNCH
+  } else if (c->jac_mode > 0) {
+    const size_t shm = jac_smem(c, c->jac_mode, sizeof(T));
+    const int grid = std::min(c->nsub, c->jac_grid);
+#define GDSW_JAC_LAUNCH(TS, MODE)                                                                         \
+  k_local_jac<T, TS, MODE><<<grid, c->jac_threads, shm, s>>>(                                            \
+      r, c->om_ptr, c->om_dofs, c->jac_stream, c->jac_off16, c->jac_bytes,                               \
+      static_cast<int>(jac_slot_a(c, c->jac_mode)), static_cast<int>(jac_slot_b(c, c->jac_mode)),        \
+      c->max_m, c->nsub, c->opt.sweeps_trsv, zl, ks, c->derr, c->wait_cycles, gate, c->stall_test)
+    if (c->fp16) {
+      if constexpr (std::is_same<T, float>::value) {
+        if (c->jac_mode == 2) GDSW_JAC_LAUNCH(__half, 2); else GDSW_JAC_LAUNCH(__half, 1);
+      }
+    } else {
+      if (c->jac_mode == 2) GDSW_JAC_LAUNCH(T, 2); else GDSW_JAC_LAUNCH(T, 1);
+    }
+#undef GDSW_JAC_LAUNCH
   } else {
     const int jac = c->opt.trsv == GDSW_TRSV_JACOBI;
     const size_t shm = size_t(c->max_m) * sizeof(T) * (jac ? 3 : 1);
@@ -1284,7 +1504,7 @@ gdsw_status tune_local(Ctx* c) {
   const int n_kinds = c->rec_tpr == 1 ? 2 : 1;
   for (int kind = 0; kind < n_kinds && st == GDSW_OK; ++kind)
   for (int q = 0; q < 4 && st == GDSW_OK; ++q) {
-    for (int nt : {64, 128, 256, 512, 992}) {
+    for (int nt : {64, 128, 256, 512}) {
       if (c->rec_tpr == 8 && nt < 256) continue;
       c->rec_stages = cand[q];
       c->rec_consumers = nt;
@@ -1333,6 +1553,70 @@ gdsw_status tune_local(Ctx* c) {
   if (r) cudaFree(r);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (st == GDSW_OK) st = check_device_errors(c, nullptr);
+  return st;
+}
+
+// Resident CTAs per SM of the resident-block Jacobi kernel (raises its
+// dynamic shared memory limit first; 0 when it does not fit).
+template <class TT, class TS>
+gdsw_status jac_occupancy_t(int mode, size_t shm, int threads, int* per_sm) {
+  *per_sm = 0;
+  auto one = [&](auto kernel) -> gdsw_status {
+    GDSW_CK(allow_max_dynamic_smem(kernel));
+    cudaFuncAttributes fa;
+    GDSW_CK(cudaFuncGetAttributes(&fa, kernel));
+    if (shm + fa.sharedSizeBytes > size_t(max_block_smem_optin())) return GDSW_OK;
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, shm));
+    return GDSW_OK;
+  };
+  return mode == 2 ? one(k_local_jac<TT, TS, 2>) : one(k_local_jac<TT, TS, 1>);
+}
+
+gdsw_status jac_occupancy(const Ctx* c, int mode, size_t shm, int threads, int* per_sm) {
+  if (c->fp16) return jac_occupancy_t<float, __half>(mode, shm, threads, per_sm);
+  if (c->fp32) return jac_occupancy_t<float, float>(mode, shm, threads, per_sm);
+  return jac_occupancy_t<double, double>(mode, shm, threads, per_sm);
+}
+
+// Threads of the resident-block Jacobi solve, chosen by timing (three launches
+// each after a warm-up, on a zero right-hand side); every choice computes the
+// same values.
+gdsw_status tune_jacobi(Ctx* c) {
+  cudaStream_t s;
+  GDSW_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  double* r = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  gdsw_status st = GDSW_OK;
+  cudaError_t e = cudaMalloc(&r, sizeof(double) * std::max(1, c->n));
+  if (e == cudaSuccess) e = cudaMemsetAsync(r, 0, sizeof(double) * std::max(1, c->n), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { set_error("Jacobi tuning: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; }
+  float best = 3.4e38f;
+  int best_t = c->jac_threads;
+  for (int th : {256, 512, 1024}) {
+    if (st != GDSW_OK) break;
+    c->jac_threads = th;
+    auto one = [&]() {
+      return c->fp32 ? launch_local<float>(c, r, s, nullptr, BatchGate{})
+                     : launch_local<double>(c, r, s, nullptr, BatchGate{});
+    };
+    st = one();
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep) st = one();
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { set_error("Jacobi tuning: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; break; }
+    if (ms < best) { best = ms; best_t = th; }
+  }
+  c->jac_threads = best_t;
+  if (r) cudaFree(r);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   cudaStreamDestroy(s);
   if (st == GDSW_OK) st = check_device_errors(c, nullptr);
   return st;
@@ -1396,6 +1680,32 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(allow_max_dynamic_smem(k_local_tri<double>));
     GDSW_CK(allow_max_dynamic_smem(k_local_dense<double>));
   }
+  // resident-block Jacobi sweeps: mode 2 when an L and a U block fit beside
+  // the vectors, else mode 1; GDSW_JACOBI_RESIDENT=0 keeps the unpipelined
+  // Jacobi kernel (which reads the factors from L2/HBM on every sweep)
+  c->jac_mode = 0;
+  if (c->jac_stream != nullptr && !(getenv("GDSW_JACOBI_RESIDENT") && getenv("GDSW_JACOBI_RESIDENT")[0] == '0')) {
+    int dev = 0, sms = kNumSMs;
+    GDSW_CK(cudaGetDevice(&dev));
+    GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int force = getenv("GDSW_JACOBI_MODE") ? atoi(getenv("GDSW_JACOBI_MODE")) : 0;
+    for (int mode : {2, 1}) {
+      if (force != 0 && mode != force) continue;
+      const size_t shm = jac_smem(c, mode, es);
+      int per_sm = 0;
+      GDSW_TRY(jac_occupancy(c, mode, shm, c->jac_threads, &per_sm));
+      if (per_sm > 0) {
+        c->jac_mode = mode;
+        c->jac_grid = sms * per_sm;
+        break;
+      }
+    }
+    if (c->jac_mode > 0 && c->opt.autotune && !getenv("GDSW_LOCAL_SHAPE")) GDSW_TRY(tune_jacobi(c));
+    if (const char* e = getenv("GDSW_LOCAL_SHAPE")) {
+      int st = 0, nt = 0;
+      if (sscanf(e, "%d,%d", &st, &nt) == 2 && (nt == 256 || nt == 512 || nt == 1024)) c->jac_threads = nt;
+    }
+  }
   // records prefetched into L2 ahead of the ring (bytes per subdomain);
   // GDSW_PIPE_PREFETCH overrides the default
   c->rec_prefetch = 0;
@@ -1411,9 +1721,9 @@ gdsw_status apply_configure(Ctx* c) {
     int st = 0, nt = 0, sf = 0;
     const int got = sscanf(shape, "%d,%d,%d", &st, &nt, &sf);
     if (got >= 2 && (st == 0 || st == 2 || st == 4 || st == 8 || st == 16) &&
-        (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 992 || nt == 1024)) {
+        (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 1024)) {
       c->rec_stages = st;
-      if (st > 0) c->rec_consumers = nt == 1024 ? 992 : nt; else c->tri_threads = nt == 992 ? 1024 : nt;
+      if (st > 0) c->rec_consumers = nt == 1024 ? 512 : nt; else c->tri_threads = nt;
       c->rec_sf = st > 0 && got == 3 && sf == 1 && c->rec_tpr == 1;
       int per_sm = 0;
       if (st > 0) GDSW_TRY(pipe_occupancy(c, st, c->rec_sf, &per_sm));

@@ -58,7 +58,7 @@ bool valid_options(const gdsw_options* o) {
          o->precision <= 2 && o->krylov >= 0 && o->krylov <= 1 && o->restart >= 1 &&
          o->maxit >= 1 && o->coarse >= 0 && o->coarse <= 2 && o->tol > 0.0 && o->wait_budget_cycles >= 0 &&
          o->fill_level >= 0 && (o->fill_level == 0 || o->local_solver != GDSW_LOCAL_EXACT) &&
-         (o->autotune == 0 || o->autotune == 1) && (o->gmres_orth == 0 || o->gmres_orth == 1);
+         (o->autotune == 0 || o->autotune == 1) && (o->gmres_orth >= 0 && o->gmres_orth <= 2);
 }
 }  // namespace
 
@@ -215,7 +215,9 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
   S.device_bytes = static_cast<int64_t>(c->bytes);
   S.n_problems = P.nprob;
   S.local_stages = c->rec_stages;
-  S.local_threads = c->rec_stages > 0 ? c->rec_consumers : c->tri_threads;
+  S.local_threads = c->jac_mode > 0 ? c->jac_threads : c->rec_stages > 0 ? c->rec_consumers : c->tri_threads;
+  S.local_kernel = c->mf ? 1 : o.local_solver == GDSW_LOCAL_EXACT ? 0 : c->jac_mode > 0 ? 5
+                 : c->rec_stages > 0 ? (c->rec_sf ? 4 : 3) : 2;
   S.setup_seconds = now_s() - t0;
   *out = h;
   return GDSW_OK;

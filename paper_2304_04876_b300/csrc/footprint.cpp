@@ -40,6 +40,28 @@ int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec) {
   return total;
 }
 
+// Bytes of the resident Jacobi blocks (one per subdomain and triangle: header,
+// inverse diagonal, values and columns at the subdomain's widest row).
+int64_t jacobi_block_bytes(const Plan& P, int64_t vb) {
+  int64_t total = 16;
+  for (int q = 0; q < P.nsub; ++q) {
+    const int64_t m = P.om_ptr[q + 1] - P.om_ptr[q];
+    for (int side = 0; side < 2; ++side) {
+      const EllPlan& E = side == 0 ? P.L : P.U;
+      if (E.sub_lev.empty()) continue;
+      int64_t K = 0;
+      for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l)
+        for (int t = 0; t < E.lev_nr[l]; ++t) {
+          int64_t w = 0;
+          for (int k = 0; k < E.lev_K[l]; ++k) w += E.src[E.lev_off[l] + int64_t(k) * E.lev_nr[l] + t] >= 0;
+          K = std::max(K, w);
+        }
+      total += 16 + a16(m * vb) + a16(K * m * vb) + a16(2 * K * m);
+    }
+  }
+  return total;
+}
+
 gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
                                int64_t* scratch_peak) {
   const bool exact = o.local_solver == GDSW_LOCAL_EXACT;
@@ -65,6 +87,7 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
     }
     int64_t nrec = 0;
     R += arr(record_stream_bytes(P, vrec, &nrec), 1) + arr(nsub + 1, 4) + 2 * arr(nrec, 4);
+    if (o.trsv == GDSW_TRSV_JACOBI) R += arr(jacobi_block_bytes(P, vrec), 1) + 2 * arr(2 * nsub, 4);
   } else if (P.max_m > exact_dense_max() || [&] {
                int64_t d = 0;
                for (int q = 0; q < P.nsub; ++q) d += int64_t(P.om_ptr[q + 1] - P.om_ptr[q]) * (P.om_ptr[q + 1] - P.om_ptr[q]);
@@ -123,8 +146,11 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
   // Krylov workspace: six vectors, the reduction buffer, scalars; GMRES basis
   // (reduction buffer: partials of any SpMV grid, at most 32 CTAs per SM)
   R += 6 * arr(n, 8) + arr(2 * (nsub + int64_t(P.ncomp)) + 32 * 148 + 64, 8) + 256;
+  // GMRES: basis and preconditioned directions, its state, and the reduction
+  // buffer of its fused dot products (2 restart + 4 partial sums per CTA)
   if (o.krylov == GDSW_KRYLOV_GMRES)
-    R += (2 * int64_t(o.restart) + 1) * arr(n, 8) + arr(o.restart + 2, 8) + (int64_t(o.restart) + 2) * 10000;
+    R += (2 * int64_t(o.restart) + 1) * arr(n, 8) + arr(o.restart + 2, 8) + (int64_t(o.restart) + 2) * 10000 +
+         arr((2 * int64_t(o.restart) + 4) * 148 * 8 + 64, 8);
   // batched handles: tiles, per-problem states, the problem of each
   // subdomain, Phi block and unknown range
   if (P.nprob > 1)

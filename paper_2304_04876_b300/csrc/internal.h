@@ -395,6 +395,14 @@ struct Ctx {
   int rec_prefetch = 0;              // bytes of records kept on their way into L2 ahead of the ring
   bool rec_sf = false;               // pipelined solve without a barrier per level (per-row flags)
   int tri_threads = 256;             // threads of the unpipelined level / Jacobi solve
+  // resident Jacobi blocks (see the setup): per subdomain L then U
+  uint8_t* jac_stream = nullptr;
+  uint32_t* jac_off16 = nullptr;     // 2*nsub: block offsets in 16-byte units
+  uint32_t* jac_bytes = nullptr;     // 2*nsub: block sizes
+  int jac_max_bytes[2] = {0, 0};     // largest L / U block
+  int jac_mode = 0;                  // 0 off, 1 one block resident at a time, 2 the next one arriving meanwhile
+  int jac_threads = 1024;            // threads of the resident-block Jacobi kernel (chosen by timing)
+  int jac_grid = kNumSMsForCtx;      // its persistent CTAs
   int* derr = nullptr;               // device error flags (bounded waits that ran out)
   long long wait_cycles = 0;         // bound on each device-side wait, SM clock cycles
   int stall_test = 0;                // failure test: one record copy withheld
@@ -484,7 +492,8 @@ struct Ctx {
   cudaStream_t bgraph_stream = nullptr;
   int spmv_R = 256, spmv_maxne = 1, spmv_tiles = 1, spmv_grid = kNumSMsForCtx;
   int spmv_W = 0;                    // lanes per row for long rows (0: the tiled kernel)
-  int spmv_pipe = 0;                 // tiled kernel with the next tile's loads in flight (chosen by timing)
+  int spmv_pipe = 0;                 // SpMV kernel for short rows (chosen by timing): 0 tiled, 1 tiled with
+                                     // the next tile's loads in flight, 2 a thread per row
 };
 
 template <class T>

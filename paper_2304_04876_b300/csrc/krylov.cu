@@ -197,6 +197,55 @@ __global__ void __launch_bounds__(R, 2048 / R / 2) k_spmv_pipe(int n, int ntiles
   }
 }
 
+// The same product with no shared memory: one thread per row loads its own
+// entries (the first eight in flight at once; neighbouring rows' entries are
+// adjacent, so the warp's loads share L1 lines) and sums them in column order,
+// so the FP64 FMAs do not queue behind shared-memory traffic.
+__global__ void __launch_bounds__(256, 4) k_spmv_thread(int n, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ colind,
+                                                     const double* __restrict__ val,
+                                                     const double* __restrict__ x, double* __restrict__ y,
+                                                     double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
+  __shared__ double sh[32];
+  if (ks != nullptr && ks->done) return;
+  constexpr int U = 8;
+  double dot = 0.0;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int row = base + threadIdx.x;
+    if (gate_rows_off(gate, base, min(n, base + int(blockDim.x)))) continue;
+    if (row < n) {
+      const int e0 = rowptr[row], e1 = rowptr[row + 1];
+      int c[U];
+      double a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        c[u] = e0 + u < e1 ? colind[e0 + u] : -1;
+        a[u] = e0 + u < e1 ? val[e0 + u] : 0.0;
+      }
+      double xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
+      double acc = 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c[u] >= 0) acc = fma(a[u], xv[u], acc);
+      for (int e = e0 + U; e < e1; ++e) acc = fma(val[e], x[colind[e]], acc);
+      y[row] = acc;
+      dot = fma(x[row], acc, dot);
+    }
+  }
+  if (ks == nullptr) return;
+  const double tsum = block_sum(dot, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = tsum;
+  if (arrive_last(&ks->ticket[0])) {
+    const double s2 = sum_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      ks->pq = s2;
+      ks->alpha = ks->rz / s2;
+    }
+  }
+}
+
 // y = A x and (x, y) for matrices with long rows: W lanes per row stride over
 // its entries (coalesced values and columns), the partial sums meet in a
 // shuffle tree of width W; the dot product as in k_spmv_stream.
@@ -347,6 +396,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, const double* __re
 // ---- single-reduce GMRES (device-resident Arnoldi and Givens) ----
 // Layout of the GMRES state in one device array of doubles (restart m):
 // H (m+1) x m row-major | cs m | sn m | g m+1 | h1 m+2 | h2 m+2 | beta 2.
+// (with delayed reorthogonalisation: Hraw (m+1) x m the unrotated Hessenberg
+// matrix | hp m+1 the new vector's first-pass coefficients | ca m and cc m+1
+// the coefficients of the vector update | sc 4 scalars | dt 2m+3 reductions)
 struct GmLayout {
   int m;
   __host__ __device__ explicit GmLayout(int m_) : m(m_) {}
@@ -356,8 +408,212 @@ struct GmLayout {
   __host__ __device__ int h1() const { return g() + m + 1; }
   __host__ __device__ int h2() const { return h1() + m + 2; }
   __host__ __device__ int beta() const { return h2() + m + 2; }
-  __host__ __device__ int total() const { return beta() + 2; }
+  __host__ __device__ int hraw() const { return beta() + 2; }
+  __host__ __device__ int hp() const { return hraw() + (m + 1) * m; }
+  __host__ __device__ int ca() const { return hp() + m + 1; }
+  __host__ __device__ int cc() const { return ca() + m; }
+  __host__ __device__ int sc() const { return cc() + m + 1; }
+  __host__ __device__ int dt() const { return sc() + 4; }
+  __host__ __device__ int total() const { return dt() + 2 * m + 3; }
 };
+
+// ---- GMRES with delayed reorthogonalisation (one reduction per step) ----
+//
+// The Arnoldi step k applies the operator B = A M^-1 to a vector u_k that is
+// orthogonal to the finished basis F = [q_0 .. q_{k-1}] only once.  One fused
+// reduction gives a = F^T u_k, (u_k, u_k), F^T w, (u_k, w), (w, w) for w = B u_k.
+// From them (one thread): u_k is finished as q_k = (u_k - F a) / sigma, sigma^2
+// = (u_k, u_k) - |a|^2 (its second Gram-Schmidt pass, delayed by one step),
+// which also finishes Hessenberg column k-1; since B F = Q_{k+1} H (Arnoldi),
+// B q_k = (w - Q_{k+1} H a) / sigma, whose projections on Q_{k+1} follow from
+// the reduced quantities, and the next vector u_{k+1} = (B q_k - Q_{k+1} h) /
+// rho (rho its Pythagorean norm) is formed in the same vector pass that writes
+// q_k and M^-1 q_k.  In exact arithmetic this is CGS2 with one reduction per
+// step; column k-1 is complete one step later, so the convergence test lags by
+// one operator application.
+
+// Partial sums for step k: dots j < k of (V_j, u), then (V_j, w), then (u, u),
+// (u, w), (w, w); without w only (V_j, u) and (u, u).  Columns go 8 at a time.
+__global__ void __launch_bounds__(kThreads) k_dc_dots(int n, int k, const double* __restrict__ V,
+                                                      const double* __restrict__ u,
+                                                      const double* __restrict__ w, double* __restrict__ red,
+                                                      const KrylovScalars* __restrict__ ks) {
+  __shared__ double sh[32];
+  if (ks->done) return;
+  const int nd = w != nullptr ? 2 * k + 3 : k + 1;
+  auto store = [&](int d, double v) {
+    const double t = block_sum(v, sh);
+    if (threadIdx.x == 0) red[int64_t(d) * gridDim.x + blockIdx.x] = t;
+  };
+  for (int c0 = 0; c0 < k || c0 == 0; c0 += 8) {
+    double au[8], aw[8], uu = 0.0, uw = 0.0, ww = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { au[q] = 0.0; aw[q] = 0.0; }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double ui = u[i];
+      const double wi = w != nullptr ? w[i] : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (c0 + q < k) {
+          const double vj = V[int64_t(c0 + q) * n + i];
+          au[q] = fma(vj, ui, au[q]);
+          aw[q] = fma(vj, wi, aw[q]);
+        }
+      }
+      if (c0 == 0) {
+        uu = fma(ui, ui, uu);
+        uw = fma(ui, wi, uw);
+        ww = fma(wi, wi, ww);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (c0 + q < k) {
+        store(c0 + q, au[q]);
+        if (w != nullptr) store(k + c0 + q, aw[q]);
+      }
+    }
+    if (c0 == 0) {
+      if (w != nullptr) {
+        store(2 * k, uu);
+        store(2 * k + 1, uw);
+        store(2 * k + 2, ww);
+      } else {
+        store(k, uu);
+      }
+    }
+    (void)nd;
+  }
+}
+
+// Step k's scalar work (one thread): finish u_k and Hessenberg column k-1
+// (with its Givens rotation and the residual estimate, which may end the
+// cycle), then the coefficients of the vector update.  At the last step of a
+// cycle (`final`) only the first part.
+__global__ void k_dc_coef(int k, int m, double* __restrict__ gm, KrylovScalars* ks, int final_step) {
+  if (threadIdx.x != 0 || ks->done) return;
+  const GmLayout L(m);
+  double* H = gm;
+  double* cs = gm + L.cs();
+  double* sn = gm + L.sn();
+  double* g = gm + L.g();
+  double* Hr = gm + L.hraw();
+  double* hp = gm + L.hp();
+  double* ca = gm + L.ca();
+  double* cc = gm + L.cc();
+  double* sc = gm + L.sc();
+  const double* dt = gm + L.dt();
+  const double* a = dt;
+  const double alpha = final_step ? dt[k] : dt[2 * k];
+  double aa = 0.0;
+  for (int j = 0; j < k; ++j) aa = fma(a[j], a[j], aa);
+  const double s2 = alpha - aa;
+  if (!(s2 > 0.0) || !isfinite(s2)) {     // u_k has no new direction: stop the cycle
+    if (!isfinite(s2)) ks->bad = 1;
+    ks->done = 1;
+    return;
+  }
+  const double sigma = sqrt(s2);
+  if (k >= 1) {
+    // column k-1: w_{k-1} = Q_k hp + rho u_k = Q_k (hp + rho a) + rho sigma q_k
+    const int j = k - 1;
+    const double rho = sc[2];
+    for (int i = 0; i < k; ++i) Hr[i * m + j] = fma(rho, a[i], hp[i]);
+    Hr[k * m + j] = rho * sigma;
+    for (int i = 0; i <= j; ++i) H[i * m + j] = Hr[i * m + j];
+    const double hn = Hr[k * m + j];
+    for (int i = 0; i < j; ++i) {
+      const double x0 = H[i * m + j], x1 = H[(i + 1) * m + j];
+      H[i * m + j] = cs[i] * x0 + sn[i] * x1;
+      H[(i + 1) * m + j] = -sn[i] * x0 + cs[i] * x1;
+    }
+    const double d = H[j * m + j];
+    const double den = hypot(d, hn);
+    if (den == 0.0) {
+      ks->bad = 1;
+      ks->done = 1;
+      return;
+    }
+    cs[j] = d / den;
+    sn[j] = hn / den;
+    H[j * m + j] = den;
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    ks->iter += 1;
+    if (!isfinite(g[j + 1])) ks->bad = 1;
+    if (!(g[j + 1] * g[j + 1] > ks->tol2) || ks->iter >= ks->maxit || ks->bad || hn <= 1e-14 * fabs(den)) {
+      ks->done = 1;
+      return;
+    }
+  }
+  if (final_step) return;
+  // B q_k = (w - Q_{k+1} gv) / sigma with gv = Hr a (columns 0..k-1, rows 0..k);
+  // its projections qw / sigma - gv / sigma on Q_{k+1} become hp, and the update
+  // u_{k+1} = (w - Q_{k+1} (gv + sigma hp)) / (sigma rho)
+  const double* bw = dt + k;
+  const double beta = dt[2 * k + 1], gamma = dt[2 * k + 2];
+  double ab = 0.0;
+  for (int j = 0; j < k; ++j) ab = fma(a[j], bw[j], ab);
+  double qg = 0.0, gg = 0.0, hh = 0.0;
+  for (int i = 0; i <= k; ++i) {
+    double gv = 0.0;
+    for (int j = 0; j < k; ++j) gv = fma(Hr[i * m + j], a[j], gv);
+    const double qw = i < k ? bw[i] : (beta - ab) / sigma;
+    const double h = (qw - gv) / sigma;
+    qg = fma(qw, gv, qg);
+    gg = fma(gv, gv, gg);
+    hh = fma(h, h, hh);
+    hp[i] = h;
+    cc[i] = fma(sigma, h, gv);
+  }
+  for (int j = 0; j < k; ++j) ca[j] = a[j];
+  const double wt2 = (gamma - 2.0 * qg + gg) / s2;
+  const double r2 = wt2 - hh;
+  if (!(wt2 >= 0.0) || !isfinite(wt2)) {
+    ks->bad = 1;
+    ks->done = 1;
+    return;
+  }
+  // (a Pythagorean norm lost to cancellation only scales u_{k+1}; the next
+  // step's reorthogonalisation measures its true length)
+  const double rho = sqrt(r2 > 1e-28 * wt2 ? r2 : 1e-28 * wt2 + 1e-300);
+  sc[0] = 1.0 / sigma;
+  sc[1] = 1.0 / (sigma * rho);
+  sc[2] = rho;
+  sc[3] = sigma;
+}
+
+// q_k = (u - F a) / sigma into V_k, M^-1 q_k = (zu - Z_F a) / sigma into Z_k,
+// u_{k+1} = (w - Q_{k+1} cc) / (sigma rho) into u (each element read first).
+__global__ void __launch_bounds__(kThreads) k_dc_update(int n, int k, int m, double* __restrict__ V,
+                                                        double* __restrict__ Zk, double* __restrict__ u,
+                                                        const double* __restrict__ zu,
+                                                        const double* __restrict__ w,
+                                                        const double* __restrict__ gm,
+                                                        const KrylovScalars* __restrict__ ks) {
+  if (ks->done) return;
+  const GmLayout L(m);
+  const double* ca = gm + L.ca();
+  const double* cc = gm + L.cc();
+  const double is = gm[L.sc()], isr = gm[L.sc() + 1];
+  double* vk = V + int64_t(k) * n;
+  double* zk = Zk + int64_t(k) * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double uq = u[i], zz = zu[i], ww = w[i];
+    for (int j = 0; j < k; ++j) {
+      const double vj = V[int64_t(j) * n + i];
+      uq = fma(-ca[j], vj, uq);
+      ww = fma(-cc[j], vj, ww);
+      zz = fma(-ca[j], Zk[int64_t(j) * n + i], zz);
+    }
+    const double q = uq * is;
+    vk[i] = q;
+    zk[i] = zz * is;
+    ww = fma(-cc[k], q, ww);
+    u[i] = ww * isr;
+  }
+}
 
 // Partial sums of (V_i, w) for the k basis vectors and of (w, w) (slot k), in
 // one pass over w: the single global reduction of an Arnoldi step.  Columns
@@ -514,6 +770,12 @@ gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, Kryl
     GDSW_CK(cudaGetLastError());
     return GDSW_OK;
   }
+  if (c->spmv_pipe == 2) {
+    const int grid = std::max(1, std::min(c->spmv_grid, (c->n + 255) / 256));
+    k_spmv_thread<<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate);
+    GDSW_CK(cudaGetLastError());
+    return GDSW_OK;
+  }
   const int grid = std::min(c->spmv_grid, c->spmv_tiles);
   const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
   if (c->spmv_pipe) {
@@ -638,25 +900,32 @@ gdsw_status spmv_grids(size_t shm, int* g_stream, int* g_pipe) {
   return GDSW_OK;
 }
 
-// Measured choice between the two tiled SpMV kernels (three timed launches
-// each after a warm-up, CUDA events, on the Krylov workspace): both compute
-// the same sums in the same order, so the choice changes the speed only.
-// GDSW_SPMV=stream|pipe fixes it instead (for profilers).
+// Measured choice among the SpMV kernels for short rows (the two tiled ones
+// and the one with a thread per row; three timed launches each after a
+// warm-up, CUDA events, on the Krylov workspace): all compute the same sums in
+// the same order, so the choice changes the speed only.
+// GDSW_SPMV=stream|pipe|thread fixes it instead (for profilers).
 gdsw_status spmv_tune(Ctx* c, cudaStream_t s) {
   if (c->spmv_W > 0) return GDSW_OK;
   const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
-  int g[2] = {c->spmv_grid, c->spmv_grid};
+  int g[3] = {c->spmv_grid, c->spmv_grid, c->spmv_grid};
   switch (c->spmv_R) {
     case 256: GDSW_TRY(spmv_grids<256>(shm, &g[0], &g[1])); break;
     case 128: GDSW_TRY(spmv_grids<128>(shm, &g[0], &g[1])); break;
     case 64: GDSW_TRY(spmv_grids<64>(shm, &g[0], &g[1])); break;
     default: GDSW_TRY(spmv_grids<32>(shm, &g[0], &g[1])); break;
   }
+  {
+    int per_sm = 1;
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_thread, 256, 0));
+    g[2] = std::max(1, per_sm) * kNumSMs;
+  }
   // the pipelined kernel holds eight entries per thread of a tile
   const bool pipe_ok = c->spmv_maxne <= 8 * c->spmv_R;
   const char* env = getenv("GDSW_SPMV");
-  if (env != nullptr || !pipe_ok) {
-    c->spmv_pipe = (pipe_ok && env != nullptr && std::string(env) == "pipe") ? 1 : 0;
+  if (env != nullptr) {
+    const std::string k(env);
+    c->spmv_pipe = (k == "pipe" && pipe_ok) ? 1 : k == "thread" ? 2 : 0;
     c->spmv_grid = g[c->spmv_pipe];
     return GDSW_OK;
   }
@@ -666,7 +935,8 @@ gdsw_status spmv_tune(Ctx* c, cudaStream_t s) {
   float best = 3.4e38f;
   int best_k = 0;
   gdsw_status st = GDSW_OK;
-  for (int k = 0; k < 2 && st == GDSW_OK; ++k) {
+  for (int k = 0; k < 3 && st == GDSW_OK; ++k) {
+    if (k == 1 && !pipe_ok) continue;
     c->spmv_pipe = k;
     c->spmv_grid = g[k];
     st = launch_spmv(c, c->p, c->q, s, nullptr);
@@ -698,6 +968,7 @@ gdsw_status spmv_enqueue_batch(Ctx* c, const double* x, double* y, cudaStream_t 
 }
 
 gdsw_status gmres_cycle(Ctx* c, cudaStream_t s);
+gdsw_status gmres_cycle_dc(Ctx* c, cudaStream_t s);
 
 gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   const int n = c->n;
@@ -705,7 +976,7 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   // (any SpMV grid: at most 32 resident CTAs per SM)
   c->red_len = std::max(std::max(2 * c->red_grid, 2 * c->nblk), std::max(c->spmv_grid, 32 * kNumSMs)) + 64;
   if (c->opt.krylov == GDSW_KRYLOV_GMRES)
-    c->red_len = std::max<int>(c->red_len, (c->opt.restart + 2) * c->red_grid + 64);
+    c->red_len = std::max<int>(c->red_len, (2 * c->opt.restart + 4) * c->red_grid + 64);
   GDSW_TRY(dalloc(c, &c->red, c->red_len));
   GDSW_TRY(dalloc(c, &c->x, n));
   GDSW_TRY(dalloc(c, &c->r, n));
@@ -759,7 +1030,8 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   if (c->opt.krylov == GDSW_KRYLOV_GMRES && use_graph && c->nprob == 1) {
     if (c->graph_stream == nullptr) GDSW_CK(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     GDSW_CK(cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal));
-    gdsw_status st = gmres_cycle(c, c->graph_stream);
+    gdsw_status st = c->opt.gmres_orth == GDSW_GMRES_ORTH_DCGS2 ? gmres_cycle_dc(c, c->graph_stream)
+                                                               : gmres_cycle(c, c->graph_stream);
     cudaError_t e = cudaStreamEndCapture(c->graph_stream, &c->gm_graph);
     if (st != GDSW_OK) return st;
     GDSW_CK(e);
@@ -930,6 +1202,36 @@ gdsw_status gmres_cycle(Ctx* c, cudaStream_t s) {
   return GDSW_OK;
 }
 
+// One restart cycle with delayed reorthogonalisation: per step the apply, the
+// SpMV, one fused reduction, the scalar step and one vector pass; a last
+// reduction finishes the final column.  u, M^-1 u and w live in the PCG
+// vectors p, z and q; the driver has put q_0 = r / beta in V_0.
+gdsw_status gmres_cycle_dc(Ctx* c, cudaStream_t s) {
+  const int n = c->n;
+  const int m = std::max(1, c->opt.restart);
+  const int G = vec_grid(c);
+  const GmLayout L(m);
+  double* u = c->p;
+  double* zu = c->z;
+  double* w = c->q;
+  double* dots = c->gm + L.dt();
+  GDSW_CK(cudaMemcpyAsync(u, c->V, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  for (int k = 0; k < m; ++k) {
+    GDSW_TRY(apply_enqueue_gated(c, u, zu, s));
+    GDSW_TRY(launch_spmv(c, zu, w, s, c->ks));
+    k_dc_dots<<<G, kThreads, 0, s>>>(n, k, c->V, u, w, c->red, c->ks);
+    k_gs_reduce<<<2 * k + 3, kThreads, 0, s>>>(G, c->red, dots, c->ks, 0);
+    k_dc_coef<<<1, 32, 0, s>>>(k, m, c->gm, c->ks, 0);
+    k_dc_update<<<G, kThreads, 0, s>>>(n, k, m, c->V, c->Zk, u, zu, w, c->gm, c->ks);
+    GDSW_CK(cudaGetLastError());
+  }
+  k_dc_dots<<<G, kThreads, 0, s>>>(n, m, c->V, u, nullptr, c->red, c->ks);
+  k_gs_reduce<<<m + 1, kThreads, 0, s>>>(G, c->red, dots, c->ks, 0);
+  k_dc_coef<<<1, 32, 0, s>>>(m, m, c->gm, c->ks, 1);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
 // Right-preconditioned restarted GMRES(m) (Sec. VII) with the Arnoldi
 // process, the Hessenberg matrix and the Givens rotations on the device: each
 // Gram-Schmidt pass is one fused reduction (V^T w together with (w, w)); two
@@ -983,6 +1285,7 @@ gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* inf
     kh->gm_mode = 1;
     GDSW_CK(cudaMemcpyAsync(c->ks, kh, sizeof(KrylovScalars), cudaMemcpyHostToDevice, s));
     if (c->gm_exec != nullptr) GDSW_CK(cudaGraphLaunch(c->gm_exec, s));
+    else if (c->opt.gmres_orth == GDSW_GMRES_ORTH_DCGS2) GDSW_TRY(gmres_cycle_dc(c, s));
     else GDSW_TRY(gmres_cycle(c, s));
     GDSW_CK(cudaMemcpyAsync(gmh.data(), c->gm, sizeof(double) * L.total(), cudaMemcpyDeviceToHost, s));
     GDSW_TRY(read_scalars(c, s));

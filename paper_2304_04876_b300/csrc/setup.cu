@@ -969,10 +969,15 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         stage = std::max<size_t>(stage, rec_bytes[rr]);
       }
       // Consecutive records of a subdomain are contiguous in the stream: pack
-      // them greedily into one bulk copy while the pack stays within the largest
-      // single record (so a ring stage still holds any pack).  The first record
-      // of a pack carries the pack's record count (header word 7); every record
-      // its own size (word 6), so the consumers step through the pack.
+      // them greedily into one bulk copy while the pack stays within a ring
+      // stage: the largest single record, or GDSW_PACK_BYTES if larger (fewer,
+      // larger copies).  The first record of a pack carries the pack's record
+      // count (header word 7); every record its own size (word 6), so the
+      // consumers step through the pack.
+      if (const char* e = getenv("GDSW_PACK_BYTES")) {
+        const long want = atol(e);
+        if (want > 0) stage = std::max<size_t>(stage, (static_cast<size_t>(want) + 15) & ~size_t(15));
+      }
       std::vector<int> pk_ptr(nsub + 1, 0);
       std::vector<uint32_t> pk_off16, pk_bytes;
       for (int q = 0; q < nsub; ++q) {
@@ -1021,6 +1026,106 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         else
           k_fill_records<double><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
                                                                        reinterpret_cast<double*>(d_stream));
+        GDSW_CK(cudaGetLastError());
+      }
+    }
+    // Resident blocks for the Jacobi sweeps (Sec. V-B3): per subdomain and
+    // triangle one block that a CTA copies into shared memory once and sweeps
+    // there: int4 {rows m, width K, values offset, columns offset} | m x T
+    // inverse diagonal | K*m x T values | K*m x uint16 columns, slot k of local
+    // row i at k*m + i, every section 16-byte aligned.  A row's entries keep
+    // the order of the level-sliced ELL (so each sum is formed as by the
+    // unpipelined Jacobi kernel); rows shorter than K are padded with a zero
+    // entry pointing at the row itself.  Blocks are in subdomain order, L then
+    // U; one spare 16 bytes at the end absorb the ELL's own padding entries.
+    if (o.trsv == GDSW_TRSV_JACOBI) {
+      const size_t vb = c->fp16 ? sizeof(__half) : c->fp32 ? sizeof(float) : sizeof(double);
+      auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+      std::vector<uint32_t> joff(size_t(2) * nsub), jbytes(size_t(2) * nsub);
+      std::vector<int> jK(size_t(2) * nsub, 0);
+      size_t total = 0, maxb[2] = {0, 0};
+      for (int q = 0; q < nsub; ++q) {
+        const size_t m = size_t(P.om_ptr[q + 1] - P.om_ptr[q]);
+        for (int side = 0; side < 2; ++side) {
+          const EllPlan& E = side == 0 ? P.L : P.U;
+          int K = 0;
+          for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l)
+            for (int t = 0; t < E.lev_nr[l]; ++t) {
+              int w = 0;
+              for (int k = 0; k < E.lev_K[l]; ++k) w += E.src[E.lev_off[l] + int64_t(k) * E.lev_nr[l] + t] >= 0;
+              K = std::max(K, w);
+            }
+          jK[2 * q + side] = K;
+          const size_t bytes = 16 + a16(m * vb) + a16(size_t(K) * m * vb) + a16(size_t(K) * m * 2);
+          joff[2 * q + side] = static_cast<uint32_t>(total / 16);
+          jbytes[2 * q + side] = static_cast<uint32_t>(bytes);
+          maxb[side] = std::max(maxb[side], bytes);
+          total += bytes;
+          if (total / 16 >= (size_t(1) << 32) || total / vb >= (size_t(1) << 32)) {
+            set_error("Jacobi blocks too large"); return GDSW_ERR_UNSUPPORTED;
+          }
+        }
+      }
+      const size_t dummy = total / vb;            // element receiving the ELL padding
+      std::vector<uint8_t> host(total + 16, 0);
+      std::vector<uint32_t> vpos[2] = {std::vector<uint32_t>(P.L.slots), std::vector<uint32_t>(P.U.slots)};
+      std::vector<uint32_t> dpos[2] = {std::vector<uint32_t>(P.sum_m), std::vector<uint32_t>(P.sum_m)};
+      for (int q = 0; q < nsub; ++q) {
+        const int m = P.om_ptr[q + 1] - P.om_ptr[q];
+        for (int side = 0; side < 2; ++side) {
+          const EllPlan& E = side == 0 ? P.L : P.U;
+          const int K = jK[2 * q + side];
+          const size_t base = size_t(joff[2 * q + side]) * 16;
+          const size_t o_d = 16, o_v = o_d + a16(size_t(m) * vb), o_c = o_v + a16(size_t(K) * m * vb);
+          const int hdr[4] = {m, K, static_cast<int>(o_v), static_cast<int>(o_c)};
+          std::memcpy(&host[base], hdr, 16);
+          uint16_t* cc = reinterpret_cast<uint16_t*>(&host[base + o_c]);
+          for (int i = 0; i < m; ++i)
+            for (int k = 0; k < K; ++k) cc[size_t(k) * m + i] = static_cast<uint16_t>(i);
+          for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
+            const int nr = E.lev_nr[l];
+            for (int t = 0; t < nr; ++t) {
+              const int row = E.lrows[E.lev_start[l] + t];
+              dpos[side][E.lev_start[l] + t] = static_cast<uint32_t>((base + o_d) / vb + row);
+              int kk = 0;
+              for (int k = 0; k < E.lev_K[l]; ++k) {
+                const int64_t slot = E.lev_off[l] + int64_t(k) * nr + t;
+                if (E.src[slot] >= 0) {
+                  cc[size_t(kk) * m + row] = E.col[slot];
+                  vpos[side][slot] = static_cast<uint32_t>((base + o_v) / vb + size_t(kk) * m + row);
+                  ++kk;
+                } else {
+                  vpos[side][slot] = static_cast<uint32_t>(dummy);
+                }
+              }
+            }
+          }
+        }
+      }
+      uint8_t* d_js;
+      GDSW_TRY(upload(c, &d_js, host, s));
+      c->jac_stream = d_js;
+      GDSW_TRY(upload(c, &c->jac_off16, joff, s));
+      GDSW_TRY(upload(c, &c->jac_bytes, jbytes, s));
+      c->jac_max_bytes[0] = static_cast<int>(maxb[0]);
+      c->jac_max_bytes[1] = static_cast<int>(maxb[1]);
+      for (int side = 0; side < 2; ++side) {
+        const EllPlan& E = side == 0 ? P.L : P.U;
+        uint32_t *d_vp, *d_dp;
+        int *d_src, *d_dsrc;
+        GDSW_TRY(sc.put(&d_vp, vpos[side], s));
+        GDSW_TRY(sc.put(&d_dp, dpos[side], s));
+        GDSW_TRY(sc.put(&d_src, E.src, s));
+        GDSW_TRY(sc.put(&d_dsrc, E.dsrc, s));
+        if (c->fp16)
+          k_fill_records<__half><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                       reinterpret_cast<__half*>(d_js));
+        else if (c->fp32)
+          k_fill_records<float><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                      reinterpret_cast<float*>(d_js));
+        else
+          k_fill_records<double><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                       reinterpret_cast<double*>(d_js));
         GDSW_CK(cudaGetLastError());
       }
     }

@@ -22,7 +22,7 @@ TRSV = {"levelsched": 0, "jacobi": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2}
 KRYLOV = {"pcg": 0, "gmres": 1}
 COARSE = {"gdsw": 0, "none": 1, "rgdsw": 2}
-GMRES_ORTH = {"cgs2": 0, "single": 1}
+GMRES_ORTH = {"cgs2": 0, "single": 1, "dcgs2": 2}
 
 
 class CSRStruct(C.Structure):
@@ -70,7 +70,8 @@ class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in (
         "n", "nnz", "n_sub", "n0", "n_comp", "sum_omega", "max_omega", "nnz_L", "nnz_U", "ell_L",
         "ell_U", "nnz_phi", "n_levels_L", "n_levels_U", "max_levels", "dense_local", "n_blocks",
-        "device_bytes", "n_problems", "a0_entries", "local_stages", "local_threads", "mf_supernodes", "mf_levels")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8)]
+        "device_bytes", "n_problems", "a0_entries", "local_stages", "local_threads", "mf_supernodes", "mf_levels")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8),
+                                                          ("local_kernel", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "setup_phase_seconds"}
