@@ -717,7 +717,7 @@ def run_serving(args, world, rank, dist, barrier):
     import torch
     from paper_2304_04876_b300 import gdsw
     from paper_2304_04876_b300 import serving as S
-    pool = P.serving_pool(args.pool, seed=rank)
+    pool = P.serving_pool(args.pool, seed=rank, dofs_max=args.serving_max_dofs)
     byname = {p.name: p for p in pool}
     opts = dict(local_solver="ic0", trsv="levelsched", precision="fp32")
     zof = lambda pr: pr.Z if pr.part.dpn == 3 else None  # noqa: E731
@@ -765,7 +765,8 @@ def run_serving(args, world, rank, dist, barrier):
         "value": world * top["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.requests,
         "warmup": len(slots), "ms_per_step": 1e3 / top["solves_per_s"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"serving_pool{len(pool)}_poisson+elasticity_32^3-160^3", "pool_unknowns": sizes,
+        "config": {"workload": f"serving_pool{len(pool)}_poisson+elasticity_32^3-"
+                               f"{round(args.serving_max_dofs ** (1 / 3))}^3", "pool_unknowns": sizes,
                    "slots": len(slots), "admitted_problems": len(admitted), "budget_bytes": budget,
                    "iterations_per_round": args.serving_iters, "rates_req_per_s": args.rates,
                    "requests_per_rate": args.requests, "parallelism": f"replicas{world}"},
@@ -792,7 +793,9 @@ def config_summaries(args, world, rank, dist, barrier) -> dict:
             "one_at_a_time_problems_per_s", "p50_ms", "p99_ms", "plain_fp64_one_at_a_time", "served_over_plain",
             "rates", "slots", "roofline", "apply_phase_ms", "spmv_ms", "variants")
     for cfg, extra in ((1, dict(steps=20, warmup=3)), (3, dict(steps=3, warmup=3)),
-                       (4, dict(steps=2, warmup=3)), (5, dict(requests=40, rates=[100.0, 1000.0]))):
+                       (4, dict(steps=2, warmup=3)),
+                       # (config 5 bounded: 10 problems of at most 96^3 unknowns, two rates)
+                       (5, dict(requests=40, rates=[30.0, 1000.0], pool=10, serving_max_dofs=96 ** 3))):
         a = copy.copy(args)
         a.config, a.variant, a.no_cpu_baseline = cfg, None, True
         for k, v in extra.items():
@@ -860,6 +863,7 @@ def main():
     ap.add_argument("--pool", type=int, default=16, help="serving: distinct problems")
     ap.add_argument("--serving-copies", type=int, default=2, help="serving: most slots per problem")
     ap.add_argument("--serving-iters", type=int, default=4, help="serving: PCG iterations per round")
+    ap.add_argument("--serving-max-dofs", type=int, default=160 ** 3, help="serving: largest problem (unknowns)")
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per rate")
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
     ap.add_argument("--workers", type=int, default=4)

@@ -284,9 +284,8 @@ __device__ __forceinline__ void level_rows(const unsigned char* rec, T* v, const
 
 // The pipelined local solve runs NT consumer threads (64 to 512, chosen at
 // setup) that update the rows, plus one producer warp that only streams the
-// level records into the ring (at most 544 threads, so a thread may hold up to
-// 112 registers: the gather keeps 32 values in flight and a level's row data
-// is loaded ahead of its barrier).
+// level records into the ring (at most 544 threads, so the compiler may give a
+// thread up to 112 registers instead of the 64 that 1024 threads would leave).
 constexpr int kPipeMaxThreads = 544;
 
 // Barrier of the `nt` consumer threads only (named barrier 1), every warp
@@ -309,8 +308,7 @@ __device__ __forceinline__ bool consumers_sync_or(bool pred, int nt) {
 }
 
 // v = R_s r from indices already staged in shared memory (`idx`: this
-// subdomain's slice of the overlap map), 32 values in flight per thread (16
-// for FP64 vectors, whose kernels have more live registers).
+// subdomain's slice of the overlap map), sixteen values in flight per thread.
 // For FP32 vectors `idx` and `v` share their words: each thread reads and
 // writes only its own positions.  For FP64 `idx` sits in the upper half of
 // the vector's space, and a barrier between the index reads and the value
@@ -319,7 +317,7 @@ __device__ __forceinline__ bool consumers_sync_or(bool pred, int nt) {
 template <class T>
 __device__ __forceinline__ void gather_staged(const double* __restrict__ r, const int* idx, T* v, int m,
                                               int nt) {
-  constexpr int U = sizeof(T) == 4 ? 32 : 16;
+  constexpr int U = 16;
   const int tid = threadIdx.x;
   for (int i0 = 0; i0 < m; i0 += U * nt) {
     double rv[U];
@@ -335,49 +333,6 @@ __device__ __forceinline__ void gather_staged(const double* __restrict__ r, cons
       if (i < m) v[i] = T(rv[u]);
     }
   }
-}
-
-// The row-invariant data of one level record whose rows are row-major by 4
-// (layout 1, one thread per row, at most NT rows): loaded before the barrier
-// that precedes the record's level, so that after it only the reads of the
-// solution values remain on the level's critical path.
-template <class T>
-struct RowAhead {
-  int row;
-  ushort4 c;
-  T a[4];
-  T d;
-  bool on;
-};
-
-template <class T, class TS>
-__device__ __forceinline__ bool row_ahead_load(const unsigned char* rec, int nt, RowAhead<T>& p) {
-  const int4 hdr = *reinterpret_cast<const int4*>(rec);
-  const int layout = reinterpret_cast<const int*>(rec)[5] & 0xff;
-  const int nr = hdr.x;
-  if (layout != 1 || nr > nt) return false;
-  const int t = threadIdx.x;
-  p.on = t < nr;
-  if (p.on) {
-    const uint16_t* lrows = reinterpret_cast<const uint16_t*>(rec + 32);
-    const TS* dinv = reinterpret_cast<const TS*>(rec + 32 + ((2 * nr + 15) & ~15));
-    p.row = lrows[t];
-    p.c = reinterpret_cast<const ushort4*>(rec + hdr.w)[t];
-    load4<T, TS>(reinterpret_cast<const TS*>(rec + hdr.z), t, p.a);
-    p.d = load_as<T, TS>(dinv, t);
-  }
-  return true;
-}
-
-template <class T>
-__device__ __forceinline__ void row_ahead_apply(const RowAhead<T>& p, T* v) {
-  if (!p.on) return;
-  T acc = v[p.row];
-  acc = fma(-p.a[0], v[p.c.x], acc);
-  acc = fma(-p.a[1], v[p.c.y], acc);
-  acc = fma(-p.a[2], v[p.c.z], acc);
-  acc = fma(-p.a[3], v[p.c.w], acc);
-  v[p.row] = acc * p.d;
 }
 
 // Shared memory of the pipelined solve's local vector: m values plus the room
@@ -543,18 +498,10 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1) k_local_pipe(const double*
     // after its last record
     const unsigned char* rec = stages + size_t(st) * stage_bytes;
     const int count = reinterpret_cast<const int*>(rec)[7];
-    RowAhead<T> ahead;
-    bool have_ahead = false;
     for (int q = 0; q < count; ++q) {
       const unsigned char* next = rec + reinterpret_cast<const int*>(rec)[6];
       const bool level_end = (reinterpret_cast<const int*>(rec)[5] & kRecLevelEnd) != 0;
-      if (have_ahead) row_ahead_apply(ahead, v);
-      else level_rows<T, TS, TPR>(rec, v, nt, grp);
-      // the next record of this pack: its row data before the barrier
-      have_ahead = false;
-      if constexpr (TPR == 1) {
-        if (q + 1 < count) have_ahead = row_ahead_load<T, TS>(next, nt, ahead);
-      }
+      level_rows<T, TS, TPR>(rec, v, nt, grp);
       // each warp releases the stage as soon as its lanes are done reading it
       if (q + 1 == count) {
         __syncwarp();
