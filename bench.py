@@ -482,6 +482,8 @@ def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=N
     else:
         kernel_ms = {**phase_ms, "spmv": spmv_ms}
     per_kernel = rooflines(kernel_ms, work, hbm, src, fp64_rate)
+    for k in per_kernel:
+        per_kernel[k]["traffic"] = profiled_traffic(k, workload, variant)
     dom = max(per_kernel, key=lambda k: per_kernel[k]["us"])
     achieved = per_kernel[dom]["gbs"]
     dom_entry = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -506,6 +508,7 @@ def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=N
 
 
 KERNEL_SOURCE = {"local": "apply.cu", "phiT": "apply.cu", "coarse": "apply.cu", "combine": "apply.cu",
+                 "update": "krylov.cu", "pupdate": "krylov.cu",
                  "spmv": "krylov.cu"}
 
 
