@@ -127,7 +127,8 @@ def iteration_work(st: dict, vb: int, fb: int, flexible: bool) -> dict:
     tri = st["nnz_L"] + st["nnz_U"] - 2 * st["sum_omega"]
     return {
         "spmv": {"bytes": spmv_bytes(st), "fma64": nnz + n},
-        "update": {"bytes": 48 * n, "fma64": 3 * n},
+        "update": {"bytes": 24 * n, "fma64": 2 * n},
+        "xupdate": {"bytes": 24 * n, "fma64": n},
         "local": {"bytes": ab["local"], "fma64": tri if fp64_pre and not st["dense_local"] else 0},
         "phiT": {"bytes": ab["phiT"], "fma64": st["nnz_phi"] if fp64_pre else 0},
         "coarse": {"bytes": ab["coarse"], "fma64": st.get("a0_entries", st["n0"] ** 2)},
@@ -478,7 +479,7 @@ def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=N
         kernel_ms = acc
         if krylov != "pcg":
             # GMRES has its own vector kernels; keep the SpMV and the apply's phases
-            kernel_ms = {k: v for k, v in acc.items() if k not in ("update", "pupdate")}
+            kernel_ms = {k: v for k, v in acc.items() if k not in ("update", "pupdate", "xupdate")}
     else:
         kernel_ms = {**phase_ms, "spmv": spmv_ms}
     per_kernel = rooflines(kernel_ms, work, hbm, src, fp64_rate)
@@ -508,7 +509,7 @@ def kernel_measurements(h, st, vb, stream, v0, workload=None, variant=None, fb=N
 
 
 KERNEL_SOURCE = {"local": "apply.cu", "phiT": "apply.cu", "coarse": "apply.cu", "combine": "apply.cu",
-                 "update": "krylov.cu", "pupdate": "krylov.cu",
+                 "update": "krylov.cu", "pupdate": "krylov.cu", "xupdate": "krylov.cu",
                  "spmv": "krylov.cu"}
 
 

@@ -279,9 +279,10 @@ GDSW_API gdsw_status gdsw_apply_timed(gdsw_handle h, const double* r, double* z,
  * vector, n entries; x0 = 0, r = b, z = M^-1 r, p = z), runs one iteration
  * with every kernel on `stream` in order (the apply's two branches are not
  * overlapped) and CUDA events between them, waits, and writes the device times
- * in ms to kernel_ms[7]: [0] SpMV with (p, Ap), [1] x, r update with ||r||^2,
+ * in ms to kernel_ms[8]: [0] SpMV with (p, Ap), [1] r update with ||r||^2,
  * [2] gather + local solve, [3] Phi^T r, [4] coarse solve, [5] scatter-add +
- * prolongation with the PCG dots, [6] new direction p.  Overwrites the
+ * prolongation with the PCG dots, [6] new direction p, [7] x update (in a
+ * solve it runs on a second stream beside the apply).  Overwrites the
  * handle's Krylov workspace.  Errors: INVALID_ARG (NULL), UNSUPPORTED
  * (batched handle), TIMEOUT, CUDA. */
 GDSW_API gdsw_status gdsw_pcg_iteration_timed(gdsw_handle h, const double* b, void* stream,
@@ -384,6 +385,16 @@ GDSW_API gdsw_status gdsw_spmv_dot_noalloc(int32_t n, int64_t nnz, const int32_t
  * frees a few KB of device memory; runs about 0.1 s on `stream`, then
  * synchronises.  Errors: INVALID_ARG (precision, NULL output), CUDA. */
 GDSW_API gdsw_status gdsw_measure_fma_rate(int32_t precision, double* fma_per_second, void* stream);
+
+/* Self-check of the library's own FP64 <-> FP32 conversions (integer-ALU
+ * rewrites of the IEEE 754 fields, used where the apply narrows r to FP32 and
+ * widens its FP32 sums: B300's hardware conversions issue on the slow FP64
+ * pipe) against the hardware conversions, bit for bit, on `count` random bit
+ * patterns drawn from `seed`.  Writes the number of differing results to
+ * mismatches[0] (double -> float, round to nearest even) and mismatches[1]
+ * (float -> double); both must be 0.  Allocates 16 bytes of device memory,
+ * synchronises `stream`.  Errors: INVALID_ARG (NULL, count < 0), CUDA. */
+GDSW_API gdsw_status gdsw_check_conversions(uint64_t seed, int64_t count, uint64_t* mismatches, void* stream);
 
 GDSW_API const char* gdsw_status_string(gdsw_status s);
 GDSW_API const char* gdsw_last_error(void);

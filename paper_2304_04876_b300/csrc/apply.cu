@@ -47,7 +47,7 @@ __device__ __forceinline__ void gather_sub(const double* __restrict__ r, const i
     for (int u = 0; u < U; ++u) rv[u] = idx[u] >= 0 ? r[idx[u]] : 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (i0 + u * nt < m) v[i0 + u * nt] = T(rv[u]);
+      if (i0 + u * nt < m) v[i0 + u * nt] = narrow<T>(rv[u]);
   }
 }
 
@@ -330,7 +330,7 @@ __device__ __forceinline__ void gather_staged(const double* __restrict__ r, cons
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + tid + u * nt;
-      if (i < m) v[i] = T(rv[u]);
+      if (i < m) v[i] = narrow<T>(rv[u]);
     }
   }
 }
@@ -946,7 +946,7 @@ __device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict_
       for (int j = 0; j < 4; ++j) g[j] = ib + 32 * j < i1 ? brow_dof[p0 + ib + 32 * j] : -1;
       T rv[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) rv[j] = g[j] >= 0 ? T(r[g[j]]) : T(0);
+      for (int j = 0; j < 4; ++j) rv[j] = g[j] >= 0 ? narrow<T>(r[g[j]]) : T(0);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (g[j] < 0) continue;
@@ -1005,7 +1005,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
     for (int j = 0; j < 4; ++j) g[j] = ib + 256 * j < rows ? brow_dof[p0 + i0 + ib + 256 * j] : -1;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (g[j] >= 0) rs[ib + 256 * j] = T(r[g[j]]);
+      if (g[j] >= 0) rs[ib + 256 * j] = narrow<T>(r[g[j]]);
   }
   __syncthreads();
   // one warp per column: the column is contiguous in the block's panel
@@ -1026,51 +1026,54 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
 
 __global__ void k_coarse_c(int n0, const int* __restrict__ cs_ptr, const int* __restrict__ cs_idx,
                            const double* __restrict__ partial, double* __restrict__ c,
-                           const KrylovScalars* __restrict__ ks, BatchGate gate) {
+                           float* __restrict__ c32, const KrylovScalars* __restrict__ ks, BatchGate gate) {
   if (ks != nullptr && ks->done) return;
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n0; l += gridDim.x * blockDim.x) {
     if (gate_col_off(gate, l)) continue;
     double v = 0.0;
     for (int q = cs_ptr[l]; q < cs_ptr[l + 1]; ++q) v += partial[cs_idx[q]];
     c[l] = v;
+    if (c32 != nullptr) c32[l] = float(v);
   }
 }
 
-// y = A0^-1 c with the explicit inverse (one dense block per problem).  Two
-// warps per row, each over half of the columns with eight independent FMA
-// chains per lane (FP64 latency); the halves are added in a fixed order.  c is
-// read through L1/L2, not staged in shared memory, so the CTAs need almost
-// none and fit beside the local solve's CTAs on the same SMs (the two branches
-// of the apply overlap).
-__global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __restrict__ Ainv,
+// y = A0^-1 c with the explicit inverse (one dense block per problem), in the
+// inverse's stored type TA (FP64, or FP32 for a single-precision apply, whose
+// FMAs then leave B300's slow FP64 pipe).  Two warps per row, each over half
+// of the columns with eight independent FMA chains per lane; the halves are
+// added in a fixed order.  c is read through L1/L2, not staged in shared
+// memory, so the CTAs need almost none and fit beside the local solve's CTAs
+// on the same SMs (the two branches of the apply overlap).
+template <class TA>
+__global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const TA* __restrict__ Ainv,
                                                      const int* __restrict__ coarse_prob,
                                                      const int* __restrict__ prob_c0,
                                                      const int64_t* __restrict__ a0_off,
-                                                     const double* __restrict__ c,
+                                                     const TA* __restrict__ c,
                                                      double* __restrict__ y, float* __restrict__ y32,
                                                      const KrylovScalars* __restrict__ ks, BatchGate gate) {
-  __shared__ double half_sum[4][2];
+  __shared__ TA half_sum[4][2];
   if (ks != nullptr && ks->done) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int slot = w >> 1, h = w & 1;                  // row slot in the CTA, half of the row
   for (int row0 = blockIdx.x * 4; row0 < n0; row0 += gridDim.x * 4) {
     const int row = row0 + slot;
-    double acc = 0.0;
+    TA acc = TA(0);
     const bool live = row < n0 && !gate_col_off(gate, row);
     if (live) {
       const int pr = coarse_prob[row];
       const int cp = prob_c0[pr], np = prob_c0[pr + 1] - cp;
-      const double* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
-      const double* cv = c + cp;
+      const TA* Ar = Ainv + a0_off[pr] + int64_t(row - cp) * np;
+      const TA* cv = c + cp;
       // short rows (small problems of a batch) go whole to the first warp
       const int split = np >= 1024 ? np / 2 : np;
       const int j0 = h == 0 ? 0 : split, j1 = h == 0 ? split : np;
-      double a[8];
+      TA a[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = 0.0;
+      for (int u = 0; u < 8; ++u) a[u] = TA(0);
       int j = j0 + lane;
       for (; j + 7 * 32 < j1; j += 8 * 32) {
-        double m[8];
+        TA m[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) m[u] = Ar[j + 32 * u];
 #pragma unroll
@@ -1083,8 +1086,8 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const double* __res
     if (lane == 0) half_sum[slot][h] = acc;
     __syncthreads();
     if (h == 0 && lane == 0 && live) {
-      const double v = half_sum[slot][0] + half_sum[slot][1];
-      y[row] = v;
+      const TA v = half_sum[slot][0] + half_sum[slot][1];
+      y[row] = double(v);
       if (y32 != nullptr) y32[row] = float(v);   // converted once, not per scatter position
     }
     __syncthreads();
@@ -1118,7 +1121,7 @@ __device__ __forceinline__ double combine_one(int p, const int* __restrict__ pos
     const T* Ph = phi + phi_off[b] + (p - p0);
     for (int u = 0; u < k; ++u) acc = fma(Ph[int64_t(u) * nr], y[bcol[c0 + u]], acc);
   }
-  return double(acc);
+  return widen<T>(acc);
 }
 
 template <class T>
@@ -1314,11 +1317,15 @@ gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovSca
 
 gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const BatchGate& gate) {
   if (c->n0 == 0) return GDSW_OK;
-  k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, ks, gate);
+  k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, c->cvec32,
+                                                  ks, gate);
   const int grid = std::min((c->n0 + 3) / 4, kNumSMs * 8);
-
-  k_coarse_gemv<<<grid, 256, 0, s>>>(c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off, c->cvec, c->yvec,
-                                      c->yvec32, ks, gate);
+  if (c->A0inv32 != nullptr)
+    k_coarse_gemv<float><<<grid, 256, 0, s>>>(c->n0, c->A0inv32, c->coarse_prob, c->prob_c0, c->a0_off,
+                                              c->cvec32, c->yvec, c->yvec32, ks, gate);
+  else
+    k_coarse_gemv<double><<<grid, 256, 0, s>>>(c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off,
+                                               c->cvec, c->yvec, c->yvec32, ks, gate);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -1575,6 +1582,8 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
     GDSW_CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     GDSW_CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    GDSW_CK(cudaEventCreateWithFlags(&c->ev_x, cudaEventDisableTiming));
+    GDSW_CK(cudaEventCreateWithFlags(&c->ev_xdone, cudaEventDisableTiming));
   }
   if (c->derr == nullptr) {
     GDSW_TRY(dalloc(c, &c->derr, 4));

@@ -44,6 +44,8 @@ void release(Ctx* c) {
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_x) cudaEventDestroy(c->ev_x);
+  if (c->ev_xdone) cudaEventDestroy(c->ev_xdone);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->ks_host) cudaFreeHost(c->ks_host);

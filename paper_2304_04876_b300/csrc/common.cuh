@@ -39,11 +39,85 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Sum over the CTA in a fixed tree order; the result is valid in thread 0.
-// `sh` needs blockDim.x/32 entries.  Ends with a barrier so `sh` can be reused.
+// ---- FP64 <-> FP32 conversions on the integer ALUs ----------------------
+// On B300 the hardware conversions between double and float issue on the FP64
+// pipe (one warp instruction per 16 SM cycles, shared with every DFMA).  These
+// two convert normal numbers by rewriting the IEEE 754 binary64 / binary32
+// fields (exponent bias 1023 vs 127, 52 vs 23 fraction bits) with integer
+// operations; zeros take a direct path and only subnormals, infinities and
+// NaNs go to the hardware conversion.  The narrowing rounds to nearest, ties
+// to even (the default IEEE 754 rounding): the dropped 29 fraction bits are
+// compared with one half ulp, a carry out of the fraction correctly bumps the
+// exponent and, at the top of the range, produces the infinity that rounding
+// gives.  Both are checked bit for bit against the hardware conversion over
+// random bit patterns (gdsw_check_conversions).
+static __device__ __noinline__ float f32_from_f64_hw(double d) { return __double2float_rn(d); }
+static __device__ __noinline__ double f64_from_f32_hw(float f) { return static_cast<double>(f); }
+
+__device__ __forceinline__ float f32_from_f64(double d) {
+  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(d));
+  const uint64_t a = u & 0x7fffffffffffffffull;
+  const uint32_t sign = static_cast<uint32_t>(u >> 32) & 0x80000000u;
+  // binary64 exponents 897..1150 are the binary32 normal exponents 1..254
+  if (a - (uint64_t(897) << 52) < (uint64_t(1151 - 897) << 52)) {
+    const uint64_t t = a - (uint64_t(896) << 52);
+    uint32_t f = static_cast<uint32_t>(t >> 29);
+    const uint32_t rem = static_cast<uint32_t>(t) & 0x1fffffffu;
+    f += (rem > 0x10000000u) | ((rem == 0x10000000u) & f);
+    return __uint_as_float(f | sign);
+  }
+  if (a == 0) return __uint_as_float(sign);
+  return f32_from_f64_hw(d);
+}
+
+__device__ __forceinline__ double f64_from_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t a = u & 0x7fffffffu;
+  const uint64_t sign = static_cast<uint64_t>(u & 0x80000000u) << 32;
+  if (a - 0x00800000u < 0x7f000000u)   // normal: exponent 1..254
+    return __longlong_as_double(static_cast<long long>(((static_cast<uint64_t>(a) << 29) + (uint64_t(896) << 52)) | sign));
+  if (a == 0) return __longlong_as_double(static_cast<long long>(sign));
+  return f64_from_f32_hw(f);
+}
+
+// Narrowing of an FP64 vector entry to the apply's compute type.
+template <class T>
+__device__ __forceinline__ T narrow(double d) { return static_cast<T>(d); }
+template <>
+__device__ __forceinline__ float narrow<float>(double d) { return f32_from_f64(d); }
+
+// Widening of a compute-type value to FP64.
+template <class T>
+__device__ __forceinline__ double widen(T v) { return static_cast<double>(v); }
+template <>
+__device__ __forceinline__ double widen<float>(float v) { return f64_from_f32(v); }
+
+// Sum over the CTA in a fixed order; the result is valid in thread 0.  `sh`
+// needs blockDim.x/32 entries.  Ends with a barrier so `sh` can be reused.
+// B300's FP64 pipe issues one warp instruction per 16 SM cycles however few
+// lanes are active, so for doubles in CTAs of up to 256 threads the values are
+// parked in shared memory and summed by one warp (lane l adds the l-th value of
+// each warp in ascending warp order, then a shuffle tree): 8 + 5 FP64
+// instructions per CTA instead of a shuffle tree in every warp (45).
 template <class T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (sizeof(T) == 8 && blockDim.x <= 256) {
+    __shared__ T park[256];
+    park[threadIdx.x] = v;
+    __syncthreads();
+    T s = T(0);
+    if (w == 0) {
+      s = lane < int(blockDim.x) ? park[lane] : T(0);
+      for (int q = 1; q < nw; ++q) {
+        const int i = q * 32 + lane;
+        if (i < int(blockDim.x)) s += park[i];
+      }
+      s = warp_sum(s);
+    }
+    __syncthreads();
+    return s;
+  }
   v = warp_sum(v);
   if (lane == 0) sh[w] = v;
   __syncthreads();

@@ -138,8 +138,11 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
       maxb = std::max(maxb, nb);
     }
     for (int q = 0; q < P.nsub; ++q) band += int64_t(P.int_ptr[q + 1] - P.int_ptr[q]) * (int64_t(P.int_bw[q]) + 1);
-    R += arr(C.n0, 4) + arr(P.nprob + 1, 4) + arr(P.nprob + 1, 8) + arr(a0, 8) + arr(C.phi_len, v);
-    S += arr(C.phi_len, 8) + arr(a0, 8) + arr((maxb + 63) / 64 * 64 * maxb, 8) +
+    // A0^-1 kept in the apply precision; a low-precision apply builds the FP64
+    // inverse in scratch and rounds it once (plus c in FP32)
+    R += arr(C.n0, 4) + arr(P.nprob + 1, 4) + arr(P.nprob + 1, 8) + arr(a0, v) + arr(C.phi_len, v) +
+         (low ? arr(C.n0, 4) : 0);
+    S += arr(C.phi_len, 8) + arr(a0, 8) + (low ? arr(a0, 8) : 0) + arr((maxb + 63) / 64 * 64 * maxb, 8) +
          std::min<int64_t>(band * 8, int64_t(6) << 30) + 8 * arr(nsub + 1, 8) + 6 * arr(n, 4) + 2 * arr(C.n0, 4);
   }
 

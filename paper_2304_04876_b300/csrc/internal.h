@@ -286,6 +286,7 @@ struct KrylovScalars {
   double rz, rz_new, rz_oldz;    // (r,z), new (r,z), (r, z_old) for flexible beta
   double pq, rr, bb;
   double alpha, beta;
+  double xalpha;                 // PCG: alpha of the x update still to run (0: none)
   double tol2;                   // tol^2 * ||b||^2
   int iter, done, maxit, flexible;
   int bad;                       // NaN / Inf seen
@@ -442,7 +443,9 @@ struct Ctx {
   double* cvec = nullptr;
   double* yvec = nullptr;
   float* yvec32 = nullptr;           // A0^-1 c rounded once for the FP32 scatter (n0)
-  double* A0inv = nullptr;        // one dense block per problem
+  double* A0inv = nullptr;        // one dense block per problem (FP64 apply)
+  float* A0inv32 = nullptr;       // the same, rounded once (FP32/FP16 apply)
+  float* cvec32 = nullptr;        // c = Phi^T r in FP32 (FP32/FP16 apply)
   int* coarse_prob = nullptr;     // problem of each coarse column
   int* prob_c0 = nullptr;         // coarse column range of each problem
   int64_t* a0_off = nullptr;      // offset of each problem's block
@@ -469,6 +472,7 @@ struct Ctx {
   cudaStream_t graph_stream = nullptr;
   cudaStream_t aux_stream = nullptr;     // coarse branch of the apply
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_x = nullptr, ev_xdone = nullptr;   // PCG x update on the second stream
   // host staging for gdsw_solve_host
   double* hpin = nullptr;
   // events for timed apply
@@ -491,6 +495,7 @@ struct Ctx {
   bool serving = false;                  // members started one by one (gdsw_batch_start)
   cudaStream_t bgraph_stream = nullptr;
   int spmv_R = 256, spmv_maxne = 1, spmv_tiles = 1, spmv_grid = kNumSMsForCtx;
+  int spmv_U = 8;                      // entries in flight per row in the thread-per-row SpMV
   int spmv_W = 0;                    // lanes per row for long rows (0: the tiled kernel)
   int spmv_pipe = 0;                 // SpMV kernel for short rows (chosen by timing): 0 tiled, 1 tiled with
                                      // the next tile's loads in flight, 2 a thread per row

@@ -198,9 +198,11 @@ __global__ void __launch_bounds__(R, 2048 / R / 2) k_spmv_pipe(int n, int ntiles
 }
 
 // The same product with no shared memory: one thread per row loads its own
-// entries (the first eight in flight at once; neighbouring rows' entries are
-// adjacent, so the warp's loads share L1 lines) and sums them in column order,
-// so the FP64 FMAs do not queue behind shared-memory traffic.
+// entries (the first U in flight at once, U the longest row within 4..8;
+// neighbouring rows' entries are adjacent, so the warp's loads share L1 lines)
+// and sums them in column order, so the FP64 FMAs do not queue behind
+// shared-memory traffic.
+template <int U>
 __global__ void __launch_bounds__(256, 4) k_spmv_thread(int n, const int* __restrict__ rowptr,
                                                      const int* __restrict__ colind,
                                                      const double* __restrict__ val,
@@ -208,7 +210,6 @@ __global__ void __launch_bounds__(256, 4) k_spmv_thread(int n, const int* __rest
                                                      double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
-  constexpr int U = 8;
   double dot = 0.0;
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int row = base + threadIdx.x;
@@ -287,12 +288,11 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int n, const int* __restrict_
   }
 }
 
-// With alpha = (r,z)/(p,q) (divided once by the SpMV's last CTA): x += alpha p;
-// r -= alpha q; rr = ||r||^2; then the last CTA counts the iteration and
-// decides whether the loop ends.
-__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restrict__ x,
-                                                         double* __restrict__ r,
-                                                         const double* __restrict__ p,
+// With alpha = (r,z)/(p,q) (divided once by the SpMV's last CTA): r -= alpha q;
+// rr = ||r||^2; then the last CTA counts the iteration, hands alpha to the x
+// update (which runs beside the preconditioner: nothing before the next SpMV
+// reads x) and decides whether the loop ends.
+__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restrict__ r,
                                                          const double* __restrict__ q,
                                                          double* __restrict__ red, KrylovScalars* ks,
                                                          cudaGraphConditionalHandle handle,
@@ -307,24 +307,20 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
   double rr = 0.0;
   const int n2 = n >> 1;
   const int stride = gridDim.x * blockDim.x;
-  double2* x2 = reinterpret_cast<double2*>(x);
   double2* r2 = reinterpret_cast<double2*>(r);
-  const double2* p2 = reinterpret_cast<const double2*>(p);
   const double2* q2 = reinterpret_cast<const double2*>(q);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-    const double2 pi = p2[i], qi = q2[i];
-    double2 xi = x2[i], ri = r2[i];
-    xi.x += alpha * pi.x; xi.y += alpha * pi.y;
-    ri.x -= alpha * qi.x; ri.y -= alpha * qi.y;
-    x2[i] = xi;
+    const double2 qi = q2[i];
+    double2 ri = r2[i];
+    ri.x = fma(-alpha, qi.x, ri.x);
+    ri.y = fma(-alpha, qi.y, ri.y);
     r2[i] = ri;
     rr = fma(ri.x, ri.x, rr);
     rr = fma(ri.y, ri.y, rr);
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int i = n - 1;
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
+    const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
     rr = fma(ri, ri, rr);
   }
@@ -335,6 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
     if (threadIdx.x == 0) {
       ks->rr = s;
       ks->iter += 1;
+      ks->xalpha = alpha;
       int done = 0;
       if (!isfinite(s) || !isfinite(alpha) || !(ks->pq > 0.0)) { ks->bad = 1; done = 1; }
       else if (s <= ks->tol2) done = 1;
@@ -345,6 +342,31 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
       }
     }
   }
+}
+
+// x += alpha p with the alpha the update kernel handed over (0 when no
+// iteration ran since the last x update: nothing to add).  It runs on the
+// second stream after the coarse branch and must end before p changes (the
+// next k_pupdate waits for it); every CTA reads alpha before it arrives, and
+// the last one clears it.
+__global__ void __launch_bounds__(kThreads) k_pcg_xupdate(int n, double* __restrict__ x,
+                                                          const double* __restrict__ p,
+                                                          KrylovScalars* ks) {
+  const double alpha = ks->xalpha;
+  if (alpha != 0.0) {
+    const int n2 = n >> 1;
+    double2* x2 = reinterpret_cast<double2*>(x);
+    const double2* p2 = reinterpret_cast<const double2*>(p);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+      const double2 pi = p2[i];
+      double2 xi = x2[i];
+      xi.x = fma(alpha, pi.x, xi.x);
+      xi.y = fma(alpha, pi.y, xi.y);
+      x2[i] = xi;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) x[n - 1] = fma(alpha, p[n - 1], x[n - 1]);
+  }
+  if (arrive_last(&ks->ticket[4]) && threadIdx.x == 0) ks->xalpha = 0.0;
 }
 
 __global__ void k_pupdate(int n, const double* __restrict__ z, double* __restrict__ p,
@@ -772,7 +794,16 @@ gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, Kryl
   }
   if (c->spmv_pipe == 2) {
     const int grid = std::max(1, std::min(c->spmv_grid, (c->n + 255) / 256));
-    k_spmv_thread<<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate);
+    switch (c->spmv_U) {
+#define GDSW_SPMV_T(UU) \
+  case UU: k_spmv_thread<UU><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+      GDSW_SPMV_T(4)
+      GDSW_SPMV_T(5)
+      GDSW_SPMV_T(6)
+      GDSW_SPMV_T(7)
+      default: GDSW_SPMV_T(8)
+#undef GDSW_SPMV_T
+    }
     GDSW_CK(cudaGetLastError());
     return GDSW_OK;
   }
@@ -804,9 +835,21 @@ int vec_grid(const Ctx* c) { return std::min(c->red_grid, (c->n + kThreads - 1) 
 // once ks->done is set).
 gdsw_status pcg_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
   GDSW_TRY(launch_spmv(c, c->p, c->q, s, c->ks));
-  k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(c->n, c->x, c->r, c->p, c->q, c->red, c->ks, h, use_handle);
+  k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(c->n, c->r, c->q, c->red, c->ks, h, use_handle);
   GDSW_CK(cudaGetLastError());
+  // x += alpha p is off the path to the next SpMV: it goes on the second
+  // stream behind the coarse branch and is joined before p is overwritten
+  const bool aside = c->aux_stream != nullptr;
+  if (aside) GDSW_CK(cudaEventRecord(c->ev_x, s));
   GDSW_TRY(apply_enqueue(c, c->r, c->z, s, true));
+  cudaStream_t xs = aside ? c->aux_stream : s;
+  if (aside) GDSW_CK(cudaStreamWaitEvent(xs, c->ev_x, 0));
+  k_pcg_xupdate<<<vec_grid(c), kThreads, 0, xs>>>(c->n, c->x, c->p, c->ks);
+  GDSW_CK(cudaGetLastError());
+  if (aside) {
+    GDSW_CK(cudaEventRecord(c->ev_xdone, xs));
+    GDSW_CK(cudaStreamWaitEvent(s, c->ev_xdone, 0));
+  }
   k_pupdate<<<vec_grid(c), kThreads, 0, s>>>(c->n, c->z, c->p, c->ks);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
@@ -853,6 +896,11 @@ gdsw_status spmv_configure(Ctx* c, const int* rowptr) {
     c->spmv_tiles = 1;
     return GDSW_OK;
   }
+  // the thread-per-row kernel keeps the first U entries of a row in flight;
+  // U is the longest row (4..8), so no FP64 FMA is issued for an empty slot
+  int longest = 0;
+  for (int i = 0; i < n; ++i) longest = std::max(longest, rowptr[i + 1] - rowptr[i]);
+  c->spmv_U = std::min(8, std::max(4, longest));
   int R = 256, maxne = 0;
   for (; R >= 32; R >>= 1) {
     maxne = 0;
@@ -917,7 +965,7 @@ gdsw_status spmv_tune(Ctx* c, cudaStream_t s) {
   }
   {
     int per_sm = 1;
-    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_thread, 256, 0));
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_thread<8>, 256, 0));
     g[2] = std::max(1, per_sm) * kNumSMs;
   }
   // the pipelined kernel holds eight entries per thread of a tile
@@ -1140,21 +1188,23 @@ gdsw_status pcg_iteration_timed(Ctx* c, const double* b, cudaStream_t s, double*
   }
   if (st == GDSW_OK) {
     cudaEventRecord(ev[1], s);
-    k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(n, c->x, c->r, c->p, c->q, c->red, c->ks,
-                                                   cudaGraphConditionalHandle{}, 0);
+    k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(n, c->r, c->q, c->red, c->ks, cudaGraphConditionalHandle{}, 0);
     if (cudaGetLastError() != cudaSuccess) { set_error("vector update launch failed"); st = GDSW_ERR_CUDA; }
   }
   if (st == GDSW_OK) st = apply_timed_dots(c, c->r, c->z, s, ap);
   if (st == GDSW_OK) {
-    k_pupdate<<<vec_grid(c), kThreads, 0, s>>>(n, c->z, c->p, c->ks);
+    // one stream: the x update after the apply, then p
+    k_pcg_xupdate<<<vec_grid(c), kThreads, 0, s>>>(n, c->x, c->p, c->ks);
     cudaEventRecord(ev[7], s);
-    if (cudaEventSynchronize(ev[7]) != cudaSuccess) { set_error("timed iteration failed"); st = GDSW_ERR_CUDA; }
+    k_pupdate<<<vec_grid(c), kThreads, 0, s>>>(n, c->z, c->p, c->ks);
+    cudaEventRecord(ev[8], s);
+    if (cudaEventSynchronize(ev[8]) != cudaSuccess) { set_error("timed iteration failed"); st = GDSW_ERR_CUDA; }
   }
   if (st == GDSW_OK) st = check_device_errors(c, s);
   if (st == GDSW_OK) {
-    // spmv, update, local, phiT, coarse, combine (events ev[1..6]), pupdate
-    const int from[7] = {0, 1, 2, 3, 4, 5, 6}, to[7] = {1, 2, 3, 4, 5, 6, 7};
-    for (int q = 0; q < 7; ++q) {
+    // spmv, update, local, phiT, coarse, combine (events ev[0..6]), pupdate, x update
+    const int from[8] = {0, 1, 2, 3, 4, 5, 7, 6}, to[8] = {1, 2, 3, 4, 5, 6, 8, 7};
+    for (int q = 0; q < 8; ++q) {
       float t = 0.f;
       cudaEventElapsedTime(&t, ev[from[q]], ev[to[q]]);
       ms[q] = t;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 
+#include "common.cuh"
 #include "internal.h"
 
 namespace gdsw {
@@ -69,6 +70,26 @@ gdsw_status rate_t(double* fma_per_second, cudaStream_t s) {
   return st;
 }
 
+// One random 64-bit pattern per index (splitmix64 of seed + i * golden ratio):
+// as a double (every other one with its exponent moved into or near the
+// binary32 range, where rounding matters) narrowed both ways, and its low 32
+// bits as a float widened both ways; counts the results that differ in any bit
+// (NaNs compare equal to NaNs).
+__global__ void k_check_conversions(uint64_t seed, int64_t count, unsigned long long* bad) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
+    uint64_t x = seed + static_cast<uint64_t>(i) * 0x9E3779B97F4A7C15ull;
+    x ^= x >> 30; x *= 0xBF58476D1CE4E5B9ull; x ^= x >> 27; x *= 0x94D049BB133111EBull; x ^= x >> 31;
+    uint64_t y = x;
+    if (i & 1) y = (x & 0x800fffffffffffffull) | (uint64_t(870 + (x >> 20) % 300) << 52);
+    const double d = __longlong_as_double(static_cast<long long>(y));
+    const float hw = __double2float_rn(d), sw = f32_from_f64(d);
+    if (__float_as_uint(hw) != __float_as_uint(sw) && !(hw != hw && sw != sw)) atomicAdd(bad, 1ull);
+    const float f = __uint_as_float(static_cast<uint32_t>(x));
+    const double hd = static_cast<double>(f), sd = f64_from_f32(f);
+    if (__double_as_longlong(hd) != __double_as_longlong(sd) && !(hd != hd && sd != sd)) atomicAdd(bad + 1, 1ull);
+  }
+}
+
 }  // namespace
 
 }  // namespace gdsw
@@ -81,4 +102,32 @@ extern "C" GDSW_API gdsw_status gdsw_measure_fma_rate(int32_t precision, double*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return precision == GDSW_PREC_FP64 ? gdsw::rate_t<double>(fma_per_second, s)
                                 : gdsw::rate_t<float>(fma_per_second, s);
+}
+
+extern "C" GDSW_API gdsw_status gdsw_check_conversions(uint64_t seed, int64_t count, uint64_t* mismatches,
+                                                      void* stream) {
+  if (mismatches == nullptr || count < 0) {
+    gdsw::set_error("gdsw_check_conversions: mismatches must be non-NULL and count >= 0");
+    return GDSW_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* bad = nullptr;
+  unsigned long long host[2] = {0, 0};
+  cudaError_t e = cudaMalloc(&bad, sizeof(host));
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(host), s);
+  if (e == cudaSuccess && count > 0) {
+    const int grid = static_cast<int>(std::min<int64_t>((count + 255) / 256, int64_t(gdsw::kNumSMs) * 16));
+    gdsw::k_check_conversions<<<grid, 256, 0, s>>>(seed, count, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, bad, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (bad) cudaFree(bad);
+  if (e != cudaSuccess) {
+    gdsw::set_error("gdsw_check_conversions: %s", cudaGetErrorString(e));
+    return GDSW_ERR_CUDA;
+  }
+  mismatches[0] = host[0];
+  mismatches[1] = host[1];
+  return GDSW_OK;
 }

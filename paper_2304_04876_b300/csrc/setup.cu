@@ -1297,7 +1297,17 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     GDSW_CK(cudaGetLastError());
     c->stats.setup_phase_seconds[4] = now_s() - t0;
     t0 = now_s();
-    GDSW_TRY(dalloc(c, &c->A0inv, a0_off[np_]));
+    // the inverse is formed in FP64; an FP32/FP16 apply keeps it rounded once to
+    // FP32 (the whole preconditioner in single precision, Sec. VIII)
+    double* a0inv64 = nullptr;
+    if (c->fp32) {
+      GDSW_TRY(sc.get(&a0inv64, a0_off[np_]));
+      GDSW_TRY(dalloc(c, &c->A0inv32, a0_off[np_]));
+      GDSW_TRY(dalloc(c, &c->cvec32, std::max(1, C.n0)));
+    } else {
+      GDSW_TRY(dalloc(c, &c->A0inv, a0_off[np_]));
+      a0inv64 = c->A0inv;
+    }
     c->stats.a0_entries = a0_off[np_];
     double* d_W;
     const int maxnbk = (maxb + NB - 1) / NB;
@@ -1315,8 +1325,10 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
           k_syrk_update<<<dim3(rest, rest), 256, 0, s>>>(Aq, nb0, J);
         }
       }
-      k_chol_inverse<<<nbk, 256, 0, s>>>(Aq, nb0, d_W, c->A0inv + a0_off[q]);
+      k_chol_inverse<<<nbk, 256, 0, s>>>(Aq, nb0, d_W, a0inv64 + a0_off[q]);
     }
+    if (c->fp32)
+      k_convert<float><<<grid_for(a0_off[np_], 256), 256, 0, s>>>(a0_off[np_], a0inv64, c->A0inv32);
     GDSW_CK(cudaGetLastError());
     GDSW_TRY(read_err(d_err, s, "coarse Cholesky"));
     // Phi in the apply precision

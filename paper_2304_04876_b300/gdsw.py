@@ -120,6 +120,7 @@ SIGNATURES = {
     "gdsw_spmv_dot_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gdsw_measure_fma_rate": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
+    "gdsw_check_conversions": (C.c_int, [C.c_uint64, C.c_int64, C.POINTER(C.c_uint64), C.c_void_p]),
     "gdsw_status_string": (C.c_char_p, [C.c_int]),
     "gdsw_last_error": (C.c_char_p, []),
 }
@@ -284,11 +285,11 @@ class Handle:
                "gdsw_apply_timed")
         return list(ms)
 
-    PCG_KERNELS = ("spmv", "update", "local", "phiT", "coarse", "combine", "pupdate")
+    PCG_KERNELS = ("spmv", "update", "local", "phiT", "coarse", "combine", "pupdate", "xupdate")
 
     def pcg_iteration_timed(self, b, stream=None) -> dict:
         """Device ms of each kernel of one PCG iteration from right-hand side b (CUDA events)."""
-        ms = (C.c_double * 7)()
+        ms = (C.c_double * len(self.PCG_KERNELS))()
         _check(load().gdsw_pcg_iteration_timed(self._handle(), _ptr(b), _stream(stream), ms),
                "gdsw_pcg_iteration_timed")
         return dict(zip(self.PCG_KERNELS, list(ms)))
@@ -401,6 +402,14 @@ def measure_fma_rate(precision: str = "fp64", stream=None) -> float:
     _check(load().gdsw_measure_fma_rate(PRECISION[precision], C.byref(out), _stream(stream)),
            "gdsw_measure_fma_rate")
     return out.value
+
+
+def check_conversions(seed: int, count: int, stream=None) -> tuple:
+    """(double->float, float->double) mismatch counts of the library's integer-ALU
+    conversions against the hardware ones on `count` random bit patterns."""
+    out = (C.c_uint64 * 2)()
+    _check(load().gdsw_check_conversions(seed, count, out, _stream(stream)), "gdsw_check_conversions")
+    return int(out[0]), int(out[1])
 
 
 def spmv_dot_noalloc(rowptr, colind, val, x, y, dot, nnz: int, stream=None):
