@@ -183,7 +183,9 @@ typedef struct {
                              L2 (level-scheduled or Jacobi), 3 level records
                              streamed with a barrier per level, 4 the same
                              without one (per-row flags), 5 Jacobi sweeps on
-                             blocks resident in shared memory              */
+                             blocks resident in shared memory, 6 row
+                             programs with per-thread prefetch (FP32, rows of
+                             at most 3 entries)                              */
 } gdsw_stats;
 
 typedef struct gdsw_ctx* gdsw_handle;

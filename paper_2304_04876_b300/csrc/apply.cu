@@ -514,6 +514,123 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1) k_local_pipe(const double*
   for (int i = threadIdx.x; i < m; i += nt) zloc[base + i] = v[i];
 }
 
+// ---- level-scheduled solve from row programs ----
+//
+// One CTA of kStepRows threads per subdomain executes the subdomain's row
+// program (its L levels, then its U levels, each level cut into steps of at
+// most kStepRows rows; thread t takes row t of a step).  Thread t's
+// instruction of a step -- A: float4 {a0, a1, a2, inverse diagonal}, C: uint2
+// {c0 | c1 << 16, c2 | row << 16} -- comes with its own cp.async copies into
+// its slot of a D-step ring, issued D - 1 steps ahead; no thread waits on
+// another for data, so the only synchronisation is one CTA barrier at the end
+// of each level, and there is no spin-wait that could run out.  Per row: acc
+// = z[row]; acc -= a_k z[c_k] (k = 0, 1, 2, slot order); z[row] = acc *
+// inverse diagonal -- the arithmetic of the row-major records, so the result
+// equals k_local_pipe's.  The overlap indices arrive the same way (16-byte
+// copies of the 4-word-padded slice) before r is gathered.
+//
+// (Bulk copies of whole steps by one thread into mbarrier-tracked slots were
+// measured slower here: every thread then polls the barrier, and the refills
+// wait for the level barriers.)
+template <int D>
+__global__ void __launch_bounds__(kStepRows, 4) k_local_steps(const double* __restrict__ r,
+                                                           const int* __restrict__ om_ptr,
+                                                           const int* __restrict__ om_dofs,
+                                                           const int* __restrict__ step_ptr,
+                                                           const int2* __restrict__ steps,
+                                                           const float4* __restrict__ prog_a,
+                                                           const uint2* __restrict__ prog_c,
+                                                           int step_max, float* __restrict__ zloc,
+                                                           const KrylovScalars* __restrict__ ks, BatchGate gate) {
+  static_assert(D >= 3, "the ring refills the slot read one step earlier");
+  constexpr int NT = kStepRows;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (ks != nullptr && ks->done) return;
+  const int s = blockIdx.x;
+  if (gate_sub_off(gate, s)) return;
+  const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+  const int st0 = step_ptr[s], nst = step_ptr[s + 1] - st0;
+  const int t = threadIdx.x;
+  float4* ring_a = reinterpret_cast<float4*>(smem_raw);
+  uint2* ring_c = reinterpret_cast<uint2*>(smem_raw + size_t(D) * NT * 16);
+  int2* stp = reinterpret_cast<int2*>(smem_raw + size_t(D) * NT * 24);
+  unsigned char* vreg = smem_raw + size_t(D) * NT * 24 + ((size_t(step_max) * 8 + 15) & ~size_t(15));
+  const int off = base & 3;
+  const int cnt = m > 0 ? (off + m + 3) & ~3 : 0;
+  const int* idx = reinterpret_cast<const int*>(vreg) + off;
+  float* v = reinterpret_cast<float*>(vreg) + off;
+  // group 0: the overlap indices; groups 1..D: the first D steps
+  for (int q = t; q < cnt / 4; q += NT) cp_async16(vreg + 16 * q, om_dofs + (base - off) + 4 * q);
+  cp_async_commit();
+  for (int d = 0; d < D; ++d) {
+    if (d < nst) {
+      const int2 sd = steps[st0 + d];
+      if (t < (sd.y & 0xffff)) {
+        cp_async16(&ring_a[d * NT + t], prog_a + sd.x + t);
+        cp_async8(&ring_c[d * NT + t], prog_c + sd.x + t);
+      }
+    }
+    cp_async_commit();
+  }
+  for (int q = t; q < nst; q += NT) stp[q] = steps[st0 + q];
+  cp_async_wait<D>();
+  __syncthreads();
+  gather_staged(r, idx, v, m, NT);
+  // the first step's instruction into registers; each later one is read
+  // before the previous step's barrier, so a step starts from registers
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  uint2 cc = make_uint2(0u, 0u);
+  if (nst > 0) {
+    cp_async_wait<D - 1>();
+    if (t < (stp[0].y & 0xffff)) {
+      a = ring_a[t];
+      cc = ring_c[t];
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < nst; ++i) {
+    const int2 sd = stp[i];
+    // refill the slot read during the previous step (its values are already
+    // in registers, so the copy cannot overtake the read) with step i - 1 + D
+    if (i > 0) {
+      const int j = i - 1 + D;
+      if (j < nst) {
+        const int2 sn = stp[j];
+        const int slot = (i - 1) % D;
+        if (t < (sn.y & 0xffff)) {
+          cp_async16(&ring_a[slot * NT + t], prog_a + sn.x + t);
+          cp_async8(&ring_c[slot * NT + t], prog_c + sn.x + t);
+        }
+      }
+      cp_async_commit();
+    }
+    if (t < (sd.y & 0xffff)) {
+      const int row = cc.y >> 16;
+      float acc = v[row];
+      acc = fmaf(-a.x, v[cc.x & 0xffff], acc);
+      acc = fmaf(-a.y, v[cc.x >> 16], acc);
+      acc = fmaf(-a.z, v[cc.y & 0xffff], acc);
+      v[row] = acc * a.w;
+    }
+    if (i + 1 < nst) {
+      // step i + 1's group: D + i groups of steps committed, i + 2 of them done
+      cp_async_wait<D - 2>();
+      if (t < (stp[i + 1].y & 0xffff)) {
+        const int slot = (i + 1) % D;
+        a = ring_a[slot * NT + t];
+        cc = ring_c[slot * NT + t];
+      }
+    }
+    if (sd.y >> 16) __syncthreads();
+  }
+  for (int q = t; q < m; q += NT) zloc[base + q] = v[q];
+}
+
+// Shared memory of k_local_steps with D slots.
+inline size_t steps_smem_bytes(int D, int step_max, int max_m) {
+  return size_t(D) * kStepRows * 24 + ((size_t(step_max) * 8 + 15) & ~size_t(15)) + pipe_vector_bytes(max_m, 4);
+}
+
 // ---- level-scheduled solve without a barrier per level ----
 //
 // The same records and producer as k_local_pipe, but the consumers meet at no
@@ -1094,71 +1211,108 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const TA* __restric
   }
 }
 
-// z_g = sum over subdomains containing g of (z_s)_g (ascending subdomain
-// order) + (Phi y)_g, one unknown per thread over the block-row positions
-// (pos_blk gives the Phi block of each position).  With `dots`, also
-// (r, z_new) and (r, z_old), reduced by the last CTA, which sets beta and
-// (r, z) for the PCG update.
+// yb[i] = y[bcol[i]]: the coarse solution at every column slot of the Phi
+// blocks, in the apply's precision, so the scatter-add reads one array (no
+// column index, then value, per Phi entry).
 template <class T>
-__device__ __forceinline__ double combine_one(int p, const int* __restrict__ pos_blk,
-                                              const int* __restrict__ brow_ptr,
-                                              const int* __restrict__ bcol_ptr,
-                                              const int* __restrict__ bcol,
-                                              const int64_t* __restrict__ phi_off,
-                                              const T* __restrict__ phi, const T* __restrict__ y,
-                                              const int* __restrict__ pull_ptr,
-                                              const int* __restrict__ pull_pos,
-                                              const T* __restrict__ zloc) {
-  // summed in the preconditioner's precision T, converted once
-  T acc = T(0);
-  const int q0 = pull_ptr[p], q1 = pull_ptr[p + 1];
-  for (int q = q0; q < q1; ++q) acc += zloc[pull_pos[q]];
-  const int b = pos_blk[p];
-  const int c0 = bcol_ptr[b], k = bcol_ptr[b + 1] - c0;
-  if (k > 0) {
-    const int p0 = brow_ptr[b];
-    const int nr = brow_ptr[b + 1] - p0;
-    const T* Ph = phi + phi_off[b] + (p - p0);
-    for (int u = 0; u < k; ++u) acc = fma(Ph[int64_t(u) * nr], y[bcol[c0 + u]], acc);
-  }
-  return widen<T>(acc);
+__global__ void k_coarse_slots(int nslots, const int* __restrict__ bcol, const T* __restrict__ y,
+                               T* __restrict__ yb, const KrylovScalars* __restrict__ ks) {
+  if (ks != nullptr && ks->done) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) yb[i] = y[bcol[i]];
 }
 
-template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_combine(
+// z_g = sum over subdomains containing g of (z_s)_g (ascending subdomain
+// order) + (Phi y)_g, one unknown per thread over the block-row positions
+// (pos_blk gives the Phi block of each position), summed in the
+// preconditioner's precision T and widened once.  With `dots`, also
+// (r, z_new) and (r, z_old), reduced by the last CTA, which sets beta and
+// (r, z) for the PCG update.
+//
+// Each thread takes NP positions per trip and moves through them in phases,
+// so that the loads of a phase are in flight together for all of them:
+// indices; then r, the first two pulls and the block's shape; then the local
+// values and the Phi row, four columns at a time (each position's sum is still
+// formed in the order pulls, then Phi columns).
+template <class T, int NP>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_combine(
     int n, const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_dof,
     const int* __restrict__ pos_blk, const int* __restrict__ brow_ptr,
-    const int* __restrict__ bcol_ptr, const int* __restrict__ bcol,
-    const int64_t* __restrict__ phi_off, const T* __restrict__ phi, const T* __restrict__ y,
-    const int* __restrict__ pull_ptr, const int* __restrict__ pull_pos, const T* __restrict__ zloc,
-    int dots, double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
+    const int* __restrict__ bcol_ptr, const int64_t* __restrict__ phi_off, const T* __restrict__ phi,
+    const T* __restrict__ yb, const int* __restrict__ pull_ptr, const int* __restrict__ pull_pos,
+    const T* __restrict__ zloc, int dots, double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
   double d_new = 0.0, d_old = 0.0;
   const int stride = gridDim.x * blockDim.x;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += 4 * stride) {
-    // four independent positions per trip keep more loads in flight
-    int g[4];
-    double a[4];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += NP * stride) {
+    int g[NP], b[NP], q0[NP], q1[NP];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NP; ++j) {
       const int pj = p + j * stride;
-      const bool live = pj < n && !gate_blk_off(gate, pos_blk[pj]);
-      g[j] = live ? brow_dof[pj] : -1;
-      a[j] = live ? combine_one(pj, pos_blk, brow_ptr, bcol_ptr, bcol, phi_off, phi, y, pull_ptr, pull_pos, zloc)
-                  : 0.0;
+      const bool in = pj < n;
+      b[j] = in ? pos_blk[pj] : 0;
+      g[j] = in ? brow_dof[pj] : -1;
+      q0[j] = in ? pull_ptr[pj] : 0;
+      q1[j] = in ? pull_ptr[pj + 1] : 0;
     }
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      if (g[j] >= 0 && gate_blk_off(gate, b[j])) g[j] = -1;
+    double rg[NP], zo[NP];
+    int pull0[NP], pull1[NP], c0[NP], k[NP], p0[NP], nr[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const bool live = g[j] >= 0;
+      rg[j] = live && dots ? r[g[j]] : 0.0;
+      zo[j] = live && dots > 1 ? z[g[j]] : 0.0;
+      pull0[j] = live && q0[j] < q1[j] ? pull_pos[q0[j]] : -1;
+      pull1[j] = live && q0[j] + 1 < q1[j] ? pull_pos[q0[j] + 1] : -1;
+      c0[j] = live ? bcol_ptr[b[j]] : 0;
+      k[j] = live ? bcol_ptr[b[j] + 1] - c0[j] : 0;
+      p0[j] = live ? brow_ptr[b[j]] : 0;
+      nr[j] = live ? brow_ptr[b[j] + 1] - p0[j] : 0;
+    }
+    T acc[NP];
+    const T* ph[NP];
+    int kmax = 0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      acc[j] = T(0);
+      if (pull0[j] >= 0) acc[j] += zloc[pull0[j]];
+      if (pull1[j] >= 0) acc[j] += zloc[pull1[j]];
+      for (int q = q0[j] + 2; q < q1[j]; ++q) acc[j] += zloc[pull_pos[q]];
+      ph[j] = phi + (k[j] > 0 ? phi_off[b[j]] + (p + j * stride - p0[j]) : 0);
+      kmax = max(kmax, k[j]);
+    }
+    for (int u0 = 0; u0 < kmax; u0 += 4) {
+      T pv[NP][4], yv[NP][4];
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool on = u0 + u < k[j];
+          pv[j][u] = on ? ph[j][int64_t(u0 + u) * nr[j]] : T(0);
+          yv[j][u] = on ? yb[c0[j] + u0 + u] : T(0);
+        }
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u0 + u < k[j]) acc[j] = fma(pv[j][u], yv[j][u], acc[j]);
+    }
+    double a[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) a[j] = widen<T>(acc[j]);
     if (dots) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < NP; ++j) {
         if (g[j] < 0) continue;
-        const double rg = r[g[j]];
-        if (dots > 1) d_old = fma(rg, z[g[j]], d_old);
-        d_new = fma(rg, a[j], d_new);
+        if (dots > 1) d_old = fma(rg[j], zo[j], d_old);
+        d_new = fma(rg[j], a[j], d_new);
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NP; ++j)
       if (g[j] >= 0) z[g[j]] = a[j];
   }
   if (!dots) return;
@@ -1209,6 +1363,22 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
     dim3 grid((c->max_m + 31) / 32, c->nsub);
     k_local_dense<T><<<grid, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
                                             c->ainv_off, zl, ks, gate);
+  } else if (c->step_depth > 0) {
+    // row programs with per-thread prefetch (FP32, rows of at most 3 entries)
+    if constexpr (std::is_same<T, float>::value) {
+      const size_t shm = steps_smem_bytes(c->step_depth, c->step_max, c->max_m);
+#define GDSW_STEPS_LAUNCH(DD)                                                                                  \
+  k_local_steps<DD><<<c->nsub, kStepRows, shm, s>>>(r, c->om_ptr, c->om_dofs, c->step_ptr, c->steps,           \
+                                                   reinterpret_cast<const float4*>(c->step_a),                 \
+                                                   reinterpret_cast<const uint2*>(c->step_c), c->step_max, zl, \
+                                                   ks, gate)
+      switch (c->step_depth) {
+        case 4: GDSW_STEPS_LAUNCH(4); break;
+        case 12: GDSW_STEPS_LAUNCH(12); break;
+        default: GDSW_STEPS_LAUNCH(8); break;
+      }
+#undef GDSW_STEPS_LAUNCH
+    }
   } else if (c->rec_stages > 0 && c->rec_sf) {
     // without a barrier per level (one unknown per row group of at most 4, rows of up to 8 entries)
     const int vb = static_cast<int>(pipe_vector_bytes(c->max_m, sizeof(T)));
@@ -1326,6 +1496,13 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const
   else
     k_coarse_gemv<double><<<grid, 256, 0, s>>>(c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off,
                                                c->cvec, c->yvec, c->yvec32, ks, gate);
+  if (c->n_bslots > 0) {
+    const int sg = std::min((c->n_bslots + 255) / 256, kNumSMs * 4);
+    if (c->fp32)
+      k_coarse_slots<float><<<sg, 256, 0, s>>>(c->n_bslots, c->bcol, c->yvec32, static_cast<float*>(c->yslot), ks);
+    else
+      k_coarse_slots<double><<<sg, 256, 0, s>>>(c->n_bslots, c->bcol, c->yvec, static_cast<double*>(c->yslot), ks);
+  }
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -1334,11 +1511,11 @@ template <class T>
 gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated,
                            const BatchGate& gate) {
   const int grid = std::max(1, std::min(c->combine_grid, (c->n + 255) / 256));
-  k_combine<T><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
-                                    c->bcol, c->phi_off, static_cast<const T*>(c->phi),
-                                    c->fp32 ? reinterpret_cast<const T*>(c->yvec32) : reinterpret_cast<const T*>(c->yvec),
-                                    c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),
-                                    dots ? (c->flexible ? 2 : 1) : 0, c->red, (dots || gated) ? c->ks : nullptr, gate);
+  k_combine<T, 2><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
+                                       c->phi_off, static_cast<const T*>(c->phi),
+                                       static_cast<const T*>(c->yslot), c->pull_ptr, c->pull_pos,
+                                       static_cast<const T*>(c->zloc), dots ? (c->flexible ? 2 : 1) : 0, c->red,
+                                       (dots || gated) ? c->ks : nullptr, gate);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -1427,6 +1604,29 @@ gdsw_status pipe_occupancy(const Ctx* c, int S, bool sf, int* per_sm) {
                          : pipe_occupancy_t<double, double, 1>(S, sf, shm, th, per_sm);
 }
 
+// Resident CTAs per SM of the row-program solve with D slots per thread
+// (raises its dynamic shared memory limit first; 0 when it does not fit).
+gdsw_status steps_occupancy(Ctx* c, int D, int* per_sm) {
+  const size_t shm = steps_smem_bytes(D, c->step_max, c->max_m);
+  *per_sm = 0;
+  if (shm > size_t(max_block_smem_optin())) return GDSW_OK;
+  switch (D) {
+    case 4:
+      GDSW_CK(allow_max_dynamic_smem(k_local_steps<4>));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_steps<4>, kStepRows, shm));
+      break;
+    case 12:
+      GDSW_CK(allow_max_dynamic_smem(k_local_steps<12>));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_steps<12>, kStepRows, shm));
+      break;
+    default:
+      GDSW_CK(allow_max_dynamic_smem(k_local_steps<8>));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_steps<8>, kStepRows, shm));
+      break;
+  }
+  return GDSW_OK;
+}
+
 // Measured choice of the pipelined local solve's shape: every ring depth that
 // fits, with 128 to 992 consumer threads, timed over three launches each
 // (CUDA events, after one warm-up launch) on a zero right-hand side, and the
@@ -1481,6 +1681,27 @@ gdsw_status tune_local(Ctx* c) {
     }
   }
   c->rec_sf = false;
+  // the row-program kernel with 4, 8 or 12 steps in flight per thread
+  int best_depth = 0;
+  if (c->steps != nullptr && c->fp32 && !c->fp16) {
+    for (int D : {4, 8, 12}) {
+      if (st != GDSW_OK) break;
+      int per_sm = 0;
+      st = steps_occupancy(c, D, &per_sm);
+      if (st != GDSW_OK || per_sm == 0) continue;
+      c->step_depth = D;
+      st = launch_local<float>(c, r, s, nullptr, BatchGate{});
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep) st = launch_local<float>(c, r, s, nullptr, BatchGate{});
+      cudaEventRecord(e1, s);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) { fail(e); break; }
+      if (ms < best) { best = ms; best_depth = D; }
+    }
+    c->step_depth = 0;
+  }
   // the unpipelined level-scheduled kernel (factors read through L2), with
   // 256 to 1024 threads, as further candidates
   int best_tri = c->tri_threads;
@@ -1497,8 +1718,9 @@ gdsw_status tune_local(Ctx* c) {
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) { fail(e); break; }
-    if (ms < best) { best = ms; best_s = 0; best_tri = tt; }
+    if (ms < best) { best = ms; best_s = 0; best_tri = tt; best_depth = 0; }
   }
+  c->step_depth = best_depth;
   c->rec_stages = best_s;
   c->rec_consumers = best_nt;
   c->rec_sf = best_s > 0 && best_sf;
@@ -1668,15 +1890,23 @@ gdsw_status apply_configure(Ctx* c) {
   if (const char* e = getenv("GDSW_PIPE_PREFETCH")) c->rec_prefetch = std::max(0, atoi(e)) & ~15;
   // GDSW_TEST_STALL=1: the failure test of the bounded waits (see k_local_pipe)
   if (const char* e = getenv("GDSW_TEST_STALL")) c->stall_test = e[0] == '1';
-  // GDSW_LOCAL_SHAPE="stages,threads[,barrier_free]" fixes the shape instead
-  // of timing it (for profilers, under which the timings mean nothing, and for
-  // the failure tests); barrier_free 1 selects the solve without a barrier
-  // per level
+  // GDSW_LOCAL_SHAPE="stages,threads[,kind]" fixes the shape instead of
+  // timing it (for profilers, under which the timings mean nothing, and for
+  // the failure tests); kind 1 selects the solve without a barrier per level,
+  // kind 2 the row programs with `stages` steps in flight per thread
   const char* shape = getenv("GDSW_LOCAL_SHAPE");
   if (c->rec_stages > 0 && shape != nullptr) {
     int st = 0, nt = 0, sf = 0;
     const int got = sscanf(shape, "%d,%d,%d", &st, &nt, &sf);
-    if (got >= 2 && (st == 0 || st == 2 || st == 4 || st == 8 || st == 16) &&
+    if (got == 3 && sf == 2 && c->steps != nullptr && c->fp32 && !c->fp16 && (st == 4 || st == 8 || st == 12)) {
+      int per_sm = 0;
+      GDSW_TRY(steps_occupancy(c, st, &per_sm));
+      if (per_sm == 0) {
+        set_error("GDSW_LOCAL_SHAPE=%s does not fit the shared memory", shape);
+        return GDSW_ERR_UNSUPPORTED;
+      }
+      c->step_depth = st;
+    } else if (got >= 2 && (st == 0 || st == 2 || st == 4 || st == 8 || st == 16) &&
         (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 1024)) {
       c->rec_stages = st;
       if (st > 0) c->rec_consumers = nt == 1024 ? 512 : nt; else c->tri_threads = nt;
@@ -1696,8 +1926,8 @@ gdsw_status apply_configure(Ctx* c) {
     int dev = 0, sms = kNumSMs, per_sm = 1;
     GDSW_CK(cudaGetDevice(&dev));
     GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (c->fp32) GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<float>, 256, 0));
-    else GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<double>, 256, 0));
+    if (c->fp32) GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<float, 2>, 256, 0));
+    else GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<double, 2>, 256, 0));
     c->combine_grid = std::max(1, per_sm) * sms;
   }
   return GDSW_OK;

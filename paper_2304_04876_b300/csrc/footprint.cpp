@@ -88,6 +88,17 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
     int64_t nrec = 0;
     R += arr(record_stream_bytes(P, vrec, &nrec), 1) + arr(nsub + 1, 4) + 2 * arr(nrec, 4);
     if (o.trsv == GDSW_TRSV_JACOBI) R += arr(jacobi_block_bytes(P, vrec), 1) + 2 * arr(2 * nsub, 4);
+    // row programs (FP32, one unknown per node, rows of at most 3 entries):
+    // 24 bytes per row of each triangle, one int2 per step
+    int maxK = 0;
+    for (int k : P.L.lev_K) maxK = std::max(maxK, k);
+    for (int k : P.U.lev_K) maxK = std::max(maxK, k);
+    if (P.dpn == 1 && o.precision == GDSW_PREC_FP32 && o.trsv == GDSW_TRSV_LEVELSCHED && maxK <= 3 && sum_m > 0) {
+      int64_t nsteps = 0;
+      for (const EllPlan* E : {&P.L, &P.U})
+        for (int nr : E->lev_nr) nsteps += (nr + kStepRows - 1) / kStepRows;
+      R += arr(2 * sum_m, 16) + arr(2 * sum_m, 8) + arr(nsteps, 8) + arr(nsub + 1, 4);
+    }
   } else if (P.max_m > exact_dense_max() || [&] {
                int64_t d = 0;
                for (int q = 0; q < P.nsub; ++q) d += int64_t(P.om_ptr[q + 1] - P.om_ptr[q]) * (P.om_ptr[q + 1] - P.om_ptr[q]);
@@ -122,6 +133,7 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
   GDSW_TRY(build_coarse_plan(P, SP, rank, coarse && nown > 0, &C));
   auto vb = [](const std::vector<int>& x) { return arr(static_cast<int64_t>(x.size()), 4); };
   R += vb(C.brow_ptr) + vb(C.brow_dof) + vb(C.bcol_ptr) + vb(C.bcol) +
+       arr(std::max<int64_t>(1, static_cast<int64_t>(C.bcol.size())), v) +
        arr(static_cast<int64_t>(C.phi_off.size()), 8) + vb(C.cs_ptr) + vb(C.cs_idx) + vb(C.pull_ptr) +
        vb(C.pull_pos) + vb(C.pos_blk) + vb(C.chunk_blk) + vb(C.chunk_r0) + vb(C.chunk_r1) + vb(C.chunk_slot) +
        arr(C.n_slots, 8) + 2 * arr(C.n0, 8);

@@ -295,6 +295,7 @@ struct KrylovScalars {
 };
 
 constexpr int kNumSMsForCtx = 148;
+constexpr int kStepRows = 128;       // rows per step of a row program (= its kernel's threads)
 
 // Per-problem PCG state of a batched handle.  `start` makes the next
 // iteration the PCG prologue for this problem (step lengths 0: r stays, z = M r,
@@ -390,6 +391,13 @@ struct Ctx {
   int64_t rec_total_bytes = 0;
   int rec_stages = 0;                // ring depth chosen at setup (0 = not used)
   int rec_max_width = 0;             // widest level (off-diagonal entries per row)
+  // row programs of the prefetching level-scheduled solve (k_local_steps)
+  float* step_a = nullptr;           // float4 per row: three entries, inverse diagonal
+  uint32_t* step_c = nullptr;        // uint2 per row: three columns, the row
+  int2* steps = nullptr;             // {first row, rows | level end << 16}
+  int* step_ptr = nullptr;           // nsub+1: step range of each subdomain
+  int step_max = 0;                  // most steps of one subdomain
+  int step_depth = 0;                // steps in flight per thread; 0: kernel not used
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int rec_max_rows = 0;              // most rows in one level
   int rec_consumers = 256;           // consumer threads of the pipelined solve
@@ -429,6 +437,8 @@ struct Ctx {
   // Phi blocks
   int* brow_ptr = nullptr; int* brow_dof = nullptr;
   int* bcol_ptr = nullptr; int* bcol = nullptr;
+  int n_bslots = 0;                // entries of bcol (column slots of all Phi blocks)
+  void* yslot = nullptr;           // y at every column slot, apply precision
   int64_t* phi_off = nullptr;
   void* phi = nullptr;
   int* cs_ptr = nullptr; int* cs_idx = nullptr;

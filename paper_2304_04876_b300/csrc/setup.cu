@@ -1029,6 +1029,83 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         GDSW_CK(cudaGetLastError());
       }
     }
+    // Row programs for the level-scheduled solve (k_local_steps): one unknown
+    // per node, FP32, at most three off-diagonal entries per row (IC(0)/ILU(0)
+    // of 7-point stencils).  Every row of every
+    // level becomes one 24-byte instruction in two arrays, A: float4 {a0, a1,
+    // a2, inverse diagonal} and C: uint2 {c0 | c1 << 16, c2 | row << 16} (the
+    // level-sliced ELL's entries in slot order, rows narrower than three padded
+    // with a zero entry on the row itself, as the row-major records are).  A
+    // subdomain's program is its L levels then its U levels, each level cut
+    // into steps of at most kStepRows rows (thread t takes row t of a step); a
+    // step is int2 {first instruction, rows | 1 << 16 when the level ends}.
+    if (P.dpn == 1 && c->fp32 && !c->fp16 && o.trsv == GDSW_TRSV_LEVELSCHED && c->rec_max_width <= 3 &&
+        P.sum_m > 0) {
+      std::vector<int> sp(nsub + 1, 0);
+      std::vector<int2> steps;
+      std::vector<uint32_t> ccode;               // two words per instruction
+      std::vector<uint32_t> vposL(P.L.slots), vposU(P.U.slots), dposL(P.sum_m), dposU(P.sum_m);
+      int64_t ninstr = 0;
+      int max_steps = 0;
+      for (int q = 0; q < nsub; ++q) {
+        for (int side = 0; side < 2; ++side) {
+          const EllPlan& E = side == 0 ? P.L : P.U;
+          uint32_t* vp = side == 0 ? vposL.data() : vposU.data();
+          uint32_t* dp = side == 0 ? dposL.data() : dposU.data();
+          for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
+            const int L_nr = E.lev_nr[l], K = E.lev_K[l];
+            for (int t0 = 0; t0 < L_nr; t0 += kStepRows) {
+              const int nr = std::min(kStepRows, L_nr - t0);
+              steps.push_back(make_int2(static_cast<int>(ninstr), nr | (t0 + nr == L_nr ? 1 << 16 : 0)));
+              for (int t = t0; t < t0 + nr; ++t) {
+                const int row = E.lrows[E.lev_start[l] + t];
+                uint16_t cc[3];
+                for (int k = 0; k < 3; ++k) {
+                  if (k < K) {
+                    const int64_t slot = E.lev_off[l] + int64_t(k) * L_nr + t;
+                    cc[k] = E.col[slot];
+                    vp[slot] = static_cast<uint32_t>(ninstr * 4 + k);
+                  } else {
+                    cc[k] = static_cast<uint16_t>(row);
+                  }
+                }
+                dp[E.lev_start[l] + t] = static_cast<uint32_t>(ninstr * 4 + 3);
+                ccode.push_back(uint32_t(cc[0]) | uint32_t(cc[1]) << 16);
+                ccode.push_back(uint32_t(cc[2]) | uint32_t(row) << 16);
+                ++ninstr;
+              }
+            }
+          }
+        }
+        sp[q + 1] = static_cast<int>(steps.size());
+        max_steps = std::max(max_steps, sp[q + 1] - sp[q]);
+      }
+      if (ninstr * 4 >= (int64_t(1) << 32)) { set_error("row programs too large"); return GDSW_ERR_UNSUPPORTED; }
+      float* d_a;
+      GDSW_TRY(dalloc(c, &d_a, size_t(ninstr) * 4));
+      GDSW_CK(cudaMemsetAsync(d_a, 0, sizeof(float) * size_t(ninstr) * 4, s));
+      uint32_t* d_c;
+      GDSW_TRY(upload(c, &d_c, ccode, s));
+      int2* d_steps;
+      GDSW_TRY(upload(c, &d_steps, steps, s));
+      GDSW_TRY(upload(c, &c->step_ptr, sp, s));
+      c->step_a = d_a;
+      c->step_c = d_c;
+      c->steps = d_steps;
+      c->step_max = max_steps;
+      for (int side = 0; side < 2; ++side) {
+        const EllPlan& E = side == 0 ? P.L : P.U;
+        uint32_t *d_vp, *d_dp;
+        int *d_src, *d_dsrc;
+        GDSW_TRY(sc.put(&d_vp, side == 0 ? vposL : vposU, s));
+        GDSW_TRY(sc.put(&d_dp, side == 0 ? dposL : dposU, s));
+        GDSW_TRY(sc.put(&d_src, E.src, s));
+        GDSW_TRY(sc.put(&d_dsrc, E.dsrc, s));
+        k_fill_records<float><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                    d_a);
+        GDSW_CK(cudaGetLastError());
+      }
+    }
     // Resident blocks for the Jacobi sweeps (Sec. V-B3): per subdomain and
     // triangle one block that a CTA copies into shared memory once and sweeps
     // there: int4 {rows m, width K, values offset, columns offset} | m x T
@@ -1181,6 +1258,16 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   GDSW_TRY(upload(c, &c->brow_dof, C.brow_dof, s));
   GDSW_TRY(upload(c, &c->bcol_ptr, C.bcol_ptr, s));
   GDSW_TRY(upload(c, &c->bcol, C.bcol, s));
+  c->n_bslots = static_cast<int>(C.bcol.size());
+  if (c->fp32) {
+    float* yb;
+    GDSW_TRY(dalloc(c, &yb, std::max<size_t>(1, C.bcol.size())));
+    c->yslot = yb;
+  } else {
+    double* yb;
+    GDSW_TRY(dalloc(c, &yb, std::max<size_t>(1, C.bcol.size())));
+    c->yslot = yb;
+  }
   GDSW_TRY(upload(c, &c->phi_off, C.phi_off, s));
   GDSW_TRY(upload(c, &c->cs_ptr, C.cs_ptr, s));
   GDSW_TRY(upload(c, &c->cs_idx, C.cs_idx, s));
