@@ -54,8 +54,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 static __device__ __noinline__ float f32_from_f64_hw(double d) { return __double2float_rn(d); }
 static __device__ __noinline__ double f64_from_f32_hw(float f) { return static_cast<double>(f); }
 
-__device__ __forceinline__ float f32_from_f64(double d) {
-  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(d));
+// From the binary64 bit pattern (callers that load the bits directly keep the
+// compiler from handling the value as a double at all).
+__device__ __forceinline__ float f32_from_f64_bits(uint64_t u) {
   const uint64_t a = u & 0x7fffffffffffffffull;
   const uint32_t sign = static_cast<uint32_t>(u >> 32) & 0x80000000u;
   // binary64 exponents 897..1150 are the binary32 normal exponents 1..254
@@ -67,7 +68,11 @@ __device__ __forceinline__ float f32_from_f64(double d) {
     return __uint_as_float(f | sign);
   }
   if (a == 0) return __uint_as_float(sign);
-  return f32_from_f64_hw(d);
+  return f32_from_f64_hw(__longlong_as_double(static_cast<long long>(u)));
+}
+
+__device__ __forceinline__ float f32_from_f64(double d) {
+  return f32_from_f64_bits(static_cast<uint64_t>(__double_as_longlong(d)));
 }
 
 __device__ __forceinline__ double f64_from_f32(float f) {
@@ -85,6 +90,14 @@ template <class T>
 __device__ __forceinline__ T narrow(double d) { return static_cast<T>(d); }
 template <>
 __device__ __forceinline__ float narrow<float>(double d) { return f32_from_f64(d); }
+
+// Entry i of an FP64 vector narrowed to T, loaded as its bit pattern for FP32.
+template <class T>
+__device__ __forceinline__ T load_narrow(const double* __restrict__ x, int i) { return static_cast<T>(x[i]); }
+template <>
+__device__ __forceinline__ float load_narrow<float>(const double* __restrict__ x, int i) {
+  return f32_from_f64_bits(reinterpret_cast<const unsigned long long*>(x)[i]);
+}
 
 // Widening of a compute-type value to FP64.
 template <class T>
