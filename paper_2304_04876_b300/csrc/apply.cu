@@ -40,14 +40,14 @@ __device__ __forceinline__ void gather_sub(const double* __restrict__ r, const i
   constexpr int U = 16;
   for (int i0 = tid; i0 < m; i0 += U * nt) {
     int idx[U];
-    T rv[U];
+    uint64_t rv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) idx[u] = i0 + u * nt < m ? om_dofs[base + i0 + u * nt] : -1;
 #pragma unroll
-    for (int u = 0; u < U; ++u) rv[u] = idx[u] >= 0 ? load_narrow<T>(r, idx[u]) : T(0);
+    for (int u = 0; u < U; ++u) rv[u] = idx[u] >= 0 ? load_bits(r, idx[u]) : 0ull;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (i0 + u * nt < m) v[i0 + u * nt] = rv[u];
+      if (i0 + u * nt < m) v[i0 + u * nt] = narrow_bits<T>(rv[u]);
   }
 }
 
@@ -320,17 +320,17 @@ __device__ __forceinline__ void gather_staged(const double* __restrict__ r, cons
   constexpr int U = 16;
   const int tid = threadIdx.x;
   for (int i0 = 0; i0 < m; i0 += U * nt) {
-    T rv[U];
+    uint64_t rv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + tid + u * nt;
-      rv[u] = i < m ? load_narrow<T>(r, idx[i]) : T(0);
+      rv[u] = i < m ? load_bits(r, idx[i]) : 0ull;
     }
     if (sizeof(T) == 8) consumers_sync_or(false, nt);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + tid + u * nt;
-      if (i < m) v[i] = rv[u];
+      if (i < m) v[i] = narrow_bits<T>(rv[u]);
     }
   }
 }
@@ -1061,9 +1061,12 @@ __device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict_
       int g[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) g[j] = ib + 32 * j < i1 ? brow_dof[p0 + ib + 32 * j] : -1;
+      uint64_t rb[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rb[j] = g[j] >= 0 ? load_bits(r, g[j]) : 0ull;
       T rv[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) rv[j] = g[j] >= 0 ? load_narrow<T>(r, g[j]) : T(0);
+      for (int j = 0; j < 4; ++j) rv[j] = narrow_bits<T>(rb[j]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (g[j] < 0) continue;
@@ -1120,9 +1123,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
     int g[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) g[j] = ib + 256 * j < rows ? brow_dof[p0 + i0 + ib + 256 * j] : -1;
+    uint64_t rb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) rb[j] = g[j] >= 0 ? load_bits(r, g[j]) : 0ull;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (g[j] >= 0) rs[ib + 256 * j] = load_narrow<T>(r, g[j]);
+      if (g[j] >= 0) rs[ib + 256 * j] = narrow_bits<T>(rb[j]);
   }
   __syncthreads();
   // one warp per column: the column is contiguous in the block's panel

@@ -91,13 +91,17 @@ __device__ __forceinline__ T narrow(double d) { return static_cast<T>(d); }
 template <>
 __device__ __forceinline__ float narrow<float>(double d) { return f32_from_f64(d); }
 
-// Entry i of an FP64 vector narrowed to T, loaded as its bit pattern for FP32.
-template <class T>
-__device__ __forceinline__ T load_narrow(const double* __restrict__ x, int i) { return static_cast<T>(x[i]); }
-template <>
-__device__ __forceinline__ float load_narrow<float>(const double* __restrict__ x, int i) {
-  return f32_from_f64_bits(reinterpret_cast<const unsigned long long*>(x)[i]);
+// An FP64 vector entry as its bit pattern, and a bit pattern narrowed to T.
+// Gathers load every entry's bits first and convert afterwards: the
+// conversion's rare hardware branch would otherwise keep the compiler from
+// issuing the later loads before the earlier conversions.
+__device__ __forceinline__ uint64_t load_bits(const double* __restrict__ x, int i) {
+  return reinterpret_cast<const unsigned long long*>(x)[i];
 }
+template <class T>
+__device__ __forceinline__ T narrow_bits(uint64_t u) { return __longlong_as_double(static_cast<long long>(u)); }
+template <>
+__device__ __forceinline__ float narrow_bits<float>(uint64_t u) { return f32_from_f64_bits(u); }
 
 // Widening of a compute-type value to FP64.
 template <class T>

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_local_mf(const 
   const uint16_t* bidx = a.bidx + a.sub_brow[q];
   const int* pullB_ptr = a.pullB_ptr + a.sub_brow[q];
   T* arena = arena_all + int64_t(q) * a.arena;
-  for (int p = tid; p < m; p += nt) v[p] = load_narrow<T>(r, a.nd_dof[base + p]);
+  for (int p = tid; p < m; p += nt) v[p] = narrow_bits<T>(load_bits(r, a.nd_dof[base + p]));
   __syncthreads();
   const int l0 = a.sub_lv[q], l1 = a.sub_lv[q + 1];
   // ---- forward sweep, leaves first ----
