@@ -167,7 +167,7 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
   if (st == GDSW_OK) st = c->fp32 ? dalloc(c, reinterpret_cast<float**>(&c->zloc), P.sum_m)
                                   : dalloc(c, reinterpret_cast<double**>(&c->zloc), P.sum_m);
   if (st == GDSW_OK) st = apply_configure(c);
-  if (st == GDSW_OK) st = spmv_configure(c, A->rowptr);
+  if (st == GDSW_OK) st = spmv_configure(c, A->rowptr, A->colind);
   const double t1 = now_s();
   if (st == GDSW_OK) st = krylov_init(c, s);
   if (st == GDSW_OK && P.nprob > 1) {

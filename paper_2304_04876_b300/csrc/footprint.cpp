@@ -161,6 +161,8 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
   // Krylov workspace: six vectors, the reduction buffer, scalars; GMRES basis
   // (reduction buffer: partials of any SpMV grid, at most 32 CTAs per SM)
   R += 6 * arr(n, 8) + arr(2 * (nsub + int64_t(P.ncomp)) + 32 * 148 + 64, 8) + 256;
+  // the SpMV's 16-bit column offsets (when they fit)
+  R += arr(P.nnz, 2);
   // GMRES: basis and preconditioned directions, its state, and the reduction
   // buffer of its fused dot products (2 restart + 4 partial sums per CTA)
   if (o.krylov == GDSW_KRYLOV_GMRES)

@@ -202,9 +202,14 @@ __global__ void __launch_bounds__(R, 2048 / R / 2) k_spmv_pipe(int n, int ntiles
 // neighbouring rows' entries are adjacent, so the warp's loads share L1 lines)
 // and sums them in column order, so the FP64 FMAs do not queue behind
 // shared-memory traffic.
-template <int U>
+// Column of entry e of row `row`: stored absolute (int) or as a 16-bit offset
+// from the row (int16_t: 2 bytes per entry fewer, when every offset fits).
+__device__ __forceinline__ int col_of(const int* __restrict__ ci, int e, int) { return ci[e]; }
+__device__ __forceinline__ int col_of(const int16_t* __restrict__ ci, int e, int row) { return row + ci[e]; }
+
+template <int U, class CI>
 __global__ void __launch_bounds__(256, 4) k_spmv_thread(int n, const int* __restrict__ rowptr,
-                                                     const int* __restrict__ colind,
+                                                     const CI* __restrict__ colind,
                                                      const double* __restrict__ val,
                                                      const double* __restrict__ x, double* __restrict__ y,
                                                      double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(256, 4) k_spmv_thread(int n, const int* __rest
       double a[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        c[u] = e0 + u < e1 ? colind[e0 + u] : -1;
+        c[u] = e0 + u < e1 ? col_of(colind, e0 + u, row) : -1;
         a[u] = e0 + u < e1 ? val[e0 + u] : 0.0;
       }
       double xv[U];
@@ -230,7 +235,7 @@ __global__ void __launch_bounds__(256, 4) k_spmv_thread(int n, const int* __rest
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (c[u] >= 0) acc = fma(a[u], xv[u], acc);
-      for (int e = e0 + U; e < e1; ++e) acc = fma(val[e], x[colind[e]], acc);
+      for (int e = e0 + U; e < e1; ++e) acc = fma(val[e], x[col_of(colind, e, row)], acc);
       y[row] = acc;
       dot = fma(x[row], acc, dot);
     }
@@ -304,20 +309,38 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
     return;
   }
   const double alpha = ks->alpha;
-  double rr = 0.0;
+  double rr = 0.0, rr1 = 0.0;
   const int n2 = n >> 1;
   const int stride = gridDim.x * blockDim.x;
   double2* r2 = reinterpret_cast<double2*>(r);
   const double2* q2 = reinterpret_cast<const double2*>(q);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-    const double2 qi = q2[i];
-    double2 ri = r2[i];
-    ri.x = fma(-alpha, qi.x, ri.x);
-    ri.y = fma(-alpha, qi.y, ri.y);
-    r2[i] = ri;
-    rr = fma(ri.x, ri.x, rr);
-    rr = fma(ri.y, ri.y, rr);
+  // two pairs per trip, their loads in flight together and their squares in
+  // two accumulators (added at the end)
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < n2; i += 2 * stride) {
+    const double2 qa = q2[i], qb = q2[i + stride];
+    double2 ra = r2[i], rb = r2[i + stride];
+    ra.x = fma(-alpha, qa.x, ra.x);
+    ra.y = fma(-alpha, qa.y, ra.y);
+    rb.x = fma(-alpha, qb.x, rb.x);
+    rb.y = fma(-alpha, qb.y, rb.y);
+    r2[i] = ra;
+    r2[i + stride] = rb;
+    rr = fma(ra.x, ra.x, rr);
+    rr1 = fma(rb.x, rb.x, rr1);
+    rr = fma(ra.y, ra.y, rr);
+    rr1 = fma(rb.y, rb.y, rr1);
   }
+  if (i < n2) {
+    const double2 qa = q2[i];
+    double2 ra = r2[i];
+    ra.x = fma(-alpha, qa.x, ra.x);
+    ra.y = fma(-alpha, qa.y, ra.y);
+    r2[i] = ra;
+    rr = fma(ra.x, ra.x, rr);
+    rr = fma(ra.y, ra.y, rr);
+  }
+  rr += rr1;
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int i = n - 1;
     const double ri = fma(-alpha, q[i], r[i]);
@@ -795,8 +818,13 @@ gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, Kryl
   if (c->spmv_pipe == 2) {
     const int grid = std::max(1, std::min(c->spmv_grid, (c->n + 255) / 256));
     switch (c->spmv_U) {
-#define GDSW_SPMV_T(UU) \
-  case UU: k_spmv_thread<UU><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); break;
+#define GDSW_SPMV_T(UU)                                                                                    \
+  case UU:                                                                                                 \
+    if (c->dcol16 != nullptr)                                                                              \
+      k_spmv_thread<UU, int16_t><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->dcol16, c->val, x, y, c->red, ks, gate); \
+    else                                                                                                   \
+      k_spmv_thread<UU, int><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->colind, c->val, x, y, c->red, ks, gate); \
+    break;
       GDSW_SPMV_T(4)
       GDSW_SPMV_T(5)
       GDSW_SPMV_T(6)
@@ -875,8 +903,22 @@ gdsw_status set_done(Ctx* c, cudaStream_t s, int v) {
 // Tile height for the stream SpMV: the largest R in {256, 128, 64, 32} whose
 // worst tile keeps its products within 64 KB of shared memory; the grid is the
 // number of CTAs that fit on the SMs at once.
-gdsw_status spmv_configure(Ctx* c, const int* rowptr) {
+gdsw_status spmv_configure(Ctx* c, const int* rowptr, const int* colind) {
   const int n = c->n;
+  // columns as 16-bit offsets from the row when every one fits (the
+  // thread-per-row kernel then reads 10 bytes per entry instead of 12)
+  {
+    bool fits = n > 0;
+    for (int i = 0; i < n && fits; ++i)
+      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+        if (colind[e] - i < -32768 || colind[e] - i > 32767) { fits = false; break; }
+    if (fits && c->dcol16 == nullptr) {
+      std::vector<int16_t> d(static_cast<size_t>(rowptr[n]));
+      for (int i = 0; i < n; ++i)
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) d[e] = static_cast<int16_t>(colind[e] - i);
+      GDSW_TRY(upload(c, &c->dcol16, d, nullptr));
+    }
+  }
   // long rows (more than 16 entries on average): W lanes per row, W the power
   // of two nearest to a tenth of the mean row length, within 4..32
   const double mean = n > 0 ? double(rowptr[n]) / n : 0.0;
@@ -965,7 +1007,7 @@ gdsw_status spmv_tune(Ctx* c, cudaStream_t s) {
   }
   {
     int per_sm = 1;
-    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_thread<8>, 256, 0));
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv_thread<8, int>, 256, 0));
     g[2] = std::max(1, per_sm) * kNumSMs;
   }
   // the pipelined kernel holds eight entries per thread of a tile
