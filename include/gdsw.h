@@ -186,6 +186,10 @@ typedef struct {
                              blocks resident in shared memory, 6 row
                              programs with per-thread prefetch (FP32, rows of
                              at most 3 entries)                              */
+  int64_t pcg_persistent_grid; /* CTAs of the persistent PCG launch (the whole
+                             iteration loop as one cooperative kernel, for
+                             one problem with dense exact local solves and at
+                             most 128 coarse columns); 0 when not used       */
 } gdsw_stats;
 
 typedef struct gdsw_ctx* gdsw_handle;

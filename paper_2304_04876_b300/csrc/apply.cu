@@ -994,6 +994,31 @@ __global__ void __launch_bounds__(1024, 1) k_local_jac(const double* __restrict_
   }
 }
 
+// One row of a dense inverse times r_s (in shared memory) by a warp: eight
+// independent partial sums per lane, so eight loads of the row are in flight
+// at once, added in a fixed tree order at the end.
+template <class T>
+__device__ __forceinline__ T dense_row_dot(const T* __restrict__ Ai, const T* rs, int m, int lane) {
+  T acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = T(0);
+  int j = lane;
+  for (; j + 7 * 32 < m; j += 8 * 32) {
+    T a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = Ai[j + 32 * u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = fma(a[u], rs[j + 32 * u], acc[u]);
+  }
+  for (int u = 0; j < m; j += 32, ++u) acc[u & 7] = fma(Ai[j], rs[j], acc[u & 7]);
+  const T t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  return warp_sum(t);
+}
+
+// Rows of one subdomain per CTA of the dense local solve: one per warp, so a
+// row's loads are the only chain a warp waits on (more CTAs each gather r_s).
+constexpr int kDenseRows = 8;
+
 // Exact local solver: z_s = A_s^-1 r_s with the stored dense inverse
 // (symmetric, so row i is read contiguously).  Grid (row chunks of 32, nsub).
 template <class T>
@@ -1010,19 +1035,16 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
   const int s = blockIdx.y;
   if (gate_sub_off(gate, s)) return;
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
-  const int row0 = blockIdx.x * 32;
+  const int row0 = blockIdx.x * kDenseRows;
   if (row0 >= m) return;
   gather_sub(r, om_dofs, base, m, rs, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const T* A = ainv + ainv_off[s];
-  for (int rr = w; rr < 32; rr += 8) {
+  for (int rr = w; rr < kDenseRows; rr += 8) {
     const int i = row0 + rr;
     if (i >= m) break;
-    const T* Ai = A + int64_t(i) * m;
-    T acc = T(0);
-    for (int j = lane; j < m; j += 32) acc += Ai[j] * rs[j];
-    acc = warp_sum(acc);
+    const T acc = dense_row_dot(A + int64_t(i) * m, rs, m, lane);
     if (lane == 0) zloc[base + i] = acc;
   }
 }
@@ -1346,6 +1368,228 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_combine(
   }
 }
 
+// ---- PCG as one persistent kernel ----
+//
+// For small problems the PCG iteration is bound by its launches (config 1: ten
+// kernels of a few microseconds each), so single-problem handles with dense
+// exact local solves and a small coarse space (n0 <= kPersistMaxN0) can run the
+// whole loop in one cooperative launch.  Each iteration is the graph body's
+// sequence, phase by phase over the whole grid, with a grid barrier (bounded
+// spin on a monotonic counter) between phases: q = A p and (p, q); r -= alpha q,
+// ||r||^2, x += alpha p, the stopping test; the dense local solves and Phi^T r;
+// the coarse solve (every CTA, redundantly, in shared memory) and the
+// scatter-add with the PCG dots; p = z + beta p.  Every CTA sums the per-CTA
+// partials of a reduction itself in the same fixed order, so all agree on
+// alpha, beta and the stopping decision without another barrier.  A barrier
+// wait that runs out sets the error flag and the CTA returns (the others' waits
+// run out in turn).
+constexpr int kPersistMaxN0 = 128;
+constexpr int kPersistPerSM = 1;   // CTAs per SM: fewer arrivals on the barrier counter
+
+struct PersistArgs {
+  int n, nsub, n0, n_chunks, n_units, dots;
+  const int* rowptr; const int* colind; const int16_t* dcol16; const double* val;
+  double *x, *r, *p, *q, *z;
+  const int* om_ptr; const int* om_dofs; const void* ainv; const int64_t* ainv_off; const int* unit_ptr; void* zloc;
+  const int* brow_ptr; const int* brow_dof; const int* bcol_ptr; const int* bcol; const int64_t* phi_off;
+  const void* phi; const int* chunk_blk; const int* chunk_r0; const int* chunk_r1; const int* chunk_slot;
+  double* partial; const int* cs_ptr; const int* cs_idx; const void* a0inv;
+  const int* pos_blk; const int* pull_ptr; const int* pull_pos;
+  double* red; unsigned* bar; KrylovScalars* ks; int* err; long long wait_cycles; int max_m;
+  int stall_test;   // CTA 0 withholds its first barrier arrival (the failure test)
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, long long cycles, int* s_flag,
+                                             bool withhold = false) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (!withhold) atomicAdd(bar, 1u);
+    const volatile unsigned* vb = bar;
+    int ok = 1;
+    if (*vb < target) {
+      const long long t0 = clock64();
+      while (*vb < target) {
+        __nanosleep(64);          // fewer polls of the shared line
+        if (clock64() - t0 > cycles) { ok = 0; break; }
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// The grid-wide sum of `count` per-CTA partials, in index order, in every thread.
+__device__ __forceinline__ double grid_total(const double* part, int count, double* sh, double* s_out) {
+  const double v = sum_partials(part, count, sh);
+  if (threadIdx.x == 0) *s_out = v;
+  __syncthreads();
+  const double t = *s_out;
+  __syncthreads();
+  return t;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_pcg_persistent(PersistArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[32];
+  __shared__ double s_out;
+  __shared__ int s_flag;
+  T* rs = reinterpret_cast<T*>(smem_raw);                                     // r_s of one subdomain
+  T* cs = reinterpret_cast<T*>(smem_raw + ((size_t(a.max_m) * sizeof(T) + 15) & ~size_t(15)));
+  T* ys = cs + kPersistMaxN0;                                                 // coarse rhs and solution
+  KrylovScalars* ks = a.ks;
+  const int G = gridDim.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = G * blockDim.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gwarp = blockIdx.x * (blockDim.x >> 5) + w, nwarps = G * (blockDim.x >> 5);
+  double rz = ks->rz;
+  int iter = ks->iter;
+  const int maxit = ks->maxit;
+  const double tol2 = ks->tol2;
+  unsigned epoch = 0;
+  double* red0 = a.red;            // (p, q)
+  double* red1 = a.red + G;        // ||r||^2
+  double* red2 = a.red + 2 * G;    // the scatter-add's two dots
+  const T* ainv = static_cast<const T*>(a.ainv);
+  const T* phi = static_cast<const T*>(a.phi);
+  const T* a0 = static_cast<const T*>(a.a0inv);
+  T* zloc = static_cast<T*>(a.zloc);
+  for (;;) {
+    // q = A p, (p, q)
+    double dot = 0.0;
+    for (int row = gtid; row < a.n; row += stride) {
+      const int e0 = a.rowptr[row], e1 = a.rowptr[row + 1];
+      double acc = 0.0;
+      for (int e = e0; e < e1; ++e) {
+        const int col = a.dcol16 != nullptr ? row + a.dcol16[e] : a.colind[e];
+        acc = fma(a.val[e], a.p[col], acc);
+      }
+      a.q[row] = acc;
+      dot = fma(a.p[row], acc, dot);
+    }
+    {
+      const double t = block_sum(dot, sh);
+      if (threadIdx.x == 0) red0[blockIdx.x] = t;
+    }
+    if (!grid_barrier(a.bar, (++epoch) * G, a.wait_cycles, &s_flag, a.stall_test && blockIdx.x == 0 && epoch == 1))
+      break;
+    const double pq = grid_total(red0, G, sh, &s_out);
+    const double alpha = rz / pq;
+    // r -= alpha q, ||r||^2, x += alpha p
+    double rr = 0.0;
+    for (int i = gtid; i < a.n; i += stride) {
+      const double ri = fma(-alpha, a.q[i], a.r[i]);
+      a.r[i] = ri;
+      rr = fma(ri, ri, rr);
+      a.x[i] = fma(alpha, a.p[i], a.x[i]);
+    }
+    {
+      const double t = block_sum(rr, sh);
+      if (threadIdx.x == 0) red1[blockIdx.x] = t;
+    }
+    if (!grid_barrier(a.bar, (++epoch) * G, a.wait_cycles, &s_flag)) break;
+    rr = grid_total(red1, G, sh, &s_out);
+    ++iter;
+    int done = 0, bad = 0;
+    if (!isfinite(rr) || !isfinite(alpha) || !(pq > 0.0)) { bad = 1; done = 1; }
+    else if (rr <= tol2) done = 1;
+    else if (iter >= maxit) done = 1;
+    if (done) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ks->rr = rr; ks->pq = pq; ks->alpha = alpha; ks->iter = iter; ks->bad = bad; ks->done = 1; ks->rz = rz;
+      }
+      return;
+    }
+    // dense local solves, kDenseRows rows of one subdomain per unit
+    for (int u = blockIdx.x; u < a.n_units; u += G) {
+      int lo = 0, hi = a.nsub;                  // the subdomain of unit u
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.unit_ptr[mid] <= u) lo = mid; else hi = mid;
+      }
+      const int s = lo;
+      const int base = a.om_ptr[s], m = a.om_ptr[s + 1] - base;
+      const int row0 = (u - a.unit_ptr[s]) * kDenseRows;
+      gather_sub(a.r, a.om_dofs, base, m, rs, threadIdx.x, blockDim.x);
+      __syncthreads();
+      const T* A = ainv + a.ainv_off[s];
+      for (int rw = w; rw < kDenseRows; rw += 8) {
+        const int i = row0 + rw;
+        if (i >= m) break;
+        const T acc = dense_row_dot(A + int64_t(i) * m, rs, m, lane);
+        if (lane == 0) zloc[base + i] = acc;
+      }
+      __syncthreads();
+    }
+    // Phi^T r by chunks, a warp each
+    for (int qq = gwarp; qq < a.n_chunks; qq += nwarps)
+      phiT_warp_chunk<T>(qq, a.r, a.brow_ptr, a.brow_dof, a.bcol_ptr, a.phi_off, phi, a.chunk_blk, a.chunk_r0,
+                         a.chunk_r1, a.chunk_slot, a.partial);
+    if (!grid_barrier(a.bar, (++epoch) * G, a.wait_cycles, &s_flag)) break;
+    // coarse solve, redundantly in every CTA: c = Phi^T r by columns, y = A0^-1 c
+    for (int l = threadIdx.x; l < a.n0; l += blockDim.x) {
+      double v = 0.0;
+      for (int qq = a.cs_ptr[l]; qq < a.cs_ptr[l + 1]; ++qq) v += __ldcg(a.partial + a.cs_idx[qq]);
+      cs[l] = static_cast<T>(v);
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < a.n0; l += blockDim.x) {
+      T v = T(0);
+      for (int j = 0; j < a.n0; ++j) v = fma(a0[int64_t(l) * a.n0 + j], cs[j], v);
+      ys[l] = v;
+    }
+    __syncthreads();
+    // z = sum_s R_s^T z_s + Phi y, (r, z) and (r, z_old)
+    double d_new = 0.0, d_old = 0.0;
+    for (int pp = gtid; pp < a.n; pp += stride) {
+      const int g = a.brow_dof[pp], b = a.pos_blk[pp];
+      T acc = T(0);
+      for (int q2 = a.pull_ptr[pp]; q2 < a.pull_ptr[pp + 1]; ++q2) acc += zloc[a.pull_pos[q2]];
+      const int c0 = a.bcol_ptr[b], k = a.bcol_ptr[b + 1] - c0;
+      if (k > 0) {
+        const int p0 = a.brow_ptr[b], nr = a.brow_ptr[b + 1] - p0;
+        const T* Ph = phi + a.phi_off[b] + (pp - p0);
+        for (int u = 0; u < k; ++u) acc = fma(Ph[int64_t(u) * nr], ys[a.bcol[c0 + u]], acc);
+      }
+      const double zg = widen<T>(acc);
+      const double rg = a.r[g];
+      if (a.dots > 1) d_old = fma(rg, a.z[g], d_old);
+      d_new = fma(rg, zg, d_new);
+      a.z[g] = zg;
+    }
+    {
+      const double tn = block_sum(d_new, sh);
+      const double to = block_sum(d_old, sh);
+      if (threadIdx.x == 0) { red2[2 * blockIdx.x] = tn; red2[2 * blockIdx.x + 1] = to; }
+    }
+    if (!grid_barrier(a.bar, (++epoch) * G, a.wait_cycles, &s_flag)) break;
+    double sn = 0.0, so = 0.0;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) {
+      sn += __ldcg(red2 + 2 * i);
+      so += __ldcg(red2 + 2 * i + 1);
+    }
+    sn = block_sum(sn, sh);
+    so = block_sum(so, sh);
+    if (threadIdx.x == 0) { s_out = sn; sh[0] = so; }
+    __syncthreads();
+    sn = s_out;
+    so = sh[0];
+    __syncthreads();
+    const double beta = (a.dots > 1 ? (sn - so) : sn) / rz;
+    rz = sn;
+    // p = z + beta p
+    for (int i = gtid; i < a.n; i += stride) a.p[i] = fma(beta, a.p[i], a.z[i]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ks->iter = iter; ks->rr = rr; ks->rz = rz; ks->rz_new = sn; ks->rz_oldz = so; ks->beta = beta;
+    }
+    if (!grid_barrier(a.bar, (++epoch) * G, a.wait_cycles, &s_flag)) break;
+  }
+  if (threadIdx.x == 0) atomicOr(a.err, 1);
+}
+
 template <class T>
 EllDev<T> ell(const Ctx* c, bool lower) {
   EllDev<T> e;
@@ -1366,7 +1610,7 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
   if (c->mf) return mf_launch_local(c, r, s, ks);
   if (c->opt.local_solver == GDSW_LOCAL_EXACT) {
     const size_t shm = size_t(c->max_m) * sizeof(T);
-    dim3 grid((c->max_m + 31) / 32, c->nsub);
+    dim3 grid((c->max_m + kDenseRows - 1) / kDenseRows, c->nsub);
     k_local_dense<T><<<grid, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
                                             c->ainv_off, zl, ks, gate);
   } else if (c->step_depth > 0) {
@@ -1995,6 +2239,76 @@ gdsw_status apply_timed(Ctx* c, const double* r, double* z, cudaStream_t s, doub
     GDSW_CK(cudaEventElapsedTime(&t, c->ev[q], c->ev[q + 1]));
     ms[q] = t;
   }
+  return GDSW_OK;
+}
+
+// The persistent PCG kernel for this handle, or none: PCG on one problem with
+// dense exact local solves and at most kPersistMaxN0 coarse columns, when
+// GDSW_PERSISTENT=1 asks for it (measured slower than the graph-launched loop
+// on the Poisson 16^3 workload, 1.44 against 1.11 ms per solve: every phase
+// runs on one CTA per SM and waits at a grid barrier, where the graph's kernels
+// each fill the GPU).  Sets the unit table, the barrier counter and the
+// cooperative grid (every CTA resident at once, kPersistPerSM per SM).
+gdsw_status persistent_configure(Ctx* c) {
+  c->persist_grid = 0;
+  const char* e = getenv("GDSW_PERSISTENT");
+  if (e == nullptr || e[0] != '1') return GDSW_OK;
+  if (c->opt.krylov != GDSW_KRYLOV_PCG || c->nprob != 1 || c->mf || c->ainv == nullptr ||
+      c->opt.local_solver != GDSW_LOCAL_EXACT || c->n0 < 1 || c->n0 > kPersistMaxN0 || c->n <= 0)
+    return GDSW_OK;
+  std::vector<int> om(size_t(c->nsub) + 1);
+  GDSW_CK(cudaMemcpy(om.data(), c->om_ptr, sizeof(int) * om.size(), cudaMemcpyDeviceToHost));
+  std::vector<int> up(size_t(c->nsub) + 1, 0);
+  for (int q = 0; q < c->nsub; ++q) up[q + 1] = up[q] + (om[q + 1] - om[q] + kDenseRows - 1) / kDenseRows;
+  GDSW_TRY(upload(c, &c->unit_ptr, up, nullptr));
+  c->n_units = up[c->nsub];
+  if (c->pbar == nullptr) GDSW_TRY(dalloc(c, &c->pbar, 1));
+  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  c->persist_smem = ((size_t(c->max_m) * es + 15) & ~size_t(15)) + 2 * kPersistMaxN0 * es;
+  int dev = 0, sms = kNumSMs, per_sm = 0;
+  GDSW_CK(cudaGetDevice(&dev));
+  GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (c->fp32) {
+    GDSW_CK(allow_max_dynamic_smem(k_pcg_persistent<float>));
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<float>, 256, c->persist_smem));
+  } else {
+    GDSW_CK(allow_max_dynamic_smem(k_pcg_persistent<double>));
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<double>, 256, c->persist_smem));
+  }
+  if (per_sm <= 0) return GDSW_OK;
+  // the reduction buffer holds four partials per CTA
+  c->persist_grid = std::min(std::min(per_sm, kPersistPerSM) * sms, (c->red_len - 64) / 4);
+  return GDSW_OK;
+}
+
+// PCG iterations from the current state until the stopping test holds, as one
+// cooperative launch (see k_pcg_persistent); the state stays in the handle's
+// Krylov workspace and scalars exactly as after the graph loop.
+gdsw_status pcg_persistent_run(Ctx* c, cudaStream_t s) {
+  GDSW_CK(cudaMemsetAsync(c->pbar, 0, sizeof(unsigned), s));
+  PersistArgs a = {};
+  a.n = c->n; a.nsub = c->nsub; a.n0 = c->n0; a.n_chunks = c->n0 > 0 ? c->n_chunks : 0; a.n_units = c->n_units;
+  a.dots = c->flexible ? 2 : 1;
+  a.rowptr = c->rowptr; a.colind = c->colind; a.dcol16 = c->dcol16; a.val = c->val;
+  a.x = c->x; a.r = c->r; a.p = c->p; a.q = c->q; a.z = c->z;
+  a.om_ptr = c->om_ptr; a.om_dofs = c->om_dofs; a.ainv = c->ainv; a.ainv_off = c->ainv_off;
+  a.unit_ptr = c->unit_ptr; a.zloc = c->zloc;
+  a.brow_ptr = c->brow_ptr; a.brow_dof = c->brow_dof; a.bcol_ptr = c->bcol_ptr; a.bcol = c->bcol;
+  a.phi_off = c->phi_off; a.phi = c->phi; a.chunk_blk = c->chunk_blk; a.chunk_r0 = c->chunk_r0;
+  a.chunk_r1 = c->chunk_r1; a.chunk_slot = c->chunk_slot; a.partial = c->partial;
+  a.cs_ptr = c->cs_ptr; a.cs_idx = c->cs_idx;
+  a.a0inv = c->fp32 ? static_cast<const void*>(c->A0inv32) : static_cast<const void*>(c->A0inv);
+  a.pos_blk = c->pos_blk; a.pull_ptr = c->pull_ptr; a.pull_pos = c->pull_pos;
+  a.red = c->red; a.bar = c->pbar; a.ks = c->ks; a.err = c->derr; a.wait_cycles = c->wait_cycles;
+  a.max_m = c->max_m;
+  a.stall_test = c->stall_test ? 1 : 0;
+  void* args[] = {&a};
+  if (c->fp32)
+    GDSW_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_pcg_persistent<float>), dim3(c->persist_grid),
+                                        dim3(256), args, c->persist_smem, s));
+  else
+    GDSW_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_pcg_persistent<double>), dim3(c->persist_grid),
+                                        dim3(256), args, c->persist_smem, s));
   return GDSW_OK;
 }
 

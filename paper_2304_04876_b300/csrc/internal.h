@@ -507,6 +507,13 @@ struct Ctx {
   int spmv_R = 256, spmv_maxne = 1, spmv_tiles = 1, spmv_grid = kNumSMsForCtx;
   int spmv_U = 8;                      // entries in flight per row in the thread-per-row SpMV
   int16_t* dcol16 = nullptr;           // columns as offsets from the row (when all fit in 16 bits)
+  // persistent PCG (k_pcg_persistent): cooperative grid (0: not used), units of
+  // 32 local rows per subdomain, grid barrier counter
+  int persist_grid = 0;
+  size_t persist_smem = 0;
+  int* unit_ptr = nullptr;
+  int n_units = 0;
+  unsigned* pbar = nullptr;
   int spmv_W = 0;                    // lanes per row for long rows (0: the tiled kernel)
   int spmv_pipe = 0;                 // SpMV kernel for short rows (chosen by timing): 0 tiled, 1 tiled with
                                      // the next tile's loads in flight, 2 a thread per row
@@ -572,6 +579,8 @@ gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s);
 // y = A x on the rows of problems that have not stopped (batched iteration).
 gdsw_status spmv_enqueue_batch(Ctx* c, const double* x, double* y, cudaStream_t s);
 gdsw_status spmv_configure(Ctx* c, const int* rowptr_host, const int* colind_host);
+gdsw_status persistent_configure(Ctx* c);
+gdsw_status pcg_persistent_run(Ctx* c, cudaStream_t s);
 gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
 // One PCG iteration from x = 0 (after its prologue), kernel by kernel on one
 // stream with CUDA events: ms[0] SpMV, [1] vector update, [2] local solve,

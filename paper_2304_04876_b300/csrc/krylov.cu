@@ -1127,6 +1127,7 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
     GDSW_CK(e);
     GDSW_CK(cudaGraphInstantiate(&c->gm_exec, c->gm_graph, 0));
   }
+  GDSW_TRY(persistent_configure(c));
   return GDSW_OK;
 }
 
@@ -1165,7 +1166,11 @@ gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info,
     GDSW_TRY(apply_enqueue(c, c->r, c->z, s, true));
     GDSW_CK(cudaMemcpyAsync(c->p, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     for (;;) {
-      if (c->pcg_exec != nullptr) {
+      if (c->persist_grid > 0) {
+        GDSW_TRY(pcg_persistent_run(c, s));
+        // a grid barrier that ran out ends the solve (GDSW_ERR_TIMEOUT)
+        GDSW_TRY(check_device_errors(c, s));
+      } else if (c->pcg_exec != nullptr) {
         GDSW_CK(cudaGraphLaunch(c->pcg_exec, s));
       } else {
         // the same iteration body launched from the host (no CUDA graph), with

@@ -71,7 +71,8 @@ class Stats(C.Structure):
         "n", "nnz", "n_sub", "n0", "n_comp", "sum_omega", "max_omega", "nnz_L", "nnz_U", "ell_L",
         "ell_U", "nnz_phi", "n_levels_L", "n_levels_U", "max_levels", "dense_local", "n_blocks",
         "device_bytes", "n_problems", "a0_entries", "local_stages", "local_threads", "mf_supernodes", "mf_levels")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8),
-                                                          ("local_kernel", C.c_int64)]
+                                                          ("local_kernel", C.c_int64),
+                                                          ("pcg_persistent_grid", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "setup_phase_seconds"}
