@@ -24,6 +24,21 @@ namespace {
 constexpr int kTileRows = 4096;
 constexpr int kThreads = 256;
 
+// Per-member workspace: H ((m+1) x m, row-major), cs, sn (m), g (m+1),
+// h1, h2 (m+2: k coefficients and (w, w)), beta (2).
+struct BgLayout {
+  int m;
+  __host__ __device__ explicit BgLayout(int m_) : m(m_) {}
+  __host__ __device__ int cs() const { return (m + 1) * m; }
+  __host__ __device__ int sn() const { return cs() + m; }
+  __host__ __device__ int g() const { return sn() + m; }
+  __host__ __device__ int h1() const { return g() + m + 1; }
+  __host__ __device__ int h2() const { return h1() + m + 2; }
+  __host__ __device__ int beta() const { return h2() + m + 2; }
+  __host__ __device__ int total() const { return beta() + 2; }
+};
+
+
 // per-tile partial of (a, b) into part[2 t + slot] (tiles of stopped problems skip)
 __global__ void __launch_bounds__(kThreads) k_bdot(const int* __restrict__ tile_prob,
                                                    const int* __restrict__ tile_r0,
@@ -266,9 +281,21 @@ gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, const std::
   c->prob_dof_host = prob_dof_ptr;
   GDSW_TRY(dalloc(c, &c->bks, np));
   GDSW_TRY(dalloc(c, &c->bctl, 1));
-  if (c->red_len < 4 * c->n_tiles + 64) {        // the initial residual uses two partial arrays
-    GDSW_TRY(dalloc(c, &c->red, 4 * c->n_tiles + 64));
-    c->red_len = 4 * c->n_tiles + 64;
+  // partials: the initial residual uses two arrays; batched GMRES one per dot
+  // of an Arnoldi step (restart + 2 per tile)
+  const int64_t need = c->opt.krylov == GDSW_KRYLOV_GMRES
+                           ? std::max<int64_t>(4 * int64_t(c->n_tiles), int64_t(c->n_tiles) * (c->opt.restart + 2))
+                           : 4 * int64_t(c->n_tiles);
+  if (c->red_len < need + 64) {
+    GDSW_TRY(dalloc(c, &c->red, size_t(need) + 64));
+    c->red_len = static_cast<int>(need) + 64;
+  }
+  if (c->opt.krylov == GDSW_KRYLOV_GMRES) {
+    const int m = std::max(1, c->opt.restart);
+    GDSW_TRY(dalloc(c, &c->bgm, size_t(np) * BgLayout(m).total()));
+    GDSW_TRY(dalloc(c, &c->bgm_y, size_t(np) * m));
+    GDSW_TRY(dalloc(c, &c->bgm_jd, size_t(np)));
+    return GDSW_OK;                                 // the PCG graph is not needed
   }
   const char* env = getenv("GDSW_PCG_GRAPH");
   if (env != nullptr && env[0] == '0') return GDSW_OK;
@@ -523,6 +550,319 @@ gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info*
   }
   if (!all_ok) { set_error("batched PCG: some problems did not converge"); return GDSW_ERR_NOT_CONVERGED; }
   return GDSW_OK;
+}
+
+// ---- batched GMRES(m) --------------------------------------------------------
+//
+// Restarted right-preconditioned GMRES on every member of a batched handle at
+// once (Sec. II's GMRES with the GDSW preconditioner of Eq. 1): the apply and
+// the SpMV of an Arnoldi step are one launch for all members (stopped members
+// skipped), and the Gram-Schmidt passes run on the member-owned tiles of the
+// vectors -- each tile writes its partial (V_i, w), a warp per (member, i) adds
+// its tiles in order, one thread per member forms the norm, applies the
+// Givens rotations and tests convergence on its own least-squares residual.
+// Two Gram-Schmidt passes per step (CGS2), or the single-reduce form with a
+// second pass only where the Pythagorean norm cancels.  The host back-solves
+// each member's small triangular system after a cycle and adds Z y per member.
+
+namespace {
+
+// V0 = r / beta_p on the tiles of live members
+__global__ void __launch_bounds__(kThreads) k_bgm_scale(const int* __restrict__ tile_prob,
+                                                        const int* __restrict__ tile_r0,
+                                                        const int* __restrict__ tile_r1,
+                                                        const double* __restrict__ r,
+                                                        const double* __restrict__ inv_beta,
+                                                        const BatchScalars* __restrict__ bs, double* __restrict__ v) {
+  const int t = blockIdx.x, p = tile_prob[t];
+  if (bs[p].done) return;
+  const double sc = inv_beta[p];
+  for (int i = tile_r0[t] + threadIdx.x; i < tile_r1[t]; i += blockDim.x) v[i] = r[i] * sc;
+}
+
+// partials of (V_i, w), i < k, and (w, w) of one tile into part[t * stride + i]
+// (pass 2 only for members whose first pass asked for it)
+__global__ void __launch_bounds__(kThreads) k_bgm_dots(int n, int k, const int* __restrict__ tile_prob,
+                                                       const int* __restrict__ tile_r0,
+                                                       const int* __restrict__ tile_r1,
+                                                       const double* __restrict__ V, const double* __restrict__ w,
+                                                       const BatchScalars* __restrict__ bs, double* __restrict__ part,
+                                                       int stride, int pass) {
+  __shared__ double sh[32];
+  const int t = blockIdx.x, p = tile_prob[t];
+  if (bs[p].done || (pass == 2 && bs[p].mode != 2)) return;
+  for (int c0 = 0; c0 <= k; c0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+    for (int i = tile_r0[t] + threadIdx.x; i < tile_r1[t]; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int col = c0 + u;
+        if (col < k) acc[u] = fma(V[int64_t(col) * n + i], wi, acc[u]);
+        else if (col == k) acc[u] = fma(wi, wi, acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (c0 + u <= k) {
+        const double v = block_sum(acc[u], sh);
+        if (threadIdx.x == 0) part[int64_t(t) * stride + c0 + u] = v;
+      }
+    }
+  }
+}
+
+// h[p][i] = the sum of member p's tile partials of dot i (a warp per (p, i), tiles in order)
+__global__ void k_bgm_reduce(int np, int k, const int* __restrict__ prob_tile_ptr,
+                             const double* __restrict__ part, int stride, const BatchScalars* __restrict__ bs,
+                             double* __restrict__ gm, int m, int pass) {
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (wid >= np * (k + 1)) return;
+  const int p = wid / (k + 1), i = wid % (k + 1);
+  if (bs[p].done || (pass == 2 && bs[p].mode != 2)) return;
+  double v = 0.0;
+  for (int t = prob_tile_ptr[p] + lane; t < prob_tile_ptr[p + 1]; t += 32) v += part[int64_t(t) * stride + i];
+  v = warp_sum(v);
+  const BgLayout L(m);
+  if (lane == 0) gm[int64_t(p) * L.total() + (pass == 1 ? L.h1() : L.h2()) + i] = v;
+}
+
+// A thread per member.  Pass 1: ||w - V h||^2 = (w, w) - ||h||^2; below `keep`
+// of (w, w) (or always, keep > 1) a second pass follows (mode 2).  Pass 2: the
+// norm after it.
+__global__ void k_bgm_norm(int np, int k, double* __restrict__ gm, int m, BatchScalars* bs, int pass,
+                           double keep) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  BatchScalars& S = bs[p];
+  if (S.done || (pass == 2 && S.mode != 2)) return;
+  const BgLayout L(m);
+  double* g = gm + int64_t(p) * L.total();
+  const double* h = g + (pass == 1 ? L.h1() : L.h2());
+  double sq = 0.0;
+  for (int i = 0; i < k; ++i) sq = fma(h[i], h[i], sq);
+  const double b2 = h[k] - sq;
+  if (pass == 1) {
+    if (b2 > keep * h[k]) { S.mode = 1; g[L.beta()] = sqrt(b2); }
+    else { S.mode = 2; g[L.beta()] = 0.0; }
+  } else {
+    g[L.beta() + 1] = b2 > 0.0 ? sqrt(b2) : 0.0;
+  }
+}
+
+// w -= V h_p on the tiles of live members; the pass that completes the
+// orthogonalisation divides by beta (zero beta: left unscaled)
+__global__ void __launch_bounds__(kThreads) k_bgm_orth(int n, int k, const int* __restrict__ tile_prob,
+                                                       const int* __restrict__ tile_r0,
+                                                       const int* __restrict__ tile_r1,
+                                                       const double* __restrict__ V, const double* __restrict__ gm,
+                                                       int m, const BatchScalars* __restrict__ bs,
+                                                       double* __restrict__ w, int pass) {
+  const int t = blockIdx.x, p = tile_prob[t];
+  const BatchScalars& S = bs[p];
+  if (S.done || (pass == 2 && S.mode != 2)) return;
+  const bool last = pass == 2 || S.mode == 1;
+  const BgLayout L(m);
+  const double* g = gm + int64_t(p) * L.total();
+  const double* h = g + (pass == 1 ? L.h1() : L.h2());
+  const double b = last ? g[L.beta() + pass - 1] : 1.0;
+  const double inv = b > 0.0 ? 1.0 / b : 1.0;
+  for (int i = tile_r0[t] + threadIdx.x; i < tile_r1[t]; i += blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < k; ++j) acc = fma(-h[j], V[int64_t(j) * n + i], acc);
+    w[i] = last ? acc * inv : acc;
+  }
+}
+
+// A thread per member: Hessenberg column j, the earlier rotations, the new one,
+// and the stopping test on |g_{j+1}| (tolerance, iteration limit, breakdown).
+__global__ void k_bgm_givens(int np, int j, int m, double* __restrict__ gm, BatchScalars* bs, int maxit) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  BatchScalars& S = bs[p];
+  if (S.done) return;
+  const BgLayout L(m);
+  double* H = gm + int64_t(p) * L.total();
+  double* cs = H + L.cs();
+  double* sn = H + L.sn();
+  double* g = H + L.g();
+  const double* h1 = H + L.h1();
+  const double* h2 = H + L.h2();
+  const bool two = S.mode == 2;
+  for (int i = 0; i <= j; ++i) H[i * m + j] = two ? h1[i] + h2[i] : h1[i];
+  const double hn = H[L.beta() + (two ? 1 : 0)];
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * m + j], b = H[(i + 1) * m + j];
+    H[i * m + j] = cs[i] * a + sn[i] * b;
+    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+  }
+  const double d = H[j * m + j];
+  const double den = hypot(d, hn);
+  if (den == 0.0) { S.bad = 1; S.done = 1; return; }
+  cs[j] = d / den;
+  sn[j] = hn / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  S.iter += 1;
+  if (!isfinite(g[j + 1])) S.bad = 1;
+  if (!(g[j + 1] * g[j + 1] > S.tol2) || S.iter >= maxit || hn == 0.0 || S.bad) S.done = 1;
+}
+
+// x += Z y_p (jd[p] columns) on every tile of a member with steps this cycle
+__global__ void __launch_bounds__(kThreads) k_bgm_update_x(int n, const int* __restrict__ tile_prob,
+                                                           const int* __restrict__ tile_r0,
+                                                           const int* __restrict__ tile_r1,
+                                                           const double* __restrict__ Zk,
+                                                           const double* __restrict__ yv,
+                                                           const int* __restrict__ jd, int m,
+                                                           double* __restrict__ x) {
+  const int t = blockIdx.x, p = tile_prob[t];
+  const int k = jd[p];
+  if (k <= 0) return;
+  const double* y = yv + int64_t(p) * m;
+  for (int i = tile_r0[t] + threadIdx.x; i < tile_r1[t]; i += blockDim.x) {
+    double acc = x[i];
+    for (int j = 0; j < k; ++j) acc = fma(y[j], Zk[int64_t(j) * n + i], acc);
+    x[i] = acc;
+  }
+}
+
+}  // namespace
+
+gdsw_status solve_gmres_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s) {
+  const double t0 = now_s();
+  const int n = c->n, np = c->nprob, nt = c->n_tiles;
+  const int m = std::max(1, c->opt.restart);
+  const BgLayout L(m);
+  const int stride = m + 2;
+  const double keep = c->opt.gmres_orth == GDSW_GMRES_ORTH_SINGLE ? 1e-4 : 2.0;
+  GDSW_CK(cudaMemcpyAsync(c->b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaMemcpyAsync(c->x, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  c->serving = false;
+  const int vg = std::min(kNumSMs * 8, (n + kThreads - 1) / kThreads);
+  std::vector<int> tile_ptr(np + 1, 0);
+  {
+    int t = 0;
+    for (int q = 0; q < np; ++q) {
+      for (int r0 = c->prob_dof_host[q]; r0 < c->prob_dof_host[q + 1]; r0 += kTileRows) ++t;
+      tile_ptr[q + 1] = t;
+    }
+  }
+  std::vector<BatchScalars> hs(np);
+  std::vector<double> bb(np, 0.0), rr(np, 0.0), part(4 * size_t(nt));
+  std::vector<int> it(np, 0), stalled(np, 0), bad(np, 0), conv(np, 0);
+  std::vector<double> gmh(size_t(np) * L.total()), invb(np), yv(size_t(np) * m);
+  std::vector<int> jd(np);
+  for (int cycle = 0;; ++cycle) {
+    // true residual of every member, and ||b||^2 on the first cycle
+    for (auto& v : hs) v = BatchScalars{};
+    GDSW_CK(cudaMemcpyAsync(c->bks, hs.data(), sizeof(BatchScalars) * np, cudaMemcpyHostToDevice, s));
+    GDSW_TRY(spmv_enqueue(c, c->x, c->q, s));
+    k_bresidual<<<vg, kThreads, 0, s>>>(n, c->b, c->q, c->r);
+    if (cycle == 0)
+      k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->b, c->b, c->bks, c->red, 0);
+    k_bdot<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->r, c->bks, c->red + 2 * nt, 0);
+    GDSW_CK(cudaGetLastError());
+    GDSW_CK(cudaMemcpyAsync(part.data(), c->red, sizeof(double) * 4 * nt, cudaMemcpyDeviceToHost, s));
+    GDSW_CK(cudaStreamSynchronize(s));
+    int nlive = 0;
+    for (int q = 0; q < np; ++q) {
+      double r2 = 0.0, b2 = 0.0;
+      for (int t = tile_ptr[q]; t < tile_ptr[q + 1]; ++t) { r2 += part[2 * nt + 2 * t]; b2 += part[2 * t]; }
+      if (cycle == 0) bb[q] = b2;
+      rr[q] = r2;
+      const double beta = std::sqrt(r2), tolabs = c->opt.tol * std::sqrt(bb[q]);
+      conv[q] = bb[q] == 0.0 || beta <= tolabs;
+      const bool stop = conv[q] || it[q] >= c->opt.maxit || !std::isfinite(beta) || bad[q] || stalled[q];
+      hs[q] = BatchScalars{};
+      hs[q].done = stop ? 1 : 0;
+      hs[q].iter = it[q];
+      hs[q].tol2 = tolabs * tolabs;
+      hs[q].mode = 1;
+      invb[q] = stop ? 0.0 : 1.0 / beta;
+      std::fill(gmh.begin() + int64_t(q) * L.total(), gmh.begin() + int64_t(q + 1) * L.total(), 0.0);
+      gmh[int64_t(q) * L.total() + L.g()] = beta;
+      nlive += stop ? 0 : 1;
+    }
+    if (nlive == 0) break;
+    GDSW_CK(cudaMemcpyAsync(c->bks, hs.data(), sizeof(BatchScalars) * np, cudaMemcpyHostToDevice, s));
+    GDSW_CK(cudaMemcpyAsync(c->bgm, gmh.data(), sizeof(double) * gmh.size(), cudaMemcpyHostToDevice, s));
+    GDSW_CK(cudaMemcpyAsync(c->bgm_y, invb.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    k_bgm_scale<<<nt, kThreads, 0, s>>>(c->tile_prob, c->tile_r0, c->tile_r1, c->r, c->bgm_y, c->bks, c->V);
+    GDSW_CK(cudaGetLastError());
+    const int pg = (np + 255) / 256;
+    for (int j = 0; j < m; ++j) {
+      const int k = j + 1;
+      double* vj = c->V + int64_t(j) * n;
+      double* zj = c->Zk + int64_t(j) * n;
+      double* w = c->V + int64_t(k) * n;
+      GDSW_TRY(apply_enqueue_batch(c, vj, zj, s));
+      GDSW_TRY(spmv_enqueue_batch(c, zj, w, s));
+      const int rg = (np * (k + 1) + 7) / 8;
+      for (int pass = 1; pass <= 2; ++pass) {
+        k_bgm_dots<<<nt, kThreads, 0, s>>>(n, k, c->tile_prob, c->tile_r0, c->tile_r1, c->V, w, c->bks, c->red,
+                                           stride, pass);
+        k_bgm_reduce<<<rg, 256, 0, s>>>(np, k, c->prob_tile_ptr, c->red, stride, c->bks, c->bgm, m, pass);
+        k_bgm_norm<<<pg, 256, 0, s>>>(np, k, c->bgm, m, c->bks, pass, keep);
+        k_bgm_orth<<<nt, kThreads, 0, s>>>(n, k, c->tile_prob, c->tile_r0, c->tile_r1, c->V, c->bgm, m, c->bks, w,
+                                           pass);
+      }
+      k_bgm_givens<<<pg, 256, 0, s>>>(np, j, m, c->bgm, c->bks, c->opt.maxit);
+      GDSW_CK(cudaGetLastError());
+    }
+    GDSW_CK(cudaMemcpyAsync(gmh.data(), c->bgm, sizeof(double) * gmh.size(), cudaMemcpyDeviceToHost, s));
+    std::vector<BatchScalars> after(np);
+    GDSW_CK(cudaMemcpyAsync(after.data(), c->bks, sizeof(BatchScalars) * np, cudaMemcpyDeviceToHost, s));
+    GDSW_CK(cudaStreamSynchronize(s));
+    // y = R^-1 g per member (back substitution), x += Z y
+    for (int q = 0; q < np; ++q) {
+      jd[q] = 0;
+      if (hs[q].done) continue;
+      const int steps = after[q].iter - it[q];
+      const double* G = gmh.data() + int64_t(q) * L.total();
+      double* y = yv.data() + int64_t(q) * m;
+      for (int i = steps - 1; i >= 0; --i) {
+        double v = G[L.g() + i];
+        for (int kk = i + 1; kk < steps; ++kk) v -= G[size_t(i) * m + kk] * y[kk];
+        y[i] = v / G[size_t(i) * m + i];
+      }
+      jd[q] = steps;
+      it[q] = after[q].iter;
+      bad[q] = after[q].bad;
+      stalled[q] = steps == 0;
+    }
+    GDSW_CK(cudaMemcpyAsync(c->bgm_y, yv.data(), sizeof(double) * yv.size(), cudaMemcpyHostToDevice, s));
+    GDSW_CK(cudaMemcpyAsync(c->bgm_jd, jd.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    k_bgm_update_x<<<nt, kThreads, 0, s>>>(n, c->tile_prob, c->tile_r0, c->tile_r1, c->Zk, c->bgm_y, c->bgm_jd, m,
+                                           c->x);
+    GDSW_CK(cudaGetLastError());
+  }
+  GDSW_CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GDSW_CK(cudaStreamSynchronize(s));
+  GDSW_TRY(check_device_errors(c, s));
+  bool all_ok = true;
+  const double el = now_s() - t0;
+  for (int q = 0; q < np; ++q) {
+    all_ok = all_ok && conv[q];
+    if (info) {
+      info[q].iters = it[q];
+      info[q].converged = conv[q];
+      info[q].true_relres = bb[q] == 0.0 ? 0.0 : std::sqrt(rr[q] / bb[q]);
+      info[q].seconds = el;
+    }
+  }
+  if (!all_ok) { set_error("batched GMRES: some problems did not converge"); return GDSW_ERR_NOT_CONVERGED; }
+  return GDSW_OK;
+}
+
+gdsw_status solve_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s) {
+  return c->opt.krylov == GDSW_KRYLOV_GMRES ? solve_gmres_batch(c, b, x, info, s)
+                                            : solve_pcg_batch(c, b, x, info, s);
 }
 
 }  // namespace gdsw

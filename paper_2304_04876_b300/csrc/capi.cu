@@ -78,7 +78,7 @@ gdsw_status apply_configure(Ctx* c);
 gdsw_status solve_any(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s) {
   if (c->nprob > 1) {
     std::vector<gdsw_solve_info> all(c->nprob);
-    gdsw_status st = solve_pcg_batch(c, b, x, all.data(), s);
+    gdsw_status st = solve_batch(c, b, x, all.data(), s);
     if (info) {
       *info = gdsw_solve_info{0, 1, 0.0, 0.0};
       for (const auto& a : all) {
@@ -384,7 +384,10 @@ gdsw_status gdsw_setup_batch(int32_t count, const gdsw_csr* A, const gdsw_partit
   if (count < 1 || !A || !parts) { set_error("batch needs count >= 1 matrices and partitions"); return GDSW_ERR_INVALID_ARG; }
   gdsw_options o;
   if (!prepare_options(opt, &o)) return GDSW_ERR_INVALID_ARG;
-  if (o.krylov != GDSW_KRYLOV_PCG) { set_error("batched solves use PCG"); return GDSW_ERR_UNSUPPORTED; }
+  if (o.krylov == GDSW_KRYLOV_GMRES && o.gmres_orth == GDSW_GMRES_ORTH_DCGS2) {
+    set_error("batched GMRES uses CGS2 or the single-reduce form");
+    return GDSW_ERR_UNSUPPORTED;
+  }
   const double t0 = now_s();
   std::vector<HostCsr> hosts(count);
   for (int p = 0; p < count; ++p) GDSW_TRY(host_csr(&A[p], &hosts[p]));
@@ -474,6 +477,7 @@ gdsw_status gdsw_batch_start(gdsw_handle h, int32_t member, const double* b, voi
   if (!h || !b) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
   Ctx* c = &h->c;
   if (c->nprob < 2 || c->bks == nullptr) { set_error("gdsw_batch_start needs a batched handle"); return GDSW_ERR_INVALID_ARG; }
+  if (c->opt.krylov != GDSW_KRYLOV_PCG) { set_error("continuous batching runs PCG"); return GDSW_ERR_UNSUPPORTED; }
   if (member < 0 || member >= c->nprob) { set_error("member %d out of range [0, %d)", member, c->nprob); return GDSW_ERR_INVALID_ARG; }
   return batch_start(c, member, b, static_cast<cudaStream_t>(stream));
 }
@@ -482,6 +486,7 @@ gdsw_status gdsw_batch_iterate(gdsw_handle h, int32_t iterations, void* stream) 
   if (!h || iterations < 0) { set_error("null handle or negative iteration count"); return GDSW_ERR_INVALID_ARG; }
   Ctx* c = &h->c;
   if (c->nprob < 2 || c->bks == nullptr) { set_error("gdsw_batch_iterate needs a batched handle"); return GDSW_ERR_INVALID_ARG; }
+  if (c->opt.krylov != GDSW_KRYLOV_PCG) { set_error("continuous batching runs PCG"); return GDSW_ERR_UNSUPPORTED; }
   return batch_iterate(c, iterations, static_cast<cudaStream_t>(stream));
 }
 
@@ -522,7 +527,7 @@ gdsw_status gdsw_solve_batch(gdsw_handle h, const double* b, double* x, gdsw_sol
   if (!h || !b || !x) { set_error("null argument"); return GDSW_ERR_INVALID_ARG; }
   Ctx* c = &h->c;
   if (c->nprob == 1) return solve_any(c, b, x, info, static_cast<cudaStream_t>(stream));
-  return solve_pcg_batch(c, b, x, info, static_cast<cudaStream_t>(stream));
+  return solve_batch(c, b, x, info, static_cast<cudaStream_t>(stream));
 }
 
 gdsw_status gdsw_solve_host(gdsw_handle h, const double* b_host, double* x_host,

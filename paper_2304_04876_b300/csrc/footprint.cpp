@@ -173,6 +173,13 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
   if (P.nprob > 1)
     R += 4 * arr(n / 4096 + 2 * P.nprob + 1, 4) + arr(P.nprob, 256) + arr(4 * (n / 4096 + P.nprob) + 64, 8) +
          arr(nsub, 4) + arr(nsub + P.ncomp, 4) + arr(P.nprob + 1, 4);
+  // batched GMRES: per member its Hessenberg workspace, y and step count; the
+  // partials of an Arnoldi step's dots (restart + 2 per tile)
+  if (P.nprob > 1 && o.krylov == GDSW_KRYLOV_GMRES) {
+    const int64_t m = std::max(1, o.restart);
+    R += arr(P.nprob * ((m + 1) * m + 5 * m + 8), 8) + arr(P.nprob * m, 8) + arr(P.nprob, 4) +
+         arr((n / 4096 + P.nprob) * (m + 2) + 64, 8);
+  }
   *resident = R;
   *scratch_peak = S;
   return GDSW_OK;

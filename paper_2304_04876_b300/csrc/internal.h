@@ -304,6 +304,8 @@ constexpr int kStepRows = 128;       // rows per step of a row program (= its ke
 struct BatchScalars {
   double rz, pq, rr, bb, tol2, alpha, beta;
   int iter, done, bad, start;
+  int mode;                 // GMRES: 1 one Gram-Schmidt pass this step, 2 a second pass
+  int pad;
 };
 
 // Per-problem gating of the apply and SpMV kernels of a batched handle: a
@@ -490,6 +492,9 @@ struct Ctx {
   int red_grid = 0;
   // batched handle (several independent problems)
   int n_tiles = 0;
+  double* bgm = nullptr;          // batched GMRES: per-member Hessenberg, rotations, g, coefficients
+  double* bgm_y = nullptr;        // per member: 1 / beta at a cycle's start, then y of the cycle
+  int* bgm_jd = nullptr;          // per member: Arnoldi steps of the cycle
   int *tile_prob = nullptr, *tile_r0 = nullptr, *tile_r1 = nullptr, *prob_tile_ptr = nullptr;
   std::vector<int> prob_dof_host;
   BatchScalars* bks = nullptr;
@@ -594,6 +599,8 @@ gdsw_status solve_gmres(Ctx* c, const double* b, double* x, gdsw_solve_info* inf
 gdsw_status batch_init(Ctx* c, const std::vector<int>& prob_dof_ptr, const std::vector<int>& sub_prob,
                        const std::vector<int>& blk_prob, cudaStream_t s);
 gdsw_status solve_pcg_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
+gdsw_status solve_gmres_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
+gdsw_status solve_batch(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);
 // Continuous batching on a batched handle: members start, iterate together
 // and finish independently (see gdsw_batch_start and the entry points after it).
 gdsw_status batch_start(Ctx* c, int member, const double* b, cudaStream_t s);

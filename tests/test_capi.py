@@ -107,8 +107,8 @@ def test_batch_rejects_bad_members_on_host(lib):
     with pytest.raises(G.GdswError) as ex:      # different unknowns per node
         G.Handle.batch([(a.A, a.part, None), (e.A, e.part, None)], stream=False)
     assert ex.value.status == G.ERR_INVALID_ARG
-    with pytest.raises(G.GdswError) as ex:      # GMRES is not batched
-        G.Handle.batch([(a.A, a.part, None)], stream=False, krylov="gmres")
+    with pytest.raises(G.GdswError) as ex:      # batched GMRES: CGS2 or single-reduce only
+        G.Handle.batch([(a.A, a.part, None)], stream=False, krylov="gmres", gmres_orth="dcgs2")
     assert ex.value.status == G.ERR_UNSUPPORTED
 
 
