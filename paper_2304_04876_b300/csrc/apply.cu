@@ -1159,9 +1159,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
     const T* col = phi + phi_off[b] + int64_t(u) * nr + i0;
     T acc[4] = {T(0), T(0), T(0), T(0)};
     int i = lane;
-    for (; i + 96 < rows; i += 128) {
+    // software-pipelined: the next four values of the column are loaded before
+    // the current four are used
+    if (i + 96 < rows) {
+      T cv[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fma(col[i + 32 * j], rs[i + 32 * j], acc[j]);
+      for (int j = 0; j < 4; ++j) cv[j] = col[i + 32 * j];
+      for (; i + 128 + 96 < rows; i += 128) {
+        T nx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) nx[j] = col[i + 128 + 32 * j];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = fma(cv[j], rs[i + 32 * j], acc[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cv[j] = nx[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fma(cv[j], rs[i + 32 * j], acc[j]);
+      i += 128;
     }
     for (; i < rows; i += 32) acc[0] = fma(col[i], rs[i], acc[0]);
     const T t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
@@ -1217,12 +1232,24 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(int n0, const TA* __restric
 #pragma unroll
       for (int u = 0; u < 8; ++u) a[u] = TA(0);
       int j = j0 + lane;
-      for (; j + 7 * 32 < j1; j += 8 * 32) {
+      // software-pipelined: the next eight values of the row are loaded before
+      // the current eight are used, so two trips' loads are in flight
+      if (j + 7 * 32 < j1) {
         TA m[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) m[u] = Ar[j + 32 * u];
+        for (; j + 15 * 32 < j1; j += 8 * 32) {
+          TA nx[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) nx[u] = Ar[j + 8 * 32 + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) a[u] = fma(m[u], cv[j + 32 * u], a[u]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) m[u] = nx[u];
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) a[u] = fma(m[u], cv[j + 32 * u], a[u]);
+        j += 8 * 32;
       }
       for (; j < j1; j += 32) a[0] = fma(Ar[j], cv[j], a[0]);
       acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
