@@ -588,40 +588,54 @@ __global__ void __launch_bounds__(kStepRows, 4) k_local_steps(const double* __re
     }
   }
   __syncthreads();
-  for (int i = 0; i < nst; ++i) {
-    const int2 sd = stp[i];
-    // refill the slot read during the previous step (its values are already
-    // in registers, so the copy cannot overtake the read) with step i - 1 + D
-    if (i > 0) {
-      const int j = i - 1 + D;
-      if (j < nst) {
-        const int2 sn = stp[j];
-        const int slot = (i - 1) % D;
-        if (t < (sn.y & 0xffff)) {
-          cp_async16(&ring_a[slot * NT + t], prog_a + sn.x + t);
-          cp_async8(&ring_c[slot * NT + t], prog_c + sn.x + t);
+  // the steps go D at a time, unrolled, so every ring slot is a compile-time
+  // offset from this thread's slot 0; the step table entries of the current,
+  // refilled and next steps are read once each
+  const float4* pa = prog_a + t;
+  const uint2* pc = prog_c + t;
+  float4* ra = ring_a + t;
+  uint2* rc = ring_c + t;
+  int2 sd_next = nst > 0 ? stp[0] : make_int2(0, 0);
+  for (int i0 = 0; i0 < nst; i0 += D) {
+#pragma unroll
+    for (int u = 0; u < D; ++u) {
+      const int i = i0 + u;
+      if (i >= nst) break;
+      const int2 sd = sd_next;
+      // refill the slot read during the previous step (its values are already
+      // in registers, so the copy cannot overtake the read) with step i - 1 + D
+      if (i > 0) {
+        const int j = i - 1 + D;
+        if (j < nst) {
+          const int2 sn = stp[j];
+          const int slot = (u + D - 1) % D;   // a constant once unrolled
+          if (t < (sn.y & 0xffff)) {
+            cp_async16(ra + slot * NT, pa + sn.x);
+            cp_async8(rc + slot * NT, pc + sn.x);
+          }
+        }
+        cp_async_commit();
+      }
+      if (t < (sd.y & 0xffff)) {
+        const int row = cc.y >> 16;
+        float acc = v[row];
+        acc = fmaf(-a.x, v[cc.x & 0xffff], acc);
+        acc = fmaf(-a.y, v[cc.x >> 16], acc);
+        acc = fmaf(-a.z, v[cc.y & 0xffff], acc);
+        v[row] = acc * a.w;
+      }
+      if (i + 1 < nst) {
+        // step i + 1's group: D + i groups of steps committed, i + 2 of them done
+        cp_async_wait<D - 2>();
+        sd_next = stp[i + 1];
+        if (t < (sd_next.y & 0xffff)) {
+          const int slot = (u + 1) % D;
+          a = ra[slot * NT];
+          cc = rc[slot * NT];
         }
       }
-      cp_async_commit();
+      if (sd.y >> 16) __syncthreads();
     }
-    if (t < (sd.y & 0xffff)) {
-      const int row = cc.y >> 16;
-      float acc = v[row];
-      acc = fmaf(-a.x, v[cc.x & 0xffff], acc);
-      acc = fmaf(-a.y, v[cc.x >> 16], acc);
-      acc = fmaf(-a.z, v[cc.y & 0xffff], acc);
-      v[row] = acc * a.w;
-    }
-    if (i + 1 < nst) {
-      // step i + 1's group: D + i groups of steps committed, i + 2 of them done
-      cp_async_wait<D - 2>();
-      if (t < (stp[i + 1].y & 0xffff)) {
-        const int slot = (i + 1) % D;
-        a = ring_a[slot * NT + t];
-        cc = ring_c[slot * NT + t];
-      }
-    }
-    if (sd.y >> 16) __syncthreads();
   }
   for (int q = t; q < m; q += NT) zloc[base + q] = v[q];
 }
