@@ -640,9 +640,149 @@ __global__ void __launch_bounds__(kStepRows, 4) k_local_steps(const double* __re
   for (int q = t; q < m; q += NT) zloc[base + q] = v[q];
 }
 
+// ---- level-scheduled solve from node programs (three unknowns per node) ----
+//
+// One CTA of kNodeThreads threads per subdomain; eight lanes per node.  The
+// pieces of the subdomain's node program (see the setup's node programs) come
+// by bulk copies, issued by thread 0, into a ring of S slots (an mbarrier per
+// slot completing on the bytes, waits bounded), S pieces ahead.  Per node: each
+// lane sums its share of the node's off-node columns for the three rows at
+// once (z at a column is read once for all three), the eight lanes' partial
+// sums meet in a shuffle tree, and the node's first lane solves the three rows
+// in order with the in-node coefficients; one barrier per piece, after which
+// thread 0 refills the slot.  A wait that runs out sets the failure flag; the
+// threads leave together at the next barrier, thread 0 lets its copies land,
+// and z_s is not written.
+template <int S>
+__global__ void __launch_bounds__(kNodeThreads, 1) k_local_nodes(const double* __restrict__ r,
+                                                                const int* __restrict__ om_ptr,
+                                                                const int* __restrict__ om_dofs,
+                                                                const int* __restrict__ node_ptr,
+                                                                const int4* __restrict__ pieces,
+                                                                const uint8_t* __restrict__ stream,
+                                                                int slot_bytes, float* __restrict__ zloc,
+                                                                const KrylovScalars* __restrict__ ks, int* err,
+                                                                long long wait_cycles, int stall_test,
+                                                                BatchGate gate) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[S];
+  __shared__ __align__(8) uint64_t gbar;
+  __shared__ int s_fail;
+  if (ks != nullptr && ks->done) return;
+  const int s = blockIdx.x;
+  if (gate_sub_off(gate, s)) return;
+  const int base = om_ptr[s], m = om_ptr[s + 1] - base;
+  const int p0 = node_ptr[s], np = node_ptr[s + 1] - p0;
+  unsigned char* ring = smem_raw;
+  unsigned char* vreg = smem_raw + size_t(S) * slot_bytes;
+  const int off = base & 3;
+  const int cnt = m > 0 ? (off + m + 3) & ~3 : 0;
+  const int* idx = reinterpret_cast<const int*>(vreg) + off;
+  float* v = reinterpret_cast<float*>(vreg) + off;
+  const int t = threadIdx.x, lane8 = t & 7, group = t >> 3;
+  constexpr int NG = kNodeThreads / 8;
+  const bool withhold = stall_test && s == 0;
+  int issued = 0;
+  auto issue = [&](int j) {
+    const int4 pc = pieces[p0 + j];
+    mbar_expect_tx(&full[j % S], unsigned(pc.y + 15) & ~15u);
+    bulk_g2s(ring + size_t(j % S) * slot_bytes, stream + size_t(pc.x) * 16, unsigned(pc.y + 15) & ~15u,
+             &full[j % S]);
+  };
+  if (t == 0) {
+    for (int d = 0; d < S; ++d) mbar_init(&full[d], 1);
+    mbar_init(&gbar, 1);
+    s_fail = 0;
+    fence_mbar_init();
+    if (cnt > 0) {
+      mbar_expect_tx(&gbar, unsigned(cnt) * 4u);
+      bulk_g2s(vreg, om_dofs + (base - off), unsigned(cnt) * 4u, &gbar);
+    }
+    issued = min(S, np);
+    for (int j = withhold ? 1 : 0; j < issued; ++j) issue(j);
+  }
+  __syncthreads();
+  if (cnt > 0 && !mbar_wait_bounded(&gbar, 0, wait_cycles)) s_fail = 1;
+  __syncthreads();
+  bool failed = s_fail != 0;
+  if (!failed) gather_staged(r, idx, v, m, kNodeThreads);
+  __syncthreads();
+  int waited = -1;                           // last piece whose copy this thread saw land
+  int i = 0;
+  for (; i < np && !failed; ++i) {
+    if (!mbar_wait_bounded(&full[i % S], (i / S) & 1, wait_cycles)) {
+      s_fail = 1;
+    } else {
+      waited = i;
+      const unsigned char* pc = ring + size_t(i % S) * slot_bytes;
+      const int4 hdr = *reinterpret_cast<const int4*>(pc);
+      const int N = hdr.x & 0xffff, K = hdr.y;
+      const bool upper = (hdr.x >> 16) != 0;    // U sweep: the node's rows solved last to first
+      const uint16_t* nodes = reinterpret_cast<const uint16_t*>(pc + 16);
+      const float* coef = reinterpret_cast<const float*>(pc + 16 + ((2 * N + 15) & ~15));
+      const uint16_t* cols = reinterpret_cast<const uint16_t*>(pc + hdr.z);
+      const float* vals = reinterpret_cast<const float*>(pc + hdr.w);
+      for (int round = 0; round < N; round += NG) {
+        const int n = round + group;
+        const bool valid = n < N;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        if (valid) {
+          const uint16_t* cn = cols + size_t(n) * K;
+          const float* vn = vals + size_t(n) * 3 * K;
+          for (int k = lane8; k < K; k += 8) {
+            const float x = v[cn[k]];
+            s0 = fmaf(vn[k], x, s0);
+            s1 = fmaf(vn[K + k], x, s1);
+            s2 = fmaf(vn[2 * K + k], x, s2);
+          }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o, 8);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o, 8);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, o, 8);
+        }
+        if (valid && lane8 == 0) {
+          const int g = nodes[n];
+          const float* cf = coef + size_t(n) * 8;
+          // the row of solve step q: 3g + q in the L sweep, 3g + 2 - q in the U sweep
+          const int ra = upper ? 3 * g + 2 : 3 * g, rc = upper ? 3 * g : 3 * g + 2;
+          const float y0 = (v[ra] - s0) * cf[0];
+          const float y1 = (v[3 * g + 1] - s1 - cf[3] * y0) * cf[1];
+          const float y2 = (v[rc] - s2 - cf[4] * y0 - cf[5] * y1) * cf[2];
+          v[ra] = y0;
+          v[3 * g + 1] = y1;
+          v[rc] = y2;
+        }
+      }
+    }
+    __syncthreads();
+    failed = s_fail != 0;
+    if (t == 0 && !failed) {
+      const int lim = min(np, i + 1 + S);
+      if (issued < lim) fence_proxy_async_smem();
+      for (; issued < lim; ++issued) issue(issued);
+    }
+  }
+  if (failed) {
+    if (t == 0) {
+      atomicOr(err, 1);
+      for (int j = waited + 1; j < issued; ++j)
+        if (!(withhold && j == 0)) mbar_wait_bounded(&full[j % S], (j / S) & 1, wait_cycles);
+    }
+    return;
+  }
+  for (int q = t; q < m; q += kNodeThreads) zloc[base + q] = v[q];
+}
+
 // Shared memory of k_local_steps with D slots.
 inline size_t steps_smem_bytes(int D, int step_max, int max_m) {
   return size_t(D) * kStepRows * 24 + ((size_t(step_max) * 8 + 15) & ~size_t(15)) + pipe_vector_bytes(max_m, 4);
+}
+
+// Shared memory of k_local_nodes with S ring slots.
+inline size_t nodes_smem_bytes(int S, int slot_bytes, int max_m) {
+  return size_t(S) * slot_bytes + pipe_vector_bytes(max_m, 4);
 }
 
 // ---- level-scheduled solve without a barrier per level ----
@@ -1654,6 +1794,21 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
     dim3 grid((c->max_m + kDenseRows - 1) / kDenseRows, c->nsub);
     k_local_dense<T><<<grid, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
                                             c->ainv_off, zl, ks, gate);
+  } else if (c->node_stages > 0) {
+    // node programs (FP32, three unknowns per node)
+    if constexpr (std::is_same<T, float>::value) {
+      const size_t shm = nodes_smem_bytes(c->node_stages, c->node_slot_bytes, c->max_m);
+#define GDSW_NODES_LAUNCH(SS)                                                                              \
+  k_local_nodes<SS><<<c->nsub, kNodeThreads, shm, s>>>(r, c->om_ptr, c->om_dofs, c->node_ptr, c->node_piece, \
+                                                      c->node_stream, c->node_slot_bytes, zl, ks, c->derr,   \
+                                                      c->wait_cycles, c->stall_test, gate)
+      switch (c->node_stages) {
+        case 2: GDSW_NODES_LAUNCH(2); break;
+        case 4: GDSW_NODES_LAUNCH(4); break;
+        default: GDSW_NODES_LAUNCH(3); break;
+      }
+#undef GDSW_NODES_LAUNCH
+    }
   } else if (c->step_depth > 0) {
     // row programs with per-thread prefetch (FP32, rows of at most 3 entries)
     if constexpr (std::is_same<T, float>::value) {
@@ -1918,6 +2073,29 @@ gdsw_status steps_occupancy(Ctx* c, int D, int* per_sm) {
   return GDSW_OK;
 }
 
+// Resident CTAs per SM of the node-program solve with S ring slots (raises
+// its dynamic shared memory limit first; 0 when it does not fit).
+gdsw_status nodes_occupancy(Ctx* c, int S, int* per_sm) {
+  const size_t shm = nodes_smem_bytes(S, c->node_slot_bytes, c->max_m);
+  *per_sm = 0;
+  if (shm > size_t(max_block_smem_optin())) return GDSW_OK;
+  switch (S) {
+    case 2:
+      GDSW_CK(allow_max_dynamic_smem(k_local_nodes<2>));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<2>, kNodeThreads, shm));
+      break;
+    case 4:
+      GDSW_CK(allow_max_dynamic_smem(k_local_nodes<4>));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<4>, kNodeThreads, shm));
+      break;
+    default:
+      GDSW_CK(allow_max_dynamic_smem(k_local_nodes<3>));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<3>, kNodeThreads, shm));
+      break;
+  }
+  return GDSW_OK;
+}
+
 // Measured choice of the pipelined local solve's shape: every ring depth that
 // fits, with 128 to 992 consumer threads, timed over three launches each
 // (CUDA events, after one warm-up launch) on a zero right-hand side, and the
@@ -1993,6 +2171,27 @@ gdsw_status tune_local(Ctx* c) {
     }
     c->step_depth = 0;
   }
+  // the node-program kernel with 2 to 4 ring slots
+  int best_nodes = 0;
+  if (c->node_stream != nullptr && c->fp32 && !c->fp16) {
+    for (int S : {2, 3, 4}) {
+      if (st != GDSW_OK) break;
+      int per_sm = 0;
+      st = nodes_occupancy(c, S, &per_sm);
+      if (st != GDSW_OK || per_sm == 0) continue;
+      c->node_stages = S;
+      st = launch_local<float>(c, r, s, nullptr, BatchGate{});
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep) st = launch_local<float>(c, r, s, nullptr, BatchGate{});
+      cudaEventRecord(e1, s);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) { fail(e); break; }
+      if (ms < best) { best = ms; best_nodes = S; best_depth = 0; }
+    }
+    c->node_stages = 0;
+  }
   // the unpipelined level-scheduled kernel (factors read through L2), with
   // 256 to 1024 threads, as further candidates
   int best_tri = c->tri_threads;
@@ -2009,9 +2208,10 @@ gdsw_status tune_local(Ctx* c) {
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) { fail(e); break; }
-    if (ms < best) { best = ms; best_s = 0; best_tri = tt; best_depth = 0; }
+    if (ms < best) { best = ms; best_s = 0; best_tri = tt; best_depth = 0; best_nodes = 0; }
   }
   c->step_depth = best_depth;
+  c->node_stages = best_nodes;
   c->rec_stages = best_s;
   c->rec_consumers = best_nt;
   c->rec_sf = best_s > 0 && best_sf;
@@ -2189,7 +2389,15 @@ gdsw_status apply_configure(Ctx* c) {
   if (c->rec_stages > 0 && shape != nullptr) {
     int st = 0, nt = 0, sf = 0;
     const int got = sscanf(shape, "%d,%d,%d", &st, &nt, &sf);
-    if (got == 3 && sf == 2 && c->steps != nullptr && c->fp32 && !c->fp16 && (st == 4 || st == 8 || st == 12)) {
+    if (got == 3 && sf == 3 && c->node_stream != nullptr && (st == 2 || st == 3 || st == 4)) {
+      int per_sm = 0;
+      GDSW_TRY(nodes_occupancy(c, st, &per_sm));
+      if (per_sm == 0) {
+        set_error("GDSW_LOCAL_SHAPE=%s does not fit the shared memory", shape);
+        return GDSW_ERR_UNSUPPORTED;
+      }
+      c->node_stages = st;
+    } else if (got == 3 && sf == 2 && c->steps != nullptr && c->fp32 && !c->fp16 && (st == 4 || st == 8 || st == 12)) {
       int per_sm = 0;
       GDSW_TRY(steps_occupancy(c, st, &per_sm));
       if (per_sm == 0) {

@@ -5,6 +5,7 @@
 // upper bounds (equal when no column is dropped).
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <vector>
 
 #include "internal.h"
@@ -62,6 +63,65 @@ int64_t jacobi_block_bytes(const Plan& P, int64_t vb) {
   return total;
 }
 
+size_t node_piece_cap() {
+  size_t cap = kNodePieceBytes;
+  if (const char* e = getenv("GDSW_NODE_PIECE_BYTES")) cap = std::min<size_t>(cap, std::max<long>(1024, atol(e)));
+  return cap;
+}
+
+bool plan_node_pieces(const Plan& P, size_t cap, std::vector<NodePiece>* pieces, std::vector<int>* pptr,
+                      size_t* total, size_t* max_bytes) {
+  const int nsub = P.nsub;
+  pieces->clear();
+  pptr->assign(nsub + 1, 0);
+  *total = 0;
+  *max_bytes = 0;
+  for (int q = 0; q < nsub; ++q) {
+    for (int side = 0; side < 2; ++side) {
+      const EllPlan& E = side == 0 ? P.L : P.U;
+      for (int l = E.sub_lev[q]; l < E.sub_lev[q + 1]; ++l) {
+        const int L_nr = E.lev_nr[l];
+        if (L_nr % 3 != 0) return false;
+        const int nodes = L_nr / 3;
+        // the rows of a node consecutive, in solve order (L: 3g, 3g+1, 3g+2; U: reversed)
+        for (int t = 0; t < L_nr; ++t) {
+          const int g = E.lrows[E.lev_start[l] + t - t % 3] / 3, st = t % 3;
+          if (E.lrows[E.lev_start[l] + t] != 3 * g + (side == 0 ? st : 2 - st)) return false;
+        }
+        // the level's widest union of off-node columns
+        int K = 0;
+        std::vector<int> u;
+        for (int gi = 0; gi < nodes; ++gi) {
+          u.clear();
+          const int g = E.lrows[E.lev_start[l] + 3 * gi] / 3;
+          for (int st = 0; st < 3; ++st)
+            for (int k = 0; k < E.lev_K[l]; ++k) {
+              const int64_t slot = E.lev_off[l] + int64_t(k) * L_nr + 3 * gi + st;
+              if (E.src[slot] >= 0 && E.col[slot] / 3 != g) u.push_back(E.col[slot]);
+            }
+          std::sort(u.begin(), u.end());
+          K = std::max<int>(K, static_cast<int>(std::unique(u.begin(), u.end()) - u.begin()));
+        }
+        K = std::max(K, 1);
+        // node index, float[8] coefficients, K columns and 3K values per node
+        const size_t per_node = 34 + 14 * size_t(K);
+        const int cap_nodes = std::max(1, static_cast<int>((cap - 96) / per_node));
+        for (int n0 = 0; n0 < nodes; n0 += cap_nodes) {
+          const int N = std::min(cap_nodes, nodes - n0);
+          const size_t bytes = 16 + size_t(a16(2 * int64_t(N))) + 32 * size_t(N) +
+                               size_t(a16(2 * int64_t(N) * K)) + 12 * size_t(N) * K;
+          if (bytes > cap) return false;
+          pieces->push_back(NodePiece{q, side, l, n0, N, K, *total, bytes});
+          *total += size_t(a16(int64_t(bytes)));
+          *max_bytes = std::max(*max_bytes, size_t(a16(int64_t(bytes))));
+        }
+      }
+    }
+    (*pptr)[q + 1] = static_cast<int>(pieces->size());
+  }
+  return *total / 4 < (size_t(1) << 31);
+}
+
 gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
                                int64_t* scratch_peak) {
   const bool exact = o.local_solver == GDSW_LOCAL_EXACT;
@@ -98,6 +158,18 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
       for (const EllPlan* E : {&P.L, &P.U})
         for (int nr : E->lev_nr) nsteps += (nr + kStepRows - 1) / kStepRows;
       R += arr(2 * sum_m, 16) + arr(2 * sum_m, 8) + arr(nsteps, 8) + arr(nsub + 1, 4);
+    }
+    // node programs (FP32, three unknowns per node): the stream, piece ranges
+    // and table; scratch: value and coefficient positions and sources per sweep
+    if (P.dpn == 3 && o.precision == GDSW_PREC_FP32 && o.trsv == GDSW_TRSV_LEVELSCHED && sum_m > 0) {
+      std::vector<NodePiece> pcs;
+      std::vector<int> pptr;
+      size_t total = 0, maxb = 0;
+      if (plan_node_pieces(P, node_piece_cap(), &pcs, &pptr, &total, &maxb)) {
+        R += arr(static_cast<int64_t>(total) + 16, 1) + arr(nsub + 1, 4) +
+             arr(static_cast<int64_t>(pcs.size()), 16);
+        for (const EllPlan* E : {&P.L, &P.U}) S += 2 * arr(E->slots, 4) + 2 * arr(sum_m, 4);
+      }
     }
   } else if (P.max_m > exact_dense_max() || [&] {
                int64_t d = 0;

@@ -253,6 +253,18 @@ inline int mf_leaf_size() {
 gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
                                int64_t* scratch_peak);
 int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec);
+// Pieces of the node programs (three unknowns per node, FP32): per subdomain,
+// sweep (L then U) and level, runs of at most `cap` bytes; each piece's
+// subdomain, sweep, level, first node, nodes, widest union of off-node columns
+// (K), offset in the stream and bytes.  False when the plan does not take them
+// (a level whose rows do not come as whole nodes in solve order, or a node
+// wider than a piece).
+struct NodePiece { int sub, side, lev, t0, nodes, K; size_t off, bytes; };
+// The piece limit: kNodePieceBytes, or less by GDSW_NODE_PIECE_BYTES (at least
+// 1 KB; several pieces per level, for tests).
+size_t node_piece_cap();
+bool plan_node_pieces(const Plan& P, size_t cap, std::vector<NodePiece>* pieces, std::vector<int>* pptr,
+                      size_t* total, size_t* max_bytes);
 
 gdsw_status build_plan(const gdsw_csr* A, const gdsw_partition* part, const gdsw_options* opt,
                        bool need_levels, Plan* P);
@@ -296,6 +308,8 @@ struct KrylovScalars {
 
 constexpr int kNumSMsForCtx = 148;
 constexpr int kStepRows = 128;       // rows per step of a row program (= its kernel's threads)
+constexpr int kNodePieceBytes = 48 * 1024;   // largest piece of a node program
+constexpr int kNodeThreads = 512;            // threads of the node-program kernel (8 per node)
 
 // Per-problem PCG state of a batched handle.  `start` makes the next
 // iteration the PCG prologue for this problem (step lengths 0: r stays, z = M r,
@@ -400,6 +414,12 @@ struct Ctx {
   int* step_ptr = nullptr;           // nsub+1: step range of each subdomain
   int step_max = 0;                  // most steps of one subdomain
   int step_depth = 0;                // steps in flight per thread; 0: kernel not used
+  // node programs of the three-unknowns-per-node solve (k_local_nodes)
+  uint8_t* node_stream = nullptr;
+  int* node_ptr = nullptr;           // nsub+1: piece range of each subdomain
+  int4* node_piece = nullptr;        // {offset / 16, bytes, 0, 0}
+  int node_slot_bytes = 0;           // largest piece
+  int node_stages = 0;               // ring slots; 0: kernel not used
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int rec_max_rows = 0;              // most rows in one level
   int rec_consumers = 256;           // consumer threads of the pipelined solve

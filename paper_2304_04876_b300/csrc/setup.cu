@@ -1106,6 +1106,100 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
         GDSW_CK(cudaGetLastError());
       }
     }
+    // Node programs for the level-scheduled solve with three unknowns per node
+    // (k_local_nodes; FP32): the rows of a node share their couplings to other
+    // nodes, so per subdomain, sweep (L then U) and level, pieces of at most
+    // kNodePieceBytes hold for each node: its index, its three inverse
+    // diagonals and in-node coefficients by solve step (float[8]: d0, d1, d2,
+    // c10, c20, c21), the union of its rows' off-node columns (uint16, K per
+    // node, the level's widest) and the three rows' values over that union
+    // (float[3][K], zero where a row lacks the column).  Section layout: int4
+    // {nodes | U sweep << 16, K, columns offset, values offset} | uint16 node[N] | float[N][8] |
+    // uint16[N][K] | float[N][3][K], each 16-byte aligned.  Values are placed
+    // on the device (k_fill_records) from the factor; ELL padding goes to a
+    // spare element at the end.
+    if (P.dpn == 3 && c->fp32 && !c->fp16 && o.trsv == GDSW_TRSV_LEVELSCHED && P.sum_m > 0) {
+      auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+      std::vector<NodePiece> pieces;
+      std::vector<int> pptr;
+      size_t total = 0, maxb = 0;
+      const bool ok = plan_node_pieces(P, node_piece_cap(), &pieces, &pptr, &total, &maxb);
+      if (ok) {
+        const size_t dummy = total / 4;            // float element absorbing ELL padding
+        std::vector<uint8_t> host(total + 16, 0);
+        std::vector<uint32_t> vpos[2] = {std::vector<uint32_t>(P.L.slots, uint32_t(dummy)),
+                                         std::vector<uint32_t>(P.U.slots, uint32_t(dummy))};
+        std::vector<uint32_t> dpos[2] = {std::vector<uint32_t>(P.sum_m, uint32_t(dummy)),
+                                         std::vector<uint32_t>(P.sum_m, uint32_t(dummy))};
+        std::vector<int4> ptab(pieces.size());
+        for (size_t pi = 0; pi < pieces.size(); ++pi) {
+          const NodePiece& pc = pieces[pi];
+          const EllPlan& E = pc.side == 0 ? P.L : P.U;
+          const int l = pc.lev, L_nr = E.lev_nr[l], N = pc.nodes, K = pc.K;
+          const size_t o_node = 16, o_coef = o_node + a16(2 * size_t(N)), o_col = o_coef + 32 * size_t(N),
+                       o_val = o_col + a16(2 * size_t(N) * K);
+          const int hdr[4] = {N | (pc.side << 16), K, static_cast<int>(o_col), static_cast<int>(o_val)};
+          std::memcpy(&host[pc.off], hdr, 16);
+          uint16_t* nodes = reinterpret_cast<uint16_t*>(&host[pc.off + o_node]);
+          uint16_t* cols = reinterpret_cast<uint16_t*>(&host[pc.off + o_col]);
+          for (int gi = 0; gi < N; ++gi) {
+            const int tbase = 3 * (pc.t0 + gi);
+            const int row0 = E.lrows[E.lev_start[l] + tbase];
+            const int g = row0 / 3;
+            nodes[gi] = static_cast<uint16_t>(g);
+            std::vector<uint16_t> u;
+            for (int st = 0; st < 3; ++st)
+              for (int k = 0; k < E.lev_K[l]; ++k) {
+                const int64_t slot = E.lev_off[l] + int64_t(k) * L_nr + tbase + st;
+                if (E.src[slot] >= 0 && E.col[slot] / 3 != g) u.push_back(E.col[slot]);
+              }
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            for (int k = 0; k < K; ++k)
+              cols[size_t(gi) * K + k] = k < static_cast<int>(u.size()) ? u[k] : static_cast<uint16_t>(row0);
+            for (int st = 0; st < 3; ++st) {
+              const int t = tbase + st;
+              dpos[pc.side][E.lev_start[l] + t] = static_cast<uint32_t>((pc.off + o_coef + 32 * size_t(gi)) / 4 + st);
+              for (int k = 0; k < E.lev_K[l]; ++k) {
+                const int64_t slot = E.lev_off[l] + int64_t(k) * L_nr + t;
+                if (E.src[slot] < 0) continue;
+                const int col = E.col[slot];
+                size_t fpos;
+                if (col / 3 == g) {
+                  // in-node coefficient of step st on the step that solved col
+                  const int sp = pc.side == 0 ? col % 3 : 2 - col % 3;
+                  const int ci = st == 1 ? 0 : (sp == 0 ? 1 : 2);      // c10, c20, c21
+                  fpos = (pc.off + o_coef + 32 * size_t(gi)) / 4 + 3 + ci;
+                } else {
+                  const int k2 = static_cast<int>(std::lower_bound(u.begin(), u.end(), static_cast<uint16_t>(col)) - u.begin());
+                  fpos = (pc.off + o_val) / 4 + (size_t(gi) * 3 + st) * K + k2;
+                }
+                vpos[pc.side][slot] = static_cast<uint32_t>(fpos);
+              }
+            }
+          }
+          ptab[pi] = make_int4(static_cast<int>(pc.off / 16), static_cast<int>(pc.bytes), 0, 0);
+        }
+        uint8_t* d_stream;
+        GDSW_TRY(upload(c, &d_stream, host, s));
+        GDSW_TRY(upload(c, &c->node_ptr, pptr, s));
+        GDSW_TRY(upload(c, &c->node_piece, ptab, s));
+        c->node_stream = d_stream;
+        c->node_slot_bytes = static_cast<int>(maxb);
+        for (int side = 0; side < 2; ++side) {
+          const EllPlan& E = side == 0 ? P.L : P.U;
+          uint32_t *d_vp, *d_dp;
+          int *d_src, *d_dsrc;
+          GDSW_TRY(sc.put(&d_vp, vpos[side], s));
+          GDSW_TRY(sc.put(&d_dp, dpos[side], s));
+          GDSW_TRY(sc.put(&d_src, E.src, s));
+          GDSW_TRY(sc.put(&d_dsrc, E.dsrc, s));
+          k_fill_records<float><<<grid_for(E.slots, 256), 256, 0, s>>>(E.slots, d_src, d_vp, P.sum_m, d_dsrc, d_dp, G,
+                                                                      reinterpret_cast<float*>(d_stream));
+          GDSW_CK(cudaGetLastError());
+        }
+      }
+    }
     // Resident blocks for the Jacobi sweeps (Sec. V-B3): per subdomain and
     // triangle one block that a CTA copies into shared memory once and sweeps
     // there: int4 {rows m, width K, values offset, columns offset} | m x T
