@@ -642,19 +642,19 @@ __global__ void __launch_bounds__(kStepRows, 4) k_local_steps(const double* __re
 
 // ---- level-scheduled solve from node programs (three unknowns per node) ----
 //
-// One CTA of kNodeThreads threads per subdomain; eight lanes per node.  The
+// One CTA of NT threads per subdomain; eight lanes per node.  The
 // pieces of the subdomain's node program (see the setup's node programs) come
-// by bulk copies, issued by thread 0, into a ring of S slots (an mbarrier per
-// slot completing on the bytes, waits bounded), S pieces ahead.  Per node: each
-// lane sums its share of the node's off-node columns for the three rows at
-// once (z at a column is read once for all three), the eight lanes' partial
+// by bulk copies, issued by one thread, into a ring of S slots (an mbarrier
+// per slot completing on the bytes, waits bounded), S pieces ahead.  Per node:
+// each lane sums its share of the node's off-node columns for the three rows
+// at once (z at a column is read once for all three), the eight lanes' partial
 // sums meet in a shuffle tree, and the node's first lane solves the three rows
 // in order with the in-node coefficients; one barrier per piece, after which
-// thread 0 refills the slot.  A wait that runs out sets the failure flag; the
-// threads leave together at the next barrier, thread 0 lets its copies land,
-// and z_s is not written.
-template <int S>
-__global__ void __launch_bounds__(kNodeThreads, 1) k_local_nodes(const double* __restrict__ r,
+// the issuing thread refills the slot.  A wait that runs out sets the failure
+// flag; the threads leave together at the next barrier, the issuing thread
+// lets its copies land, and z_s is not written.
+template <int S, int NT>
+__global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict__ r,
                                                                 const int* __restrict__ om_ptr,
                                                                 const int* __restrict__ om_dofs,
                                                                 const int* __restrict__ node_ptr,
@@ -680,16 +680,21 @@ __global__ void __launch_bounds__(kNodeThreads, 1) k_local_nodes(const double* _
   const int* idx = reinterpret_cast<const int*>(vreg) + off;
   float* v = reinterpret_cast<float*>(vreg) + off;
   const int t = threadIdx.x, lane8 = t & 7, group = t >> 3;
-  constexpr int NG = kNodeThreads / 8;
+  constexpr int NG = NT / 8;
   const bool withhold = stall_test && s == 0;
+  // the copies are issued by the last thread, whose warp has nodes only in
+  // the widest levels; it holds the table entry of the next piece in a
+  // register, loaded a level ahead
+  constexpr int kIssuer = NT - 1;
   int issued = 0;
+  int4 nxt = make_int4(0, 0, 0, 0);
   auto issue = [&](int j) {
-    const int4 pc = pieces[p0 + j];
-    mbar_expect_tx(&full[j % S], unsigned(pc.y + 15) & ~15u);
-    bulk_g2s(ring + size_t(j % S) * slot_bytes, stream + size_t(pc.x) * 16, unsigned(pc.y + 15) & ~15u,
-             &full[j % S]);
+    const unsigned bytes = unsigned(nxt.y + 15) & ~15u;
+    mbar_expect_tx(&full[j % S], bytes);
+    bulk_g2s(ring + size_t(j % S) * slot_bytes, stream + size_t(nxt.x) * 16, bytes, &full[j % S]);
+    if (j + 1 < np) nxt = pieces[p0 + j + 1];
   };
-  if (t == 0) {
+  if (t == kIssuer) {
     for (int d = 0; d < S; ++d) mbar_init(&full[d], 1);
     mbar_init(&gbar, 1);
     s_fail = 0;
@@ -698,14 +703,21 @@ __global__ void __launch_bounds__(kNodeThreads, 1) k_local_nodes(const double* _
       mbar_expect_tx(&gbar, unsigned(cnt) * 4u);
       bulk_g2s(vreg, om_dofs + (base - off), unsigned(cnt) * 4u, &gbar);
     }
+    if (np > 0) nxt = pieces[p0];
     issued = min(S, np);
-    for (int j = withhold ? 1 : 0; j < issued; ++j) issue(j);
+    for (int j = 0; j < issued; ++j) {
+      if (withhold && j == 0) {
+        if (1 < np) nxt = pieces[p0 + 1];
+      } else {
+        issue(j);
+      }
+    }
   }
   __syncthreads();
   if (cnt > 0 && !mbar_wait_bounded(&gbar, 0, wait_cycles)) s_fail = 1;
   __syncthreads();
   bool failed = s_fail != 0;
-  if (!failed) gather_staged(r, idx, v, m, kNodeThreads);
+  if (!failed) gather_staged(r, idx, v, m, NT);
   __syncthreads();
   int waited = -1;                           // last piece whose copy this thread saw land
   int i = 0;
@@ -719,16 +731,35 @@ __global__ void __launch_bounds__(kNodeThreads, 1) k_local_nodes(const double* _
       const int N = hdr.x & 0xffff, K = hdr.y;
       const bool upper = (hdr.x >> 16) != 0;    // U sweep: the node's rows solved last to first
       const uint16_t* nodes = reinterpret_cast<const uint16_t*>(pc + 16);
-      const float* coef = reinterpret_cast<const float*>(pc + 16 + ((2 * N + 15) & ~15));
+      const float4* coef = reinterpret_cast<const float4*>(pc + 16 + ((2 * N + 15) & ~15));
       const uint16_t* cols = reinterpret_cast<const uint16_t*>(pc + hdr.z);
       const float* vals = reinterpret_cast<const float*>(pc + hdr.w);
       for (int round = 0; round < N; round += NG) {
         const int n = round + group;
         const bool valid = n < N;
+        const bool solver = valid && lane8 == 0;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        // the solving lane's operands (its own rows: no other node writes them
+        // in this level), loaded before the sums so their latency overlaps
+        int ra = 0, rb = 0, rc = 0;
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f), cc = d;
+        float va = 0.f, vb = 0.f, vc = 0.f;
+        if (solver) {
+          const int g = nodes[n];
+          // the row of solve step q: 3g + q in the L sweep, 3g + 2 - q in the U sweep
+          ra = upper ? 3 * g + 2 : 3 * g;
+          rb = 3 * g + 1;
+          rc = upper ? 3 * g : 3 * g + 2;
+          d = coef[2 * n];
+          cc = coef[2 * n + 1];
+          va = v[ra];
+          vb = v[rb];
+          vc = v[rc];
+        }
         if (valid) {
           const uint16_t* cn = cols + size_t(n) * K;
           const float* vn = vals + size_t(n) * 3 * K;
+#pragma unroll 4
           for (int k = lane8; k < K; k += 8) {
             const float x = v[cn[k]];
             s0 = fmaf(vn[k], x, s0);
@@ -742,37 +773,34 @@ __global__ void __launch_bounds__(kNodeThreads, 1) k_local_nodes(const double* _
           s1 += __shfl_xor_sync(0xffffffffu, s1, o, 8);
           s2 += __shfl_xor_sync(0xffffffffu, s2, o, 8);
         }
-        if (valid && lane8 == 0) {
-          const int g = nodes[n];
-          const float* cf = coef + size_t(n) * 8;
-          // the row of solve step q: 3g + q in the L sweep, 3g + 2 - q in the U sweep
-          const int ra = upper ? 3 * g + 2 : 3 * g, rc = upper ? 3 * g : 3 * g + 2;
-          const float y0 = (v[ra] - s0) * cf[0];
-          const float y1 = (v[3 * g + 1] - s1 - cf[3] * y0) * cf[1];
-          const float y2 = (v[rc] - s2 - cf[4] * y0 - cf[5] * y1) * cf[2];
+        if (solver) {
+          // coefficients: d = {1/d0, 1/d1, 1/d2, c10}, cc = {c20, c21, -, -}
+          const float y0 = (va - s0) * d.x;
+          const float y1 = (vb - s1 - d.w * y0) * d.y;
+          const float y2 = (vc - s2 - cc.x * y0 - cc.y * y1) * d.z;
           v[ra] = y0;
-          v[3 * g + 1] = y1;
+          v[rb] = y1;
           v[rc] = y2;
         }
       }
     }
     __syncthreads();
     failed = s_fail != 0;
-    if (t == 0 && !failed) {
+    if (t == kIssuer && !failed) {
       const int lim = min(np, i + 1 + S);
       if (issued < lim) fence_proxy_async_smem();
       for (; issued < lim; ++issued) issue(issued);
     }
   }
   if (failed) {
-    if (t == 0) {
+    if (t == kIssuer) {
       atomicOr(err, 1);
       for (int j = waited + 1; j < issued; ++j)
         if (!(withhold && j == 0)) mbar_wait_bounded(&full[j % S], (j / S) & 1, wait_cycles);
     }
     return;
   }
-  for (int q = t; q < m; q += kNodeThreads) zloc[base + q] = v[q];
+  for (int q = t; q < m; q += NT) zloc[base + q] = v[q];
 }
 
 // Shared memory of k_local_steps with D slots.
@@ -1798,14 +1826,22 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
     // node programs (FP32, three unknowns per node)
     if constexpr (std::is_same<T, float>::value) {
       const size_t shm = nodes_smem_bytes(c->node_stages, c->node_slot_bytes, c->max_m);
-#define GDSW_NODES_LAUNCH(SS)                                                                              \
-  k_local_nodes<SS><<<c->nsub, kNodeThreads, shm, s>>>(r, c->om_ptr, c->om_dofs, c->node_ptr, c->node_piece, \
-                                                      c->node_stream, c->node_slot_bytes, zl, ks, c->derr,   \
-                                                      c->wait_cycles, c->stall_test, gate)
-      switch (c->node_stages) {
-        case 2: GDSW_NODES_LAUNCH(2); break;
-        case 4: GDSW_NODES_LAUNCH(4); break;
-        default: GDSW_NODES_LAUNCH(3); break;
+#define GDSW_NODES_LAUNCH(SS, TT)                                                                          \
+  k_local_nodes<SS, TT><<<c->nsub, TT, shm, s>>>(r, c->om_ptr, c->om_dofs, c->node_ptr, c->node_piece,       \
+                                                c->node_stream, c->node_slot_bytes, zl, ks, c->derr,         \
+                                                c->wait_cycles, c->stall_test, gate)
+      if (c->node_threads == 256) {
+        switch (c->node_stages) {
+          case 2: GDSW_NODES_LAUNCH(2, 256); break;
+          case 4: GDSW_NODES_LAUNCH(4, 256); break;
+          default: GDSW_NODES_LAUNCH(3, 256); break;
+        }
+      } else {
+        switch (c->node_stages) {
+          case 2: GDSW_NODES_LAUNCH(2, 512); break;
+          case 4: GDSW_NODES_LAUNCH(4, 512); break;
+          default: GDSW_NODES_LAUNCH(3, 512); break;
+        }
       }
 #undef GDSW_NODES_LAUNCH
     }
@@ -2073,26 +2109,32 @@ gdsw_status steps_occupancy(Ctx* c, int D, int* per_sm) {
   return GDSW_OK;
 }
 
-// Resident CTAs per SM of the node-program solve with S ring slots (raises
+// Resident CTAs per SM of the node-program solve with S ring slots and NT
+// threads (raises
 // its dynamic shared memory limit first; 0 when it does not fit).
-gdsw_status nodes_occupancy(Ctx* c, int S, int* per_sm) {
+gdsw_status nodes_occupancy(Ctx* c, int S, int NT, int* per_sm) {
   const size_t shm = nodes_smem_bytes(S, c->node_slot_bytes, c->max_m);
   *per_sm = 0;
   if (shm > size_t(max_block_smem_optin())) return GDSW_OK;
-  switch (S) {
-    case 2:
-      GDSW_CK(allow_max_dynamic_smem(k_local_nodes<2>));
-      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<2>, kNodeThreads, shm));
-      break;
-    case 4:
-      GDSW_CK(allow_max_dynamic_smem(k_local_nodes<4>));
-      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<4>, kNodeThreads, shm));
-      break;
-    default:
-      GDSW_CK(allow_max_dynamic_smem(k_local_nodes<3>));
-      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<3>, kNodeThreads, shm));
-      break;
+#define GDSW_NODES_OCC(SS, TT)                                                                \
+  do {                                                                                        \
+    GDSW_CK(allow_max_dynamic_smem(k_local_nodes<SS, TT>));                                   \
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<SS, TT>, TT, shm)); \
+  } while (0)
+  if (NT == 256) {
+    switch (S) {
+      case 2: GDSW_NODES_OCC(2, 256); break;
+      case 4: GDSW_NODES_OCC(4, 256); break;
+      default: GDSW_NODES_OCC(3, 256); break;
+    }
+  } else {
+    switch (S) {
+      case 2: GDSW_NODES_OCC(2, 512); break;
+      case 4: GDSW_NODES_OCC(4, 512); break;
+      default: GDSW_NODES_OCC(3, 512); break;
+    }
   }
+#undef GDSW_NODES_OCC
   return GDSW_OK;
 }
 
@@ -2172,14 +2214,16 @@ gdsw_status tune_local(Ctx* c) {
     c->step_depth = 0;
   }
   // the node-program kernel with 2 to 4 ring slots
-  int best_nodes = 0;
+  int best_nodes = 0, best_node_nt = kNodeThreads;
   if (c->node_stream != nullptr && c->fp32 && !c->fp16) {
-    for (int S : {2, 3, 4}) {
+    for (int S : {2, 3, 4})
+    for (int NT : {256, 512}) {
       if (st != GDSW_OK) break;
       int per_sm = 0;
-      st = nodes_occupancy(c, S, &per_sm);
+      st = nodes_occupancy(c, S, NT, &per_sm);
       if (st != GDSW_OK || per_sm == 0) continue;
       c->node_stages = S;
+      c->node_threads = NT;
       st = launch_local<float>(c, r, s, nullptr, BatchGate{});
       cudaEventRecord(e0, s);
       for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep) st = launch_local<float>(c, r, s, nullptr, BatchGate{});
@@ -2188,7 +2232,7 @@ gdsw_status tune_local(Ctx* c) {
       float ms = 0.f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       if (e != cudaSuccess) { fail(e); break; }
-      if (ms < best) { best = ms; best_nodes = S; best_depth = 0; }
+      if (ms < best) { best = ms; best_nodes = S; best_node_nt = NT; best_depth = 0; }
     }
     c->node_stages = 0;
   }
@@ -2212,6 +2256,7 @@ gdsw_status tune_local(Ctx* c) {
   }
   c->step_depth = best_depth;
   c->node_stages = best_nodes;
+  c->node_threads = best_node_nt;
   c->rec_stages = best_s;
   c->rec_consumers = best_nt;
   c->rec_sf = best_s > 0 && best_sf;
@@ -2384,19 +2429,22 @@ gdsw_status apply_configure(Ctx* c) {
   // GDSW_LOCAL_SHAPE="stages,threads[,kind]" fixes the shape instead of
   // timing it (for profilers, under which the timings mean nothing, and for
   // the failure tests); kind 1 selects the solve without a barrier per level,
-  // kind 2 the row programs with `stages` steps in flight per thread
+  // kind 2 the row programs with `stages` steps in flight per thread, kind 3
+  // the node programs with `stages` ring slots and 256 or 512 threads
   const char* shape = getenv("GDSW_LOCAL_SHAPE");
   if (c->rec_stages > 0 && shape != nullptr) {
     int st = 0, nt = 0, sf = 0;
     const int got = sscanf(shape, "%d,%d,%d", &st, &nt, &sf);
-    if (got == 3 && sf == 3 && c->node_stream != nullptr && (st == 2 || st == 3 || st == 4)) {
+    if (got == 3 && sf == 3 && c->node_stream != nullptr && (st == 2 || st == 3 || st == 4) &&
+        (nt == 256 || nt == 512)) {
       int per_sm = 0;
-      GDSW_TRY(nodes_occupancy(c, st, &per_sm));
+      GDSW_TRY(nodes_occupancy(c, st, nt, &per_sm));
       if (per_sm == 0) {
         set_error("GDSW_LOCAL_SHAPE=%s does not fit the shared memory", shape);
         return GDSW_ERR_UNSUPPORTED;
       }
       c->node_stages = st;
+      c->node_threads = nt;
     } else if (got == 3 && sf == 2 && c->steps != nullptr && c->fp32 && !c->fp16 && (st == 4 || st == 8 || st == 12)) {
       int per_sm = 0;
       GDSW_TRY(steps_occupancy(c, st, &per_sm));

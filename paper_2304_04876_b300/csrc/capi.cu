@@ -217,7 +217,7 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
   S.device_bytes = static_cast<int64_t>(c->bytes);
   S.n_problems = P.nprob;
   S.local_stages = c->node_stages > 0 ? c->node_stages : c->step_depth > 0 ? c->step_depth : c->rec_stages;
-  S.local_threads = c->jac_mode > 0 ? c->jac_threads : c->node_stages > 0 ? kNodeThreads
+  S.local_threads = c->jac_mode > 0 ? c->jac_threads : c->node_stages > 0 ? c->node_threads
                   : c->step_depth > 0 ? kStepRows : c->rec_stages > 0 ? c->rec_consumers : c->tri_threads;
   S.local_kernel = c->mf ? 1 : o.local_solver == GDSW_LOCAL_EXACT ? 0 : c->jac_mode > 0 ? 5
                  : c->node_stages > 0 ? 7 : c->step_depth > 0 ? 6 : c->rec_stages > 0 ? (c->rec_sf ? 4 : 3) : 2;

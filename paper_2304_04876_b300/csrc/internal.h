@@ -309,7 +309,7 @@ struct KrylovScalars {
 constexpr int kNumSMsForCtx = 148;
 constexpr int kStepRows = 128;       // rows per step of a row program (= its kernel's threads)
 constexpr int kNodePieceBytes = 48 * 1024;   // largest piece of a node program
-constexpr int kNodeThreads = 512;            // threads of the node-program kernel (8 per node)
+constexpr int kNodeThreads = 512;            // default threads of the node-program kernel (8 per node)
 
 // Per-problem PCG state of a batched handle.  `start` makes the next
 // iteration the PCG prologue for this problem (step lengths 0: r stays, z = M r,
@@ -420,6 +420,7 @@ struct Ctx {
   int4* node_piece = nullptr;        // {offset / 16, bytes, 0, 0}
   int node_slot_bytes = 0;           // largest piece
   int node_stages = 0;               // ring slots; 0: kernel not used
+  int node_threads = 512;            // threads of the node-program kernel (256 or 512)
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int rec_max_rows = 0;              // most rows in one level
   int rec_consumers = 256;           // consumer threads of the pipelined solve

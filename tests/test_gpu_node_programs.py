@@ -1,7 +1,7 @@
 """The level-scheduled local solve from node programs (Sec. V-B2 substitution with the
 ILU(0) factors of Sec. V-B3 on elasticity, three unknowns per node; eight threads
 per node sum the couplings of the node's three rows to other nodes at once, then one
-thread solves the three rows in order): forced by shape, it stays within the FP32
+thread solves the three rows in order; 256 or 512 threads): forced by shape, it stays within the FP32
 tolerance of the oracle and of the record-streaming kernel, with pieces split inside
 a level as well as whole, solves GMRES with the oracle's iteration count, is not
 used outside its scope, and its bounded wait for a withheld piece reports a
@@ -61,11 +61,12 @@ def test_node_programs_match_oracle_and_record_kernel(name, make, opts, split):
     env = {"GDSW_LOCAL_SHAPE": "3,512,3"}
     if split:
         env["GDSW_NODE_PIECE_BYTES"] = "1024"     # a few nodes per piece
-    for stages in (2, 3, 4):
-        env["GDSW_LOCAL_SHAPE"] = f"{stages},512,3"
+    for stages, nt in ((2, 512), (3, 512), (4, 512), (3, 256)):
+        env["GDSW_LOCAL_SHAPE"] = f"{stages},{nt},3"
         h = handle_env(prob, env, precision="fp32", **hopts)
         st = h.stats()
         assert st["local_kernel"] == 7 and st["local_stages"] == stages, (name, stages, st["local_kernel"])
+        assert st["local_threads"] == nt
         for r, z0 in zip(rs, base):
             z = gpu_apply(h, r)
             assert relerr(z, M.apply(r)) <= 2e-5, (name, stages)
@@ -110,7 +111,7 @@ def test_node_programs_gmres_matches_oracle():
 
 def test_node_programs_wait_that_runs_out_reports_timeout(monkeypatch):
     """GDSW_TEST_STALL=1 withholds the first piece of CTA 0: every thread's bounded
-    wait for it runs out (about 10 ms), thread 0 lets the copies it issued land, the
+    wait for it runs out (about 10 ms), the issuing thread lets its other copies land, the
     kernel returns without writing z, the host reports GDSW_ERR_TIMEOUT, and a handle
     without the stall then computes normally on the same context."""
     from paper_2304_04876_b300 import gdsw as G
