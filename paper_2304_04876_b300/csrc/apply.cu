@@ -642,30 +642,85 @@ __global__ void __launch_bounds__(kStepRows, 4) k_local_steps(const double* __re
 
 // ---- level-scheduled solve from node programs (three unknowns per node) ----
 //
-// One CTA of NT threads per subdomain; eight lanes per node.  The
+// One CTA of NT threads per subdomain; LPN lanes (2, 4 or 8) per node.  The
 // pieces of the subdomain's node program (see the setup's node programs) come
-// by bulk copies, issued by one thread, into a ring of S slots (an mbarrier
-// per slot completing on the bytes, waits bounded), S pieces ahead.  Per node:
-// each lane sums its share of the node's off-node columns for the three rows
-// at once (z at a column is read once for all three), the eight lanes' partial
+// by bulk copies, issued by one thread, into a ring of S (at most kNodeSlots)
+// slots (an mbarrier per slot completing on the bytes, waits bounded), S
+// pieces ahead.  Per node: each lane sums a contiguous run of K / LPN of the
+// node's off-node columns for the three rows at once (z at a column is read
+// once for all three; columns and values by vector loads), the lanes' partial
 // sums meet in a shuffle tree, and the node's first lane solves the three rows
-// in order with the in-node coefficients; one barrier per piece, after which
-// the issuing thread refills the slot.  A wait that runs out sets the failure
-// flag; the threads leave together at the next barrier, the issuing thread
-// lets its copies land, and z_s is not written.
-template <int S, int NT>
+// in order with the in-node coefficients; warps without a node in the level
+// go straight to the barrier that ends the piece, after which the issuing
+// thread refills the slot.  A wait that runs out sets the failure flag; the
+// threads leave together at the next barrier, the issuing thread lets its
+// copies land, and z_s is not written.
+constexpr int kNodeSlots = 4;
+
+template <int VW>
+struct NodeVec;
+template <>
+struct NodeVec<1> {
+  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int T, const float* v, float& s0,
+                              float& s1, float& s2) {
+#pragma unroll 4
+    for (int j = 0; j < T; ++j) {
+      const float x = v[cn[j]];
+      s0 = fmaf(vn[j], x, s0);
+      s1 = fmaf(vn[K + j], x, s1);
+      s2 = fmaf(vn[2 * K + j], x, s2);
+    }
+  }
+};
+template <>
+struct NodeVec<2> {
+  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int T, const float* v, float& s0,
+                              float& s1, float& s2) {
+#pragma unroll 2
+    for (int j = 0; j < T; j += 2) {
+      const uint32_t c = *reinterpret_cast<const uint32_t*>(cn + j);
+      const float x0 = v[c & 0xffffu], x1 = v[c >> 16];
+      const float2 a = *reinterpret_cast<const float2*>(vn + j);
+      const float2 b = *reinterpret_cast<const float2*>(vn + K + j);
+      const float2 d = *reinterpret_cast<const float2*>(vn + 2 * K + j);
+      s0 = fmaf(a.y, x1, fmaf(a.x, x0, s0));
+      s1 = fmaf(b.y, x1, fmaf(b.x, x0, s1));
+      s2 = fmaf(d.y, x1, fmaf(d.x, x0, s2));
+    }
+  }
+};
+template <>
+struct NodeVec<4> {
+  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int T, const float* v, float& s0,
+                              float& s1, float& s2) {
+    for (int j = 0; j < T; j += 4) {
+      const uint2 c = *reinterpret_cast<const uint2*>(cn + j);
+      const float x0 = v[c.x & 0xffffu], x1 = v[c.x >> 16], x2 = v[c.y & 0xffffu], x3 = v[c.y >> 16];
+      const float4 a = *reinterpret_cast<const float4*>(vn + j);
+      const float4 b = *reinterpret_cast<const float4*>(vn + K + j);
+      const float4 d = *reinterpret_cast<const float4*>(vn + 2 * K + j);
+      s0 = fmaf(a.w, x3, fmaf(a.z, x2, fmaf(a.y, x1, fmaf(a.x, x0, s0))));
+      s1 = fmaf(b.w, x3, fmaf(b.z, x2, fmaf(b.y, x1, fmaf(b.x, x0, s1))));
+      s2 = fmaf(d.w, x3, fmaf(d.z, x2, fmaf(d.y, x1, fmaf(d.x, x0, s2))));
+    }
+  }
+};
+
+template <int NT, int LPN>
 __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict__ r,
-                                                                const int* __restrict__ om_ptr,
-                                                                const int* __restrict__ om_dofs,
-                                                                const int* __restrict__ node_ptr,
-                                                                const int4* __restrict__ pieces,
-                                                                const uint8_t* __restrict__ stream,
-                                                                int slot_bytes, float* __restrict__ zloc,
-                                                                const KrylovScalars* __restrict__ ks, int* err,
-                                                                long long wait_cycles, int stall_test,
-                                                                BatchGate gate) {
+                                                       const int* __restrict__ om_ptr,
+                                                       const int* __restrict__ om_dofs,
+                                                       const int* __restrict__ node_ptr,
+                                                       const int4* __restrict__ pieces,
+                                                       const uint8_t* __restrict__ stream, int S,
+                                                       int slot_bytes, float* __restrict__ zloc,
+                                                       const KrylovScalars* __restrict__ ks, int* err,
+                                                       long long wait_cycles, int stall_test, BatchGate gate) {
+  static_assert(LPN == 2 || LPN == 4 || LPN == 8, "2, 4 or 8 lanes per node");
+  // K is a multiple of 8, so K / LPN is a multiple of 8 / LPN: vector width
+  constexpr int VW = 8 / LPN;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[S];
+  __shared__ __align__(8) uint64_t full[kNodeSlots];
   __shared__ __align__(8) uint64_t gbar;
   __shared__ int s_fail;
   if (ks != nullptr && ks->done) return;
@@ -679,8 +734,10 @@ __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict_
   const int cnt = m > 0 ? (off + m + 3) & ~3 : 0;
   const int* idx = reinterpret_cast<const int*>(vreg) + off;
   float* v = reinterpret_cast<float*>(vreg) + off;
-  const int t = threadIdx.x, lane8 = t & 7, group = t >> 3;
-  constexpr int NG = NT / 8;
+  const int t = threadIdx.x, lane = t % LPN, group = t / LPN;
+  constexpr int NG = NT / LPN;
+  constexpr int kWarpGroups = 32 / LPN;
+  const int warp_first = (t >> 5) * kWarpGroups;
   const bool withhold = stall_test && s == 0;
   // the copies are issued by the last thread, whose warp has nodes only in
   // the widest levels; it holds the table entry of the next piece in a
@@ -720,24 +777,27 @@ __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict_
   if (!failed) gather_staged(r, idx, v, m, NT);
   __syncthreads();
   int waited = -1;                           // last piece whose copy this thread saw land
-  int i = 0;
+  int i = 0, slot = 0;
+  unsigned phase = 0;
   for (; i < np && !failed; ++i) {
-    if (!mbar_wait_bounded(&full[i % S], (i / S) & 1, wait_cycles)) {
+    if (!mbar_wait_bounded(&full[slot], phase, wait_cycles)) {
       s_fail = 1;
     } else {
       waited = i;
-      const unsigned char* pc = ring + size_t(i % S) * slot_bytes;
+      const unsigned char* pc = ring + size_t(slot) * slot_bytes;
       const int4 hdr = *reinterpret_cast<const int4*>(pc);
-      const int N = hdr.x & 0xffff, K = hdr.y;
+      const int N = hdr.x & 0xffff, K = hdr.y, T = K / LPN;
       const bool upper = (hdr.x >> 16) != 0;    // U sweep: the node's rows solved last to first
       const uint16_t* nodes = reinterpret_cast<const uint16_t*>(pc + 16);
       const float4* coef = reinterpret_cast<const float4*>(pc + 16 + ((2 * N + 15) & ~15));
       const uint16_t* cols = reinterpret_cast<const uint16_t*>(pc + hdr.z);
       const float* vals = reinterpret_cast<const float*>(pc + hdr.w);
-      for (int round = 0; round < N; round += NG) {
+      // rounds of NG nodes; a warp whose first node is past the level's end
+      // has none in this round or later ones (warp-uniform exit)
+      for (int round = 0; round + warp_first < N; round += NG) {
         const int n = round + group;
         const bool valid = n < N;
-        const bool solver = valid && lane8 == 0;
+        const bool solver = valid && lane == 0;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         // the solving lane's operands (its own rows: no other node writes them
         // in this level), loaded before the sums so their latency overlaps
@@ -756,22 +816,14 @@ __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict_
           vb = v[rb];
           vc = v[rc];
         }
-        if (valid) {
-          const uint16_t* cn = cols + size_t(n) * K;
-          const float* vn = vals + size_t(n) * 3 * K;
-#pragma unroll 4
-          for (int k = lane8; k < K; k += 8) {
-            const float x = v[cn[k]];
-            s0 = fmaf(vn[k], x, s0);
-            s1 = fmaf(vn[K + k], x, s1);
-            s2 = fmaf(vn[2 * K + k], x, s2);
-          }
-        }
+        if (valid)
+          NodeVec<VW>::sums(cols + size_t(n) * K + lane * T, vals + size_t(n) * 3 * K + lane * T, K, T, v, s0,
+                            s1, s2);
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-          s0 += __shfl_xor_sync(0xffffffffu, s0, o, 8);
-          s1 += __shfl_xor_sync(0xffffffffu, s1, o, 8);
-          s2 += __shfl_xor_sync(0xffffffffu, s2, o, 8);
+        for (int o = LPN / 2; o > 0; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPN);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o, LPN);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, o, LPN);
         }
         if (solver) {
           // coefficients: d = {1/d0, 1/d1, 1/d2, c10}, cc = {c20, c21, -, -}
@@ -790,6 +842,10 @@ __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict_
       const int lim = min(np, i + 1 + S);
       if (issued < lim) fence_proxy_async_smem();
       for (; issued < lim; ++issued) issue(issued);
+    }
+    if (++slot == S) {
+      slot = 0;
+      phase ^= 1u;
     }
   }
   if (failed) {
@@ -1826,22 +1882,18 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
     // node programs (FP32, three unknowns per node)
     if constexpr (std::is_same<T, float>::value) {
       const size_t shm = nodes_smem_bytes(c->node_stages, c->node_slot_bytes, c->max_m);
-#define GDSW_NODES_LAUNCH(SS, TT)                                                                          \
-  k_local_nodes<SS, TT><<<c->nsub, TT, shm, s>>>(r, c->om_ptr, c->om_dofs, c->node_ptr, c->node_piece,       \
-                                                c->node_stream, c->node_slot_bytes, zl, ks, c->derr,         \
-                                                c->wait_cycles, c->stall_test, gate)
-      if (c->node_threads == 256) {
-        switch (c->node_stages) {
-          case 2: GDSW_NODES_LAUNCH(2, 256); break;
-          case 4: GDSW_NODES_LAUNCH(4, 256); break;
-          default: GDSW_NODES_LAUNCH(3, 256); break;
-        }
-      } else {
-        switch (c->node_stages) {
-          case 2: GDSW_NODES_LAUNCH(2, 512); break;
-          case 4: GDSW_NODES_LAUNCH(4, 512); break;
-          default: GDSW_NODES_LAUNCH(3, 512); break;
-        }
+#define GDSW_NODES_LAUNCH(TT, LL)                                                                           \
+  k_local_nodes<TT, LL><<<c->nsub, TT, shm, s>>>(r, c->om_ptr, c->om_dofs, c->node_ptr, c->node_piece,        \
+                                                c->node_stream, c->node_stages, c->node_slot_bytes, zl, ks,   \
+                                                c->derr, c->wait_cycles, c->stall_test, gate)
+      const int sel = (c->node_threads == 256 ? 0 : 3) + (c->node_lanes == 2 ? 0 : c->node_lanes == 4 ? 1 : 2);
+      switch (sel) {
+        case 0: GDSW_NODES_LAUNCH(256, 2); break;
+        case 1: GDSW_NODES_LAUNCH(256, 4); break;
+        case 2: GDSW_NODES_LAUNCH(256, 8); break;
+        case 3: GDSW_NODES_LAUNCH(512, 2); break;
+        case 4: GDSW_NODES_LAUNCH(512, 4); break;
+        default: GDSW_NODES_LAUNCH(512, 8); break;
       }
 #undef GDSW_NODES_LAUNCH
     }
@@ -2109,30 +2161,26 @@ gdsw_status steps_occupancy(Ctx* c, int D, int* per_sm) {
   return GDSW_OK;
 }
 
-// Resident CTAs per SM of the node-program solve with S ring slots and NT
-// threads (raises
+// Resident CTAs per SM of the node-program solve with S ring slots, NT
+// threads and LPN lanes per node (raises
 // its dynamic shared memory limit first; 0 when it does not fit).
-gdsw_status nodes_occupancy(Ctx* c, int S, int NT, int* per_sm) {
+gdsw_status nodes_occupancy(Ctx* c, int S, int NT, int LPN, int* per_sm) {
   const size_t shm = nodes_smem_bytes(S, c->node_slot_bytes, c->max_m);
   *per_sm = 0;
-  if (shm > size_t(max_block_smem_optin())) return GDSW_OK;
-#define GDSW_NODES_OCC(SS, TT)                                                                \
+  if (S < 2 || S > kNodeSlots || shm > size_t(max_block_smem_optin())) return GDSW_OK;
+#define GDSW_NODES_OCC(TT, LL)                                                                \
   do {                                                                                        \
-    GDSW_CK(allow_max_dynamic_smem(k_local_nodes<SS, TT>));                                   \
-    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<SS, TT>, TT, shm)); \
+    GDSW_CK(allow_max_dynamic_smem(k_local_nodes<TT, LL>));                                   \
+    GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_nodes<TT, LL>, TT, shm)); \
   } while (0)
-  if (NT == 256) {
-    switch (S) {
-      case 2: GDSW_NODES_OCC(2, 256); break;
-      case 4: GDSW_NODES_OCC(4, 256); break;
-      default: GDSW_NODES_OCC(3, 256); break;
-    }
-  } else {
-    switch (S) {
-      case 2: GDSW_NODES_OCC(2, 512); break;
-      case 4: GDSW_NODES_OCC(4, 512); break;
-      default: GDSW_NODES_OCC(3, 512); break;
-    }
+  const int sel = (NT == 256 ? 0 : 3) + (LPN == 2 ? 0 : LPN == 4 ? 1 : 2);
+  switch (sel) {
+    case 0: GDSW_NODES_OCC(256, 2); break;
+    case 1: GDSW_NODES_OCC(256, 4); break;
+    case 2: GDSW_NODES_OCC(256, 8); break;
+    case 3: GDSW_NODES_OCC(512, 2); break;
+    case 4: GDSW_NODES_OCC(512, 4); break;
+    default: GDSW_NODES_OCC(512, 8); break;
   }
 #undef GDSW_NODES_OCC
   return GDSW_OK;
@@ -2214,16 +2262,18 @@ gdsw_status tune_local(Ctx* c) {
     c->step_depth = 0;
   }
   // the node-program kernel with 2 to 4 ring slots
-  int best_nodes = 0, best_node_nt = kNodeThreads;
+  int best_nodes = 0, best_node_nt = kNodeThreads, best_node_lanes = 4;
   if (c->node_stream != nullptr && c->fp32 && !c->fp16) {
-    for (int S : {2, 3, 4})
-    for (int NT : {256, 512}) {
+    for (int S : {2, 4})
+    for (int NT : {256, 512})
+    for (int LPN : {2, 4, 8}) {
       if (st != GDSW_OK) break;
       int per_sm = 0;
-      st = nodes_occupancy(c, S, NT, &per_sm);
+      st = nodes_occupancy(c, S, NT, LPN, &per_sm);
       if (st != GDSW_OK || per_sm == 0) continue;
       c->node_stages = S;
       c->node_threads = NT;
+      c->node_lanes = LPN;
       st = launch_local<float>(c, r, s, nullptr, BatchGate{});
       cudaEventRecord(e0, s);
       for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep) st = launch_local<float>(c, r, s, nullptr, BatchGate{});
@@ -2232,7 +2282,7 @@ gdsw_status tune_local(Ctx* c) {
       float ms = 0.f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       if (e != cudaSuccess) { fail(e); break; }
-      if (ms < best) { best = ms; best_nodes = S; best_node_nt = NT; best_depth = 0; }
+      if (ms < best) { best = ms; best_nodes = S; best_node_nt = NT; best_node_lanes = LPN; best_depth = 0; }
     }
     c->node_stages = 0;
   }
@@ -2257,6 +2307,7 @@ gdsw_status tune_local(Ctx* c) {
   c->step_depth = best_depth;
   c->node_stages = best_nodes;
   c->node_threads = best_node_nt;
+  c->node_lanes = best_node_lanes;
   c->rec_stages = best_s;
   c->rec_consumers = best_nt;
   c->rec_sf = best_s > 0 && best_sf;
@@ -2430,21 +2481,23 @@ gdsw_status apply_configure(Ctx* c) {
   // timing it (for profilers, under which the timings mean nothing, and for
   // the failure tests); kind 1 selects the solve without a barrier per level,
   // kind 2 the row programs with `stages` steps in flight per thread, kind 3
-  // the node programs with `stages` ring slots and 256 or 512 threads
+  // the node programs with `stages` ring slots, 256 or 512 threads and a
+  // fourth field of 2, 4 (default) or 8 lanes per node
   const char* shape = getenv("GDSW_LOCAL_SHAPE");
   if (c->rec_stages > 0 && shape != nullptr) {
-    int st = 0, nt = 0, sf = 0;
-    const int got = sscanf(shape, "%d,%d,%d", &st, &nt, &sf);
-    if (got == 3 && sf == 3 && c->node_stream != nullptr && (st == 2 || st == 3 || st == 4) &&
-        (nt == 256 || nt == 512)) {
+    int st = 0, nt = 0, sf = 0, lanes = 4;
+    const int got = sscanf(shape, "%d,%d,%d,%d", &st, &nt, &sf, &lanes);
+    if (got >= 3 && sf == 3 && c->node_stream != nullptr && st >= 2 && st <= kNodeSlots &&
+        (nt == 256 || nt == 512) && (lanes == 2 || lanes == 4 || lanes == 8)) {
       int per_sm = 0;
-      GDSW_TRY(nodes_occupancy(c, st, nt, &per_sm));
+      GDSW_TRY(nodes_occupancy(c, st, nt, lanes, &per_sm));
       if (per_sm == 0) {
         set_error("GDSW_LOCAL_SHAPE=%s does not fit the shared memory", shape);
         return GDSW_ERR_UNSUPPORTED;
       }
       c->node_stages = st;
       c->node_threads = nt;
+      c->node_lanes = lanes;
     } else if (got == 3 && sf == 2 && c->steps != nullptr && c->fp32 && !c->fp16 && (st == 4 || st == 8 || st == 12)) {
       int per_sm = 0;
       GDSW_TRY(steps_occupancy(c, st, &per_sm));
@@ -2453,7 +2506,7 @@ gdsw_status apply_configure(Ctx* c) {
         return GDSW_ERR_UNSUPPORTED;
       }
       c->step_depth = st;
-    } else if (got >= 2 && (st == 0 || st == 2 || st == 4 || st == 8 || st == 16) &&
+    } else if (got >= 2 && got <= 3 && (st == 0 || st == 2 || st == 4 || st == 8 || st == 16) &&
         (nt == 64 || nt == 128 || nt == 256 || nt == 512 || nt == 1024)) {
       c->rec_stages = st;
       if (st > 0) c->rec_consumers = nt == 1024 ? 512 : nt; else c->tri_threads = nt;

@@ -309,7 +309,7 @@ struct KrylovScalars {
 constexpr int kNumSMsForCtx = 148;
 constexpr int kStepRows = 128;       // rows per step of a row program (= its kernel's threads)
 constexpr int kNodePieceBytes = 48 * 1024;   // largest piece of a node program
-constexpr int kNodeThreads = 512;            // default threads of the node-program kernel (8 per node)
+constexpr int kNodeThreads = 512;            // default threads of the node-program kernel
 
 // Per-problem PCG state of a batched handle.  `start` makes the next
 // iteration the PCG prologue for this problem (step lengths 0: r stays, z = M r,
@@ -421,6 +421,7 @@ struct Ctx {
   int node_slot_bytes = 0;           // largest piece
   int node_stages = 0;               // ring slots; 0: kernel not used
   int node_threads = 512;            // threads of the node-program kernel (256 or 512)
+  int node_lanes = 4;                // lanes per node of the node-program kernel (2, 4 or 8)
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int rec_max_rows = 0;              // most rows in one level
   int rec_consumers = 256;           // consumer threads of the pipelined solve

@@ -1112,8 +1112,9 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
     // kNodePieceBytes hold for each node: its index, its three inverse
     // diagonals and in-node coefficients by solve step (float[8]: d0, d1, d2,
     // c10, c20, c21), the union of its rows' off-node columns (uint16, K per
-    // node, the level's widest) and the three rows' values over that union
-    // (float[3][K], zero where a row lacks the column).  Section layout: int4
+    // node: the level's widest, rounded up to a multiple of 8, padded with the
+    // node's first row) and the three rows' values over that union
+    // (float[3][K], zero where a row lacks the column or on padding).  Section layout: int4
     // {nodes | U sweep << 16, K, columns offset, values offset} | uint16 node[N] | float[N][8] |
     // uint16[N][K] | float[N][3][K], each 16-byte aligned.  Values are placed
     // on the device (k_fill_records) from the factor; ELL padding goes to a

@@ -1,7 +1,7 @@
 """The level-scheduled local solve from node programs (Sec. V-B2 substitution with the
-ILU(0) factors of Sec. V-B3 on elasticity, three unknowns per node; eight threads
+ILU(0) factors of Sec. V-B3 on elasticity, three unknowns per node; 2, 4 or 8 lanes
 per node sum the couplings of the node's three rows to other nodes at once, then one
-thread solves the three rows in order; 256 or 512 threads): forced by shape, it stays within the FP32
+lane solves the three rows in order; 256 or 512 threads): forced by shape, it stays within the FP32
 tolerance of the oracle and of the record-streaming kernel, with pieces split inside
 a level as well as whole, solves GMRES with the oracle's iteration count, is not
 used outside its scope, and its bounded wait for a withheld piece reports a
@@ -61,8 +61,8 @@ def test_node_programs_match_oracle_and_record_kernel(name, make, opts, split):
     env = {"GDSW_LOCAL_SHAPE": "3,512,3"}
     if split:
         env["GDSW_NODE_PIECE_BYTES"] = "1024"     # a few nodes per piece
-    for stages, nt in ((2, 512), (3, 512), (4, 512), (3, 256)):
-        env["GDSW_LOCAL_SHAPE"] = f"{stages},{nt},3"
+    for stages, nt, lanes in ((2, 512, 4), (3, 512, 8), (4, 256, 2), (4, 512, 4), (2, 256, 8)):
+        env["GDSW_LOCAL_SHAPE"] = f"{stages},{nt},3,{lanes}"
         h = handle_env(prob, env, precision="fp32", **hopts)
         st = h.stats()
         assert st["local_kernel"] == 7 and st["local_stages"] == stages, (name, stages, st["local_kernel"])
