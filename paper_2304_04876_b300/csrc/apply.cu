@@ -646,25 +646,29 @@ __global__ void __launch_bounds__(kStepRows, 4) k_local_steps(const double* __re
 // pieces of the subdomain's node program (see the setup's node programs) come
 // by bulk copies, issued by one thread, into a ring of S (at most kNodeSlots)
 // slots (an mbarrier per slot completing on the bytes, waits bounded), S
-// pieces ahead.  Per node: each lane sums a contiguous run of K / LPN of the
-// node's off-node columns for the three rows at once (z at a column is read
-// once for all three; columns and values by vector loads), the lanes' partial
+// pieces ahead.  Per node: each lane sums VW = 8 / LPN consecutive columns of
+// every chunk of eight of the node's off-node columns, for the three rows at
+// once (z at a column is read once for all three; columns and values by
+// vector loads, a node's lanes reading each chunk contiguously), the lanes' partial
 // sums meet in a shuffle tree, and the node's first lane solves the three rows
 // in order with the in-node coefficients; warps without a node in the level
 // go straight to the barrier that ends the piece, after which the issuing
 // thread refills the slot.  A wait that runs out sets the failure flag; the
 // threads leave together at the next barrier, the issuing thread lets its
 // copies land, and z_s is not written.
-constexpr int kNodeSlots = 4;
+constexpr int kNodeSlots = 6;
 
+// The lane's share of a node's sums: chunks of eight columns, the lane taking
+// VW consecutive columns of each (lane * VW onward), so the LPN = 8 / VW lanes
+// of a node read each chunk's columns and values contiguously.
 template <int VW>
 struct NodeVec;
 template <>
 struct NodeVec<1> {
-  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int T, const float* v, float& s0,
+  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int j0, const float* v, float& s0,
                               float& s1, float& s2) {
 #pragma unroll 4
-    for (int j = 0; j < T; ++j) {
+    for (int j = j0; j < K; j += 8) {
       const float x = v[cn[j]];
       s0 = fmaf(vn[j], x, s0);
       s1 = fmaf(vn[K + j], x, s1);
@@ -674,10 +678,10 @@ struct NodeVec<1> {
 };
 template <>
 struct NodeVec<2> {
-  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int T, const float* v, float& s0,
+  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int j0, const float* v, float& s0,
                               float& s1, float& s2) {
 #pragma unroll 2
-    for (int j = 0; j < T; j += 2) {
+    for (int j = j0; j < K; j += 8) {
       const uint32_t c = *reinterpret_cast<const uint32_t*>(cn + j);
       const float x0 = v[c & 0xffffu], x1 = v[c >> 16];
       const float2 a = *reinterpret_cast<const float2*>(vn + j);
@@ -691,9 +695,9 @@ struct NodeVec<2> {
 };
 template <>
 struct NodeVec<4> {
-  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int T, const float* v, float& s0,
+  __device__ static void sums(const uint16_t* cn, const float* vn, int K, int j0, const float* v, float& s0,
                               float& s1, float& s2) {
-    for (int j = 0; j < T; j += 4) {
+    for (int j = j0; j < K; j += 8) {
       const uint2 c = *reinterpret_cast<const uint2*>(cn + j);
       const float x0 = v[c.x & 0xffffu], x1 = v[c.x >> 16], x2 = v[c.y & 0xffffu], x3 = v[c.y >> 16];
       const float4 a = *reinterpret_cast<const float4*>(vn + j);
@@ -717,7 +721,8 @@ __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict_
                                                        const KrylovScalars* __restrict__ ks, int* err,
                                                        long long wait_cycles, int stall_test, BatchGate gate) {
   static_assert(LPN == 2 || LPN == 4 || LPN == 8, "2, 4 or 8 lanes per node");
-  // K is a multiple of 8, so K / LPN is a multiple of 8 / LPN: vector width
+  // K is a multiple of 8: a node's LPN lanes take VW = 8 / LPN columns of
+  // each chunk of eight
   constexpr int VW = 8 / LPN;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kNodeSlots];
@@ -786,7 +791,7 @@ __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict_
       waited = i;
       const unsigned char* pc = ring + size_t(slot) * slot_bytes;
       const int4 hdr = *reinterpret_cast<const int4*>(pc);
-      const int N = hdr.x & 0xffff, K = hdr.y, T = K / LPN;
+      const int N = hdr.x & 0xffff, K = hdr.y;
       const bool upper = (hdr.x >> 16) != 0;    // U sweep: the node's rows solved last to first
       const uint16_t* nodes = reinterpret_cast<const uint16_t*>(pc + 16);
       const float4* coef = reinterpret_cast<const float4*>(pc + 16 + ((2 * N + 15) & ~15));
@@ -816,9 +821,7 @@ __global__ void __launch_bounds__(NT, 1) k_local_nodes(const double* __restrict_
           vb = v[rb];
           vc = v[rc];
         }
-        if (valid)
-          NodeVec<VW>::sums(cols + size_t(n) * K + lane * T, vals + size_t(n) * 3 * K + lane * T, K, T, v, s0,
-                            s1, s2);
+        if (valid) NodeVec<VW>::sums(cols + size_t(n) * K, vals + size_t(n) * 3 * K, K, lane * VW, v, s0, s1, s2);
 #pragma unroll
         for (int o = LPN / 2; o > 0; o >>= 1) {
           s0 += __shfl_xor_sync(0xffffffffu, s0, o, LPN);
@@ -2264,7 +2267,7 @@ gdsw_status tune_local(Ctx* c) {
   // the node-program kernel with 2 to 4 ring slots
   int best_nodes = 0, best_node_nt = kNodeThreads, best_node_lanes = 4;
   if (c->node_stream != nullptr && c->fp32 && !c->fp16) {
-    for (int S : {2, 4})
+    for (int S : {2, 4, 6})
     for (int NT : {256, 512})
     for (int LPN : {2, 4, 8}) {
       if (st != GDSW_OK) break;

@@ -102,8 +102,8 @@ bool plan_node_pieces(const Plan& P, size_t cap, std::vector<NodePiece>* pieces,
           std::sort(u.begin(), u.end());
           K = std::max<int>(K, static_cast<int>(std::unique(u.begin(), u.end()) - u.begin()));
         }
-        // padded to a multiple of 8: with 2, 4 or 8 lanes per node each lane
-        // takes a contiguous run of K / lanes columns (vector loads)
+        // padded to a multiple of 8: chunks of eight columns, of which each of
+        // a node's 2, 4 or 8 lanes takes 4, 2 or 1 (vector loads)
         K = (std::max(K, 1) + 7) & ~7;
         // node index, float[8] coefficients, K columns and 3K values per node
         const size_t per_node = 34 + 14 * size_t(K);

@@ -61,7 +61,7 @@ def test_node_programs_match_oracle_and_record_kernel(name, make, opts, split):
     env = {"GDSW_LOCAL_SHAPE": "3,512,3"}
     if split:
         env["GDSW_NODE_PIECE_BYTES"] = "1024"     # a few nodes per piece
-    for stages, nt, lanes in ((2, 512, 4), (3, 512, 8), (4, 256, 2), (4, 512, 4), (2, 256, 8)):
+    for stages, nt, lanes in ((2, 512, 4), (3, 512, 8), (4, 256, 2), (6, 256, 4), (2, 256, 8)):
         env["GDSW_LOCAL_SHAPE"] = f"{stages},{nt},3,{lanes}"
         h = handle_env(prob, env, precision="fp32", **hopts)
         st = h.stats()
