@@ -660,38 +660,6 @@ __global__ void __launch_bounds__(kThreads) k_dc_update(int n, int k, int m, dou
   }
 }
 
-// Partial sums of (V_i, w) for the k basis vectors and of (w, w) (slot k), in
-// one pass over w: the single global reduction of an Arnoldi step.  Columns
-// go 8 at a time.  Gated on the stop flag and, for the second pass, on mode 2.
-__global__ void __launch_bounds__(kThreads) k_gs_dots(int n, int k, const double* __restrict__ V,
-                                                      const double* __restrict__ w,
-                                                      double* __restrict__ red,
-                                                      const KrylovScalars* __restrict__ ks, int need_mode) {
-  __shared__ double sh[32];
-  if (ks->done || (need_mode != 0 && ks->gm_mode != need_mode)) return;
-  for (int c0 = 0; c0 <= k; c0 += 8) {
-    double acc[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int col = c0 + u;
-        if (col < k) acc[u] = fma(V[int64_t(col) * n + i], wi, acc[u]);
-        else if (col == k) acc[u] = fma(wi, wi, acc[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (c0 + u <= k) {
-        const double t = block_sum(acc[u], sh);
-        if (threadIdx.x == 0) red[int64_t(c0 + u) * gridDim.x + blockIdx.x] = t;
-      }
-    }
-  }
-}
-
 // h[j] = the sum of the partials of dot j (one CTA per dot, fixed order).
 __global__ void k_gs_reduce(int parts, const double* __restrict__ red, double* __restrict__ h,
                             const KrylovScalars* __restrict__ ks, int need_mode) {
@@ -701,58 +669,118 @@ __global__ void k_gs_reduce(int parts, const double* __restrict__ red, double* _
   if (threadIdx.x == 0) h[blockIdx.x] = v;
 }
 
-// After the first pass: ||w - V h||^2 = (w, w) - ||h||^2 when V is
-// orthonormal.  If that keeps less than `keep` of (w, w) the subtraction
-// cancels too much for the formula, and a second pass (mode 2) follows;
-// keep > 1 asks for the second pass at every step (CGS2).
-__global__ void k_gs_norm1(int k, const double* __restrict__ h1, double* __restrict__ beta,
-                           KrylovScalars* ks, double keep) {
-  if (threadIdx.x != 0 || ks->done) return;
-  double sq = 0.0;
-  for (int i = 0; i < k; ++i) sq = fma(h1[i], h1[i], sq);
-  const double ww = h1[k], b2 = ww - sq;
-  if (b2 > keep * ww) {
-    ks->gm_mode = 1;
-    beta[0] = sqrt(b2);
-  } else {
-    ks->gm_mode = 2;
-    beta[0] = 0.0;
+// ---- classical Gram-Schmidt of an Arnoldi step (Sec. VII's GMRES) ----
+//
+// Three launches per step on a grid of a few CTAs per SM, each CTA a
+// grid-stride share of the rows (FP64: one DFMA per entry, the FP64 pipe and
+// the vector stream are the bounds):
+//   k_gs_pass1   h1 = [V, w]^T w; the last CTA (ticket) adds the partials in a
+//                fixed order and decides on the second pass (mode);
+//   k_gs_orth1   w -= V h1, then in mode 2 h2 = [V, w]^T w on the new w (the
+//                last CTA adds them), in mode 1 the scaling by 1 / beta and the
+//                Givens step (last CTA);
+//   k_gs_orth2   mode 2: w -= V h2, scaled by 1 / beta, and the Givens step.
+// Every kernel is gated on the stop flag; the mode is uniform over the grid.
+
+// Partial dots of this CTA's rows for columns c0 .. c0 + NC - 1 of [V_0 ..
+// V_{k-1}, x] with x (column k is (x, x)), into red[col * gridDim.x + CTA]:
+// per column a warp sum, then the warps' sums in warp order.
+template <int NC>
+__device__ __forceinline__ void gs_dots_group(int n, int k, int c0, const double* __restrict__ V,
+                                              const double* x, double* __restrict__ red, double (*sh)[8]) {
+  const double* col[NC];
+#pragma unroll
+  for (int u = 0; u < NC; ++u) col[u] = c0 + u < k ? V + int64_t(c0 + u) * n : x;
+  double acc[NC];
+#pragma unroll
+  for (int u = 0; u < NC; ++u) acc[u] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double xi = x[i];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) acc[u] = fma(col[u][i], xi, acc[u]);
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int u = 0; u < NC; ++u) {
+    const double t = warp_sum(acc[u]);
+    if (lane == 0) sh[wp][u] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < NC) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += sh[q][threadIdx.x];
+    red[int64_t(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// All k + 1 columns, eight at a time (the last group as wide as it needs).
+__device__ __forceinline__ void gs_dots(int n, int k, const double* __restrict__ V, const double* x,
+                                        double* __restrict__ red, double (*sh)[8]) {
+  for (int c0 = 0; c0 <= k; c0 += 8) {
+    switch (min(8, k + 1 - c0)) {
+      case 1: gs_dots_group<1>(n, k, c0, V, x, red, sh); break;
+      case 2: gs_dots_group<2>(n, k, c0, V, x, red, sh); break;
+      case 3: gs_dots_group<3>(n, k, c0, V, x, red, sh); break;
+      case 4: gs_dots_group<4>(n, k, c0, V, x, red, sh); break;
+      case 5: gs_dots_group<5>(n, k, c0, V, x, red, sh); break;
+      case 6: gs_dots_group<6>(n, k, c0, V, x, red, sh); break;
+      case 7: gs_dots_group<7>(n, k, c0, V, x, red, sh); break;
+      default: gs_dots_group<8>(n, k, c0, V, x, red, sh); break;
+    }
   }
 }
 
-__global__ void k_gs_norm2(int k, const double* __restrict__ h2, double* __restrict__ beta, KrylovScalars* ks) {
-  if (threadIdx.x != 0 || ks->done || ks->gm_mode != 2) return;
+// By the last CTA: h[c] = the CTAs' partials of column c added in CTA order
+// (one warp per column), c = 0 .. k; then ||h[0 .. k-1]||^2 by warp 0 (lane
+// 0 holds it).  Deterministic whichever CTA is last.
+__device__ __forceinline__ double gs_reduce_last(int k, const double* __restrict__ red, double* h) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = gridDim.x;
+  for (int cc = wp; cc <= k; cc += nw) {
+    double t = 0.0;
+    for (int q = lane; q < G; q += 32) t += __ldcg(red + int64_t(cc) * G + q);
+    t = warp_sum(t);
+    if (lane == 0) h[cc] = t;
+  }
+  __syncthreads();
   double sq = 0.0;
-  for (int i = 0; i < k; ++i) sq = fma(h2[i], h2[i], sq);
-  const double b2 = h2[k] - sq;
-  beta[1] = b2 > 0.0 ? sqrt(b2) : 0.0;
+  if (wp == 0) {
+    for (int i = lane; i < k; i += 32) {
+      const double hi = h[i];
+      sq = fma(hi, hi, sq);
+    }
+    sq = warp_sum(sq);
+  }
+  return sq;
 }
 
-// w -= V h (k columns); the pass that completes the orthogonalisation also
-// divides by beta (a zero beta, an exact breakdown, leaves w unscaled).
-__global__ void __launch_bounds__(kThreads) k_gs_orth(int n, int k, const double* __restrict__ V,
-                                                      const double* __restrict__ h,
-                                                      const double* __restrict__ beta, double* __restrict__ w,
-                                                      const KrylovScalars* __restrict__ ks, int pass) {
-  if (ks->done) return;
-  const int mode = ks->gm_mode;
-  if (pass == 2 && mode != 2) return;
-  const bool last = pass == 2 || mode == 1;
-  const double b = last ? beta[pass - 1] : 1.0;
-  const double inv = b > 0.0 ? 1.0 / b : 1.0;
+// w -= V h (k columns) over this CTA's rows; scaled by `inv` when `last`.
+__device__ __forceinline__ void gs_orth_rows(int n, int k, const double* __restrict__ V, const double* h,
+                                             double* w, bool last, double inv) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc = w[i];
-    for (int j = 0; j < k; ++j) acc = fma(-h[j], V[int64_t(j) * n + i], acc);
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      const double v0 = V[int64_t(j) * n + i], v1 = V[int64_t(j + 1) * n + i];
+      const double v2 = V[int64_t(j + 2) * n + i], v3 = V[int64_t(j + 3) * n + i];
+      acc = fma(-h[j], v0, acc);
+      acc = fma(-h[j + 1], v1, acc);
+      acc = fma(-h[j + 2], v2, acc);
+      acc = fma(-h[j + 3], v3, acc);
+    }
+    for (; j < k; ++j) acc = fma(-h[j], V[int64_t(j) * n + i], acc);
     w[i] = last ? acc * inv : acc;
   }
 }
 
-// Column j of the Hessenberg matrix (the Gram-Schmidt coefficients of both
-// passes and beta), the earlier rotations applied to it, the new rotation,
-// and the least-squares residual |g_{j+1}|, which ends the cycle (and the
-// solve) when it is at most tol ||b||, or at maxit, or on breakdown.
-__global__ void k_givens(int j, int m, double* __restrict__ gm, KrylovScalars* ks) {
-  if (threadIdx.x != 0 || ks->done) return;
+// Column j of the Hessenberg matrix (the coefficients of both passes and
+// beta), the earlier rotations applied to it, the new rotation, and the
+// least-squares residual |g_{j+1}|, which ends the cycle (and the solve) when
+// it is at most tol ||b||, or at maxit, or on breakdown.  Run by the whole
+// last CTA: the column and the rotations are staged in shared memory (stage:
+// 3m + 4 doubles), one thread rotates, all write the column back.
+__device__ void gs_givens(int j, int m, double* __restrict__ gm, KrylovScalars* ks, double* stage) {
   const GmLayout L(m);
   double* H = gm;
   double* cs = gm + L.cs();
@@ -760,30 +788,118 @@ __global__ void k_givens(int j, int m, double* __restrict__ gm, KrylovScalars* k
   double* g = gm + L.g();
   const double* h1 = gm + L.h1();
   const double* h2 = gm + L.h2();
+  __shared__ int ok;
   const bool two = ks->gm_mode == 2;
-  for (int i = 0; i <= j; ++i) H[i * m + j] = two ? h1[i] + h2[i] : h1[i];
-  const double hn = gm[L.beta() + (two ? 1 : 0)];
-  for (int i = 0; i < j; ++i) {
-    const double a = H[i * m + j], b = H[(i + 1) * m + j];
-    H[i * m + j] = cs[i] * a + sn[i] * b;
-    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+  double* col = stage;                 // j + 2
+  double* cj = stage + (j + 2);        // j
+  double* sj = cj + j;                 // j
+  for (int i = threadIdx.x; i <= j; i += blockDim.x)
+    col[i] = two ? __ldcg(h1 + i) + __ldcg(h2 + i) : __ldcg(h1 + i);
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cj[i] = __ldcg(cs + i);
+    sj[i] = __ldcg(sn + i);
   }
-  const double d = H[j * m + j];
-  const double den = hypot(d, hn);
-  if (den == 0.0) {                      // singular: stop, the host sees it as not converged
-    ks->bad = 1;
-    ks->done = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = __ldcg(gm + L.beta() + (two ? 1 : 0));
+    for (int i = 0; i < j; ++i) {
+      const double a = col[i], b = col[i + 1];
+      col[i] = cj[i] * a + sj[i] * b;
+      col[i + 1] = -sj[i] * a + cj[i] * b;
+    }
+    const double d = col[j];
+    const double den = hypot(d, hn);
+    ok = den != 0.0;
+    if (den == 0.0) {                    // singular: stop, the host sees it as not converged
+      ks->bad = 1;
+      ks->done = 1;
+    } else {
+      const double c = d / den, sv = hn / den;
+      cs[j] = c;
+      sn[j] = sv;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      const double gj = __ldcg(g + j);
+      g[j + 1] = -sv * gj;
+      g[j] = c * gj;
+      ks->iter += 1;
+      const double gn = -sv * gj;
+      if (!isfinite(gn)) ks->bad = 1;
+      if (!(gn * gn > ks->tol2) || ks->iter >= ks->maxit || hn == 0.0 || ks->bad) ks->done = 1;
+    }
+  }
+  __syncthreads();
+  if (ok)
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[int64_t(i) * m + j] = col[i];
+}
+
+// Pass 1: h1 = V^T w and (w, w) in slot k; the last CTA adds the partials and
+// chooses: ||w - V h1||^2 = (w, w) - ||h1||^2 when V is orthonormal; if that
+// keeps more than `keep` of (w, w) one pass suffices (mode 1, beta[0] from
+// the formula), else a second pass follows (mode 2).  keep > 1 asks for the
+// second pass at every step (CGS2).
+__global__ void __launch_bounds__(kThreads) k_gs_pass1(int n, int k, const double* __restrict__ V,
+                                                       const double* __restrict__ w, double* __restrict__ red,
+                                                       double* __restrict__ h1, double* __restrict__ beta,
+                                                       KrylovScalars* ks, double keep) {
+  __shared__ double sh[kThreads / 32][8];
+  if (ks->done) return;
+  gs_dots(n, k, V, w, red, sh);
+  if (arrive_last(&ks->ticket[5])) {
+    const double sq = gs_reduce_last(k, red, h1);
+    if (threadIdx.x == 0) {
+      const double ww = h1[k], b2 = ww - sq;
+      if (b2 > keep * ww) {
+        ks->gm_mode = 1;
+        beta[0] = sqrt(b2);
+      } else {
+        ks->gm_mode = 2;
+        beta[0] = 0.0;
+      }
+    }
+  }
+}
+
+// w -= V h1; mode 1: scaled by 1 / beta[0] (a zero beta, an exact breakdown,
+// leaves w unscaled) and the last CTA takes the Givens step; mode 2: h2 =
+// [V, w]^T w on the new w, added up by the last CTA with beta[1] =
+// sqrt((w, w) - ||h2||^2).
+__global__ void __launch_bounds__(kThreads) k_gs_orth1(int n, int k, const double* __restrict__ V,
+                                                       const double* __restrict__ h1, double* __restrict__ beta,
+                                                       double* __restrict__ w, double* __restrict__ red,
+                                                       double* __restrict__ h2, int j, int m, double* gm,
+                                                       KrylovScalars* ks) {
+  extern __shared__ double stage[];
+  __shared__ double sh[kThreads / 32][8];
+  if (ks->done) return;
+  const int mode = ks->gm_mode;
+  const double b0 = beta[0];
+  gs_orth_rows(n, k, V, h1, w, mode == 1, mode == 1 && b0 > 0.0 ? 1.0 / b0 : 1.0);
+  if (mode == 1) {
+    if (arrive_last(&ks->ticket[6])) gs_givens(j, m, gm, ks, stage);
     return;
   }
-  cs[j] = d / den;
-  sn[j] = hn / den;
-  H[j * m + j] = den;
-  H[(j + 1) * m + j] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  ks->iter += 1;
-  if (!isfinite(g[j + 1])) ks->bad = 1;
-  if (!(g[j + 1] * g[j + 1] > ks->tol2) || ks->iter >= ks->maxit || hn == 0.0 || ks->bad) ks->done = 1;
+  gs_dots(n, k, V, w, red, sh);
+  if (arrive_last(&ks->ticket[6])) {
+    const double sq = gs_reduce_last(k, red, h2);
+    if (threadIdx.x == 0) {
+      const double b2 = h2[k] - sq;
+      beta[1] = b2 > 0.0 ? sqrt(b2) : 0.0;
+    }
+  }
+}
+
+// Mode 2: w -= V h2, scaled by 1 / beta[1] (unscaled when zero), and the
+// Givens step by the last CTA.
+__global__ void __launch_bounds__(kThreads) k_gs_orth2(int n, int k, const double* __restrict__ V,
+                                                       const double* __restrict__ h2,
+                                                       const double* __restrict__ beta, double* __restrict__ w,
+                                                       int j, int m, double* gm, KrylovScalars* ks) {
+  extern __shared__ double stage[];
+  if (ks->done || ks->gm_mode != 2) return;
+  const double b1 = beta[1];
+  gs_orth_rows(n, k, V, h2, w, true, b1 > 0.0 ? 1.0 / b1 : 1.0);
+  if (arrive_last(&ks->ticket[7])) gs_givens(j, m, gm, ks, stage);
 }
 
 // b = a * (*scal); a and b may be the same vector
@@ -858,6 +974,13 @@ gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, Kryl
 }
 
 int vec_grid(const Ctx* c) { return std::min(c->red_grid, (c->n + kThreads - 1) / kThreads); }
+
+// Grid of the Gram-Schmidt kernels: two CTAs per SM, each with several rows
+// per thread, so the per-CTA partial sums stay few.
+int gs_grid(const Ctx* c) { return std::max(1, std::min(2 * kNumSMs, (c->n + kThreads - 1) / kThreads)); }
+
+// Dynamic shared memory of the Givens step (column j + 2, rotations 2 j).
+size_t gs_stage_bytes(int m) { return sizeof(double) * (3 * size_t(m) + 4); }
 
 // One PCG iteration body (everything after the convergence test is skipped
 // once ks->done is set).
@@ -1086,6 +1209,19 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
     GDSW_TRY(dalloc(c, &c->hcol, m + 2));
     GDSW_TRY(dalloc(c, &c->gm, GmLayout(m).total()));
   }
+  if (c->opt.krylov == GDSW_KRYLOV_GMRES) {
+    // the Givens step's staging in shared memory (more than the default 48 KB
+    // only for restarts beyond 2000)
+    const size_t gsm = gs_stage_bytes(std::max(1, c->opt.restart));
+    if (gsm > size_t(max_block_smem_optin())) {
+      set_error("GMRES restart %d too long for the Givens staging", c->opt.restart);
+      return GDSW_ERR_UNSUPPORTED;
+    }
+    if (gsm > 48 * 1024) {
+      GDSW_CK(cudaFuncSetAttribute(k_gs_orth1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(gsm)));
+      GDSW_CK(cudaFuncSetAttribute(k_gs_orth2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(gsm)));
+    }
+  }
   for (int q = 0; q < 8; ++q) GDSW_CK(cudaEventCreate(&c->ev[q]));
   GDSW_CK(cudaStreamSynchronize(s));
   // the SpMV kernel is chosen by timing before the graphs capture it
@@ -1273,11 +1409,12 @@ gdsw_status gmres_cycle(Ctx* c, cudaStream_t s) {
   // Pythagorean norm cancels (single reduction per step)
   c->gm_keep = c->opt.gmres_orth == GDSW_GMRES_ORTH_SINGLE ? 1e-4 : 2.0;
   const int m = std::max(1, c->opt.restart);
-  const int G = vec_grid(c);
   const GmLayout L(m);
   double* h1 = c->gm + L.h1();
   double* h2 = c->gm + L.h2();
   double* bt = c->gm + L.beta();
+  const int Ggs = gs_grid(c);
+  const size_t gsm = gs_stage_bytes(m);
   for (int j = 0; j < m; ++j) {
     const int k = j + 1;
     double* vj = c->V + int64_t(j) * n;
@@ -1285,15 +1422,9 @@ gdsw_status gmres_cycle(Ctx* c, cudaStream_t s) {
     double* w = c->V + int64_t(k) * n;
     GDSW_TRY(apply_enqueue_gated(c, vj, zj, s));
     GDSW_TRY(launch_spmv(c, zj, w, s, c->ks));
-    k_gs_dots<<<G, kThreads, 0, s>>>(n, k, c->V, w, c->red, c->ks, 0);
-    k_gs_reduce<<<k + 1, kThreads, 0, s>>>(G, c->red, h1, c->ks, 0);
-    k_gs_norm1<<<1, 32, 0, s>>>(k, h1, bt, c->ks, c->gm_keep);
-    k_gs_orth<<<G, kThreads, 0, s>>>(n, k, c->V, h1, bt, w, c->ks, 1);
-    k_gs_dots<<<G, kThreads, 0, s>>>(n, k, c->V, w, c->red, c->ks, 2);
-    k_gs_reduce<<<k + 1, kThreads, 0, s>>>(G, c->red, h2, c->ks, 2);
-    k_gs_norm2<<<1, 32, 0, s>>>(k, h2, bt, c->ks);
-    k_gs_orth<<<G, kThreads, 0, s>>>(n, k, c->V, h2, bt, w, c->ks, 2);
-    k_givens<<<1, 32, 0, s>>>(j, m, c->gm, c->ks);
+    k_gs_pass1<<<Ggs, kThreads, 0, s>>>(n, k, c->V, w, c->red, h1, bt, c->ks, c->gm_keep);
+    k_gs_orth1<<<Ggs, kThreads, gsm, s>>>(n, k, c->V, h1, bt, w, c->red, h2, j, m, c->gm, c->ks);
+    k_gs_orth2<<<Ggs, kThreads, gsm, s>>>(n, k, c->V, h2, bt, w, j, m, c->gm, c->ks);
     GDSW_CK(cudaGetLastError());
   }
   return GDSW_OK;
