@@ -18,6 +18,7 @@ namespace gdsw {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kGsThreads = 512;      // threads of the Gram-Schmidt kernels (one CTA per SM)
 
 // y = A x by row tiles of R rows: the tile's values and the gathered x
 // entries are loaded once, coalesced, into shared memory, then one thread per
@@ -671,8 +672,8 @@ __global__ void k_gs_reduce(int parts, const double* __restrict__ red, double* _
 
 // ---- classical Gram-Schmidt of an Arnoldi step (Sec. VII's GMRES) ----
 //
-// Three launches per step on a grid of a few CTAs per SM, each CTA a
-// grid-stride share of the rows (FP64: one DFMA per entry, the FP64 pipe and
+// Three launches per step on a grid of one CTA of kGsThreads per SM, each
+// CTA a grid-stride share of the rows (FP64: one DFMA per entry, the FP64 pipe and
 // the vector stream are the bounds):
 //   k_gs_pass1   h1 = [V, w]^T w; the last CTA (ticket) adds the partials in a
 //                fixed order and decides on the second pass (mode);
@@ -682,29 +683,66 @@ __global__ void k_gs_reduce(int parts, const double* __restrict__ red, double* _
 //   k_gs_orth2   mode 2: w -= V h2, scaled by 1 / beta, and the Givens step.
 // Every kernel is gated on the stop flag; the mode is uniform over the grid.
 
+// Sums over the 32 lanes of eight values per lane (a[0..7]) as a butterfly
+// that halves the values a lane carries at each of the first three steps:
+// 4 + 2 + 1 + 1 + 1 adds instead of 8 x 5 (on B300 every FP64 add of a warp
+// costs the FP64 pipe as much as a full one).  Afterwards lane l holds the
+// warp's sum of column (l >> 2) & 7 in a[0]; fixed order, deterministic.
+__device__ __forceinline__ void warp_sum8(double* a) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double mine = b4 ? a[u + 4] : a[u], other = b4 ? a[u] : a[u + 4];
+    a[u] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const double mine = b3 ? a[u + 2] : a[u], other = b3 ? a[u] : a[u + 2];
+    a[u] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+  }
+  {
+    const double mine = b2 ? a[1] : a[0], other = b2 ? a[0] : a[1];
+    a[0] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
+  }
+  a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+  a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
 // Partial dots of this CTA's rows for columns c0 .. c0 + NC - 1 of [V_0 ..
 // V_{k-1}, x] with x (column k is (x, x)), into red[col * gridDim.x + CTA]:
-// per column a warp sum, then the warps' sums in warp order.
+// per warp the butterfly sums, then the warps' sums in warp order.  Two rows
+// per thread per trip keep twice the loads in flight.
 template <int NC>
 __device__ __forceinline__ void gs_dots_group(int n, int k, int c0, const double* __restrict__ V,
                                               const double* x, double* __restrict__ red, double (*sh)[8]) {
   const double* col[NC];
 #pragma unroll
   for (int u = 0; u < NC; ++u) col[u] = c0 + u < k ? V + int64_t(c0 + u) * n : x;
-  double acc[NC];
+  double acc[8];
 #pragma unroll
-  for (int u = 0; u < NC; ++u) acc[u] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double xi = x[i];
+  for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    const double x0 = x[i], x1 = x[i + stride];
+    double v0[NC], v1[NC];
 #pragma unroll
-    for (int u = 0; u < NC; ++u) acc[u] = fma(col[u][i], xi, acc[u]);
+    for (int u = 0; u < NC; ++u) {
+      v0[u] = col[u][i];
+      v1[u] = col[u][i + stride];
+    }
+#pragma unroll
+    for (int u = 0; u < NC; ++u) acc[u] = fma(v1[u], x1, fma(v0[u], x0, acc[u]));
   }
+  if (i < n) {
+    const double x0 = x[i];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) acc[u] = fma(col[u][i], x0, acc[u]);
+  }
+  warp_sum8(acc);
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int u = 0; u < NC; ++u) {
-    const double t = warp_sum(acc[u]);
-    if (lane == 0) sh[wp][u] = t;
-  }
+  if ((lane & 3) == 0) sh[wp][lane >> 2] = acc[0];
   __syncthreads();
   if (threadIdx.x < NC) {
     double t = 0.0;
@@ -756,18 +794,18 @@ __device__ __forceinline__ double gs_reduce_last(int k, const double* __restrict
 }
 
 // w -= V h (k columns) over this CTA's rows; scaled by `inv` when `last`.
+// Eight columns' loads in flight per thread.
 __device__ __forceinline__ void gs_orth_rows(int n, int k, const double* __restrict__ V, const double* h,
                                              double* w, bool last, double inv) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc = w[i];
     int j = 0;
-    for (; j + 4 <= k; j += 4) {
-      const double v0 = V[int64_t(j) * n + i], v1 = V[int64_t(j + 1) * n + i];
-      const double v2 = V[int64_t(j + 2) * n + i], v3 = V[int64_t(j + 3) * n + i];
-      acc = fma(-h[j], v0, acc);
-      acc = fma(-h[j + 1], v1, acc);
-      acc = fma(-h[j + 2], v2, acc);
-      acc = fma(-h[j + 3], v3, acc);
+    for (; j + 8 <= k; j += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V[int64_t(j + u) * n + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = fma(-h[j + u], v[u], acc);
     }
     for (; j < k; ++j) acc = fma(-h[j], V[int64_t(j) * n + i], acc);
     w[i] = last ? acc * inv : acc;
@@ -838,11 +876,11 @@ __device__ void gs_givens(int j, int m, double* __restrict__ gm, KrylovScalars* 
 // keeps more than `keep` of (w, w) one pass suffices (mode 1, beta[0] from
 // the formula), else a second pass follows (mode 2).  keep > 1 asks for the
 // second pass at every step (CGS2).
-__global__ void __launch_bounds__(kThreads) k_gs_pass1(int n, int k, const double* __restrict__ V,
+__global__ void __launch_bounds__(kGsThreads, 1) k_gs_pass1(int n, int k, const double* __restrict__ V,
                                                        const double* __restrict__ w, double* __restrict__ red,
                                                        double* __restrict__ h1, double* __restrict__ beta,
                                                        KrylovScalars* ks, double keep) {
-  __shared__ double sh[kThreads / 32][8];
+  __shared__ double sh[kGsThreads / 32][8];
   if (ks->done) return;
   gs_dots(n, k, V, w, red, sh);
   if (arrive_last(&ks->ticket[5])) {
@@ -864,13 +902,13 @@ __global__ void __launch_bounds__(kThreads) k_gs_pass1(int n, int k, const doubl
 // leaves w unscaled) and the last CTA takes the Givens step; mode 2: h2 =
 // [V, w]^T w on the new w, added up by the last CTA with beta[1] =
 // sqrt((w, w) - ||h2||^2).
-__global__ void __launch_bounds__(kThreads) k_gs_orth1(int n, int k, const double* __restrict__ V,
+__global__ void __launch_bounds__(kGsThreads, 1) k_gs_orth1(int n, int k, const double* __restrict__ V,
                                                        const double* __restrict__ h1, double* __restrict__ beta,
                                                        double* __restrict__ w, double* __restrict__ red,
                                                        double* __restrict__ h2, int j, int m, double* gm,
                                                        KrylovScalars* ks) {
   extern __shared__ double stage[];
-  __shared__ double sh[kThreads / 32][8];
+  __shared__ double sh[kGsThreads / 32][8];
   if (ks->done) return;
   const int mode = ks->gm_mode;
   const double b0 = beta[0];
@@ -891,7 +929,7 @@ __global__ void __launch_bounds__(kThreads) k_gs_orth1(int n, int k, const doubl
 
 // Mode 2: w -= V h2, scaled by 1 / beta[1] (unscaled when zero), and the
 // Givens step by the last CTA.
-__global__ void __launch_bounds__(kThreads) k_gs_orth2(int n, int k, const double* __restrict__ V,
+__global__ void __launch_bounds__(kGsThreads, 1) k_gs_orth2(int n, int k, const double* __restrict__ V,
                                                        const double* __restrict__ h2,
                                                        const double* __restrict__ beta, double* __restrict__ w,
                                                        int j, int m, double* gm, KrylovScalars* ks) {
@@ -975,9 +1013,9 @@ gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, Kryl
 
 int vec_grid(const Ctx* c) { return std::min(c->red_grid, (c->n + kThreads - 1) / kThreads); }
 
-// Grid of the Gram-Schmidt kernels: two CTAs per SM, each with several rows
+// Grid of the Gram-Schmidt kernels: one CTA per SM, each with several rows
 // per thread, so the per-CTA partial sums stay few.
-int gs_grid(const Ctx* c) { return std::max(1, std::min(2 * kNumSMs, (c->n + kThreads - 1) / kThreads)); }
+int gs_grid(const Ctx* c) { return std::max(1, std::min(kNumSMs, (c->n + kGsThreads - 1) / kGsThreads)); }
 
 // Dynamic shared memory of the Givens step (column j + 2, rotations 2 j).
 size_t gs_stage_bytes(int m) { return sizeof(double) * (3 * size_t(m) + 4); }
@@ -1422,9 +1460,9 @@ gdsw_status gmres_cycle(Ctx* c, cudaStream_t s) {
     double* w = c->V + int64_t(k) * n;
     GDSW_TRY(apply_enqueue_gated(c, vj, zj, s));
     GDSW_TRY(launch_spmv(c, zj, w, s, c->ks));
-    k_gs_pass1<<<Ggs, kThreads, 0, s>>>(n, k, c->V, w, c->red, h1, bt, c->ks, c->gm_keep);
-    k_gs_orth1<<<Ggs, kThreads, gsm, s>>>(n, k, c->V, h1, bt, w, c->red, h2, j, m, c->gm, c->ks);
-    k_gs_orth2<<<Ggs, kThreads, gsm, s>>>(n, k, c->V, h2, bt, w, j, m, c->gm, c->ks);
+    k_gs_pass1<<<Ggs, kGsThreads, 0, s>>>(n, k, c->V, w, c->red, h1, bt, c->ks, c->gm_keep);
+    k_gs_orth1<<<Ggs, kGsThreads, gsm, s>>>(n, k, c->V, h1, bt, w, c->red, h2, j, m, c->gm, c->ks);
+    k_gs_orth2<<<Ggs, kGsThreads, gsm, s>>>(n, k, c->V, h2, bt, w, j, m, c->gm, c->ks);
     GDSW_CK(cudaGetLastError());
   }
   return GDSW_OK;
