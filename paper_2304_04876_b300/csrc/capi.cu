@@ -167,7 +167,7 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
   if (st == GDSW_OK) st = c->fp32 ? dalloc(c, reinterpret_cast<float**>(&c->zloc), P.sum_m)
                                   : dalloc(c, reinterpret_cast<double**>(&c->zloc), P.sum_m);
   if (st == GDSW_OK) st = apply_configure(c);
-  if (st == GDSW_OK) st = spmv_configure(c, A->rowptr, A->colind);
+  if (st == GDSW_OK) st = spmv_configure(c, A->rowptr, A->colind, A->val);
   const double t1 = now_s();
   if (st == GDSW_OK) st = krylov_init(c, s);
   if (st == GDSW_OK && P.nprob > 1) {
@@ -305,7 +305,7 @@ gdsw_status gdsw_bytes_required(const gdsw_csr* A, const gdsw_partition* part, c
   gdsw_status st = build_plan(A, part, &o, o.local_solver != GDSW_LOCAL_EXACT, &P);
   if (st != GDSW_OK) return st;
   int64_t r = 0, sc = 0;
-  st = estimate_footprint(P, o, Z ? nn : 0, &r, &sc);
+  st = estimate_footprint(P, A, o, Z ? nn : 0, &r, &sc);
   if (st != GDSW_OK) return st;
   if (resident) *resident = r;
   if (setup_scratch) *setup_scratch = sc;

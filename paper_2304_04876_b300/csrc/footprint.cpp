@@ -63,6 +63,26 @@ int64_t jacobi_block_bytes(const Plan& P, int64_t vb) {
   return total;
 }
 
+bool plan_sell(int n, const int* rowptr, const int* colind, std::vector<int64_t>* sptr) {
+  sptr->clear();
+  if (n <= 0 || double(rowptr[n]) <= 16.0 * n) return false;
+  for (int i = 0; i < n; ++i)
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (colind[e] - i < -32768 || colind[e] - i > 32767) return false;
+  const int nsl = (n + kSellRows - 1) / kSellRows;
+  sptr->assign(size_t(nsl) + 1, 0);
+  for (int q = 0; q < nsl; ++q) {
+    int w = 0;
+    for (int i = q * kSellRows; i < std::min(n, (q + 1) * kSellRows); ++i) w = std::max(w, rowptr[i + 1] - rowptr[i]);
+    (*sptr)[q + 1] = (*sptr)[q] + int64_t(w) * kSellRows;
+  }
+  if ((*sptr)[nsl] * 2 > int64_t(rowptr[n]) * 3) {
+    sptr->clear();
+    return false;
+  }
+  return true;
+}
+
 size_t node_piece_cap() {
   size_t cap = kNodePieceBytes;
   if (const char* e = getenv("GDSW_NODE_PIECE_BYTES")) cap = std::min<size_t>(cap, std::max<long>(1024, atol(e)));
@@ -124,7 +144,7 @@ bool plan_node_pieces(const Plan& P, size_t cap, std::vector<NodePiece>* pieces,
   return *total / 4 < (size_t(1) << 31);
 }
 
-gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
+gdsw_status estimate_footprint(const Plan& P, const gdsw_csr* A, const gdsw_options& o, int nn, int64_t* resident,
                                int64_t* scratch_peak) {
   const bool exact = o.local_solver == GDSW_LOCAL_EXACT;
   const bool low = o.precision != GDSW_PREC_FP64;
@@ -235,8 +255,14 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int
   // Krylov workspace: six vectors, the reduction buffer, scalars; GMRES basis
   // (reduction buffer: partials of any SpMV grid, at most 32 CTAs per SM)
   R += 6 * arr(n, 8) + arr(2 * (nsub + int64_t(P.ncomp)) + 32 * 148 + 64, 8) + 256;
-  // the SpMV's 16-bit column offsets (when they fit)
+  // the SpMV's 16-bit column offsets (when they fit), and the sliced ELL copy
+  // for long rows (values, offsets, slice starts)
   R += arr(P.nnz, 2);
+  {
+    std::vector<int64_t> sptr;
+    if (plan_sell(P.n, A->rowptr, A->colind, &sptr))
+      R += arr(sptr.back(), 8) + arr(sptr.back(), 2) + arr(static_cast<int64_t>(sptr.size()), 8);
+  }
   // GMRES: basis and preconditioned directions, its state, and the reduction
   // buffer of its fused dot products (2 restart + 4 partial sums per CTA)
   if (o.krylov == GDSW_KRYLOV_GMRES)

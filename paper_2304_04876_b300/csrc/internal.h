@@ -250,7 +250,7 @@ inline int mf_leaf_size() {
 
 // Device bytes of a handle built from this plan and of the setup's scratch
 // (upper bounds; host work only).
-gdsw_status estimate_footprint(const Plan& P, const gdsw_options& o, int nn, int64_t* resident,
+gdsw_status estimate_footprint(const Plan& P, const gdsw_csr* A, const gdsw_options& o, int nn, int64_t* resident,
                                int64_t* scratch_peak);
 int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec);
 // Pieces of the node programs (three unknowns per node, FP32): per subdomain,
@@ -260,6 +260,16 @@ int64_t record_stream_bytes(const Plan& P, int64_t vb, int64_t* nrec);
 // (a level whose rows do not come as whole nodes in solve order, or a node
 // wider than a piece).
 struct NodePiece { int sub, side, lev, t0, nodes, K; size_t off, bytes; };
+// Sliced ELL copy of the global matrix for the SpMV with long rows: slices of
+// kSellRows consecutive rows, each as wide as its longest row, entries
+// column-major within a slice (entry e of the slice's row r at slice start + e
+// * kSellRows + r), columns as 16-bit offsets from the row.  Taken when the mean
+// row is longer than 16 entries, every offset fits 16 bits and the padding
+// stays under half of the entries; sptr (slices + 1 entry offsets) then holds
+// the layout.
+constexpr int kSellRows = 32;
+bool plan_sell(int n, const int* rowptr, const int* colind, std::vector<int64_t>* sptr);
+
 // The piece limit: kNodePieceBytes, or less by GDSW_NODE_PIECE_BYTES (at least
 // 1 KB; several pieces per level, for tests).
 size_t node_piece_cap();
@@ -421,6 +431,12 @@ struct Ctx {
   int node_slot_bytes = 0;           // largest piece
   int node_stages = 0;               // ring slots; 0: kernel not used
   int node_threads = 512;            // threads of the node-program kernel (256 or 512)
+  // sliced ELL copy for the SpMV with long rows (k_spmv_sell)
+  int64_t* sell_ptr = nullptr;
+  int16_t* sell_col = nullptr;
+  double* sell_val = nullptr;
+  int sell_slices = 0;
+  int spmv_sell = 0;                 // 1: the sliced ELL kernel runs the SpMV
   int node_lanes = 4;                // lanes per node of the node-program kernel (2, 4 or 8)
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int rec_max_rows = 0;              // most rows in one level
@@ -605,7 +621,7 @@ gdsw_status krylov_init(Ctx* c, cudaStream_t s);
 gdsw_status spmv_enqueue(Ctx* c, const double* x, double* y, cudaStream_t s);
 // y = A x on the rows of problems that have not stopped (batched iteration).
 gdsw_status spmv_enqueue_batch(Ctx* c, const double* x, double* y, cudaStream_t s);
-gdsw_status spmv_configure(Ctx* c, const int* rowptr_host, const int* colind_host);
+gdsw_status spmv_configure(Ctx* c, const int* rowptr_host, const int* colind_host, const double* val_host);
 gdsw_status persistent_configure(Ctx* c);
 gdsw_status pcg_persistent_run(Ctx* c, cudaStream_t s);
 gdsw_status solve_pcg(Ctx* c, const double* b, double* x, gdsw_solve_info* info, cudaStream_t s);

@@ -294,6 +294,58 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int n, const int* __restrict_
   }
 }
 
+// y = A x and (x, y) from the sliced ELL copy (slices of kSellRows = 32 rows,
+// entries column-major within a slice, columns as 16-bit offsets from the
+// row): a warp per slice, a lane per row, U entries of each row in flight.
+// No cross-lane sums (on B300 every FP64 add of a warp costs the FP64 pipe a
+// full slot); a slice's padding entries (value 0, offset 0) cost one DFMA
+// each.  The dot product as in k_spmv_stream.
+template <int U>
+__global__ void __launch_bounds__(256) k_spmv_sell(int n, const int64_t* __restrict__ sptr,
+                                                   const int16_t* __restrict__ scol,
+                                                   const double* __restrict__ sval,
+                                                   const double* __restrict__ x, double* __restrict__ y,
+                                                   double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
+  __shared__ double sh[32];
+  if (ks != nullptr && ks->done) return;
+  const int lane = threadIdx.x & 31;
+  const int nsl = (n + kSellRows - 1) / kSellRows;
+  constexpr int kWarps = 256 / 32;
+  double dot = 0.0;
+  for (int sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < nsl; sl += gridDim.x * kWarps) {
+    const int row = sl * kSellRows + lane;
+    const bool valid = row < n && !gate_rows_off(gate, row, row + 1);
+    if (!valid) continue;
+    const int64_t o1 = sptr[sl + 1];
+    int64_t e = sptr[sl] + lane;
+    double acc = 0.0;
+    for (; e + (U - 1) * kSellRows < o1; e += U * kSellRows) {
+      int d[U];
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        d[u] = scol[e + u * kSellRows];
+        v[u] = sval[e + u * kSellRows];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc = fma(v[u], x[row + d[u]], acc);
+    }
+    for (; e < o1; e += kSellRows) acc = fma(sval[e], x[row + scol[e]], acc);
+    y[row] = acc;
+    dot = fma(x[row], acc, dot);
+  }
+  if (ks == nullptr) return;
+  const double t = block_sum(dot, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = t;
+  if (arrive_last(&ks->ticket[0])) {
+    const double s2 = sum_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      ks->pq = s2;
+      ks->alpha = ks->rz / s2;
+    }
+  }
+}
+
 // With alpha = (r,z)/(p,q) (divided once by the SpMV's last CTA): r -= alpha q;
 // rr = ||r||^2; then the last CTA counts the iteration, hands alpha to the x
 // update (which runs beside the preconditioner: nothing before the next SpMV
@@ -958,6 +1010,12 @@ __global__ void k_update_x(int n, int k, const double* __restrict__ Zk, const do
 
 gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, KrylovScalars* ks,
                         const BatchGate& gate = BatchGate{}) {
+  if (c->spmv_sell) {
+    const int grid = std::max(1, std::min(c->spmv_grid, (c->sell_slices + 7) / 8));
+    k_spmv_sell<8><<<grid, 256, 0, s>>>(c->n, c->sell_ptr, c->sell_col, c->sell_val, x, y, c->red, ks, gate);
+    GDSW_CK(cudaGetLastError());
+    return GDSW_OK;
+  }
   if (c->spmv_W > 0) {
     const int grid = std::max(1, std::min(c->spmv_grid, (c->n + 256 / c->spmv_W - 1) / (256 / c->spmv_W)));
     switch (c->spmv_W) {
@@ -1064,8 +1122,29 @@ gdsw_status set_done(Ctx* c, cudaStream_t s, int v) {
 // Tile height for the stream SpMV: the largest R in {256, 128, 64, 32} whose
 // worst tile keeps its products within 64 KB of shared memory; the grid is the
 // number of CTAs that fit on the SMs at once.
-gdsw_status spmv_configure(Ctx* c, const int* rowptr, const int* colind) {
+gdsw_status spmv_configure(Ctx* c, const int* rowptr, const int* colind, const double* val) {
   const int n = c->n;
+  // long rows: the sliced ELL copy, beside the CSR kernel (the choice is timed)
+  {
+    std::vector<int64_t> sptr;
+    if (plan_sell(n, rowptr, colind, &sptr)) {
+      const int64_t total = sptr.back();
+      std::vector<int16_t> scol(static_cast<size_t>(total), 0);
+      std::vector<double> sval(static_cast<size_t>(total), 0.0);
+      for (int i = 0; i < n; ++i) {
+        const int q = i / kSellRows, r = i % kSellRows;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+          const int64_t at = sptr[q] + int64_t(e - rowptr[i]) * kSellRows + r;
+          scol[at] = static_cast<int16_t>(colind[e] - i);
+          sval[at] = val[e];
+        }
+      }
+      GDSW_TRY(upload(c, &c->sell_ptr, sptr, nullptr));
+      GDSW_TRY(upload(c, &c->sell_col, scol, nullptr));
+      GDSW_TRY(upload(c, &c->sell_val, sval, nullptr));
+      c->sell_slices = static_cast<int>(sptr.size()) - 1;
+    }
+  }
   // columns as 16-bit offsets from the row when every one fits (the
   // thread-per-row kernel then reads 10 bytes per entry instead of 12)
   {
@@ -1156,8 +1235,41 @@ gdsw_status spmv_grids(size_t shm, int* g_stream, int* g_pipe) {
 // warm-up, CUDA events, on the Krylov workspace): all compute the same sums in
 // the same order, so the choice changes the speed only.
 // GDSW_SPMV=stream|pipe|thread fixes it instead (for profilers).
+// The sliced ELL kernel against the CSR kernel for long rows, three launches
+// each (CUDA events, after one warm-up); GDSW_SPMV=sell forces the first, any
+// other value the second.
+gdsw_status spmv_tune_long(Ctx* c, cudaStream_t s) {
+  c->spmv_sell = 0;
+  if (c->sell_ptr == nullptr) return GDSW_OK;
+  const char* env = getenv("GDSW_SPMV");
+  if (env != nullptr) {                 // forced: the sliced ELL kernel only for "sell"
+    c->spmv_sell = std::string(env) == "sell";
+    return GDSW_OK;
+  }
+  cudaEvent_t e0, e1;
+  GDSW_CK(cudaEventCreate(&e0));
+  GDSW_CK(cudaEventCreate(&e1));
+  float t[2] = {0.f, 0.f};
+  gdsw_status st = GDSW_OK;
+  for (int k = 0; k < 2 && st == GDSW_OK; ++k) {
+    c->spmv_sell = k;
+    st = launch_spmv(c, c->p, c->q, s, nullptr);
+    if (st != GDSW_OK) break;
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep) st = launch_spmv(c, c->p, c->q, s, nullptr);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t[k], e0, e1);
+    if (e != cudaSuccess) { set_error("SpMV tuning: %s", cudaGetErrorString(e)); st = GDSW_ERR_CUDA; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->spmv_sell = st == GDSW_OK && t[1] < t[0] ? 1 : 0;
+  return st;
+}
+
 gdsw_status spmv_tune(Ctx* c, cudaStream_t s) {
-  if (c->spmv_W > 0) return GDSW_OK;
+  if (c->spmv_W > 0) return spmv_tune_long(c, s);
   const size_t shm = size_t(c->spmv_maxne) * 2 * sizeof(double);
   int g[3] = {c->spmv_grid, c->spmv_grid, c->spmv_grid};
   switch (c->spmv_R) {
