@@ -436,6 +436,7 @@ struct Ctx {
   int16_t* sell_col = nullptr;
   double* sell_val = nullptr;
   int sell_slices = 0;
+  int upd_grid = 148;                // CTAs of the PCG residual update (one wave)
   int spmv_sell = 0;                 // 1: the sliced ELL kernel runs the SpMV
   int node_lanes = 4;                // lanes per node of the node-program kernel (2, 4 or 8)
   int rec_tpr = 1;                   // threads per row in the pipelined solve

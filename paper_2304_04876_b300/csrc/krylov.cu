@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kGsThreads = 512;      // threads of the Gram-Schmidt kernels (one CTA per SM)
+constexpr int kUpdPairs = 4;         // pairs of the residual update in flight per thread
 
 // y = A x by row tiles of R rows: the tile's values and the gathered x
 // entries are loaded once, coalesced, into shared memory, then one thread per
@@ -367,24 +368,31 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, double* __restri
   const int stride = gridDim.x * blockDim.x;
   double2* r2 = reinterpret_cast<double2*>(r);
   const double2* q2 = reinterpret_cast<const double2*>(q);
-  // two pairs per trip, their loads in flight together and their squares in
-  // two accumulators (added at the end)
+  // kUpdPairs pairs per trip, their loads in flight together and their squares
+  // in two accumulators (added at the end)
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + stride < n2; i += 2 * stride) {
-    const double2 qa = q2[i], qb = q2[i + stride];
-    double2 ra = r2[i], rb = r2[i + stride];
-    ra.x = fma(-alpha, qa.x, ra.x);
-    ra.y = fma(-alpha, qa.y, ra.y);
-    rb.x = fma(-alpha, qb.x, rb.x);
-    rb.y = fma(-alpha, qb.y, rb.y);
-    r2[i] = ra;
-    r2[i + stride] = rb;
-    rr = fma(ra.x, ra.x, rr);
-    rr1 = fma(rb.x, rb.x, rr1);
-    rr = fma(ra.y, ra.y, rr);
-    rr1 = fma(rb.y, rb.y, rr1);
+  for (; i + (kUpdPairs - 1) * stride < n2; i += kUpdPairs * stride) {
+    double2 qa[kUpdPairs], ra[kUpdPairs];
+#pragma unroll
+    for (int u = 0; u < kUpdPairs; ++u) {
+      qa[u] = q2[i + u * stride];
+      ra[u] = r2[i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < kUpdPairs; ++u) {
+      ra[u].x = fma(-alpha, qa[u].x, ra[u].x);
+      ra[u].y = fma(-alpha, qa[u].y, ra[u].y);
+      r2[i + u * stride] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < kUpdPairs; u += 2) {
+      rr = fma(ra[u].x, ra[u].x, rr);
+      rr = fma(ra[u].y, ra[u].y, rr);
+      rr1 = fma(ra[u + 1].x, ra[u + 1].x, rr1);
+      rr1 = fma(ra[u + 1].y, ra[u + 1].y, rr1);
+    }
   }
-  if (i < n2) {
+  for (; i < n2; i += stride) {
     const double2 qa = q2[i];
     double2 ra = r2[i];
     ra.x = fma(-alpha, qa.x, ra.x);
@@ -1071,6 +1079,9 @@ gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, Kryl
 
 int vec_grid(const Ctx* c) { return std::min(c->red_grid, (c->n + kThreads - 1) / kThreads); }
 
+// Grid of the residual update (upd_grid CTAs of kThreads).
+int upd_grid(const Ctx* c) { return std::max(1, std::min(c->upd_grid, (c->n / 2 + kThreads - 1) / kThreads)); }
+
 // Grid of the Gram-Schmidt kernels: one CTA per SM, each with several rows
 // per thread, so the per-CTA partial sums stay few.
 int gs_grid(const Ctx* c) { return std::max(1, std::min(kNumSMs, (c->n + kGsThreads - 1) / kGsThreads)); }
@@ -1082,7 +1093,7 @@ size_t gs_stage_bytes(int m) { return sizeof(double) * (3 * size_t(m) + 4); }
 // once ks->done is set).
 gdsw_status pcg_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
   GDSW_TRY(launch_spmv(c, c->p, c->q, s, c->ks));
-  k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(c->n, c->r, c->q, c->red, c->ks, h, use_handle);
+  k_pcg_update<<<upd_grid(c), kThreads, 0, s>>>(c->n, c->r, c->q, c->red, c->ks, h, use_handle);
   GDSW_CK(cudaGetLastError());
   // x += alpha p is off the path to the next SpMV: it goes on the second
   // stream behind the coarse branch and is joined before p is overwritten
@@ -1336,6 +1347,10 @@ gdsw_status gmres_cycle_dc(Ctx* c, cudaStream_t s);
 gdsw_status krylov_init(Ctx* c, cudaStream_t s) {
   const int n = c->n;
   c->red_grid = kNumSMs * 8;
+  // two CTAs per SM: few partial sums for the last CTA (and few arrivals on
+  // its ticket), each thread several trips of kUpdPairs pairs
+  c->upd_grid = 2 * kNumSMs;
+  if (const char* e = getenv("GDSW_UPD_CTAS_PER_SM")) c->upd_grid = std::max(1, std::min(8, atoi(e))) * kNumSMs;
   // (any SpMV grid: at most 32 resident CTAs per SM)
   c->red_len = std::max(std::max(2 * c->red_grid, 2 * c->nblk), std::max(c->spmv_grid, 32 * kNumSMs)) + 64;
   if (c->opt.krylov == GDSW_KRYLOV_GMRES)
@@ -1521,7 +1536,7 @@ gdsw_status pcg_iteration_timed(Ctx* c, const double* b, cudaStream_t s, double*
   }
   if (st == GDSW_OK) {
     cudaEventRecord(ev[1], s);
-    k_pcg_update<<<vec_grid(c), kThreads, 0, s>>>(n, c->r, c->q, c->red, c->ks, cudaGraphConditionalHandle{}, 0);
+    k_pcg_update<<<upd_grid(c), kThreads, 0, s>>>(n, c->r, c->q, c->red, c->ks, cudaGraphConditionalHandle{}, 0);
     if (cudaGetLastError() != cudaSuccess) { set_error("vector update launch failed"); st = GDSW_ERR_CUDA; }
   }
   if (st == GDSW_OK) st = apply_timed_dots(c, c->r, c->z, s, ap);
