@@ -132,3 +132,38 @@ def test_node_programs_wait_that_runs_out_reports_timeout(monkeypatch):
     h2 = handle_env(prob, {"GDSW_LOCAL_SHAPE": "3,512,3"}, local_solver="ilu0", precision="fp32")
     assert relerr(gpu_apply(h2, r), M.apply(r)) <= 2e-5
     h2.close()
+
+
+def test_node_programs_in_a_batched_handle():
+    """A batched FP32 handle of elasticity members (three unknowns per node) takes the
+    node programs; a member that has stopped is skipped (the per-subdomain gate), and
+    every member converges with the iteration count of the record kernel (within one)
+    and a solution within 1e-6."""
+    import torch
+    from paper_2304_04876_b300 import gdsw as G
+    mem = [P.elasticity_problem(4, 2), P.elasticity_problem(6, 2), P.elasticity_problem(6, 3)]
+    b = np.concatenate([m.b for m in mem])
+    out = {}
+    for shape, kernel in (("4,256,0", 3), ("3,256,3,4", 7)):
+        old = os.environ.get("GDSW_LOCAL_SHAPE")
+        os.environ["GDSW_LOCAL_SHAPE"] = shape
+        try:
+            h = G.Handle.batch([(m.A, m.part, None if m.Z is None or m.Z.shape[1] == 1 else m.Z) for m in mem],
+                               local_solver="ilu0", precision="fp32")
+        finally:
+            if old is None:
+                os.environ.pop("GDSW_LOCAL_SHAPE")
+            else:
+                os.environ["GDSW_LOCAL_SHAPE"] = old
+        assert h.stats()["local_kernel"] == kernel, shape
+        bt = torch.tensor(b, dtype=torch.float64, device="cuda")
+        xt = torch.zeros_like(bt)
+        infos = h.solve_batch(bt, xt)
+        torch.cuda.synchronize()
+        assert all(i.converged and i.true_relres <= 1e-8 for i in infos), shape
+        out[shape] = (xt.cpu().numpy(), [i.iters for i in infos])
+        h.close()
+    (x0, it0), (x1, it1) = out["4,256,0"], out["3,256,3,4"]
+    assert all(abs(a - c) <= 1 for a, c in zip(it0, it1)), (it0, it1)
+    assert relerr(x1, x0) <= 1e-6
+
