@@ -796,7 +796,7 @@ def config_summaries(args, world, rank, dist, barrier) -> dict:
     keep = ("metric", "value", "unit", "ms_per_step", "iters", "iters_min_max", "true_relres_max", "setup_s",
             "one_at_a_time_problems_per_s", "p50_ms", "p99_ms", "plain_fp64_one_at_a_time", "served_over_plain",
             "rates", "slots", "roofline", "apply_phase_ms", "spmv_ms", "variants")
-    for cfg, extra in ((1, dict(steps=20, warmup=3)), (3, dict(steps=3, warmup=3)),
+    for cfg, extra in ((1, dict(steps=40, warmup=20)), (3, dict(steps=3, warmup=3)),
                        (4, dict(steps=2, warmup=3)),
                        # (config 5 bounded: 10 problems of at most 96^3 unknowns, two rates)
                        (5, dict(requests=40, rates=[30.0, 1000.0], pool=10, serving_max_dofs=96 ** 3))):
