@@ -538,65 +538,11 @@ struct GmLayout {
 // step; column k-1 is complete one step later, so the convergence test lags by
 // one operator application.
 
-// Partial sums for step k: dots j < k of (V_j, u), then (V_j, w), then (u, u),
-// (u, w), (w, w); without w only (V_j, u) and (u, u).  Columns go 8 at a time.
-__global__ void __launch_bounds__(kThreads) k_dc_dots(int n, int k, const double* __restrict__ V,
-                                                      const double* __restrict__ u,
-                                                      const double* __restrict__ w, double* __restrict__ red,
-                                                      const KrylovScalars* __restrict__ ks) {
-  __shared__ double sh[32];
-  if (ks->done) return;
-  const int nd = w != nullptr ? 2 * k + 3 : k + 1;
-  auto store = [&](int d, double v) {
-    const double t = block_sum(v, sh);
-    if (threadIdx.x == 0) red[int64_t(d) * gridDim.x + blockIdx.x] = t;
-  };
-  for (int c0 = 0; c0 < k || c0 == 0; c0 += 8) {
-    double au[8], aw[8], uu = 0.0, uw = 0.0, ww = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) { au[q] = 0.0; aw[q] = 0.0; }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      const double ui = u[i];
-      const double wi = w != nullptr ? w[i] : 0.0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (c0 + q < k) {
-          const double vj = V[int64_t(c0 + q) * n + i];
-          au[q] = fma(vj, ui, au[q]);
-          aw[q] = fma(vj, wi, aw[q]);
-        }
-      }
-      if (c0 == 0) {
-        uu = fma(ui, ui, uu);
-        uw = fma(ui, wi, uw);
-        ww = fma(wi, wi, ww);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (c0 + q < k) {
-        store(c0 + q, au[q]);
-        if (w != nullptr) store(k + c0 + q, aw[q]);
-      }
-    }
-    if (c0 == 0) {
-      if (w != nullptr) {
-        store(2 * k, uu);
-        store(2 * k + 1, uw);
-        store(2 * k + 2, ww);
-      } else {
-        store(k, uu);
-      }
-    }
-    (void)nd;
-  }
-}
-
-// Step k's scalar work (one thread): finish u_k and Hessenberg column k-1
+// Step k's scalar work (thread 0 of the reducing CTA): finish u_k and Hessenberg column k-1
 // (with its Givens rotation and the residual estimate, which may end the
 // cycle), then the coefficients of the vector update.  At the last step of a
 // cycle (`final`) only the first part.
-__global__ void k_dc_coef(int k, int m, double* __restrict__ gm, KrylovScalars* ks, int final_step) {
+__device__ void dc_coef(int k, int m, double* __restrict__ gm, KrylovScalars* ks, int final_step) {
   if (threadIdx.x != 0 || ks->done) return;
   const GmLayout L(m);
   double* H = gm;
@@ -692,12 +638,12 @@ __global__ void k_dc_coef(int k, int m, double* __restrict__ gm, KrylovScalars* 
 
 // q_k = (u - F a) / sigma into V_k, M^-1 q_k = (zu - Z_F a) / sigma into Z_k,
 // u_{k+1} = (w - Q_{k+1} cc) / (sigma rho) into u (each element read first).
-__global__ void __launch_bounds__(kThreads) k_dc_update(int n, int k, int m, double* __restrict__ V,
-                                                        double* __restrict__ Zk, double* __restrict__ u,
-                                                        const double* __restrict__ zu,
-                                                        const double* __restrict__ w,
-                                                        const double* __restrict__ gm,
-                                                        const KrylovScalars* __restrict__ ks) {
+__global__ void __launch_bounds__(kGsThreads, 1) k_dc_update(int n, int k, int m, double* __restrict__ V,
+                                                              double* __restrict__ Zk, double* __restrict__ u,
+                                                              const double* __restrict__ zu,
+                                                              const double* __restrict__ w,
+                                                              const double* __restrict__ gm,
+                                                              const KrylovScalars* __restrict__ ks) {
   if (ks->done) return;
   const GmLayout L(m);
   const double* ca = gm + L.ca();
@@ -707,7 +653,23 @@ __global__ void __launch_bounds__(kThreads) k_dc_update(int n, int k, int m, dou
   double* zk = Zk + int64_t(k) * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double uq = u[i], zz = zu[i], ww = w[i];
-    for (int j = 0; j < k; ++j) {
+    int j = 0;
+    // four columns of V and of Z in flight per trip
+    for (; j + 4 <= k; j += 4) {
+      double vj[4], zj[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        vj[q] = V[int64_t(j + q) * n + i];
+        zj[q] = Zk[int64_t(j + q) * n + i];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uq = fma(-ca[j + q], vj[q], uq);
+        ww = fma(-cc[j + q], vj[q], ww);
+        zz = fma(-ca[j + q], zj[q], zz);
+      }
+    }
+    for (; j < k; ++j) {
       const double vj = V[int64_t(j) * n + i];
       uq = fma(-ca[j], vj, uq);
       ww = fma(-cc[j], vj, ww);
@@ -998,6 +960,138 @@ __global__ void __launch_bounds__(kGsThreads, 1) k_gs_orth2(int n, int k, const 
   const double b1 = beta[1];
   gs_orth_rows(n, k, V, h2, w, true, b1 > 0.0 ? 1.0 / b1 : 1.0);
   if (arrive_last(&ks->ticket[7])) gs_givens(j, m, gm, ks, stage);
+}
+
+// ---- delayed reorthogonalisation: the step's reduction in one launch ----
+
+// Partial dots of this CTA's rows for columns c0 .. c0 + NC - 1 of V against u
+// (into red rows c0 ..) and, with W, against w (rows k + c0 ..): butterfly warp
+// sums, then the warps' sums in warp order.
+template <int NC, bool W>
+__device__ __forceinline__ void dc_dots_group(int n, int k, int c0, const double* __restrict__ V,
+                                              const double* __restrict__ u, const double* __restrict__ w,
+                                              double* __restrict__ red, double (*sh)[8], double (*sh2)[8]) {
+  const double* col[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) col[q] = V + int64_t(c0 + q) * n;
+  double au[8], aw[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    au[q] = 0.0;
+    aw[q] = 0.0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double ui = u[i];
+    const double wi = W ? w[i] : 0.0;
+    double vv[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) vv[q] = col[q][i];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      au[q] = fma(vv[q], ui, au[q]);
+      if (W) aw[q] = fma(vv[q], wi, aw[q]);
+    }
+  }
+  warp_sum8(au);
+  if (W) warp_sum8(aw);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((lane & 3) == 0) {
+    sh[wp][lane >> 2] = au[0];
+    if (W) sh2[wp][lane >> 2] = aw[0];
+  }
+  __syncthreads();
+  if (threadIdx.x < NC) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += sh[q][threadIdx.x];
+    red[int64_t(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  } else if (W && threadIdx.x >= 32 && threadIdx.x < 32 + NC) {
+    const int cq = threadIdx.x - 32;
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += sh2[q][cq];
+    red[int64_t(k + c0 + cq) * gridDim.x + blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+template <bool W>
+__device__ __forceinline__ void dc_dots(int n, int k, const double* __restrict__ V, const double* __restrict__ u,
+                                        const double* __restrict__ w, double* __restrict__ red, double (*sh)[8],
+                                        double (*sh2)[8]) {
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    switch (min(8, k - c0)) {
+      case 1: dc_dots_group<1, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+      case 2: dc_dots_group<2, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+      case 3: dc_dots_group<3, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+      case 4: dc_dots_group<4, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+      case 5: dc_dots_group<5, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+      case 6: dc_dots_group<6, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+      case 7: dc_dots_group<7, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+      default: dc_dots_group<8, W>(n, k, c0, V, u, w, red, sh, sh2); break;
+    }
+  }
+}
+
+// Step k of the delayed-reorthogonalisation cycle: the partial sums of (V_j,
+// u), (V_j, w) for j < k and of (u, u), (u, w), (w, w) (without w only
+// (V_j, u) and (u, u)); the last CTA adds them in CTA order into the dots
+// array and takes the step's scalar work (dc_coef).  One launch in place of a
+// dot, a reduction and a scalar kernel.
+__global__ void __launch_bounds__(kGsThreads, 1) k_dc_step(int n, int k, int m, const double* __restrict__ V,
+                                                           const double* __restrict__ u,
+                                                           const double* __restrict__ w, double* __restrict__ red,
+                                                           double* __restrict__ gm, KrylovScalars* ks,
+                                                           int final_step) {
+  __shared__ double sh[kGsThreads / 32][8], sh2[kGsThreads / 32][8];
+  if (ks->done) return;
+  const bool W = w != nullptr;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // (u, u), (u, w), (w, w)
+  {
+    double uu = 0.0, uw = 0.0, ww = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double ui = u[i];
+      uu = fma(ui, ui, uu);
+      if (W) {
+        const double wi = w[i];
+        uw = fma(ui, wi, uw);
+        ww = fma(wi, wi, ww);
+      }
+    }
+    uu = warp_sum(uu);
+    if (W) {
+      uw = warp_sum(uw);
+      ww = warp_sum(ww);
+    }
+    if (lane == 0) {
+      sh[wp][0] = uu;
+      sh[wp][1] = uw;
+      sh[wp][2] = ww;
+    }
+    __syncthreads();
+    if (threadIdx.x < (W ? 3 : 1)) {
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += sh[q][threadIdx.x];
+      const int row = W ? 2 * k + threadIdx.x : k;
+      red[int64_t(row) * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  if (W) dc_dots<true>(n, k, V, u, w, red, sh, sh2);
+  else dc_dots<false>(n, k, V, u, w, red, sh, sh2);
+  if (arrive_last(&ks->ticket[5])) {
+    const GmLayout L(m);
+    double* dt = gm + L.dt();
+    const int nd = W ? 2 * k + 3 : k + 1;
+    const int G = gridDim.x;
+    for (int cc = wp; cc < nd; cc += nw) {
+      double t = 0.0;
+      for (int q = lane; q < G; q += 32) t += __ldcg(red + int64_t(cc) * G + q);
+      t = warp_sum(t);
+      if (lane == 0) dt[cc] = t;
+    }
+    __syncthreads();
+    dc_coef(k, m, gm, ks, final_step);
+  }
 }
 
 // b = a * (*scal); a and b may be the same vector
@@ -1596,31 +1690,25 @@ gdsw_status gmres_cycle(Ctx* c, cudaStream_t s) {
 }
 
 // One restart cycle with delayed reorthogonalisation: per step the apply, the
-// SpMV, one fused reduction, the scalar step and one vector pass; a last
-// reduction finishes the final column.  u, M^-1 u and w live in the PCG
+// SpMV, one launch for the fused reduction and the scalar step (k_dc_step),
+// and one vector pass; a last reduction finishes the final column.  u, M^-1 u and w live in the PCG
 // vectors p, z and q; the driver has put q_0 = r / beta in V_0.
 gdsw_status gmres_cycle_dc(Ctx* c, cudaStream_t s) {
   const int n = c->n;
   const int m = std::max(1, c->opt.restart);
-  const int G = vec_grid(c);
-  const GmLayout L(m);
+  const int Ggs = gs_grid(c);
   double* u = c->p;
   double* zu = c->z;
   double* w = c->q;
-  double* dots = c->gm + L.dt();
   GDSW_CK(cudaMemcpyAsync(u, c->V, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   for (int k = 0; k < m; ++k) {
     GDSW_TRY(apply_enqueue_gated(c, u, zu, s));
     GDSW_TRY(launch_spmv(c, zu, w, s, c->ks));
-    k_dc_dots<<<G, kThreads, 0, s>>>(n, k, c->V, u, w, c->red, c->ks);
-    k_gs_reduce<<<2 * k + 3, kThreads, 0, s>>>(G, c->red, dots, c->ks, 0);
-    k_dc_coef<<<1, 32, 0, s>>>(k, m, c->gm, c->ks, 0);
-    k_dc_update<<<G, kThreads, 0, s>>>(n, k, m, c->V, c->Zk, u, zu, w, c->gm, c->ks);
+    k_dc_step<<<Ggs, kGsThreads, 0, s>>>(n, k, m, c->V, u, w, c->red, c->gm, c->ks, 0);
+    k_dc_update<<<Ggs, kGsThreads, 0, s>>>(n, k, m, c->V, c->Zk, u, zu, w, c->gm, c->ks);
     GDSW_CK(cudaGetLastError());
   }
-  k_dc_dots<<<G, kThreads, 0, s>>>(n, m, c->V, u, nullptr, c->red, c->ks);
-  k_gs_reduce<<<m + 1, kThreads, 0, s>>>(G, c->red, dots, c->ks, 0);
-  k_dc_coef<<<1, 32, 0, s>>>(m, m, c->gm, c->ks, 1);
+  k_dc_step<<<Ggs, kGsThreads, 0, s>>>(n, m, m, c->V, u, nullptr, c->red, c->gm, c->ks, 1);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
