@@ -267,7 +267,7 @@ struct NodePiece { int sub, side, lev, t0, nodes, K; size_t off, bytes; };
 // row is longer than 16 entries, every offset fits 16 bits and the padding
 // stays under half of the entries; sptr (slices + 1 entry offsets) then holds
 // the layout.
-constexpr int kSellRows = 32;
+constexpr int kSellRows = 8;
 bool plan_sell(int n, const int* rowptr, const int* colind, std::vector<int64_t>* sptr);
 
 // The piece limit: kNodePieceBytes, or less by GDSW_NODE_PIECE_BYTES (at least
@@ -437,7 +437,7 @@ struct Ctx {
   double* sell_val = nullptr;
   int sell_slices = 0;
   int upd_grid = 148;                // CTAs of the PCG residual update (one wave)
-  int spmv_sell = 0;                 // 1: the sliced ELL kernel runs the SpMV
+  int spmv_sell = 0;                 // 1 / 2: the sliced ELL kernel (4 / 8 in flight) runs the SpMV
   int node_lanes = 4;                // lanes per node of the node-program kernel (2, 4 or 8)
   int rec_tpr = 1;                   // threads per row in the pipelined solve
   int rec_max_rows = 0;              // most rows in one level

@@ -295,45 +295,54 @@ __global__ void __launch_bounds__(256) k_spmv_rows(int n, const int* __restrict_
   }
 }
 
-// y = A x and (x, y) from the sliced ELL copy (slices of kSellRows = 32 rows,
+// y = A x and (x, y) from the sliced ELL copy (slices of kSellRows = 8 rows,
 // entries column-major within a slice, columns as 16-bit offsets from the
-// row): a warp per slice, a lane per row, U entries of each row in flight.
-// No cross-lane sums (on B300 every FP64 add of a warp costs the FP64 pipe a
-// full slot); a slice's padding entries (value 0, offset 0) cost one DFMA
-// each.  The dot product as in k_spmv_stream.
+// row): a warp per slice, four lanes per row (lane l takes row l % 8 and every
+// fourth of its entries from l / 8 on, so the warp reads 32 consecutive
+// entries at a time), U entries of a lane in flight, the four partial sums
+// added with two shuffles.  Small slices keep the warps' shares even (a 32-row
+// slice per warp left most warps idle while a seventh ran a second one); a
+// slice's padding entries (value 0, offset 0) cost one DFMA each.  The dot
+// product as in k_spmv_stream.
 template <int U>
 __global__ void __launch_bounds__(256) k_spmv_sell(int n, const int64_t* __restrict__ sptr,
                                                    const int16_t* __restrict__ scol,
                                                    const double* __restrict__ sval,
                                                    const double* __restrict__ x, double* __restrict__ y,
                                                    double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
+  static_assert(kSellRows == 8, "four lanes per row of an 8-row slice");
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, rr = lane & 7;
   const int nsl = (n + kSellRows - 1) / kSellRows;
   constexpr int kWarps = 256 / 32;
   double dot = 0.0;
   for (int sl = blockIdx.x * kWarps + (threadIdx.x >> 5); sl < nsl; sl += gridDim.x * kWarps) {
-    const int row = sl * kSellRows + lane;
+    const int row = sl * kSellRows + rr;
     const bool valid = row < n && !gate_rows_off(gate, row, row + 1);
-    if (!valid) continue;
-    const int64_t o1 = sptr[sl + 1];
-    int64_t e = sptr[sl] + lane;
     double acc = 0.0;
-    for (; e + (U - 1) * kSellRows < o1; e += U * kSellRows) {
-      int d[U];
-      double v[U];
+    if (valid) {
+      const int64_t o1 = sptr[sl + 1];
+      int64_t e = sptr[sl] + lane;
+      for (; e + (U - 1) * 32 < o1; e += U * 32) {
+        int d[U];
+        double v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        d[u] = scol[e + u * kSellRows];
-        v[u] = sval[e + u * kSellRows];
+        for (int u = 0; u < U; ++u) {
+          d[u] = scol[e + u * 32];
+          v[u] = sval[e + u * 32];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc = fma(v[u], x[row + d[u]], acc);
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) acc = fma(v[u], x[row + d[u]], acc);
+      for (; e < o1; e += 32) acc = fma(sval[e], x[row + scol[e]], acc);
     }
-    for (; e < o1; e += kSellRows) acc = fma(sval[e], x[row + scol[e]], acc);
-    y[row] = acc;
-    dot = fma(x[row], acc, dot);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (valid && lane < 8) {
+      y[row] = acc;
+      dot = fma(x[row], acc, dot);
+    }
   }
   if (ks == nullptr) return;
   const double t = block_sum(dot, sh);
@@ -1114,7 +1123,10 @@ gdsw_status launch_spmv(Ctx* c, const double* x, double* y, cudaStream_t s, Kryl
                         const BatchGate& gate = BatchGate{}) {
   if (c->spmv_sell) {
     const int grid = std::max(1, std::min(c->spmv_grid, (c->sell_slices + 7) / 8));
-    k_spmv_sell<8><<<grid, 256, 0, s>>>(c->n, c->sell_ptr, c->sell_col, c->sell_val, x, y, c->red, ks, gate);
+    if (c->spmv_sell == 2)
+      k_spmv_sell<8><<<grid, 256, 0, s>>>(c->n, c->sell_ptr, c->sell_col, c->sell_val, x, y, c->red, ks, gate);
+    else
+      k_spmv_sell<4><<<grid, 256, 0, s>>>(c->n, c->sell_ptr, c->sell_col, c->sell_val, x, y, c->red, ks, gate);
     GDSW_CK(cudaGetLastError());
     return GDSW_OK;
   }
@@ -1340,23 +1352,23 @@ gdsw_status spmv_grids(size_t shm, int* g_stream, int* g_pipe) {
 // warm-up, CUDA events, on the Krylov workspace): all compute the same sums in
 // the same order, so the choice changes the speed only.
 // GDSW_SPMV=stream|pipe|thread fixes it instead (for profilers).
-// The sliced ELL kernel against the CSR kernel for long rows, three launches
-// each (CUDA events, after one warm-up); GDSW_SPMV=sell forces the first, any
-// other value the second.
+// The sliced ELL kernel (4 or 8 entries of a lane in flight) against the CSR
+// kernel for long rows, three launches each (CUDA events, after one warm-up);
+// GDSW_SPMV=sell or sell8 forces the first, any other value the second.
 gdsw_status spmv_tune_long(Ctx* c, cudaStream_t s) {
   c->spmv_sell = 0;
   if (c->sell_ptr == nullptr) return GDSW_OK;
   const char* env = getenv("GDSW_SPMV");
-  if (env != nullptr) {                 // forced: the sliced ELL kernel only for "sell"
-    c->spmv_sell = std::string(env) == "sell";
+  if (env != nullptr) {                 // forced: the sliced ELL kernel only for "sell" / "sell8"
+    c->spmv_sell = std::string(env) == "sell" ? 1 : std::string(env) == "sell8" ? 2 : 0;
     return GDSW_OK;
   }
   cudaEvent_t e0, e1;
   GDSW_CK(cudaEventCreate(&e0));
   GDSW_CK(cudaEventCreate(&e1));
-  float t[2] = {0.f, 0.f};
+  float t[3] = {0.f, 0.f, 0.f};
   gdsw_status st = GDSW_OK;
-  for (int k = 0; k < 2 && st == GDSW_OK; ++k) {
+  for (int k = 0; k < 3 && st == GDSW_OK; ++k) {
     c->spmv_sell = k;
     st = launch_spmv(c, c->p, c->q, s, nullptr);
     if (st != GDSW_OK) break;
@@ -1369,7 +1381,10 @@ gdsw_status spmv_tune_long(Ctx* c, cudaStream_t s) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->spmv_sell = st == GDSW_OK && t[1] < t[0] ? 1 : 0;
+  int best = 0;
+  for (int k = 1; k < 3; ++k)
+    if (t[k] < t[best]) best = k;
+  c->spmv_sell = st == GDSW_OK ? best : 0;
   return st;
 }
 

@@ -1,6 +1,6 @@
-"""The SpMV for long rows from the sliced ELL copy (slices of 32 rows, entries
-column-major within a slice, 16-bit column offsets; a lane per row, no cross-lane
-sums) against the CSR kernel with lanes per row, both forced instead of chosen by
+"""The SpMV for long rows from the sliced ELL copy (slices of 8 rows, entries
+column-major within a slice, 16-bit column offsets; four lanes per row, 4 or 8 of a
+lane's entries in flight) against the CSR kernel with lanes per row, both forced instead of chosen by
 timing: each within 1e-13 of the CSR product on elasticity (81 entries per interior
 row, shorter rows on the boundary and a ragged last slice), and the Krylov solves
 that use it (PCG with the fused (p, Ap), GMRES, a batched handle whose stopped
@@ -45,7 +45,7 @@ def test_sell_matches_csr_product(make):
     for seed in range(2):
         x = np.random.default_rng(seed).uniform(-1, 1, prob.A.n)
         ref = ref_fn @ x
-        for kind in ("sell", "rows"):
+        for kind in ("sell", "sell8", "rows"):
             h = _with_spmv(kind, lambda: gpu_handle(prob, local_solver="ilu0"))
             y = gpu_spmv(h, x)
             assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max(), kind
