@@ -1529,8 +1529,8 @@ __global__ void k_coarse_slots(int nslots, const int* __restrict__ bcol, const T
 // indices; then r, the first two pulls and the block's shape; then the local
 // values and the Phi row, four columns at a time (each position's sum is still
 // formed in the order pulls, then Phi columns).
-template <class T, int NP>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_combine(
+template <class T, int NP, int CB>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CB > 4 ? 3 : 5) : (CB > 4 ? 2 : 3)) k_combine(
     int n, const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_dof,
     const int* __restrict__ pos_blk, const int* __restrict__ brow_ptr,
     const int* __restrict__ bcol_ptr, const int64_t* __restrict__ phi_off, const T* __restrict__ phi,
@@ -1580,12 +1580,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_combine(
       ph[j] = phi + (k[j] > 0 ? phi_off[b[j]] + (p + j * stride - p0[j]) : 0);
       kmax = max(kmax, k[j]);
     }
-    for (int u0 = 0; u0 < kmax; u0 += 4) {
-      T pv[NP][4], yv[NP][4];
+    for (int u0 = 0; u0 < kmax; u0 += CB) {
+      T pv[NP][CB], yv[NP][CB];
 #pragma unroll
       for (int j = 0; j < NP; ++j)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < CB; ++u) {
           const bool on = u0 + u < k[j];
           pv[j][u] = on ? ph[j][int64_t(u0 + u) * nr[j]] : T(0);
           yv[j][u] = on ? yb[c0[j] + u0 + u] : T(0);
@@ -1593,7 +1593,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_combine(
 #pragma unroll
       for (int j = 0; j < NP; ++j)
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < CB; ++u)
           if (u0 + u < k[j]) acc[j] = fma(pv[j][u], yv[j][u], acc[j]);
     }
     double a[NP];
@@ -2047,12 +2047,16 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const
 template <class T>
 gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated,
                            const BatchGate& gate) {
-  const int grid = std::max(1, std::min(c->combine_grid, (c->n + 255) / 256));
-  k_combine<T, 2><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,
-                                       c->phi_off, static_cast<const T*>(c->phi),
-                                       static_cast<const T*>(c->yslot), c->pull_ptr, c->pull_pos,
-                                       static_cast<const T*>(c->zloc), dots ? (c->flexible ? 2 : 1) : 0, c->red,
-                                       (dots || gated) ? c->ks : nullptr, gate);
+  const int grid = std::max(1, std::min(c->combine_cb == 8 ? c->combine_grid8 : c->combine_grid, (c->n + 255) / 256));
+#define GDSW_COMBINE_LAUNCH(CBB)                                                                            \
+  k_combine<T, 2, CBB><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,      \
+                                            c->phi_off, static_cast<const T*>(c->phi),                         \
+                                            static_cast<const T*>(c->yslot), c->pull_ptr, c->pull_pos,         \
+                                            static_cast<const T*>(c->zloc), dots ? (c->flexible ? 2 : 1) : 0,  \
+                                            c->red, (dots || gated) ? c->ks : nullptr, gate)
+  if (c->combine_cb == 8) GDSW_COMBINE_LAUNCH(8);
+  else GDSW_COMBINE_LAUNCH(4);
+#undef GDSW_COMBINE_LAUNCH
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -2187,6 +2191,44 @@ gdsw_status nodes_occupancy(Ctx* c, int S, int NT, int LPN, int* per_sm) {
   }
 #undef GDSW_NODES_OCC
   return GDSW_OK;
+}
+
+// The scatter-add with 4 and with 8 Phi columns per trip, three launches each
+// (CUDA events, after one warm-up, without the dots) on scratch vectors; the
+// faster is kept.  Both form every sum in the same order.
+gdsw_status tune_combine(Ctx* c) {
+  cudaStream_t s;
+  GDSW_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  double* buf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  gdsw_status st = GDSW_OK;
+  cudaError_t e = cudaMalloc(&buf, sizeof(double) * 2 * size_t(c->n));
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(double) * 2 * size_t(c->n), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float t[2] = {0.f, 0.f};
+  for (int k = 0; k < 2 && e == cudaSuccess && st == GDSW_OK; ++k) {
+    c->combine_cb = k == 0 ? 4 : 8;
+    st = c->fp32 ? launch_combine<float>(c, buf, buf + c->n, s, false, false, BatchGate{})
+                 : launch_combine<double>(c, buf, buf + c->n, s, false, false, BatchGate{});
+    e = cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && st == GDSW_OK; ++rep)
+      st = c->fp32 ? launch_combine<float>(c, buf, buf + c->n, s, false, false, BatchGate{})
+                   : launch_combine<double>(c, buf, buf + c->n, s, false, false, BatchGate{});
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t[k], e0, e1);
+  }
+  if (e != cudaSuccess && st == GDSW_OK) {
+    set_error("scatter-add tuning: %s", cudaGetErrorString(e));
+    st = GDSW_ERR_CUDA;
+  }
+  c->combine_cb = t[1] < t[0] ? 8 : 4;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (buf) cudaFree(buf);
+  cudaStreamDestroy(s);
+  return st;
 }
 
 // Measured choice of the pipelined local solve's shape: every ring depth that
@@ -2529,9 +2571,25 @@ gdsw_status apply_configure(Ctx* c) {
     int dev = 0, sms = kNumSMs, per_sm = 1;
     GDSW_CK(cudaGetDevice(&dev));
     GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (c->fp32) GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<float, 2>, 256, 0));
-    else GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<double, 2>, 256, 0));
+    int per_sm8 = 1;
+    if (c->fp32) {
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<float, 2, 4>, 256, 0));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, k_combine<float, 2, 8>, 256, 0));
+    } else {
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<double, 2, 4>, 256, 0));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, k_combine<double, 2, 8>, 256, 0));
+    }
     c->combine_grid = std::max(1, per_sm) * sms;
+    c->combine_grid8 = std::max(1, per_sm8) * sms;
+  }
+  // Phi columns per trip of the scatter-add: 4 (more CTAs per SM, for many
+  // positions per thread) or 8 (more loads in flight, for wide Phi blocks),
+  // timed; GDSW_COMBINE_CB=4 or 8 fixes it
+  c->combine_cb = 4;
+  if (const char* e = getenv("GDSW_COMBINE_CB")) {
+    c->combine_cb = atoi(e) == 8 ? 8 : 4;
+  } else if (c->opt.autotune && !c->stall_test && c->n > 0 && !c->mf) {
+    GDSW_TRY(tune_combine(c));
   }
   return GDSW_OK;
 }
