@@ -1,5 +1,5 @@
 """The level-scheduled local solve from node programs (Sec. V-B2 substitution with the
-ILU(0) factors of Sec. V-B3 on elasticity, three unknowns per node; 2, 4 or 8 lanes
+ILU(0) and IC(0) factors of Sec. V-B3 on elasticity, three unknowns per node; 2, 4 or 8 lanes
 per node sum the couplings of the node's three rows to other nodes at once, then one
 lane solves the three rows in order; 256 or 512 threads): forced by shape, it stays within the FP32
 tolerance of the oracle and of the record-streaming kernel, with pieces split inside
@@ -44,6 +44,7 @@ CASES = [
     ("elast_ragged7_ilu0", lambda: P.elasticity_problem(7, 3), dict(local="ilu0")),
     ("elast6_overlap2", lambda: P.elasticity_problem(6, 3), dict(local="ilu0", overlap=2)),
     ("elast8_rgdsw", lambda: P.elasticity_problem(8, 4), dict(local="ilu0", coarse="rgdsw")),
+    ("elast6_ic0", lambda: P.elasticity_problem(6, 2), dict(local="ic0")),
 ]
 
 
@@ -106,6 +107,21 @@ def test_node_programs_gmres_matches_oracle():
     _, io = O.gmres(M.spmv, M.apply, prob.b, tol=1e-8, restart=30)
     assert info.converged and info.true_relres <= 1e-8
     assert abs(info.iters - io.iters) <= 2, (info.iters, io.iters)
+    h.close()
+
+
+def test_node_programs_pcg_ic0_matches_oracle():
+    """IC(0) factors (Sec. V-B3) on elasticity through the node programs: PCG within
+    one iteration of the oracle's count and to the tolerance on the true residual."""
+    from oracle import gdsw_oracle as O
+    prob = P.elasticity_problem(8, 4)
+    h = handle_env(prob, {"GDSW_LOCAL_SHAPE": "3,256,3,4"}, local_solver="ic0", precision="fp32")
+    assert h.stats()["local_kernel"] == 7
+    M = oracle_for(prob, local="ic0")
+    x, info = gpu_solve(h, prob.b)
+    _, io = O.pcg(M.spmv, M.apply, prob.b)
+    assert info.converged and info.true_relres <= 1e-8
+    assert abs(info.iters - io.iters) <= 1, (info.iters, io.iters)
     h.close()
 
 
