@@ -1517,8 +1517,45 @@ __global__ void k_coarse_slots(int nslots, const int* __restrict__ bcol, const T
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) yb[i] = y[bcol[i]];
 }
 
+// u_p = (Phi y) at block-row position p, in the preconditioner's precision T,
+// eight Phi columns in flight per thread (each sum in column order).  It runs
+// on the coarse stream after the column-slot gather, beside the local solves,
+// so the scatter-add only adds u; positions of stopped problems are skipped.
+template <class T>
+__global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ pos_blk,
+                                                 const int* __restrict__ brow_ptr,
+                                                 const int* __restrict__ bcol_ptr,
+                                                 const int64_t* __restrict__ phi_off, const T* __restrict__ phi,
+                                                 const T* __restrict__ yb, T* __restrict__ ub,
+                                                 const KrylovScalars* __restrict__ ks, BatchGate gate) {
+  if (ks != nullptr && ks->done) return;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int b = pos_blk[p];
+    if (gate_blk_off(gate, b)) continue;
+    const int c0 = bcol_ptr[b], k = bcol_ptr[b + 1] - c0, p0 = brow_ptr[b], nr = brow_ptr[b + 1] - p0;
+    T acc = T(0);
+    if (k > 0) {
+      const T* ph = phi + phi_off[b] + (p - p0);
+      int u = 0;
+      for (; u + 8 <= k; u += 8) {
+        T pv[8], yv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          pv[q] = ph[int64_t(u + q) * nr];
+          yv[q] = yb[c0 + u + q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc = fma(pv[q], yv[q], acc);
+      }
+      for (; u < k; ++u) acc = fma(ph[int64_t(u) * nr], yb[c0 + u], acc);
+    }
+    ub[p] = acc;
+  }
+}
+
 // z_g = sum over subdomains containing g of (z_s)_g (ascending subdomain
-// order) + (Phi y)_g, one unknown per thread over the block-row positions
+// order) + (Phi y)_g (formed here, or with PROL read from k_prolong's output
+// by position), one unknown per thread over the block-row positions
 // (pos_blk gives the Phi block of each position), summed in the
 // preconditioner's precision T and widened once.  With `dots`, also
 // (r, z_new) and (r, z_old), reduced by the last CTA, which sets beta and
@@ -1529,12 +1566,13 @@ __global__ void k_coarse_slots(int nslots, const int* __restrict__ bcol, const T
 // indices; then r, the first two pulls and the block's shape; then the local
 // values and the Phi row, four columns at a time (each position's sum is still
 // formed in the order pulls, then Phi columns).
-template <class T, int NP, int CB>
+template <class T, int NP, int CB, bool PROL>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CB > 4 ? 3 : 5) : (CB > 4 ? 2 : 3)) k_combine(
     int n, const double* __restrict__ r, double* __restrict__ z, const int* __restrict__ brow_dof,
     const int* __restrict__ pos_blk, const int* __restrict__ brow_ptr,
     const int* __restrict__ bcol_ptr, const int64_t* __restrict__ phi_off, const T* __restrict__ phi,
-    const T* __restrict__ yb, const int* __restrict__ pull_ptr, const int* __restrict__ pull_pos,
+    const T* __restrict__ yb, const T* __restrict__ ub, const int* __restrict__ pull_ptr,
+    const int* __restrict__ pull_pos,
     const T* __restrict__ zloc, int dots, double* __restrict__ red, KrylovScalars* ks, BatchGate gate) {
   __shared__ double sh[32];
   if (ks != nullptr && ks->done) return;
@@ -1579,6 +1617,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CB > 4 ? 3 : 5) : (CB >
       for (int q = q0[j] + 2; q < q1[j]; ++q) acc[j] += zloc[pull_pos[q]];
       ph[j] = phi + (k[j] > 0 ? phi_off[b[j]] + (p + j * stride - p0[j]) : 0);
       kmax = max(kmax, k[j]);
+    }
+    if constexpr (PROL) {
+      // Phi y formed beside the local solves (k_prolong), one value per position
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        if (g[j] >= 0) acc[j] += ub[p + j * stride];
+      kmax = 0;
     }
     for (int u0 = 0; u0 < kmax; u0 += CB) {
       T pv[NP][CB], yv[NP][CB];
@@ -2045,17 +2090,31 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const
 }
 
 template <class T>
+gdsw_status launch_prolong(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const BatchGate& gate) {
+  if (!c->prolong) return GDSW_OK;
+  const int grid = std::max(1, std::min((c->n + 255) / 256, kNumSMs * 8));
+  k_prolong<T><<<grid, 256, 0, s>>>(c->n, c->pos_blk, c->brow_ptr, c->bcol_ptr, c->phi_off,
+                                    static_cast<const T*>(c->phi), static_cast<const T*>(c->yslot),
+                                    static_cast<T*>(c->ubuf), ks, gate);
+  GDSW_CK(cudaGetLastError());
+  return GDSW_OK;
+}
+
+template <class T>
 gdsw_status launch_combine(Ctx* c, const double* r, double* z, cudaStream_t s, bool dots, bool gated,
                            const BatchGate& gate) {
-  const int grid = std::max(1, std::min(c->combine_cb == 8 ? c->combine_grid8 : c->combine_grid, (c->n + 255) / 256));
-#define GDSW_COMBINE_LAUNCH(CBB)                                                                            \
-  k_combine<T, 2, CBB><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,      \
-                                            c->phi_off, static_cast<const T*>(c->phi),                         \
-                                            static_cast<const T*>(c->yslot), c->pull_ptr, c->pull_pos,         \
-                                            static_cast<const T*>(c->zloc), dots ? (c->flexible ? 2 : 1) : 0,  \
-                                            c->red, (dots || gated) ? c->ks : nullptr, gate)
-  if (c->combine_cb == 8) GDSW_COMBINE_LAUNCH(8);
-  else GDSW_COMBINE_LAUNCH(4);
+  const int grid = std::max(1, std::min(c->combine_cb == 8 && !c->prolong ? c->combine_grid8 : c->combine_grid,
+                                        (c->n + 255) / 256));
+#define GDSW_COMBINE_LAUNCH(CBB, PP)                                                                        \
+  k_combine<T, 2, CBB, PP><<<grid, 256, 0, s>>>(c->n, r, z, c->brow_dof, c->pos_blk, c->brow_ptr, c->bcol_ptr,  \
+                                                c->phi_off, static_cast<const T*>(c->phi),                     \
+                                                static_cast<const T*>(c->yslot), static_cast<const T*>(c->ubuf), \
+                                                c->pull_ptr, c->pull_pos, static_cast<const T*>(c->zloc),      \
+                                                dots ? (c->flexible ? 2 : 1) : 0, c->red,                      \
+                                                (dots || gated) ? c->ks : nullptr, gate)
+  if (c->prolong) GDSW_COMBINE_LAUNCH(4, true);
+  else if (c->combine_cb == 8) GDSW_COMBINE_LAUNCH(8, false);
+  else GDSW_COMBINE_LAUNCH(4, false);
 #undef GDSW_COMBINE_LAUNCH
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
@@ -2076,6 +2135,7 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
     GDSW_CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
     GDSW_TRY(launch_phiT<T>(c, r, c->aux_stream, ks, gate));
     GDSW_TRY(launch_coarse(c, c->aux_stream, ks, gate));
+    GDSW_TRY(launch_prolong<T>(c, c->aux_stream, ks, gate));
     GDSW_CK(cudaEventRecord(c->ev_join, c->aux_stream));
     GDSW_TRY(launch_local<T>(c, r, s, ks, gate));
     GDSW_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -2088,6 +2148,7 @@ gdsw_status apply_t(Ctx* c, const double* r, double* z, cudaStream_t s, bool dot
   GDSW_TRY(launch_phiT<T>(c, r, s, ks, gate));
   if (ev) GDSW_CK(cudaEventRecord(ev[2], s));
   GDSW_TRY(launch_coarse(c, s, ks, gate));
+  GDSW_TRY(launch_prolong<T>(c, s, ks, gate));
   if (ev) GDSW_CK(cudaEventRecord(ev[3], s));
   GDSW_TRY(launch_combine<T>(c, r, z, s, dots, gated, gate));
   if (ev) GDSW_CK(cudaEventRecord(ev[4], s));
@@ -2573,14 +2634,23 @@ gdsw_status apply_configure(Ctx* c) {
     GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int per_sm8 = 1;
     if (c->fp32) {
-      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<float, 2, 4>, 256, 0));
-      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, k_combine<float, 2, 8>, 256, 0));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<float, 2, 4, false>, 256, 0));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, k_combine<float, 2, 8, false>, 256, 0));
     } else {
-      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<double, 2, 4>, 256, 0));
-      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, k_combine<double, 2, 8>, 256, 0));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<double, 2, 4, false>, 256, 0));
+      GDSW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, k_combine<double, 2, 8, false>, 256, 0));
     }
     c->combine_grid = std::max(1, per_sm) * sms;
     c->combine_grid8 = std::max(1, per_sm8) * sms;
+  }
+  // Phi y beside the local solves (k_prolong on the coarse stream, one value
+  // per block-row position) whenever there is a coarse space; the scatter-add
+  // then only adds it.  GDSW_PROLONG=0 keeps the product in the scatter-add.
+  c->prolong = 0;
+  if (c->n0 > 0 && !(getenv("GDSW_PROLONG") && getenv("GDSW_PROLONG")[0] == '0')) {
+    if (c->fp32) GDSW_TRY(dalloc(c, reinterpret_cast<float**>(&c->ubuf), c->n));
+    else GDSW_TRY(dalloc(c, reinterpret_cast<double**>(&c->ubuf), c->n));
+    c->prolong = 1;
   }
   // Phi columns per trip of the scatter-add: 4 (more CTAs per SM, for many
   // positions per thread) or 8 (more loads in flight, for wide Phi blocks),
@@ -2588,7 +2658,7 @@ gdsw_status apply_configure(Ctx* c) {
   c->combine_cb = 4;
   if (const char* e = getenv("GDSW_COMBINE_CB")) {
     c->combine_cb = atoi(e) == 8 ? 8 : 4;
-  } else if (c->opt.autotune && !c->stall_test && c->n > 0 && !c->mf) {
+  } else if (c->opt.autotune && !c->stall_test && c->n > 0 && !c->mf && !c->prolong) {
     GDSW_TRY(tune_combine(c));
   }
   return GDSW_OK;

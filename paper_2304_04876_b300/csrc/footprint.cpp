@@ -248,6 +248,8 @@ gdsw_status estimate_footprint(const Plan& P, const gdsw_csr* A, const gdsw_opti
     // inverse in scratch and rounds it once (plus c in FP32)
     R += arr(C.n0, 4) + arr(P.nprob + 1, 4) + arr(P.nprob + 1, 8) + arr(a0, v) + arr(C.phi_len, v) +
          (low ? arr(C.n0, 4) : 0);
+    // Phi y by block-row position, formed beside the local solves
+    if (C.n0 > 0) R += arr(n, v);
     S += arr(C.phi_len, 8) + arr(a0, 8) + (low ? arr(a0, 8) : 0) + arr((maxb + 63) / 64 * 64 * maxb, 8) +
          std::min<int64_t>(band * 8, int64_t(6) << 30) + 8 * arr(nsub + 1, 8) + 6 * arr(n, 4) + 2 * arr(C.n0, 4);
   }

@@ -490,6 +490,8 @@ struct Ctx {
   int combine_grid = 0;              // resident CTAs of the scatter-add (grid-stride), 4 columns per trip
   int combine_grid8 = 0;             // the same with 8 Phi columns per trip
   int combine_cb = 4;                // Phi columns per trip of the scatter-add (4 or 8)
+  int prolong = 0;                   // 1: Phi y formed on the coarse stream (k_prolong) into ubuf
+  void* ubuf = nullptr;              // n values of Phi y by block-row position (apply precision)
   int max_bcols = 0;
   int n_slots = 0;
   double* partial = nullptr;     // per (block, column) slot
