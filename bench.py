@@ -109,6 +109,11 @@ def apply_bytes(st: dict, vbytes: int, fbytes: int = None) -> dict:
     coarse = st.get("a0_entries", n0 * n0) * 8 + n0 * 8 * 3 if n0 else 0
     combine = (sum_m * 4 + (n + 1) * 4 + sum_m * vbytes + n * 4 + st["nnz_phi"] * vbytes
                + n * 8 + nblk * 16)
+    if n0 and st.get("phi_beside_local"):
+        # Phi y formed on the coarse stream (Phi read, u written) and added by the
+        # scatter-add (u read)
+        coarse += st["nnz_phi"] * vbytes + n * vbytes
+        combine += n * vbytes - st["nnz_phi"] * vbytes
     return {"local": local, "phiT": phit, "coarse": coarse, "combine": combine}
 
 
@@ -131,9 +136,10 @@ def iteration_work(st: dict, vb: int, fb: int, flexible: bool) -> dict:
         "xupdate": {"bytes": 24 * n, "fma64": n},
         "local": {"bytes": ab["local"], "fma64": tri if fp64_pre and not st["dense_local"] else 0},
         "phiT": {"bytes": ab["phiT"], "fma64": st["nnz_phi"] if fp64_pre else 0},
-        "coarse": {"bytes": ab["coarse"], "fma64": st.get("a0_entries", st["n0"] ** 2)},
+        "coarse": {"bytes": ab["coarse"], "fma64": st.get("a0_entries", st["n0"] ** 2)
+                   + (st["nnz_phi"] if fp64_pre and st.get("phi_beside_local") else 0)},
         "combine": {"bytes": ab["combine"] + 8 * dots * n,
-                    "fma64": dots * n + (st["nnz_phi"] if fp64_pre else 0)},
+                    "fma64": dots * n + (st["nnz_phi"] if fp64_pre and not st.get("phi_beside_local") else 0)},
         "pupdate": {"bytes": 24 * n, "fma64": n},
     }
 

@@ -191,6 +191,10 @@ typedef struct {
                              iteration loop as one cooperative kernel, for
                              one problem with dense exact local solves and at
                              most 128 coarse columns); 0 when not used       */
+  int64_t phi_beside_local; /* 1 when Phi y (Eq. 1's prolongation) is formed on
+                             the coarse stream beside the local solves and
+                             the scatter-add only adds it; 0 when the
+                             scatter-add forms it                            */
 } gdsw_stats;
 
 typedef struct gdsw_ctx* gdsw_handle;

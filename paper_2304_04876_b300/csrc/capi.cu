@@ -222,6 +222,7 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
   S.local_kernel = c->mf ? 1 : o.local_solver == GDSW_LOCAL_EXACT ? 0 : c->jac_mode > 0 ? 5
                  : c->node_stages > 0 ? 7 : c->step_depth > 0 ? 6 : c->rec_stages > 0 ? (c->rec_sf ? 4 : 3) : 2;
   S.pcg_persistent_grid = c->persist_grid;
+  S.phi_beside_local = c->prolong;
   S.setup_seconds = now_s() - t0;
   *out = h;
   return GDSW_OK;
