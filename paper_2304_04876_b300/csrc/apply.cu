@@ -2644,10 +2644,21 @@ gdsw_status apply_configure(Ctx* c) {
     c->combine_grid8 = std::max(1, per_sm8) * sms;
   }
   // Phi y beside the local solves (k_prolong on the coarse stream, one value
-  // per block-row position) whenever there is a coarse space; the scatter-add
-  // then only adds it.  GDSW_PROLONG=0 keeps the product in the scatter-add.
+  // per block-row position), the scatter-add then only adding it: when the
+  // local solves leave SMs idle (fewer subdomains than SMs, one CTA each) and
+  // the problem is large enough that one more launch per apply does not
+  // matter (a fixed rule, so a handle's rounding never depends on a timing).
+  // GDSW_PROLONG=1 or 0 forces it on or off.
   c->prolong = 0;
-  if (c->n0 > 0 && !(getenv("GDSW_PROLONG") && getenv("GDSW_PROLONG")[0] == '0')) {
+  bool want_prolong = false;
+  {
+    int dev = 0, sms = kNumSMs;
+    GDSW_CK(cudaGetDevice(&dev));
+    GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    want_prolong = c->nsub < sms && c->n >= 65536;
+    if (const char* e = getenv("GDSW_PROLONG")) want_prolong = e[0] == '1';
+  }
+  if (c->n0 > 0 && want_prolong) {
     if (c->fp32) GDSW_TRY(dalloc(c, reinterpret_cast<float**>(&c->ubuf), c->n));
     else GDSW_TRY(dalloc(c, reinterpret_cast<double**>(&c->ubuf), c->n));
     c->prolong = 1;
