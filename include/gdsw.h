@@ -186,7 +186,7 @@ typedef struct {
                              blocks resident in shared memory, 6 row
                              programs with per-thread prefetch (FP32, rows of
                              at most 3 entries), 7 node programs (FP32, three
-                             unknowns per node, eight threads per node)      */
+                             unknowns per node, 2, 4 or 8 lanes per node)    */
   int64_t pcg_persistent_grid; /* CTAs of the persistent PCG launch (the whole
                              iteration loop as one cooperative kernel, for
                              one problem with dense exact local solves and at
