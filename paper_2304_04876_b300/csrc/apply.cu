@@ -1260,10 +1260,58 @@ __device__ __forceinline__ T dense_row_dot(const T* __restrict__ Ai, const T* rs
 // row's loads are the only chain a warp waits on (more CTAs each gather r_s).
 constexpr int kDenseRows = 8;
 
-// Exact local solver: z_s = A_s^-1 r_s with the stored dense inverse
-// (symmetric, so row i is read contiguously).  Grid (row chunks of 32, nsub).
+// Four consecutive rows of a dense inverse times r_s (in shared memory) by a
+// warp: one partial sum per row and lane, each r_s value read once for the
+// four rows (two columns per trip, eight loads of the rows in flight), then a
+// transposing butterfly: after the exchanges at distance 16 and 8 each lane
+// keeps one row's sums, and three more leave row q's total in lanes 8q..8q+7
+// -- six additions for the four rows where a shuffle tree per row takes five
+// each (FP64 additions issue at the FMA rate).  Rows from nr on are not read.
 template <class T>
-__global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ r,
+__device__ __forceinline__ T dense_rows4_dot(const T* __restrict__ A, const T* rs, int m, int nr, int lane) {
+  T acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = T(0);
+  int j = lane;
+  for (; j + 32 < m; j += 64) {
+    const T x0 = rs[j], x1 = rs[j + 32];
+    T a[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = q < nr ? A[int64_t(q) * m + j] : T(0);
+      a[4 + q] = q < nr ? A[int64_t(q) * m + j + 32] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(a[q], x0, acc[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(a[4 + q], x1, acc[q]);
+  }
+  if (j < m) {
+    const T x0 = rs[j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(q < nr ? A[int64_t(q) * m + j] : T(0), x0, acc[q]);
+  }
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  T b = h16 ? acc[2] : acc[0];
+  T e = h16 ? acc[3] : acc[1];
+  b += __shfl_xor_sync(0xffffffffu, h16 ? acc[0] : acc[2], 16);
+  e += __shfl_xor_sync(0xffffffffu, h16 ? acc[1] : acc[3], 16);
+  T f = h8 ? e : b;
+  f += __shfl_xor_sync(0xffffffffu, h8 ? b : e, 8);
+  f += __shfl_xor_sync(0xffffffffu, f, 4);
+  f += __shfl_xor_sync(0xffffffffu, f, 2);
+  f += __shfl_xor_sync(0xffffffffu, f, 1);
+  return f;
+}
+
+// Rows of one subdomain per CTA of the dense local solve: four warps of four
+// rows each.
+constexpr int kDenseCtaRows = 16;
+
+// Exact local solver: z_s = A_s^-1 r_s with the stored dense inverse
+// (symmetric, so row i is read contiguously).  Grid (row chunks of 16, nsub).
+template <class T>
+__global__ void __launch_bounds__(128) k_local_dense(const double* __restrict__ r,
                                                      const int* __restrict__ om_ptr,
                                                      const int* __restrict__ om_dofs,
                                                      const T* __restrict__ ainv,
@@ -1276,18 +1324,16 @@ __global__ void __launch_bounds__(256) k_local_dense(const double* __restrict__ 
   const int s = blockIdx.y;
   if (gate_sub_off(gate, s)) return;
   const int base = om_ptr[s], m = om_ptr[s + 1] - base;
-  const int row0 = blockIdx.x * kDenseRows;
+  const int row0 = blockIdx.x * kDenseCtaRows;
   if (row0 >= m) return;
   gather_sub(r, om_dofs, base, m, rs, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const T* A = ainv + ainv_off[s];
-  for (int rr = w; rr < kDenseRows; rr += 8) {
-    const int i = row0 + rr;
-    if (i >= m) break;
-    const T acc = dense_row_dot(A + int64_t(i) * m, rs, m, lane);
-    if (lane == 0) zloc[base + i] = acc;
-  }
+  const int i = row0 + 4 * w;
+  if (i >= m) return;
+  const int nr = min(4, m - i);
+  const T v = dense_rows4_dot(ainv + ainv_off[s] + int64_t(i) * m, rs, m, nr, lane);
+  if ((lane & 7) == 0 && (lane >> 3) < nr) zloc[base + i + (lane >> 3)] = v;
 }
 
 // Partial products Phi_b^T r_b.  The first n_cta chunks (more than 256 rows,
@@ -1923,8 +1969,8 @@ gdsw_status launch_local(Ctx* c, const double* r, cudaStream_t s, const KrylovSc
   if (c->mf) return mf_launch_local(c, r, s, ks);
   if (c->opt.local_solver == GDSW_LOCAL_EXACT) {
     const size_t shm = size_t(c->max_m) * sizeof(T);
-    dim3 grid((c->max_m + kDenseRows - 1) / kDenseRows, c->nsub);
-    k_local_dense<T><<<grid, 256, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
+    dim3 grid((c->max_m + kDenseCtaRows - 1) / kDenseCtaRows, c->nsub);
+    k_local_dense<T><<<grid, 128, shm, s>>>(r, c->om_ptr, c->om_dofs, static_cast<const T*>(c->ainv),
                                             c->ainv_off, zl, ks, gate);
   } else if (c->node_stages > 0) {
     // node programs (FP32, three unknowns per node)
