@@ -195,6 +195,9 @@ typedef struct {
                              the coarse stream beside the local solves and
                              the scatter-add only adds it; 0 when the
                              scatter-add forms it                            */
+  int64_t phiT_wide;        /* 1 when Phi^T r takes eight columns at a time over
+                             each chunk's rows (wide coarse blocks), 0 when
+                             a warp per column                               */
 } gdsw_stats;
 
 typedef struct gdsw_ctx* gdsw_handle;

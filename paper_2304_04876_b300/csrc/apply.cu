@@ -1339,9 +1339,10 @@ __global__ void __launch_bounds__(128) k_local_dense(const double* __restrict__ 
 // Partial products Phi_b^T r_b.  The first n_cta chunks (more than 256 rows,
 // at most 1024, of a block) take one CTA each: the chunk's r is staged in
 // shared memory, then each warp takes whole columns, which are contiguous in
-// the column-major panel.  The small chunks (interface components) take one
-// warp each, eight per CTA, with shuffle sums; their CTAs are placed first in
-// the grid.
+// the column-major panel, or (WIDE, for handles whose blocks are wide) the
+// warps split the rows and take eight columns at a time.  The small chunks
+// (interface components) take one warp each, eight per CTA, with shuffle
+// sums; their CTAs are placed first in the grid.
 template <class T>
 __device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict__ r,
                                                 const int* __restrict__ brow_ptr,
@@ -1395,8 +1396,33 @@ __device__ __forceinline__ void phiT_warp_chunk(int q, const double* __restrict_
   }
 }
 
+// Sums of eight values over a warp's lanes, transposed: the exchanges at
+// distance 16, 8 and 4 each halve the values a lane keeps (4 + 2 + 1
+// additions), two more complete the sums, and lanes 4q..4q+3 return the sum of
+// value q.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chunks, int n_cta, const double* __restrict__ r,
+__device__ __forceinline__ T phiT_butterfly8(const T (&v)[8], int lane) {
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0;
+  T a[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T keep = h16 ? v[4 + j] : v[j], give = h16 ? v[j] : v[4 + j];
+    a[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+  }
+  T c[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T keep = h8 ? a[2 + j] : a[j], give = h8 ? a[j] : a[2 + j];
+    c[j] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+  }
+  T e = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h4 ? c[0] : c[1], 4);
+  e += __shfl_xor_sync(0xffffffffu, e, 2);
+  e += __shfl_xor_sync(0xffffffffu, e, 1);
+  return e;
+}
+
+template <class T, bool WIDE>
+__global__ void __launch_bounds__(256, WIDE || sizeof(T) == 8 ? 4 : 6) k_phiT(int n_chunks, int n_cta, const double* __restrict__ r,
                                               const int* __restrict__ brow_ptr,
                                               const int* __restrict__ brow_dof,
                                               const int* __restrict__ bcol_ptr,
@@ -1409,6 +1435,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
                                               double* __restrict__ partial,
                                               const KrylovScalars* __restrict__ ks, BatchGate gate) {
   __shared__ T rs[kPhiChunkRows];          // r of a chunk
+  __shared__ T red[WIDE ? 8 : 1][8];       // the warps' sums of eight columns
   if (ks != nullptr && ks->done) return;
   // the small chunks' CTAs come first in the grid, so that their longer
   // chains of dependent loads overlap the big chunks instead of trailing them
@@ -1440,34 +1467,72 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_phiT(int n_chun
       if (g[j] >= 0) rs[ib + 256 * j] = narrow_bits<T>(rb[j]);
   }
   __syncthreads();
-  // one warp per column: the column is contiguous in the block's panel
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int u = w; u < k; u += 8) {
-    const T* col = phi + phi_off[b] + int64_t(u) * nr + i0;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    int i = lane;
-    // software-pipelined: the next four values of the column are loaded before
-    // the current four are used
-    if (i + 96 < rows) {
-      T cv[4];
+  if constexpr (WIDE) {
+    // eight columns at a time: warp w takes rows w * 32 + lane + 256 j, two
+    // rows per trip with the eight columns' values of both loaded together
+    // (sixteen coalesced loads in flight per lane, r read once per row); then
+    // a transposing butterfly leaves column q's warp sum in lanes 4q..4q+3 and
+    // the eight warps' sums are added in warp order
+    const T* P0 = phi + phi_off[b] + i0;
+    for (int c0 = 0; c0 < k; c0 += 8) {
+      const int kc = min(8, k - c0);
+      T acc[8];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) cv[j] = col[i + 32 * j];
-      for (; i + 128 + 96 < rows; i += 128) {
-        T nx[4];
+      for (int u = 0; u < 8; ++u) acc[u] = T(0);
+      for (int i = w * 32 + lane; i < rows; i += 512) {
+        const bool two = i + 256 < rows;
+        const T x0 = rs[i], x1 = two ? rs[i + 256] : T(0);
+        T a0[8], a1[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) nx[j] = col[i + 128 + 32 * j];
+        for (int u = 0; u < 8; ++u) {
+          const T* col = P0 + int64_t(c0 + u) * nr;
+          a0[u] = u < kc ? col[i] : T(0);
+          a1[u] = u < kc && two ? col[i + 256] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = fma(a1[u], x1, fma(a0[u], x0, acc[u]));
+      }
+      const T v = phiT_butterfly8(acc, lane);
+      if ((lane & 3) == 0) red[w][lane >> 2] = v;
+      __syncthreads();
+      if (threadIdx.x < kc) {
+        T t = red[0][threadIdx.x];
+#pragma unroll
+        for (int ww = 1; ww < 8; ++ww) t += red[ww][threadIdx.x];
+        partial[chunk_slot[q] + c0 + threadIdx.x] = double(t);
+      }
+      __syncthreads();
+    }
+  } else {
+    // one warp per column: the column is contiguous in the block's panel
+    for (int u = w; u < k; u += 8) {
+      const T* col = phi + phi_off[b] + int64_t(u) * nr + i0;
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      int i = lane;
+      // software-pipelined: the next four values of the column are loaded
+      // before the current four are used
+      if (i + 96 < rows) {
+        T cv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cv[j] = col[i + 32 * j];
+        for (; i + 128 + 96 < rows; i += 128) {
+          T nx[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) nx[j] = col[i + 128 + 32 * j];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j] = fma(cv[j], rs[i + 32 * j], acc[j]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cv[j] = nx[j];
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[j] = fma(cv[j], rs[i + 32 * j], acc[j]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cv[j] = nx[j];
+        i += 128;
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fma(cv[j], rs[i + 32 * j], acc[j]);
-      i += 128;
+      for (; i < rows; i += 32) acc[0] = fma(col[i], rs[i], acc[0]);
+      const T t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+      if (lane == 0) partial[chunk_slot[q] + u] = double(t);
     }
-    for (; i < rows; i += 32) acc[0] = fma(col[i], rs[i], acc[0]);
-    const T t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
-    if (lane == 0) partial[chunk_slot[q] + u] = double(t);
   }
 }
 
@@ -2105,10 +2170,14 @@ gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovSca
   if (c->n0 == 0) return GDSW_OK;
   if (c->n_chunks == 0) return GDSW_OK;
   const int grid = c->n_cta_chunks + (c->n_chunks - c->n_cta_chunks + 7) / 8;
-  k_phiT<T><<<grid, 256, 0, s>>>(c->n_chunks, c->n_cta_chunks, r, c->brow_ptr, c->brow_dof, c->bcol_ptr,
-                                 c->phi_off,
-                                        static_cast<const T*>(c->phi), c->chunk_blk, c->chunk_r0,
-                                        c->chunk_r1, c->chunk_slot, c->partial, ks, gate);
+  if (c->phiT_wide)
+    k_phiT<T, true><<<grid, 256, 0, s>>>(c->n_chunks, c->n_cta_chunks, r, c->brow_ptr, c->brow_dof, c->bcol_ptr,
+                                         c->phi_off, static_cast<const T*>(c->phi), c->chunk_blk, c->chunk_r0,
+                                         c->chunk_r1, c->chunk_slot, c->partial, ks, gate);
+  else
+    k_phiT<T, false><<<grid, 256, 0, s>>>(c->n_chunks, c->n_cta_chunks, r, c->brow_ptr, c->brow_dof, c->bcol_ptr,
+                                          c->phi_off, static_cast<const T*>(c->phi), c->chunk_blk, c->chunk_r0,
+                                          c->chunk_r1, c->chunk_slot, c->partial, ks, gate);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;
 }
@@ -2690,10 +2759,13 @@ gdsw_status apply_configure(Ctx* c) {
     c->combine_grid8 = std::max(1, per_sm8) * sms;
   }
   // Phi y beside the local solves (k_prolong on the coarse stream, one value
-  // per block-row position), the scatter-add then only adding it: when the
-  // local solves leave SMs idle (fewer subdomains than SMs, one CTA each) and
-  // the problem is large enough that one more launch per apply does not
-  // matter (a fixed rule, so a handle's rounding never depends on a timing).
+  // per block-row position), the scatter-add then only adding it: for one
+  // problem (not a batch, whose members stop at different iterations) when
+  // the local solves leave SMs idle (fewer subdomains than SMs, one CTA each)
+  // and the problem is large enough that one more launch per apply does not
+  // matter (n >= 65,536), or when the problem is so large (n >= 2^20) that
+  // the local solves outlast the coarse branch with the product added to it
+  // (a fixed rule, so a handle's rounding never depends on a timing).
   // GDSW_PROLONG=1 or 0 forces it on or off.
   c->prolong = 0;
   bool want_prolong = false;
@@ -2701,7 +2773,7 @@ gdsw_status apply_configure(Ctx* c) {
     int dev = 0, sms = kNumSMs;
     GDSW_CK(cudaGetDevice(&dev));
     GDSW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    want_prolong = c->nsub < sms && c->n >= 65536;
+    want_prolong = c->nprob == 1 && (c->nsub < sms ? c->n >= 65536 : c->n >= (1 << 20));
     if (const char* e = getenv("GDSW_PROLONG")) want_prolong = e[0] == '1';
   }
   if (c->n0 > 0 && want_prolong) {

@@ -223,6 +223,7 @@ gdsw_status setup_from_plan(const Plan& P, const gdsw_csr* A, const double* Z, i
                  : c->node_stages > 0 ? 7 : c->step_depth > 0 ? 6 : c->rec_stages > 0 ? (c->rec_sf ? 4 : 3) : 2;
   S.pcg_persistent_grid = c->persist_grid;
   S.phi_beside_local = c->prolong;
+  S.phiT_wide = c->phiT_wide ? 1 : 0;
   S.setup_seconds = now_s() - t0;
   *out = h;
   return GDSW_OK;

@@ -487,6 +487,7 @@ struct Ctx {
   int* pos_blk = nullptr;
   int* chunk_blk = nullptr; int* chunk_r0 = nullptr; int* chunk_r1 = nullptr; int* chunk_slot = nullptr;
   int n_chunks = 0, n_cta_chunks = 0;
+  bool phiT_wide = false;            // Phi^T r: eight columns at a time over a chunk's rows
   int combine_grid = 0;              // resident CTAs of the scatter-add (grid-stride), 4 columns per trip
   int combine_grid8 = 0;             // the same with 8 Phi columns per trip
   int combine_cb = 4;                // Phi columns per trip of the scatter-add (4 or 8)

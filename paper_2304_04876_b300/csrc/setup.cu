@@ -1375,6 +1375,17 @@ gdsw_status numeric_setup(Ctx* c, const Plan& P, const gdsw_csr* A, const double
   GDSW_TRY(upload(c, &c->chunk_slot, C.chunk_slot, s));
   c->n_chunks = static_cast<int>(C.chunk_blk.size());
   c->n_cta_chunks = C.n_cta_chunks;
+  // Phi^T r by eight columns at a time over each chunk's rows where the CTA
+  // chunks' blocks are wide (48 columns or more on average: rigid-body coarse
+  // spaces of elasticity), else by a warp per column (a fixed rule, so the
+  // rounding never depends on a timing); GDSW_PHIT=wide or cols forces one
+  {
+    int64_t kc_sum = 0;
+    for (int q = 0; q < C.n_cta_chunks; ++q)
+      kc_sum += C.bcol_ptr[C.chunk_blk[q] + 1] - C.bcol_ptr[C.chunk_blk[q]];
+    c->phiT_wide = C.n_cta_chunks > 0 && kc_sum >= int64_t(48) * C.n_cta_chunks;
+    if (const char* e = getenv("GDSW_PHIT")) c->phiT_wide = e[0] == 'w';
+  }
   c->n_slots = C.n_slots;
   c->stats.nnz_phi = C.phi_len;
   c->max_bcols = 0;

@@ -73,7 +73,8 @@ class Stats(C.Structure):
         "device_bytes", "n_problems", "a0_entries", "local_stages", "local_threads", "mf_supernodes", "mf_levels")] + [("setup_seconds", C.c_double), ("setup_phase_seconds", C.c_double * 8),
                                                           ("local_kernel", C.c_int64),
                                                           ("pcg_persistent_grid", C.c_int64),
-                                                          ("phi_beside_local", C.c_int64)]
+                                                          ("phi_beside_local", C.c_int64),
+                                                          ("phiT_wide", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "setup_phase_seconds"}

@@ -98,7 +98,7 @@ def test_structs_match_header(lib):
     assert fields == [f for f, _ in G.Options._fields_]
     assert C.sizeof(G.Options) == 14 * 4 + 8 + 8
     assert C.sizeof(G.CSRStruct) == 40          # n, three pointers, mem (padded)
-    assert C.sizeof(G.Stats) == 24 * 8 + 9 * 8 + 3 * 8   # ... setup times, local_kernel, persistent grid, Phi y
+    assert C.sizeof(G.Stats) == 24 * 8 + 9 * 8 + 4 * 8   # ... setup times, local_kernel, persistent grid, Phi y, Phi^T r
 
 
 def test_batch_rejects_bad_members_on_host(lib):

@@ -2,8 +2,8 @@
 (k_prolong, one value per block-row position that the scatter-add adds) against the
 product formed inside the scatter-add, both forced: the applies agree to rounding
 (FP64 1e-13, FP32 1e-6) and with the oracle, the Krylov solves take the same number of
-iterations, a batched handle skips a stopped member's positions, and the stats report
-where the product was formed."""
+iterations, a batched handle skips a stopped member's positions, the stats report
+where the product was formed, and without the override the fixed rule decides."""
 import os
 
 import numpy as np
@@ -95,3 +95,24 @@ def test_prolongation_in_a_batched_handle():
         h.close()
     assert all(abs(a - c) <= 1 for a, c in zip(out["1"][1], out["0"][1]))
     assert relerr(out["1"][0], out["0"][0]) <= 1e-8
+
+
+def test_prolongation_default_rule():
+    """Without GDSW_PROLONG: beside the local solves for one problem with fewer
+    subdomains than SMs and n >= 65,536, or with n >= 2^20; in the scatter-add for
+    smaller problems and for a batch."""
+    from paper_2304_04876_b300 import gdsw as G
+    assert os.environ.get("GDSW_PROLONG") is None
+    for make, want in ((lambda: P.poisson_problem(12, 4), 0),        # n = 1,728
+                       (lambda: P.poisson_problem(48, 12), 1),       # 64 subdomains, n = 110,592
+                       (lambda: P.poisson_problem(48, 6), 0),        # 512 subdomains, n = 110,592
+                       (lambda: P.poisson_problem(102, 17), 1)):     # 216 subdomains, n = 1,061,208
+        prob = make()
+        h = gpu_handle(prob, local_solver="ic0", precision="fp32")
+        assert h.stats()["phi_beside_local"] == want, prob.name
+        h.close()
+    # 16 subdomains, ~150 K unknowns: beside the local solves were it one problem
+    mem = P.diffusion_batch(2, seed=2, nmin=40, nmax=44, smin=20, smax=22)
+    h = G.Handle.batch([(m.A, m.part, None) for m in mem], local_solver="ic0")
+    assert h.stats()["phi_beside_local"] == 0
+    h.close()
