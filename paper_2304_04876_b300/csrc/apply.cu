@@ -1629,16 +1629,21 @@ __global__ void k_coarse_slots(int nslots, const int* __restrict__ bcol, const T
 }
 
 // u_p = (Phi y) at block-row position p, in the preconditioner's precision T,
-// eight Phi columns in flight per thread (each sum in column order).  It runs
-// on the coarse stream after the column-slot gather, beside the local solves,
-// so the scatter-add only adds u; positions of stopped problems are skipped.
+// eight Phi columns in flight per thread (each sum in column order), y read
+// through the block-column map `bcol` (the values the column-slot gather
+// copies, so the sums are the same), or with bcol null from the slots `y`
+// themselves (wide blocks, whose many map reads per position cost more than
+// the gather).  It runs on the coarse stream after the GEMV, beside the local
+// solves, so the scatter-add only adds u; positions of stopped problems are
+// skipped.
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ pos_blk,
                                                  const int* __restrict__ brow_ptr,
                                                  const int* __restrict__ bcol_ptr,
                                                  const int64_t* __restrict__ phi_off, const T* __restrict__ phi,
-                                                 const T* __restrict__ yb, T* __restrict__ ub,
-                                                 const KrylovScalars* __restrict__ ks, BatchGate gate) {
+                                                 const int* __restrict__ bcol, const T* __restrict__ y,
+                                                 T* __restrict__ ub, const KrylovScalars* __restrict__ ks,
+                                                 BatchGate gate) {
   if (ks != nullptr && ks->done) return;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int b = pos_blk[p];
@@ -1650,15 +1655,18 @@ __global__ void __launch_bounds__(256) k_prolong(int n, const int* __restrict__ 
       int u = 0;
       for (; u + 8 <= k; u += 8) {
         T pv[8], yv[8];
+        int cj[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           pv[q] = ph[int64_t(u + q) * nr];
-          yv[q] = yb[c0 + u + q];
+          cj[q] = bcol != nullptr ? bcol[c0 + u + q] : c0 + u + q;
         }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) yv[q] = y[cj[q]];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc = fma(pv[q], yv[q], acc);
       }
-      for (; u < k; ++u) acc = fma(ph[int64_t(u) * nr], yb[c0 + u], acc);
+      for (; u < k; ++u) acc = fma(ph[int64_t(u) * nr], y[bcol != nullptr ? bcol[c0 + u] : c0 + u], acc);
     }
     ub[p] = acc;
   }
@@ -2182,6 +2190,11 @@ gdsw_status launch_phiT(Ctx* c, const double* r, cudaStream_t s, const KrylovSca
   return GDSW_OK;
 }
 
+// Phi y beside the local solves reads y through the block-column map where
+// the blocks are narrow (no slot gather launched); a fixed rule, as the form
+// of Phi^T r it follows.
+inline bool prolong_via_map(const Ctx* c) { return c->prolong && !c->phiT_wide; }
+
 gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const BatchGate& gate) {
   if (c->n0 == 0) return GDSW_OK;
   k_coarse_c<<<(c->n0 + 255) / 256, 256, 0, s>>>(c->n0, c->cs_ptr, c->cs_idx, c->partial, c->cvec, c->cvec32,
@@ -2193,7 +2206,9 @@ gdsw_status launch_coarse(Ctx* c, cudaStream_t s, const KrylovScalars* ks, const
   else
     k_coarse_gemv<double><<<grid, 256, 0, s>>>(c->n0, c->A0inv, c->coarse_prob, c->prob_c0, c->a0_off,
                                                c->cvec, c->yvec, c->yvec32, ks, gate);
-  if (c->n_bslots > 0) {
+  // y at every block-column slot, for the scatter-add's Phi y or for
+  // k_prolong on wide blocks
+  if (c->n_bslots > 0 && !prolong_via_map(c)) {
     const int sg = std::min((c->n_bslots + 255) / 256, kNumSMs * 4);
     if (c->fp32)
       k_coarse_slots<float><<<sg, 256, 0, s>>>(c->n_bslots, c->bcol, c->yvec32, static_cast<float*>(c->yslot), ks);
@@ -2209,7 +2224,10 @@ gdsw_status launch_prolong(Ctx* c, cudaStream_t s, const KrylovScalars* ks, cons
   if (!c->prolong) return GDSW_OK;
   const int grid = std::max(1, std::min((c->n + 255) / 256, kNumSMs * 8));
   k_prolong<T><<<grid, 256, 0, s>>>(c->n, c->pos_blk, c->brow_ptr, c->bcol_ptr, c->phi_off,
-                                    static_cast<const T*>(c->phi), static_cast<const T*>(c->yslot),
+                                    static_cast<const T*>(c->phi), prolong_via_map(c) ? c->bcol : nullptr,
+                                    !prolong_via_map(c) ? static_cast<const T*>(c->yslot)
+                                    : c->fp32 ? reinterpret_cast<const T*>(c->yvec32)
+                                              : reinterpret_cast<const T*>(c->yvec),
                                     static_cast<T*>(c->ubuf), ks, gate);
   GDSW_CK(cudaGetLastError());
   return GDSW_OK;

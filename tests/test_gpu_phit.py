@@ -91,3 +91,24 @@ def test_phiT_default_rule(make, want):
     h = _with(None, lambda: gpu_handle(prob, local_solver="ilu0" if prob.Z.shape[1] > 1 else "ic0"))
     assert h.stats()["phiT_wide"] == want
     h.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_prolongation_reads_y_by_map_or_slots(monkeypatch, precision, tol):
+    """Phi y beside the local solves (forced) reads y through the block-column map with
+    the column form and from the gathered slots with the wide form: the same values,
+    so the applies agree with each other to rounding and with the oracle."""
+    prob = P.elasticity_problem(18, 6)
+    monkeypatch.setenv("GDSW_PROLONG", "1")
+    hw = _with("wide", lambda: gpu_handle(prob, local_solver="ilu0", precision=precision))
+    hc = _with("cols", lambda: gpu_handle(prob, local_solver="ilu0", precision=precision))
+    for h, wide in ((hw, 1), (hc, 0)):
+        st = h.stats()
+        assert st["phi_beside_local"] == 1 and st["phiT_wide"] == wide
+    M = oracle_for(prob, local="ilu0")
+    r = np.random.default_rng(7).uniform(-1, 1, prob.A.n)
+    zw, zc = gpu_apply(hw, r), gpu_apply(hc, r)
+    assert relerr(zw, zc) <= tol
+    assert relerr(zc, M.apply(r)) <= (1e-10 if precision == "fp64" else 2e-5)
+    hw.close()
+    hc.close()
